@@ -1,0 +1,202 @@
+"""ORACLE -- test infrastructure only, never part of the product path.
+
+A plain, slow FP64 CPU implementation of the DGSEM residual, numerical fluxes, SSP-RK3
+stage and time-step bound of the paper's method (arXiv 2605.26388, Sec. 2, Sec. 3.1.1,
+App. A, App. B), written in C++ (``dg_oracle.cpp``) and loaded here with ctypes.  It
+shares no code with the CUDA library.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import it.
+
+Parity status of each function is stated in its docstring ("pinned by ..." or
+"parity unpinned").
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "dg_oracle.cpp")
+_LIB = os.path.join(_HERE, "_build", "liboracle.so")
+
+# enumerations of the oracle's own problem description (dg_oracle.cpp)
+EULER, NAVIER_STOKES, NS_REACTING = 0, 1, 2
+VOL_STRONG, VOL_WEAK, VOL_EC, VOL_CENTRAL = 0, 1, 2, 3
+SURF_RUSANOV, SURF_HLLC, SURF_HLL, SURF_EC, SURF_CENTRAL = 0, 1, 2, 3, 4
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library with g++ (-O2, OpenMP over elements)."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        cmd = ["g++", "-std=c++17", "-O2", "-fopenmp", "-fPIC", "-shared", _SRC, "-o", _LIB]
+        subprocess.run(cmd, check=True)
+    return _LIB
+
+
+class _Problem(C.Structure):
+    _fields_ = [
+        ("dim", C.c_int), ("N", C.c_int), ("nel", C.c_int * 3),
+        ("lo", C.c_double * 3), ("hi", C.c_double * 3),
+        ("equations", C.c_int), ("volume", C.c_int), ("surface", C.c_int),
+        ("gamma", C.c_double), ("mu", C.c_double), ("prandtl", C.c_double),
+        ("rho_floor", C.c_double), ("p_floor", C.c_double),
+    ]
+
+
+@dataclass
+class Problem:
+    """The oracle's description of one periodic Cartesian DGSEM problem."""
+    dim: int
+    N: int
+    nel: tuple
+    lo: tuple
+    hi: tuple
+    volume: int = VOL_STRONG
+    surface: int = SURF_RUSANOV
+    gamma: float = 1.4
+    equations: int = EULER
+    mu: float = 0.0
+    prandtl: float = 0.72
+    rho_floor: float = 0.0
+    p_floor: float = 0.0
+
+    @property
+    def nvars(self) -> int:
+        return self.dim + 2
+
+    @property
+    def n_elem(self) -> int:
+        n = 1
+        for l in range(self.dim):
+            n *= self.nel[l]
+        return n
+
+    @property
+    def n_nodes(self) -> int:
+        return (self.N + 1) ** self.dim
+
+    @property
+    def shape(self) -> tuple:
+        return (self.nvars, self.n_elem, self.n_nodes)
+
+    def _c(self) -> _Problem:
+        nel = list(self.nel) + [1] * (3 - len(self.nel))
+        lo = list(self.lo) + [0.0] * (3 - len(self.lo))
+        hi = list(self.hi) + [1.0] * (3 - len(self.hi))
+        return _Problem(self.dim, self.N, (C.c_int * 3)(*nel), (C.c_double * 3)(*lo),
+                        (C.c_double * 3)(*hi), self.equations, self.volume, self.surface,
+                        self.gamma, self.mu, self.prandtl, self.rho_floor, self.p_floor)
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        dp = C.POINTER(C.c_double)
+        pp = C.POINTER(_Problem)
+        _lib.orc_gll.argtypes = [C.c_int, dp, dp]
+        _lib.orc_dmat.argtypes = [C.c_int, dp]
+        _lib.orc_log_mean.argtypes = [C.c_double, C.c_double]
+        _lib.orc_log_mean.restype = C.c_double
+        _lib.orc_point_flux.argtypes = [C.c_int, C.c_int, C.c_double, dp, dp]
+        _lib.orc_two_point_flux.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, dp, dp, dp]
+        _lib.orc_rhs.argtypes = [pp, dp, dp]
+        _lib.orc_rk3_stage.argtypes = [pp, C.c_int, dp, dp, C.c_double, dp]
+        _lib.orc_rk3.argtypes = [pp, dp, C.c_double, C.c_int]
+        _lib.orc_max_dt.argtypes = [pp, dp, C.c_double, dp]
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise ValueError(f"oracle {what} rejected the problem (code {rc})")
+
+
+def gll(N: int):
+    """GLL nodes and weights (Sec. 3.1.1). Pinned by closed forms for N <= 4 and by
+    exact quadrature of monomials (tests/test_oracle_operators.py)."""
+    x = np.zeros(N + 1)
+    w = np.zeros(N + 1)
+    _check(lib().orc_gll(N, _ptr(x), _ptr(w)), "gll")
+    return x, w
+
+
+def dmat(N: int) -> np.ndarray:
+    """GLL differentiation matrix D_ij = l_j'(x_i). Pinned by polynomial exactness, the
+    SBP identity and D_00 = -N(N+1)/4."""
+    D = np.zeros((N + 1) * (N + 1))
+    _check(lib().orc_dmat(N, _ptr(D)), "dmat")
+    return D.reshape(N + 1, N + 1)
+
+
+def log_mean(a: float, b: float) -> float:
+    """Logarithmic mean (a-b)/(ln a - ln b) (App. A). Pinned by a mpmath-free
+    high-precision series check and by its closed-form special cases."""
+    return lib().orc_log_mean(a, b)
+
+
+def point_flux(dim: int, l: int, gamma: float, u) -> np.ndarray:
+    """Cartesian Euler flux F^l(U) (Sec. 2)."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    F = np.zeros(dim + 2)
+    lib().orc_point_flux(dim, l, gamma, _ptr(u), _ptr(F))
+    return F
+
+
+def two_point_flux(kind: int, dim: int, l: int, gamma: float, uL, uR) -> np.ndarray:
+    """Numerical two-point flux: kind = -1 Ranocha EC volume flux, else a SURF_* kind."""
+    uL = np.ascontiguousarray(uL, dtype=np.float64)
+    uR = np.ascontiguousarray(uR, dtype=np.float64)
+    F = np.zeros(dim + 2)
+    lib().orc_two_point_flux(kind, dim, l, gamma, _ptr(uL), _ptr(uR), _ptr(F))
+    return F
+
+
+def rhs(P: Problem, U: np.ndarray) -> np.ndarray:
+    """Semi-discrete residual L(U) (Eqs. vol_weak / vol_split / surf_int). State layout
+    U[var, elem, node], elements x-fastest, nodes i-fastest."""
+    U = np.ascontiguousarray(U, dtype=np.float64).reshape(P.shape)
+    dU = np.zeros_like(U)
+    c = P._c()
+    _check(lib().orc_rhs(C.byref(c), _ptr(U), _ptr(dU)), "rhs")
+    return dU
+
+
+def rk3_stage(P: Problem, stage: int, Un: np.ndarray, Uprev: np.ndarray, dt: float):
+    """One Shu-Osher SSP-RK3 stage (App. B)."""
+    Un = np.ascontiguousarray(Un, dtype=np.float64).reshape(P.shape)
+    Uprev = np.ascontiguousarray(Uprev, dtype=np.float64).reshape(P.shape)
+    out = np.zeros_like(Un)
+    c = P._c()
+    _check(lib().orc_rk3_stage(C.byref(c), stage, _ptr(Un), _ptr(Uprev), dt, _ptr(out)),
+           "rk3_stage")
+    return out
+
+
+def rk3(P: Problem, U: np.ndarray, dt: float, n_steps: int) -> np.ndarray:
+    """n_steps SSP-RK3 steps; returns the new state (the input is not modified)."""
+    U = np.array(U, dtype=np.float64, order="C").reshape(P.shape)
+    c = P._c()
+    _check(lib().orc_rk3(C.byref(c), _ptr(U), dt, n_steps), "rk3")
+    return U
+
+
+def max_dt(P: Problem, U: np.ndarray, cfl: float) -> float:
+    """Convective time-step bound dt = cfl dx_min / ((2N+1) lambda_max) (Eq. dt_hyp)."""
+    U = np.ascontiguousarray(U, dtype=np.float64).reshape(P.shape)
+    out = np.zeros(1)
+    c = P._c()
+    _check(lib().orc_max_dt(C.byref(c), _ptr(U), cfl, _ptr(out)), "max_dt")
+    return float(out[0])

@@ -1,0 +1,596 @@
+// dg_oracle.cpp -- ORACLE: test infrastructure, not part of the product path.
+//
+// A plain, slow, FP64 CPU implementation of what the DGSEM hot path computes: the
+// semi-discrete residual dU/dt = L(U) of the compressible Euler equations on periodic
+// Cartesian meshes (2D and 3D), its numerical fluxes, the SSP-RK3 stage update and the
+// explicit time-step bound.  It shares no source, header, table or helper with the CUDA
+// path, and the CUDA path never loads it.  Only the test-suite, the smoke check and the
+// benchmark's CPU-baseline leg may load it.
+//
+// Every function names the passage of the paper (arXiv 2605.26388) it follows:
+//   Sec. 2           Euler equations, ideal-gas closure p = (gamma-1)(E - rho|u|^2/2)
+//   Sec. 3.1.1       Eq. vol_weak (strong-form volume term), Eq. vol_split (two-point
+//                    flux-differencing volume term), surface fluxes (LF / HLL), Eq. surf_int
+//                    (surface lifting and Jacobian rescale)
+//   App. A           Eq. split_form_3D and the Ranocha entropy-conservative two-point flux
+//   App. B           SSP-RK in Shu-Osher form; convective time-step bound Delta t_C
+// Readings of passages the paper leaves open are marked READING below.
+//
+// Loops are written per element, per node, per direction, exactly in the order the
+// formulas are stated; there is no blocking, fusion or reordering.  The element loop may
+// run on several OpenMP threads: each element writes only its own residual, so the
+// arithmetic per element is the same on one thread or many.
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+namespace {
+
+// ---------------------------------------------------------------------------------------
+// Problem description (the oracle's own; it mirrors nothing from the CUDA library).
+// ---------------------------------------------------------------------------------------
+enum { ORC_EULER = 0, ORC_NAVIER_STOKES = 1, ORC_NS_REACTING = 2 };
+enum { ORC_VOL_STRONG = 0, ORC_VOL_WEAK = 1, ORC_VOL_EC = 2, ORC_VOL_CENTRAL = 3 };
+enum { ORC_SURF_RUSANOV = 0, ORC_SURF_HLLC = 1, ORC_SURF_HLL = 2, ORC_SURF_EC = 3,
+       ORC_SURF_CENTRAL = 4 };
+
+}  // namespace
+
+extern "C" {
+
+struct OrcProblem {
+  int dim;             // 2 or 3
+  int N;               // polynomial degree; N+1 GLL nodes per direction
+  int nel[3];          // elements per direction (nel[2] = 1 in 2D)
+  double lo[3], hi[3]; // periodic box
+  int equations;       // ORC_EULER (others are added with the viscous and reacting paths)
+  int volume;          // ORC_VOL_*
+  int surface;         // ORC_SURF_*
+  double gamma;        // ratio of specific heats
+  double mu, prandtl;  // viscous parameters (unused for Euler)
+  double rho_floor, p_floor;  // <= 0 disables the positivity floor
+};
+
+}  // extern "C"
+
+namespace {
+
+// ---------------------------------------------------------------------------------------
+// Legendre polynomials and the Gauss-Lobatto-Legendre rule (Sec. 3.1.1: "collocated at
+// the (P+1)^d tensor-product GLL nodes with weights w_i").  Nodes are -1, +1 and the
+// roots of P_N'; weights w_i = 2 / (N (N+1) P_N(x_i)^2).  Newton iteration in long
+// double on q(x) = P_{N+1}(x) - P_{N-1}(x), which vanishes exactly at the GLL nodes.
+// ---------------------------------------------------------------------------------------
+void legendre(int n, long double x, long double& Pn, long double& Pnm1) {
+  // three-term recurrence (k+1) P_{k+1} = (2k+1) x P_k - k P_{k-1}
+  long double p0 = 1.0L, p1 = x;
+  if (n == 0) { Pn = p0; Pnm1 = 0.0L; return; }
+  for (int k = 1; k < n; ++k) {
+    long double p2 = ((2 * k + 1) * x * p1 - k * p0) / (k + 1);
+    p0 = p1;
+    p1 = p2;
+  }
+  Pn = p1;
+  Pnm1 = p0;
+}
+
+void gll_rule(int N, std::vector<long double>& x, std::vector<long double>& w) {
+  x.assign(N + 1, 0.0L);
+  w.assign(N + 1, 0.0L);
+  const long double pi = 3.141592653589793238462643383279502884L;
+  for (int i = 0; i <= N; ++i) {
+    long double xi = -cosl(pi * i / N);  // Chebyshev-Gauss-Lobatto start
+    if (i == 0) xi = -1.0L;
+    else if (i == N) xi = 1.0L;
+    else {
+      for (int it = 0; it < 100; ++it) {
+        long double PN, PNm1, PNp1, tmp;
+        legendre(N, xi, PN, PNm1);
+        legendre(N + 1, xi, PNp1, tmp);
+        long double q = PNp1 - PNm1;       // (2N+1)/... * (x^2-1) P_N'(x) up to a factor
+        long double dq = (2 * N + 1) * PN; // d/dx (P_{N+1} - P_{N-1}) = (2N+1) P_N
+        long double dx = q / dq;
+        xi -= dx;
+        if (fabsl(dx) < 1e-19L) break;
+      }
+    }
+    x[i] = xi;
+    long double PN, PNm1;
+    legendre(N, xi, PN, PNm1);
+    w[i] = 2.0L / (N * (N + 1) * PN * PN);
+  }
+}
+
+// Lagrange differentiation matrix D_ij = l_j'(x_i) on the GLL nodes (Sec. 3.1.1: "the
+// one-dimensional GLL differentiation matrix D"), from barycentric weights
+// lambda_j = 1 / prod_{k != j} (x_j - x_k):  D_ij = (lambda_j / lambda_i) / (x_i - x_j)
+// for i != j, and the diagonal by the negative row sum (derivative of a constant is 0).
+void diff_matrix(int N, const std::vector<long double>& x, std::vector<long double>& D) {
+  const int n = N + 1;
+  std::vector<long double> lam(n, 1.0L);
+  for (int j = 0; j < n; ++j)
+    for (int k = 0; k < n; ++k)
+      if (k != j) lam[j] *= (x[j] - x[k]);
+  for (int j = 0; j < n; ++j) lam[j] = 1.0L / lam[j];
+  D.assign(n * n, 0.0L);
+  for (int i = 0; i < n; ++i) {
+    long double rowsum = 0.0L;
+    for (int j = 0; j < n; ++j) {
+      if (i == j) continue;
+      D[i * n + j] = (lam[j] / lam[i]) / (x[i] - x[j]);
+      rowsum += D[i * n + j];
+    }
+    D[i * n + i] = -rowsum;
+  }
+}
+
+// Operators of one degree, rounded to double once.
+struct Ops {
+  int N = 0;
+  std::vector<double> x, w, D;  // D row-major: D[i*(N+1)+m]
+  explicit Ops(int N_) : N(N_) {
+    std::vector<long double> xl, wl, Dl;
+    gll_rule(N, xl, wl);
+    diff_matrix(N, xl, Dl);
+    x.assign(xl.begin(), xl.end());
+    w.assign(wl.begin(), wl.end());
+    D.assign(Dl.begin(), Dl.end());
+  }
+};
+
+// ---------------------------------------------------------------------------------------
+// Euler physics (Sec. 2): U = (rho, rho u, rho v[, rho w], E), F^l the Cartesian flux in
+// direction l, p = (gamma-1)(E - rho|u|^2/2), a = sqrt(gamma p / rho).
+// ---------------------------------------------------------------------------------------
+struct Prim {
+  double rho, v[3], p;
+};
+
+Prim primitives(int dim, const double* u, double gamma) {
+  Prim q;
+  q.rho = u[0];
+  double kin = 0.0;
+  for (int d = 0; d < 3; ++d) q.v[d] = 0.0;
+  for (int d = 0; d < dim; ++d) {
+    q.v[d] = u[1 + d] / q.rho;
+    kin += u[1 + d] * q.v[d];
+  }
+  q.p = (gamma - 1.0) * (u[dim + 1] - 0.5 * kin);
+  return q;
+}
+
+void euler_flux(int dim, int l, const double* u, double gamma, double* F) {
+  Prim q = primitives(dim, u, gamma);
+  F[0] = u[1 + l];
+  for (int d = 0; d < dim; ++d) F[1 + d] = u[1 + l] * q.v[d] + (d == l ? q.p : 0.0);
+  F[dim + 1] = (u[dim + 1] + q.p) * q.v[l];
+}
+
+double sound_speed(const Prim& q, double gamma) { return std::sqrt(gamma * q.p / q.rho); }
+
+// Logarithmic mean {{a}}^ln = (a_L - a_R) / (ln a_L - ln a_R) (App. A, below the Ranocha
+// flux).  The paper is silent at a_L = a_R; the definition's limit there is a.  Written
+// in long double, with ln a_L - ln a_R = log1p((a_L - a_R)/a_R) when the ratio is near 1,
+// so that the quotient keeps full double accuracy however close a_L and a_R are.
+double log_mean(double aL, double aR) {
+  if (aL == aR) return aL;
+  long double a = aL, b = aR;
+  long double d = a - b;
+  long double r = d / b;
+  long double lnratio = (fabsl(r) < 0.5L) ? log1pl(r) : (logl(a) - logl(b));
+  return (double)(d / lnratio);
+}
+
+// Ranocha's entropy-conservative, kinetic-energy-preserving two-point flux in direction
+// e_l (App. A, Eq. split_form_3D and the flux listed after it).
+// READING: the printed energy component is not consistent (F#(U,U) != F(U)); we use the
+// published form  f_E = f_rho (1/((gamma-1) {{beta}}^ln) + u_L.u_R / 2)
+//                      + (p_L u_{l,R} + p_R u_{l,L}) / 2,   beta = rho/p = 1/T,
+// which is the unique f_E satisfying Tadmor's entropy-conservation condition given the
+// printed f_rho and f_m (checked in the tests).
+void ec_flux(int dim, int l, const double* uL, const double* uR, double gamma, double* F) {
+  Prim L = primitives(dim, uL, gamma), R = primitives(dim, uR, gamma);
+  double rho_ln = log_mean(L.rho, R.rho);
+  double beta_ln = log_mean(L.rho / L.p, R.rho / R.p);
+  double vavg[3], vLvR = 0.0;
+  for (int d = 0; d < 3; ++d) vavg[d] = 0.5 * (L.v[d] + R.v[d]);
+  for (int d = 0; d < dim; ++d) vLvR += L.v[d] * R.v[d];
+  double pavg = 0.5 * (L.p + R.p);
+  double frho = rho_ln * vavg[l];
+  F[0] = frho;
+  for (int d = 0; d < dim; ++d) F[1 + d] = frho * vavg[d] + (d == l ? pavg : 0.0);
+  F[dim + 1] = frho * (1.0 / ((gamma - 1.0) * beta_ln) + 0.5 * vLvR) +
+               0.5 * (L.p * R.v[l] + R.p * L.v[l]);
+}
+
+// Central two-point flux (F(U_L) + F(U_R))/2: with it the flux-differencing form equals
+// the strong form (App. A, text after Eq. split_form_3D).  Test option only.
+void central_flux(int dim, int l, const double* uL, const double* uR, double gamma,
+                  double* F) {
+  double FL[8], FR[8];
+  euler_flux(dim, l, uL, gamma, FL);
+  euler_flux(dim, l, uR, gamma, FR);
+  for (int v = 0; v < dim + 2; ++v) F[v] = 0.5 * (FL[v] + FR[v]);
+}
+
+// Local Lax-Friedrichs (Rusanov) flux, the paper's "(local) Lax-Friedrichs" surface flux
+// (Sec. 3.1.1 "Surface Fluxes"; Sec. 4 case set-ups).
+// READING: dissipation speed lambda = max(|u_{l,L}| + a_L, |u_{l,R}| + a_R).
+void rusanov_flux(int dim, int l, const double* uL, const double* uR, double gamma,
+                  double* F) {
+  Prim L = primitives(dim, uL, gamma), R = primitives(dim, uR, gamma);
+  double lam = std::fmax(std::fabs(L.v[l]) + sound_speed(L, gamma),
+                         std::fabs(R.v[l]) + sound_speed(R, gamma));
+  double FL[8], FR[8];
+  euler_flux(dim, l, uL, gamma, FL);
+  euler_flux(dim, l, uR, gamma, FR);
+  for (int v = 0; v < dim + 2; ++v) F[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * lam * (uR[v] - uL[v]);
+}
+
+// Roe-averaged normal velocity and sound speed, used for the Davis/Einfeldt wave-speed
+// estimates of HLL and HLLC.
+void roe_speeds(int dim, int l, const double* uL, const double* uR, double gamma,
+                double& SL, double& SR) {
+  Prim L = primitives(dim, uL, gamma), R = primitives(dim, uR, gamma);
+  double sL = std::sqrt(L.rho), sR = std::sqrt(R.rho);
+  double HL = (uL[dim + 1] + L.p) / L.rho, HR = (uR[dim + 1] + R.p) / R.rho;
+  double vt[3], v2 = 0.0;
+  for (int d = 0; d < dim; ++d) {
+    vt[d] = (sL * L.v[d] + sR * R.v[d]) / (sL + sR);
+    v2 += vt[d] * vt[d];
+  }
+  double Ht = (sL * HL + sR * HR) / (sL + sR);
+  double at = std::sqrt((gamma - 1.0) * (Ht - 0.5 * v2));
+  double aL = sound_speed(L, gamma), aR = sound_speed(R, gamma);
+  SL = std::fmin(L.v[l] - aL, vt[l] - at);
+  SR = std::fmax(R.v[l] + aR, vt[l] + at);
+}
+
+// HLL flux (Harten, Lax, van Leer), the paper's second surface-flux option (Sec. 3.1.1).
+void hll_flux(int dim, int l, const double* uL, const double* uR, double gamma, double* F) {
+  double SL, SR;
+  roe_speeds(dim, l, uL, uR, gamma, SL, SR);
+  double FL[8], FR[8];
+  euler_flux(dim, l, uL, gamma, FL);
+  euler_flux(dim, l, uR, gamma, FR);
+  const int nv = dim + 2;
+  if (SL >= 0.0) { for (int v = 0; v < nv; ++v) F[v] = FL[v]; return; }
+  if (SR <= 0.0) { for (int v = 0; v < nv; ++v) F[v] = FR[v]; return; }
+  for (int v = 0; v < nv; ++v)
+    F[v] = (SR * FL[v] - SL * FR[v] + SL * SR * (uR[v] - uL[v])) / (SR - SL);
+}
+
+// HLLC flux (Toro, Spruce and Speares 1994) with the same Davis/Einfeldt speeds.
+// READING: the paper names LF and HLL only; HLLC is the surface flux of the 3D
+// Taylor-Green workload.  Branches: S_L >= 0 -> F_L; S* >= 0 -> F*_L; S_R > 0 -> F*_R;
+// else F_R.  Star states U*_K = rho_K (S_K - u_K)/(S_K - S*) (1, S* e_l + tangential u,
+// E_K/rho_K + (S* - u_K)(S* + p_K/(rho_K (S_K - u_K)))).
+void hllc_flux(int dim, int l, const double* uL, const double* uR, double gamma, double* F) {
+  double SL, SR;
+  roe_speeds(dim, l, uL, uR, gamma, SL, SR);
+  Prim L = primitives(dim, uL, gamma), R = primitives(dim, uR, gamma);
+  double FL[8], FR[8];
+  euler_flux(dim, l, uL, gamma, FL);
+  euler_flux(dim, l, uR, gamma, FR);
+  const int nv = dim + 2;
+  double uLn = L.v[l], uRn = R.v[l];
+  double Sstar = (R.p - L.p + L.rho * uLn * (SL - uLn) - R.rho * uRn * (SR - uRn)) /
+                 (L.rho * (SL - uLn) - R.rho * (SR - uRn));
+  auto star = [&](const Prim& K, const double* uK, double SK, double* Us) {
+    double fac = K.rho * (SK - K.v[l]) / (SK - Sstar);
+    Us[0] = fac;
+    for (int d = 0; d < dim; ++d) Us[1 + d] = fac * (d == l ? Sstar : K.v[d]);
+    Us[dim + 1] = fac * (uK[dim + 1] / K.rho +
+                         (Sstar - K.v[l]) * (Sstar + K.p / (K.rho * (SK - K.v[l]))));
+  };
+  double Us[8];
+  if (SL >= 0.0) {
+    for (int v = 0; v < nv; ++v) F[v] = FL[v];
+  } else if (Sstar >= 0.0) {
+    star(L, uL, SL, Us);
+    for (int v = 0; v < nv; ++v) F[v] = FL[v] + SL * (Us[v] - uL[v]);
+  } else if (SR > 0.0) {
+    star(R, uR, SR, Us);
+    for (int v = 0; v < nv; ++v) F[v] = FR[v] + SR * (Us[v] - uR[v]);
+  } else {
+    for (int v = 0; v < nv; ++v) F[v] = FR[v];
+  }
+}
+
+void surface_flux(int kind, int dim, int l, const double* uL, const double* uR, double gamma,
+                  double* F) {
+  switch (kind) {
+    case ORC_SURF_RUSANOV: rusanov_flux(dim, l, uL, uR, gamma, F); break;
+    case ORC_SURF_HLLC: hllc_flux(dim, l, uL, uR, gamma, F); break;
+    case ORC_SURF_HLL: hll_flux(dim, l, uL, uR, gamma, F); break;
+    case ORC_SURF_EC: ec_flux(dim, l, uL, uR, gamma, F); break;
+    default: central_flux(dim, l, uL, uR, gamma, F); break;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Mesh indexing.  Element order is lexicographic with x fastest; node order within an
+// element is lexicographic with i (the x index) fastest.  The state is SoA:
+// U[(v * n_elem + e) * n_nodes + node].
+// ---------------------------------------------------------------------------------------
+struct Mesh {
+  int dim, N, n1, nel[3], n_elem, n_nodes;
+  double dx[3];
+  explicit Mesh(const OrcProblem& P) {
+    dim = P.dim;
+    N = P.N;
+    n1 = N + 1;
+    n_elem = 1;
+    n_nodes = 1;
+    for (int l = 0; l < 3; ++l) {
+      nel[l] = (l < dim) ? P.nel[l] : 1;
+      dx[l] = (l < dim) ? (P.hi[l] - P.lo[l]) / nel[l] : 1.0;
+      n_elem *= nel[l];
+      if (l < dim) n_nodes *= n1;
+    }
+  }
+  int elem(const int c[3]) const { return c[0] + nel[0] * (c[1] + nel[1] * c[2]); }
+  void elem_coords(int e, int c[3]) const {
+    c[0] = e % nel[0];
+    c[1] = (e / nel[0]) % nel[1];
+    c[2] = e / (nel[0] * nel[1]);
+  }
+  int node(const int ijk[3]) const { return ijk[0] + n1 * (ijk[1] + n1 * ijk[2]); }
+  void node_coords(int nd, int ijk[3]) const {
+    ijk[0] = nd % n1;
+    ijk[1] = (nd / n1) % n1;
+    ijk[2] = nd / (n1 * n1);
+    if (dim == 2) ijk[2] = 0;
+  }
+  // periodic neighbour of element e in direction l, offset +1 or -1
+  int neighbour(int e, int l, int off) const {
+    int c[3];
+    elem_coords(e, c);
+    c[l] = (c[l] + off + nel[l]) % nel[l];
+    return elem(c);
+  }
+};
+
+void load_node(const Mesh& M, int nv, const double* U, int e, int nd, double* u) {
+  for (int v = 0; v < nv; ++v) u[v] = U[((size_t)v * M.n_elem + e) * M.n_nodes + nd];
+}
+
+// ---------------------------------------------------------------------------------------
+// Semi-discrete Euler residual on one element (Sec. 3.1.1).
+//   strong (Eq. vol_weak):     R_i = -sum_l (2/dx_l) sum_m D_{i_l m} F^l(U_m)
+//   weak (by parts, SBP):      R_i =  sum_l (2/dx_l) sum_m (w_m/w_{i_l}) D_{m i_l} F^l(U_m)
+//   two-point (Eq. vol_split): R_i = -sum_l (2/dx_l) 2 sum_m D_{i_l m} F#^l(U_i, U_m)
+// On the affine Cartesian element J = prod_l dx_l/2 and Ja^l = J (2/dx_l) e_l, so
+// (1/J) D Ja^l.F = (2/dx_l) D F^l and the averaged metric in Eq. vol_split is exact.
+// Surface (Eq. surf_int): with F* = F*(U_L, U_R; e_l) computed left-to-right,
+//   upper face (i_l = N):  R -= (2/dx_l)/w_N (F* - F^l(U_own))
+//   lower face (i_l = 0):  R += (2/dx_l)/w_0 (F* - F^l(U_own))
+// and in the weak form only F* is lifted (the volume term already carries F^l(U_own)).
+// ---------------------------------------------------------------------------------------
+void euler_element_residual(const OrcProblem& P, const Mesh& M, const Ops& ops,
+                            const double* U, int e, double* dU) {
+  const int dim = M.dim, n1 = M.n1, N = M.N, nv = dim + 2;
+  const double gamma = P.gamma;
+  std::vector<double> R((size_t)M.n_nodes * nv, 0.0);
+  double ui[8], um[8], F[8];
+
+  // volume term
+  for (int nd = 0; nd < M.n_nodes; ++nd) {
+    int ijk[3];
+    M.node_coords(nd, ijk);
+    load_node(M, nv, U, e, nd, ui);
+    for (int l = 0; l < dim; ++l) {
+      const double s = 2.0 / M.dx[l];
+      const int il = ijk[l];
+      for (int m = 0; m < n1; ++m) {
+        int mk[3] = {ijk[0], ijk[1], ijk[2]};
+        mk[l] = m;
+        load_node(M, nv, U, e, M.node(mk), um);
+        if (P.volume == ORC_VOL_STRONG) {
+          euler_flux(dim, l, um, gamma, F);
+          for (int v = 0; v < nv; ++v) R[nd * nv + v] -= s * ops.D[il * n1 + m] * F[v];
+        } else if (P.volume == ORC_VOL_WEAK) {
+          euler_flux(dim, l, um, gamma, F);
+          for (int v = 0; v < nv; ++v)
+            R[nd * nv + v] += s * (ops.w[m] / ops.w[il]) * ops.D[m * n1 + il] * F[v];
+        } else {
+          if (P.volume == ORC_VOL_EC) ec_flux(dim, l, ui, um, gamma, F);
+          else central_flux(dim, l, ui, um, gamma, F);
+          for (int v = 0; v < nv; ++v) R[nd * nv + v] -= s * 2.0 * ops.D[il * n1 + m] * F[v];
+        }
+      }
+    }
+  }
+
+  // surface term: both faces of each direction, every face node
+  const bool weak = (P.volume == ORC_VOL_WEAK);
+  for (int l = 0; l < dim; ++l) {
+    const double s = 2.0 / M.dx[l];
+    for (int nd = 0; nd < M.n_nodes; ++nd) {
+      int ijk[3];
+      M.node_coords(nd, ijk);
+      if (ijk[l] != N && ijk[l] != 0) continue;
+      double uown[8], unbr[8], Fs[8], Fown[8];
+      load_node(M, nv, U, e, nd, uown);
+      euler_flux(dim, l, uown, gamma, Fown);
+      if (ijk[l] == N) {  // upper face: own state is the left state
+        int nk[3] = {ijk[0], ijk[1], ijk[2]};
+        nk[l] = 0;
+        load_node(M, nv, U, M.neighbour(e, l, +1), M.node(nk), unbr);
+        surface_flux(P.surface, dim, l, uown, unbr, gamma, Fs);
+        for (int v = 0; v < nv; ++v)
+          R[nd * nv + v] -= s / ops.w[N] * (Fs[v] - (weak ? 0.0 : Fown[v]));
+      }
+      if (ijk[l] == 0) {  // lower face: own state is the right state
+        int nk[3] = {ijk[0], ijk[1], ijk[2]};
+        nk[l] = N;
+        load_node(M, nv, U, M.neighbour(e, l, -1), M.node(nk), unbr);
+        surface_flux(P.surface, dim, l, unbr, uown, gamma, Fs);
+        for (int v = 0; v < nv; ++v)
+          R[nd * nv + v] += s / ops.w[0] * (Fs[v] - (weak ? 0.0 : Fown[v]));
+      }
+    }
+  }
+
+  for (int nd = 0; nd < M.n_nodes; ++nd)
+    for (int v = 0; v < nv; ++v)
+      dU[((size_t)v * M.n_elem + e) * M.n_nodes + nd] = R[nd * nv + v];
+}
+
+int n_vars(const OrcProblem& P) { return P.dim + 2; }
+
+int check_problem(const OrcProblem& P) {
+  if (P.dim != 2 && P.dim != 3) return -1;
+  if (P.N < 1 || P.N > 15) return -1;
+  for (int l = 0; l < P.dim; ++l)
+    if (P.nel[l] < 1 || !(P.hi[l] > P.lo[l])) return -1;
+  if (P.equations != ORC_EULER) return -6;
+  return 0;
+}
+
+void residual(const OrcProblem& P, const double* U, double* dU) {
+  Mesh M(P);
+  Ops ops(P.N);
+#pragma omp parallel for schedule(static)
+  for (int e = 0; e < M.n_elem; ++e) euler_element_residual(P, M, ops, U, e, dU);
+}
+
+// Positivity floor (Sec. 4.1 and 4.2 set-ups: "a per-stage positivity floor enforces
+// rho >= ..., p >= ...").  READING: the paper does not say how; here rho is raised to
+// rho_floor (momentum kept), then E is reset so that p = p_floor where p < p_floor.
+void positivity_floor(const OrcProblem& P, double* U) {
+  if (!(P.rho_floor > 0.0) && !(P.p_floor > 0.0)) return;
+  Mesh M(P);
+  const int dim = M.dim, nv = dim + 2;
+  const size_t stride = (size_t)M.n_elem * M.n_nodes;
+  for (size_t q = 0; q < stride; ++q) {
+    double u[8];
+    for (int v = 0; v < nv; ++v) u[v] = U[v * stride + q];
+    if (P.rho_floor > 0.0 && u[0] < P.rho_floor) u[0] = P.rho_floor;
+    Prim pr = primitives(dim, u, P.gamma);
+    if (P.p_floor > 0.0 && pr.p < P.p_floor) {
+      double kin = 0.0;
+      for (int d = 0; d < dim; ++d) kin += u[1 + d] * u[1 + d] / u[0];
+      u[dim + 1] = P.p_floor / (P.gamma - 1.0) + 0.5 * kin;
+    }
+    for (int v = 0; v < nv; ++v) U[v * stride + q] = u[v];
+  }
+}
+
+}  // namespace
+
+// =======================================================================================
+// C entry points used by the Python test harness (ctypes).  Return 0 on success and a
+// negative code on a bad description; they never abort.
+// =======================================================================================
+extern "C" {
+
+int orc_gll(int N, double* x, double* w) {
+  if (N < 1 || N > 15) return -1;
+  std::vector<long double> xl, wl;
+  gll_rule(N, xl, wl);
+  for (int i = 0; i <= N; ++i) { x[i] = (double)xl[i]; w[i] = (double)wl[i]; }
+  return 0;
+}
+
+int orc_dmat(int N, double* D) {
+  if (N < 1 || N > 15) return -1;
+  std::vector<long double> xl, wl, Dl;
+  gll_rule(N, xl, wl);
+  diff_matrix(N, xl, Dl);
+  for (int i = 0; i < (N + 1) * (N + 1); ++i) D[i] = (double)Dl[i];
+  return 0;
+}
+
+int orc_nvars(const OrcProblem* P) { return n_vars(*P); }
+
+double orc_log_mean(double a, double b) { return log_mean(a, b); }
+
+// Point fluxes in direction l for one (left, right) pair of states, for the tests.
+int orc_point_flux(int dim, int l, double gamma, const double* u, double* F) {
+  euler_flux(dim, l, u, gamma, F);
+  return 0;
+}
+int orc_two_point_flux(int kind, int dim, int l, double gamma, const double* uL,
+                       const double* uR, double* F) {
+  if (kind == -1) ec_flux(dim, l, uL, uR, gamma, F);
+  else surface_flux(kind, dim, l, uL, uR, gamma, F);
+  return 0;
+}
+
+// dU/dt = L(U) (Appendix B, Eq. for the semi-discrete system).
+int orc_rhs(const OrcProblem* P, const double* U, double* dU) {
+  int rc = check_problem(*P);
+  if (rc) return rc;
+  residual(*P, U, dU);
+  return 0;
+}
+
+// One SSP-RK3 stage in Shu-Osher form (App. B: U^(i) = sum_k alpha_ik U^(k) + dt beta_ik
+// L(U^(k)); the three-stage third-order scheme of Shu and Osher, whose coefficients the
+// paper cites but does not print):
+//   stage 1: U1 = Un + dt L(Un)
+//   stage 2: U2 = 3/4 Un + 1/4 (U1 + dt L(U1))
+//   stage 3: U3 = 1/3 Un + 2/3 (U2 + dt L(U2))
+// followed by the positivity floor when it is enabled.
+int orc_rk3_stage(const OrcProblem* P, int stage, const double* Un, const double* Uprev,
+                  double dt, double* Uout) {
+  int rc = check_problem(*P);
+  if (rc) return rc;
+  if (stage < 1 || stage > 3) return -1;
+  Mesh M(*P);
+  const size_t n = (size_t)n_vars(*P) * M.n_elem * M.n_nodes;
+  std::vector<double> L(n);
+  residual(*P, Uprev, L.data());
+  for (size_t q = 0; q < n; ++q) {
+    if (stage == 1) Uout[q] = Un[q] + dt * L[q];
+    else if (stage == 2) Uout[q] = 0.75 * Un[q] + 0.25 * (Uprev[q] + dt * L[q]);
+    else Uout[q] = (1.0 / 3.0) * Un[q] + (2.0 / 3.0) * (Uprev[q] + dt * L[q]);
+  }
+  positivity_floor(*P, Uout);
+  return 0;
+}
+
+// n_steps full SSP-RK3 steps, in place.
+int orc_rk3(const OrcProblem* P, double* U, double dt, int n_steps) {
+  int rc = check_problem(*P);
+  if (rc) return rc;
+  Mesh M(*P);
+  const size_t n = (size_t)n_vars(*P) * M.n_elem * M.n_nodes;
+  std::vector<double> U1(n), U2(n);
+  for (int s = 0; s < n_steps; ++s) {
+    orc_rk3_stage(P, 1, U, U, dt, U1.data());
+    orc_rk3_stage(P, 2, U, U1.data(), dt, U2.data());
+    orc_rk3_stage(P, 3, U, U2.data(), dt, U);
+  }
+  return 0;
+}
+
+// Convective time-step bound (Sec. 3.1.2 Eq. dt_hyp; App. B):
+//   dt = cfl * dx_min / ((2N+1) lambda_max),  lambda_max = max over nodes of |u| + a.
+// READING: |u| is the speed (vector magnitude); the SSP coefficient of SSP-RK3 is 1, so
+// cfl multiplies nothing else; dx_min is the smallest element edge.
+int orc_max_dt(const OrcProblem* P, const double* U, double cfl, double* dt) {
+  int rc = check_problem(*P);
+  if (rc) return rc;
+  Mesh M(*P);
+  const int dim = M.dim, nv = dim + 2;
+  const size_t stride = (size_t)M.n_elem * M.n_nodes;
+  double lam = 0.0;
+  for (size_t q = 0; q < stride; ++q) {
+    double u[8];
+    for (int v = 0; v < nv; ++v) u[v] = U[v * stride + q];
+    Prim pr = primitives(dim, u, P->gamma);
+    double speed = 0.0;
+    for (int d = 0; d < dim; ++d) speed += pr.v[d] * pr.v[d];
+    lam = std::fmax(lam, std::sqrt(speed) + sound_speed(pr, P->gamma));
+  }
+  double dxmin = M.dx[0];
+  for (int l = 1; l < dim; ++l) dxmin = std::fmin(dxmin, M.dx[l]);
+  *dt = cfl * dxmin / ((2 * P->N + 1) * lam);
+  return 0;
+}
+
+}  // extern "C"
