@@ -1,0 +1,319 @@
+"""Benchmark: RK-stage DOF-updates/s of the fused DGSEM stage on one B300.
+
+Workload (the 3D Taylor-Green case): compressible Euler, DGSEM N = 4 (125 GLL nodes per
+element), 64^3 periodic elements on [0, 2pi]^3, Taylor-Green vortex at Ma = 0.1,
+Ranocha two-point flux-differencing volume term, HLLC surface flux, SSP-RK3 with a fixed
+dt from the CFL-0.5 bound.  163,840,000 DOF; a step is one SSP-RK3 step (3 fused stage
+launches) = 491,520,000 DOF-updates.  The headline runs the FP32-flux / FP64-state path;
+the plain FP64 path is measured beside it.
+
+Timing: W untimed warm-up steps, then K steps replayed from a CUDA graph, bracketed by
+CUDA events on the solver's stream with a device synchronize (and a barrier under
+torchrun) on both sides.  The three 1.31 GB state buffers exceed the 126 MB L2, so no
+flush is needed between steps.  Multi-GPU: independent replicas (the path has no data
+exchange on one box), value = all ranks' DOF-updates / max time.
+
+`--impl reference` times the plain CPU oracle (the only other place this script runs
+oracle code) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NEL, N, GAMMA, MACH, CFL = 64, 4, 1.4, 0.1, 0.5
+NV = 5
+NP = (N + 1) ** 3
+DOF = NEL ** 3 * NP * NV
+BYTES_PER_DOF_UPDATE = (16 + 24 + 24) / 3.0  # stage 1 reads U^n, writes U^1; stages 2-3 read 2, write 1
+WORKLOAD = "tgv3d_euler_N4_64cube_ec_hllc_ssprk3"
+
+# DRAM bytes per stage launch from the committed ncu capture of the current kernel
+# (profiles/); None when the kernel changed after the capture.
+TRAFFIC_PER_LAUNCH = {"fp32_mixed": None, "fp64": None}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[3:7]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def oracle_sample(seconds_hint: float = 10.0):
+    """Time the plain FP64 CPU oracle on a bounded sample of the same workload: full SSP-RK3
+    steps of the Taylor-Green N=4 EC/HLLC problem on a 12^3 sub-mesh (same per-DOF work)."""
+    import oracle
+    from paper_2605_26388_b300 import workloads as wl
+    oracle.build()
+    nel = 12
+    P = oracle.Problem(dim=3, N=N, nel=(nel,) * 3, lo=(0.0,) * 3, hi=(2 * math.pi,) * 3,
+                       volume=oracle.VOL_EC, surface=oracle.SURF_HLLC, gamma=GAMMA)
+    xi, _ = oracle.gll(N)
+    U = wl.taylor_green_3d(nel, xi, MACH, GAMMA)
+    dt = oracle.max_dt(P, U, CFL)
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        U = oracle.rk3(P, U, dt, 1)
+        steps += 1
+        if time.perf_counter() - t0 >= seconds_hint:
+            break
+    el = time.perf_counter() - t0
+    dof = nel ** 3 * NP * NV
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": 3 * steps * dof / el, "unit": "DOF-updates/s", "cores": cores, "kind": "oracle",
+            "sample": f"{steps} SSP-RK3 step(s) of the same TGV N=4 EC+HLLC problem on a {nel}^3 sub-mesh "
+                      f"({dof} DOF), FP64, {el:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    per_step = []
+    total_dof_updates, t_all = 0.0, 0.0
+    import oracle
+    from paper_2605_26388_b300 import workloads as wl
+    oracle.build()
+    nel = 8
+    P = oracle.Problem(dim=3, N=N, nel=(nel,) * 3, lo=(0.0,) * 3, hi=(2 * math.pi,) * 3,
+                       volume=oracle.VOL_EC, surface=oracle.SURF_HLLC, gamma=GAMMA)
+    xi, _ = oracle.gll(N)
+    U = wl.taylor_green_3d(nel, xi, MACH, GAMMA)
+    dt = oracle.max_dt(P, U, CFL)
+    for _ in range(args.warmup):
+        U = oracle.rk3(P, U, dt, 1)
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        U = oracle.rk3(P, U, dt, 1)
+        per_step.append(time.perf_counter() - t0)
+    dof = nel ** 3 * NP * NV
+    t_all = sum(per_step)
+    value = 3 * dof * args.steps / t_all
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {"impl": "reference", "metric": "RK-stage DOF-updates/s (3D Euler DGSEM N=4, TGV, EC+HLLC)",
+            "value": value, "unit": "DOF-updates/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_all / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": f"each step: one SSP-RK3 step on a {nel}^3 sub-mesh "
+                                                        f"of the same problem ({dof} DOF) on the host CPU"},
+            "cpu_baseline": {"value": value, "unit": "DOF-updates/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} SSP-RK3 steps on a {nel}^3 sub-mesh, FP64"},
+            "e2e": {"value": value, "unit": "DOF-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=None)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    from paper_2605_26388_b300 import build, dgsem, workloads as wl
+    build.build_library()
+    x, w, _ = dgsem.gll(N)
+    U0 = wl.taylor_green_3d(NEL, x, MACH, GAMMA).reshape(NV, -1)
+    U0_dev = torch.from_numpy(U0).cuda()
+    peak, peak_kind = measured_peaks()
+
+    def run(precision, steps, warmup):
+        S = dgsem.Solver(dgsem.Mesh(3, N, (NEL,) * 3, (0.0,) * 3, (2 * math.pi,) * 3), volume=dgsem.VOL_EC,
+                         surface=dgsem.SURF_HLLC, precision=precision, gamma=GAMMA)
+        S.set_state(U0_dev)
+        dt = S.max_dt(CFL)
+        S.rk_step(dt, warmup)
+        S.check()
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            torch.cuda.synchronize()
+            barrier()
+            e0.record(stream)
+            S.rk_step(dt, steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            barrier()
+        S.check()
+        ms = e0.elapsed_time(e1)
+        if ws > 1:
+            import torch.distributed as dist
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return S, dt, ms, clk.summary()
+
+    fp64_steps = args.fp64_steps or max(3, args.steps // 10)
+    S32, dt, ms32, clk32 = run(dgsem.FP32_MIXED, args.steps, args.warmup)
+    S32.close()
+    S64, _, ms64, clk64 = run(dgsem.FP64, fp64_steps, 3)
+    S64.close()
+
+    def roofline(ms, steps, prec):
+        launch_ms = ms / (3 * steps)
+        alg = BYTES_PER_DOF_UPDATE * DOF  # algorithmic bytes per average launch
+        ach = alg / (launch_ms * 1e-3) / 1e9
+        return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "traffic": TRAFFIC_PER_LAUNCH[prec], "peak_kind": peak_kind,
+                "kernel": "k_euler_stage<3,4,EC," + ("float" if prec == "fp32_mixed" else "double") + ">",
+                "avg_launch_ms": launch_ms, "alg_bytes_per_launch": alg}
+
+    total_updates = 3 * DOF * args.steps * ws
+    value = total_updates / (ms32 * 1e-3)
+
+    # end to end through the C-ABI with host buffers: every step uploads the state from
+    # pinned host memory, advances one SSP-RK3 step, and reads the new state back
+    host_in = torch.from_numpy(U0).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    Se = dgsem.Solver(dgsem.Mesh(3, N, (NEL,) * 3, (0.0,) * 3, (2 * math.pi,) * 3), volume=dgsem.VOL_EC,
+                      surface=dgsem.SURF_HLLC, precision=dgsem.FP32_MIXED, gamma=GAMMA)
+    for _ in range(2):
+        Se.set_state(host_in)
+        Se.rk_step(dt, 1)
+        Se.get_state(host_out)
+    Se.check()
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        Se.set_state(host_in)
+        Se.rk_step(dt, 1)
+        Se.get_state(host_out)
+    Se.check()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    barrier()
+    Se.close()
+    nbytes = U0.nbytes
+    e2e = {"value": 3 * DOF * args.e2e_steps * ws / e2e_s, "unit": "DOF-updates/s",
+           "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+           "note": "per step: dg_set_state from pinned host memory, one SSP-RK3 step, dg_get_state to pinned host memory"}
+
+    if rank != 0:
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+    cpu = None if args.no_cpu_baseline or ws > 1 else oracle_sample()
+    line = {
+        "metric": "RK-stage DOF-updates/s (3D Euler DGSEM N=4, TGV Ma 0.1, EC flux differencing + HLLC; FP32-mixed vs FP64)",
+        "value": value, "unit": "DOF-updates/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms32 / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 flux / f64 state", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "mesh": f"{NEL}^3 periodic on [0,2pi]^3", "N": N, "dof": DOF,
+                   "precision": "fp32_mixed", "dt": dt, "cfl": CFL,
+                   "l2": "inputs larger than L2: three 1.31 GB state buffers per replica",
+                   "parallelism": f"replicas x{ws}"},
+        "roofline": roofline(ms32, args.steps, "fp32_mixed"),
+        "fp64": {"value": 3 * DOF * fp64_steps * ws / (ms64 * 1e-3), "unit": "DOF-updates/s", "steps": fp64_steps,
+                 "ms_per_step": ms64 / fp64_steps, "roofline": roofline(ms64, fp64_steps, "fp64"),
+                 "bound_note": "FP64-pipe bound on B300 (measured DFMA rate 475 G/s)", "clocks": clk64},
+        "clocks": clk32,
+        "e2e": e2e,
+        "gpu_launches": 3 * args.steps,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

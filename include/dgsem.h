@@ -1,0 +1,155 @@
+/* dgsem.h -- C-ABI of the B300 (sm_103a) DGSEM residual and SSP-RK3 stage library.
+ *
+ * The library evaluates the semi-discrete DGSEM residual of the compressible Euler
+ * equations on periodic Cartesian meshes and advances it with the three-stage SSP-RK
+ * scheme, entirely in hand-written CUDA kernels (one fused kernel per RK stage).  The
+ * operations follow arXiv 2605.26388:
+ *   - equations and ideal-gas closure: Sec. 2;
+ *   - element-local DGSEM on (N+1)^d GLL nodes: Sec. 3.1.1 and App. A;
+ *   - volume term: Eq. vol_weak (strong form; the weak form is the same operator by the
+ *     SBP property) or Eq. vol_split / Eq. split_form_3D (flux differencing with the
+ *     Ranocha entropy-conservative two-point flux);
+ *   - surface term: Eq. surf_int with a Riemann flux (Sec. 3.1.1 "Surface Fluxes");
+ *   - time integration: App. B (SSP-RK, Shu-Osher form) and Eq. dt_hyp (time-step bound).
+ *
+ * Conventions shared by every entry point:
+ *   - State layout (SoA, FP64): U[v * n_nodes_total + node_offset(instance) + e * n_p + q]
+ *     with v the conserved variable (rho, rho u, rho v[, rho w], E), e the element index
+ *     within its instance (lexicographic, x fastest), q the node index within the element
+ *     (lexicographic, i fastest) and n_p = (N+1)^dim.  n_nodes_total is the sum over
+ *     instances of n_elem * n_p.
+ *   - Array arguments are owned by the caller; the library never frees them.  Unless an
+ *     entry point says otherwise they are DEVICE pointers on the context's device.
+ *   - Launches are asynchronous on the context's CUDA stream.  Device-side faults of the
+ *     state (non-finite values, non-positive density or pressure) are recorded in a
+ *     device error word and reported by dg_check(), which synchronizes the stream.
+ *   - No entry point aborts, prints or traps.  Errors are returned as dg_status, with a
+ *     message in dg_last_error().
+ */
+#ifndef DGSEM_H
+#define DGSEM_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define DG_API __attribute__((visibility("default")))
+#else
+#define DG_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dg_ctx dg_ctx; /* opaque: mesh, operators, stage buffers, error word */
+
+typedef enum {
+  DG_OK = 0,
+  DG_EINVAL = -1,       /* bad argument or description */
+  DG_ENOMEM = -2,       /* device allocation failed */
+  DG_ECUDA = -3,        /* a CUDA runtime call failed */
+  DG_ENONFINITE = -4,   /* a kernel produced a non-finite value */
+  DG_EPOSITIVITY = -5,  /* a kernel read a state with rho <= 0 or p <= 0 */
+  DG_EUNSUPPORTED = -6  /* valid but not implemented (e.g. non-periodic boundaries) */
+} dg_status;
+
+enum { DG_EULER = 0 };
+/* Volume term: strong form (Eq. vol_weak), weak form (integrated by parts; equal to the
+ * strong form by SBP), or two-point flux differencing with Ranocha's EC flux
+ * (Eq. vol_split). */
+enum { DG_VOL_STRONG = 0, DG_VOL_WEAK = 1, DG_VOL_EC = 2 };
+/* Riemann flux at element faces: local Lax-Friedrichs (Rusanov), HLLC, HLL, or Ranocha's
+ * EC flux (no dissipation; used to check entropy conservation). */
+enum { DG_SURF_RUSANOV = 0, DG_SURF_HLLC = 1, DG_SURF_HLL = 2, DG_SURF_EC = 3 };
+/* Arithmetic: plain FP64 throughout, or FP32 volume/surface flux arithmetic with the
+ * state, the RK accumulation and the positivity decision kept in FP64. */
+enum { DG_FP64 = 0, DG_FP32_MIXED = 1 };
+
+/* One periodic Cartesian mesh instance (Sec. 3.1.1: element-wise affine map of the
+ * reference cube; collocation on (N+1)^dim GLL nodes). */
+typedef struct {
+  int dim;          /* 2 or 3 */
+  int N;            /* polynomial degree: 1..7 in 2D, 1..5 in 3D */
+  int nel[3];       /* elements per direction (nel[2] ignored in 2D) */
+  double lo[3];     /* box lower corner */
+  double hi[3];     /* box upper corner */
+  int periodic[3];  /* must be 1 in every used direction, else DG_EUNSUPPORTED */
+} dg_mesh_desc;
+
+typedef struct {
+  int equations;    /* DG_EULER */
+  int volume;       /* DG_VOL_* */
+  int surface;      /* DG_SURF_* */
+  int precision;    /* DG_FP64 | DG_FP32_MIXED */
+  double gamma;     /* ratio of specific heats (Sec. 2 closure) */
+  double rho_floor; /* > 0: clamp rho after each stage (Sec. 4 set-ups); <= 0: off */
+  double p_floor;   /* > 0: reset E so that p >= p_floor after each stage; <= 0: off */
+} dg_physics;
+
+/* Build a context for n_inst instances (all of the same dim) sharing one physics
+ * description.  Allocates the context-held state and stage buffers on the current CUDA
+ * device.  `cuda_stream` is a cudaStream_t (NULL = legacy default stream).
+ * Returns DG_EINVAL on a bad description, DG_EUNSUPPORTED on non-periodic meshes or an
+ * unsupported (dim, N), DG_ENOMEM if allocation fails.  *out is NULL on failure. */
+DG_API dg_status dg_init_mesh(const dg_mesh_desc* inst, int n_inst, const dg_physics* phys,
+                       void* cuda_stream, dg_ctx** out);
+
+/* Total number of doubles of one state (n_vars * n_nodes_total) and n_vars. */
+DG_API dg_status dg_state_size(const dg_ctx* ctx, int64_t* n_doubles, int* n_vars);
+
+/* Node offset of instance i within a variable's slab. */
+DG_API dg_status dg_instance_offset(const dg_ctx* ctx, int i, int64_t* offset);
+
+/* Copy a state into / out of the context-held state.  U may be a device pointer or a host
+ * pointer (pinned host memory gives full PCIe/C2C speed); unified addressing resolves the
+ * direction.  Asynchronous on the context's stream (the host buffer must stay valid until
+ * the stream reaches the copy). */
+DG_API dg_status dg_set_state(dg_ctx* ctx, const double* U);
+DG_API dg_status dg_get_state(const dg_ctx* ctx, double* U);
+
+/* dUdt = L(U) at time t (the Euler residual does not depend on t).  U and dUdt are device
+ * pointers of dg_state_size() doubles and must not overlap. */
+DG_API dg_status dg_rhs(dg_ctx* ctx, const double* U, double* dUdt, double t);
+
+/* One SSP-RK3 stage (App. B, Shu-Osher form) on caller buffers:
+ *   stage 1: Uout = Un + dt L(Un)                       (Uprev must equal Un)
+ *   stage 2: Uout = 3/4 Un + 1/4 (Uprev + dt L(Uprev))
+ *   stage 3: Uout = 1/3 Un + 2/3 (Uprev + dt L(Uprev))
+ * followed by the positivity floor when enabled.  Uout must not alias Un or Uprev. */
+DG_API dg_status dg_rk_stage(dg_ctx* ctx, int stage, const double* Un, const double* Uprev,
+                      double dt, double* Uout);
+
+/* n_steps SSP-RK3 steps of size dt on the context-held state (3 fused stage launches per
+ * step, replayed from a CUDA graph).  Asynchronous: call dg_check() to synchronize and
+ * collect device-side errors. */
+DG_API dg_status dg_rk_step(dg_ctx* ctx, double dt, int n_steps);
+
+/* Convective time-step bound of Eq. dt_hyp on the context-held state:
+ *   dt = cfl * dx_min / ((2N+1) * max over nodes of (|u| + a)),
+ * taking the minimum over instances.  Synchronizes the stream; *dt_out is a host double. */
+DG_API dg_status dg_max_dt(dg_ctx* ctx, double cfl, double* dt_out);
+
+/* Synchronize the context's stream, then read and clear the device error word:
+ * DG_ENONFINITE or DG_EPOSITIVITY if a kernel since the last check flagged the state. */
+DG_API dg_status dg_check(dg_ctx* ctx);
+
+/* The library's own GLL nodes x[0..N], weights w[0..N] and differentiation matrix
+ * D[(N+1)*(N+1)] (row-major, D[i*(N+1)+m] = l_m'(x_i)); host pointers, N in 1..7. */
+DG_API dg_status dg_gll(int N, double* x, double* w, double* D);
+
+/* Evaluate the device's two-point flux for n state pairs (device pointers, AoS n x n_vars)
+ * in direction l: kind = -1 the EC volume flux, else a DG_SURF_* kind.  Uses the context's
+ * precision and gamma.  Test and inspection aid. */
+DG_API dg_status dg_two_point_flux(dg_ctx* ctx, int kind, int l, int n, const double* uL,
+                            const double* uR, double* F);
+
+/* Message of the last error on this context (static string if ctx is NULL). */
+DG_API const char* dg_last_error(const dg_ctx* ctx);
+
+/* Release everything the context owns.  Safe on NULL. */
+DG_API void dg_free(dg_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DGSEM_H */

@@ -108,6 +108,7 @@ def lib():
         _lib.orc_point_flux.argtypes = [C.c_int, C.c_int, C.c_double, dp, dp]
         _lib.orc_two_point_flux.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, dp, dp, dp]
         _lib.orc_rhs.argtypes = [pp, dp, dp]
+        _lib.orc_rhs_elements.argtypes = [pp, dp, C.POINTER(C.c_int), C.c_int, dp]
         _lib.orc_rk3_stage.argtypes = [pp, C.c_int, dp, dp, C.c_double, dp]
         _lib.orc_rk3.argtypes = [pp, dp, C.c_double, C.c_int]
         _lib.orc_max_dt.argtypes = [pp, dp, C.c_double, dp]
@@ -172,6 +173,17 @@ def rhs(P: Problem, U: np.ndarray) -> np.ndarray:
     c = P._c()
     _check(lib().orc_rhs(C.byref(c), _ptr(U), _ptr(dU)), "rhs")
     return dU
+
+
+def rhs_elements(P: Problem, U: np.ndarray, elems) -> np.ndarray:
+    """L(U) on the listed elements only; returns an array (n_vars, len(elems), n_nodes)."""
+    U = np.ascontiguousarray(U, dtype=np.float64).reshape(P.shape)
+    el = np.ascontiguousarray(elems, dtype=np.int32)
+    dU = np.zeros_like(U)
+    c = P._c()
+    _check(lib().orc_rhs_elements(C.byref(c), _ptr(U), el.ctypes.data_as(C.POINTER(C.c_int)), len(el),
+                                  _ptr(dU)), "rhs_elements")
+    return dU[:, el, :]
 
 
 def rk3_stage(P: Problem, stage: int, Un: np.ndarray, Uprev: np.ndarray, dt: float):

@@ -528,6 +528,21 @@ int orc_rhs(const OrcProblem* P, const double* U, double* dU) {
   return 0;
 }
 
+// L(U) on a list of elements only (rows of dU for other elements are left untouched);
+// lets full-size problems be checked on a sample of elements.
+int orc_rhs_elements(const OrcProblem* P, const double* U, const int* elems, int n, double* dU) {
+  int rc = check_problem(*P);
+  if (rc) return rc;
+  Mesh M(*P);
+  Ops ops(P->N);
+  for (int k = 0; k < n; ++k) {
+    if (elems[k] < 0 || elems[k] >= M.n_elem) return -1;
+  }
+#pragma omp parallel for schedule(static)
+  for (int k = 0; k < n; ++k) euler_element_residual(*P, M, ops, U, elems[k], dU);
+  return 0;
+}
+
 // One SSP-RK3 stage in Shu-Osher form (App. B: U^(i) = sum_k alpha_ik U^(k) + dt beta_ik
 // L(U^(k)); the three-stage third-order scheme of Shu and Osher, whose coefficients the
 // paper cites but does not print):

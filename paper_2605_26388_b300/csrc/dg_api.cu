@@ -1,0 +1,426 @@
+// dg_api.cu -- the C-ABI of include/dgsem.h: context lifecycle, operators, launches.
+//
+// Host side only.  The context owns three FP64 state buffers (the current state and two
+// stage buffers, rotated so that no launch writes a buffer it reads), the device error
+// word, a scratch word for the time-step reduction, a private capture stream and the CUDA
+// graph that replays three SSP-RK3 steps (nine fused stage launches).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/dgsem.h"
+#include "dg_internal.h"
+
+struct dg_ctx {
+  std::vector<dg_mesh_desc> inst;
+  dg_physics phys{};
+  cudaStream_t stream = nullptr;     // caller's stream
+  cudaStream_t cap = nullptr;        // private stream for graph capture
+  int dim = 0, nv = 0;
+  long long n_nodes_total = 0;
+  std::vector<long long> offs;       // node offset per instance
+  double* buf[3] = {nullptr, nullptr, nullptr};
+  int cur = 0;                       // index of the buffer holding the current state
+  unsigned* err = nullptr;
+  unsigned long long* lam = nullptr;
+  std::string msg;
+  cudaGraphExec_t gexec = nullptr;   // three RK steps starting from buf[0]
+  double g_dt = 0.0;
+};
+
+namespace {
+
+const char* kNullCtxMsg = "null context";
+
+dg_status fail(dg_ctx* c, dg_status s, const std::string& m) {
+  if (c) c->msg = m;
+  return s;
+}
+
+dg_status cuda_fail(dg_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, DG_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+// ---------------------------------------------------------------------------------------
+// GLL rule and differentiation matrix (Sec. 3.1.1).  Interior nodes are the zeros of
+// P_N', found by Newton's method with P_N'' from Legendre's equation
+// (1-x^2) P'' = 2x P' - N(N+1) P; weights w_i = 2 / (N(N+1) P_N(x_i)^2).  The derivative
+// matrix uses the closed form for Lobatto nodes:
+//   D_ij = P_N(x_i) / (P_N(x_j) (x_i - x_j))  (i != j),  D_00 = -N(N+1)/4,
+//   D_NN = N(N+1)/4, other diagonal entries 0.
+// ---------------------------------------------------------------------------------------
+void legendre_p(int N, double x, double& P, double& dP) {
+  double pm = 1.0, p = x;  // P_0, P_1
+  if (N == 0) { P = 1.0; dP = 0.0; return; }
+  for (int k = 2; k <= N; ++k) {
+    const double pn = ((2.0 * k - 1.0) * x * p - (k - 1.0) * pm) / k;
+    pm = p;
+    p = pn;
+  }
+  P = p;
+  dP = (std::fabs(x) < 1.0) ? N * (pm - x * p) / (1.0 - x * x) : 0.0;
+}
+
+void gll_table(int N, double* x, double* w, double* D) {
+  const double pi = 3.14159265358979323846;
+  for (int i = 0; i <= N; ++i) {
+    if (i == 0) { x[i] = -1.0; continue; }
+    if (i == N) { x[i] = 1.0; continue; }
+    double xi = -std::cos(pi * i / N);
+    for (int it = 0; it < 60; ++it) {
+      double P, dP;
+      legendre_p(N, xi, P, dP);
+      const double d2P = (2.0 * xi * dP - N * (N + 1.0) * P) / (1.0 - xi * xi);
+      const double step = dP / d2P;
+      xi -= step;
+      if (std::fabs(step) < 1e-17) break;
+    }
+    x[i] = xi;
+  }
+  // symmetrise (the rule is symmetric about 0)
+  for (int i = 0; i <= N / 2; ++i) {
+    const double a = 0.5 * (x[N - i] - x[i]);
+    x[i] = -a;
+    x[N - i] = a;
+  }
+  if (N % 2 == 0) x[N / 2] = 0.0;
+  std::vector<double> PN(N + 1);
+  for (int i = 0; i <= N; ++i) {
+    double P, dP;
+    legendre_p(N, x[i], P, dP);
+    PN[i] = P;
+    w[i] = 2.0 / (N * (N + 1.0) * P * P);
+  }
+  if (D) {
+    for (int i = 0; i <= N; ++i)
+      for (int j = 0; j <= N; ++j)
+        D[i * (N + 1) + j] = (i == j) ? 0.0 : PN[i] / (PN[j] * (x[i] - x[j]));
+    D[0] = -N * (N + 1.0) / 4.0;
+    D[N * (N + 1) + N] = N * (N + 1.0) / 4.0;
+  }
+}
+
+dg_status check_desc(const dg_mesh_desc& m, int dim0, std::string& why) {
+  if (m.dim != 2 && m.dim != 3) { why = "dim must be 2 or 3"; return DG_EINVAL; }
+  if (m.dim != dim0) { why = "all instances must have the same dim"; return DG_EINVAL; }
+  if (m.N < 1) { why = "N must be >= 1"; return DG_EINVAL; }
+  if (!dg::have_kernels(m.dim, m.N)) { why = "no kernels for this (dim, N)"; return DG_EUNSUPPORTED; }
+  for (int l = 0; l < m.dim; ++l) {
+    if (m.nel[l] < 1) { why = "nel must be >= 1"; return DG_EINVAL; }
+    if (!(m.hi[l] > m.lo[l])) { why = "hi must exceed lo"; return DG_EINVAL; }
+    if (m.periodic[l] != 1) { why = "only periodic meshes are supported"; return DG_EUNSUPPORTED; }
+  }
+  const long long ne = (long long)m.nel[0] * m.nel[1] * (m.dim == 3 ? m.nel[2] : 1);
+  if (ne > (1LL << 31) - 1) { why = "too many elements"; return DG_EINVAL; }
+  return DG_OK;
+}
+
+long long n_elem_of(const dg_mesh_desc& m) {
+  return (long long)m.nel[0] * m.nel[1] * (m.dim == 3 ? m.nel[2] : 1);
+}
+int n_p_of(const dg_mesh_desc& m) {
+  int n = 1;
+  for (int l = 0; l < m.dim; ++l) n *= (m.N + 1);
+  return n;
+}
+
+// Fill the launch arguments of instance i.
+void stage_args(const dg_ctx* c, int i, dg::StageArgs& a) {
+  const dg_mesh_desc& m = c->inst[i];
+  std::memset(&a, 0, sizeof(a));
+  a.stride = c->n_nodes_total;
+  a.base = c->offs[i];
+  for (int l = 0; l < 3; ++l) {
+    a.nel[l] = (l < m.dim) ? m.nel[l] : 1;
+    a.s[l] = (l < m.dim) ? 2.0 / ((m.hi[l] - m.lo[l]) / m.nel[l]) : 0.0;
+  }
+  a.n_elem = (int)n_elem_of(m);
+  a.gamma = c->phys.gamma;
+  a.surface = c->phys.surface;
+  a.weak = (c->phys.volume == DG_VOL_WEAK) ? 1 : 0;
+  a.rho_floor = c->phys.rho_floor;
+  a.p_floor = c->phys.p_floor;
+  a.err = c->err;
+  const int N = m.N, n1 = N + 1;
+  double x[dg::kMaxN + 1], w[dg::kMaxN + 1], D[(dg::kMaxN + 1) * (dg::kMaxN + 1)];
+  gll_table(N, x, w, D);
+  for (int r = 0; r < n1; ++r)
+    for (int k = 0; k < n1; ++k) {
+      double v;
+      if (c->phys.volume == DG_VOL_WEAK) v = -(w[k] / w[r]) * D[k * n1 + r];
+      else if (c->phys.volume == DG_VOL_EC) v = 2.0 * D[r * n1 + k];
+      else v = D[r * n1 + k];
+      a.Dv[r * n1 + k] = v;
+    }
+  a.lift = 1.0 / w[0];
+}
+
+// One fused launch per instance: mode 0 writes L(U), mode 1 the stage update.
+dg_status run_stage(dg_ctx* c, const double* U, const double* Un, double* out, int mode,
+                    double ca, double cb, double dt, cudaStream_t s) {
+  for (size_t i = 0; i < c->inst.size(); ++i) {
+    dg::StageArgs a;
+    stage_args(c, (int)i, a);
+    a.U = U;
+    a.Un = Un;
+    a.out = out;
+    a.mode = mode;
+    a.ca = ca;
+    a.cb = cb;
+    a.dt = dt;
+    cudaError_t e = dg::launch_euler_stage(c->inst[i].dim, c->inst[i].N,
+                                           c->phys.volume == DG_VOL_EC,
+                                           c->phys.precision == DG_FP32_MIXED, a, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "stage launch");
+  }
+  return DG_OK;
+}
+
+const double kStageA[3] = {0.0, 0.75, 1.0 / 3.0};
+const double kStageB[3] = {1.0, 0.25, 2.0 / 3.0};
+
+// One SSP-RK3 step from buf[cur]; the new state lands in another buffer and cur moves.
+dg_status one_step(dg_ctx* c, double dt, cudaStream_t s) {
+  double* A = c->buf[c->cur];
+  double* B = c->buf[(c->cur + 1) % 3];
+  double* C = c->buf[(c->cur + 2) % 3];
+  dg_status st;
+  if ((st = run_stage(c, A, A, B, 1, kStageA[0], kStageB[0], dt, s))) return st;
+  if ((st = run_stage(c, B, A, C, 1, kStageA[1], kStageB[1], dt, s))) return st;
+  if ((st = run_stage(c, C, A, B, 1, kStageA[2], kStageB[2], dt, s))) return st;
+  c->cur = (c->cur + 1) % 3;
+  return DG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dg_status dg_init_mesh(const dg_mesh_desc* inst, int n_inst, const dg_physics* phys,
+                       void* cuda_stream, dg_ctx** out) {
+  if (!out) return DG_EINVAL;
+  *out = nullptr;
+  if (!inst || n_inst < 1 || !phys) return DG_EINVAL;
+  std::string why;
+  for (int i = 0; i < n_inst; ++i) {
+    dg_status s = check_desc(inst[i], inst[0].dim, why);
+    if (s) return s;
+  }
+  if (phys->equations != DG_EULER) return DG_EUNSUPPORTED;
+  if (phys->volume < DG_VOL_STRONG || phys->volume > DG_VOL_EC) return DG_EINVAL;
+  if (phys->surface < DG_SURF_RUSANOV || phys->surface > DG_SURF_EC) return DG_EINVAL;
+  if (phys->precision != DG_FP64 && phys->precision != DG_FP32_MIXED) return DG_EINVAL;
+  if (!(phys->gamma > 1.0)) return DG_EINVAL;
+
+  dg_ctx* c = new dg_ctx();
+  c->inst.assign(inst, inst + n_inst);
+  c->phys = *phys;
+  c->stream = (cudaStream_t)cuda_stream;
+  c->dim = inst[0].dim;
+  c->nv = c->dim + 2;
+  long long off = 0;
+  for (int i = 0; i < n_inst; ++i) {
+    c->offs.push_back(off);
+    off += n_elem_of(inst[i]) * n_p_of(inst[i]);
+  }
+  c->n_nodes_total = off;
+  const size_t bytes = sizeof(double) * (size_t)c->nv * (size_t)off;
+  for (int b = 0; b < 3; ++b) {
+    if (cudaMalloc(&c->buf[b], bytes) != cudaSuccess) {
+      cudaGetLastError();
+      dg_free(c);
+      return DG_ENOMEM;
+    }
+  }
+  if (cudaMalloc(&c->err, sizeof(unsigned)) != cudaSuccess ||
+      cudaMalloc(&c->lam, sizeof(unsigned long long)) != cudaSuccess) {
+    cudaGetLastError();
+    dg_free(c);
+    return DG_ENOMEM;
+  }
+  if (cudaMemset(c->err, 0, sizeof(unsigned)) != cudaSuccess ||
+      cudaMemset(c->buf[0], 0, bytes) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    dg_free(c);
+    return DG_ECUDA;
+  }
+  for (int i = 0; i < n_inst; ++i) {
+    cudaError_t e = dg::prepare_euler_stage(inst[i].dim, inst[i].N, phys->volume == DG_VOL_EC,
+                                            phys->precision == DG_FP32_MIXED);
+    if (e != cudaSuccess) {
+      dg_free(c);
+      return DG_ECUDA;
+    }
+  }
+  *out = c;
+  return DG_OK;
+}
+
+dg_status dg_state_size(const dg_ctx* c, int64_t* n_doubles, int* n_vars) {
+  if (!c) return DG_EINVAL;
+  if (n_doubles) *n_doubles = (int64_t)c->nv * c->n_nodes_total;
+  if (n_vars) *n_vars = c->nv;
+  return DG_OK;
+}
+
+dg_status dg_instance_offset(const dg_ctx* c, int i, int64_t* offset) {
+  if (!c || !offset || i < 0 || i >= (int)c->inst.size()) return DG_EINVAL;
+  *offset = c->offs[i];
+  return DG_OK;
+}
+
+dg_status dg_set_state(dg_ctx* c, const double* U) {
+  if (!c) return DG_EINVAL;
+  if (!U) return fail(c, DG_EINVAL, "null state pointer");
+  const size_t bytes = sizeof(double) * (size_t)c->nv * c->n_nodes_total;
+  cudaError_t e = cudaMemcpyAsync(c->buf[c->cur], U, bytes, cudaMemcpyDefault, c->stream);
+  return e == cudaSuccess ? DG_OK : cuda_fail(c, e, "dg_set_state");
+}
+
+dg_status dg_get_state(const dg_ctx* c, double* U) {
+  if (!c) return DG_EINVAL;
+  dg_ctx* m = const_cast<dg_ctx*>(c);
+  if (!U) return fail(m, DG_EINVAL, "null state pointer");
+  const size_t bytes = sizeof(double) * (size_t)c->nv * c->n_nodes_total;
+  cudaError_t e = cudaMemcpyAsync(U, c->buf[c->cur], bytes, cudaMemcpyDefault, c->stream);
+  return e == cudaSuccess ? DG_OK : cuda_fail(m, e, "dg_get_state");
+}
+
+dg_status dg_rhs(dg_ctx* c, const double* U, double* dUdt, double t) {
+  (void)t;
+  if (!c) return DG_EINVAL;
+  if (!U || !dUdt) return fail(c, DG_EINVAL, "null pointer");
+  if (U == dUdt) return fail(c, DG_EINVAL, "U and dUdt must not overlap");
+  return run_stage(c, U, U, dUdt, 0, 0.0, 0.0, 0.0, c->stream);
+}
+
+dg_status dg_rk_stage(dg_ctx* c, int stage, const double* Un, const double* Uprev, double dt,
+                      double* Uout) {
+  if (!c) return DG_EINVAL;
+  if (stage < 1 || stage > 3) return fail(c, DG_EINVAL, "stage must be 1, 2 or 3");
+  if (!Un || !Uprev || !Uout) return fail(c, DG_EINVAL, "null pointer");
+  if (Uout == Un || Uout == Uprev) return fail(c, DG_EINVAL, "Uout must not alias an input");
+  if (!std::isfinite(dt)) return fail(c, DG_EINVAL, "dt must be finite");
+  return run_stage(c, Uprev, Un, Uout, 1, kStageA[stage - 1], kStageB[stage - 1], dt,
+                   c->stream);
+}
+
+dg_status dg_rk_step(dg_ctx* c, double dt, int n_steps) {
+  if (!c) return DG_EINVAL;
+  if (n_steps < 0) return fail(c, DG_EINVAL, "n_steps must be >= 0");
+  if (!std::isfinite(dt)) return fail(c, DG_EINVAL, "dt must be finite");
+  dg_status st;
+  // single steps until the current state sits in buf[0] (the graph's entry buffer)
+  while (n_steps > 0 && c->cur != 0) {
+    if ((st = one_step(c, dt, c->stream))) return st;
+    --n_steps;
+  }
+  const int triples = n_steps / 3;  // three steps bring the rotation back to buf[0]
+  if (triples > 0) {
+    if (!c->gexec || c->g_dt != dt) {
+      if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+      cudaGraph_t g;
+      cudaError_t e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) return cuda_fail(c, e, "begin capture");
+      const int saved = c->cur;
+      for (int k = 0; k < 3; ++k) {
+        if ((st = one_step(c, dt, c->cap))) {
+          cudaStreamEndCapture(c->cap, &g);
+          cudaGetLastError();
+          c->cur = saved;
+          return st;
+        }
+      }
+      c->cur = saved;
+      e = cudaStreamEndCapture(c->cap, &g);
+      if (e != cudaSuccess) return cuda_fail(c, e, "end capture");
+      e = cudaGraphInstantiate(&c->gexec, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) { c->gexec = nullptr; return cuda_fail(c, e, "graph instantiate"); }
+      c->g_dt = dt;
+    }
+    for (int k = 0; k < triples; ++k) {
+      cudaError_t e = cudaGraphLaunch(c->gexec, c->stream);
+      if (e != cudaSuccess) return cuda_fail(c, e, "graph launch");
+    }
+    n_steps -= 3 * triples;
+  }
+  while (n_steps > 0) {
+    if ((st = one_step(c, dt, c->stream))) return st;
+    --n_steps;
+  }
+  return DG_OK;
+}
+
+dg_status dg_max_dt(dg_ctx* c, double cfl, double* dt_out) {
+  if (!c) return DG_EINVAL;
+  if (!dt_out || !(cfl > 0.0)) return fail(c, DG_EINVAL, "bad cfl or output pointer");
+  double best = INFINITY;
+  for (size_t i = 0; i < c->inst.size(); ++i) {
+    const dg_mesh_desc& m = c->inst[i];
+    cudaError_t e = cudaMemsetAsync(c->lam, 0, sizeof(unsigned long long), c->stream);
+    if (e == cudaSuccess)
+      e = dg::launch_max_speed(m.dim, c->buf[c->cur], c->n_nodes_total, c->offs[i],
+                               n_elem_of(m) * n_p_of(m), c->phys.gamma, c->lam, c->stream);
+    unsigned long long bits = 0;
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(&bits, c->lam, sizeof(bits), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "dg_max_dt");
+    double lam;
+    std::memcpy(&lam, &bits, sizeof(lam));
+    if (!(lam > 0.0) || !std::isfinite(lam)) return fail(c, DG_ENONFINITE, "no finite signal speed");
+    double dxmin = INFINITY;
+    for (int l = 0; l < m.dim; ++l) dxmin = std::fmin(dxmin, (m.hi[l] - m.lo[l]) / m.nel[l]);
+    best = std::fmin(best, cfl * dxmin / ((2 * m.N + 1) * lam));
+  }
+  *dt_out = best;
+  return DG_OK;
+}
+
+dg_status dg_check(dg_ctx* c) {
+  if (!c) return DG_EINVAL;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "dg_check sync");
+  unsigned w = 0;
+  e = cudaMemcpy(&w, c->err, sizeof(w), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemset(c->err, 0, sizeof(unsigned));
+  if (e != cudaSuccess) return cuda_fail(c, e, "dg_check read");
+  if (w & 1u) return fail(c, DG_ENONFINITE, "a kernel produced a non-finite value");
+  if (w & 2u) return fail(c, DG_EPOSITIVITY, "a kernel read a state with rho <= 0 or p <= 0");
+  return DG_OK;
+}
+
+dg_status dg_gll(int N, double* x, double* w, double* D) {
+  if (N < 1 || N > dg::kMaxN || !x || !w) return DG_EINVAL;
+  gll_table(N, x, w, D);
+  return DG_OK;
+}
+
+dg_status dg_two_point_flux(dg_ctx* c, int kind, int l, int n, const double* uL,
+                            const double* uR, double* F) {
+  if (!c) return DG_EINVAL;
+  if (kind < -1 || kind > DG_SURF_EC || l < 0 || l >= c->dim || n < 0 || !uL || !uR || !F)
+    return fail(c, DG_EINVAL, "bad two-point flux arguments");
+  cudaError_t e = dg::launch_two_point(c->dim, c->phys.precision == DG_FP32_MIXED, kind, l, n,
+                                       c->phys.gamma, uL, uR, F, c->stream);
+  return e == cudaSuccess ? DG_OK : cuda_fail(c, e, "two-point flux launch");
+}
+
+const char* dg_last_error(const dg_ctx* c) { return c ? c->msg.c_str() : kNullCtxMsg; }
+
+void dg_free(dg_ctx* c) {
+  if (!c) return;
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  for (int b = 0; b < 3; ++b)
+    if (c->buf[b]) cudaFree(c->buf[b]);
+  if (c->err) cudaFree(c->err);
+  if (c->lam) cudaFree(c->lam);
+  if (c->cap) cudaStreamDestroy(c->cap);
+  delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,306 @@
+// dg_device.cuh -- device-side building blocks of the fused DGSEM stage kernels.
+//
+// Arithmetic traits for the two precisions, FP64 <-> FP32 conversions done in integer
+// arithmetic, the element geometry of a tensor-product GLL element, and the Euler fluxes
+// of Sec. 2 / Sec. 3.1.1 / App. A (point flux, Ranocha two-point flux, Rusanov, HLL,
+// HLLC), all templated on the flux arithmetic type R (double or float).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dg {
+
+// ---------------------------------------------------------------------------------------
+// FP64 <-> FP32 conversion in integer arithmetic.
+// On sm_103a the hardware double->float conversion issues at under one result per clock
+// per SM (slower than an FP64 FMA), so the mixed-precision path converts the FP64 state
+// with integer instructions instead, written from the IEEE-754 binary64/binary32
+// encodings: round-to-nearest-even on the 29 discarded mantissa bits; results below the
+// smallest normal float flush to a signed zero; overflow gives infinity; NaN stays NaN.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ float d2f_rn(double x) {
+  const uint32_t hi = (uint32_t)__double2hiint(x);
+  const uint32_t lo = (uint32_t)__double2loint(x);
+  const uint32_t sign = hi & 0x80000000u;
+  const int ex = (int)((hi >> 20) & 0x7ffu);
+  const uint32_t man = ((hi & 0x000fffffu) << 3) | (lo >> 29);  // top 23 mantissa bits
+  const uint32_t rest = lo & 0x1fffffffu;                         // 29 discarded bits
+  const uint32_t up = (rest > 0x10000000u) | ((rest == 0x10000000u) & man);
+  const int fe = ex - 1023 + 127;
+  uint32_t bits = ((uint32_t)fe << 23) + man + (up & 1u);  // mantissa carry bumps exponent
+  if (fe <= 0) bits = 0u;                                   // below FLT_MIN: flush to zero
+  if (fe >= 255) bits = 0x7f800000u | ((ex == 0x7ff && ((hi & 0xfffffu) | lo)) ? 0x400000u : 0u);
+  return __uint_as_float(sign | bits);
+}
+
+__device__ __forceinline__ double f2d(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const uint32_t sign = b & 0x80000000u;
+  const uint32_t ex = (b >> 23) & 0xffu;
+  const uint32_t man = b & 0x7fffffu;
+  uint32_t hi, lo;
+  if (ex == 0u) {  // zero (float subnormals flush to zero; the kernels never produce them)
+    hi = sign;
+    lo = 0u;
+  } else if (ex == 255u) {
+    hi = sign | 0x7ff00000u | (man >> 3);
+    lo = man << 29;
+  } else {
+    hi = sign | ((ex + 896u) << 20) | (man >> 3);
+    lo = man << 29;
+  }
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+// Finite test on the exponent bits only (integer pipe).
+__device__ __forceinline__ bool finite64(double x) {
+  return (((uint32_t)__double2hiint(x)) & 0x7ff00000u) != 0x7ff00000u;
+}
+
+// ---------------------------------------------------------------------------------------
+// Arithmetic traits.  FP32 uses the fast reciprocal/rsqrt unit (a few ulp); FP64 uses
+// correctly rounded division and sqrt.
+// ---------------------------------------------------------------------------------------
+template <class R> struct Ar;
+
+template <> struct Ar<double> {
+  static __device__ __forceinline__ double load(double x) { return x; }
+  static __device__ __forceinline__ double widen(double x) { return x; }
+  static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+  static __device__ __forceinline__ double div(double a, double b) { return a / b; }
+  static __device__ __forceinline__ double sqrt(double x) { return ::sqrt(x); }
+  static __device__ __forceinline__ double log(double x) { return ::log(x); }
+  static __device__ __forceinline__ double fmax(double a, double b) { return ::fmax(a, b); }
+  static __device__ __forceinline__ double fmin(double a, double b) { return ::fmin(a, b); }
+  static __device__ __forceinline__ double abs(double a) { return ::fabs(a); }
+  // |f|^2 below this uses the series of the log mean (error ~ 0.02 u^5 < 1e-16)
+  static constexpr double kLogMeanSeries = 1e-3;
+};
+
+template <> struct Ar<float> {
+  static __device__ __forceinline__ float load(double x) { return d2f_rn(x); }
+  static __device__ __forceinline__ double widen(float x) { return f2d(x); }
+  static __device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
+  static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
+  static __device__ __forceinline__ float sqrt(float x) { return x * rsqrtf(x); }
+  static __device__ __forceinline__ float log(float x) { return logf(x); }
+  static __device__ __forceinline__ float fmax(float a, float b) { return fmaxf(a, b); }
+  static __device__ __forceinline__ float fmin(float a, float b) { return fminf(a, b); }
+  static __device__ __forceinline__ float abs(float a) { return fabsf(a); }
+  // |f|^2 below this uses the series (error ~ 0.02 u^5 ~ 2e-12, below FP32 rounding)
+  static constexpr float kLogMeanSeries = 1e-2f;
+};
+
+// ---------------------------------------------------------------------------------------
+// Tensor-product element geometry.
+// ---------------------------------------------------------------------------------------
+template <int DIM, int N> struct Geo {
+  static constexpr int N1 = N + 1;
+  static constexpr int NP = (DIM == 2) ? N1 * N1 : N1 * N1 * N1;  // nodes per element
+  static constexpr int NFN = (DIM == 2) ? N1 : N1 * N1;            // nodes per face
+  static constexpr int NLINE = NP / N1;                            // lines per direction
+  static constexpr int NPAIR = N * N1 / 2;                         // pairs a<b per line
+  static constexpr int NV = DIM + 2;                               // conserved variables
+  static constexpr int EPB = (NP >= 96) ? 1 : (128 / NP);          // elements per block
+  static constexpr int THREADS = ((EPB * NP + 31) / 32) * 32;
+  // stride of direction l in the node index (i fastest)
+  static __host__ __device__ constexpr int stride(int l) { return l == 0 ? 1 : (l == 1 ? N1 : N1 * N1); }
+  // node index of the m-th point on line q of direction l
+  static __device__ __forceinline__ int line_node(int l, int q, int m) {
+    const int S = stride(l);
+    return (q % S) + m * S + (q / S) * S * N1;
+  }
+  // line index and position along direction l of node nd
+  static __device__ __forceinline__ int node_line(int l, int nd) {
+    const int S = stride(l);
+    return (nd % S) + (nd / (S * N1)) * S;
+  }
+  static __device__ __forceinline__ int node_pos(int l, int nd) { return (nd / stride(l)) % N1; }
+};
+
+// ---------------------------------------------------------------------------------------
+// Euler physics (Sec. 2).  u: conserved (rho, m_1..m_DIM, E).
+// ---------------------------------------------------------------------------------------
+template <int DIM, class R> struct Prim {
+  R rho, irho, v[DIM], p;
+};
+
+template <int DIM, class R>
+__device__ __forceinline__ Prim<DIM, R> prims(const R* u, R gm1) {
+  Prim<DIM, R> q;
+  q.rho = u[0];
+  q.irho = Ar<R>::rcp(u[0]);
+  R kin = R(0);
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    q.v[d] = u[1 + d] * q.irho;
+    kin += u[1 + d] * q.v[d];
+  }
+  q.p = gm1 * (u[DIM + 1] - R(0.5) * kin);
+  return q;
+}
+
+// Cartesian flux F^L(U) in direction L (compile-time), from conserved u and primitives.
+template <int DIM, int L, class R>
+__device__ __forceinline__ void point_flux(const R* u, const Prim<DIM, R>& q, R* F) {
+  const R mn = u[1 + L];
+  F[0] = mn;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) F[1 + d] = mn * q.v[d] + (d == L ? q.p : R(0));
+  F[DIM + 1] = (u[DIM + 1] + q.p) * q.v[L];
+}
+
+// Logarithmic mean pieces for Ranocha's flux (App. A): with s = a+b, f = (a-b)/s, u = f^2,
+//   a^ln = (s/2) G(u),  G = 1/F,  F(u) = sum_k u^k/(2k+1) = atanh(f)/f,
+// where the Taylor series of 1/F is 1 - u/3 - 4u^2/45 - 44u^3/945 - c4 u^4 (c4 =
+// 0.0301940...), used for small u (the Ismail-Roe idea of a series near a = b, here
+// expanded for the reciprocal so that no division is needed); otherwise a^ln =
+// (a-b)/ln(a/b).
+template <class R>
+__device__ __forceinline__ R log_mean_from(R a, R b, R s, R f) {
+  const R u = f * f;
+  if (u < R(Ar<R>::kLogMeanSeries)) {
+    const R G = R(1) - u * (R(1.0 / 3.0) + u * (R(4.0 / 45.0) + u * (R(44.0 / 945.0) +
+                                                                      u * R(0.030194003527336861))));
+    return R(0.5) * s * G;
+  }
+  return Ar<R>::div(a - b, Ar<R>::log(Ar<R>::div(a, b)));
+}
+
+// Ranocha's EC two-point flux in direction L (App. A; energy component in the published
+// consistent form f_E = f_rho (1/((gamma-1) beta^ln) + u_L.u_R/2) + (p_L u_R + p_R u_L)/2,
+// beta = rho/p).  Inputs are per-node primitives rho, v, p and beta = rho/p.
+template <int DIM, int L, class R>
+__device__ __forceinline__ void ec_flux_prims(R rL, const R* vL, R pL, R bL, R rR, const R* vR,
+                                              R pR, R bR, R igm1, R* F) {
+  const R sr = rL + rR, sb = bL + bR;
+  const R inv = Ar<R>::rcp(sr * sb);  // one reciprocal serves both f's
+  const R fr = (rL - rR) * (sb * inv);
+  const R fb = (bL - bR) * (sr * inv);
+  const R rho_ln = log_mean_from(rL, rR, sr, fr);
+  const R beta_ln = log_mean_from(bL, bR, sb, fb);
+  R vavg[DIM];
+  R vLvR = R(0);
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    vavg[d] = R(0.5) * (vL[d] + vR[d]);
+    vLvR += vL[d] * vR[d];
+  }
+  const R frho = rho_ln * vavg[L];
+  const R pavg = R(0.5) * (pL + pR);
+  F[0] = frho;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) F[1 + d] = frho * vavg[d] + (d == L ? pavg : R(0));
+  F[DIM + 1] = frho * (igm1 * Ar<R>::rcp(beta_ln) + R(0.5) * vLvR) +
+               R(0.5) * (pL * vR[L] + pR * vL[L]);
+}
+
+template <int DIM, int L, class R>
+__device__ __forceinline__ void ec_flux(const R* uL, const R* uR, R gm1, R* F) {
+  const Prim<DIM, R> a = prims<DIM>(uL, gm1), b = prims<DIM>(uR, gm1);
+  ec_flux_prims<DIM, L>(a.rho, a.v, a.p, a.rho * Ar<R>::rcp(a.p), b.rho, b.v, b.p,
+                        b.rho * Ar<R>::rcp(b.p), Ar<R>::rcp(gm1), F);
+}
+
+// Local Lax-Friedrichs (Rusanov): F* = (F_L + F_R)/2 - lambda/2 (U_R - U_L),
+// lambda = max(|u_L| + a_L, |u_R| + a_R) along L (Sec. 3.1.1 "Lax-Friedrichs").
+template <int DIM, int L, class R>
+__device__ __forceinline__ void rusanov(const R* uL, const R* uR, R gamma, R* F) {
+  const Prim<DIM, R> a = prims<DIM>(uL, gamma - R(1)), b = prims<DIM>(uR, gamma - R(1));
+  const R cL = Ar<R>::sqrt(gamma * a.p * a.irho), cR = Ar<R>::sqrt(gamma * b.p * b.irho);
+  const R lam = Ar<R>::fmax(Ar<R>::abs(a.v[L]) + cL, Ar<R>::abs(b.v[L]) + cR);
+  R FL[DIM + 2], FR[DIM + 2];
+  point_flux<DIM, L>(uL, a, FL);
+  point_flux<DIM, L>(uR, b, FR);
+#pragma unroll
+  for (int v = 0; v < DIM + 2; ++v) F[v] = R(0.5) * (FL[v] + FR[v]) - R(0.5) * lam * (uR[v] - uL[v]);
+}
+
+// Davis/Einfeldt wave-speed estimates with Roe averages (for HLL and HLLC).
+template <int DIM, int L, class R>
+__device__ __forceinline__ void wave_speeds(const R* uL, const R* uR, const Prim<DIM, R>& a,
+                                            const Prim<DIM, R>& b, R gamma, R& SL, R& SR) {
+  const R sL = Ar<R>::sqrt(a.rho), sR = Ar<R>::sqrt(b.rho);
+  const R iw = Ar<R>::rcp(sL + sR);
+  R v2 = R(0), vtL = R(0);
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    const R vt = (sL * a.v[d] + sR * b.v[d]) * iw;
+    v2 += vt * vt;
+    if (d == L) vtL = vt;
+  }
+  const R HL = (uL[DIM + 1] + a.p) * a.irho, HR = (uR[DIM + 1] + b.p) * b.irho;
+  const R Ht = (sL * HL + sR * HR) * iw;
+  const R at = Ar<R>::sqrt((gamma - R(1)) * (Ht - R(0.5) * v2));
+  const R cL = Ar<R>::sqrt(gamma * a.p * a.irho), cR = Ar<R>::sqrt(gamma * b.p * b.irho);
+  SL = Ar<R>::fmin(a.v[L] - cL, vtL - at);
+  SR = Ar<R>::fmax(b.v[L] + cR, vtL + at);
+}
+
+template <int DIM, int L, class R>
+__device__ __forceinline__ void hll(const R* uL, const R* uR, R gamma, R* F) {
+  const Prim<DIM, R> a = prims<DIM>(uL, gamma - R(1)), b = prims<DIM>(uR, gamma - R(1));
+  R SL, SR;
+  wave_speeds<DIM, L>(uL, uR, a, b, gamma, SL, SR);
+  R FL[DIM + 2], FR[DIM + 2];
+  point_flux<DIM, L>(uL, a, FL);
+  point_flux<DIM, L>(uR, b, FR);
+  if (SL >= R(0)) {
+#pragma unroll
+    for (int v = 0; v < DIM + 2; ++v) F[v] = FL[v];
+  } else if (SR <= R(0)) {
+#pragma unroll
+    for (int v = 0; v < DIM + 2; ++v) F[v] = FR[v];
+  } else {
+    const R iS = Ar<R>::rcp(SR - SL);
+#pragma unroll
+    for (int v = 0; v < DIM + 2; ++v) F[v] = (SR * FL[v] - SL * FR[v] + SL * SR * (uR[v] - uL[v])) * iS;
+  }
+}
+
+// HLLC (Toro, Spruce and Speares): branches S_L >= 0 -> F_L; S* >= 0 -> F*_L; S_R > 0 ->
+// F*_R; else F_R.  Star state U*_K = rho_K (S_K - u_K)/(S_K - S*) (1, S* e_L + tangential,
+// E_K/rho_K + (S* - u_K)(S* + p_K/(rho_K (S_K - u_K)))).
+template <int DIM, int L, class R>
+__device__ __forceinline__ void hllc(const R* uL, const R* uR, R gamma, R* F) {
+  const Prim<DIM, R> a = prims<DIM>(uL, gamma - R(1)), b = prims<DIM>(uR, gamma - R(1));
+  R SL, SR;
+  wave_speeds<DIM, L>(uL, uR, a, b, gamma, SL, SR);
+  R FL[DIM + 2], FR[DIM + 2];
+  point_flux<DIM, L>(uL, a, FL);
+  point_flux<DIM, L>(uR, b, FR);
+  const R mL = a.rho * (SL - a.v[L]), mR = b.rho * (SR - b.v[L]);
+  const R Ss = Ar<R>::div(b.p - a.p + a.v[L] * mL - b.v[L] * mR, mL - mR);
+  if (SL >= R(0)) {
+#pragma unroll
+    for (int v = 0; v < DIM + 2; ++v) F[v] = FL[v];
+  } else if (SR <= R(0) && Ss < R(0)) {
+#pragma unroll
+    for (int v = 0; v < DIM + 2; ++v) F[v] = FR[v];
+  } else {
+    // one star state: left if S* >= 0, else right (selects, not pointers, keep it in
+    // registers)
+    const bool left = (Ss >= R(0));
+    const R SK = left ? SL : SR;
+    const R mK = left ? mL : mR;  // rho_K (S_K - u_K)
+    const R irK = left ? a.irho : b.irho;
+    const R pK = left ? a.p : b.p;
+    const R vnK = left ? a.v[L] : b.v[L];
+    const R fac = Ar<R>::div(mK, SK - Ss);
+    R Us[DIM + 2];
+    Us[0] = fac;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) Us[1 + d] = fac * (d == L ? Ss : (left ? a.v[d] : b.v[d]));
+    const R EK = left ? uL[DIM + 1] : uR[DIM + 1];
+    Us[DIM + 1] = fac * (EK * irK + (Ss - vnK) * (Ss + Ar<R>::div(pK, mK)));
+#pragma unroll
+    for (int v = 0; v < DIM + 2; ++v) {
+      const R uKv = left ? uL[v] : uR[v];
+      const R FKv = left ? FL[v] : FR[v];
+      F[v] = FKv + SK * (Us[v] - uKv);
+    }
+  }
+}
+
+}  // namespace dg

@@ -1,0 +1,54 @@
+// dg_internal.h -- declarations shared by the C-ABI layer (dg_api.cu) and the kernel
+// translation unit (dg_kernels.cu).  Not part of the public interface.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dg {
+
+constexpr int kMaxN = 7;  // largest polynomial degree with compiled kernels (2D); 3D: 5
+
+// Arguments of one fused stage launch over one mesh instance (passed by value).
+struct StageArgs {
+  const double* U;     // input state U^(k-1) (or the residual's input)
+  const double* Un;    // U^n (stages 2 and 3), else unused
+  double* out;         // U^(k) (mode 1) or L(U) (mode 0)
+  unsigned* err;       // device error word (bit 0 non-finite, bit 1 non-positive)
+  long long stride;    // per-variable stride of the SoA state (total nodes)
+  long long base;      // node offset of this instance
+  int nel[3];
+  int n_elem;
+  double s[3];         // 2/dx_l
+  double gamma;
+  double ca, cb, dt;   // U^(k) = ca Un + cb (U^(k-1) + dt L)
+  int mode;            // 0: out = L(U); 1: RK stage update
+  int surface;         // DG_SURF_*
+  int weak;            // 1: weak-form volume operator (surface lifts F* only)
+  double rho_floor, p_floor;
+  double lift;         // 1 / w_0 (= 1 / w_N) of the GLL rule
+  double Dv[(kMaxN + 1) * (kMaxN + 1)];  // volume operator, row-major (N+1)^2
+};
+
+// Launch the fused Euler stage kernel for one instance.  Returns a CUDA error code.
+cudaError_t launch_euler_stage(int dim, int N, int ec, int fp32, const StageArgs& a,
+                               cudaStream_t s);
+
+// Set the kernel attributes (dynamic shared memory) of one stage kernel; call before the
+// first launch and outside stream capture.
+cudaError_t prepare_euler_stage(int dim, int N, int ec, int fp32);
+
+// Largest signal speed |u| + a over the nodes of one instance, atomically max-ed into
+// *lam_bits (the bit pattern of a non-negative double).
+cudaError_t launch_max_speed(int dim, const double* U, long long stride, long long base,
+                             long long n_nodes, double gamma, unsigned long long* lam_bits,
+                             cudaStream_t s);
+
+// Evaluate a device two-point flux for n AoS state pairs.
+cudaError_t launch_two_point(int dim, int fp32, int kind, int l, int n, double gamma,
+                             const double* uL, const double* uR, double* F, cudaStream_t s);
+
+// Whether (dim, N) has compiled kernels.
+bool have_kernels(int dim, int N);
+
+}  // namespace dg

@@ -1,0 +1,237 @@
+"""Thin Python binding of the C-ABI in ``include/dgsem.h`` (ctypes).
+
+Argument marshalling only: every step of the residual and the RK stage runs in the CUDA
+library ``_lib/libdgsem.so``.  PyTorch provides device memory and the CUDA stream.  There
+is no CPU fallback: if the library is missing, importing :func:`lib` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass, field
+from typing import Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libdgsem.so")
+
+DG_OK, DG_EINVAL, DG_ENOMEM, DG_ECUDA, DG_ENONFINITE, DG_EPOSITIVITY, DG_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
+DG_EULER = 0
+VOL_STRONG, VOL_WEAK, VOL_EC = 0, 1, 2
+SURF_RUSANOV, SURF_HLLC, SURF_HLL, SURF_EC = 0, 1, 2, 3
+FP64, FP32_MIXED = 0, 1
+
+_STATUS = {0: "DG_OK", -1: "DG_EINVAL", -2: "DG_ENOMEM", -3: "DG_ECUDA", -4: "DG_ENONFINITE",
+           -5: "DG_EPOSITIVITY", -6: "DG_EUNSUPPORTED"}
+
+# Every entry point include/dgsem.h declares (checked by the CPU tests).
+EXPORTS = ["dg_init_mesh", "dg_state_size", "dg_instance_offset", "dg_set_state", "dg_get_state",
+           "dg_rhs", "dg_rk_stage", "dg_rk_step", "dg_max_dt", "dg_check", "dg_gll",
+           "dg_two_point_flux", "dg_last_error", "dg_free"]
+
+
+class DGError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class MeshDesc(C.Structure):
+    _fields_ = [("dim", C.c_int), ("N", C.c_int), ("nel", C.c_int * 3), ("lo", C.c_double * 3),
+                ("hi", C.c_double * 3), ("periodic", C.c_int * 3)]
+
+
+class Physics(C.Structure):
+    _fields_ = [("equations", C.c_int), ("volume", C.c_int), ("surface", C.c_int),
+                ("precision", C.c_int), ("gamma", C.c_double), ("rho_floor", C.c_double),
+                ("p_floor", C.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    """Load the CUDA library (raises OSError if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise OSError(f"CUDA library not built: {LIB_PATH} (run python -m paper_2605_26388_b300.build)")
+        L = C.CDLL(LIB_PATH)
+        vp, dp, ip = C.c_void_p, C.POINTER(C.c_double), C.c_int
+        L.dg_init_mesh.argtypes = [C.POINTER(MeshDesc), ip, C.POINTER(Physics), vp, C.POINTER(vp)]
+        L.dg_state_size.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int)]
+        L.dg_instance_offset.argtypes = [vp, ip, C.POINTER(C.c_int64)]
+        L.dg_set_state.argtypes = [vp, vp]
+        L.dg_get_state.argtypes = [vp, vp]
+        L.dg_rhs.argtypes = [vp, vp, vp, C.c_double]
+        L.dg_rk_stage.argtypes = [vp, ip, vp, vp, C.c_double, vp]
+        L.dg_rk_step.argtypes = [vp, C.c_double, ip]
+        L.dg_max_dt.argtypes = [vp, C.c_double, dp]
+        L.dg_check.argtypes = [vp]
+        L.dg_gll.argtypes = [ip, dp, dp, dp]
+        L.dg_two_point_flux.argtypes = [vp, ip, ip, ip, vp, vp, vp]
+        L.dg_last_error.argtypes = [vp]
+        L.dg_last_error.restype = C.c_char_p
+        L.dg_free.argtypes = [vp]
+        L.dg_free.restype = None
+        for name in EXPORTS:
+            if name not in ("dg_last_error", "dg_free"):
+                getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def gll(N: int):
+    """The library's GLL nodes, weights and differentiation matrix (host computation)."""
+    x = np.zeros(N + 1)
+    w = np.zeros(N + 1)
+    D = np.zeros((N + 1) * (N + 1))
+    st = lib().dg_gll(N, x.ctypes.data_as(C.POINTER(C.c_double)), w.ctypes.data_as(C.POINTER(C.c_double)),
+                      D.ctypes.data_as(C.POINTER(C.c_double)))
+    if st != DG_OK:
+        raise DGError(st, f"dg_gll({N})")
+    return x, w, D.reshape(N + 1, N + 1)
+
+
+@dataclass
+class Mesh:
+    """One periodic Cartesian instance."""
+    dim: int
+    N: int
+    nel: Sequence[int]
+    lo: Sequence[float]
+    hi: Sequence[float]
+
+    def c(self) -> MeshDesc:
+        nel = list(self.nel) + [1] * (3 - len(self.nel))
+        lo = list(self.lo) + [0.0] * (3 - len(self.lo))
+        hi = list(self.hi) + [1.0] * (3 - len(self.hi))
+        return MeshDesc(self.dim, self.N, (C.c_int * 3)(*nel), (C.c_double * 3)(*lo),
+                        (C.c_double * 3)(*hi), (C.c_int * 3)(1, 1, 1))
+
+    @property
+    def n_elem(self) -> int:
+        return int(np.prod(list(self.nel)[: self.dim]))
+
+    @property
+    def n_nodes(self) -> int:
+        return (self.N + 1) ** self.dim
+
+
+class Solver:
+    """A DGSEM context: instances + physics, bound to the current CUDA stream.
+
+    Tensors passed in and out are float64, contiguous, on the context's device, in the
+    SoA layout U[var, node] (node = instance offset + elem * n_p + local node)."""
+
+    def __init__(self, meshes, volume=VOL_STRONG, surface=SURF_RUSANOV, precision=FP64,
+                 gamma=1.4, rho_floor=0.0, p_floor=0.0, stream=None):
+        import torch
+        if isinstance(meshes, Mesh):
+            meshes = [meshes]
+        self.meshes = list(meshes)
+        arr = (MeshDesc * len(self.meshes))(*[m.c() for m in self.meshes])
+        phys = Physics(DG_EULER, volume, surface, precision, gamma, rho_floor, p_floor)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = C.c_void_p()
+        st = lib().dg_init_mesh(arr, len(self.meshes), C.byref(phys), C.c_void_p(stream.cuda_stream), C.byref(h))
+        if st != DG_OK:
+            raise DGError(st, "dg_init_mesh")
+        self._h = h
+        n = C.c_int64()
+        nv = C.c_int()
+        self._call(lib().dg_state_size(self._h, C.byref(n), C.byref(nv)), "dg_state_size")
+        self.n_doubles, self.nv = int(n.value), int(nv.value)
+        self.n_nodes = self.n_doubles // self.nv
+        self.offsets = []
+        for i in range(len(self.meshes)):
+            o = C.c_int64()
+            self._call(lib().dg_instance_offset(self._h, i, C.byref(o)), "dg_instance_offset")
+            self.offsets.append(int(o.value))
+
+    # -- helpers -------------------------------------------------------------------------
+    def _call(self, st: int, what: str):
+        if st != DG_OK:
+            msg = lib().dg_last_error(self._h if getattr(self, "_h", None) else None)
+            raise DGError(st, f"{what}: {msg.decode() if msg else ''}")
+
+    def _dev(self, t, what):
+        import torch
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+            raise TypeError(f"{what} must be a contiguous float64 CUDA tensor")
+        if t.numel() != self.n_doubles:
+            raise ValueError(f"{what} has {t.numel()} values, expected {self.n_doubles}")
+        return C.c_void_p(t.data_ptr())
+
+    @property
+    def shape(self):
+        return (self.nv, self.n_nodes)
+
+    # -- entry points --------------------------------------------------------------------
+    def set_state(self, U):
+        """Copy a state (CUDA tensor, or host tensor / array) into the context."""
+        import torch
+        if isinstance(U, np.ndarray):
+            U = torch.from_numpy(np.ascontiguousarray(U, dtype=np.float64))
+        if U.numel() != self.n_doubles or U.dtype != torch.float64 or not U.is_contiguous():
+            raise ValueError("state must be contiguous float64 with n_vars * n_nodes values")
+        self._keep = U  # the copy is asynchronous; keep the source alive
+        self._call(lib().dg_set_state(self._h, C.c_void_p(U.data_ptr())), "dg_set_state")
+
+    def get_state(self, out=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.shape, dtype=torch.float64, device="cuda")
+        self._call(lib().dg_get_state(self._h, C.c_void_p(out.data_ptr())), "dg_get_state")
+        return out
+
+    def rhs(self, U, out=None):
+        import torch
+        if out is None:
+            out = torch.empty_like(U)
+        self._call(lib().dg_rhs(self._h, self._dev(U, "U"), self._dev(out, "dUdt"), 0.0), "dg_rhs")
+        return out
+
+    def rk_stage(self, stage: int, Un, Uprev, dt: float, out=None):
+        import torch
+        if out is None:
+            out = torch.empty_like(Un)
+        self._call(lib().dg_rk_stage(self._h, stage, self._dev(Un, "Un"), self._dev(Uprev, "Uprev"), dt,
+                                     self._dev(out, "Uout")), "dg_rk_stage")
+        return out
+
+    def rk_step(self, dt: float, n_steps: int = 1):
+        self._call(lib().dg_rk_step(self._h, dt, n_steps), "dg_rk_step")
+
+    def max_dt(self, cfl: float) -> float:
+        out = C.c_double()
+        self._call(lib().dg_max_dt(self._h, cfl, C.byref(out)), "dg_max_dt")
+        return out.value
+
+    def check(self):
+        """Synchronize and raise DGError if a kernel flagged a non-finite or non-positive state."""
+        self._call(lib().dg_check(self._h), "dg_check")
+
+    def two_point_flux(self, kind: int, l: int, uL, uR, out=None):
+        import torch
+        n = uL.shape[0]
+        if out is None:
+            out = torch.empty_like(uL)
+        self._call(lib().dg_two_point_flux(self._h, kind, l, n, C.c_void_p(uL.data_ptr()),
+                                           C.c_void_p(uR.data_ptr()), C.c_void_p(out.data_ptr())),
+                   "dg_two_point_flux")
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().dg_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

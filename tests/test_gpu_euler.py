@@ -1,0 +1,235 @@
+"""Parity of the CUDA path (through the C-ABI) against the oracle, on the GPU.
+
+Inputs are seeded synthetic states built with the oracle's GLL nodes; expected values come
+from the oracle only.  Bars: FP64 relative L2 error <= 1e-12 per variable (after 100 steps
+where stated); FP32-mixed <= 1e-5; integer-like properties (conservation sums, determinism,
+translation) as stated per test.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2605_26388_b300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+GAMMA = 1.4
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return t
+
+
+@pytest.fixture(scope="module")
+def dg():
+    from paper_2605_26388_b300 import build, dgsem
+    build.build_library()
+    return dgsem
+
+
+def rel_l2(a, b):
+    """max over variables of ||a_v - b_v||_2 / ||b_v||_2 (b_v = 0 -> absolute, scaled by max |b|)."""
+    a = np.asarray(a).reshape(a.shape[0], -1)
+    b = np.asarray(b).reshape(b.shape[0], -1)
+    scale = np.max(np.abs(b))
+    worst = 0.0
+    for v in range(a.shape[0]):
+        nb = np.linalg.norm(b[v])
+        d = np.linalg.norm(a[v] - b[v])
+        worst = max(worst, d / nb if nb > 1e-300 * scale and nb > 1e-8 * scale * math.sqrt(b[v].size) else d / (scale * math.sqrt(b[v].size)))
+    return worst
+
+
+def setup(orc, dg, torch, dim, N, nel, vol, surf, prec, lo=None, hi=None):
+    lo = lo or (0.0,) * dim
+    hi = hi or (2.0,) * dim
+    nel_t = tuple(nel) if isinstance(nel, (tuple, list)) else (nel,) * dim
+    P = orc.Problem(dim=dim, N=N, nel=nel_t, lo=tuple(lo), hi=tuple(hi), volume=vol, surface=surf, gamma=GAMMA)
+    S = dg.Solver(dg.Mesh(dim, N, nel_t, lo, hi), volume=vol, surface=surf, precision=prec, gamma=GAMMA)
+    return P, S
+
+
+def smooth_state(orc, P, seed=1, rough=0.0, amp=0.2):
+    xi, _ = orc.gll(P.N)
+    X = wl.node_coordinates(P.dim, P.nel, P.lo, P.hi, xi)
+    rho = 1.0 + amp * wl.fourier_field(seed, X, P.lo, P.hi, 2)
+    vel = [0.3 * wl.fourier_field(seed + 1 + d, X, P.lo, P.hi, 2) for d in range(P.dim)]
+    p = 1.0 + amp * wl.fourier_field(seed + 7, X, P.lo, P.hi, 2)
+    U = wl.conserved(rho, vel, p, GAMMA)
+    if rough:
+        U = wl.perturbed(U, seed + 11, rough)
+    return U
+
+
+def to_dev(torch, U):
+    return torch.from_numpy(np.ascontiguousarray(U.reshape(U.shape[0], -1))).cuda()
+
+
+CASES = [
+    # dim, N, nel, vol, surf
+    (2, 3, (5, 3), 0, 0), (2, 3, (5, 3), 1, 0), (2, 4, (3, 4), 2, 1), (2, 2, (7, 2), 2, 2),
+    (2, 1, (3, 3), 0, 1), (2, 5, (2, 3), 2, 3), (2, 7, (2, 2), 0, 0), (2, 6, (1, 1), 2, 1),
+    (3, 4, (3, 2, 2), 2, 1), (3, 4, (2, 2, 3), 0, 0), (3, 2, (3, 3, 2), 2, 0), (3, 3, (2, 3, 2), 1, 1),
+    (3, 1, (2, 2, 2), 2, 2), (3, 5, (2, 1, 2), 2, 1), (3, 3, (1, 1, 1), 2, 3),
+]
+
+
+@pytest.mark.parametrize("dim,N,nel,vol,surf", CASES)
+@pytest.mark.parametrize("prec", [0, 1])
+def test_rhs_parity(orc, dg, torch, dim, N, nel, vol, surf, prec):
+    P, S = setup(orc, dg, torch, dim, N, nel, vol, surf, prec)
+    U = smooth_state(orc, P, seed=3 + N, rough=0.02)
+    ref = orc.rhs(P, U)
+    got = S.rhs(to_dev(torch, U)).cpu().numpy().reshape(ref.shape)
+    S.check()
+    tol = 1e-12 if prec == 0 else 1e-5
+    assert rel_l2(got, ref) <= tol, rel_l2(got, ref)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_density_wave_100_steps(orc, dg, torch, prec):
+    """The 2D workload at full size: 16x16, N=3, weak form, Rusanov, CFL 0.5, 100 steps."""
+    P, S = setup(orc, dg, torch, 2, 3, 16, 1, 0, prec)
+    xi, _ = orc.gll(3)
+    U0 = wl.density_wave_2d(16, xi, GAMMA)
+    dt = orc.max_dt(P, U0, 0.5)
+    ref = orc.rk3(P, U0, dt, 100)
+    S.set_state(to_dev(torch, U0))
+    assert abs(S.max_dt(0.5) - dt) <= 1e-14 * dt
+    S.rk_step(dt, 100)
+    S.check()
+    got = S.get_state().cpu().numpy().reshape(ref.shape)
+    tol = 1e-12 if prec == 0 else 1e-5
+    assert rel_l2(got, ref) <= tol, rel_l2(got, ref)
+    if prec == 0:
+        # conservation of every variable to round-off after 100 steps
+        _, w = orc.gll(3)
+        wq = np.multiply.outer(w, w).ravel()
+        for v in range(4):
+            m0 = np.sum(U0[v] * wq)
+            m1 = np.sum(got[v] * wq)
+            assert abs(m1 - m0) <= 1e-13 * np.sum(np.abs(U0[v]) * wq), v
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_tgv_reduced_100_steps(orc, dg, torch, prec):
+    """The 3D Taylor-Green workload (N=4, EC volume, HLLC) on a 4^3 mesh, 100 steps."""
+    P, S = setup(orc, dg, torch, 3, 4, 4, 2, 1, prec, lo=(0.0,) * 3, hi=(2 * math.pi,) * 3)
+    xi, _ = orc.gll(4)
+    U0 = wl.taylor_green_3d(4, xi, 0.1, GAMMA)
+    dt = orc.max_dt(P, U0, 0.5)
+    ref = orc.rk3(P, U0, dt, 100)
+    S.set_state(to_dev(torch, U0))
+    S.rk_step(dt, 100)
+    S.check()
+    got = S.get_state().cpu().numpy().reshape(ref.shape)
+    tol = 1e-12 if prec == 0 else 1e-5
+    assert rel_l2(got, ref) <= tol, rel_l2(got, ref)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_tgv_full_size_sampled_stage(orc, dg, torch, prec):
+    """64^3 N=4 (the benchmark launch configuration): one stage, checked on sampled
+    elements (interior, faces, edges and corners of the periodic box) against the oracle."""
+    n = 64
+    P, S = setup(orc, dg, torch, 3, 4, n, 2, 1, prec, lo=(0.0,) * 3, hi=(2 * math.pi,) * 3)
+    xi, _ = orc.gll(4)
+    U0 = wl.taylor_green_3d(n, xi, 0.1, GAMMA)
+    dt = 1e-3
+    Ud = to_dev(torch, U0)
+    out = S.rk_stage(1, Ud, Ud, dt)
+    S.check()
+    corners = [0, n - 1, n * (n - 1), n * n - 1, n ** 3 - 1, n * n * (n - 1), n * n * (n - 1) + n - 1]
+    r = wl.uniform(77, 40)
+    elems = sorted(set(corners + [int(x * n ** 3) for x in r]))
+    L = orc.rhs_elements(P, U0, elems)
+    ref = U0[:, elems, :] + dt * L
+    got = out.cpu().numpy().reshape(U0.shape)[:, elems, :]
+    tol = 1e-12 if prec == 0 else 1e-5
+    # compare the increment, which carries all of the residual's arithmetic
+    inc_ref = ref - U0[:, elems, :]
+    inc_got = got - U0[:, elems, :]
+    assert rel_l2(inc_got, inc_ref) <= tol * 10, rel_l2(inc_got, inc_ref)
+    assert rel_l2(got, ref) <= tol
+
+
+@pytest.mark.parametrize("kind", [-1, 0, 1, 2])
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_two_point_flux_parity(orc, dg, torch, kind, dim, prec):
+    S = dg.Solver(dg.Mesh(dim, 2, (1,) * dim, (0.0,) * dim, (1.0,) * dim), precision=prec, gamma=GAMMA)
+    n = 2000
+    r = wl.uniform(91 + dim, n * (dim + 2)).reshape(n, dim + 2)
+    rho = 0.5 + 1.5 * r[:, 0]
+    vel = [-1.0 + 2.0 * r[:, 1 + d] for d in range(dim)]
+    p = 0.5 + 1.5 * r[:, dim + 1]
+    uL = wl.conserved(rho, vel, p, GAMMA).T.copy()
+    # right states: relative offsets spanning 1e-9 .. 1 around the log-mean series threshold
+    scale = 10.0 ** (-9.0 * wl.uniform(95, n))
+    uR = uL * (1.0 + scale[:, None] * (wl.uniform(96, n * (dim + 2)).reshape(n, dim + 2) - 0.5))
+    tol = 1e-13 if prec == 0 else 2e-6
+    for l in range(dim):
+        got = S.two_point_flux(kind, l, torch.from_numpy(uL).cuda(), torch.from_numpy(uR).cuda()).cpu().numpy()
+        ref = np.array([orc.two_point_flux(kind, dim, l, GAMMA, a, b) for a, b in zip(uL, uR)])
+        err = np.max(np.abs(got - ref) / (np.abs(ref) + np.max(np.abs(ref), axis=1, keepdims=True)))
+        assert err <= tol, err
+
+
+def test_rk_step_graph_equals_stages(orc, dg, torch):
+    P, S = setup(orc, dg, torch, 2, 4, (6, 5), 2, 1, 0)
+    U0 = to_dev(torch, smooth_state(orc, P, seed=41))
+    dt = 2e-3
+    U = U0.clone()
+    for _ in range(7):
+        U1 = S.rk_stage(1, U, U, dt)
+        U2 = S.rk_stage(2, U, U1, dt)
+        U = S.rk_stage(3, U, U2, dt)
+    S.set_state(U0)
+    S.rk_step(dt, 7)
+    S.check()
+    assert torch.equal(S.get_state(), U)
+
+
+def test_deterministic_and_translation_bitwise(orc, dg, torch):
+    P, S = setup(orc, dg, torch, 2, 3, (4, 4), 2, 1, 1)
+    U = smooth_state(orc, P, seed=43, rough=0.05)
+    a = S.rhs(to_dev(torch, U))
+    b = S.rhs(to_dev(torch, U))
+    assert torch.equal(a, b)
+    sh = np.roll(U.reshape(4, 4, 4, -1), 1, axis=2).reshape(U.shape)
+    c = S.rhs(to_dev(torch, sh)).cpu().numpy().reshape(U.shape)
+    assert np.array_equal(c, np.roll(a.cpu().numpy().reshape(4, 4, 4, -1), 1, axis=2).reshape(U.shape))
+
+
+def test_error_word_reports_bad_states(orc, dg, torch):
+    P, S = setup(orc, dg, torch, 2, 2, (3, 3), 0, 0, 0)
+    U = smooth_state(orc, P, seed=47)
+    bad = U.copy()
+    bad[0, 4, 3] = -0.5  # negative density at one node
+    S.rhs(to_dev(torch, bad))
+    with pytest.raises(dg.DGError) as ei:
+        S.check()
+    assert ei.value.status == dg.DG_EPOSITIVITY
+    S.check()  # the word was cleared
+    nan = U.copy()
+    nan[3, 2, 1] = float("nan")
+    S.rhs(to_dev(torch, nan))
+    with pytest.raises(dg.DGError) as ei:
+        S.check()
+    assert ei.value.status in (dg.DG_ENONFINITE, dg.DG_EPOSITIVITY)
+
+
+def test_positivity_floor_matches_oracle(orc, dg, torch):
+    P = orc.Problem(dim=2, N=3, nel=(4, 4), lo=(0.0, 0.0), hi=(1.0, 1.0), volume=0, surface=0, gamma=GAMMA,
+                    rho_floor=0.9, p_floor=0.95)
+    S = dg.Solver(dg.Mesh(2, 3, (4, 4), (0.0, 0.0), (1.0, 1.0)), volume=0, surface=0, precision=0, gamma=GAMMA,
+                  rho_floor=0.9, p_floor=0.95)
+    U = smooth_state(orc, P, seed=53)
+    ref = orc.rk3_stage(P, 1, U, U, 1e-3)
+    got = S.rk_stage(1, to_dev(torch, U), to_dev(torch, U), 1e-3).cpu().numpy().reshape(ref.shape)
+    assert rel_l2(got, ref) <= 1e-12
