@@ -62,7 +62,8 @@ enum { DG_VOL_STRONG = 0, DG_VOL_WEAK = 1, DG_VOL_EC = 2 };
  * EC flux (no dissipation; used to check entropy conservation). */
 enum { DG_SURF_RUSANOV = 0, DG_SURF_HLLC = 1, DG_SURF_HLL = 2, DG_SURF_EC = 3 };
 /* Arithmetic: plain FP64 throughout, or FP32 volume/surface flux arithmetic with the
- * state, the RK accumulation and the positivity decision kept in FP64. */
+ * state, the RK accumulation, the pressure (from the FP64 total energy) and the
+ * positivity decision kept in FP64. */
 enum { DG_FP64 = 0, DG_FP32_MIXED = 1 };
 
 /* One periodic Cartesian mesh instance (Sec. 3.1.1: element-wise affine map of the
@@ -84,6 +85,11 @@ typedef struct {
   double gamma;     /* ratio of specific heats (Sec. 2 closure) */
   double rho_floor; /* > 0: clamp rho after each stage (Sec. 4 set-ups); <= 0: off */
   double p_floor;   /* > 0: reset E so that p >= p_floor after each stage; <= 0: off */
+  double p_ref;     /* constant subtracted from the pressure in the momentum flux, p -> p - p_ref.
+                     * Leaves the discrete operator unchanged in exact arithmetic (rows of D sum
+                     * to zero; F* - F(U_own) is invariant to a common constant) and keeps FP32
+                     * flux arithmetic out of cancellation at low Mach number.  0 = no shift.
+                     * dg_two_point_flux reports momentum fluxes with this shift applied. */
 } dg_physics;
 
 /* Build a context for n_inst instances (all of the same dim) sharing one physics

@@ -142,6 +142,7 @@ void stage_args(const dg_ctx* c, int i, dg::StageArgs& a) {
   a.weak = (c->phys.volume == DG_VOL_WEAK) ? 1 : 0;
   a.rho_floor = c->phys.rho_floor;
   a.p_floor = c->phys.p_floor;
+  a.p_ref = c->phys.p_ref;
   a.err = c->err;
   const int N = m.N, n1 = N + 1;
   double x[dg::kMaxN + 1], w[dg::kMaxN + 1], D[(dg::kMaxN + 1) * (dg::kMaxN + 1)];
@@ -213,6 +214,7 @@ dg_status dg_init_mesh(const dg_mesh_desc* inst, int n_inst, const dg_physics* p
   if (phys->surface < DG_SURF_RUSANOV || phys->surface > DG_SURF_EC) return DG_EINVAL;
   if (phys->precision != DG_FP64 && phys->precision != DG_FP32_MIXED) return DG_EINVAL;
   if (!(phys->gamma > 1.0)) return DG_EINVAL;
+  if (!std::isfinite(phys->p_ref)) return DG_EINVAL;
 
   dg_ctx* c = new dg_ctx();
   c->inst.assign(inst, inst + n_inst);
@@ -406,7 +408,7 @@ dg_status dg_two_point_flux(dg_ctx* c, int kind, int l, int n, const double* uL,
   if (kind < -1 || kind > DG_SURF_EC || l < 0 || l >= c->dim || n < 0 || !uL || !uR || !F)
     return fail(c, DG_EINVAL, "bad two-point flux arguments");
   cudaError_t e = dg::launch_two_point(c->dim, c->phys.precision == DG_FP32_MIXED, kind, l, n,
-                                       c->phys.gamma, uL, uR, F, c->stream);
+                                       c->phys.gamma, c->phys.p_ref, uL, uR, F, c->stream);
   return e == cudaSuccess ? DG_OK : cuda_fail(c, e, "two-point flux launch");
 }
 

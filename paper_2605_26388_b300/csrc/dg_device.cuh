@@ -121,37 +121,68 @@ template <int DIM, int N> struct Geo {
 
 // ---------------------------------------------------------------------------------------
 // Euler physics (Sec. 2).  u: conserved (rho, m_1..m_DIM, E).
+//
+// Pressure enters the fluxes as the deviation pd = p - p_ref from a global constant p_ref:
+// the momentum fluxes use pd, everything else p = pd + p_ref.  A constant added to the
+// momentum flux leaves the discrete operator unchanged in exact arithmetic (the rows of D
+// sum to zero, and F* - F(U_own) is invariant), and at low Mach number it keeps the
+// pressure gradient out of FP32 cancellation.  pd itself is evaluated from the FP64 total
+// energy (the ideal-gas closure of Sec. 2): pd = (gamma-1)(E - |m|^2/(2 rho)) - p_ref, with
+// the kinetic energy formed in R.  Explicit-rounding intrinsics make every call site
+// produce the same bits, so the two elements sharing a face see the same pd.
 // ---------------------------------------------------------------------------------------
+template <int DIM>
+__device__ __forceinline__ float pdev(const double* u64, const float* u, double gm1,
+                                      double p_ref, double& rhoe64) {
+  const float irho = __fdividef(1.0f, u[0]);
+  float m2 = __fmul_rn(u[1], u[1]);
+#pragma unroll
+  for (int d = 1; d < DIM; ++d) m2 = __fmaf_rn(u[1 + d], u[1 + d], m2);
+  const float ke = __fmul_rn(__fmul_rn(0.5f, m2), irho);
+  rhoe64 = __dsub_rn(u64[DIM + 1], f2d(ke));  // internal energy density, FP64
+  return d2f_rn(__fma_rn(gm1, rhoe64, -p_ref));
+}
+
+template <int DIM>
+__device__ __forceinline__ double pdev(const double* u64, const double* u, double gm1,
+                                       double p_ref, double& rhoe64) {
+  const double irho = __drcp_rn(u[0]);
+  double m2 = __dmul_rn(u[1], u[1]);
+#pragma unroll
+  for (int d = 1; d < DIM; ++d) m2 = __fma_rn(u[1 + d], u[1 + d], m2);
+  const double ke = __dmul_rn(__dmul_rn(0.5, m2), irho);
+  (void)u64;
+  rhoe64 = __dsub_rn(u[DIM + 1], ke);
+  return __fma_rn(gm1, rhoe64, -p_ref);
+}
+
 template <int DIM, class R> struct Prim {
-  R rho, irho, v[DIM], p;
+  R rho, irho, v[DIM], p, pd;
 };
 
 template <int DIM, class R>
-__device__ __forceinline__ Prim<DIM, R> prims(const R* u, R gm1) {
+__device__ __forceinline__ Prim<DIM, R> prims(const R* u, R pd, R p_ref) {
   Prim<DIM, R> q;
   q.rho = u[0];
   q.irho = Ar<R>::rcp(u[0]);
-  R kin = R(0);
 #pragma unroll
-  for (int d = 0; d < DIM; ++d) {
-    q.v[d] = u[1 + d] * q.irho;
-    kin += u[1 + d] * q.v[d];
-  }
-  q.p = gm1 * (u[DIM + 1] - R(0.5) * kin);
+  for (int d = 0; d < DIM; ++d) q.v[d] = u[1 + d] * q.irho;
+  q.pd = pd;
+  q.p = pd + p_ref;
   return q;
 }
 
-// Cartesian flux F^L(U) in direction L (compile-time), from conserved u and primitives.
+// Cartesian flux F^L(U) in direction L (compile-time); momentum carries pd.
 template <int DIM, int L, class R>
 __device__ __forceinline__ void point_flux(const R* u, const Prim<DIM, R>& q, R* F) {
   const R mn = u[1 + L];
   F[0] = mn;
 #pragma unroll
-  for (int d = 0; d < DIM; ++d) F[1 + d] = mn * q.v[d] + (d == L ? q.p : R(0));
+  for (int d = 0; d < DIM; ++d) F[1 + d] = mn * q.v[d] + (d == L ? q.pd : R(0));
   F[DIM + 1] = (u[DIM + 1] + q.p) * q.v[L];
 }
 
-// Logarithmic mean pieces for Ranocha's flux (App. A): with s = a+b, f = (a-b)/s, u = f^2,
+// Logarithmic mean for Ranocha's flux (App. A): with s = a+b, f = (a-b)/s, u = f^2,
 //   a^ln = (s/2) G(u),  G = 1/F,  F(u) = sum_k u^k/(2k+1) = atanh(f)/f,
 // where the Taylor series of 1/F is 1 - u/3 - 4u^2/45 - 44u^3/945 - c4 u^4 (c4 =
 // 0.0301940...), used for small u (the Ismail-Roe idea of a series near a = b, here
@@ -170,10 +201,10 @@ __device__ __forceinline__ R log_mean_from(R a, R b, R s, R f) {
 
 // Ranocha's EC two-point flux in direction L (App. A; energy component in the published
 // consistent form f_E = f_rho (1/((gamma-1) beta^ln) + u_L.u_R/2) + (p_L u_R + p_R u_L)/2,
-// beta = rho/p).  Inputs are per-node primitives rho, v, p and beta = rho/p.
+// beta = rho/p).  Inputs are per-node rho, v, pd and beta = rho/p.
 template <int DIM, int L, class R>
-__device__ __forceinline__ void ec_flux_prims(R rL, const R* vL, R pL, R bL, R rR, const R* vR,
-                                              R pR, R bR, R igm1, R* F) {
+__device__ __forceinline__ void ec_flux_prims(R rL, const R* vL, R pdL, R bL, R rR, const R* vR,
+                                              R pdR, R bR, R igm1, R p_ref, R* F) {
   const R sr = rL + rR, sb = bL + bR;
   const R inv = Ar<R>::rcp(sr * sb);  // one reciprocal serves both f's
   const R fr = (rL - rR) * (sb * inv);
@@ -188,26 +219,28 @@ __device__ __forceinline__ void ec_flux_prims(R rL, const R* vL, R pL, R bL, R r
     vLvR += vL[d] * vR[d];
   }
   const R frho = rho_ln * vavg[L];
-  const R pavg = R(0.5) * (pL + pR);
+  const R pdavg = R(0.5) * (pdL + pdR);
   F[0] = frho;
 #pragma unroll
-  for (int d = 0; d < DIM; ++d) F[1 + d] = frho * vavg[d] + (d == L ? pavg : R(0));
+  for (int d = 0; d < DIM; ++d) F[1 + d] = frho * vavg[d] + (d == L ? pdavg : R(0));
   F[DIM + 1] = frho * (igm1 * Ar<R>::rcp(beta_ln) + R(0.5) * vLvR) +
-               R(0.5) * (pL * vR[L] + pR * vL[L]);
+               R(0.5) * ((pdL + p_ref) * vR[L] + (pdR + p_ref) * vL[L]);
 }
 
 template <int DIM, int L, class R>
-__device__ __forceinline__ void ec_flux(const R* uL, const R* uR, R gm1, R* F) {
-  const Prim<DIM, R> a = prims<DIM>(uL, gm1), b = prims<DIM>(uR, gm1);
-  ec_flux_prims<DIM, L>(a.rho, a.v, a.p, a.rho * Ar<R>::rcp(a.p), b.rho, b.v, b.p,
-                        b.rho * Ar<R>::rcp(b.p), Ar<R>::rcp(gm1), F);
+__device__ __forceinline__ void ec_flux(const R* uL, const R* uR, R pdL, R pdR, R gm1, R p_ref,
+                                        R* F) {
+  const Prim<DIM, R> a = prims<DIM>(uL, pdL, p_ref), b = prims<DIM>(uR, pdR, p_ref);
+  ec_flux_prims<DIM, L>(a.rho, a.v, a.pd, a.rho * Ar<R>::rcp(a.p), b.rho, b.v, b.pd,
+                        b.rho * Ar<R>::rcp(b.p), Ar<R>::rcp(gm1), p_ref, F);
 }
 
 // Local Lax-Friedrichs (Rusanov): F* = (F_L + F_R)/2 - lambda/2 (U_R - U_L),
 // lambda = max(|u_L| + a_L, |u_R| + a_R) along L (Sec. 3.1.1 "Lax-Friedrichs").
 template <int DIM, int L, class R>
-__device__ __forceinline__ void rusanov(const R* uL, const R* uR, R gamma, R* F) {
-  const Prim<DIM, R> a = prims<DIM>(uL, gamma - R(1)), b = prims<DIM>(uR, gamma - R(1));
+__device__ __forceinline__ void rusanov(const R* uL, const R* uR, R pdL, R pdR, R gamma, R p_ref,
+                                        R* F) {
+  const Prim<DIM, R> a = prims<DIM>(uL, pdL, p_ref), b = prims<DIM>(uR, pdR, p_ref);
   const R cL = Ar<R>::sqrt(gamma * a.p * a.irho), cR = Ar<R>::sqrt(gamma * b.p * b.irho);
   const R lam = Ar<R>::fmax(Ar<R>::abs(a.v[L]) + cL, Ar<R>::abs(b.v[L]) + cR);
   R FL[DIM + 2], FR[DIM + 2];
@@ -239,8 +272,8 @@ __device__ __forceinline__ void wave_speeds(const R* uL, const R* uR, const Prim
 }
 
 template <int DIM, int L, class R>
-__device__ __forceinline__ void hll(const R* uL, const R* uR, R gamma, R* F) {
-  const Prim<DIM, R> a = prims<DIM>(uL, gamma - R(1)), b = prims<DIM>(uR, gamma - R(1));
+__device__ __forceinline__ void hll(const R* uL, const R* uR, R pdL, R pdR, R gamma, R p_ref, R* F) {
+  const Prim<DIM, R> a = prims<DIM>(uL, pdL, p_ref), b = prims<DIM>(uR, pdR, p_ref);
   R SL, SR;
   wave_speeds<DIM, L>(uL, uR, a, b, gamma, SL, SR);
   R FL[DIM + 2], FR[DIM + 2];
@@ -261,17 +294,17 @@ __device__ __forceinline__ void hll(const R* uL, const R* uR, R gamma, R* F) {
 
 // HLLC (Toro, Spruce and Speares): branches S_L >= 0 -> F_L; S* >= 0 -> F*_L; S_R > 0 ->
 // F*_R; else F_R.  Star state U*_K = rho_K (S_K - u_K)/(S_K - S*) (1, S* e_L + tangential,
-// E_K/rho_K + (S* - u_K)(S* + p_K/(rho_K (S_K - u_K)))).
+// E_K/rho_K + (S* - u_K)(S* + p_K/(rho_K (S_K - u_K)))).  p_R - p_L is taken as pd_R - pd_L.
 template <int DIM, int L, class R>
-__device__ __forceinline__ void hllc(const R* uL, const R* uR, R gamma, R* F) {
-  const Prim<DIM, R> a = prims<DIM>(uL, gamma - R(1)), b = prims<DIM>(uR, gamma - R(1));
+__device__ __forceinline__ void hllc(const R* uL, const R* uR, R pdL, R pdR, R gamma, R p_ref, R* F) {
+  const Prim<DIM, R> a = prims<DIM>(uL, pdL, p_ref), b = prims<DIM>(uR, pdR, p_ref);
   R SL, SR;
   wave_speeds<DIM, L>(uL, uR, a, b, gamma, SL, SR);
   R FL[DIM + 2], FR[DIM + 2];
   point_flux<DIM, L>(uL, a, FL);
   point_flux<DIM, L>(uR, b, FR);
   const R mL = a.rho * (SL - a.v[L]), mR = b.rho * (SR - b.v[L]);
-  const R Ss = Ar<R>::div(b.p - a.p + a.v[L] * mL - b.v[L] * mR, mL - mR);
+  const R Ss = Ar<R>::div(b.pd - a.pd + a.v[L] * mL - b.v[L] * mR, mL - mR);
   if (SL >= R(0)) {
 #pragma unroll
     for (int v = 0; v < DIM + 2; ++v) F[v] = FL[v];

@@ -26,6 +26,7 @@ struct StageArgs {
   int surface;         // DG_SURF_*
   int weak;            // 1: weak-form volume operator (surface lifts F* only)
   double rho_floor, p_floor;
+  double p_ref;        // constant subtracted from the pressure in the momentum flux
   double lift;         // 1 / w_0 (= 1 / w_N) of the GLL rule
   double Dv[(kMaxN + 1) * (kMaxN + 1)];  // volume operator, row-major (N+1)^2
 };
@@ -45,7 +46,7 @@ cudaError_t launch_max_speed(int dim, const double* U, long long stride, long lo
                              cudaStream_t s);
 
 // Evaluate a device two-point flux for n AoS state pairs.
-cudaError_t launch_two_point(int dim, int fp32, int kind, int l, int n, double gamma,
+cudaError_t launch_two_point(int dim, int fp32, int kind, int l, int n, double gamma, double p_ref,
                              const double* uL, const double* uR, double* F, cudaStream_t s);
 
 // Whether (dim, N) has compiled kernels.

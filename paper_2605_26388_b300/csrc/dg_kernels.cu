@@ -43,12 +43,13 @@ __device__ __forceinline__ int pair_index(int a, int b) {  // a < b
 }
 
 template <int DIM, int L, class R>
-__device__ __forceinline__ void surface_flux(int kind, const R* uL, const R* uR, R gamma, R* F) {
+__device__ __forceinline__ void surface_flux(int kind, const R* uL, const R* uR, R pdL, R pdR,
+                                             R gamma, R p_ref, R* F) {
   switch (kind) {
-    case 1: hllc<DIM, L>(uL, uR, gamma, F); break;
-    case 2: hll<DIM, L>(uL, uR, gamma, F); break;
-    case 3: ec_flux<DIM, L>(uL, uR, gamma - R(1), F); break;
-    default: rusanov<DIM, L>(uL, uR, gamma, F); break;
+    case 1: hllc<DIM, L>(uL, uR, pdL, pdR, gamma, p_ref, F); break;
+    case 2: hll<DIM, L>(uL, uR, pdL, pdR, gamma, p_ref, F); break;
+    case 3: ec_flux<DIM, L>(uL, uR, pdL, pdR, gamma - R(1), p_ref, F); break;
+    default: rusanov<DIM, L>(uL, uR, pdL, pdR, gamma, p_ref, F); break;
   }
 }
 
@@ -57,7 +58,10 @@ struct EulerStage {
   using G = Geo<DIM, N>;
   static constexpr int NV = G::NV, NP = G::NP, N1 = G::N1, EPB = G::EPB, NFN = G::NFN;
   static constexpr int NLINE = G::NLINE, NPAIR = G::NPAIR, T = G::THREADS;
-  static constexpr int NQ = EC ? (DIM + 3) : (DIM * NV);  // per-node staged quantities
+  // per-node staged quantities: EC -- rho, v_1..v_DIM, pd, beta = rho/p; strong/weak -- the
+  // DIM point fluxes (NV each) and pd
+  static constexpr int NQ = EC ? (DIM + 3) : (DIM * NV + 1);
+  static constexpr int PD = EC ? (DIM + 1) : (DIM * NV);  // slot of pd
   // shared-memory layout (in units of R)
   static constexpr int OFF_U = 0;                                 // [EPB][NV][NP]
   static constexpr int OFF_Q = OFF_U + EPB * NV * NP;             // [EPB][NQ][NP]
@@ -69,19 +73,19 @@ struct EulerStage {
 
   // point flux of direction L at node nd of element el from the staged state
   template <int L>
-  static __device__ __forceinline__ void staged_point_flux(const R* sm, int el, int nd, R gm1,
+  static __device__ __forceinline__ void staged_point_flux(const R* sm, int el, int nd, R p_ref,
                                                            R* F) {
     R u[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) u[v] = sm[OFF_U + (el * NV + v) * NP + nd];
-    const Prim<DIM, R> q = prims<DIM>(u, gm1);
+    const Prim<DIM, R> q = prims<DIM>(u, sm[OFF_Q + (el * NQ + PD) * NP + nd], p_ref);
     point_flux<DIM, L>(u, q, F);
   }
 
   // two-point volume term of direction L for this node (EC form)
   template <int L>
   static __device__ __forceinline__ void ec_direction(R* sm, const StageArgs& A, int el, int nd,
-                                                      bool active, R gm1, R igm1, R* acc) {
+                                                      bool active, R p_ref, R igm1, R* acc) {
     const int e0 = blockIdx.x * EPB;
     // pair phase: every pair (a<b) of every line, once
     for (int J = threadIdx.x; J < EPB * NLINE * NPAIR; J += T) {
@@ -101,8 +105,8 @@ struct EulerStage {
         vB[d] = Q[(1 + d) * NP + nb];
       }
       R F[NV];
-      ec_flux_prims<DIM, L>(Q[na], vA, Q[(DIM + 1) * NP + na], Q[(DIM + 2) * NP + na], Q[nb], vB,
-                            Q[(DIM + 1) * NP + nb], Q[(DIM + 2) * NP + nb], igm1, F);
+      ec_flux_prims<DIM, L>(Q[na], vA, Q[PD * NP + na], Q[(DIM + 2) * NP + na], Q[nb], vB,
+                            Q[PD * NP + nb], Q[(DIM + 2) * NP + nb], igm1, p_ref, F);
       R* X = sm + OFF_X + ((ej * NLINE + q) * NPAIR + p) * NV;
 #pragma unroll
       for (int v = 0; v < NV; ++v) X[v] = F[v];
@@ -124,7 +128,7 @@ struct EulerStage {
       // diagonal term: F#(U_i, U_i) = F(U_i); only the end nodes have D_ii != 0
       if (i == 0 || i == N) {
         R F[NV];
-        staged_point_flux<L>(sm, el, nd, gm1, F);
+        staged_point_flux<L>(sm, el, nd, p_ref, F);
         const R c = s * Dv[i * N1 + i];
 #pragma unroll
         for (int v = 0; v < NV; ++v) acc[v] -= c * F[v];
@@ -139,7 +143,7 @@ struct EulerStage {
     const R s = R(A.s[L]);
     const int q = G::node_line(L, nd), i = G::node_pos(L, nd);
     const R* Dv = sm + OFF_D;
-    const R* Fq = sm + OFF_Q + (el * DIM + L) * NV * NP;
+    const R* Fq = sm + OFF_Q + (el * NQ + L * NV) * NP;
 #pragma unroll
     for (int m = 0; m < N1; ++m) {
       const int n2 = G::line_node(L, q, m);
@@ -152,7 +156,7 @@ struct EulerStage {
   // one surface job in direction L: face node f of face `side` of element ej
   template <int L>
   static __device__ __forceinline__ void surface_job(R* sm, const StageArgs& A, int ej, int side,
-                                                     int f, R gamma) {
+                                                     int f, R gamma, R p_ref) {
     const int e = blockIdx.x * EPB + ej;
     const int ndo = G::line_node(L, f, side ? N : 0);
     // periodic neighbour element across this face
@@ -167,25 +171,31 @@ struct EulerStage {
     const int ndn = G::line_node(L, f, side ? 0 : N);
     const long long gn = A.base + (long long)en * NP + ndn;
     R own[NV], nbr[NV];
+    double n64[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       own[v] = sm[OFF_U + (ej * NV + v) * NP + ndo];
-      nbr[v] = Ar<R>::load(__ldg(A.U + v * A.stride + gn));
+      n64[v] = __ldg(A.U + v * A.stride + gn);
+      nbr[v] = Ar<R>::load(n64[v]);
     }
+    const R pd_own = sm[OFF_Q + (ej * NQ + PD) * NP + ndo];
+    double rhoe;
+    const R pd_nbr = pdev<DIM>(n64, nbr, A.gamma - 1.0, A.p_ref, rhoe);
     R uL[NV], uR[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       uL[v] = side ? own[v] : nbr[v];
       uR[v] = side ? nbr[v] : own[v];
     }
+    const R pdL = side ? pd_own : pd_nbr, pdR = side ? pd_nbr : pd_own;
     R Fs[NV];
-    surface_flux<DIM, L>(A.surface, uL, uR, gamma, Fs);  // the single call site
+    surface_flux<DIM, L>(A.surface, uL, uR, pdL, pdR, gamma, p_ref, Fs);  // the single call site
     R Fo[NV];
     if (A.weak) {
 #pragma unroll
       for (int v = 0; v < NV; ++v) Fo[v] = R(0);
     } else {
-      const Prim<DIM, R> q = prims<DIM>(own, gamma - R(1));
+      const Prim<DIM, R> q = prims<DIM>(own, pd_own, p_ref);
       point_flux<DIM, L>(own, q, Fo);
     }
     const R lf = (side ? R(-1) : R(1)) * R(A.s[L]) * R(A.lift);
@@ -201,7 +211,7 @@ struct EulerStage {
     const int el = t / NP, nd = t - (t / NP) * NP;
     const int e = blockIdx.x * EPB + el;
     const bool active = (el < EPB) && (e < A.n_elem);
-    const R gamma = R(A.gamma), gm1 = gamma - R(1), igm1 = R(1) / gm1;
+    const R gamma = R(A.gamma), gm1 = gamma - R(1), igm1 = R(1) / gm1, p_ref = R(A.p_ref);
 
     for (int k = t; k < N1 * N1; k += T) sm[OFF_D + k] = R(A.Dv[k]);
 
@@ -221,31 +231,22 @@ struct EulerStage {
         u[v] = Ar<R>::load(u64[v]);
         sm[OFF_U + (el * NV + v) * NP + nd] = u[v];
       }
-      const Prim<DIM, R> q = prims<DIM>(u, gm1);
-      // positivity of the state this stage reads (decided in FP64)
-      bool ok;
-      if (sizeof(R) == 8) {
-        ok = (u64[0] > 0.0) && (q.p > R(0));
-      } else {
-        ok = (u64[0] > 0.0) && (q.p > R(1e-4) * gm1 * u[DIM + 1]);
-        if (!ok && u64[0] > 0.0) {  // close call: recompute the pressure in FP64
-          double kin = 0.0;
-#pragma unroll
-          for (int d = 0; d < DIM; ++d) kin += u64[1 + d] * u64[1 + d];
-          ok = (A.gamma - 1.0) * (u64[DIM + 1] - 0.5 * kin / u64[0]) > 0.0;
-        }
-      }
+      // pressure deviation from the FP64 energy; positivity of the state this stage reads
+      // (rho > 0 and rho e > 0) decided in FP64
+      double rhoe;
+      const R pd = pdev<DIM>(u64, u, A.gamma - 1.0, A.p_ref, rhoe);
+      const Prim<DIM, R> q = prims<DIM>(u, pd, p_ref);
+      const bool ok = (u64[0] > 0.0) && (rhoe > 0.0);
       if (!ok) atomicOr(A.err, 2u);
+      R* Q = sm + OFF_Q + el * NQ * NP;
+      Q[PD * NP + nd] = pd;
       if (EC) {
-        R* Q = sm + OFF_Q + el * NQ * NP;
         Q[nd] = q.rho;
 #pragma unroll
         for (int d = 0; d < DIM; ++d) Q[(1 + d) * NP + nd] = q.v[d];
-        Q[(DIM + 1) * NP + nd] = q.p;
         Q[(DIM + 2) * NP + nd] = q.rho * Ar<R>::rcp(q.p);
       } else {
         R F[NV];
-        R* Q = sm + OFF_Q + el * NQ * NP;
         point_flux<DIM, 0>(u, q, F);
 #pragma unroll
         for (int v = 0; v < NV; ++v) Q[(0 * NV + v) * NP + nd] = F[v];
@@ -266,9 +267,9 @@ struct EulerStage {
 #pragma unroll
     for (int v = 0; v < NV; ++v) acc[v] = R(0);
     if constexpr (EC) {
-      ec_direction<0>(sm, A, el, nd, active, gm1, igm1, acc);
-      ec_direction<1>(sm, A, el, nd, active, gm1, igm1, acc);
-      if constexpr (DIM == 3) ec_direction<2>(sm, A, el, nd, active, gm1, igm1, acc);
+      ec_direction<0>(sm, A, el, nd, active, p_ref, igm1, acc);
+      ec_direction<1>(sm, A, el, nd, active, p_ref, igm1, acc);
+      if constexpr (DIM == 3) ec_direction<2>(sm, A, el, nd, active, p_ref, igm1, acc);
     } else {
       if (active) {
         sbp_direction<0>(sm, A, el, nd, acc);
@@ -286,9 +287,9 @@ struct EulerStage {
       const int f = r - face * NFN;
       if (e0 + ej >= A.n_elem) continue;
       const int l = face >> 1, side = face & 1;
-      if (l == 0) surface_job<0>(sm, A, ej, side, f, gamma);
-      else if (l == 1) surface_job<1>(sm, A, ej, side, f, gamma);
-      else if constexpr (DIM == 3) surface_job<2>(sm, A, ej, side, f, gamma);
+      if (l == 0) surface_job<0>(sm, A, ej, side, f, gamma, p_ref);
+      else if (l == 1) surface_job<1>(sm, A, ej, side, f, gamma, p_ref);
+      else if constexpr (DIM == 3) surface_job<2>(sm, A, ej, side, f, gamma, p_ref);
     }
     __syncthreads();
 
@@ -457,40 +458,46 @@ cudaError_t launch_max_speed(int dim, const double* U, long long stride, long lo
 // ---------------------------------------------------------------------------------------
 template <int DIM, int L, class R>
 __device__ void two_point_one(int kind, const double* uL, const double* uR, double gamma,
-                              double* F) {
+                              double p_ref, double* F) {
   R a[DIM + 2], b[DIM + 2], f[DIM + 2];
+  double a64[DIM + 2], b64[DIM + 2];
 #pragma unroll
   for (int v = 0; v < DIM + 2; ++v) {
-    a[v] = Ar<R>::load(uL[v]);
-    b[v] = Ar<R>::load(uR[v]);
+    a64[v] = uL[v];
+    b64[v] = uR[v];
+    a[v] = Ar<R>::load(a64[v]);
+    b[v] = Ar<R>::load(b64[v]);
   }
-  if (kind < 0) ec_flux<DIM, L>(a, b, R(gamma) - R(1), f);
-  else surface_flux<DIM, L>(kind, a, b, R(gamma), f);
+  double ea, eb;
+  const R pda = pdev<DIM>(a64, a, gamma - 1.0, p_ref, ea);
+  const R pdb = pdev<DIM>(b64, b, gamma - 1.0, p_ref, eb);
+  if (kind < 0) ec_flux<DIM, L>(a, b, pda, pdb, R(gamma) - R(1), R(p_ref), f);
+  else surface_flux<DIM, L>(kind, a, b, pda, pdb, R(gamma), R(p_ref), f);
 #pragma unroll
   for (int v = 0; v < DIM + 2; ++v) F[v] = Ar<R>::widen(f[v]);
 }
 
 template <int DIM, class R>
-__global__ void k_two_point(int kind, int l, int n, double gamma, const double* uL,
+__global__ void k_two_point(int kind, int l, int n, double gamma, double p_ref, const double* uL,
                             const double* uR, double* F) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int nv = DIM + 2;
-  if (l == 0) two_point_one<DIM, 0, R>(kind, uL + i * nv, uR + i * nv, gamma, F + i * nv);
-  else if (l == 1) two_point_one<DIM, 1, R>(kind, uL + i * nv, uR + i * nv, gamma, F + i * nv);
-  else if constexpr (DIM == 3) two_point_one<DIM, 2, R>(kind, uL + i * nv, uR + i * nv, gamma, F + i * nv);
+  if (l == 0) two_point_one<DIM, 0, R>(kind, uL + i * nv, uR + i * nv, gamma, p_ref, F + i * nv);
+  else if (l == 1) two_point_one<DIM, 1, R>(kind, uL + i * nv, uR + i * nv, gamma, p_ref, F + i * nv);
+  else if constexpr (DIM == 3) two_point_one<DIM, 2, R>(kind, uL + i * nv, uR + i * nv, gamma, p_ref, F + i * nv);
 }
 
-cudaError_t launch_two_point(int dim, int fp32, int kind, int l, int n, double gamma,
+cudaError_t launch_two_point(int dim, int fp32, int kind, int l, int n, double gamma, double p_ref,
                              const double* uL, const double* uR, double* F, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const int blocks = (n + 127) / 128;
   if (dim == 2) {
-    if (fp32) k_two_point<2, float><<<blocks, 128, 0, s>>>(kind, l, n, gamma, uL, uR, F);
-    else k_two_point<2, double><<<blocks, 128, 0, s>>>(kind, l, n, gamma, uL, uR, F);
+    if (fp32) k_two_point<2, float><<<blocks, 128, 0, s>>>(kind, l, n, gamma, p_ref, uL, uR, F);
+    else k_two_point<2, double><<<blocks, 128, 0, s>>>(kind, l, n, gamma, p_ref, uL, uR, F);
   } else {
-    if (fp32) k_two_point<3, float><<<blocks, 128, 0, s>>>(kind, l, n, gamma, uL, uR, F);
-    else k_two_point<3, double><<<blocks, 128, 0, s>>>(kind, l, n, gamma, uL, uR, F);
+    if (fp32) k_two_point<3, float><<<blocks, 128, 0, s>>>(kind, l, n, gamma, p_ref, uL, uR, F);
+    else k_two_point<3, double><<<blocks, 128, 0, s>>>(kind, l, n, gamma, p_ref, uL, uR, F);
   }
   return cudaGetLastError();
 }

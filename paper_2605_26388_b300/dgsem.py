@@ -45,7 +45,7 @@ class MeshDesc(C.Structure):
 class Physics(C.Structure):
     _fields_ = [("equations", C.c_int), ("volume", C.c_int), ("surface", C.c_int),
                 ("precision", C.c_int), ("gamma", C.c_double), ("rho_floor", C.c_double),
-                ("p_floor", C.c_double)]
+                ("p_floor", C.c_double), ("p_ref", C.c_double)]
 
 
 _lib = None
@@ -126,13 +126,13 @@ class Solver:
     SoA layout U[var, node] (node = instance offset + elem * n_p + local node)."""
 
     def __init__(self, meshes, volume=VOL_STRONG, surface=SURF_RUSANOV, precision=FP64,
-                 gamma=1.4, rho_floor=0.0, p_floor=0.0, stream=None):
+                 gamma=1.4, rho_floor=0.0, p_floor=0.0, p_ref=0.0, stream=None):
         import torch
         if isinstance(meshes, Mesh):
             meshes = [meshes]
         self.meshes = list(meshes)
         arr = (MeshDesc * len(self.meshes))(*[m.c() for m in self.meshes])
-        phys = Physics(DG_EULER, volume, surface, precision, gamma, rho_floor, p_floor)
+        phys = Physics(DG_EULER, volume, surface, precision, gamma, rho_floor, p_floor, p_ref)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream

@@ -43,7 +43,7 @@ def test_library_gll_matches_oracle(dg, orc, N):
 
 def _init(dg, mesh, **kw):
     phys = dg.Physics(dg.DG_EULER, kw.get("volume", 0), kw.get("surface", 0), kw.get("precision", 0),
-                      kw.get("gamma", 1.4), 0.0, 0.0)
+                      kw.get("gamma", 1.4), 0.0, 0.0, kw.get("p_ref", 0.0))
     arr = (dg.MeshDesc * 1)(mesh)
     h = C.c_void_p()
     st = dg.lib().dg_init_mesh(arr, 1, C.byref(phys), None, C.byref(h))
