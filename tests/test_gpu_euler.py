@@ -160,11 +160,13 @@ def test_tgv_full_size_sampled_stage(orc, dg, torch, prec):
     got = out.cpu().numpy().reshape(U0.shape)[:, elems, :]
     tol = 1e-12 if prec == 0 else 1e-5
     assert rel_l2(got, ref) <= tol, rel_l2(got, ref)
-    # the increment dt L carries all of the residual's arithmetic; in FP64 it matches to
-    # round-off, in FP32 the low-Mach residual keeps about four digits
-    inc_ref = ref - U0[:, elems, :]
-    inc_got = got - U0[:, elems, :]
-    assert rel_l2(inc_got, inc_ref) <= (1e-10 if prec == 0 else 2e-3), rel_l2(inc_got, inc_ref)
+    del out
+    # the residual itself, as one vector (its mass part is a near-cancellation, ~1e-7, in the
+    # divergence-free vortex): FP64 to round-off; FP32 keeps about four digits at Ma 0.1
+    Lg = S.rhs(Ud).cpu().numpy().reshape(U0.shape)[:, elems, :]
+    S.check()
+    err = np.linalg.norm(Lg - L) / np.linalg.norm(L)
+    assert err <= (1e-12 if prec == 0 else 2e-3), err
 
 
 @pytest.mark.parametrize("kind", [-1, 0, 1, 2])
@@ -183,11 +185,18 @@ def test_two_point_flux_parity(orc, dg, torch, kind, dim, prec):
     scale = 10.0 ** (-9.0 * wl.uniform(95, n))
     uR = uL * (1.0 + scale[:, None] * (wl.uniform(96, n * (dim + 2)).reshape(n, dim + 2) - 0.5))
     tol = 1e-13 if prec == 0 else 2e-6
+    # magnitude of the terms that enter the flux: |F| and lambda |U| (lambda = |v| + c); FP32
+    # rounding of the inputs alone is ~6e-8 of it
+    rho = uL[:, 0]
+    v = uL[:, 1:dim + 1] / rho[:, None]
+    pp = (GAMMA - 1) * (uL[:, dim + 1] - 0.5 * rho * np.sum(v * v, axis=1))
+    lam = np.max(np.abs(v), axis=1) + np.sqrt(GAMMA * np.abs(pp) / rho)
     for l in range(dim):
         got = S.two_point_flux(kind, l, torch.from_numpy(uL).cuda(), torch.from_numpy(uR).cuda()).cpu().numpy()
         ref = np.array([orc.two_point_flux(kind, dim, l, GAMMA, a, b) for a, b in zip(uL, uR)])
         ref[:, 1 + l] -= 0.8  # the library reports momentum fluxes with p - p_ref
-        rel = np.abs(got - ref) / (np.abs(ref) + np.max(np.abs(ref), axis=1, keepdims=True))
+        scale = np.max(np.abs(ref), axis=1) + lam * np.max(np.abs(uL), axis=1)
+        rel = np.abs(got - ref) / scale[:, None]
         k = np.unravel_index(np.argmax(rel), rel.shape)
         assert rel[k] <= tol, (rel[k], k, uL[k[0]], uR[k[0]], got[k[0]], ref[k[0]])
 
