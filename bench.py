@@ -189,6 +189,10 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=None)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--only", default="both", choices=["both", "fp32", "fp64"],
+                    help="precision(s) to time (profiling runs)")
+    ap.add_argument("--nel", type=int, default=NEL, help="elements per direction (profiling runs)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -196,6 +200,9 @@ def main():
         return
 
     import torch
+    global NEL, DOF
+    NEL = args.nel
+    DOF = NEL ** 3 * NP * NV
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
     if ws > 1:
@@ -241,10 +248,14 @@ def main():
         return S, dt, ms, clk.summary()
 
     fp64_steps = args.fp64_steps or max(3, args.steps // 10)
-    S32, dt, ms32, clk32 = run(dgsem.FP32_MIXED, args.steps, args.warmup)
-    S32.close()
-    S64, _, ms64, clk64 = run(dgsem.FP64, fp64_steps, 3)
-    S64.close()
+    ms32 = ms64 = None
+    clk32 = clk64 = None
+    if args.only in ("both", "fp32"):
+        S32, dt, ms32, clk32 = run(dgsem.FP32_MIXED, args.steps, args.warmup)
+        S32.close()
+    if args.only in ("both", "fp64"):
+        S64, dt, ms64, clk64 = run(dgsem.FP64, fp64_steps, 3)
+        S64.close()
 
     def roofline(ms, steps, prec):
         launch_ms = ms / (3 * steps)
@@ -256,10 +267,51 @@ def main():
                 "avg_launch_ms": launch_ms, "alg_bytes_per_launch": alg}
 
     total_updates = 3 * DOF * args.steps * ws
-    value = total_updates / (ms32 * 1e-3)
+    value = total_updates / (ms32 * 1e-3) if ms32 else None
+    if args.no_e2e or ms32 is None:
+        e2e = None
+    else:
+        e2e = run_e2e(args, U0, dt, ws, barrier)
+    if rank != 0:
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+    cpu = None if args.no_cpu_baseline or ws > 1 else oracle_sample()
+    fp64 = None
+    if ms64:
+        fp64 = {"value": 3 * DOF * fp64_steps * ws / (ms64 * 1e-3), "unit": "DOF-updates/s", "steps": fp64_steps,
+                "ms_per_step": ms64 / fp64_steps, "roofline": roofline(ms64, fp64_steps, "fp64"),
+                "bound_note": "FP64-pipe bound on B300 (measured DFMA rate 475 G/s)", "clocks": clk64}
+    line = {
+        "metric": "RK-stage DOF-updates/s (3D Euler DGSEM N=4, TGV Ma 0.1, EC flux differencing + HLLC; FP32-mixed vs FP64)",
+        "value": value, "unit": "DOF-updates/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms32 / args.steps if ms32 else None, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 flux / f64 state", "data": "synthetic",
+        "config": {"workload": WORKLOAD if NEL == 64 else f"{WORKLOAD} (profiling size {NEL}^3)",
+                   "mesh": f"{NEL}^3 periodic on [0,2pi]^3", "N": N, "dof": DOF,
+                   "precision": "fp32_mixed", "dt": dt, "cfl": CFL, "p_ref": P_REF,
+                   "l2": "inputs larger than L2: three state buffers of %.2f GB per replica" % (DOF * 8 / 1e9),
+                   "parallelism": f"replicas x{ws}"},
+        "roofline": roofline(ms32, args.steps, "fp32_mixed") if ms32 else None,
+        "fp64": fp64,
+        "clocks": clk32 if clk32 else clk64,
+        "e2e": e2e,
+        "gpu_launches": 3 * args.steps,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
 
-    # end to end through the C-ABI with host buffers: every step uploads the state from
-    # pinned host memory, advances one SSP-RK3 step, and reads the new state back
+
+def run_e2e(args, U0, dt, ws, barrier):
+    """The same metric through the C-ABI with host buffers: every step uploads the state from
+    pinned host memory, advances one SSP-RK3 step and reads the new state back."""
+    import torch
+    from paper_2605_26388_b300 import dgsem
+
     host_in = torch.from_numpy(U0).pin_memory()
     host_out = torch.empty_like(host_in).pin_memory()
     Se = dgsem.Solver(dgsem.Mesh(3, N, (NEL,) * 3, (0.0,) * 3, (2 * math.pi,) * 3), volume=dgsem.VOL_EC,
@@ -282,39 +334,9 @@ def main():
     barrier()
     Se.close()
     nbytes = U0.nbytes
-    e2e = {"value": 3 * DOF * args.e2e_steps * ws / e2e_s, "unit": "DOF-updates/s",
-           "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
-           "note": "per step: dg_set_state from pinned host memory, one SSP-RK3 step, dg_get_state to pinned host memory"}
-
-    if rank != 0:
-        if ws > 1:
-            import torch.distributed as dist
-            dist.destroy_process_group()
-        return
-    cpu = None if args.no_cpu_baseline or ws > 1 else oracle_sample()
-    line = {
-        "metric": "RK-stage DOF-updates/s (3D Euler DGSEM N=4, TGV Ma 0.1, EC flux differencing + HLLC; FP32-mixed vs FP64)",
-        "value": value, "unit": "DOF-updates/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms32 / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 flux / f64 state", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "mesh": f"{NEL}^3 periodic on [0,2pi]^3", "N": N, "dof": DOF,
-                   "precision": "fp32_mixed", "dt": dt, "cfl": CFL,
-                   "l2": "inputs larger than L2: three 1.31 GB state buffers per replica",
-                   "parallelism": f"replicas x{ws}"},
-        "roofline": roofline(ms32, args.steps, "fp32_mixed"),
-        "fp64": {"value": 3 * DOF * fp64_steps * ws / (ms64 * 1e-3), "unit": "DOF-updates/s", "steps": fp64_steps,
-                 "ms_per_step": ms64 / fp64_steps, "roofline": roofline(ms64, fp64_steps, "fp64"),
-                 "bound_note": "FP64-pipe bound on B300 (measured DFMA rate 475 G/s)", "clocks": clk64},
-        "clocks": clk32,
-        "e2e": e2e,
-        "gpu_launches": 3 * args.steps,
-        "cpu_baseline": cpu,
-    }
-    print(json.dumps(line), flush=True)
-    if ws > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
-
+    return {"value": 3 * DOF * args.e2e_steps * ws / e2e_s, "unit": "DOF-updates/s",
+            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+            "note": "per step: dg_set_state from pinned host memory, one SSP-RK3 step, dg_get_state to pinned host memory"}
 
 if __name__ == "__main__":
     main()
