@@ -181,6 +181,7 @@ def run_reference(args):
 
 
 def main():
+    global NEL, DOF
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=60)
@@ -200,7 +201,6 @@ def main():
         return
 
     import torch
-    global NEL, DOF
     NEL = args.nel
     DOF = NEL ** 3 * NP * NV
     ws, rank, local = dist_env()
