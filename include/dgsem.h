@@ -50,7 +50,8 @@ typedef enum {
   DG_ECUDA = -3,        /* a CUDA runtime call failed */
   DG_ENONFINITE = -4,   /* a kernel produced a non-finite value */
   DG_EPOSITIVITY = -5,  /* a kernel read a state with rho <= 0 or p <= 0 */
-  DG_EUNSUPPORTED = -6  /* valid but not implemented (e.g. non-periodic boundaries) */
+  DG_EUNSUPPORTED = -6, /* valid but not implemented (e.g. non-periodic boundaries) */
+  DG_ETOOLARGE = -7     /* more instances than dg_max_dt_noalloc's static scratch holds */
 } dg_status;
 
 enum { DG_EULER = 0 };
@@ -148,6 +149,27 @@ DG_API dg_status dg_gll(int N, double* x, double* w, double* D);
  * precision and gamma.  Test and inspection aid. */
 DG_API dg_status dg_two_point_flux(dg_ctx* ctx, int kind, int l, int n, const double* uL,
                             const double* uR, double* F);
+
+/* The time-step bound of dg_max_dt() for callers that cannot allocate GPU memory -- for
+ * example code running under another framework's caching allocator, which has already
+ * reserved the device's memory, or an application that fixes its GPU footprint up front.
+ * The paper has no counterpart; this is an interface convenience.  It needs no context:
+ * the caller passes the instance descriptions (as for dg_init_mesh), gamma, a device
+ * pointer U to a state in the library's SoA layout (instances concatenated in the order
+ * given), cfl, and a cudaStream_t (NULL = legacy default stream).  *dt_out (host) receives
+ * min over instances of cfl * dx_min / ((2N+1) * max(|u| + a)).  If msg is not NULL it
+ * receives a static description of any error.
+ * It calls no cudaMalloc/cudaFree: the per-instance reduction scratch is a static device
+ * array of DG_NOALLOC_MAX_INSTANCES 64-bit slots inside the library, held by every GPU that
+ * loads the library until exit.  n_inst above that limit returns DG_ETOOLARGE.  The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress), so make that
+ * first call before any stream capture.  All calls share the array and each clears the slots
+ * it uses; calls that overlap on the GPU (different streams or threads) race and must be
+ * serialized by the caller.  Synchronizes the stream. */
+#define DG_NOALLOC_MAX_INSTANCES 4096
+DG_API dg_status dg_max_dt_noalloc(const dg_mesh_desc* inst, int n_inst, double gamma,
+                                   const double* U, double cfl, void* cuda_stream,
+                                   double* dt_out, const char** msg);
 
 /* Message of the last error on this context (static string if ctx is NULL). */
 DG_API const char* dg_last_error(const dg_ctx* ctx);

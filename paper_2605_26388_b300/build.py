@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libdgsem.so")
-SOURCES = ["dg_api.cu", "dg_kernels.cu"]
+SOURCES = ["dg_api.cu", "dg_kernels.cu", "dg_noalloc.cu"]
 HEADERS = ["dg_device.cuh", "dg_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

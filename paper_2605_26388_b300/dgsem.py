@@ -17,18 +17,20 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_lib", "libdgsem.so")
 
 DG_OK, DG_EINVAL, DG_ENOMEM, DG_ECUDA, DG_ENONFINITE, DG_EPOSITIVITY, DG_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
+DG_ETOOLARGE = -7
+NOALLOC_MAX_INSTANCES = 4096
 DG_EULER = 0
 VOL_STRONG, VOL_WEAK, VOL_EC = 0, 1, 2
 SURF_RUSANOV, SURF_HLLC, SURF_HLL, SURF_EC = 0, 1, 2, 3
 FP64, FP32_MIXED = 0, 1
 
 _STATUS = {0: "DG_OK", -1: "DG_EINVAL", -2: "DG_ENOMEM", -3: "DG_ECUDA", -4: "DG_ENONFINITE",
-           -5: "DG_EPOSITIVITY", -6: "DG_EUNSUPPORTED"}
+           -5: "DG_EPOSITIVITY", -6: "DG_EUNSUPPORTED", -7: "DG_ETOOLARGE"}
 
 # Every entry point include/dgsem.h declares (checked by the CPU tests).
 EXPORTS = ["dg_init_mesh", "dg_state_size", "dg_instance_offset", "dg_set_state", "dg_get_state",
            "dg_rhs", "dg_rk_stage", "dg_rk_step", "dg_max_dt", "dg_check", "dg_gll",
-           "dg_two_point_flux", "dg_last_error", "dg_free"]
+           "dg_two_point_flux", "dg_max_dt_noalloc", "dg_last_error", "dg_free"]
 
 
 class DGError(RuntimeError):
@@ -71,6 +73,8 @@ def lib():
         L.dg_check.argtypes = [vp]
         L.dg_gll.argtypes = [ip, dp, dp, dp]
         L.dg_two_point_flux.argtypes = [vp, ip, ip, ip, vp, vp, vp]
+        L.dg_max_dt_noalloc.argtypes = [C.POINTER(MeshDesc), ip, C.c_double, vp, C.c_double, vp, dp,
+                                         C.POINTER(C.c_char_p)]
         L.dg_last_error.argtypes = [vp]
         L.dg_last_error.restype = C.c_char_p
         L.dg_free.argtypes = [vp]
