@@ -158,6 +158,28 @@ void stage_args(const dg_ctx* c, int i, dg::StageArgs& a) {
   a.lift = 1.0 / w[0];
 }
 
+// Precompute the per-launch scalars in both precisions and the uniform flags.
+void fill_scalars(dg::StageArgs& a) {
+  auto& d = a.pd;
+  for (int l = 0; l < 3; ++l) d.s[l] = a.s[l];
+  d.lift = a.lift;
+  d.gamma = a.gamma;
+  d.gm1 = a.gamma - 1.0;
+  d.igm1 = 1.0 / (a.gamma - 1.0);
+  d.p_ref = a.p_ref;
+  d.cbdt = a.cb * a.dt;
+  auto& f = a.pf;
+  for (int l = 0; l < 3; ++l) f.s[l] = (float)d.s[l];
+  f.lift = (float)d.lift;
+  f.gamma = (float)d.gamma;
+  f.gm1 = (float)a.gamma - 1.0f;
+  f.igm1 = 1.0f / f.gm1;
+  f.p_ref = (float)d.p_ref;
+  f.cbdt = (float)d.cbdt;
+  a.need_un = (a.mode == 1 && a.ca != 0.0) ? 1 : 0;
+  a.floor_on = (a.rho_floor > 0.0 || a.p_floor > 0.0) ? 1 : 0;
+}
+
 // One fused launch per instance: mode 0 writes L(U), mode 1 the stage update.
 dg_status run_stage(dg_ctx* c, const double* U, const double* Un, double* out, int mode,
                     double ca, double cb, double dt, cudaStream_t s) {
@@ -171,6 +193,7 @@ dg_status run_stage(dg_ctx* c, const double* U, const double* Un, double* out, i
     a.ca = ca;
     a.cb = cb;
     a.dt = dt;
+    fill_scalars(a);
     cudaError_t e = dg::launch_euler_stage(c->inst[i].dim, c->inst[i].N,
                                            c->phys.volume == DG_VOL_EC,
                                            c->phys.precision == DG_FP32_MIXED, a, s);

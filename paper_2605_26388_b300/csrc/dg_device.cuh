@@ -22,16 +22,17 @@ namespace dg {
 __device__ __forceinline__ float d2f_rn(double x) {
   const uint32_t hi = (uint32_t)__double2hiint(x);
   const uint32_t lo = (uint32_t)__double2loint(x);
-  const uint32_t sign = hi & 0x80000000u;
-  const int ex = (int)((hi >> 20) & 0x7ffu);
-  const uint32_t man = ((hi & 0x000fffffu) << 3) | (lo >> 29);  // top 23 mantissa bits
-  const uint32_t rest = lo & 0x1fffffffu;                         // 29 discarded bits
-  const uint32_t up = (rest > 0x10000000u) | ((rest == 0x10000000u) & man);
-  const int fe = ex - 1023 + 127;
-  uint32_t bits = ((uint32_t)fe << 23) + man + (up & 1u);  // mantissa carry bumps exponent
-  if (fe <= 0) bits = 0u;                                   // below FLT_MIN: flush to zero
-  if (fe >= 255) bits = 0x7f800000u | ((ex == 0x7ff && ((hi & 0xfffffu) | lo)) ? 0x400000u : 0u);
-  return __uint_as_float(sign | bits);
+  const uint32_t ah = hi & 0x7fffffffu;
+  // (ah << 3) | (lo >> 29): the low 9 exponent bits over the top 23 mantissa bits.
+  // Subtracting 384 (= 896 mod 512) in that 9-bit field rebiases 1023 -> 127 for every
+  // exponent that has a normal float image (the field result is then 1..254).
+  uint32_t b = __funnelshift_l(lo, ah, 3) - 0xC0000000u;
+  const uint32_t rest = lo & 0x1fffffffu;                        // 29 discarded bits
+  b += (rest > 0x10000000u) | ((rest == 0x10000000u) & b);      // nearest, ties to even
+  if (ah < 0x38100000u) b = 0u;                                  // below FLT_MIN: flush to zero
+  if (ah >= 0x47f00000u)                                         // overflow, inf, nan
+    b = 0x7f800000u | ((ah > 0x7ff00000u || (ah == 0x7ff00000u && lo)) ? 0x400000u : 0u);
+  return __uint_as_float(b | (hi & 0x80000000u));
 }
 
 __device__ __forceinline__ double f2d(float f) {
@@ -228,19 +229,17 @@ __device__ __forceinline__ void ec_flux_prims(R rL, const R* vL, R pdL, R bL, R 
 }
 
 template <int DIM, int L, class R>
-__device__ __forceinline__ void ec_flux(const R* uL, const R* uR, R pdL, R pdR, R gm1, R p_ref,
-                                        R* F) {
-  const Prim<DIM, R> a = prims<DIM>(uL, pdL, p_ref), b = prims<DIM>(uR, pdR, p_ref);
+__device__ __forceinline__ void ec_flux(const Prim<DIM, R>& a, const Prim<DIM, R>& b, R igm1,
+                                        R p_ref, R* F) {
   ec_flux_prims<DIM, L>(a.rho, a.v, a.pd, a.rho * Ar<R>::rcp(a.p), b.rho, b.v, b.pd,
-                        b.rho * Ar<R>::rcp(b.p), Ar<R>::rcp(gm1), p_ref, F);
+                        b.rho * Ar<R>::rcp(b.p), igm1, p_ref, F);
 }
 
 // Local Lax-Friedrichs (Rusanov): F* = (F_L + F_R)/2 - lambda/2 (U_R - U_L),
 // lambda = max(|u_L| + a_L, |u_R| + a_R) along L (Sec. 3.1.1 "Lax-Friedrichs").
 template <int DIM, int L, class R>
-__device__ __forceinline__ void rusanov(const R* uL, const R* uR, R pdL, R pdR, R gamma, R p_ref,
-                                        R* F) {
-  const Prim<DIM, R> a = prims<DIM>(uL, pdL, p_ref), b = prims<DIM>(uR, pdR, p_ref);
+__device__ __forceinline__ void rusanov(const R* uL, const Prim<DIM, R>& a, const R* uR,
+                                        const Prim<DIM, R>& b, R gamma, R* F) {
   const R cL = Ar<R>::sqrt(gamma * a.p * a.irho), cR = Ar<R>::sqrt(gamma * b.p * b.irho);
   const R lam = Ar<R>::fmax(Ar<R>::abs(a.v[L]) + cL, Ar<R>::abs(b.v[L]) + cR);
   R FL[DIM + 2], FR[DIM + 2];
@@ -272,8 +271,8 @@ __device__ __forceinline__ void wave_speeds(const R* uL, const R* uR, const Prim
 }
 
 template <int DIM, int L, class R>
-__device__ __forceinline__ void hll(const R* uL, const R* uR, R pdL, R pdR, R gamma, R p_ref, R* F) {
-  const Prim<DIM, R> a = prims<DIM>(uL, pdL, p_ref), b = prims<DIM>(uR, pdR, p_ref);
+__device__ __forceinline__ void hll(const R* uL, const Prim<DIM, R>& a, const R* uR,
+                                    const Prim<DIM, R>& b, R gamma, R* F) {
   R SL, SR;
   wave_speeds<DIM, L>(uL, uR, a, b, gamma, SL, SR);
   R FL[DIM + 2], FR[DIM + 2];
@@ -296,8 +295,8 @@ __device__ __forceinline__ void hll(const R* uL, const R* uR, R pdL, R pdR, R ga
 // F*_R; else F_R.  Star state U*_K = rho_K (S_K - u_K)/(S_K - S*) (1, S* e_L + tangential,
 // E_K/rho_K + (S* - u_K)(S* + p_K/(rho_K (S_K - u_K)))).  p_R - p_L is taken as pd_R - pd_L.
 template <int DIM, int L, class R>
-__device__ __forceinline__ void hllc(const R* uL, const R* uR, R pdL, R pdR, R gamma, R p_ref, R* F) {
-  const Prim<DIM, R> a = prims<DIM>(uL, pdL, p_ref), b = prims<DIM>(uR, pdR, p_ref);
+__device__ __forceinline__ void hllc(const R* uL, const Prim<DIM, R>& a, const R* uR,
+                                     const Prim<DIM, R>& b, R gamma, R* F) {
   R SL, SR;
   wave_speeds<DIM, L>(uL, uR, a, b, gamma, SL, SR);
   R FL[DIM + 2], FR[DIM + 2];

@@ -28,6 +28,16 @@ struct StageArgs {
   double rho_floor, p_floor;
   double p_ref;        // constant subtracted from the pressure in the momentum flux
   double lift;         // 1 / w_0 (= 1 / w_N) of the GLL rule
+  // Host-precomputed copies of the scalars above in both precisions, so that no thread
+  // converts a double parameter to float (that conversion issues more slowly than an FP64
+  // FMA on sm_103a) or evaluates a double comparison of a uniform flag.
+  template <class R> struct ScalarsT {
+    R s[3], lift, gamma, gm1, igm1, p_ref, cbdt;
+  };
+  ScalarsT<double> pd;
+  ScalarsT<float> pf;
+  int need_un;         // mode == 1 and ca != 0
+  int floor_on;        // rho_floor > 0 or p_floor > 0
   double Dv[(kMaxN + 1) * (kMaxN + 1)];  // volume operator, row-major (N+1)^2
 };
 
