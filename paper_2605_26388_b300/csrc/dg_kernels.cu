@@ -272,22 +272,55 @@ struct EulerStage {
     }
   }
 
-  // ---- phase 3: one face node of face (L, side) of element ej ----
-  template <int L>
+  // Cyclic relabelling of the axes that makes direction l the first one: the Euler fluxes
+  // are unchanged by a relabelling of the axes, so every face job evaluates its Riemann
+  // flux with one instantiation (normal along axis 0) -- one code path for all faces, no
+  // divergence between the directions of a warp.
+  static __device__ __forceinline__ void to_face_axes(const R* in, R* out, int l) {
+    out[0] = in[0];
+    out[NV - 1] = in[NV - 1];
+    if constexpr (DIM == 2) {
+      out[1] = l ? in[2] : in[1];
+      out[2] = l ? in[1] : in[2];
+    } else {
+      out[1] = l == 0 ? in[1] : (l == 1 ? in[2] : in[3]);
+      out[2] = l == 0 ? in[2] : (l == 1 ? in[3] : in[1]);
+      out[3] = l == 0 ? in[3] : (l == 1 ? in[1] : in[2]);
+    }
+  }
+  static __device__ __forceinline__ void from_face_axes(const R* in, R* out, int l) {
+    out[0] = in[0];
+    out[NV - 1] = in[NV - 1];
+    if constexpr (DIM == 2) {
+      out[1] = l ? in[2] : in[1];
+      out[2] = l ? in[1] : in[2];
+    } else {
+      out[1] = l == 0 ? in[1] : (l == 1 ? in[3] : in[2]);
+      out[2] = l == 0 ? in[2] : (l == 1 ? in[1] : in[3]);
+      out[3] = l == 0 ? in[3] : (l == 1 ? in[2] : in[1]);
+    }
+  }
+
+  // ---- phase 3: one face node (face r.face of element r.jel) ----
   static __device__ __forceinline__ void face_job(R* sm, const double* trace, const StageArgs& A,
                                                   const Role& r, R gamma, R igm1, R p_ref) {
-    const int ej = r.jel, side = r.face & 1;
-    R own[NV], nbr[NV];
+    const int ej = r.jel, side = r.face & 1, l = r.face >> 1;
+    R own0[NV], nbr0[NV];
     double n64[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      own[v] = sm[OFF_U + (ej * NV + v) * NP + r.ndo];
+      own0[v] = sm[OFF_U + (ej * NV + v) * NP + r.ndo];
       n64[v] = trace[((ej * NF + r.face) * NV + v) * NFN + r.f];
-      nbr[v] = Ar<R>::load(n64[v]);
+      nbr0[v] = Ar<R>::load(n64[v]);
     }
     double rhoe;
-    const Prim<DIM, R> po = prims<DIM>(own, sm[OFF_Q + (ej * NQ + PD) * NP + r.ndo], p_ref);
-    const Prim<DIM, R> pn = prims<DIM>(nbr, pdev<DIM>(n64, nbr, A.pd.gm1, A.pd.p_ref, rhoe), p_ref);
+    const R pd_own = sm[OFF_Q + (ej * NQ + PD) * NP + r.ndo];
+    const R pd_nbr = pdev<DIM>(n64, nbr0, A.pd.gm1, A.pd.p_ref, rhoe);
+    R own[NV], nbr[NV];
+    to_face_axes(own0, own, l);
+    to_face_axes(nbr0, nbr, l);
+    const Prim<DIM, R> po = prims<DIM>(own, pd_own, p_ref);
+    const Prim<DIM, R> pn = prims<DIM>(nbr, pd_nbr, p_ref);
     R uL[NV], uR[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
@@ -297,18 +330,19 @@ struct EulerStage {
     const Prim<DIM, R>& a = side ? po : pn;
     const Prim<DIM, R>& b = side ? pn : po;
     R Fs[NV];
-    surface_flux<DIM, L>(A.surface, uL, a, uR, b, gamma, igm1, p_ref, Fs);  // the single call site
-    R Fo[NV];
-    if (A.weak) {
+    surface_flux<DIM, 0>(A.surface, uL, a, uR, b, gamma, igm1, p_ref, Fs);  // the single call site
+    if (!A.weak) {
+      R Fo[NV];
+      point_flux<DIM, 0>(own, po, Fo);
 #pragma unroll
-      for (int v = 0; v < NV; ++v) Fo[v] = R(0);
-    } else {
-      point_flux<DIM, L>(own, po, Fo);
+      for (int v = 0; v < NV; ++v) Fs[v] -= Fo[v];
     }
-    const R lf = (side ? R(-1) : R(1)) * sc<R>(A).s[L] * sc<R>(A).lift;
+    R Fj[NV];
+    from_face_axes(Fs, Fj, l);
+    const R lf = (side ? R(-1) : R(1)) * sc<R>(A).s[l] * sc<R>(A).lift;
     R* Sx = sm + OFF_S + ((ej * NF + r.face) * NFN + r.f) * NV;
 #pragma unroll
-    for (int v = 0; v < NV; ++v) Sx[v] = lf * (Fs[v] - Fo[v]);
+    for (int v = 0; v < NV; ++v) Sx[v] = lf * Fj[v];
   }
 
   template <int L>
@@ -391,12 +425,7 @@ struct EulerStage {
       }
     }
     // phase 3: face jobs
-    if (t < NJS && e0 + r.jel < A.n_elem) {
-      const int l = r.face >> 1;
-      if (l == 0) face_job<0>(sm, TR, A, r, gamma, igm1, p_ref);
-      else if (l == 1) face_job<1>(sm, TR, A, r, gamma, igm1, p_ref);
-      else if constexpr (DIM == 3) face_job<2>(sm, TR, A, r, gamma, igm1, p_ref);
-    }
+    if (t < NJS && e0 + r.jel < A.n_elem) face_job(sm, TR, A, r, gamma, igm1, p_ref);
     __syncthreads();
 
     // phase 4: gather, then L or the stage update
