@@ -131,6 +131,25 @@ DG_API dg_status dg_rk_stage(dg_ctx* ctx, int stage, const double* Un, const dou
  * collect device-side errors. */
 DG_API dg_status dg_rk_step(dg_ctx* ctx, double dt, int n_steps);
 
+/* Launch modes for contexts with several instances. */
+enum { DG_LAUNCH_PER_INSTANCE = 0, DG_LAUNCH_BATCHED = 1 };
+
+/* How a stage is launched over the context's instances (SURVEY batched form; the paper runs
+ * one problem at a time): one fused launch per instance, or one persistent launch per stage
+ * over a work list of (instance, element group) items covering every instance -- the default
+ * when n_inst > 1.  group_scale (1, or 2 in 2D) multiplies the elements per work item;
+ * ctas_per_sm caps the persistent grid (0 = as many CTAs as fit); order 0 puts the heaviest
+ * items (degree, then instance) first, 1 keeps instance order.  Synchronizes the stream and
+ * rebuilds the work list; DG_EINVAL on an out-of-range choice. */
+DG_API dg_status dg_set_launch(dg_ctx* ctx, int mode, int group_scale, int ctas_per_sm, int order);
+
+/* Autotuner for the launch configuration: times n_reps SSP-RK3 steps of size dt for the
+ * per-instance mode and every batched choice (group_scale x ctas_per_sm in {0,1,2} x order),
+ * restores the context-held state afterwards, keeps the fastest configuration and reports it:
+ * config_out[4] = {mode, group_scale, ctas_per_sm, order}, *ms_out (host, may be NULL) = its
+ * time per step in ms.  Allocates one temporary state copy; synchronizes the stream. */
+DG_API dg_status dg_autotune(dg_ctx* ctx, double dt, int n_reps, int* config_out, double* ms_out);
+
 /* Convective time-step bound of Eq. dt_hyp on the context-held state:
  *   dt = cfl * dx_min / ((2N+1) * max over nodes of (|u| + a)),
  * taking the minimum over instances.  Synchronizes the stream; *dt_out is a host double. */

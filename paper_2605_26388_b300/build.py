@@ -13,8 +13,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libdgsem.so")
-SOURCES = ["dg_api.cu", "dg_kernels.cu", "dg_noalloc.cu"]
-HEADERS = ["dg_device.cuh", "dg_internal.h"]
+SOURCES = ["dg_api.cu", "dg_kernels.cu", "dg_stage2d.cu", "dg_stage3d.cu", "dg_batched2d.cu",
+           "dg_batched3d.cu", "dg_noalloc.cu"]
+HEADERS = ["dg_device.cuh", "dg_internal.h", "dg_stage.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -28,17 +29,27 @@ def _stale() -> bool:
 
 
 def build_library(force: bool = False, verbose: bool = False) -> str:
-    """Compile with nvcc (CUDA 13, -O3 -lineinfo, sm_103a) into one shared library."""
+    """Compile every translation unit with nvcc (CUDA 13, -O3 -lineinfo, sm_103a) in
+    parallel, then link them into one shared library."""
     if not force and not _stale():
         return LIB
     os.makedirs(LIBDIR, exist_ok=True)
     nvcc = os.environ.get("NVCC", "nvcc")
-    cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
-           "-Xcompiler", "-fvisibility=hidden", "--expt-relaxed-constexpr",
-           "-o", LIB + ".tmp"] + [os.path.join(CSRC, f) for f in SOURCES]
+    objdir = os.path.join(LIBDIR, "obj")
+    os.makedirs(objdir, exist_ok=True)
+    flags = [*ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler",
+             "-fvisibility=hidden", "--expt-relaxed-constexpr"]
     if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-    subprocess.run(cmd, check=True)
+        flags.append("-Xptxas=-v")
+    procs, objs = [], []
+    for f in SOURCES:
+        obj = os.path.join(objdir, f.replace(".cu", ".o"))
+        objs.append(obj)
+        procs.append((f, subprocess.Popen([nvcc, *flags, "-c", os.path.join(CSRC, f), "-o", obj])))
+    failed = [f for f, p in procs if p.wait() != 0]
+    if failed:
+        raise subprocess.CalledProcessError(1, f"nvcc {failed}")
+    subprocess.run([nvcc, *ARCH, "-shared", "-o", LIB + ".tmp", *objs], check=True)
     os.replace(LIB + ".tmp", LIB)
     return LIB
 

@@ -4,6 +4,7 @@
 // stage buffers, rotated so that no launch writes a buffer it reads), the device error
 // word, a scratch word for the time-step reduction, a private capture stream and the CUDA
 // graph that replays three SSP-RK3 steps (nine fused stage launches).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -28,6 +29,14 @@ struct dg_ctx {
   std::string msg;
   cudaGraphExec_t gexec = nullptr;   // three RK steps starting from buf[0]
   double g_dt = 0.0;
+  // batched launch (several instances): work list and per-instance arguments on the device
+  bool batched = false;
+  dg::BatchConfig bcfg{1, 0, 0};
+  dg::InstArgs* d_insts = nullptr;
+  int2* d_items = nullptr;
+  size_t items_cap = 0;
+  int n_items = 0;
+  double* d_dv = nullptr;
 };
 
 namespace {
@@ -126,25 +135,9 @@ int n_p_of(const dg_mesh_desc& m) {
   return n;
 }
 
-// Fill the launch arguments of instance i.
-void stage_args(const dg_ctx* c, int i, dg::StageArgs& a) {
-  const dg_mesh_desc& m = c->inst[i];
-  std::memset(&a, 0, sizeof(a));
-  a.stride = c->n_nodes_total;
-  a.base = c->offs[i];
-  for (int l = 0; l < 3; ++l) {
-    a.nel[l] = (l < m.dim) ? m.nel[l] : 1;
-    a.s[l] = (l < m.dim) ? 2.0 / ((m.hi[l] - m.lo[l]) / m.nel[l]) : 0.0;
-  }
-  a.n_elem = (int)n_elem_of(m);
-  a.gamma = c->phys.gamma;
-  a.surface = c->phys.surface;
-  a.weak = (c->phys.volume == DG_VOL_WEAK) ? 1 : 0;
-  a.rho_floor = c->phys.rho_floor;
-  a.p_floor = c->phys.p_floor;
-  a.p_ref = c->phys.p_ref;
-  a.err = c->err;
-  const int N = m.N, n1 = N + 1;
+// The volume operator of degree N for this context's volume form, row-major (N+1)^2.
+void volume_operator(const dg_ctx* c, int N, double* Dv, double* lift) {
+  const int n1 = N + 1;
   double x[dg::kMaxN + 1], w[dg::kMaxN + 1], D[(dg::kMaxN + 1) * (dg::kMaxN + 1)];
   gll_table(N, x, w, D);
   for (int r = 0; r < n1; ++r)
@@ -153,53 +146,136 @@ void stage_args(const dg_ctx* c, int i, dg::StageArgs& a) {
       if (c->phys.volume == DG_VOL_WEAK) v = -(w[k] / w[r]) * D[k * n1 + r];
       else if (c->phys.volume == DG_VOL_EC) v = 2.0 * D[r * n1 + k];
       else v = D[r * n1 + k];
-      a.Dv[r * n1 + k] = v;
+      Dv[r * n1 + k] = v;
     }
-  a.lift = 1.0 / w[0];
+  if (lift) *lift = 1.0 / w[0];
 }
 
-// Precompute the per-launch scalars in both precisions and the uniform flags.
-void fill_scalars(dg::StageArgs& a) {
-  auto& d = a.pd;
-  for (int l = 0; l < 3; ++l) d.s[l] = a.s[l];
-  d.lift = a.lift;
-  d.gamma = a.gamma;
-  d.gm1 = a.gamma - 1.0;
-  d.igm1 = 1.0 / (a.gamma - 1.0);
-  d.p_ref = a.p_ref;
-  d.cbdt = a.cb * a.dt;
-  auto& f = a.pf;
-  for (int l = 0; l < 3; ++l) f.s[l] = (float)d.s[l];
-  f.lift = (float)d.lift;
-  f.gamma = (float)d.gamma;
-  f.gm1 = (float)a.gamma - 1.0f;
-  f.igm1 = 1.0f / f.gm1;
-  f.p_ref = (float)d.p_ref;
-  f.cbdt = (float)d.cbdt;
-  a.need_un = (a.mode == 1 && a.ca != 0.0) ? 1 : 0;
+// The kernels' view of instance i.
+void inst_args(const dg_ctx* c, int i, dg::InstArgs& I) {
+  const dg_mesh_desc& m = c->inst[i];
+  std::memset(&I, 0, sizeof(I));
+  I.base = c->offs[i];
+  for (int l = 0; l < 3; ++l) {
+    I.nel[l] = (l < m.dim) ? m.nel[l] : 1;
+    I.s[l] = (l < m.dim) ? 2.0 / ((m.hi[l] - m.lo[l]) / m.nel[l]) : 0.0;
+    I.sf[l] = (float)I.s[l];
+  }
+  I.n_elem = (int)n_elem_of(m);
+  I.N = m.N;
+  double D[(dg::kMaxN + 1) * (dg::kMaxN + 1)];
+  volume_operator(c, m.N, D, &I.lift);
+  I.liftf = (float)I.lift;
+}
+
+// Launch-wide fields (state pointers, stage coefficients, physics) and the host-precomputed
+// scalars in both precisions.
+void launch_args(const dg_ctx* c, dg::StageArgs& a, const double* U, const double* Un, double* out,
+                 int mode, double ca, double cb, double dt) {
+  std::memset(&a, 0, sizeof(a));
+  a.U = U;
+  a.Un = Un;
+  a.out = out;
+  a.err = c->err;
+  a.stride = c->n_nodes_total;
+  a.gamma = c->phys.gamma;
+  a.ca = ca;
+  a.cb = cb;
+  a.dt = dt;
+  a.mode = mode;
+  a.surface = c->phys.surface;
+  a.weak = (c->phys.volume == DG_VOL_WEAK) ? 1 : 0;
+  a.rho_floor = c->phys.rho_floor;
+  a.p_floor = c->phys.p_floor;
+  a.p_ref = c->phys.p_ref;
+  a.pd.gamma = a.gamma;
+  a.pd.gm1 = a.gamma - 1.0;
+  a.pd.igm1 = 1.0 / (a.gamma - 1.0);
+  a.pd.p_ref = a.p_ref;
+  a.pd.cbdt = cb * dt;
+  a.pf.gamma = (float)a.gamma;
+  a.pf.gm1 = (float)a.gamma - 1.0f;
+  a.pf.igm1 = 1.0f / a.pf.gm1;
+  a.pf.p_ref = (float)a.p_ref;
+  a.pf.cbdt = (float)a.pd.cbdt;
+  a.need_un = (mode == 1 && ca != 0.0) ? 1 : 0;
   a.floor_on = (a.rho_floor > 0.0 || a.p_floor > 0.0) ? 1 : 0;
 }
 
-// One fused launch per instance: mode 0 writes L(U), mode 1 the stage update.
+// One fused stage over all instances: mode 0 writes L(U), mode 1 the stage update.  One
+// launch per instance, or one batched launch for all of them.
 dg_status run_stage(dg_ctx* c, const double* U, const double* Un, double* out, int mode,
                     double ca, double cb, double dt, cudaStream_t s) {
+  const int ec = c->phys.volume == DG_VOL_EC, fp32 = c->phys.precision == DG_FP32_MIXED;
+  dg::StageArgs a;
+  launch_args(c, a, U, Un, out, mode, ca, cb, dt);
+  if (c->batched) {
+    a.insts = c->d_insts;
+    a.items = c->d_items;
+    a.n_items = c->n_items;
+    a.dv_table = c->d_dv;
+    cudaError_t e = dg::launch_euler_stage_batched(c->dim, ec, fp32, c->bcfg.group_scale,
+                                                   c->bcfg.ctas_per_sm, a, s);
+    return e == cudaSuccess ? DG_OK : cuda_fail(c, e, "batched stage launch");
+  }
   for (size_t i = 0; i < c->inst.size(); ++i) {
-    dg::StageArgs a;
-    stage_args(c, (int)i, a);
-    a.U = U;
-    a.Un = Un;
-    a.out = out;
-    a.mode = mode;
-    a.ca = ca;
-    a.cb = cb;
-    a.dt = dt;
-    fill_scalars(a);
-    cudaError_t e = dg::launch_euler_stage(c->inst[i].dim, c->inst[i].N,
-                                           c->phys.volume == DG_VOL_EC,
-                                           c->phys.precision == DG_FP32_MIXED, a, s);
+    inst_args(c, (int)i, a.inst);
+    volume_operator(c, c->inst[i].N, a.Dv, nullptr);
+    cudaError_t e = dg::launch_euler_stage(c->inst[i].dim, c->inst[i].N, ec, fp32, a, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "stage launch");
   }
   return DG_OK;
+}
+
+// (Re)build the batched work list for the current configuration: one item per element group
+// of every instance, ordered heaviest first (nodes per item, then instance) or in instance
+// order.  Device arrays are allocated once (sized for the smallest group) and reused.
+dg_status build_batch(dg_ctx* c) {
+  const int n = (int)c->inst.size();
+  std::vector<dg::InstArgs> insts(n);
+  for (int i = 0; i < n; ++i) inst_args(c, i, insts[i]);
+  struct Item { int inst, group; long long cost; };
+  std::vector<Item> items;
+  for (int i = 0; i < n; ++i) {
+    const int gsz = dg::batched_group(c->dim, c->inst[i].N, c->bcfg.group_scale);
+    const int ng = (insts[i].n_elem + gsz - 1) / gsz;
+    const long long cost = (long long)gsz * n_p_of(c->inst[i]) * (c->inst[i].N + 1);
+    for (int g = 0; g < ng; ++g) items.push_back({i, g, cost});
+  }
+  if (c->bcfg.order == 0)
+    std::stable_sort(items.begin(), items.end(),
+                     [](const Item& x, const Item& y) { return x.cost > y.cost; });
+  std::vector<int2> host(items.size());
+  for (size_t k = 0; k < items.size(); ++k) host[k] = make_int2(items[k].inst, items[k].group);
+  const size_t cap = items.size();
+  if (!c->d_insts) {
+    if (cudaMalloc(&c->d_insts, sizeof(dg::InstArgs) * n) != cudaSuccess) return fail(c, DG_ENOMEM, "batch");
+    const int nd = (dg::kMaxN + 1) * (dg::kMaxN + 1) * (dg::kMaxN + 1);
+    if (cudaMalloc(&c->d_dv, sizeof(double) * nd) != cudaSuccess) return fail(c, DG_ENOMEM, "batch");
+    std::vector<double> dv(nd, 0.0);
+    for (int N = 1; N <= dg::kMaxN; ++N) volume_operator(c, N, dv.data() + N * (dg::kMaxN + 1) * (dg::kMaxN + 1), nullptr);
+    cudaError_t e = cudaMemcpy(c->d_dv, dv.data(), sizeof(double) * nd, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(c, e, "batch operators");
+  }
+  if (cap > c->items_cap) {
+    if (c->d_items) cudaFree(c->d_items);
+    c->d_items = nullptr;
+    if (cudaMalloc(&c->d_items, sizeof(int2) * cap) != cudaSuccess) return fail(c, DG_ENOMEM, "batch items");
+    c->items_cap = cap;
+  }
+  cudaError_t e = cudaMemcpy(c->d_insts, insts.data(), sizeof(dg::InstArgs) * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_items, host.data(), sizeof(int2) * cap, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(c, e, "batch upload");
+  c->n_items = (int)cap;
+  e = dg::prepare_euler_stage_batched(c->dim, c->phys.volume == DG_VOL_EC,
+                                      c->phys.precision == DG_FP32_MIXED, c->bcfg.group_scale);
+  if (e != cudaSuccess) return cuda_fail(c, e, "batched kernel set-up");
+  return DG_OK;
+}
+
+void drop_graph(dg_ctx* c) {
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  c->gexec = nullptr;
 }
 
 const double kStageA[3] = {0.0, 0.75, 1.0 / 3.0};
@@ -278,6 +354,16 @@ dg_status dg_init_mesh(const dg_mesh_desc* inst, int n_inst, const dg_physics* p
     if (e != cudaSuccess) {
       dg_free(c);
       return DG_ECUDA;
+    }
+  }
+  bool batchable = true;
+  for (int i = 0; i < n_inst; ++i) batchable = batchable && inst[i].N <= dg::kMaxBatchedN;
+  if (n_inst > 1 && batchable) {
+    c->batched = true;
+    dg_status st = build_batch(c);
+    if (st != DG_OK) {
+      dg_free(c);
+      return st;
     }
   }
   *out = c;
@@ -380,6 +466,75 @@ dg_status dg_rk_step(dg_ctx* c, double dt, int n_steps) {
   return DG_OK;
 }
 
+dg_status dg_set_launch(dg_ctx* c, int mode, int group_scale, int ctas_per_sm, int order) {
+  if (!c) return DG_EINVAL;
+  if (mode != DG_LAUNCH_PER_INSTANCE && mode != DG_LAUNCH_BATCHED)
+    return fail(c, DG_EINVAL, "mode must be DG_LAUNCH_PER_INSTANCE or DG_LAUNCH_BATCHED");
+  if (group_scale != 1 && !(group_scale == 2 && c->dim == 2))
+    return fail(c, DG_EINVAL, "group_scale must be 1 (or 2 in 2D)");
+  if (ctas_per_sm < 0 || (order != 0 && order != 1))
+    return fail(c, DG_EINVAL, "ctas_per_sm must be >= 0 and order 0 or 1");
+  if (mode == DG_LAUNCH_BATCHED)
+    for (const dg_mesh_desc& m : c->inst)
+      if (m.N > dg::kMaxBatchedN) return fail(c, DG_EUNSUPPORTED, "batched launches cover N <= 5");
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "dg_set_launch sync");
+  drop_graph(c);
+  c->bcfg = dg::BatchConfig{group_scale, ctas_per_sm, order};
+  c->batched = (mode == DG_LAUNCH_BATCHED);
+  if (c->batched) return build_batch(c);
+  return DG_OK;
+}
+
+dg_status dg_autotune(dg_ctx* c, double dt, int n_reps, int* config_out, double* ms_out) {
+  if (!c) return DG_EINVAL;
+  if (!std::isfinite(dt) || n_reps < 1 || !config_out) return fail(c, DG_EINVAL, "bad autotune arguments");
+  const size_t bytes = sizeof(double) * (size_t)c->nv * c->n_nodes_total;
+  double* save = nullptr;
+  if (cudaMalloc(&save, bytes) != cudaSuccess) { cudaGetLastError(); return fail(c, DG_ENOMEM, "autotune copy"); }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaMemcpyAsync(save, c->buf[c->cur], bytes, cudaMemcpyDeviceToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  struct Cand { int mode, gs, cps, order; };
+  std::vector<Cand> cands;
+  cands.push_back({DG_LAUNCH_PER_INSTANCE, 1, 0, 0});
+  for (int gs = 1; gs <= (c->dim == 2 ? 2 : 1); ++gs)
+    for (int cps : {0, 1, 2})
+      for (int order = 0; order <= 1; ++order) cands.push_back({DG_LAUNCH_BATCHED, gs, cps, order});
+  double best = INFINITY;
+  Cand bestc = cands[0];
+  dg_status st = DG_OK;
+  for (size_t k = 0; k < cands.size() && e == cudaSuccess && st == DG_OK; ++k) {
+    const Cand& q = cands[k];
+    if ((st = dg_set_launch(c, q.mode, q.gs, q.cps, q.order)) != DG_OK) break;
+    if ((st = one_step(c, dt, c->stream)) != DG_OK) break;  // warm-up
+    if ((e = cudaEventRecord(e0, c->stream)) != cudaSuccess) break;
+    for (int r = 0; r < n_reps && st == DG_OK; ++r) st = one_step(c, dt, c->stream);
+    if (st != DG_OK) break;
+    if ((e = cudaEventRecord(e1, c->stream)) != cudaSuccess) break;
+    if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+    float ms = 0.f;
+    if ((e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) break;
+    if (ms / n_reps < best) { best = ms / n_reps; bestc = q; }
+  }
+  // restore the state and keep the fastest configuration
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->buf[c->cur], save, bytes, cudaMemcpyDeviceToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(save);
+  if (e != cudaSuccess) return cuda_fail(c, e, "dg_autotune");
+  if (st != DG_OK) return st;
+  if ((st = dg_set_launch(c, bestc.mode, bestc.gs, bestc.cps, bestc.order)) != DG_OK) return st;
+  config_out[0] = bestc.mode;
+  config_out[1] = bestc.gs;
+  config_out[2] = bestc.cps;
+  config_out[3] = bestc.order;
+  if (ms_out) *ms_out = best;
+  return DG_OK;
+}
+
 dg_status dg_max_dt(dg_ctx* c, double cfl, double* dt_out) {
   if (!c) return DG_EINVAL;
   if (!dt_out || !(cfl > 0.0)) return fail(c, DG_EINVAL, "bad cfl or output pointer");
@@ -445,6 +600,9 @@ void dg_free(dg_ctx* c) {
   if (c->err) cudaFree(c->err);
   if (c->lam) cudaFree(c->lam);
   if (c->cap) cudaStreamDestroy(c->cap);
+  if (c->d_insts) cudaFree(c->d_insts);
+  if (c->d_items) cudaFree(c->d_items);
+  if (c->d_dv) cudaFree(c->d_dv);
   delete c;
 }
 

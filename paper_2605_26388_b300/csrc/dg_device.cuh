@@ -103,8 +103,9 @@ template <int DIM, int N> struct Geo {
   static constexpr int NLINE = NP / N1;                            // lines per direction
   static constexpr int NPAIR = N * N1 / 2;                         // pairs a<b per line
   static constexpr int NV = DIM + 2;                               // conserved variables
-  static constexpr int EPB = (NP >= 96) ? 1 : (128 / NP);          // elements per block
-  static constexpr int THREADS = ((EPB * NP + 31) / 32) * 32;
+  // elements per group: enough that the per-node and per-face-node roles fill ~128 threads
+  static constexpr int W = (NP > 2 * DIM * NFN) ? NP : 2 * DIM * NFN;
+  static constexpr int EPB = (W >= 96) ? 1 : (128 / W);
   // stride of direction l in the node index (i fastest)
   static __host__ __device__ constexpr int stride(int l) { return l == 0 ? 1 : (l == 1 ? N1 : N1 * N1); }
   // node index of the m-th point on line q of direction l

@@ -7,19 +7,36 @@
 
 namespace dg {
 
-constexpr int kMaxN = 7;  // largest polynomial degree with compiled kernels (2D); 3D: 5
+constexpr int kMaxN = 7;         // largest polynomial degree with compiled kernels (2D); 3D: 5
+constexpr int kMaxBatchedN = 5;  // largest degree of the batched kernel
 
-// Arguments of one fused stage launch over one mesh instance (passed by value).
+// One mesh instance as the kernels see it.
+struct InstArgs {
+  long long base;      // node offset of this instance in each variable's slab
+  int nel[3];          // elements per direction (1 in unused directions)
+  int n_elem;
+  int N;
+  double s[3];         // 2/dx_l
+  float sf[3];
+  double lift;         // 1 / w_0 (= 1 / w_N) of the GLL rule
+  float liftf;
+};
+
+// Launch-wide scalars in one precision, precomputed on the host so that no thread converts
+// a double parameter to float (that conversion issues more slowly than an FP64 FMA on
+// sm_103a) or evaluates a double comparison of a uniform flag.
+template <class R>
+struct ScalarsT {
+  R gamma, gm1, igm1, p_ref, cbdt;
+};
+
+// Arguments of one fused stage launch (passed by value).
 struct StageArgs {
   const double* U;     // input state U^(k-1) (or the residual's input)
   const double* Un;    // U^n (stages 2 and 3), else unused
   double* out;         // U^(k) (mode 1) or L(U) (mode 0)
   unsigned* err;       // device error word (bit 0 non-finite, bit 1 non-positive)
   long long stride;    // per-variable stride of the SoA state (total nodes)
-  long long base;      // node offset of this instance
-  int nel[3];
-  int n_elem;
-  double s[3];         // 2/dx_l
   double gamma;
   double ca, cb, dt;   // U^(k) = ca Un + cb (U^(k-1) + dt L)
   int mode;            // 0: out = L(U); 1: RK stage update
@@ -27,18 +44,25 @@ struct StageArgs {
   int weak;            // 1: weak-form volume operator (surface lifts F* only)
   double rho_floor, p_floor;
   double p_ref;        // constant subtracted from the pressure in the momentum flux
-  double lift;         // 1 / w_0 (= 1 / w_N) of the GLL rule
-  // Host-precomputed copies of the scalars above in both precisions, so that no thread
-  // converts a double parameter to float (that conversion issues more slowly than an FP64
-  // FMA on sm_103a) or evaluates a double comparison of a uniform flag.
-  template <class R> struct ScalarsT {
-    R s[3], lift, gamma, gm1, igm1, p_ref, cbdt;
-  };
   ScalarsT<double> pd;
   ScalarsT<float> pf;
   int need_un;         // mode == 1 and ca != 0
   int floor_on;        // rho_floor > 0 or p_floor > 0
+  // single-instance launch
+  InstArgs inst;
   double Dv[(kMaxN + 1) * (kMaxN + 1)];  // volume operator, row-major (N+1)^2
+  // batched launch: work items (instance, element group), one volume operator per degree
+  const InstArgs* insts;
+  const int2* items;
+  int n_items;
+  const double* dv_table;  // [kMaxN + 1][(kMaxN + 1)^2]
+};
+
+// Batched-launch tuning choices (picked by the autotuner).
+struct BatchConfig {
+  int group_scale;     // elements per work item = group_scale x the kernel's base group
+  int ctas_per_sm;     // 0 = as many as fit
+  int order;           // 0 = heaviest items first, 1 = instance order
 };
 
 // Launch the fused Euler stage kernel for one instance.  Returns a CUDA error code.
@@ -58,6 +82,14 @@ cudaError_t launch_max_speed(int dim, const double* U, long long stride, long lo
 // Evaluate a device two-point flux for n AoS state pairs.
 cudaError_t launch_two_point(int dim, int fp32, int kind, int l, int n, double gamma, double p_ref,
                              const double* uL, const double* uR, double* F, cudaStream_t s);
+
+// Batched persistent launch over the work items in a.items (all instances of one dim).
+cudaError_t launch_euler_stage_batched(int dim, int ec, int fp32, int group_scale, int ctas_per_sm,
+                                       const StageArgs& a, cudaStream_t s);
+// Elements per work item of the batched kernel for degree N (dim, group_scale).
+int batched_group(int dim, int N, int group_scale);
+// Threads per CTA and dynamic shared memory of the batched kernel.
+cudaError_t prepare_euler_stage_batched(int dim, int ec, int fp32, int group_scale);
 
 // Whether (dim, N) has compiled kernels.
 bool have_kernels(int dim, int N);

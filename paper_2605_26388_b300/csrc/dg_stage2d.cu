@@ -1,0 +1,67 @@
+// dg_stage2d.cu -- single-instance launches of the fused stage kernel, 2D degrees.
+#include "dg_stage.cuh"
+
+namespace dg {
+
+template <int DIM, int N, bool EC, class R>
+struct GridSize {
+  static int ctas;
+};
+template <int DIM, int N, bool EC, class R>
+int GridSize<DIM, N, EC, R>::ctas = 0;
+
+template <int DIM, int N, bool EC, class R>
+static cudaError_t prepare_one() {
+  using K = EulerStage<DIM, N, EC, R>;
+  cudaError_t e = cudaFuncSetAttribute(k_euler_stage<DIM, N, EC, R>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)K::smem_bytes());
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_euler_stage<DIM, N, EC, R>, K::T,
+                                                    K::smem_bytes());
+  if (e != cudaSuccess) return e;
+  GridSize<DIM, N, EC, R>::ctas = sms * (per_sm > 0 ? per_sm : 1);
+  return cudaSuccess;
+}
+
+template <int DIM, int N, bool EC, class R>
+static cudaError_t launch_one(const StageArgs& a, cudaStream_t s) {
+  using K = EulerStage<DIM, N, EC, R>;
+  const int groups = (a.inst.n_elem + K::EPB - 1) / K::EPB;
+  if (groups == 0) return cudaSuccess;
+  if (GridSize<DIM, N, EC, R>::ctas == 0) {
+    cudaError_t e = prepare_one<DIM, N, EC, R>();
+    if (e != cudaSuccess) return e;
+  }
+  const int blocks = groups < GridSize<DIM, N, EC, R>::ctas ? groups : GridSize<DIM, N, EC, R>::ctas;
+  k_euler_stage<DIM, N, EC, R><<<blocks, K::T, K::smem_bytes(), s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int DIM, int N>
+static cudaError_t launch_dn(int ec, int fp32, const StageArgs* a, cudaStream_t s) {
+  if (!a) {
+    if (ec) return fp32 ? prepare_one<DIM, N, true, float>() : prepare_one<DIM, N, true, double>();
+    return fp32 ? prepare_one<DIM, N, false, float>() : prepare_one<DIM, N, false, double>();
+  }
+  if (ec) return fp32 ? launch_one<DIM, N, true, float>(*a, s) : launch_one<DIM, N, true, double>(*a, s);
+  return fp32 ? launch_one<DIM, N, false, float>(*a, s) : launch_one<DIM, N, false, double>(*a, s);
+}
+
+cudaError_t dispatch_stage_2d(int N, int ec, int fp32, const StageArgs* a, cudaStream_t s) {
+  switch (N) {
+    case 1: return launch_dn<2, 1>(ec, fp32, a, s);
+    case 2: return launch_dn<2, 2>(ec, fp32, a, s);
+    case 3: return launch_dn<2, 3>(ec, fp32, a, s);
+    case 4: return launch_dn<2, 4>(ec, fp32, a, s);
+    case 5: return launch_dn<2, 5>(ec, fp32, a, s);
+    case 6: return launch_dn<2, 6>(ec, fp32, a, s);
+    case 7: return launch_dn<2, 7>(ec, fp32, a, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace dg

@@ -23,6 +23,7 @@ DG_EULER = 0
 VOL_STRONG, VOL_WEAK, VOL_EC = 0, 1, 2
 SURF_RUSANOV, SURF_HLLC, SURF_HLL, SURF_EC = 0, 1, 2, 3
 FP64, FP32_MIXED = 0, 1
+LAUNCH_PER_INSTANCE, LAUNCH_BATCHED = 0, 1
 
 _STATUS = {0: "DG_OK", -1: "DG_EINVAL", -2: "DG_ENOMEM", -3: "DG_ECUDA", -4: "DG_ENONFINITE",
            -5: "DG_EPOSITIVITY", -6: "DG_EUNSUPPORTED", -7: "DG_ETOOLARGE"}
@@ -30,7 +31,8 @@ _STATUS = {0: "DG_OK", -1: "DG_EINVAL", -2: "DG_ENOMEM", -3: "DG_ECUDA", -4: "DG
 # Every entry point include/dgsem.h declares (checked by the CPU tests).
 EXPORTS = ["dg_init_mesh", "dg_state_size", "dg_instance_offset", "dg_set_state", "dg_get_state",
            "dg_rhs", "dg_rk_stage", "dg_rk_step", "dg_max_dt", "dg_check", "dg_gll",
-           "dg_two_point_flux", "dg_max_dt_noalloc", "dg_last_error", "dg_free"]
+           "dg_two_point_flux", "dg_max_dt_noalloc", "dg_set_launch", "dg_autotune",
+           "dg_last_error", "dg_free"]
 
 
 class DGError(RuntimeError):
@@ -75,6 +77,8 @@ def lib():
         L.dg_two_point_flux.argtypes = [vp, ip, ip, ip, vp, vp, vp]
         L.dg_max_dt_noalloc.argtypes = [C.POINTER(MeshDesc), ip, C.c_double, vp, C.c_double, vp, dp,
                                          C.POINTER(C.c_char_p)]
+        L.dg_set_launch.argtypes = [vp, ip, ip, ip, ip]
+        L.dg_autotune.argtypes = [vp, C.c_double, ip, C.POINTER(C.c_int), dp]
         L.dg_last_error.argtypes = [vp]
         L.dg_last_error.restype = C.c_char_p
         L.dg_free.argtypes = [vp]
@@ -209,6 +213,18 @@ class Solver:
 
     def rk_step(self, dt: float, n_steps: int = 1):
         self._call(lib().dg_rk_step(self._h, dt, n_steps), "dg_rk_step")
+
+    def set_launch(self, mode: int, group_scale: int = 1, ctas_per_sm: int = 0, order: int = 0):
+        """Per-instance launches or one batched persistent launch per stage (see dg_set_launch)."""
+        self._call(lib().dg_set_launch(self._h, mode, group_scale, ctas_per_sm, order), "dg_set_launch")
+
+    def autotune(self, dt: float, n_reps: int = 2):
+        """Time every launch configuration on this context, keep the fastest; returns
+        ((mode, group_scale, ctas_per_sm, order), ms_per_step)."""
+        cfg = (C.c_int * 4)()
+        ms = C.c_double()
+        self._call(lib().dg_autotune(self._h, dt, n_reps, cfg, C.byref(ms)), "dg_autotune")
+        return tuple(cfg), ms.value
 
     def max_dt(self, cfl: float) -> float:
         out = C.c_double()
