@@ -112,6 +112,8 @@ def lib():
         _lib.orc_rk3_stage.argtypes = [pp, C.c_int, dp, dp, C.c_double, dp]
         _lib.orc_rk3.argtypes = [pp, dp, C.c_double, C.c_int]
         _lib.orc_max_dt.argtypes = [pp, dp, C.c_double, dp]
+        _lib.orc_rhs_jvp.argtypes = [pp, dp, dp, C.c_double, dp, dp]
+        _lib.orc_rhs_vjp_brute.argtypes = [pp, dp, dp, dp, dp]
     return _lib
 
 
@@ -203,6 +205,33 @@ def rk3(P: Problem, U: np.ndarray, dt: float, n_steps: int) -> np.ndarray:
     c = P._c()
     _check(lib().orc_rk3(C.byref(c), _ptr(U), dt, n_steps), "rk3")
     return U
+
+
+def rhs_jvp(P: Problem, U: np.ndarray, V=None, gdot: float = 0.0):
+    """(L(U), dL) with dL = (dL/dU) V + (dL/dgamma) gdot, by forward-mode dual numbers
+    (strong or weak volume form, Rusanov surface flux).  Pinned by its value against rhs()
+    and its derivative against central differences of rhs()."""
+    U = np.ascontiguousarray(U, dtype=np.float64).reshape(P.shape)
+    L = np.zeros_like(U)
+    dL = np.zeros_like(U)
+    Vp = None
+    if V is not None:
+        V = np.ascontiguousarray(V, dtype=np.float64).reshape(P.shape)
+        Vp = _ptr(V)
+    c = P._c()
+    _check(lib().orc_rhs_jvp(C.byref(c), _ptr(U), Vp, gdot, _ptr(L), _ptr(dL)), "rhs_jvp")
+    return L, dL
+
+
+def rhs_vjp_brute(P: Problem, U: np.ndarray, lam: np.ndarray):
+    """((dL/dU)^T lam, lam . dL/dgamma) assembled from one JVP per unknown (tiny meshes)."""
+    U = np.ascontiguousarray(U, dtype=np.float64).reshape(P.shape)
+    lam = np.ascontiguousarray(lam, dtype=np.float64).reshape(P.shape)
+    Ub = np.zeros_like(U)
+    gb = np.zeros(1)
+    c = P._c()
+    _check(lib().orc_rhs_vjp_brute(C.byref(c), _ptr(U), _ptr(lam), _ptr(Ub), _ptr(gb)), "rhs_vjp_brute")
+    return Ub, float(gb[0])
 
 
 def max_dt(P: Problem, U: np.ndarray, cfl: float) -> float:

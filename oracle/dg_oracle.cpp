@@ -479,6 +479,118 @@ void positivity_floor(const OrcProblem& P, double* U) {
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// Forward-mode derivatives (for checking the adjoint).  A dual number carries a value and
+// one directional derivative; the residual below is the same strong/weak-form + Rusanov
+// residual as above, written once more over a generic scalar T so that evaluating it on
+// duals gives L(U) and the directional derivative dL = (dL/dU) V + (dL/dgamma) gdot exactly
+// (up to rounding).  Non-smooth points: |x| has derivative sign(x) with sign(0) = 0; max(a, b)
+// follows the larger value, the left argument on a tie.
+// ---------------------------------------------------------------------------------------
+struct Dual {
+  double v, d;
+  Dual(double a = 0.0, double b = 0.0) : v(a), d(b) {}
+};
+inline Dual operator+(Dual a, Dual b) { return Dual(a.v + b.v, a.d + b.d); }
+inline Dual operator-(Dual a, Dual b) { return Dual(a.v - b.v, a.d - b.d); }
+inline Dual operator-(Dual a) { return Dual(-a.v, -a.d); }
+inline Dual operator*(Dual a, Dual b) { return Dual(a.v * b.v, a.d * b.v + a.v * b.d); }
+inline Dual operator/(Dual a, Dual b) { return Dual(a.v / b.v, (a.d * b.v - a.v * b.d) / (b.v * b.v)); }
+inline Dual& operator+=(Dual& a, Dual b) { a = a + b; return a; }
+inline Dual& operator-=(Dual& a, Dual b) { a = a - b; return a; }
+inline Dual dsqrt(Dual a) { double r = std::sqrt(a.v); return Dual(r, a.d / (2.0 * r)); }
+inline Dual dabs(Dual a) { return Dual(std::fabs(a.v), (a.v > 0.0) ? a.d : (a.v < 0.0 ? -a.d : 0.0)); }
+inline Dual dmax(Dual a, Dual b) { return (a.v >= b.v) ? a : b; }
+
+template <class T>
+void flux_t(int dim, int l, const T* u, T gamma, T* F) {
+  T rho = u[0], kin = T(0.0), v[3];
+  for (int d = 0; d < dim; ++d) {
+    v[d] = u[1 + d] / rho;
+    kin += u[1 + d] * v[d];
+  }
+  T p = (gamma - T(1.0)) * (u[dim + 1] - T(0.5) * kin);
+  F[0] = u[1 + l];
+  for (int d = 0; d < dim; ++d) F[1 + d] = u[1 + l] * v[d] + (d == l ? p : T(0.0));
+  F[dim + 1] = (u[dim + 1] + p) * v[l];
+}
+
+template <class T>
+T signal_speed_t(int dim, int l, const T* u, T gamma) {  // |u_l| + a
+  T rho = u[0], kin = T(0.0);
+  for (int d = 0; d < dim; ++d) kin += u[1 + d] * u[1 + d] / rho;
+  T p = (gamma - T(1.0)) * (u[dim + 1] - T(0.5) * kin);
+  return dabs(u[1 + l] / rho) + dsqrt(gamma * p / rho);
+}
+
+template <class T>
+void rusanov_t(int dim, int l, const T* uL, const T* uR, T gamma, T* F) {
+  T lam = dmax(signal_speed_t(dim, l, uL, gamma), signal_speed_t(dim, l, uR, gamma));
+  T FL[8], FR[8];
+  flux_t(dim, l, uL, gamma, FL);
+  flux_t(dim, l, uR, gamma, FR);
+  for (int v = 0; v < dim + 2; ++v) F[v] = T(0.5) * (FL[v] + FR[v]) - T(0.5) * lam * (uR[v] - uL[v]);
+}
+
+// Eq. vol_weak (strong) or its weak form, plus Eq. surf_int with the Rusanov flux, on
+// element e -- the same loops as euler_element_residual.
+template <class T>
+void element_residual_t(const OrcProblem& P, const Mesh& M, const Ops& ops, const T* U, T gamma,
+                        int e, T* dU) {
+  const int dim = M.dim, n1 = M.n1, N = M.N, nv = dim + 2;
+  std::vector<T> R((size_t)M.n_nodes * nv, T(0.0));
+  auto load = [&](int el, int nd, T* u) {
+    for (int v = 0; v < nv; ++v) u[v] = U[((size_t)v * M.n_elem + el) * M.n_nodes + nd];
+  };
+  const bool weak = (P.volume == ORC_VOL_WEAK);
+  T um[8], F[8];
+  for (int nd = 0; nd < M.n_nodes; ++nd) {
+    int ijk[3];
+    M.node_coords(nd, ijk);
+    for (int l = 0; l < dim; ++l) {
+      const double s = 2.0 / M.dx[l];
+      const int il = ijk[l];
+      for (int m = 0; m < n1; ++m) {
+        int mk[3] = {ijk[0], ijk[1], ijk[2]};
+        mk[l] = m;
+        load(e, M.node(mk), um);
+        flux_t(dim, l, um, gamma, F);
+        const double c = weak ? -s * (ops.w[m] / ops.w[il]) * ops.D[m * n1 + il] : s * ops.D[il * n1 + m];
+        for (int v = 0; v < nv; ++v) R[nd * nv + v] -= T(c) * F[v];
+      }
+    }
+  }
+  for (int l = 0; l < dim; ++l) {
+    const double s = 2.0 / M.dx[l];
+    for (int nd = 0; nd < M.n_nodes; ++nd) {
+      int ijk[3];
+      M.node_coords(nd, ijk);
+      if (ijk[l] != N && ijk[l] != 0) continue;
+      T uown[8], unbr[8], Fs[8], Fown[8];
+      load(e, nd, uown);
+      flux_t(dim, l, uown, gamma, Fown);
+      if (ijk[l] == N) {
+        int nk[3] = {ijk[0], ijk[1], ijk[2]};
+        nk[l] = 0;
+        load(M.neighbour(e, l, +1), M.node(nk), unbr);
+        rusanov_t(dim, l, uown, unbr, gamma, Fs);
+        for (int v = 0; v < nv; ++v)
+          R[nd * nv + v] -= T(s / ops.w[N]) * (Fs[v] - (weak ? T(0.0) : Fown[v]));
+      }
+      if (ijk[l] == 0) {
+        int nk[3] = {ijk[0], ijk[1], ijk[2]};
+        nk[l] = N;
+        load(M.neighbour(e, l, -1), M.node(nk), unbr);
+        rusanov_t(dim, l, unbr, uown, gamma, Fs);
+        for (int v = 0; v < nv; ++v)
+          R[nd * nv + v] += T(s / ops.w[0]) * (Fs[v] - (weak ? T(0.0) : Fown[v]));
+      }
+    }
+  }
+  for (int nd = 0; nd < M.n_nodes; ++nd)
+    for (int v = 0; v < nv; ++v) dU[((size_t)v * M.n_elem + e) * M.n_nodes + nd] = R[nd * nv + v];
+}
+
 }  // namespace
 
 // =======================================================================================
@@ -580,6 +692,55 @@ int orc_rk3(const OrcProblem* P, double* U, double dt, int n_steps) {
     orc_rk3_stage(P, 2, U, U1.data(), dt, U2.data());
     orc_rk3_stage(P, 3, U, U2.data(), dt, U);
   }
+  return 0;
+}
+
+// Directional derivative of the residual (forward mode, dual numbers): for the strong or
+// weak volume form with the Rusanov surface flux,
+//   L  = L(U; gamma)      and      dL = (dL/dU) V + (dL/dgamma) gdot.
+int orc_rhs_jvp(const OrcProblem* P, const double* U, const double* V, double gdot, double* L,
+                double* dL) {
+  int rc = check_problem(*P);
+  if (rc) return rc;
+  if ((P->volume != ORC_VOL_STRONG && P->volume != ORC_VOL_WEAK) || P->surface != ORC_SURF_RUSANOV)
+    return -6;
+  Mesh M(*P);
+  Ops ops(P->N);
+  const size_t n = (size_t)n_vars(*P) * M.n_elem * M.n_nodes;
+  std::vector<Dual> Ud(n), Ld(n);
+  for (size_t q = 0; q < n; ++q) Ud[q] = Dual(U[q], V ? V[q] : 0.0);
+  const Dual g(P->gamma, gdot);
+#pragma omp parallel for schedule(static)
+  for (int e = 0; e < M.n_elem; ++e) element_residual_t<Dual>(*P, M, ops, Ud.data(), g, e, Ld.data());
+  for (size_t q = 0; q < n; ++q) {
+    if (L) L[q] = Ld[q].v;
+    dL[q] = Ld[q].d;
+  }
+  return 0;
+}
+
+// Adjoint by brute force: (dL/dU)^T lam and lam . dL/dgamma, assembled from one
+// directional derivative per unknown (tiny meshes only).
+int orc_rhs_vjp_brute(const OrcProblem* P, const double* U, const double* lam, double* Ubar,
+                      double* gbar) {
+  int rc = check_problem(*P);
+  if (rc) return rc;
+  Mesh M(*P);
+  const size_t n = (size_t)n_vars(*P) * M.n_elem * M.n_nodes;
+  if (n > 20000) return -1;
+  std::vector<double> V(n, 0.0), dL(n);
+  for (size_t j = 0; j < n; ++j) {
+    V[j] = 1.0;
+    if ((rc = orc_rhs_jvp(P, U, V.data(), 0.0, nullptr, dL.data()))) return rc;
+    V[j] = 0.0;
+    double acc = 0.0;
+    for (size_t i = 0; i < n; ++i) acc += lam[i] * dL[i];
+    Ubar[j] = acc;
+  }
+  if ((rc = orc_rhs_jvp(P, U, nullptr, 1.0, nullptr, dL.data()))) return rc;
+  double acc = 0.0;
+  for (size_t i = 0; i < n; ++i) acc += lam[i] * dL[i];
+  *gbar = acc;
   return 0;
 }
 
