@@ -131,6 +131,24 @@ DG_API dg_status dg_rk_stage(dg_ctx* ctx, int stage, const double* Un, const dou
  * collect device-side errors. */
 DG_API dg_status dg_rk_step(dg_ctx* ctx, double dt, int n_steps);
 
+/* Adjoint of the residual (SURVEY differentiable form; the paper has no adjoint -- it is the
+ * exact transpose of the semi-discrete operator of Eq. vol_weak + Eq. surf_int with the
+ * Rusanov flux, strong or weak volume form; other choices return DG_EUNSUPPORTED):
+ *   Ubar += (dL/dU)^T lam            (device arrays of dg_state_size() doubles)
+ *   *gammabar += lam . dL/dgamma     (host double)
+ * Non-smooth points follow the forward evaluation: the larger Rusanov signal speed (the left
+ * one on a tie) carries the derivative, and d|u|/du = sign(u) with sign(0) = 0.  Ubar must not
+ * alias U or lam.  Allocates the adjoint workspace on first use; synchronizes the stream. */
+DG_API dg_status dg_rhs_vjp(dg_ctx* ctx, const double* U, const double* lam, double* Ubar,
+                            double* gammabar);
+
+/* Adjoint of one SSP-RK3 step from Un with step dt (App. B, Shu-Osher form, stages
+ * recomputed from Un): on entry lam = dJ/dU^{n+1}, on exit lam = dJ/dU^n; *gammabar (host)
+ * += dJ/dgamma through this step.  The positivity floor, if enabled, is not differentiated.
+ * lam must not alias Un.  Synchronizes the stream. */
+DG_API dg_status dg_rk_step_vjp(dg_ctx* ctx, const double* Un, double dt, double* lam,
+                                double* gammabar);
+
 /* Launch modes for contexts with several instances. */
 enum { DG_LAUNCH_PER_INSTANCE = 0, DG_LAUNCH_BATCHED = 1 };
 

@@ -37,6 +37,11 @@ struct dg_ctx {
   size_t items_cap = 0;
   int n_items = 0;
   double* d_dv = nullptr;
+  // adjoint workspace (allocated on the first adjoint call): recomputed stage states W1, W2,
+  // co-state temporaries T1..T3, per-CTA gamma partials and their device accumulator
+  double* adj[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  double* gpart = nullptr;
+  double* gacc = nullptr;
 };
 
 namespace {
@@ -273,6 +278,63 @@ dg_status build_batch(dg_ctx* c) {
   return DG_OK;
 }
 
+// ---- adjoint ----
+dg_status ensure_adjoint(dg_ctx* c) {
+  if (c->phys.volume == DG_VOL_EC || c->phys.surface != DG_SURF_RUSANOV)
+    return fail(c, DG_EUNSUPPORTED, "the adjoint covers the strong/weak volume form with the Rusanov flux");
+  if (c->gacc) return DG_OK;
+  const size_t bytes = sizeof(double) * (size_t)c->nv * c->n_nodes_total;
+  int maxb = 1;
+  for (const dg_mesh_desc& m : c->inst) maxb = std::max(maxb, dg::vjp_blocks(m.dim, m.N, n_elem_of(m)));
+  for (int k = 0; k < 5; ++k)
+    if (cudaMalloc(&c->adj[k], bytes) != cudaSuccess) { cudaGetLastError(); return fail(c, DG_ENOMEM, "adjoint workspace"); }
+  if (cudaMalloc(&c->gpart, sizeof(double) * maxb) != cudaSuccess ||
+      cudaMalloc(&c->gacc, sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, DG_ENOMEM, "adjoint workspace");
+  }
+  return DG_OK;
+}
+
+// One adjoint launch per instance (see dg::VjpArgs for the modes).
+dg_status run_vjp(dg_ctx* c, const double* U, const double* lam, double* out, int mode, double bcoef,
+                  double dt, const double* accin, double* accupd, int acc_init, double acoef, double gw) {
+  for (size_t i = 0; i < c->inst.size(); ++i) {
+    dg::VjpArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.U = U;
+    a.lam = lam;
+    a.out = out;
+    a.accin = accin;
+    a.accupd = accupd;
+    a.acc_init = acc_init;
+    a.gpart = c->gpart;
+    a.stride = c->n_nodes_total;
+    inst_args(c, (int)i, a.inst);
+    volume_operator(c, c->inst[i].N, a.Dv, nullptr);
+    a.gamma = c->phys.gamma;
+    a.dt = dt;
+    a.bcoef = bcoef;
+    a.acoef = acoef;
+    a.gw = gw;
+    a.mode = mode;
+    a.weak = (c->phys.volume == DG_VOL_WEAK) ? 1 : 0;
+    cudaError_t e = dg::launch_rhs_vjp(c->dim, c->inst[i].N, c->phys.precision == DG_FP32_MIXED, a,
+                                       c->gacc, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "adjoint launch");
+  }
+  return DG_OK;
+}
+
+dg_status read_gacc(dg_ctx* c, double* gammabar) {
+  double g = 0.0;
+  cudaError_t e = cudaMemcpyAsync(&g, c->gacc, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "adjoint gamma read");
+  if (gammabar) *gammabar += g;
+  return DG_OK;
+}
+
 void drop_graph(dg_ctx* c) {
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   c->gexec = nullptr;
@@ -466,6 +528,39 @@ dg_status dg_rk_step(dg_ctx* c, double dt, int n_steps) {
   return DG_OK;
 }
 
+dg_status dg_rhs_vjp(dg_ctx* c, const double* U, const double* lam, double* Ubar, double* gammabar) {
+  if (!c) return DG_EINVAL;
+  if (!U || !lam || !Ubar) return fail(c, DG_EINVAL, "null pointer");
+  if (Ubar == U || Ubar == lam) return fail(c, DG_EINVAL, "Ubar must not alias U or lam");
+  dg_status st = ensure_adjoint(c);
+  if (st) return st;
+  cudaError_t e = cudaMemsetAsync(c->gacc, 0, sizeof(double), c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "dg_rhs_vjp");
+  if ((st = run_vjp(c, U, lam, Ubar, 0, 1.0, 0.0, nullptr, nullptr, 0, 0.0, 1.0))) return st;
+  return read_gacc(c, gammabar);
+}
+
+dg_status dg_rk_step_vjp(dg_ctx* c, const double* Un, double dt, double* lam, double* gammabar) {
+  if (!c) return DG_EINVAL;
+  if (!Un || !lam) return fail(c, DG_EINVAL, "null pointer");
+  if (Un == lam) return fail(c, DG_EINVAL, "lam must not alias Un");
+  if (!std::isfinite(dt)) return fail(c, DG_EINVAL, "dt must be finite");
+  dg_status st = ensure_adjoint(c);
+  if (st) return st;
+  double *W1 = c->adj[0], *W2 = c->adj[1], *T1 = c->adj[2], *T2 = c->adj[3], *T3 = c->adj[4];
+  // recompute the stage states of this step
+  if ((st = run_stage(c, Un, Un, W1, 1, kStageA[0], kStageB[0], dt, c->stream))) return st;
+  if ((st = run_stage(c, W1, Un, W2, 1, kStageA[1], kStageB[1], dt, c->stream))) return st;
+  cudaError_t e = cudaMemsetAsync(c->gacc, 0, sizeof(double), c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "dg_rk_step_vjp");
+  // reverse Shu-Osher: U3 = 1/3 Un + 2/3 (U2 + dt L(U2)), U2 = 3/4 Un + 1/4 (U1 + dt L(U1)),
+  // U1 = Un + dt L(Un)
+  if ((st = run_vjp(c, W2, lam, T1, 1, kStageB[2], dt, nullptr, T2, 1, kStageA[2], kStageB[2] * dt))) return st;
+  if ((st = run_vjp(c, W1, T1, T3, 1, kStageB[1], dt, nullptr, T2, 0, kStageA[1], kStageB[1] * dt))) return st;
+  if ((st = run_vjp(c, Un, T3, lam, 1, kStageB[0], dt, T2, nullptr, 0, 0.0, kStageB[0] * dt))) return st;
+  return read_gacc(c, gammabar);
+}
+
 dg_status dg_set_launch(dg_ctx* c, int mode, int group_scale, int ctas_per_sm, int order) {
   if (!c) return DG_EINVAL;
   if (mode != DG_LAUNCH_PER_INSTANCE && mode != DG_LAUNCH_BATCHED)
@@ -603,6 +698,10 @@ void dg_free(dg_ctx* c) {
   if (c->d_insts) cudaFree(c->d_insts);
   if (c->d_items) cudaFree(c->d_items);
   if (c->d_dv) cudaFree(c->d_dv);
+  for (int k = 0; k < 5; ++k)
+    if (c->adj[k]) cudaFree(c->adj[k]);
+  if (c->gpart) cudaFree(c->gpart);
+  if (c->gacc) cudaFree(c->gacc);
   delete c;
 }
 

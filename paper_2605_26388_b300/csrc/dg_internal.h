@@ -58,6 +58,31 @@ struct StageArgs {
   const double* dv_table;  // [kMaxN + 1][(kMaxN + 1)^2]
 };
 
+// Arguments of the adjoint (vector-Jacobian product) launch over one instance.
+//   mode 0:  out += w                                   (w = (dL/dU)^T lam)
+//   mode 1:  out  = bcoef (lam + dt w) [+ accin];  accupd (=|+=) acoef lam
+// gpart[cta] receives gw x that CTA's share of lam . dL/dgamma.
+struct VjpArgs {
+  const double* U;
+  const double* lam;
+  double* out;
+  const double* accin;
+  double* accupd;
+  int acc_init;
+  double* gpart;
+  long long stride;
+  InstArgs inst;
+  double Dv[(kMaxN + 1) * (kMaxN + 1)];
+  double gamma, dt, bcoef, acoef, gw;
+  int mode, weak;
+};
+
+// Launch the adjoint of the residual for one instance, then add the weighted gamma
+// contribution (a deterministic sum of the per-CTA partials) to *gacc (device).
+cudaError_t launch_rhs_vjp(int dim, int N, int fp32, const VjpArgs& a, double* gacc, cudaStream_t s);
+// CTAs the adjoint launch uses for an instance (size of the gpart scratch).
+int vjp_blocks(int dim, int N, long long n_elem);
+
 // Batched-launch tuning choices (picked by the autotuner).
 struct BatchConfig {
   int group_scale;     // elements per work item = group_scale x the kernel's base group

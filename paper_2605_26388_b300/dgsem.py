@@ -32,6 +32,7 @@ _STATUS = {0: "DG_OK", -1: "DG_EINVAL", -2: "DG_ENOMEM", -3: "DG_ECUDA", -4: "DG
 EXPORTS = ["dg_init_mesh", "dg_state_size", "dg_instance_offset", "dg_set_state", "dg_get_state",
            "dg_rhs", "dg_rk_stage", "dg_rk_step", "dg_max_dt", "dg_check", "dg_gll",
            "dg_two_point_flux", "dg_max_dt_noalloc", "dg_set_launch", "dg_autotune",
+           "dg_rhs_vjp", "dg_rk_step_vjp",
            "dg_last_error", "dg_free"]
 
 
@@ -78,6 +79,8 @@ def lib():
         L.dg_max_dt_noalloc.argtypes = [C.POINTER(MeshDesc), ip, C.c_double, vp, C.c_double, vp, dp,
                                          C.POINTER(C.c_char_p)]
         L.dg_set_launch.argtypes = [vp, ip, ip, ip, ip]
+        L.dg_rhs_vjp.argtypes = [vp, vp, vp, vp, dp]
+        L.dg_rk_step_vjp.argtypes = [vp, vp, C.c_double, vp, dp]
         L.dg_autotune.argtypes = [vp, C.c_double, ip, C.POINTER(C.c_int), dp]
         L.dg_last_error.argtypes = [vp]
         L.dg_last_error.restype = C.c_char_p
@@ -139,6 +142,7 @@ class Solver:
         if isinstance(meshes, Mesh):
             meshes = [meshes]
         self.meshes = list(meshes)
+        self.gamma = gamma
         arr = (MeshDesc * len(self.meshes))(*[m.c() for m in self.meshes])
         phys = Physics(DG_EULER, volume, surface, precision, gamma, rho_floor, p_floor, p_ref)
         if stream is None:
@@ -213,6 +217,23 @@ class Solver:
 
     def rk_step(self, dt: float, n_steps: int = 1):
         self._call(lib().dg_rk_step(self._h, dt, n_steps), "dg_rk_step")
+
+    def rhs_vjp(self, U, lam, Ubar=None):
+        """(Ubar + (dL/dU)^T lam, lam . dL/dgamma) -- see dg_rhs_vjp."""
+        import torch
+        if Ubar is None:
+            Ubar = torch.zeros_like(U)
+        g = C.c_double(0.0)
+        self._call(lib().dg_rhs_vjp(self._h, self._dev(U, "U"), self._dev(lam, "lam"), self._dev(Ubar, "Ubar"),
+                                    C.byref(g)), "dg_rhs_vjp")
+        return Ubar, g.value
+
+    def rk_step_vjp(self, Un, dt: float, lam):
+        """In place: lam = dJ/dU^{n+1} -> dJ/dU^n; returns dJ/dgamma through this step."""
+        g = C.c_double(0.0)
+        self._call(lib().dg_rk_step_vjp(self._h, self._dev(Un, "Un"), dt, self._dev(lam, "lam"), C.byref(g)),
+                   "dg_rk_step_vjp")
+        return g.value
 
     def set_launch(self, mode: int, group_scale: int = 1, ctas_per_sm: int = 0, order: int = 0):
         """Per-instance launches or one batched persistent launch per stage (see dg_set_launch)."""
