@@ -41,9 +41,10 @@ BYTES_PER_DOF_UPDATE = (16 + 24 + 24) / 3.0  # stage 1 reads U^n, writes U^1; st
 WORKLOAD = "tgv3d_euler_N4_64cube_ec_hllc_ssprk3"
 P_REF = 1.0 / (GAMMA * MACH ** 2)  # background pressure; the momentum flux carries p - P_REF
 
-# DRAM bytes per stage launch from the committed ncu capture of the current kernel
-# (profiles/); None when the kernel changed after the capture.
-TRAFFIC_PER_LAUNCH = {"fp32_mixed": None, "fp64": None}
+# DRAM bytes per stage launch (mean of stages 1-3) of the current kernel, from the ncu
+# capture summarised in profiles/euler_stage_3d_n4_ec_hllc_tgv.md (32^3 case scaled by the
+# element count to 64^3); None where no capture of the current kernel exists.
+TRAFFIC_PER_LAUNCH = {"fp32_mixed": 3.37e9, "fp64": None}
 
 
 def measured_peaks():
