@@ -2,7 +2,8 @@
 
 A plain, slow FP64 CPU implementation of the DGSEM residual, numerical fluxes, SSP-RK3
 stage and time-step bound of the paper's method (arXiv 2605.26388, Sec. 2, Sec. 3.1.1,
-App. A, App. B), written in C++ (``dg_oracle.cpp``) and loaded here with ctypes.  It
+App. A, App. B), and of the reacting Navier-Stokes residual (BR1 viscous terms, Sec. 3.1.2;
+Arrhenius source, Sec. 3.1.3 and App. C), written in C++ (``dg_oracle.cpp``) and loaded here with ctypes.  It
 shares no code with the CUDA library.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
 CPU-baseline leg of ``bench.py`` may import it.
 
@@ -37,6 +38,33 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+class _Mech(C.Structure):
+    _fields_ = [
+        ("n_species", C.c_int), ("n_reactions", C.c_int),
+        ("W", C.c_double * 8), ("R", C.c_double * 8), ("cv", C.c_double * 8), ("h0", C.c_double * 8),
+        ("lnA", C.c_double * 32), ("b", C.c_double * 32), ("Ta", C.c_double * 32),
+        ("kc", (C.c_double * 5) * 32), ("nu_f", (C.c_int * 8) * 32), ("nu_b", (C.c_int * 8) * 32),
+    ]
+
+
+def mechanism(m: dict) -> _Mech:
+    """Pack a mechanism dictionary (species data W, R, cv, h0; per-reaction lnA, b, Ta, kc,
+    nu_f, nu_b) into the oracle's own structure."""
+    c = _Mech()
+    ns, nr = int(m["n_species"]), int(m["n_reactions"])
+    c.n_species, c.n_reactions = ns, nr
+    for s in range(ns):
+        c.W[s], c.R[s], c.cv[s], c.h0[s] = m["W"][s], m["R"][s], m["cv"][s], m["h0"][s]
+    for r in range(nr):
+        c.lnA[r], c.b[r], c.Ta[r] = m["lnA"][r], m["b"][r], m["Ta"][r]
+        for k in range(5):
+            c.kc[r][k] = m["kc"][r][k]
+        for s in range(ns):
+            c.nu_f[r][s] = int(m["nu_f"][r][s])
+            c.nu_b[r][s] = int(m["nu_b"][r][s])
+    return c
+
+
 class _Problem(C.Structure):
     _fields_ = [
         ("dim", C.c_int), ("N", C.c_int), ("nel", C.c_int * 3),
@@ -44,6 +72,7 @@ class _Problem(C.Structure):
         ("equations", C.c_int), ("volume", C.c_int), ("surface", C.c_int),
         ("gamma", C.c_double), ("mu", C.c_double), ("prandtl", C.c_double),
         ("rho_floor", C.c_double), ("p_floor", C.c_double),
+        ("mech", C.POINTER(_Mech)), ("parts", C.c_int),
     ]
 
 
@@ -63,9 +92,13 @@ class Problem:
     prandtl: float = 0.72
     rho_floor: float = 0.0
     p_floor: float = 0.0
+    mech: dict = None   # NS_REACTING: mechanism dictionary (species and reactions)
+    parts: int = 0      # NS_REACTING: 1 inviscid, 2 viscous, 4 source; 0 = all
 
     @property
     def nvars(self) -> int:
+        if self.equations == NS_REACTING:
+            return int(self.mech["n_species"]) + self.dim + 1
         return self.dim + 2
 
     @property
@@ -87,9 +120,14 @@ class Problem:
         nel = list(self.nel) + [1] * (3 - len(self.nel))
         lo = list(self.lo) + [0.0] * (3 - len(self.lo))
         hi = list(self.hi) + [1.0] * (3 - len(self.hi))
-        return _Problem(self.dim, self.N, (C.c_int * 3)(*nel), (C.c_double * 3)(*lo),
-                        (C.c_double * 3)(*hi), self.equations, self.volume, self.surface,
-                        self.gamma, self.mu, self.prandtl, self.rho_floor, self.p_floor)
+        p = _Problem(self.dim, self.N, (C.c_int * 3)(*nel), (C.c_double * 3)(*lo),
+                     (C.c_double * 3)(*hi), self.equations, self.volume, self.surface,
+                     self.gamma, self.mu, self.prandtl, self.rho_floor, self.p_floor)
+        p.parts = self.parts
+        if self.mech is not None:
+            p._mech_keep = mechanism(self.mech)  # kept alive with the structure
+            p.mech = C.pointer(p._mech_keep)
+        return p
 
 
 _lib = None
@@ -114,6 +152,9 @@ def lib():
         _lib.orc_max_dt.argtypes = [pp, dp, C.c_double, dp]
         _lib.orc_rhs_jvp.argtypes = [pp, dp, dp, C.c_double, dp, dp]
         _lib.orc_rhs_vjp_brute.argtypes = [pp, dp, dp, dp, dp]
+        _lib.orc_arrhenius.argtypes = [C.POINTER(_Mech), C.c_int, C.c_double, dp, dp]
+        _lib.orc_chem_source.argtypes = [pp, dp, dp]
+        _lib.orc_mixture.argtypes = [pp, dp, dp, dp]
     return _lib
 
 
@@ -241,3 +282,35 @@ def max_dt(P: Problem, U: np.ndarray, cfl: float) -> float:
     c = P._c()
     _check(lib().orc_max_dt(C.byref(c), _ptr(U), cfl, _ptr(out)), "max_dt")
     return float(out[0])
+
+
+def arrhenius(mech: dict, r: int, T: float):
+    """Forward rate k_f = exp(lnA + b ln T - Ta/T) and equilibrium constant
+    K_c = exp(a0/Z + a1 + a2 ln Z + a3 Z + a4 Z^2), Z = 1e4/T, of reaction r (Sec. 3.1.3,
+    Eq. src_reaction_rate; the five-term K_c form is a reading). Pinned by a long-double
+    evaluation and the hand-worked golden value in tests/golden/."""
+    kf, Kc = C.c_double(), C.c_double()
+    m = mechanism(mech)
+    _check(lib().orc_arrhenius(C.byref(m), r, T, C.byref(kf), C.byref(Kc)), "arrhenius")
+    return kf.value, Kc.value
+
+
+def chem_source(P: Problem, u) -> np.ndarray:
+    """Chemical source of one reacting node state (Sec. 3.1.3, Eq. src_omega). Pinned by
+    mass and atom conservation, zero momentum/energy source, a zero net rate at a
+    composition built to satisfy K_c, and a hand-worked single-reaction value."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    S = np.zeros(P.nvars)
+    c = P._c()
+    _check(lib().orc_chem_source(C.byref(c), _ptr(u), _ptr(S)), "chem_source")
+    return S
+
+
+def mixture(P: Problem, u):
+    """Temperature and pressure of one reacting node state (calorically perfect species,
+    Sec. 2 closure). Pinned by inverting the state constructor of the reacting workload."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    T, p = C.c_double(), C.c_double()
+    c = P._c()
+    _check(lib().orc_mixture(C.byref(c), _ptr(u), C.byref(T), C.byref(p)), "mixture")
+    return T.value, p.value

@@ -1,9 +1,9 @@
 // dg_oracle.cpp -- ORACLE: test infrastructure, not part of the product path.
 //
 // A plain, slow, FP64 CPU implementation of what the DGSEM hot path computes: the
-// semi-discrete residual dU/dt = L(U) of the compressible Euler equations on periodic
-// Cartesian meshes (2D and 3D), its numerical fluxes, the SSP-RK3 stage update and the
-// explicit time-step bound.  It shares no source, header, table or helper with the CUDA
+// semi-discrete residual dU/dt = L(U) of the compressible Euler equations and of the
+// single-temperature reacting Navier-Stokes equations on periodic Cartesian meshes (2D and
+// 3D), its numerical fluxes, the SSP-RK3 stage update and the explicit time-step bounds.  It shares no source, header, table or helper with the CUDA
 // path, and the CUDA path never loads it.  Only the test-suite, the smoke check and the
 // benchmark's CPU-baseline leg may load it.
 //
@@ -13,6 +13,9 @@
 //                    flux-differencing volume term), surface fluxes (LF / HLL), Eq. surf_int
 //                    (surface lifting and Jacobian rescale)
 //   App. A           Eq. split_form_3D and the Ranocha entropy-conservative two-point flux
+//   Sec. 3.1.2       BR1 gradients (Eq. br1_avg), viscous stress (Eq. tau), central viscous
+//                    interface flux (Eq. br1_flux), diffusive time-step bound Delta t_D
+//   Sec. 3.1.3       Arrhenius source (Eqs. src_reaction_rate, src_omega)
 //   App. B           SSP-RK in Shu-Osher form; convective time-step bound Delta t_C
 // Readings of passages the paper leaves open are marked READING below.
 //
@@ -40,17 +43,28 @@ enum { ORC_SURF_RUSANOV = 0, ORC_SURF_HLLC = 1, ORC_SURF_HLL = 2, ORC_SURF_EC = 
 
 extern "C" {
 
+// Reacting mixture (the oracle's own copy of the species and reaction data).
+struct OrcMech {
+  int n_species, n_reactions;
+  double W[8], R[8], cv[8], h0[8];        // kg/mol, J/(kg K), J/(kg K), J/kg
+  double lnA[32], b[32], Ta[32];          // k_f = exp(lnA + b ln T - Ta/T), cm-mol-s
+  double kc[32][5];                       // ln K_c = a0/Z + a1 + a2 ln Z + a3 Z + a4 Z^2, Z = 1e4/T
+  int nu_f[32][8], nu_b[32][8];           // stoichiometric coefficients nu', nu''
+};
+
 struct OrcProblem {
   int dim;             // 2 or 3
   int N;               // polynomial degree; N+1 GLL nodes per direction
   int nel[3];          // elements per direction (nel[2] = 1 in 2D)
   double lo[3], hi[3]; // periodic box
-  int equations;       // ORC_EULER (others are added with the viscous and reacting paths)
+  int equations;       // ORC_EULER or ORC_NS_REACTING
   int volume;          // ORC_VOL_*
   int surface;         // ORC_SURF_*
   double gamma;        // ratio of specific heats
   double mu, prandtl;  // viscous parameters (unused for Euler)
   double rho_floor, p_floor;  // <= 0 disables the positivity floor
+  const OrcMech* mech;        // ORC_NS_REACTING: species and reactions
+  int parts;                  // ORC_NS_REACTING: 1 inviscid, 2 viscous, 4 source (0 = all)
 };
 
 }  // extern "C"
@@ -439,20 +453,262 @@ void euler_element_residual(const OrcProblem& P, const Mesh& M, const Ops& ops,
       dU[((size_t)v * M.n_elem + e) * M.n_nodes + nd] = R[nd * nv + v];
 }
 
-int n_vars(const OrcProblem& P) { return P.dim + 2; }
+int n_vars(const OrcProblem& P) {
+  return (P.equations == ORC_NS_REACTING) ? P.mech->n_species + P.dim + 1 : P.dim + 2;
+}
 
 int check_problem(const OrcProblem& P) {
   if (P.dim != 2 && P.dim != 3) return -1;
   if (P.N < 1 || P.N > 15) return -1;
   for (int l = 0; l < P.dim; ++l)
     if (P.nel[l] < 1 || !(P.hi[l] > P.lo[l])) return -1;
+  if (P.equations == ORC_NS_REACTING) {
+    if (!P.mech || P.mech->n_species < 1 || P.mech->n_species > 8 || P.mech->n_reactions < 0 ||
+        P.mech->n_reactions > 32)
+      return -1;
+    if (P.volume != ORC_VOL_STRONG || P.surface != ORC_SURF_RUSANOV) return -6;
+    if (P.rho_floor > 0.0 || P.p_floor > 0.0) return -6;
+    if (P.mu < 0.0 || !(P.prandtl > 0.0)) return -1;
+    return 0;
+  }
   if (P.equations != ORC_EULER) return -6;
   return 0;
+}
+
+// ---------------------------------------------------------------------------------------
+// Reacting Navier-Stokes (Sec. 2 "Thermochemical non-equilibrium", single temperature):
+// U = (rho_1..rho_ns, rho u, rho v, rho w, E).  READINGS: calorically perfect species
+// (Sec. 2 closure), E = sum rho_s (cv_s T + h0_s) + rho |u|^2 / 2, p = sum rho_s R_s T;
+// frozen sound speed a^2 = (1 + sum rho_s R_s / sum rho_s cv_s) p / rho; no species
+// diffusion; constant viscosity mu; conductivity k = mu c_p / Pr with the mixture c_p.
+// ---------------------------------------------------------------------------------------
+struct Mix {
+  double rho, v[3], T, p, a, cp, rcv;  // rcv = sum rho_s cv_s
+};
+
+Mix mixture(const OrcProblem& P, const double* u) {
+  const OrcMech& m = *P.mech;
+  const int ns = m.n_species, dim = P.dim;
+  Mix q;
+  q.rho = 0.0;
+  double rR = 0.0, rcv = 0.0, rh0 = 0.0;
+  for (int s = 0; s < ns; ++s) {
+    q.rho += u[s];
+    rR += u[s] * m.R[s];
+    rcv += u[s] * m.cv[s];
+    rh0 += u[s] * m.h0[s];
+  }
+  double kin = 0.0;
+  for (int d = 0; d < 3; ++d) q.v[d] = 0.0;
+  for (int d = 0; d < dim; ++d) {
+    q.v[d] = u[ns + d] / q.rho;
+    kin += u[ns + d] * q.v[d];
+  }
+  q.T = (u[ns + dim] - 0.5 * kin - rh0) / rcv;
+  q.p = rR * q.T;
+  q.a = std::sqrt((1.0 + rR / rcv) * q.p / q.rho);
+  q.cp = (rcv + rR) / q.rho;
+  q.rcv = rcv;
+  return q;
+}
+
+// inviscid flux in direction l (Sec. 2, F_inv of the reacting system)
+void mix_flux(const OrcProblem& P, int l, const double* u, double* F) {
+  const int ns = P.mech->n_species, dim = P.dim;
+  Mix q = mixture(P, u);
+  for (int s = 0; s < ns; ++s) F[s] = u[s] * q.v[l];
+  for (int d = 0; d < dim; ++d) F[ns + d] = u[ns + l] * q.v[d] + (d == l ? q.p : 0.0);
+  F[ns + dim] = (u[ns + dim] + q.p) * q.v[l];
+}
+
+void mix_rusanov(const OrcProblem& P, int l, const double* uL, const double* uR, double* F) {
+  const int nv = n_vars(P);
+  Mix a = mixture(P, uL), b = mixture(P, uR);
+  double lam = std::fmax(std::fabs(a.v[l]) + a.a, std::fabs(b.v[l]) + b.a);
+  double FL[16], FR[16];
+  mix_flux(P, l, uL, FL);
+  mix_flux(P, l, uR, FR);
+  for (int v = 0; v < nv; ++v) F[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * lam * (uR[v] - uL[v]);
+}
+
+// Arrhenius source (Sec. 3.1.3 and App. C, Eqs. src_reaction_rate and src_omega), single
+// temperature:
+// [X_s] = rho_s / W_s (mol/cm^3), R_r = k_f prod [X]^nu' - (k_f / K_c) prod [X]^nu'',
+// omega_s = W_s sum_r (nu'' - nu') R_r (converted to kg m^-3 s^-1); momentum and energy 0.
+void arrhenius(const OrcMech& m, int r, double T, double& kf, double& Kc) {
+  const double Z = 1.0e4 / T;
+  kf = std::exp(m.lnA[r] + m.b[r] * std::log(T) - m.Ta[r] / T);
+  Kc = std::exp(m.kc[r][0] / Z + m.kc[r][1] + m.kc[r][2] * std::log(Z) + m.kc[r][3] * Z +
+                m.kc[r][4] * Z * Z);
+}
+
+void chem_source(const OrcProblem& P, const double* u, double* S) {
+  const OrcMech& m = *P.mech;
+  const int ns = m.n_species, nv = n_vars(P);
+  for (int v = 0; v < nv; ++v) S[v] = 0.0;
+  Mix q = mixture(P, u);
+  double X[8];
+  for (int s = 0; s < ns; ++s) X[s] = u[s] / m.W[s] * 1.0e-6;
+  for (int r = 0; r < m.n_reactions; ++r) {
+    double kf, Kc;
+    arrhenius(m, r, q.T, kf, Kc);
+    double pf = 1.0, pb = 1.0;
+    for (int s = 0; s < ns; ++s) {
+      for (int k = 0; k < m.nu_f[r][s]; ++k) pf *= X[s];
+      for (int k = 0; k < m.nu_b[r][s]; ++k) pb *= X[s];
+    }
+    const double Rr = kf * pf - kf / Kc * pb;
+    for (int s = 0; s < ns; ++s) S[s] += m.W[s] * 1.0e6 * (m.nu_b[r][s] - m.nu_f[r][s]) * Rr;
+  }
+}
+
+// BR1 gradient (Sec. 3.1.2 Eq. br1_avg; App. A "Viscous Volume and Interface Fluxes") of
+// W = (u, v, w, T) on element e: S_l = (2/dx_l) [D W + (upper face) (W^ - W_N)/w_N
+// - (lower face) (W^ - W_0)/w_0], W^ = (W_L + W_R)/2.  Layout G[(node * 4 + q) * 3 + l].
+void br1_gradient(const OrcProblem& P, const Mesh& M, const Ops& ops, const double* U, int e,
+                  double* G) {
+  const int dim = M.dim, n1 = M.n1, N = M.N, nv = n_vars(P);
+  auto prim = [&](int el, int nd, double* W) {
+    double u[16];
+    load_node(M, nv, U, el, nd, u);
+    Mix q = mixture(P, u);
+    W[0] = q.v[0]; W[1] = q.v[1]; W[2] = q.v[2]; W[3] = q.T;
+  };
+  for (int nd = 0; nd < M.n_nodes; ++nd) {
+    int ijk[3];
+    M.node_coords(nd, ijk);
+    for (int q = 0; q < 4; ++q)
+      for (int l = 0; l < 3; ++l) G[((size_t)(e * M.n_nodes + nd) * 4 + q) * 3 + l] = 0.0;
+    for (int l = 0; l < dim; ++l) {
+      const double s = 2.0 / M.dx[l];
+      double acc[4] = {0, 0, 0, 0}, Wm[4];
+      for (int m = 0; m < n1; ++m) {
+        int mk[3] = {ijk[0], ijk[1], ijk[2]};
+        mk[l] = m;
+        prim(e, M.node(mk), Wm);
+        for (int q = 0; q < 4; ++q) acc[q] += ops.D[ijk[l] * n1 + m] * Wm[q];
+      }
+      double Wo[4], Wn[4];
+      prim(e, nd, Wo);
+      if (ijk[l] == N) {
+        int nk[3] = {ijk[0], ijk[1], ijk[2]};
+        nk[l] = 0;
+        prim(M.neighbour(e, l, +1), M.node(nk), Wn);
+        for (int q = 0; q < 4; ++q) acc[q] += (0.5 * (Wo[q] + Wn[q]) - Wo[q]) / ops.w[N];
+      }
+      if (ijk[l] == 0) {
+        int nk[3] = {ijk[0], ijk[1], ijk[2]};
+        nk[l] = N;
+        prim(M.neighbour(e, l, -1), M.node(nk), Wn);
+        for (int q = 0; q < 4; ++q) acc[q] -= (0.5 * (Wn[q] + Wo[q]) - Wo[q]) / ops.w[0];
+      }
+      for (int q = 0; q < 4; ++q) G[((size_t)(e * M.n_nodes + nd) * 4 + q) * 3 + l] = s * acc[q];
+    }
+  }
+}
+
+// viscous flux in direction l (Sec. 2 F_v; Sec. 3.1.2 Eq. tau; q = -k grad T):
+// (0 for species, tau_{.l}, u . tau_{.l} + k dT/dx_l)
+void viscous_flux(const OrcProblem& P, int l, const double* u, const double* g, double* F) {
+  const int ns = P.mech->n_species, dim = P.dim, nv = n_vars(P);
+  Mix q = mixture(P, u);
+  const double mu = P.mu, k = mu * q.cp / P.prandtl;
+  double div = 0.0;
+  for (int d = 0; d < dim; ++d) div += g[d * 3 + d];  // du_d/dx_d
+  for (int v = 0; v < nv; ++v) F[v] = 0.0;
+  double work = 0.0;
+  for (int j = 0; j < dim; ++j) {
+    double tau = mu * (g[j * 3 + l] + g[l * 3 + j]) - (j == l ? 2.0 / 3.0 * mu * div : 0.0);
+    F[ns + j] = tau;
+    work += q.v[j] * tau;
+  }
+  F[ns + dim] = work + k * g[3 * 3 + l];
+}
+
+void reacting_element_residual(const OrcProblem& P, const Mesh& M, const Ops& ops, const double* U,
+                               const double* G, int e, double* dU) {
+  const int dim = M.dim, n1 = M.n1, N = M.N, nv = n_vars(P);
+  const int parts = P.parts ? P.parts : 7;
+  std::vector<double> R((size_t)M.n_nodes * nv, 0.0);
+  auto grad = [&](int el, int nd) { return G + (size_t)(el * M.n_nodes + nd) * 12; };
+  double um[16], F[16];
+  for (int nd = 0; nd < M.n_nodes; ++nd) {
+    int ijk[3];
+    M.node_coords(nd, ijk);
+    for (int l = 0; l < dim; ++l) {
+      const double s = 2.0 / M.dx[l];
+      for (int m = 0; m < n1; ++m) {
+        int mk[3] = {ijk[0], ijk[1], ijk[2]};
+        mk[l] = m;
+        const int nm = M.node(mk);
+        load_node(M, nv, U, e, nm, um);
+        const double c = s * ops.D[ijk[l] * n1 + m];
+        if (parts & 1) {
+          mix_flux(P, l, um, F);
+          for (int v = 0; v < nv; ++v) R[nd * nv + v] -= c * F[v];
+        }
+        if (parts & 2) {
+          viscous_flux(P, l, um, grad(e, nm), F);
+          for (int v = 0; v < nv; ++v) R[nd * nv + v] += c * F[v];
+        }
+      }
+    }
+  }
+  for (int l = 0; l < dim; ++l) {
+    const double s = 2.0 / M.dx[l];
+    for (int nd = 0; nd < M.n_nodes; ++nd) {
+      int ijk[3];
+      M.node_coords(nd, ijk);
+      if (ijk[l] != N && ijk[l] != 0) continue;
+      double uown[16], unbr[16], Fs[16], Fo[16], Fvo[16], Fvn[16];
+      load_node(M, nv, U, e, nd, uown);
+      for (int side = 0; side < 2; ++side) {
+        if ((side == 1 && ijk[l] != N) || (side == 0 && ijk[l] != 0)) continue;
+        int nk[3] = {ijk[0], ijk[1], ijk[2]};
+        nk[l] = side ? 0 : N;
+        const int en = M.neighbour(e, l, side ? +1 : -1), nn = M.node(nk);
+        load_node(M, nv, U, en, nn, unbr);
+        const double lift = s / ops.w[side ? N : 0];
+        if (parts & 1) {
+          if (side) mix_rusanov(P, l, uown, unbr, Fs);
+          else mix_rusanov(P, l, unbr, uown, Fs);
+          mix_flux(P, l, uown, Fo);
+          for (int v = 0; v < nv; ++v) R[nd * nv + v] += (side ? -lift : lift) * (Fs[v] - Fo[v]);
+        }
+        if (parts & 2) {  // BR1 central viscous flux (Eq. br1_flux)
+          viscous_flux(P, l, uown, grad(e, nd), Fvo);
+          viscous_flux(P, l, unbr, grad(en, nn), Fvn);
+          for (int v = 0; v < nv; ++v)
+            R[nd * nv + v] += (side ? lift : -lift) * (0.5 * (Fvo[v] + Fvn[v]) - Fvo[v]);
+        }
+      }
+    }
+  }
+  if (parts & 4) {
+    for (int nd = 0; nd < M.n_nodes; ++nd) {
+      load_node(M, nv, U, e, nd, um);
+      chem_source(P, um, F);
+      for (int v = 0; v < nv; ++v) R[nd * nv + v] += F[v];
+    }
+  }
+  for (int nd = 0; nd < M.n_nodes; ++nd)
+    for (int v = 0; v < nv; ++v) dU[((size_t)v * M.n_elem + e) * M.n_nodes + nd] = R[nd * nv + v];
 }
 
 void residual(const OrcProblem& P, const double* U, double* dU) {
   Mesh M(P);
   Ops ops(P.N);
+  if (P.equations == ORC_NS_REACTING) {
+    std::vector<double> G((size_t)M.n_elem * M.n_nodes * 12, 0.0);
+    const int parts = P.parts ? P.parts : 7;
+    if (parts & 2) {
+#pragma omp parallel for schedule(static)
+      for (int e = 0; e < M.n_elem; ++e) br1_gradient(P, M, ops, U, e, G.data());
+    }
+#pragma omp parallel for schedule(static)
+    for (int e = 0; e < M.n_elem; ++e) reacting_element_residual(P, M, ops, U, G.data(), e, dU);
+    return;
+  }
 #pragma omp parallel for schedule(static)
   for (int e = 0; e < M.n_elem; ++e) euler_element_residual(P, M, ops, U, e, dU);
 }
@@ -632,6 +888,29 @@ int orc_two_point_flux(int kind, int dim, int l, double gamma, const double* uL,
   return 0;
 }
 
+// Arrhenius rate and equilibrium constant of reaction r at temperature T.
+int orc_arrhenius(const OrcMech* m, int r, double T, double* kf, double* Kc) {
+  if (!m || r < 0 || r >= m->n_reactions || !(T > 0.0)) return -1;
+  arrhenius(*m, r, T, *kf, *Kc);
+  return 0;
+}
+
+// Chemical source of one node state (reacting problems).
+int orc_chem_source(const OrcProblem* P, const double* u, double* S) {
+  if (P->equations != ORC_NS_REACTING || !P->mech) return -1;
+  chem_source(*P, u, S);
+  return 0;
+}
+
+// Temperature and pressure of one node state (reacting problems).
+int orc_mixture(const OrcProblem* P, const double* u, double* T, double* p) {
+  if (P->equations != ORC_NS_REACTING || !P->mech) return -1;
+  Mix q = mixture(*P, u);
+  *T = q.T;
+  *p = q.p;
+  return 0;
+}
+
 // dU/dt = L(U) (Appendix B, Eq. for the semi-discrete system).
 int orc_rhs(const OrcProblem* P, const double* U, double* dU) {
   int rc = check_problem(*P);
@@ -649,6 +928,14 @@ int orc_rhs_elements(const OrcProblem* P, const double* U, const int* elems, int
   Ops ops(P->N);
   for (int k = 0; k < n; ++k) {
     if (elems[k] < 0 || elems[k] >= M.n_elem) return -1;
+  }
+  if (P->equations == ORC_NS_REACTING) {
+    std::vector<double> G((size_t)M.n_elem * M.n_nodes * 12, 0.0);
+#pragma omp parallel for schedule(static)
+    for (int e = 0; e < M.n_elem; ++e) br1_gradient(*P, M, ops, U, e, G.data());
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < n; ++k) reacting_element_residual(*P, M, ops, U, G.data(), elems[k], dU);
+    return 0;
   }
 #pragma omp parallel for schedule(static)
   for (int k = 0; k < n; ++k) euler_element_residual(*P, M, ops, U, elems[k], dU);
@@ -702,7 +989,8 @@ int orc_rhs_jvp(const OrcProblem* P, const double* U, const double* V, double gd
                 double* dL) {
   int rc = check_problem(*P);
   if (rc) return rc;
-  if ((P->volume != ORC_VOL_STRONG && P->volume != ORC_VOL_WEAK) || P->surface != ORC_SURF_RUSANOV)
+  if ((P->volume != ORC_VOL_STRONG && P->volume != ORC_VOL_WEAK) || P->surface != ORC_SURF_RUSANOV ||
+      P->equations != ORC_EULER)
     return -6;
   Mesh M(*P);
   Ops ops(P->N);
@@ -752,9 +1040,31 @@ int orc_max_dt(const OrcProblem* P, const double* U, double cfl, double* dt) {
   int rc = check_problem(*P);
   if (rc) return rc;
   Mesh M(*P);
-  const int dim = M.dim, nv = dim + 2;
+  const int dim = M.dim, nv = n_vars(*P);
   const size_t stride = (size_t)M.n_elem * M.n_nodes;
   double lam = 0.0;
+  if (P->equations == ORC_NS_REACTING) {
+    // reacting: frozen sound speed of the mixture for dt_C; the diffusive bound
+    // (Sec. 3.1.2 Eq. dt_para; App. B) dt_D = cfl dx_min^2 / ((2N+1)^2 nu_max) with
+    // nu_max = max over nodes of max(mu / rho, k / (rho c_p)) = max(mu/rho, mu/(rho Pr)).
+    // READING: cfl multiplies both bounds (the SSP coefficient of SSP-RK3 is 1).
+    double nu = 0.0;
+    for (size_t q = 0; q < stride; ++q) {
+      double u[16];
+      for (int v = 0; v < nv; ++v) u[v] = U[v * stride + q];
+      Mix m = mixture(*P, u);
+      double speed = 0.0;
+      for (int d = 0; d < dim; ++d) speed += m.v[d] * m.v[d];
+      lam = std::fmax(lam, std::sqrt(speed) + m.a);
+      nu = std::fmax(nu, std::fmax(P->mu / m.rho, P->mu / (m.rho * P->prandtl)));
+    }
+    double dxmin = M.dx[0];
+    for (int l = 1; l < dim; ++l) dxmin = std::fmin(dxmin, M.dx[l]);
+    const double dtc = cfl * dxmin / ((2 * P->N + 1) * lam);
+    const double n2 = (2.0 * P->N + 1) * (2.0 * P->N + 1);
+    *dt = nu > 0.0 ? std::fmin(dtc, cfl * dxmin * dxmin / (n2 * nu)) : dtc;
+    return 0;
+  }
   for (size_t q = 0; q < stride; ++q) {
     double u[8];
     for (int v = 0; v < nv; ++v) u[v] = U[v * stride + q];

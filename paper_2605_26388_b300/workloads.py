@@ -178,3 +178,98 @@ def perturbed(U: np.ndarray, seed: int, rel: float) -> np.ndarray:
     """U times (1 + rel * xi), xi ~ U[-1, 1] seeded per entry (a non-smooth test state)."""
     r = uniform(seed, U.size).reshape(U.shape)
     return U * (1.0 + rel * (2.0 * r - 1.0))
+
+
+# ------------------------------------------------------------------------------------------
+# 5-species air (N2, O2, NO, N, O): species data and a seeded reaction mechanism
+# ------------------------------------------------------------------------------------------
+R_UNIVERSAL = 8.314462618  # J/(mol K)
+SPECIES = ("N2", "O2", "NO", "N", "O")
+_W_N, _W_O = 0.0140067, 0.0159994  # kg/mol; molecules are exact sums (atom balance)
+MOLAR_MASS = (2 * _W_N, 2 * _W_O, _W_N + _W_O, _W_N, _W_O)
+DIATOMIC = (True, True, True, False, False)
+# formation enthalpies per mole (J/mol; N2 and O2 are the references), per kg below
+_H0_MOLAR = (0.0, 0.0, 90291.0, 472680.0, 249175.0)
+ATOMS_N = (2, 0, 1, 1, 0)
+ATOMS_O = (0, 2, 1, 0, 1)
+
+
+def air5_mechanism(seed: int = 1, lg10A=(12.0, 22.0), b=(-1.6, 0.0), Ta=(2.0e4, 1.2e5)):
+    """Species properties and 17 seeded reactions (dict of plain numbers):
+    r = 0..14: X + M <-> products + M for X in (N2, O2, NO) and M each of the 5 species
+    (N2 -> 2N, O2 -> 2O, NO -> N + O); r = 15: N2 + O <-> NO + N; r = 16: N + O2 <-> NO + O.
+    Forward rate k_f = exp(lnA + b ln T - Ta/T) with log10 A ~ U[12,22], b ~ U[-1.6,0],
+    Ta ~ U[2e4,1.2e5] K (cm-mol-s units); equilibrium constant
+    ln K_c = a0/Z + a1 + a2 ln Z + a3 Z + a4 Z^2, Z = 1e4/T, seeded so that |ln K_c| < 40 on
+    2000-8000 K.  Calorically perfect species: c_v = 5/2 R_s (diatomic), 3/2 R_s (atomic)."""
+    ns = 5
+    Rs = [R_UNIVERSAL / w for w in MOLAR_MASS]
+    cv = [(2.5 if d else 1.5) * r for d, r in zip(DIATOMIC, Rs)]
+    h0 = [h / w for h, w in zip(_H0_MOLAR, MOLAR_MASS)]
+    nu_f, nu_b = [], []
+    for x, prod in ((0, (3, 3)), (1, (4, 4)), (2, (3, 4))):
+        for m in range(ns):
+            f = [0] * ns
+            bk = [0] * ns
+            f[x] += 1
+            f[m] += 1
+            for p_ in prod:
+                bk[p_] += 1
+            bk[m] += 1
+            nu_f.append(f)
+            nu_b.append(bk)
+    nu_f.append([1, 0, 0, 0, 1]); nu_b.append([0, 0, 1, 1, 0])  # N2 + O <-> NO + N
+    nu_f.append([0, 1, 0, 1, 0]); nu_b.append([0, 0, 1, 0, 1])  # N + O2 <-> NO + O
+    nr = len(nu_f)
+    r = uniform(seed, 8 * nr)
+    lnA, bb, ta, kc = [], [], [], []
+    for i in range(nr):
+        lnA.append(math.log(10.0) * (lg10A[0] + (lg10A[1] - lg10A[0]) * r[8 * i]))
+        bb.append(b[0] + (b[1] - b[0]) * r[8 * i + 1])
+        ta.append(Ta[0] + (Ta[1] - Ta[0]) * r[8 * i + 2])
+        kc.append([-1.0 + 2.0 * r[8 * i + 3], -5.0 + 10.0 * r[8 * i + 4], -1.0 + 2.0 * r[8 * i + 5],
+                   -5.0 * r[8 * i + 6], -0.2 + 0.4 * r[8 * i + 7]])
+    return {"n_species": ns, "n_reactions": nr, "W": list(MOLAR_MASS), "R": Rs, "cv": cv, "h0": h0,
+            "lnA": lnA, "b": bb, "Ta": ta, "kc": kc, "nu_f": nu_f, "nu_b": nu_b}
+
+
+def reacting_conserved(rho_s, vel, T, mech: dict) -> np.ndarray:
+    """Conserved reacting state (rho_1..rho_ns, rho u, ..., E) from partial densities, velocity
+    components and temperature of calorically perfect species:
+    E = sum_s rho_s (cv_s T + h0_s) + rho |u|^2 / 2."""
+    ns = int(mech["n_species"])
+    rho = sum(np.asarray(rho_s[s], dtype=np.float64) for s in range(ns))
+    shape = np.shape(rho)
+    U = np.zeros((ns + len(vel) + 1,) + shape)
+    e = np.zeros(shape)
+    for s in range(ns):
+        U[s] = rho_s[s]
+        e = e + U[s] * (mech["cv"][s] * T + mech["h0"][s])
+    kin = np.zeros(shape)
+    for d, v in enumerate(vel):
+        U[ns + d] = rho * v
+        kin = kin + v * v
+    U[ns + len(vel)] = e + 0.5 * rho * kin
+    return U
+
+
+def reacting_tgv_3d(nel: int, xi: np.ndarray, mech: dict, seed: int = 2, U0: float = 100.0,
+                    p0: float = 101325.0, lo=(0.0, 0.0, 0.0), hi=None):
+    """The reacting workload's state (9 conserved variables rho_s, rho u, rho v, rho w, E):
+    Taylor-Green velocity of amplitude U0 on [0, 2 pi]^3 m, uniform p0, temperature
+    T = 5000 + 3000 phi/max|phi| K with phi a seeded Fourier sum (|k| <= 3), air mass
+    fractions Y = (0.767, 0.233, 1e-10, 1e-10, 1e-10) normalised.  E from the calorically
+    perfect mixture: E = sum_s rho_s (cv_s T + h0_s) + rho |u|^2 / 2, p = sum_s rho_s R_s T."""
+    if hi is None:
+        hi = (2 * math.pi,) * 3
+    X = node_coordinates(3, (nel, nel, nel), lo, hi, xi)
+    x, y, z = X
+    T = 5000.0 + 3000.0 * fourier_field(seed, X, lo, hi, 3)
+    Y = np.array([0.767, 0.233, 1e-10, 1e-10, 1e-10])
+    Y = Y / Y.sum()
+    Rmix = float(np.dot(Y, mech["R"]))
+    rho = p0 / (Rmix * T)
+    u = U0 * np.sin(x) * np.cos(y) * np.cos(z)
+    v = -U0 * np.cos(x) * np.sin(y) * np.cos(z)
+    w = np.zeros_like(x)
+    return reacting_conserved([rho * Y[s] for s in range(5)], [u, v, w], T, mech)
