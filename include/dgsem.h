@@ -1,10 +1,14 @@
 /* dgsem.h -- C-ABI of the B300 (sm_103a) DGSEM residual and SSP-RK3 stage library.
  *
  * The library evaluates the semi-discrete DGSEM residual of the compressible Euler
- * equations on periodic Cartesian meshes and advances it with the three-stage SSP-RK
- * scheme, entirely in hand-written CUDA kernels (one fused kernel per RK stage).  The
- * operations follow arXiv 2605.26388:
+ * equations, and of the single-temperature reacting Navier-Stokes equations, on periodic
+ * Cartesian meshes and advances it with the three-stage SSP-RK scheme, entirely in
+ * hand-written CUDA kernels (one fused kernel per RK stage for Euler; a BR1 gradient pass
+ * plus one fused kernel for Navier-Stokes).  The operations follow arXiv 2605.26388:
  *   - equations and ideal-gas closure: Sec. 2;
+ *   - viscous terms: BR1 lifting (Sec. 3.1.2, Eqs. br1_avg, tau, br1_flux);
+ *   - finite-rate chemistry: Arrhenius source (Sec. 3.1.3, Eqs. src_reaction_rate,
+ *     src_omega; App. C);
  *   - element-local DGSEM on (N+1)^d GLL nodes: Sec. 3.1.1 and App. A;
  *   - volume term: Eq. vol_weak (strong form; the weak form is the same operator by the
  *     SBP property) or Eq. vol_split / Eq. split_form_3D (flux differencing with the
@@ -14,7 +18,8 @@
  *
  * Conventions shared by every entry point:
  *   - State layout (SoA, FP64): U[v * n_nodes_total + node_offset(instance) + e * n_p + q]
- *     with v the conserved variable (rho, rho u, rho v[, rho w], E), e the element index
+ *     with v the conserved variable -- Euler: (rho, rho u, rho v[, rho w], E); Navier-Stokes:
+ *     (rho_1 .. rho_ns, rho u, rho v, rho w, E) -- e the element index
  *     within its instance (lexicographic, x fastest), q the node index within the element
  *     (lexicographic, i fastest) and n_p = (N+1)^dim.  n_nodes_total is the sum over
  *     instances of n_elem * n_p.
@@ -54,7 +59,11 @@ typedef enum {
   DG_ETOOLARGE = -7     /* more instances than dg_max_dt_noalloc's static scratch holds */
 } dg_status;
 
-enum { DG_EULER = 0 };
+/* Equations.  DG_NAVIER_STOKES is the single-gas, non-dimensional case (R = 1, so T = p/rho,
+ * cv = 1/(gamma-1), conductivity k = gamma mu / ((gamma-1) Pr)); DG_NS_REACTING takes its
+ * species and reactions from dg_physics.chem (SI units).  Both: 3D, strong volume form,
+ * Rusanov surface flux, FP64, no positivity floor; others return DG_EUNSUPPORTED. */
+enum { DG_EULER = 0, DG_NAVIER_STOKES = 1, DG_NS_REACTING = 2 };
 /* Volume term: strong form (Eq. vol_weak), weak form (integrated by parts; equal to the
  * strong form by SBP), or two-point flux differencing with Ranocha's EC flux
  * (Eq. vol_split). */
@@ -71,15 +80,40 @@ enum { DG_FP64 = 0, DG_FP32_MIXED = 1 };
  * reference cube; collocation on (N+1)^dim GLL nodes). */
 typedef struct {
   int dim;          /* 2 or 3 */
-  int N;            /* polynomial degree: 1..7 in 2D, 1..5 in 3D */
+  int N;            /* polynomial degree: 1..7 in 2D, 1..5 in 3D (Navier-Stokes: 1..4) */
   int nel[3];       /* elements per direction (nel[2] ignored in 2D) */
   double lo[3];     /* box lower corner */
   double hi[3];     /* box upper corner */
   int periodic[3];  /* must be 1 in every used direction, else DG_EUNSUPPORTED */
 } dg_mesh_desc;
 
+/* Species and reactions of a reacting mixture (Sec. 2 thermochemistry, single temperature;
+ * Sec. 3.1.3 and App. C).  Calorically perfect species: e_s = cv_s T + h0_s, p = sum rho_s R_s T.
+ * Reaction r: sum_s nu_f[r][s] X_s <-> sum_s nu_b[r][s] X_s with
+ *   k_f = exp(lnA + b ln T - Ta / T)                      (cm-mol-s units),
+ *   ln K_c = kc0 / Z + kc1 + kc2 ln Z + kc3 Z + kc4 Z^2,   Z = 10^4 / T,
+ *   R_r = k_f prod [X]^nu_f - (k_f / K_c) prod [X]^nu_b,   [X_s] = rho_s / W_s in mol/cm^3,
+ *   omega_s = 10^6 W_s sum_r (nu_b - nu_f) R_r            (kg m^-3 s^-1).
+ * Compiled kernels: n_species 1 or 5; each side of a reaction has at most 3 molecules. */
+#define DG_MAX_SPECIES 8
+#define DG_MAX_REACTIONS 32
+typedef struct dg_mechanism {
+  int n_species;                      /* 1..DG_MAX_SPECIES */
+  int n_reactions;                    /* 0..DG_MAX_REACTIONS */
+  double W[DG_MAX_SPECIES];           /* molar mass, kg/mol */
+  double R[DG_MAX_SPECIES];           /* specific gas constant, J/(kg K) */
+  double cv[DG_MAX_SPECIES];          /* specific heat at constant volume, J/(kg K) */
+  double h0[DG_MAX_SPECIES];          /* formation energy, J/kg */
+  double lnA[DG_MAX_REACTIONS];
+  double b[DG_MAX_REACTIONS];
+  double Ta[DG_MAX_REACTIONS];        /* activation temperature, K */
+  double kc[DG_MAX_REACTIONS][5];
+  int nu_f[DG_MAX_REACTIONS][DG_MAX_SPECIES];
+  int nu_b[DG_MAX_REACTIONS][DG_MAX_SPECIES];
+} dg_mechanism;
+
 typedef struct {
-  int equations;    /* DG_EULER */
+  int equations;    /* DG_EULER | DG_NAVIER_STOKES | DG_NS_REACTING */
   int volume;       /* DG_VOL_* */
   int surface;      /* DG_SURF_* */
   int precision;    /* DG_FP64 | DG_FP32_MIXED */
@@ -91,6 +125,10 @@ typedef struct {
                      * to zero; F* - F(U_own) is invariant to a common constant) and keeps FP32
                      * flux arithmetic out of cancellation at low Mach number.  0 = no shift.
                      * dg_two_point_flux reports momentum fluxes with this shift applied. */
+  /* Navier-Stokes only (ignored for DG_EULER): */
+  double mu;        /* constant dynamic viscosity (>= 0) */
+  double prandtl;   /* Prandtl number (> 0); conductivity k = mu c_p / Pr */
+  const dg_mechanism* chem;  /* DG_NS_REACTING: species and reactions (copied at init) */
 } dg_physics;
 
 /* Build a context for n_inst instances (all of the same dim) sharing one physics
@@ -114,7 +152,7 @@ DG_API dg_status dg_instance_offset(const dg_ctx* ctx, int i, int64_t* offset);
 DG_API dg_status dg_set_state(dg_ctx* ctx, const double* U);
 DG_API dg_status dg_get_state(const dg_ctx* ctx, double* U);
 
-/* dUdt = L(U) at time t (the Euler residual does not depend on t).  U and dUdt are device
+/* dUdt = L(U) at time t (the residual does not depend on t).  U and dUdt are device
  * pointers of dg_state_size() doubles and must not overlap. */
 DG_API dg_status dg_rhs(dg_ctx* ctx, const double* U, double* dUdt, double t);
 
@@ -131,9 +169,10 @@ DG_API dg_status dg_rk_stage(dg_ctx* ctx, int stage, const double* Un, const dou
  * collect device-side errors. */
 DG_API dg_status dg_rk_step(dg_ctx* ctx, double dt, int n_steps);
 
-/* Adjoint of the residual (SURVEY differentiable form; the paper has no adjoint -- it is the
+/* Adjoint of the residual (for differentiable rollouts; the paper has no adjoint -- it is the
  * exact transpose of the semi-discrete operator of Eq. vol_weak + Eq. surf_int with the
- * Rusanov flux, strong or weak volume form; other choices return DG_EUNSUPPORTED):
+ * Rusanov flux, strong or weak volume form, Euler equations; other choices return
+ * DG_EUNSUPPORTED):
  *   Ubar += (dL/dU)^T lam            (device arrays of dg_state_size() doubles)
  *   *gammabar += lam . dL/dgamma     (host double)
  * Non-smooth points follow the forward evaluation: the larger Rusanov signal speed (the left
@@ -152,13 +191,15 @@ DG_API dg_status dg_rk_step_vjp(dg_ctx* ctx, const double* Un, double dt, double
 /* Launch modes for contexts with several instances. */
 enum { DG_LAUNCH_PER_INSTANCE = 0, DG_LAUNCH_BATCHED = 1 };
 
-/* How a stage is launched over the context's instances (SURVEY batched form; the paper runs
+/* How a stage is launched over the context's instances (batched form; the paper runs
  * one problem at a time): one fused launch per instance, or one persistent launch per stage
  * over a work list of (instance, element group) items covering every instance -- the default
  * when n_inst > 1.  group_scale (1, or 2 in 2D) multiplies the elements per work item;
  * ctas_per_sm caps the persistent grid (0 = as many CTAs as fit); order 0 puts the heaviest
  * items (degree, then instance) first, 1 keeps instance order.  Synchronizes the stream and
- * rebuilds the work list; DG_EINVAL on an out-of-range choice. */
+ * rebuilds the work list; DG_EINVAL on an out-of-range choice.  The batched mode (and the
+ * autotuner below) exists for the Euler equations; Navier-Stokes contexts return
+ * DG_EUNSUPPORTED for it. */
 DG_API dg_status dg_set_launch(dg_ctx* ctx, int mode, int group_scale, int ctas_per_sm, int order);
 
 /* Autotuner for the launch configuration: times n_reps SSP-RK3 steps of size dt for the
@@ -170,7 +211,10 @@ DG_API dg_status dg_autotune(dg_ctx* ctx, double dt, int n_reps, int* config_out
 
 /* Convective time-step bound of Eq. dt_hyp on the context-held state:
  *   dt = cfl * dx_min / ((2N+1) * max over nodes of (|u| + a)),
- * taking the minimum over instances.  Synchronizes the stream; *dt_out is a host double. */
+ * taking the minimum over instances.  Navier-Stokes: a is the frozen mixture sound speed and
+ * the result is min(dt_C, dt_D) with the diffusive bound of Eq. dt_para,
+ *   dt_D = cfl * dx_min^2 / ((2N+1)^2 * max over nodes of max(mu/rho, mu/(rho Pr))).
+ * Synchronizes the stream; *dt_out is a host double. */
 DG_API dg_status dg_max_dt(dg_ctx* ctx, double cfl, double* dt_out);
 
 /* Synchronize the context's stream, then read and clear the device error word:
@@ -183,7 +227,7 @@ DG_API dg_status dg_gll(int N, double* x, double* w, double* D);
 
 /* Evaluate the device's two-point flux for n state pairs (device pointers, AoS n x n_vars)
  * in direction l: kind = -1 the EC volume flux, else a DG_SURF_* kind.  Uses the context's
- * precision and gamma.  Test and inspection aid. */
+ * precision and gamma.  Test and inspection aid (Euler contexts only). */
 DG_API dg_status dg_two_point_flux(dg_ctx* ctx, int kind, int l, int n, const double* uL,
                             const double* uR, double* F);
 

@@ -930,9 +930,21 @@ int orc_rhs_elements(const OrcProblem* P, const double* U, const int* elems, int
     if (elems[k] < 0 || elems[k] >= M.n_elem) return -1;
   }
   if (P->equations == ORC_NS_REACTING) {
+    // gradients are needed on the listed elements and their face neighbours only
     std::vector<double> G((size_t)M.n_elem * M.n_nodes * 12, 0.0);
+    std::vector<int> need;
+    std::vector<char> mark(M.n_elem, 0);
+    for (int k = 0; k < n; ++k) {
+      const int e = elems[k];
+      if (!mark[e]) { mark[e] = 1; need.push_back(e); }
+      for (int l = 0; l < M.dim; ++l)
+        for (int dir = -1; dir <= 1; dir += 2) {
+          const int en = M.neighbour(e, l, dir);
+          if (!mark[en]) { mark[en] = 1; need.push_back(en); }
+        }
+    }
 #pragma omp parallel for schedule(static)
-    for (int e = 0; e < M.n_elem; ++e) br1_gradient(*P, M, ops, U, e, G.data());
+    for (int k = 0; k < (int)need.size(); ++k) br1_gradient(*P, M, ops, U, need[k], G.data());
 #pragma omp parallel for schedule(static)
     for (int k = 0; k < n; ++k) reacting_element_residual(*P, M, ops, U, G.data(), elems[k], dU);
     return 0;

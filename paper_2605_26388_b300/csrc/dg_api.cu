@@ -42,6 +42,13 @@ struct dg_ctx {
   double* adj[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   double* gpart = nullptr;
   double* gacc = nullptr;
+  // Navier-Stokes: mechanism (device copy), face buffer of the BR1 pass and its per-instance
+  // offsets (doubles)
+  bool ns = false;
+  int n_species = 0;
+  dg::MechDev* d_mech = nullptr;
+  double* fb = nullptr;
+  std::vector<long long> fb_offs;
 };
 
 namespace {
@@ -131,6 +138,59 @@ dg_status check_desc(const dg_mesh_desc& m, int dim0, std::string& why) {
   return DG_OK;
 }
 
+// The kernels' copy of a mechanism: species data, per-reaction Arrhenius and K_c
+// coefficients, the species of each side's concentration product (at most three molecules;
+// index n_species stands for a factor 1) and the source coefficients W_s 1e6 (nu'' - nu').
+dg_status pack_mechanism(const dg_mechanism& m, dg::MechDev& d, std::string& why) {
+  std::memset(&d, 0, sizeof(d));
+  if (m.n_species < 1 || m.n_species > DG_MAX_SPECIES || m.n_reactions < 0 ||
+      m.n_reactions > DG_MAX_REACTIONS) {
+    why = "species or reaction count out of range";
+    return DG_EINVAL;
+  }
+  const int ns = m.n_species;
+  d.ns = ns;
+  d.nr = m.n_reactions;
+  for (int s = 0; s < ns; ++s) {
+    if (!(m.W[s] > 0.0) || !(m.R[s] > 0.0) || !(m.cv[s] > 0.0) || !std::isfinite(m.h0[s]) ||
+        !std::isfinite(m.W[s]) || !std::isfinite(m.R[s]) || !std::isfinite(m.cv[s])) {
+      why = "species data must be finite with W, R, cv > 0";
+      return DG_EINVAL;
+    }
+    d.R[s] = m.R[s];
+    d.cv[s] = m.cv[s];
+    d.h0[s] = m.h0[s];
+    d.scale[s] = 1.0e-6 / m.W[s];
+  }
+  for (int r = 0; r < m.n_reactions; ++r) {
+    dg::RxnDev& x = d.rx[r];
+    x.lnA = m.lnA[r];
+    x.b = m.b[r];
+    x.Ta = m.Ta[r];
+    bool ok = std::isfinite(x.lnA) && std::isfinite(x.b) && std::isfinite(x.Ta);
+    for (int k = 0; k < 5; ++k) {
+      x.kc[k] = m.kc[r][k];
+      ok = ok && std::isfinite(x.kc[k]);
+    }
+    if (!ok) { why = "reaction coefficients must be finite"; return DG_EINVAL; }
+    int nf = 0, nb = 0;
+    for (int k = 0; k < 3; ++k) x.f[k] = x.bk[k] = ns;
+    for (int s = 0; s < ns; ++s) {
+      if (m.nu_f[r][s] < 0 || m.nu_b[r][s] < 0) { why = "negative stoichiometric coefficient"; return DG_EINVAL; }
+      for (int k = 0; k < m.nu_f[r][s]; ++k) {
+        if (nf == 3) { why = "more than 3 molecules on one side of a reaction"; return DG_EUNSUPPORTED; }
+        x.f[nf++] = s;
+      }
+      for (int k = 0; k < m.nu_b[r][s]; ++k) {
+        if (nb == 3) { why = "more than 3 molecules on one side of a reaction"; return DG_EUNSUPPORTED; }
+        x.bk[nb++] = s;
+      }
+      x.coef[s] = m.W[s] * 1.0e6 * (double)(m.nu_b[r][s] - m.nu_f[r][s]);
+    }
+  }
+  return DG_OK;
+}
+
 long long n_elem_of(const dg_mesh_desc& m) {
   return (long long)m.nel[0] * m.nel[1] * (m.dim == 3 ? m.nel[2] : 1);
 }
@@ -209,8 +269,45 @@ void launch_args(const dg_ctx* c, dg::StageArgs& a, const double* U, const doubl
 
 // One fused stage over all instances: mode 0 writes L(U), mode 1 the stage update.  One
 // launch per instance, or one batched launch for all of them.
+dg_status run_stage_ns(dg_ctx* c, const double* U, const double* Un, double* out, int mode,
+                       double ca, double cb, double dt, cudaStream_t s) {
+  dg::ReactArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.U = U;
+  a.Un = Un;
+  a.out = out;
+  a.err = c->err;
+  a.mech = c->d_mech;
+  a.stride = c->n_nodes_total;
+  a.mode = mode;
+  a.need_un = (mode == 1 && ca != 0.0) ? 1 : 0;
+  a.ca = ca;
+  a.cb = cb;
+  a.cbdt = cb * dt;
+  a.mu = c->phys.mu;
+  a.kfac = c->phys.mu / c->phys.prandtl;
+  a.ln1e4 = std::log(1.0e4);
+  for (size_t i = 0; i < c->inst.size(); ++i) {
+    const dg_mesh_desc& m = c->inst[i];
+    a.base = c->offs[i];
+    a.fb = c->fb + c->fb_offs[i];
+    for (int l = 0; l < 3; ++l) {
+      a.nel[l] = m.nel[l];
+      a.s[l] = 2.0 / ((m.hi[l] - m.lo[l]) / m.nel[l]);
+    }
+    a.n_elem = (int)n_elem_of(m);
+    double x[dg::kMaxN + 1], w[dg::kMaxN + 1];
+    gll_table(m.N, x, w, a.D);
+    a.lift = 1.0 / w[0];
+    cudaError_t e = dg::launch_reacting(m.N, c->n_species, a, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "Navier-Stokes stage launch");
+  }
+  return DG_OK;
+}
+
 dg_status run_stage(dg_ctx* c, const double* U, const double* Un, double* out, int mode,
                     double ca, double cb, double dt, cudaStream_t s) {
+  if (c->ns) return run_stage_ns(c, U, Un, out, mode, ca, cb, dt, s);
   const int ec = c->phys.volume == DG_VOL_EC, fp32 = c->phys.precision == DG_FP32_MIXED;
   dg::StageArgs a;
   launch_args(c, a, U, Un, out, mode, ca, cb, dt);
@@ -370,19 +467,48 @@ dg_status dg_init_mesh(const dg_mesh_desc* inst, int n_inst, const dg_physics* p
     dg_status s = check_desc(inst[i], inst[0].dim, why);
     if (s) return s;
   }
-  if (phys->equations != DG_EULER) return DG_EUNSUPPORTED;
+  if (phys->equations < DG_EULER || phys->equations > DG_NS_REACTING) return DG_EINVAL;
   if (phys->volume < DG_VOL_STRONG || phys->volume > DG_VOL_EC) return DG_EINVAL;
   if (phys->surface < DG_SURF_RUSANOV || phys->surface > DG_SURF_EC) return DG_EINVAL;
   if (phys->precision != DG_FP64 && phys->precision != DG_FP32_MIXED) return DG_EINVAL;
-  if (!(phys->gamma > 1.0)) return DG_EINVAL;
+  if (phys->equations != DG_NS_REACTING && !(phys->gamma > 1.0)) return DG_EINVAL;
   if (!std::isfinite(phys->p_ref)) return DG_EINVAL;
+  const bool navier_stokes = phys->equations != DG_EULER;
+  dg::MechDev mech;
+  if (navier_stokes) {
+    if (!(phys->mu >= 0.0) || !std::isfinite(phys->mu) || !(phys->prandtl > 0.0) ||
+        !std::isfinite(phys->prandtl))
+      return DG_EINVAL;
+    if (phys->equations == DG_NS_REACTING) {
+      if (!phys->chem) return DG_EINVAL;
+      dg_status st = pack_mechanism(*phys->chem, mech, why);
+      if (st) return st;
+    } else {
+      dg_mechanism one;
+      std::memset(&one, 0, sizeof(one));
+      one.n_species = 1;
+      one.W[0] = 1.0;
+      one.R[0] = 1.0;
+      one.cv[0] = 1.0 / (phys->gamma - 1.0);
+      dg_status st = pack_mechanism(one, mech, why);
+      if (st) return st;
+    }
+    if (inst[0].dim != 3) return DG_EUNSUPPORTED;
+    for (int i = 0; i < n_inst; ++i)
+      if (!dg::have_reacting(inst[i].N, mech.ns)) return DG_EUNSUPPORTED;
+    if (phys->volume != DG_VOL_STRONG || phys->surface != DG_SURF_RUSANOV ||
+        phys->precision != DG_FP64 || phys->rho_floor > 0.0 || phys->p_floor > 0.0)
+      return DG_EUNSUPPORTED;
+  }
 
   dg_ctx* c = new dg_ctx();
   c->inst.assign(inst, inst + n_inst);
   c->phys = *phys;
   c->stream = (cudaStream_t)cuda_stream;
   c->dim = inst[0].dim;
-  c->nv = c->dim + 2;
+  c->ns = navier_stokes;
+  c->n_species = navier_stokes ? mech.ns : 0;
+  c->nv = navier_stokes ? mech.ns + 4 : c->dim + 2;
   long long off = 0;
   for (int i = 0; i < n_inst; ++i) {
     c->offs.push_back(off);
@@ -398,7 +524,7 @@ dg_status dg_init_mesh(const dg_mesh_desc* inst, int n_inst, const dg_physics* p
     }
   }
   if (cudaMalloc(&c->err, sizeof(unsigned)) != cudaSuccess ||
-      cudaMalloc(&c->lam, sizeof(unsigned long long)) != cudaSuccess) {
+      cudaMalloc(&c->lam, 2 * sizeof(unsigned long long)) != cudaSuccess) {
     cudaGetLastError();
     dg_free(c);
     return DG_ENOMEM;
@@ -409,6 +535,33 @@ dg_status dg_init_mesh(const dg_mesh_desc* inst, int n_inst, const dg_physics* p
     cudaGetLastError();
     dg_free(c);
     return DG_ECUDA;
+  }
+  if (navier_stokes) {
+    long long nfb = 0;
+    for (int i = 0; i < n_inst; ++i) {
+      c->fb_offs.push_back(nfb);
+      nfb += n_elem_of(inst[i]) * 6 * 4 * (long long)(inst[i].N + 1) * (inst[i].N + 1);
+    }
+    if (cudaMalloc(&c->d_mech, sizeof(dg::MechDev)) != cudaSuccess ||
+        cudaMalloc(&c->fb, sizeof(double) * (size_t)nfb) != cudaSuccess) {
+      cudaGetLastError();
+      dg_free(c);
+      return DG_ENOMEM;
+    }
+    if (cudaMemcpy(c->d_mech, &mech, sizeof(mech), cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaGetLastError();
+      dg_free(c);
+      return DG_ECUDA;
+    }
+    for (int i = 0; i < n_inst; ++i) {
+      if (dg::prepare_reacting(inst[i].N, mech.ns) != cudaSuccess) {
+        cudaGetLastError();
+        dg_free(c);
+        return DG_ECUDA;
+      }
+    }
+    *out = c;
+    return DG_OK;
   }
   for (int i = 0; i < n_inst; ++i) {
     cudaError_t e = dg::prepare_euler_stage(inst[i].dim, inst[i].N, phys->volume == DG_VOL_EC,
@@ -532,6 +685,7 @@ dg_status dg_rhs_vjp(dg_ctx* c, const double* U, const double* lam, double* Ubar
   if (!c) return DG_EINVAL;
   if (!U || !lam || !Ubar) return fail(c, DG_EINVAL, "null pointer");
   if (Ubar == U || Ubar == lam) return fail(c, DG_EINVAL, "Ubar must not alias U or lam");
+  if (c->ns) return fail(c, DG_EUNSUPPORTED, "the adjoint exists for the Euler equations");
   dg_status st = ensure_adjoint(c);
   if (st) return st;
   cudaError_t e = cudaMemsetAsync(c->gacc, 0, sizeof(double), c->stream);
@@ -544,6 +698,7 @@ dg_status dg_rk_step_vjp(dg_ctx* c, const double* Un, double dt, double* lam, do
   if (!c) return DG_EINVAL;
   if (!Un || !lam) return fail(c, DG_EINVAL, "null pointer");
   if (Un == lam) return fail(c, DG_EINVAL, "lam must not alias Un");
+  if (c->ns) return fail(c, DG_EUNSUPPORTED, "the adjoint exists for the Euler equations");
   if (!std::isfinite(dt)) return fail(c, DG_EINVAL, "dt must be finite");
   dg_status st = ensure_adjoint(c);
   if (st) return st;
@@ -565,6 +720,8 @@ dg_status dg_set_launch(dg_ctx* c, int mode, int group_scale, int ctas_per_sm, i
   if (!c) return DG_EINVAL;
   if (mode != DG_LAUNCH_PER_INSTANCE && mode != DG_LAUNCH_BATCHED)
     return fail(c, DG_EINVAL, "mode must be DG_LAUNCH_PER_INSTANCE or DG_LAUNCH_BATCHED");
+  if (c->ns && mode == DG_LAUNCH_BATCHED)
+    return fail(c, DG_EUNSUPPORTED, "the batched launch exists for the Euler equations");
   if (group_scale != 1 && !(group_scale == 2 && c->dim == 2))
     return fail(c, DG_EINVAL, "group_scale must be 1 (or 2 in 2D)");
   if (ctas_per_sm < 0 || (order != 0 && order != 1))
@@ -584,6 +741,7 @@ dg_status dg_set_launch(dg_ctx* c, int mode, int group_scale, int ctas_per_sm, i
 dg_status dg_autotune(dg_ctx* c, double dt, int n_reps, int* config_out, double* ms_out) {
   if (!c) return DG_EINVAL;
   if (!std::isfinite(dt) || n_reps < 1 || !config_out) return fail(c, DG_EINVAL, "bad autotune arguments");
+  if (c->ns) return fail(c, DG_EUNSUPPORTED, "the autotuner exists for the Euler equations");
   const size_t bytes = sizeof(double) * (size_t)c->nv * c->n_nodes_total;
   double* save = nullptr;
   if (cudaMalloc(&save, bytes) != cudaSuccess) { cudaGetLastError(); return fail(c, DG_ENOMEM, "autotune copy"); }
@@ -634,6 +792,36 @@ dg_status dg_max_dt(dg_ctx* c, double cfl, double* dt_out) {
   if (!c) return DG_EINVAL;
   if (!dt_out || !(cfl > 0.0)) return fail(c, DG_EINVAL, "bad cfl or output pointer");
   double best = INFINITY;
+  if (c->ns) {
+    // convective bound with the frozen mixture sound speed and the diffusive bound
+    // (Eq. dt_para): nu_max = mu * max(1/rho) / min(1, Pr)
+    for (size_t i = 0; i < c->inst.size(); ++i) {
+      const dg_mesh_desc& m = c->inst[i];
+      cudaError_t e = cudaMemsetAsync(c->lam, 0, 2 * sizeof(unsigned long long), c->stream);
+      if (e == cudaSuccess)
+        e = dg::launch_max_speed_mix(c->n_species, c->buf[c->cur], c->n_nodes_total, c->offs[i],
+                                     n_elem_of(m) * n_p_of(m), c->d_mech, c->lam, c->stream);
+      unsigned long long bits[2] = {0, 0};
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(bits, c->lam, sizeof(bits), cudaMemcpyDeviceToHost, c->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+      if (e != cudaSuccess) return cuda_fail(c, e, "dg_max_dt");
+      double lam, irho;
+      std::memcpy(&lam, &bits[0], sizeof(lam));
+      std::memcpy(&irho, &bits[1], sizeof(irho));
+      if (!(lam > 0.0) || !std::isfinite(lam) || !std::isfinite(irho))
+        return fail(c, DG_ENONFINITE, "no finite signal speed");
+      double dxmin = INFINITY;
+      for (int l = 0; l < m.dim; ++l) dxmin = std::fmin(dxmin, (m.hi[l] - m.lo[l]) / m.nel[l]);
+      const double n2 = (2.0 * m.N + 1.0) * (2.0 * m.N + 1.0);
+      const double nu = c->phys.mu * irho / std::fmin(1.0, c->phys.prandtl);
+      double dt = cfl * dxmin / ((2 * m.N + 1) * lam);
+      if (nu > 0.0) dt = std::fmin(dt, cfl * dxmin * dxmin / (n2 * nu));
+      best = std::fmin(best, dt);
+    }
+    *dt_out = best;
+    return DG_OK;
+  }
   for (size_t i = 0; i < c->inst.size(); ++i) {
     const dg_mesh_desc& m = c->inst[i];
     cudaError_t e = cudaMemsetAsync(c->lam, 0, sizeof(unsigned long long), c->stream);
@@ -678,6 +866,7 @@ dg_status dg_gll(int N, double* x, double* w, double* D) {
 dg_status dg_two_point_flux(dg_ctx* c, int kind, int l, int n, const double* uL,
                             const double* uR, double* F) {
   if (!c) return DG_EINVAL;
+  if (c->ns) return fail(c, DG_EUNSUPPORTED, "two-point fluxes exist for the Euler equations");
   if (kind < -1 || kind > DG_SURF_EC || l < 0 || l >= c->dim || n < 0 || !uL || !uR || !F)
     return fail(c, DG_EINVAL, "bad two-point flux arguments");
   cudaError_t e = dg::launch_two_point(c->dim, c->phys.precision == DG_FP32_MIXED, kind, l, n,
@@ -702,6 +891,8 @@ void dg_free(dg_ctx* c) {
     if (c->adj[k]) cudaFree(c->adj[k]);
   if (c->gpart) cudaFree(c->gpart);
   if (c->gacc) cudaFree(c->gacc);
+  if (c->d_mech) cudaFree(c->d_mech);
+  if (c->fb) cudaFree(c->fb);
   delete c;
 }
 

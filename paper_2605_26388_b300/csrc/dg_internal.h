@@ -119,4 +119,61 @@ cudaError_t prepare_euler_stage_batched(int dim, int ec, int fp32, int group_sca
 // Whether (dim, N) has compiled kernels.
 bool have_kernels(int dim, int N);
 
+// ---------------------------------------------------------------------------------------
+// Reacting Navier-Stokes (3D, FP64): species data and reactions as the kernels read them.
+// ---------------------------------------------------------------------------------------
+constexpr int kMaxSpecies = 8;
+constexpr int kMaxReactions = 32;
+constexpr int kMaxReactingN = 4;
+
+struct RxnDev {
+  double lnA, b, Ta;
+  double kc[5];                // ln K_c = kc0 / Z + kc1 + kc2 ln Z + kc3 Z + kc4 Z^2
+  double coef[kMaxSpecies];    // W_s * 1e6 * (nu''_s - nu'_s): mol/(cm^3 s) -> kg/(m^3 s)
+  int f[3], bk[3];             // species of the forward / backward concentration products;
+  int pad[2];                  //   index n_species stands for the factor 1
+};
+
+struct MechDev {
+  int ns, nr;
+  int pad[2];
+  double R[kMaxSpecies], cv[kMaxSpecies], h0[kMaxSpecies];
+  double scale[kMaxSpecies];   // 1e-6 / W_s: rho_s (kg/m^3) -> [X_s] (mol/cm^3)
+  RxnDev rx[kMaxReactions];
+};
+
+// Arguments of the two reacting launches of one stage over one instance.
+struct ReactArgs {
+  const double* U;     // input state (or the residual's input)
+  const double* Un;    // U^n (stages 2 and 3)
+  double* out;         // stage output (mode 1) or L(U) (mode 0)
+  unsigned* err;       // device error word
+  double* fb;          // face buffer of this instance: [elem][face][4][(N+1)^2]
+  const MechDev* mech; // device copy of the mechanism
+  long long stride;    // per-variable stride of the SoA state
+  long long base;      // node offset of the instance
+  int nel[3];
+  int n_elem;
+  int mode;            // 0: out = L(U); 1: stage update
+  int need_un;
+  double s[3];         // 2 / dx_l
+  double lift;         // 1 / w_0 = 1 / w_N
+  double ca, cb, cbdt;
+  double mu, kfac;     // viscosity; mu / Pr (conductivity = kfac * c_p)
+  double ln1e4;        // ln 10^4 (for ln Z = ln 10^4 - ln T)
+  double D[(kMaxReactingN + 1) * (kMaxReactingN + 1)];
+};
+
+// Whether the reacting kernels exist for degree N and n_species.
+bool have_reacting(int N, int ns);
+// Kernel attributes (dynamic shared memory); call before the first launch, outside capture.
+cudaError_t prepare_reacting(int N, int ns);
+// One stage (or residual) over one instance: the BR1 face pass, then the fused stage.
+cudaError_t launch_reacting(int N, int ns, const ReactArgs& a, cudaStream_t s);
+// Largest |u| + a (frozen mixture sound speed) and largest 1/rho over one instance,
+// atomically max-ed into out2[0] and out2[1] (bit patterns of non-negative doubles).
+cudaError_t launch_max_speed_mix(int ns, const double* U, long long stride, long long base,
+                                 long long n_nodes, const MechDev* mech,
+                                 unsigned long long* out2, cudaStream_t s);
+
 }  // namespace dg

@@ -19,7 +19,8 @@ LIB_PATH = os.path.join(HERE, "_lib", "libdgsem.so")
 DG_OK, DG_EINVAL, DG_ENOMEM, DG_ECUDA, DG_ENONFINITE, DG_EPOSITIVITY, DG_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
 DG_ETOOLARGE = -7
 NOALLOC_MAX_INSTANCES = 4096
-DG_EULER = 0
+DG_EULER, DG_NAVIER_STOKES, DG_NS_REACTING = 0, 1, 2
+MAX_SPECIES, MAX_REACTIONS = 8, 32
 VOL_STRONG, VOL_WEAK, VOL_EC = 0, 1, 2
 SURF_RUSANOV, SURF_HLLC, SURF_HLL, SURF_EC = 0, 1, 2, 3
 FP64, FP32_MIXED = 0, 1
@@ -47,10 +48,41 @@ class MeshDesc(C.Structure):
                 ("hi", C.c_double * 3), ("periodic", C.c_int * 3)]
 
 
+class Mechanism(C.Structure):
+    """dg_mechanism: species data and reactions of a reacting mixture."""
+    _fields_ = [("n_species", C.c_int), ("n_reactions", C.c_int),
+                ("W", C.c_double * MAX_SPECIES), ("R", C.c_double * MAX_SPECIES),
+                ("cv", C.c_double * MAX_SPECIES), ("h0", C.c_double * MAX_SPECIES),
+                ("lnA", C.c_double * MAX_REACTIONS), ("b", C.c_double * MAX_REACTIONS),
+                ("Ta", C.c_double * MAX_REACTIONS), ("kc", (C.c_double * 5) * MAX_REACTIONS),
+                ("nu_f", (C.c_int * MAX_SPECIES) * MAX_REACTIONS),
+                ("nu_b", (C.c_int * MAX_SPECIES) * MAX_REACTIONS)]
+
+    @classmethod
+    def from_dict(cls, m: dict) -> "Mechanism":
+        """Pack a mechanism given as a dict of plain numbers (keys n_species, n_reactions, W, R,
+        cv, h0 per species; lnA, b, Ta, kc (5 each), nu_f, nu_b per reaction)."""
+        c = cls()
+        ns, nr = int(m["n_species"]), int(m["n_reactions"])
+        if not (1 <= ns <= MAX_SPECIES and 0 <= nr <= MAX_REACTIONS):
+            raise ValueError("species or reaction count out of range")
+        c.n_species, c.n_reactions = ns, nr
+        for s in range(ns):
+            c.W[s], c.R[s], c.cv[s], c.h0[s] = m["W"][s], m["R"][s], m["cv"][s], m["h0"][s]
+        for r in range(nr):
+            c.lnA[r], c.b[r], c.Ta[r] = m["lnA"][r], m["b"][r], m["Ta"][r]
+            for k in range(5):
+                c.kc[r][k] = m["kc"][r][k]
+            for s in range(ns):
+                c.nu_f[r][s], c.nu_b[r][s] = int(m["nu_f"][r][s]), int(m["nu_b"][r][s])
+        return c
+
+
 class Physics(C.Structure):
     _fields_ = [("equations", C.c_int), ("volume", C.c_int), ("surface", C.c_int),
                 ("precision", C.c_int), ("gamma", C.c_double), ("rho_floor", C.c_double),
-                ("p_floor", C.c_double), ("p_ref", C.c_double)]
+                ("p_floor", C.c_double), ("p_ref", C.c_double), ("mu", C.c_double),
+                ("prandtl", C.c_double), ("chem", C.POINTER(Mechanism))]
 
 
 _lib = None
@@ -137,14 +169,19 @@ class Solver:
     SoA layout U[var, node] (node = instance offset + elem * n_p + local node)."""
 
     def __init__(self, meshes, volume=VOL_STRONG, surface=SURF_RUSANOV, precision=FP64,
-                 gamma=1.4, rho_floor=0.0, p_floor=0.0, p_ref=0.0, stream=None):
+                 gamma=1.4, rho_floor=0.0, p_floor=0.0, p_ref=0.0, stream=None,
+                 equations=DG_EULER, mu=0.0, prandtl=0.72, mechanism=None):
         import torch
         if isinstance(meshes, Mesh):
             meshes = [meshes]
         self.meshes = list(meshes)
         self.gamma = gamma
         arr = (MeshDesc * len(self.meshes))(*[m.c() for m in self.meshes])
-        phys = Physics(DG_EULER, volume, surface, precision, gamma, rho_floor, p_floor, p_ref)
+        phys = Physics(equations, volume, surface, precision, gamma, rho_floor, p_floor, p_ref,
+                       mu, prandtl, None)
+        if mechanism is not None:
+            mech = mechanism if isinstance(mechanism, Mechanism) else Mechanism.from_dict(mechanism)
+            phys.chem = C.pointer(mech)  # copied by dg_init_mesh
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream

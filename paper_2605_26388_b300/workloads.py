@@ -126,6 +126,33 @@ def fourier_field(seed: int, X: np.ndarray, lo, hi, kmax: int) -> np.ndarray:
     return f / np.max(np.abs(f))
 
 
+def fourier_field_3d_tensor(seed: int, nel, xi: np.ndarray, lo, hi, kmax: int) -> np.ndarray:
+    """fourier_field on a 3D Cartesian DGSEM mesh, returned as (n_elem, n_nodes): the same
+    sum (same seeded amplitudes and phases, same wave vectors), evaluated as a separable
+    product over the three axes, which is what makes full-size meshes affordable."""
+    rng = range(-kmax, kmax + 1)
+    ks = [(a, b, c) for a in rng for b in rng for c in rng if 0 < a * a + b * b + c * c <= kmax * kmax]
+    r = uniform(seed, 2 * len(ks))
+    nk = 2 * kmax + 1
+    Ck = np.zeros((nk, nk, nk), dtype=np.complex128)
+    for n, k in enumerate(ks):
+        amp = (2.0 * r[2 * n] - 1.0) / (1.0 + sum(kk * kk for kk in k))
+        Ck[k[0] + kmax, k[1] + kmax, k[2] + kmax] = amp * np.exp(1j * 2.0 * math.pi * r[2 * n + 1])
+    n1 = len(xi)
+    E = []
+    for l in range(3):
+        h = (hi[l] - lo[l]) / nel[l]
+        x = (lo[l] + h * np.arange(nel[l])[:, None] + 0.5 * h * (np.asarray(xi)[None, :] + 1.0)).reshape(-1)
+        kk = np.arange(-kmax, kmax + 1)[:, None]
+        E.append(np.exp(1j * 2.0 * math.pi * kk * (x[None, :] - lo[l]) / (hi[l] - lo[l])))
+    T1 = np.einsum("abc,ax->bcx", Ck, E[0])
+    T2 = np.einsum("bcx,by->cyx", T1, E[1])
+    F = np.einsum("cyx,cz->zyx", T2, E[2]).real
+    F = F.reshape(nel[2], n1, nel[1], n1, nel[0], n1).transpose(0, 2, 4, 1, 3, 5)
+    F = F.reshape(nel[0] * nel[1] * nel[2], n1 ** 3)
+    return F / np.max(np.abs(F))
+
+
 def acoustic_2d(nel: int, xi: np.ndarray, seed: int = 3, amp: float = 0.05, gamma: float = 1.4,
                 lo=(0.0, 0.0), hi=(1.0, 1.0)) -> np.ndarray:
     """Smooth seeded acoustic perturbation at rest: rho = 1 + amp psi_rho, p = 1 + amp psi_p,
@@ -264,7 +291,7 @@ def reacting_tgv_3d(nel: int, xi: np.ndarray, mech: dict, seed: int = 2, U0: flo
         hi = (2 * math.pi,) * 3
     X = node_coordinates(3, (nel, nel, nel), lo, hi, xi)
     x, y, z = X
-    T = 5000.0 + 3000.0 * fourier_field(seed, X, lo, hi, 3)
+    T = 5000.0 + 3000.0 * fourier_field_3d_tensor(seed, (nel, nel, nel), xi, lo, hi, 3)
     Y = np.array([0.767, 0.233, 1e-10, 1e-10, 1e-10])
     Y = Y / Y.sum()
     Rmix = float(np.dot(Y, mech["R"]))
@@ -273,3 +300,17 @@ def reacting_tgv_3d(nel: int, xi: np.ndarray, mech: dict, seed: int = 2, U0: flo
     v = -U0 * np.cos(x) * np.sin(y) * np.cos(z)
     w = np.zeros_like(x)
     return reacting_conserved([rho * Y[s] for s in range(5)], [u, v, w], T, mech)
+
+
+AIR_Y = (0.767, 0.233, 1e-10, 1e-10, 1e-10)
+
+
+def reacting_tgv_viscosity(mech: dict, U0: float = 100.0, p0: float = 101325.0, T0: float = 5000.0,
+                           L: float = 1.0, Re: float = 1600.0) -> float:
+    """Constant viscosity of the reacting workload: mu = rho0 U0 L / Re with rho0 the density
+    of the air composition at p0 and the mean temperature T0 (Re = 1600, L = 1 on the
+    [0, 2 pi]^3 box)."""
+    Y = np.array(AIR_Y)
+    Y = Y / Y.sum()
+    rho0 = p0 / (float(np.dot(Y, mech["R"])) * T0)
+    return rho0 * U0 * L / Re
