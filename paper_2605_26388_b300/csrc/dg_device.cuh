@@ -189,30 +189,36 @@ __device__ __forceinline__ void point_flux(const R* u, const Prim<DIM, R>& q, R*
 // where the Taylor series of 1/F is 1 - u/3 - 4u^2/45 - 44u^3/945 - c4 u^4 (c4 =
 // 0.0301940...), used for small u (the Ismail-Roe idea of a series near a = b, here
 // expanded for the reciprocal so that no division is needed); otherwise a^ln =
-// (a-b)/ln(a/b).
+// (a-b)/(ln a - ln b) with the logarithms la, lb computed once per node.  FP32 evaluates
+// both forms and selects (no divergent branch, one fast reciprocal); FP64 branches (the
+// division is expensive there and the branch is uniform in smooth regions).
 template <class R>
-__device__ __forceinline__ R log_mean_from(R a, R b, R s, R f) {
+__device__ __forceinline__ R log_mean_from(R a, R b, R la, R lb, R s, R f) {
   const R u = f * f;
-  if (u < R(Ar<R>::kLogMeanSeries)) {
-    const R G = R(1) - u * (R(1.0 / 3.0) + u * (R(4.0 / 45.0) + u * (R(44.0 / 945.0) +
-                                                                      u * R(0.030194003527336861))));
-    return R(0.5) * s * G;
+  const R G = R(1) - u * (R(1.0 / 3.0) + u * (R(4.0 / 45.0) + u * (R(44.0 / 945.0) +
+                                                                    u * R(0.030194003527336861))));
+  if constexpr (sizeof(R) == 4) {
+    const R lg = (a - b) * Ar<R>::rcp(la - lb);
+    return u < R(Ar<R>::kLogMeanSeries) ? R(0.5) * s * G : lg;
+  } else {
+    if (u < R(Ar<R>::kLogMeanSeries)) return R(0.5) * s * G;
+    return Ar<R>::div(a - b, la - lb);
   }
-  return Ar<R>::div(a - b, Ar<R>::log(Ar<R>::div(a, b)));
 }
 
 // Ranocha's EC two-point flux in direction L (App. A; energy component in the published
 // consistent form f_E = f_rho (1/((gamma-1) beta^ln) + u_L.u_R/2) + (p_L u_R + p_R u_L)/2,
 // beta = rho/p).  Inputs are per-node rho, v, pd and beta = rho/p.
 template <int DIM, int L, class R>
-__device__ __forceinline__ void ec_flux_prims(R rL, const R* vL, R pdL, R bL, R rR, const R* vR,
-                                              R pdR, R bR, R igm1, R p_ref, R* F) {
+__device__ __forceinline__ void ec_flux_prims(R rL, const R* vL, R pdL, R bL, R lrL, R lbL, R rR,
+                                              const R* vR, R pdR, R bR, R lrR, R lbR, R igm1,
+                                              R p_ref, R* F) {
   const R sr = rL + rR, sb = bL + bR;
   const R inv = Ar<R>::rcp(sr * sb);  // one reciprocal serves both f's
   const R fr = (rL - rR) * (sb * inv);
   const R fb = (bL - bR) * (sr * inv);
-  const R rho_ln = log_mean_from(rL, rR, sr, fr);
-  const R beta_ln = log_mean_from(bL, bR, sb, fb);
+  const R rho_ln = log_mean_from(rL, rR, lrL, lrR, sr, fr);
+  const R beta_ln = log_mean_from(bL, bR, lbL, lbR, sb, fb);
   R vavg[DIM];
   R vLvR = R(0);
 #pragma unroll
@@ -232,8 +238,9 @@ __device__ __forceinline__ void ec_flux_prims(R rL, const R* vL, R pdL, R bL, R 
 template <int DIM, int L, class R>
 __device__ __forceinline__ void ec_flux(const Prim<DIM, R>& a, const Prim<DIM, R>& b, R igm1,
                                         R p_ref, R* F) {
-  ec_flux_prims<DIM, L>(a.rho, a.v, a.pd, a.rho * Ar<R>::rcp(a.p), b.rho, b.v, b.pd,
-                        b.rho * Ar<R>::rcp(b.p), igm1, p_ref, F);
+  const R ba = a.rho * Ar<R>::rcp(a.p), bb = b.rho * Ar<R>::rcp(b.p);
+  ec_flux_prims<DIM, L>(a.rho, a.v, a.pd, ba, Ar<R>::log(a.rho), Ar<R>::log(ba), b.rho, b.v, b.pd,
+                        bb, Ar<R>::log(b.rho), Ar<R>::log(bb), igm1, p_ref, F);
 }
 
 // Local Lax-Friedrichs (Rusanov): F* = (F_L + F_R)/2 - lambda/2 (U_R - U_L),

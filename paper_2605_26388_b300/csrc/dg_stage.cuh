@@ -86,9 +86,9 @@ struct EulerStage {
   // (i, i+o mod N1) for o = 1..NO, the last offset (o = N1/2 when N1 is even) only for
   // i < N1/2, so that every unordered pair is evaluated exactly once.
   static constexpr int NO = N1 / 2;
-  // per-node staged quantities: EC -- rho, v_1..v_DIM, pd, beta = rho/p; strong/weak -- the
-  // DIM point fluxes (NV each) and pd
-  static constexpr int NQ = EC ? (DIM + 3) : (DIM * NV + 1);
+  // per-node staged quantities: EC -- rho, v_1..v_DIM, pd, beta = rho/p, ln rho, ln beta;
+  // strong/weak -- the DIM point fluxes (NV each) and pd
+  static constexpr int NQ = EC ? (DIM + 5) : (DIM * NV + 1);
   static constexpr int PD = EC ? (DIM + 1) : (DIM * NV);
   static constexpr int NXN = EC ? DIM * NO : 0;            // pair slots per node
   // FP64 staging buffer (two of them): own U [EPB][NV][NP], U^n [EPB][NV][NP],
@@ -212,6 +212,7 @@ struct EulerStage {
 #pragma unroll
     for (int d = 0; d < DIM; ++d) vi[d] = Q[(1 + d) * NP + nd];
     const R ri = Q[nd], pdi = Q[PD * NP + nd], bi = Q[(DIM + 2) * NP + nd];
+    const R lri = Q[(DIM + 3) * NP + nd], lbi = Q[(DIM + 4) * NP + nd];
     R* X = sm + OFF_X + ((el * DIM + L) * NO) * NV * NP + nd;
 #pragma unroll
     for (int o = 1; o <= NO; ++o) {
@@ -222,7 +223,8 @@ struct EulerStage {
 #pragma unroll
       for (int d = 0; d < DIM; ++d) vj[d] = Q[(1 + d) * NP + nj];
       R F[NV];
-      ec_flux_prims<DIM, L>(ri, vi, pdi, bi, Q[nj], vj, Q[PD * NP + nj], Q[(DIM + 2) * NP + nj],
+      ec_flux_prims<DIM, L>(ri, vi, pdi, bi, lri, lbi, Q[nj], vj, Q[PD * NP + nj],
+                            Q[(DIM + 2) * NP + nj], Q[(DIM + 3) * NP + nj], Q[(DIM + 4) * NP + nj],
                             igm1, p_ref, F);
       const R c = s * Dv[i * N1 + j];
 #pragma unroll
@@ -405,7 +407,10 @@ struct EulerStage {
         Q[nd] = q.rho;
 #pragma unroll
         for (int d = 0; d < DIM; ++d) Q[(1 + d) * NP + nd] = q.v[d];
-        Q[(DIM + 2) * NP + nd] = q.rho * Ar<R>::rcp(q.p);
+        const R beta = q.rho * Ar<R>::rcp(q.p);
+        Q[(DIM + 2) * NP + nd] = beta;
+        Q[(DIM + 3) * NP + nd] = Ar<R>::log(q.rho);
+        Q[(DIM + 4) * NP + nd] = Ar<R>::log(beta);
       } else {
         R F[NV];
         point_flux<DIM, 0>(u, q, F);
