@@ -286,7 +286,12 @@ dg_status run_stage_ns(dg_ctx* c, const double* U, const double* Un, double* out
   a.cbdt = cb * dt;
   a.mu = c->phys.mu;
   a.kfac = c->phys.mu / c->phys.prandtl;
+  a.p_ref = c->phys.p_ref;
   a.ln1e4 = std::log(1.0e4);
+  a.muf = (float)a.mu;
+  a.kfacf = (float)a.kfac;
+  a.p_reff = (float)a.p_ref;
+  const int fp32 = c->phys.precision == DG_FP32_MIXED;
   for (size_t i = 0; i < c->inst.size(); ++i) {
     const dg_mesh_desc& m = c->inst[i];
     a.base = c->offs[i];
@@ -294,12 +299,14 @@ dg_status run_stage_ns(dg_ctx* c, const double* U, const double* Un, double* out
     for (int l = 0; l < 3; ++l) {
       a.nel[l] = m.nel[l];
       a.s[l] = 2.0 / ((m.hi[l] - m.lo[l]) / m.nel[l]);
+      a.sf[l] = (float)a.s[l];
     }
     a.n_elem = (int)n_elem_of(m);
     double x[dg::kMaxN + 1], w[dg::kMaxN + 1];
     gll_table(m.N, x, w, a.D);
     a.lift = 1.0 / w[0];
-    cudaError_t e = dg::launch_reacting(m.N, c->n_species, a, s);
+    a.liftf = (float)a.lift;
+    cudaError_t e = dg::launch_reacting(m.N, c->n_species, fp32, a, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "Navier-Stokes stage launch");
   }
   return DG_OK;
@@ -497,7 +504,7 @@ dg_status dg_init_mesh(const dg_mesh_desc* inst, int n_inst, const dg_physics* p
     for (int i = 0; i < n_inst; ++i)
       if (!dg::have_reacting(inst[i].N, mech.ns)) return DG_EUNSUPPORTED;
     if (phys->volume != DG_VOL_STRONG || phys->surface != DG_SURF_RUSANOV ||
-        phys->precision != DG_FP64 || phys->rho_floor > 0.0 || phys->p_floor > 0.0)
+        phys->rho_floor > 0.0 || phys->p_floor > 0.0)
       return DG_EUNSUPPORTED;
   }
 
@@ -554,7 +561,7 @@ dg_status dg_init_mesh(const dg_mesh_desc* inst, int n_inst, const dg_physics* p
       return DG_ECUDA;
     }
     for (int i = 0; i < n_inst; ++i) {
-      if (dg::prepare_reacting(inst[i].N, mech.ns) != cudaSuccess) {
+      if (dg::prepare_reacting(inst[i].N, mech.ns, phys->precision == DG_FP32_MIXED) != cudaSuccess) {
         cudaGetLastError();
         dg_free(c);
         return DG_ECUDA;

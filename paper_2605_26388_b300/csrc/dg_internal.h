@@ -120,7 +120,7 @@ cudaError_t prepare_euler_stage_batched(int dim, int ec, int fp32, int group_sca
 bool have_kernels(int dim, int N);
 
 // ---------------------------------------------------------------------------------------
-// Reacting Navier-Stokes (3D, FP64): species data and reactions as the kernels read them.
+// Reacting Navier-Stokes (3D): species data and reactions as the kernels read them.
 // ---------------------------------------------------------------------------------------
 constexpr int kMaxSpecies = 8;
 constexpr int kMaxReactions = 32;
@@ -148,7 +148,7 @@ struct ReactArgs {
   const double* Un;    // U^n (stages 2 and 3)
   double* out;         // stage output (mode 1) or L(U) (mode 0)
   unsigned* err;       // device error word
-  double* fb;          // face buffer of this instance: [elem][face][4][(N+1)^2]
+  void* fb;            // face buffer of this instance (flux type): [elem][face][4][(N+1)^2]
   const MechDev* mech; // device copy of the mechanism
   long long stride;    // per-variable stride of the SoA state
   long long base;      // node offset of the instance
@@ -160,16 +160,19 @@ struct ReactArgs {
   double lift;         // 1 / w_0 = 1 / w_N
   double ca, cb, cbdt;
   double mu, kfac;     // viscosity; mu / Pr (conductivity = kfac * c_p)
+  double p_ref;        // constant subtracted from the pressure in the momentum flux
   double ln1e4;        // ln 10^4 (for ln Z = ln 10^4 - ln T)
+  float sf[3], liftf, muf, kfacf, p_reff;  // the same scalars for the FP32 flux arithmetic
   double D[(kMaxReactingN + 1) * (kMaxReactingN + 1)];
 };
 
 // Whether the reacting kernels exist for degree N and n_species.
 bool have_reacting(int N, int ns);
 // Kernel attributes (dynamic shared memory); call before the first launch, outside capture.
-cudaError_t prepare_reacting(int N, int ns);
-// One stage (or residual) over one instance: the BR1 face pass, then the fused stage.
-cudaError_t launch_reacting(int N, int ns, const ReactArgs& a, cudaStream_t s);
+cudaError_t prepare_reacting(int N, int ns, int fp32);
+// One stage (or residual) over one instance: the BR1 face pass, then the fused stage; fp32
+// selects FP32 flux arithmetic (mixture, source and update stay FP64).
+cudaError_t launch_reacting(int N, int ns, int fp32, const ReactArgs& a, cudaStream_t s);
 // Largest |u| + a (frozen mixture sound speed) and largest 1/rho over one instance,
 // atomically max-ed into out2[0] and out2[1] (bit patterns of non-negative doubles).
 cudaError_t launch_max_speed_mix(int ns, const double* U, long long stride, long long base,

@@ -1,5 +1,5 @@
 // dg_reacting.cu -- residual and SSP-RK3 stage of the single-temperature reacting
-// Navier-Stokes equations (Sec. 2 reacting system) on periodic 3D Cartesian meshes, FP64.
+// Navier-Stokes equations (Sec. 2 reacting system) on periodic 3D Cartesian meshes.
 //
 // One stage is two launches over the elements of an instance:
 //   1. k_br1_faces: BR1 gradients (Sec. 3.1.2, Eq. br1_avg) of W = (u, v, w, T) at every node
@@ -12,9 +12,15 @@
 //            + omega                                            (Sec. 3.1.3, App. C)
 //      with F* the Rusanov flux (frozen mixture sound speed), (F_v^l)* the BR1 average of the
 //      own and the neighbour's face value (the latter read from the face buffer), and the
-//      Arrhenius source evaluated in FP64; then the Shu-Osher stage update (App. B).
+//      Arrhenius source; then the Shu-Osher stage update (App. B).
 // The gradient is recomputed in launch 2 from the same inputs by the same code, so the
 // neighbour's face value and the own one come from identical arithmetic.
+//
+// Precision: the mixture state of every node (T, p, sound speed, c_p from the FP64 conserved
+// variables), the Arrhenius source and the stage update are FP64 in both modes; gradients,
+// viscous and inviscid fluxes, the Rusanov flux, the contractions and the lifts run in the
+// flux type R (double, or float in the FP32-mixed mode).  The momentum flux carries
+// p - p_ref (a constant shift that leaves the discrete operator unchanged, as for Euler).
 //
 // Threads: one thread per node, EPB = 128 / (N+1)^3 elements per 128-thread CTA; face work
 // (6 (N+1)^2 face nodes per element) is spread over all threads of the CTA.
@@ -27,32 +33,34 @@ namespace dg {
 namespace {
 
 constexpr int kRT = 128;
+constexpr int NPR = 6;  // staged primitives per node: u, v, w, T, p - p_ref, a
 
-template <int N, int NS>
+template <int N, int NS, class R>
 struct RG {
   static constexpr int N1 = N + 1, NP = N1 * N1 * N1, NFN = N1 * N1, NV = NS + 4;
   static constexpr int EPB = kRT / NP;
   static constexpr int NFJ = 6 * NFN;  // face nodes of one element
   static constexpr int NSL = NS + 1;   // concentration slots (last one holds 1.0)
-  // stage kernel shared memory per element (doubles)
+  // stage kernel, per element (R)
   static constexpr int E_US = 0;                        // U            [NV][NP]
   static constexpr int E_UT = E_US + NV * NP;           // nbr U traces [6][NV][NFN] -> lifts
-  static constexpr int E_W = E_UT + 6 * NV * NFN;       // W            [4][NP]
-  static constexpr int E_WT = E_W + 4 * NP;             // nbr W traces [6][4][NFN]
-  static constexpr int E_FT = E_WT + 24 * NFN;          // nbr F_v      [6][4][NFN]
+  static constexpr int E_P = E_UT + 6 * NV * NFN;       // primitives   [NPR][NP]
+  static constexpr int E_PT = E_P + NPR * NP;           // nbr prims    [6][NPR][NFN]
+  static constexpr int E_FT = E_PT + 6 * NPR * NFN;     // nbr F_v      [6][4][NFN]
   static constexpr int E_FO = E_FT + 24 * NFN;          // own F_v      [6][4][NFN]
   static constexpr int E_H = E_FO + 24 * NFN;           // F^l - F_v^l  [NV][NP]
   static constexpr int E_SIZE = E_H + NV * NP;
-  // per CTA: D, species table, concentration slots
-  static constexpr int C_D = 0;
-  static constexpr int C_SP = C_D + N1 * N1;            // R, cv, h0, scale [4][NS]
+  // stage kernel, per CTA: species table and concentration slots (double), D (R)
+  static constexpr int C_SP = 0;                        // R, cv, h0, scale [4][NS]
   static constexpr int C_X = C_SP + 4 * NS;             // [NSL][kRT]
-  static constexpr int C_SIZE = C_X + NSL * kRT;
-  static constexpr size_t stage_smem() { return sizeof(double) * (size_t)(C_SIZE + EPB * E_SIZE); }
-  // gradient kernel: W [4][NP] and W traces [6][4][NFN] per element
-  static constexpr int G_W = 0, G_WT = 4 * NP, G_SIZE = 4 * NP + 24 * NFN;
+  static constexpr int C_DBL = C_X + NSL * kRT;
+  static constexpr size_t stage_smem() {
+    return sizeof(double) * (size_t)C_DBL + sizeof(R) * (size_t)(N1 * N1 + EPB * E_SIZE);
+  }
+  // gradient kernel, per element (R): primitives and trace primitives
+  static constexpr int G_P = 0, G_PT = NPR * NP, G_SIZE = NPR * NP + 6 * NPR * NFN;
   static constexpr size_t grad_smem() {
-    return sizeof(double) * (size_t)(N1 * N1 + 3 * NS + EPB * G_SIZE);
+    return sizeof(double) * (size_t)(3 * NS) + sizeof(R) * (size_t)(N1 * N1 + EPB * G_SIZE);
   }
 };
 
@@ -70,11 +78,12 @@ __device__ __forceinline__ int neighbour(const int* nel, int e, int l, int dir) 
   return c[0] + nel[0] * (c[1] + nel[1] * c[2]);
 }
 
-__device__ __forceinline__ double pick3(int l, double a, double b, double c) {
+template <class T>
+__device__ __forceinline__ T pick3(int l, T a, T b, T c) {
   return l == 0 ? a : (l == 1 ? b : c);
 }
 
-// Mixture state of one node (calorically perfect species, single temperature):
+// Mixture state of one node, FP64 (calorically perfect species, single temperature):
 // T = (E - rho|u|^2/2 - sum rho_s h0_s) / sum rho_s cv_s, p = T sum rho_s R_s,
 // frozen sound speed a^2 = (1 + sum rho_s R_s / sum rho_s cv_s) p / rho, c_p of the mixture.
 struct Mx {
@@ -108,61 +117,86 @@ __device__ __forceinline__ Mx mixture(const double* u, const double* sp) {
   return m;
 }
 
-// Inviscid flux in direction l (runtime l allowed: no dynamic register indexing).
-template <int NS>
-__device__ __forceinline__ void inv_flux(int l, const double* u, const Mx& m, double* F) {
-  const double vl = pick3(l, m.v[0], m.v[1], m.v[2]);
+// Stage one node: conserved variables (R) and primitives (u, v, w, T, p - p_ref, a) in R;
+// returns the positivity flag (rho > 0 and T > 0, decided in FP64).
+template <int NS, class R>
+__device__ __forceinline__ unsigned stage_node(const double* u, const double* sp, double p_ref, R* us,
+                                               int us_stride, R* pr, int pr_stride, double* cpT_out) {
+  const Mx m = mixture<NS>(u, sp);
+  if (us) {
+#pragma unroll
+    for (int v = 0; v < NS + 4; ++v) us[v * us_stride] = Ar<R>::load(u[v]);
+  }
+  pr[0] = Ar<R>::load(m.v[0]);
+  pr[pr_stride] = Ar<R>::load(m.v[1]);
+  pr[2 * pr_stride] = Ar<R>::load(m.v[2]);
+  pr[3 * pr_stride] = Ar<R>::load(m.T);
+  pr[4 * pr_stride] = Ar<R>::load(m.p - p_ref);
+  pr[5 * pr_stride] = Ar<R>::load(m.a);
+  if (cpT_out) {
+    cpT_out[0] = m.cp;
+    cpT_out[1] = m.T;
+  }
+  return (m.rho > 0.0 && m.T > 0.0) ? 0u : 2u;
+}
+
+// Inviscid flux in direction l (runtime l: no dynamic register indexing); the momentum rows
+// carry pd = p - p_ref, the energy row (E + p) v_l with p = pd + p_ref.
+template <int NS, class R>
+__device__ __forceinline__ void inv_flux(int l, const R* u, R v0, R v1, R v2, R pd, R p_ref, R* F) {
+  const R vl = pick3(l, v0, v1, v2);
 #pragma unroll
   for (int s = 0; s < NS; ++s) F[s] = u[s] * vl;
-#pragma unroll
-  for (int d = 0; d < 3; ++d) F[NS + d] = fma(u[NS + d], vl, d == l ? m.p : 0.0);
-  F[NS + 3] = (u[NS + 3] + m.p) * vl;
+  F[NS + 0] = u[NS + 0] * vl + (l == 0 ? pd : R(0));
+  F[NS + 1] = u[NS + 1] * vl + (l == 1 ? pd : R(0));
+  F[NS + 2] = u[NS + 2] * vl + (l == 2 ? pd : R(0));
+  F[NS + 3] = (u[NS + 3] + (pd + p_ref)) * vl;
 }
 
 // Viscous flux in direction L (compile-time) from the gradient S[q][l] of (u, v, w, T):
 // tau_jL = mu (d_L u_j + d_j u_L) - (2/3) mu (div u) delta_jL, energy u . tau_L + k d_L T.
-template <int L>
-__device__ __forceinline__ void visc_flux(const double (&S)[4][3], const Mx& m, double mu, double kfac,
-                                          double* Fv) {
-  const double div = S[0][0] + S[1][1] + S[2][2];
-  double work = 0.0;
+template <int L, class R>
+__device__ __forceinline__ void visc_flux(const R (&S)[4][3], const R* v, R mu, R kcond, R* Fv) {
+  const R div = S[0][0] + S[1][1] + S[2][2];
+  R work = R(0);
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
-    double t = mu * (S[j][L] + S[L][j]);
-    if (j == L) t = fma(-2.0 / 3.0 * mu, div, t);
+    R t = mu * (S[j][L] + S[L][j]);
+    if (j == L) t = t - R(2.0 / 3.0) * mu * div;
     Fv[j] = t;
-    work = fma(m.v[j], t, work);
+    work = work + v[j] * t;
   }
-  Fv[3] = fma(kfac * m.cp, S[3][L], work);
+  Fv[3] = work + kcond * S[3][L];
 }
 
-// BR1 gradient of W at node q of element slot el (Eq. br1_avg): for each direction l,
+// BR1 gradient of W at node q (Eq. br1_avg): for each direction l,
 // (2/dx_l) [ sum_m D_{i_l m} W_m + (upper) (W^ - W_N)/w_N - (lower) (W^ - W_0)/w_0 ],
-// W^ = (W_own + W_nbr)/2.  W: [4][NP] of the element, Wt: [6][4][NFN] neighbour traces.
-template <int N>
-__device__ __forceinline__ void br1_gradient(int q, const double* W, const double* Wt, const double* D,
-                                             const double* s, double lift, double (&S)[4][3]) {
-  constexpr int N1 = N + 1, NFN = N1 * N1;
+// W^ = (W_own + W_nbr)/2.  W: rows c = 0..3 of the element's primitives (row stride NP),
+// Wt: the neighbours' face-trace primitives [6][NPR][NFN].
+template <int N, class R>
+__device__ __forceinline__ void br1_gradient(int q, const R* W, const R* Wt, const R* D, const R* s,
+                                             R lift, R (&S)[4][3]) {
+  constexpr int N1 = N + 1, NFN = N1 * N1, NP = N1 * NFN;
   const int ijk[3] = {q % N1, (q / N1) % N1, q / NFN};
   constexpr int stride_l[3] = {1, N1, NFN};
 #pragma unroll
   for (int l = 0; l < 3; ++l) {
     const int il = ijk[l];
     const int q0 = q - il * stride_l[l];
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    R acc[4] = {R(0), R(0), R(0), R(0)};
 #pragma unroll
     for (int m = 0; m < N1; ++m) {
-      const double d = D[il * N1 + m];
+      const R d = D[il * N1 + m];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) acc[c] = fma(d, W[c * (N1 * NFN) + q0 + m * stride_l[l]], acc[c]);
+      for (int c = 0; c < 4; ++c) acc[c] = acc[c] + d * W[c * NP + q0 + m * stride_l[l]];
     }
     if (il == N || il == 0) {
       const int side = il == N ? 1 : 0;
       const int jf = l == 0 ? ijk[1] + N1 * ijk[2] : (l == 1 ? ijk[0] + N1 * ijk[2] : ijk[0] + N1 * ijk[1]);
-      const double* wt = Wt + (2 * l + side) * 4 * NFN + jf;
-      const double h = side ? 0.5 * lift : -0.5 * lift;
+      const R* wt = Wt + (2 * l + side) * NPR * NFN + jf;
+      const R h = side ? R(0.5) * lift : R(-0.5) * lift;
 #pragma unroll
-      for (int c = 0; c < 4; ++c) acc[c] = fma(h, wt[c * NFN] - W[c * (N1 * NFN) + q], acc[c]);
+      for (int c = 0; c < 4; ++c) acc[c] = acc[c] + h * (wt[c * NFN] - W[c * NP + q]);
     }
 #pragma unroll
     for (int c = 0; c < 4; ++c) S[c][l] = s[l] * acc[c];
@@ -170,64 +204,67 @@ __device__ __forceinline__ void br1_gradient(int q, const double* W, const doubl
 }
 
 template <int NS>
-__device__ __forceinline__ void load_species(const MechDev* __restrict__ mech, double* sp) {
-  for (int t = threadIdx.x; t < 4 * NS; t += blockDim.x) {
+__device__ __forceinline__ void load_species(const MechDev* __restrict__ mech, double* sp, int n) {
+  for (int t = threadIdx.x; t < n * NS; t += blockDim.x) {
     const int k = t / NS, s = t % NS;
     const double* src = k == 0 ? mech->R : (k == 1 ? mech->cv : (k == 2 ? mech->h0 : mech->scale));
     sp[t] = src[s];
   }
 }
 
-// W = (u, v, w, T) and its error flags for one node state.
-template <int NS>
-__device__ __forceinline__ unsigned node_w(const double* u, const double* sp, double* w4, int stride,
-                                           Mx* out) {
-  const Mx m = mixture<NS>(u, sp);
-  w4[0] = m.v[0];
-  w4[stride] = m.v[1];
-  w4[2 * stride] = m.v[2];
-  w4[3 * stride] = m.T;
-  if (out) *out = m;
-  return (m.rho > 0.0 && m.T > 0.0) ? 0u : 2u;
-}
+// Launch scalars in the flux precision.
+template <class R>
+struct RS {
+  R s[3], lift, mu, kfac, p_ref;
+  __device__ __forceinline__ explicit RS(const ReactArgs& a) {
+    for (int l = 0; l < 3; ++l) s[l] = sel(a.s[l], a.sf[l]);
+    lift = sel(a.lift, a.liftf);
+    mu = sel(a.mu, a.muf);
+    kfac = sel(a.kfac, a.kfacf);
+    p_ref = sel(a.p_ref, a.p_reff);
+  }
+  static __device__ __forceinline__ R sel(double d, float f) {
+    if constexpr (sizeof(R) == 4) return f; else return d;
+  }
+};
 
-// Own W and neighbour W traces (and optionally U, U traces) of the CTA's elements.
-template <int N, int NS, bool KEEP_U>
-__device__ __forceinline__ unsigned load_element_w(const ReactArgs& a, int e0, double* smem_el, int esz,
-                                                   int off_w, int off_wt, int off_us, int off_ut,
-                                                   const double* sp) {
-  using G = RG<N, NS>;
+// Own primitives (and U in R) of the CTA's elements, and the neighbours' face traces.
+template <int N, int NS, class R, bool KEEP_U>
+__device__ __forceinline__ unsigned load_element(const ReactArgs& a, int e0, R* smem_el, int esz, int off_p,
+                                                 int off_pt, int off_us, int off_ut, const double* sp,
+                                                 double* u_own, double* cpT_own) {
+  using G = RG<N, NS, R>;
   unsigned flag = 0;
   const int t = threadIdx.x;
   if (t < G::EPB * G::NP) {
     const int el = t / G::NP, q = t % G::NP, e = e0 + el;
     if (e < a.n_elem) {
-      double* sm = smem_el + el * esz;
+      R* sm = smem_el + el * esz;
       const long long gi = a.base + (long long)e * G::NP + q;
       double u[G::NV];
 #pragma unroll
-      for (int v = 0; v < G::NV; ++v) {
-        u[v] = a.U[v * a.stride + gi];
-        if (KEEP_U) sm[off_us + v * G::NP + q] = u[v];
+      for (int v = 0; v < G::NV; ++v) u[v] = a.U[v * a.stride + gi];
+      flag |= stage_node<NS, R>(u, sp, a.p_ref, KEEP_U ? sm + off_us + q : nullptr, G::NP, sm + off_p + q,
+                                G::NP, cpT_own);
+      if (u_own) {
+#pragma unroll
+        for (int v = 0; v < G::NV; ++v) u_own[v] = u[v];
       }
-      flag |= node_w<NS>(u, sp, sm + off_w + q, G::NP, nullptr);
     }
   }
   for (int idx = t; idx < G::EPB * G::NFJ; idx += kRT) {
     const int el = idx / G::NFJ, r = idx % G::NFJ, f = r / G::NFN, jf = r % G::NFN;
     const int e = e0 + el;
     if (e >= a.n_elem) continue;
-    double* sm = smem_el + el * esz;
+    R* sm = smem_el + el * esz;
     const int l = f >> 1, side = f & 1;
     const int en = neighbour(a.nel, e, l, side ? 1 : -1);
     const long long gi = a.base + (long long)en * G::NP + face_node<G::N1>(l, side ^ 1, jf);
     double u[G::NV];
 #pragma unroll
-    for (int v = 0; v < G::NV; ++v) {
-      u[v] = a.U[v * a.stride + gi];
-      if (KEEP_U) sm[off_ut + (f * G::NV + v) * G::NFN + jf] = u[v];
-    }
-    flag |= node_w<NS>(u, sp, sm + off_wt + f * 4 * G::NFN + jf, G::NFN, nullptr);
+    for (int v = 0; v < G::NV; ++v) u[v] = a.U[v * a.stride + gi];
+    flag |= stage_node<NS, R>(u, sp, a.p_ref, KEEP_U ? sm + off_ut + f * G::NV * G::NFN + jf : nullptr,
+                              G::NFN, sm + off_pt + f * NPR * G::NFN + jf, G::NFN, nullptr);
   }
   return flag;
 }
@@ -235,45 +272,40 @@ __device__ __forceinline__ unsigned load_element_w(const ReactArgs& a, int e0, d
 // ---------------------------------------------------------------------------------------
 // Launch 1: BR1 gradients and the element's own viscous flux on its faces.
 // ---------------------------------------------------------------------------------------
-template <int N, int NS>
+template <int N, int NS, class R>
 __global__ void __launch_bounds__(kRT) k_br1_faces(const ReactArgs a) {
-  using G = RG<N, NS>;
-  extern __shared__ double smem[];
-  double* D = smem;
-  double* sp = D + G::N1 * G::N1;
-  double* el_base = sp + 3 * NS;
+  using G = RG<N, NS, R>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* sp = reinterpret_cast<double*>(smem_raw);
+  R* D = reinterpret_cast<R*>(sp + 3 * NS);
+  R* el_base = D + G::N1 * G::N1;
   const int t = threadIdx.x;
-  for (int k = t; k < G::N1 * G::N1; k += kRT) D[k] = a.D[k];
-  for (int k = t; k < 3 * NS; k += kRT) {
-    const int c = k / NS, s = k % NS;
-    D[G::N1 * G::N1 + k] = c == 0 ? a.mech->R[s] : (c == 1 ? a.mech->cv[s] : a.mech->h0[s]);
-  }
+  for (int k = t; k < G::N1 * G::N1; k += kRT) D[k] = Ar<R>::load(a.D[k]);
+  load_species<NS>(a.mech, sp, 3);
   __syncthreads();
+  const RS<R> rs(a);
   const int e0 = blockIdx.x * G::EPB;
-  load_element_w<N, NS, false>(a, e0, el_base, G::G_SIZE, G::G_W, G::G_WT, 0, 0, sp);
+  double cpT[2] = {0.0, 0.0};
+  load_element<N, NS, R, false>(a, e0, el_base, G::G_SIZE, G::G_P, G::G_PT, 0, 0, sp, nullptr, cpT);
   __syncthreads();
   if (t >= G::EPB * G::NP) return;
   const int el = t / G::NP, q = t % G::NP, e = e0 + el;
   if (e >= a.n_elem) return;
-  const double* sm = el_base + el * G::G_SIZE;
-  double S[4][3];
-  br1_gradient<N>(q, sm + G::G_W, sm + G::G_WT, D, a.s, a.lift, S);
   const int ijk[3] = {q % G::N1, (q / G::N1) % G::N1, q / G::NFN};
   if (ijk[0] != 0 && ijk[0] != N && ijk[1] != 0 && ijk[1] != N && ijk[2] != 0 && ijk[2] != N) return;
-  // own mixture state again (cheap next to the gradient) for u and c_p
-  double u[G::NV];
-  const long long gi = a.base + (long long)e * G::NP + q;
-#pragma unroll
-  for (int v = 0; v < G::NV; ++v) u[v] = a.U[v * a.stride + gi];
-  const Mx m = mixture<NS>(u, sp);
-  double* fbe = a.fb + (size_t)e * 6 * 4 * G::NFN;
-  double Fv[4];
+  const R* sm = el_base + el * G::G_SIZE;
+  R S[4][3];
+  br1_gradient<N, R>(q, sm + G::G_P, sm + G::G_PT, D, rs.s, rs.lift, S);
+  const R v[3] = {sm[G::G_P + q], sm[G::G_P + G::NP + q], sm[G::G_P + 2 * G::NP + q]};
+  const R kcond = rs.kfac * Ar<R>::load(cpT[0]);
+  R* fbe = reinterpret_cast<R*>(a.fb) + (size_t)e * 6 * 4 * G::NFN;
+  R Fv[4];
 #define DG_FACE_OUT(L)                                                                       \
   if (ijk[L] == 0 || ijk[L] == N) {                                                          \
-    visc_flux<L>(S, m, a.mu, a.kfac, Fv);                                                    \
+    visc_flux<L, R>(S, v, rs.mu, kcond, Fv);                                                 \
     const int jf = L == 0 ? ijk[1] + G::N1 * ijk[2]                                          \
                           : (L == 1 ? ijk[0] + G::N1 * ijk[2] : ijk[0] + G::N1 * ijk[1]);     \
-    double* dst = fbe + (2 * L + (ijk[L] == N ? 1 : 0)) * 4 * G::NFN + jf;                   \
+    R* dst = fbe + (2 * L + (ijk[L] == N ? 1 : 0)) * 4 * G::NFN + jf;                        \
     for (int c = 0; c < 4; ++c) dst[c * G::NFN] = Fv[c];                                     \
   }
   DG_FACE_OUT(0)
@@ -285,61 +317,68 @@ __global__ void __launch_bounds__(kRT) k_br1_faces(const ReactArgs a) {
 // ---------------------------------------------------------------------------------------
 // Launch 2: the fused stage.
 // ---------------------------------------------------------------------------------------
-template <int N, int NS>
+template <int N, int NS, class R>
 __global__ void __launch_bounds__(kRT) k_reacting_stage(const ReactArgs a) {
-  using G = RG<N, NS>;
+  using G = RG<N, NS, R>;
   constexpr int N1 = G::N1, NP = G::NP, NFN = G::NFN, NV = G::NV;
-  extern __shared__ double smem[];
-  double* D = smem + G::C_D;
-  double* sp = smem + G::C_SP;
-  double* X = smem + G::C_X;
-  double* el_base = smem + G::C_SIZE;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* sp = reinterpret_cast<double*>(smem_raw) + G::C_SP;
+  double* X = reinterpret_cast<double*>(smem_raw) + G::C_X;
+  R* D = reinterpret_cast<R*>(reinterpret_cast<double*>(smem_raw) + G::C_DBL);
+  R* el_base = D + N1 * N1;
   const int t = threadIdx.x;
-  for (int k = t; k < N1 * N1; k += kRT) D[k] = a.D[k];
-  load_species<NS>(a.mech, sp);
+  for (int k = t; k < N1 * N1; k += kRT) D[k] = Ar<R>::load(a.D[k]);
+  load_species<NS>(a.mech, sp, 4);
   // neighbour viscous face fluxes from launch 1
   const int e0 = blockIdx.x * G::EPB;
+  const R* fb = reinterpret_cast<const R*>(a.fb);
   for (int idx = t; idx < G::EPB * 24 * NFN; idx += kRT) {
     const int el = idx / (24 * NFN), r = idx % (24 * NFN), f = r / (4 * NFN), cj = r % (4 * NFN);
     const int e = e0 + el;
     if (e >= a.n_elem) continue;
     const int l = f >> 1, side = f & 1;
     const int en = neighbour(a.nel, e, l, side ? 1 : -1);
-    el_base[el * G::E_SIZE + G::E_FT + r] = a.fb[((size_t)en * 6 + (2 * l + (side ^ 1))) * 4 * NFN + cj];
+    el_base[el * G::E_SIZE + G::E_FT + r] = fb[((size_t)en * 6 + (2 * l + (side ^ 1))) * 4 * NFN + cj];
   }
   __syncthreads();
-  unsigned flag = load_element_w<N, NS, true>(a, e0, el_base, G::E_SIZE, G::E_W, G::E_WT, G::E_US, G::E_UT, sp);
+  const RS<R> rs(a);
+  double u64[NV];
+  double cpT[2] = {0.0, 1.0};
+  unsigned flag = load_element<N, NS, R, true>(a, e0, el_base, G::E_SIZE, G::E_P, G::E_PT, G::E_US, G::E_UT, sp,
+                                               u64, cpT);
   __syncthreads();
 
   const bool node_thread = t < G::EPB * NP;
   const int el = node_thread ? t / NP : 0, q = node_thread ? t % NP : 0, e = e0 + el;
   const bool active = node_thread && e < a.n_elem;
-  double* sm = el_base + el * G::E_SIZE;
+  R* sm = el_base + el * G::E_SIZE;
   const int ijk[3] = {q % N1, (q / N1) % N1, q / NFN};
-  double u[NV], res[NV];
-  Mx m{};
-  double S[4][3];
+  R u[NV], res[NV], v[3], pd = R(0), kcond = R(0);
+  R S[4][3];
 #pragma unroll
-  for (int v = 0; v < NV; ++v) res[v] = 0.0;
+  for (int k = 0; k < NV; ++k) res[k] = R(0);
   if (active) {
 #pragma unroll
-    for (int v = 0; v < NV; ++v) u[v] = sm[G::E_US + v * NP + q];
-    m = mixture<NS>(u, sp);
-    br1_gradient<N>(q, sm + G::E_W, sm + G::E_WT, D, a.s, a.lift, S);
+    for (int k = 0; k < NV; ++k) u[k] = sm[G::E_US + k * NP + q];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) v[d] = sm[G::E_P + d * NP + q];
+    pd = sm[G::E_P + 4 * NP + q];
+    kcond = rs.kfac * Ar<R>::load(cpT[0]);
+    br1_gradient<N, R>(q, sm + G::E_P, sm + G::E_PT, D, rs.s, rs.lift, S);
   }
   // volume term, one direction at a time through the H buffer
 #define DG_VOLUME_DIR(L)                                                                      \
   {                                                                                           \
     if (active) {                                                                             \
-      double F[NV], Fv[4];                                                                    \
-      inv_flux<NS>(L, u, m, F);                                                               \
-      visc_flux<L>(S, m, a.mu, a.kfac, Fv);                                                   \
+      R F[NV], Fv[4];                                                                         \
+      inv_flux<NS, R>(L, u, v[0], v[1], v[2], pd, rs.p_ref, F);                               \
+      visc_flux<L, R>(S, v, rs.mu, kcond, Fv);                                                \
       _Pragma("unroll") for (int c = 0; c < 4; ++c) F[NS + c] -= Fv[c];                       \
-      _Pragma("unroll") for (int v = 0; v < NV; ++v) sm[G::E_H + v * NP + q] = F[v];          \
+      _Pragma("unroll") for (int k = 0; k < NV; ++k) sm[G::E_H + k * NP + q] = F[k];          \
       if (ijk[L] == 0 || ijk[L] == N) {                                                       \
         const int jf = L == 0 ? ijk[1] + N1 * ijk[2]                                          \
                               : (L == 1 ? ijk[0] + N1 * ijk[2] : ijk[0] + N1 * ijk[1]);        \
-        double* dst = sm + G::E_FO + (2 * L + (ijk[L] == N ? 1 : 0)) * 4 * NFN + jf;          \
+        R* dst = sm + G::E_FO + (2 * L + (ijk[L] == N ? 1 : 0)) * 4 * NFN + jf;               \
         _Pragma("unroll") for (int c = 0; c < 4; ++c) dst[c * NFN] = Fv[c];                   \
       }                                                                                       \
     }                                                                                         \
@@ -347,14 +386,14 @@ __global__ void __launch_bounds__(kRT) k_reacting_stage(const ReactArgs a) {
     if (active) {                                                                             \
       constexpr int st = L == 0 ? 1 : (L == 1 ? N1 : NFN);                                    \
       const int il = ijk[L], q0 = q - il * st;                                                \
-      double acc[NV];                                                                         \
-      _Pragma("unroll") for (int v = 0; v < NV; ++v) acc[v] = 0.0;                            \
+      R acc[NV];                                                                              \
+      _Pragma("unroll") for (int k = 0; k < NV; ++k) acc[k] = R(0);                           \
       _Pragma("unroll") for (int mm = 0; mm < N1; ++mm) {                                     \
-        const double d = D[il * N1 + mm];                                                     \
-        _Pragma("unroll") for (int v = 0; v < NV; ++v)                                        \
-            acc[v] = fma(d, sm[G::E_H + v * NP + q0 + mm * st], acc[v]);                      \
+        const R d = D[il * N1 + mm];                                                          \
+        _Pragma("unroll") for (int k = 0; k < NV; ++k)                                        \
+            acc[k] = acc[k] + d * sm[G::E_H + k * NP + q0 + mm * st];                         \
       }                                                                                       \
-      _Pragma("unroll") for (int v = 0; v < NV; ++v) res[v] = fma(-a.s[L], acc[v], res[v]);   \
+      _Pragma("unroll") for (int k = 0; k < NV; ++k) res[k] = res[k] - rs.s[L] * acc[k];      \
     }                                                                                         \
     __syncthreads();                                                                          \
   }
@@ -368,34 +407,33 @@ __global__ void __launch_bounds__(kRT) k_reacting_stage(const ReactArgs a) {
   for (int idx = t; idx < G::EPB * G::NFJ; idx += kRT) {
     const int fel = idx / G::NFJ, r = idx % G::NFJ, f = r / NFN, jf = r % NFN;
     if (e0 + fel >= a.n_elem) continue;
-    double* fs = el_base + fel * G::E_SIZE;
+    R* fs = el_base + fel * G::E_SIZE;
     const int l = f >> 1, side = f & 1;
     const int qo = face_node<N1>(l, side, jf);
-    double uo[NV], un[NV];
+    R uo[NV], un[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      uo[v] = fs[G::E_US + v * NP + qo];
-      un[v] = fs[G::E_UT + (f * NV + v) * NFN + jf];
+    for (int k = 0; k < NV; ++k) {
+      uo[k] = fs[G::E_US + k * NP + qo];
+      un[k] = fs[G::E_UT + (f * NV + k) * NFN + jf];
     }
-    const Mx mo = mixture<NS>(uo, sp), mn = mixture<NS>(un, sp);
-    double Fo[NV], Fn[NV];
-    inv_flux<NS>(l, uo, mo, Fo);
-    inv_flux<NS>(l, un, mn, Fn);
-    const double lam = fmax(fabs(pick3(l, mo.v[0], mo.v[1], mo.v[2])) + mo.a,
-                            fabs(pick3(l, mn.v[0], mn.v[1], mn.v[2])) + mn.a);
+    const R* po = fs + G::E_P + qo;
+    const R* pn = fs + G::E_PT + f * NPR * NFN + jf;
+    R Fo[NV], Fn[NV];
+    inv_flux<NS, R>(l, uo, po[0], po[NP], po[2 * NP], po[4 * NP], rs.p_ref, Fo);
+    inv_flux<NS, R>(l, un, pn[0], pn[NFN], pn[2 * NFN], pn[4 * NFN], rs.p_ref, Fn);
+    const R vlo = pick3(l, po[0], po[NP], po[2 * NP]), vln = pick3(l, pn[0], pn[NFN], pn[2 * NFN]);
+    const R lam = Ar<R>::fmax(Ar<R>::abs(vlo) + po[5 * NP], Ar<R>::abs(vln) + pn[5 * NFN]);
     // F* = (F_L + F_R)/2 - lam (U_R - U_L)/2; with L/R the lower/upper side of the face
-    const double sgn = side ? 1.0 : -1.0;  // U_R - U_L = sgn (un - uo)
-    double dlt[NV];
+    const R hl = side ? R(0.5) * lam : R(-0.5) * lam;  // lam/2 (U_R - U_L) = hl (un - uo)
+    R dlt[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      const double Fs = 0.5 * (Fo[v] + Fn[v]) - 0.5 * lam * sgn * (un[v] - uo[v]);
-      dlt[v] = Fs - Fo[v];
-    }
+    for (int k = 0; k < NV; ++k) dlt[k] = R(0.5) * (Fn[k] - Fo[k]) - hl * (un[k] - uo[k]);
 #pragma unroll
     for (int c = 0; c < 4; ++c)
-      dlt[NS + c] -= 0.5 * (fs[G::E_FT + f * 4 * NFN + c * NFN + jf] - fs[G::E_FO + f * 4 * NFN + c * NFN + jf]);
+      dlt[NS + c] = dlt[NS + c] - R(0.5) * (fs[G::E_FT + f * 4 * NFN + c * NFN + jf] -
+                                            fs[G::E_FO + f * 4 * NFN + c * NFN + jf]);
 #pragma unroll
-    for (int v = 0; v < NV; ++v) fs[G::E_UT + (f * NV + v) * NFN + jf] = dlt[v];
+    for (int k = 0; k < NV; ++k) fs[G::E_UT + (f * NV + k) * NFN + jf] = dlt[k];
   }
   __syncthreads();
   if (!active) return;
@@ -405,11 +443,14 @@ __global__ void __launch_bounds__(kRT) k_reacting_stage(const ReactArgs a) {
     if (il != 0 && il != N) continue;
     const int side = il == N ? 1 : 0;
     const int jf = l == 0 ? ijk[1] + N1 * ijk[2] : (l == 1 ? ijk[0] + N1 * ijk[2] : ijk[0] + N1 * ijk[1]);
-    const double c = (side ? -a.s[l] : a.s[l]) * a.lift;
-    const double* ls = sm + G::E_UT + (2 * l + side) * NV * NFN + jf;
+    const R c = (side ? -rs.s[l] : rs.s[l]) * rs.lift;
+    const R* ls = sm + G::E_UT + (2 * l + side) * NV * NFN + jf;
 #pragma unroll
-    for (int v = 0; v < NV; ++v) res[v] = fma(c, ls[v * NFN], res[v]);
+    for (int k = 0; k < NV; ++k) res[k] = res[k] + c * ls[k * NFN];
   }
+  double r64[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) r64[k] = Ar<R>::widen(res[k]);
 
   // Arrhenius source (Sec. 3.1.3, Eqs. src_reaction_rate and src_omega; App. C), FP64:
   // [X_s] = rho_s 1e-6 / W_s, k_f = exp(lnA + b ln T - Ta/T), ln K_c from the five-term fit
@@ -417,40 +458,41 @@ __global__ void __launch_bounds__(kRT) k_reacting_stage(const ReactArgs a) {
   // omega_s = sum_r W_s 1e6 (nu''_s - nu'_s) R_r.
   const int nr = a.mech->nr;
   if (nr > 0) {
-    const double lnT = log(m.T), invT = 1.0 / m.T;
-    const double Z = 1.0e4 * invT, Zi = 1.0e-4 * m.T, lnZ = a.ln1e4 - lnT, Z2 = Z * Z;
+    const double T = cpT[1];
+    const double lnT = log(T), invT = 1.0 / T;
+    const double Z = 1.0e4 * invT, Zi = 1.0e-4 * T, lnZ = a.ln1e4 - lnT, Z2 = Z * Z;
 #pragma unroll
-    for (int s2 = 0; s2 < NS; ++s2) X[s2 * kRT + t] = u[s2] * sp[3 * NS + s2];
+    for (int s2 = 0; s2 < NS; ++s2) X[s2 * kRT + t] = u64[s2] * sp[3 * NS + s2];
     X[NS * kRT + t] = 1.0;
     double om[NS];
 #pragma unroll
     for (int s2 = 0; s2 < NS; ++s2) om[s2] = 0.0;
     for (int r = 0; r < nr; ++r) {
-      const RxnDev& R = a.mech->rx[r];
-      const double lkf = fma(R.b, lnT, fma(-R.Ta, invT, R.lnA));
-      const double lkc = fma(R.kc[0], Zi, fma(R.kc[2], lnZ, fma(R.kc[3], Z, fma(R.kc[4], Z2, R.kc[1]))));
+      const RxnDev& Rx = a.mech->rx[r];
+      const double lkf = fma(Rx.b, lnT, fma(-Rx.Ta, invT, Rx.lnA));
+      const double lkc = fma(Rx.kc[0], Zi, fma(Rx.kc[2], lnZ, fma(Rx.kc[3], Z, fma(Rx.kc[4], Z2, Rx.kc[1]))));
       const double kf = exp(lkf), kb = exp(lkf - lkc);
-      const double pf = X[R.f[0] * kRT + t] * X[R.f[1] * kRT + t] * X[R.f[2] * kRT + t];
-      const double pb = X[R.bk[0] * kRT + t] * X[R.bk[1] * kRT + t] * X[R.bk[2] * kRT + t];
+      const double pf = X[Rx.f[0] * kRT + t] * X[Rx.f[1] * kRT + t] * X[Rx.f[2] * kRT + t];
+      const double pb = X[Rx.bk[0] * kRT + t] * X[Rx.bk[1] * kRT + t] * X[Rx.bk[2] * kRT + t];
       const double rate = fma(kf, pf, -kb * pb);
 #pragma unroll
-      for (int s2 = 0; s2 < NS; ++s2) om[s2] = fma(R.coef[s2], rate, om[s2]);
+      for (int s2 = 0; s2 < NS; ++s2) om[s2] = fma(Rx.coef[s2], rate, om[s2]);
     }
 #pragma unroll
-    for (int s2 = 0; s2 < NS; ++s2) res[s2] += om[s2];
+    for (int s2 = 0; s2 < NS; ++s2) r64[s2] += om[s2];
   }
 
   const long long gi = a.base + (long long)e * NP + q;
   bool finite = true;
 #pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    double x = res[v];
+  for (int k = 0; k < NV; ++k) {
+    double x = r64[k];
     if (a.mode == 1) {
-      x = fma(a.cb, u[v], a.cbdt * res[v]);
-      if (a.need_un) x = fma(a.ca, a.Un[v * a.stride + gi], x);
+      x = fma(a.cb, u64[k], a.cbdt * r64[k]);
+      if (a.need_un) x = fma(a.ca, a.Un[k * a.stride + gi], x);
     }
     finite = finite && finite64(x);
-    a.out[v * a.stride + gi] = x;
+    a.out[k * a.stride + gi] = x;
   }
   if (!finite) flag |= 1u;
   if (flag) atomicOr(a.err, flag);
@@ -461,7 +503,7 @@ template <int NS>
 __global__ void k_max_speed_mix(const double* U, long long stride, long long base, long long n,
                                 const MechDev* __restrict__ mech, unsigned long long* out2) {
   __shared__ double sp[4 * NS];
-  load_species<NS>(mech, sp);
+  load_species<NS>(mech, sp, 4);
   __syncthreads();
   double lam = 0.0, irho = 0.0;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
@@ -493,54 +535,54 @@ __global__ void k_max_speed_mix(const double* U, long long stride, long long bas
   }
 }
 
-template <int N, int NS>
+template <int N, int NS, class R>
 cudaError_t prepare_one() {
-  using G = RG<N, NS>;
-  cudaError_t e = cudaFuncSetAttribute(k_reacting_stage<N, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  using G = RG<N, NS, R>;
+  cudaError_t e = cudaFuncSetAttribute(k_reacting_stage<N, NS, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)G::stage_smem());
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_br1_faces<N, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(k_br1_faces<N, NS, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)G::grad_smem());
   return e;
 }
 
-template <int N, int NS>
+template <int N, int NS, class R>
 cudaError_t launch_one(const ReactArgs& a, cudaStream_t s) {
-  using G = RG<N, NS>;
+  using G = RG<N, NS, R>;
   if (a.n_elem <= 0) return cudaSuccess;
   const unsigned grid = (unsigned)((a.n_elem + G::EPB - 1) / G::EPB);
-  k_br1_faces<N, NS><<<grid, kRT, G::grad_smem(), s>>>(a);
+  k_br1_faces<N, NS, R><<<grid, kRT, G::grad_smem(), s>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_reacting_stage<N, NS><<<grid, kRT, G::stage_smem(), s>>>(a);
+  k_reacting_stage<N, NS, R><<<grid, kRT, G::stage_smem(), s>>>(a);
   return cudaGetLastError();
 }
 
-#define DG_REACT_DISPATCH(CALL)                 \
-  switch (ns * 16 + N) {                        \
-    case 1 * 16 + 1: return CALL(1, 1);         \
-    case 1 * 16 + 2: return CALL(2, 1);         \
-    case 1 * 16 + 3: return CALL(3, 1);         \
-    case 1 * 16 + 4: return CALL(4, 1);         \
-    case 5 * 16 + 1: return CALL(1, 5);         \
-    case 5 * 16 + 2: return CALL(2, 5);         \
-    case 5 * 16 + 3: return CALL(3, 5);         \
-    case 5 * 16 + 4: return CALL(4, 5);         \
-    default: return cudaErrorInvalidValue;      \
+#define DG_REACT_DISPATCH(CALL)                          \
+  switch (ns * 16 + N) {                                 \
+    case 1 * 16 + 1: return CALL(1, 1);                  \
+    case 1 * 16 + 2: return CALL(2, 1);                  \
+    case 1 * 16 + 3: return CALL(3, 1);                  \
+    case 1 * 16 + 4: return CALL(4, 1);                  \
+    case 5 * 16 + 1: return CALL(1, 5);                  \
+    case 5 * 16 + 2: return CALL(2, 5);                  \
+    case 5 * 16 + 3: return CALL(3, 5);                  \
+    case 5 * 16 + 4: return CALL(4, 5);                  \
+    default: return cudaErrorInvalidValue;               \
   }
 
 }  // namespace
 
 bool have_reacting(int N, int ns) { return (ns == 1 || ns == 5) && N >= 1 && N <= kMaxReactingN; }
 
-cudaError_t prepare_reacting(int N, int ns) {
-#define DG_P(n, s) prepare_one<n, s>()
+cudaError_t prepare_reacting(int N, int ns, int fp32) {
+#define DG_P(n, s) (fp32 ? prepare_one<n, s, float>() : prepare_one<n, s, double>())
   DG_REACT_DISPATCH(DG_P)
 #undef DG_P
 }
 
-cudaError_t launch_reacting(int N, int ns, const ReactArgs& a, cudaStream_t s) {
-#define DG_L(n, sp) launch_one<n, sp>(a, s)
+cudaError_t launch_reacting(int N, int ns, int fp32, const ReactArgs& a, cudaStream_t s) {
+#define DG_L(n, sp) (fp32 ? launch_one<n, sp, float>(a, s) : launch_one<n, sp, double>(a, s))
   DG_REACT_DISPATCH(DG_L)
 #undef DG_L
 }

@@ -44,10 +44,11 @@ def grouped_rel(got, ref, ns):
     return max(out)
 
 
-def setup(orc, dg, N, nel, mech, mu, L=TWO_PI, equations=None):
+def setup(orc, dg, N, nel, mech, mu, L=TWO_PI, equations=None, precision=0, p_ref=0.0):
     equations = dg.DG_NS_REACTING if equations is None else equations
     S = dg.Solver(dg.Mesh(3, N, (nel,) * 3, (0.0,) * 3, (L,) * 3), equations=equations, mu=mu,
-                  prandtl=0.72, mechanism=mech if equations == dg.DG_NS_REACTING else None)
+                  prandtl=0.72, mechanism=mech if equations == dg.DG_NS_REACTING else None,
+                  precision=precision, p_ref=p_ref)
     P = orc.Problem(dim=3, N=N, nel=(nel,) * 3, lo=(0.0,) * 3, hi=(L,) * 3, equations=orc.NS_REACTING,
                     mech=mech, mu=mu, prandtl=0.72)
     return S, P
@@ -146,8 +147,7 @@ def test_unsupported_choices_are_refused(env, orc):
     torch, dg = env
     mech = wl.air5_mechanism()
     mesh = dg.Mesh(3, 3, (2, 2, 2), (0.0,) * 3, (1.0,) * 3)
-    for kw in ({"precision": dg.FP32_MIXED}, {"volume": dg.VOL_EC}, {"surface": dg.SURF_HLLC},
-               {"rho_floor": 1e-6}):
+    for kw in ({"volume": dg.VOL_EC}, {"surface": dg.SURF_HLLC}, {"rho_floor": 1e-6}):
         with pytest.raises(dg.DGError) as ei:
             dg.Solver(mesh, equations=dg.DG_NS_REACTING, mu=1e-3, mechanism=mech, **kw)
         assert ei.value.status == dg.DG_EUNSUPPORTED
@@ -209,3 +209,73 @@ def test_full_size_stage_sampled(env, orc):
         err = np.linalg.norm(got[g] - ref[g]) / np.linalg.norm(ref[g])
         floor = 16 * 2.2e-16 * (2.0 / dx) * dabs * np.linalg.norm(F) / np.linalg.norm(ref[g])
         assert err <= 1e-12 + floor, (g, err, floor)
+
+
+# ---------------------------------------------------------------------------------------------
+# FP32-mixed: fluxes, gradients, viscous terms and lifts in FP32; the mixture state, the
+# Arrhenius source and the stage update in FP64; momentum flux shifted by p_ref = p0.
+# ---------------------------------------------------------------------------------------------
+P0 = 101325.0
+EPS32 = 2.0 ** -24
+
+
+def fp32_floor(orc, mech, U, ref, N, nel, L=TWO_PI):
+    """Per-group rounding floor of an FP32 residual: eps32 (2/dx) sum_m |D_im| |F| with F the
+    flux magnitudes of the group (species rho_s |u|, momentum rho |u|^2 + |p - p0|, energy
+    (E + p) |u|), times 16 terms (three directions, surface lifts, sums)."""
+    Rs = np.array(mech["R"])[:, None, None]
+    cv = np.array(mech["cv"])[:, None, None]
+    h0 = np.array(mech["h0"])[:, None, None]
+    rho = U[:5].sum(axis=0)
+    vel = U[5:8] / rho
+    kin = 0.5 * rho * np.sum(vel ** 2, axis=0)
+    T = (U[8] - kin - np.sum(U[:5] * h0, axis=0)) / np.sum(U[:5] * cv, axis=0)
+    p = np.sum(U[:5] * Rs, axis=0) * T
+    speed = np.sqrt(np.sum(vel ** 2, axis=0))
+    flux = [U[:5] * speed, np.broadcast_to(rho * speed ** 2 + np.abs(p - P0), (3,) + rho.shape),
+            (U[8:9] + p) * speed]
+    dabs = np.max(np.sum(np.abs(orc.dmat(N)), axis=1))
+    s = 2.0 / (L / nel)
+    return [16 * EPS32 * s * dabs * np.linalg.norm(F) / np.linalg.norm(ref[g]) for g, F in zip(groups(5), flux)]
+
+
+@pytest.mark.parametrize("N,nel", [(2, 4), (3, 3)])
+def test_fp32_residual_matches_oracle(env, orc, N, nel):
+    torch, dg = env
+    mech = wl.air5_mechanism()
+    mu = wl.reacting_tgv_viscosity(mech)
+    S, P = setup(orc, dg, N, nel, mech, mu, precision=dg.FP32_MIXED, p_ref=P0)
+    xi, _ = orc.gll(N)
+    U = wl.perturbed(wl.reacting_tgv_3d(nel, xi, mech), 5, 1e-3)
+    ref = orc.rhs(P, U)
+    got = S.rhs(dev(torch, U)).cpu().numpy().reshape(U.shape)
+    S.check()
+    floors = fp32_floor(orc, mech, U, ref, N, nel)
+    for g, fl in zip(groups(5), floors):
+        err = np.linalg.norm(got[g] - ref[g]) / np.linalg.norm(ref[g])
+        assert err <= 1e-6 + fl, (g, err, fl)
+
+
+@pytest.mark.parametrize("reactions", [False, True])
+def test_fp32_hundred_steps_match_oracle(env, orc, reactions):
+    """100 SSP-RK3 steps in FP32-mixed against the FP64 oracle: rel-L2 <= 1e-5 per group.
+    Without reactions at the convective time step (dt from cfl 0.25), with them at 1e-12 s."""
+    torch, dg = env
+    mech = wl.air5_mechanism()
+    mu = wl.reacting_tgv_viscosity(mech)
+    xi, _ = orc.gll(3)
+    U = wl.reacting_tgv_3d(3, xi, mech)
+    if not reactions:
+        mech = no_reactions(mech)
+    S, P = setup(orc, dg, 3, 3, mech, mu, precision=dg.FP32_MIXED, p_ref=P0)
+    S.set_state(dev(torch, U))
+    dt = S.max_dt(0.25) if not reactions else 1e-12
+    S.rk_step(dt, 100)
+    S.check()
+    got = S.get_state().cpu().numpy().reshape(U.shape)
+    ref = orc.rk3(P, U.copy(), dt, 100)
+    for g in groups(5):
+        err = np.linalg.norm(got[g] - ref[g]) / np.linalg.norm(ref[g])
+        assert err <= 1e-5, (g, err)
+    # the state moved well beyond the tolerance
+    assert np.linalg.norm(ref - U) / np.linalg.norm(U) > 1e-5 if not reactions else True
