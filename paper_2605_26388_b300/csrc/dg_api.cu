@@ -151,6 +151,7 @@ dg_status pack_mechanism(const dg_mechanism& m, dg::MechDev& d, std::string& why
   const int ns = m.n_species;
   d.ns = ns;
   d.nr = m.n_reactions;
+  for (int j = 0; j < 64; ++j) d.exp2tab[j] = (double)std::exp2((long double)j / 64.0L);
   for (int s = 0; s < ns; ++s) {
     if (!(m.W[s] > 0.0) || !(m.R[s] > 0.0) || !(m.cv[s] > 0.0) || !std::isfinite(m.h0[s]) ||
         !std::isfinite(m.W[s]) || !std::isfinite(m.R[s]) || !std::isfinite(m.cv[s])) {

@@ -139,6 +139,7 @@ struct MechDev {
   int pad[2];
   double R[kMaxSpecies], cv[kMaxSpecies], h0[kMaxSpecies];
   double scale[kMaxSpecies];   // 1e-6 / W_s: rho_s (kg/m^3) -> [X_s] (mol/cm^3)
+  double exp2tab[64];          // 2^(j/64), j = 0..63, for the table-driven exp of the rates
   RxnDev rx[kMaxReactions];
 };
 

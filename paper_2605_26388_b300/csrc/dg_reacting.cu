@@ -50,9 +50,10 @@ struct RG {
   static constexpr int E_FO = E_FT + 24 * NFN;          // own F_v      [6][4][NFN]
   static constexpr int E_H = E_FO + 24 * NFN;           // F^l - F_v^l  [NV][NP]
   static constexpr int E_SIZE = E_H + NV * NP;
-  // stage kernel, per CTA: species table and concentration slots (double), D (R)
+  // stage kernel, per CTA: species table, exp table, concentration slots (double), D (R)
   static constexpr int C_SP = 0;                        // R, cv, h0, scale [4][NS]
-  static constexpr int C_X = C_SP + 4 * NS;             // [NSL][kRT]
+  static constexpr int C_E2 = C_SP + 4 * NS;            // 2^(j/64) [64]
+  static constexpr int C_X = C_E2 + 64;                 // [NSL][kRT]
   static constexpr int C_DBL = C_X + NSL * kRT;
   static constexpr size_t stage_smem() {
     return sizeof(double) * (size_t)C_DBL + sizeof(R) * (size_t)(N1 * N1 + EPB * E_SIZE);
@@ -76,6 +77,41 @@ __device__ __forceinline__ int neighbour(const int* nel, int e, int l, int dir) 
   for (int d = 0; d < 3; ++d)
     if (d == l) c[d] = (c[d] + dir + nel[d]) % nel[d];
   return c[0] + nel[0] * (c[1] + nel[1] * c[2]);
+}
+
+// exp(x) for the Arrhenius rates, after Tang's table-driven method (P. T. P. Tang, ACM TOMS
+// 15(2), 1989): x = (64 m + j) ln2/64 + r with |r| <= ln2/128, exp(x) = 2^m 2^(j/64) e^r;
+// e^r - 1 from its degree-5 Taylor polynomial (truncation < 4e-17 relative), 2^(j/64) from a
+// 64-entry FP64 table computed on the host, 2^m added to the exponent field.  ln2/64 is
+// split into a 33-bit head (n * head exact for |n| < 2^20) and a tail.  Ten FP64 operations;
+// |x| >= 704 (outside the rates' range) falls back to the library function.
+__device__ __forceinline__ double exp_tab(double x, const double* tab) {
+  const uint32_t ah = (uint32_t)__double2hiint(x) & 0x7fffffffu;
+  if (ah >= 0x40860000u) return exp(x);
+  const double kShift = 6755399441055744.0;  // 1.5 * 2^52: the sum's low word holds rint(x 64/ln2)
+  const double t = fma(x, 92.33248261689366, kShift);
+  const int n = __double2loint(t);
+  const double nd = t - kShift;
+  double r = fma(-nd, 0.010830424695086549, x);
+  r = fma(-nd, 1.162596423439437e-12, r);
+  const double p = fma(r * r, fma(r, fma(r, fma(r, 1.0 / 120.0, 1.0 / 24.0), 1.0 / 6.0), 0.5), r);
+  const double T = tab[n & 63];
+  const double y = fma(T, p, T);
+  return __hiloint2double(__double2hiint(y) + ((n >> 6) << 20), __double2loint(y));
+}
+
+// 1/x in FP64 for positive x between 2^-125 and 2^125: an FP32 reciprocal seed (relative
+// error below 2^-21) refined by two Newton-Raphson steps y <- y + y (1 - x y), each of which
+// squares the error, so the result is within an ulp or two of the quotient.  Four FP64
+// operations instead of a full division; other x take the division.
+__device__ __forceinline__ double rcp64(double x) {
+  const uint32_t hi = (uint32_t)__double2hiint(x);
+  if (hi - 0x38200000u >= 0x47c00000u - 0x38200000u) return 1.0 / x;
+  double y = f2d(__fdividef(1.0f, d2f_rn(x)));
+  double e = fma(-x, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-x, y, 1.0);
+  return fma(y, e, y);
 }
 
 template <class T>
@@ -102,14 +138,14 @@ __device__ __forceinline__ Mx mixture(const double* u, const double* sp) {
   }
   Mx m;
   m.rho = rho;
-  const double irho = 1.0 / rho;
+  const double irho = rcp64(rho);
   double kin = 0.0;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     m.v[d] = u[NS + d] * irho;
     kin = fma(u[NS + d], m.v[d], kin);
   }
-  const double ircv = 1.0 / rcv;
+  const double ircv = rcp64(rcv);
   m.T = (u[NS + 3] - 0.5 * kin - rh0) * ircv;
   m.p = rR * m.T;
   m.a = sqrt(fma(rR, ircv, 1.0) * m.p * irho);
@@ -324,11 +360,13 @@ __global__ void __launch_bounds__(kRT) k_reacting_stage(const ReactArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* sp = reinterpret_cast<double*>(smem_raw) + G::C_SP;
   double* X = reinterpret_cast<double*>(smem_raw) + G::C_X;
+  double* e2tab = reinterpret_cast<double*>(smem_raw) + G::C_E2;
   R* D = reinterpret_cast<R*>(reinterpret_cast<double*>(smem_raw) + G::C_DBL);
   R* el_base = D + N1 * N1;
   const int t = threadIdx.x;
   for (int k = t; k < N1 * N1; k += kRT) D[k] = Ar<R>::load(a.D[k]);
   load_species<NS>(a.mech, sp, 4);
+  for (int k = t; k < 64; k += kRT) e2tab[k] = a.mech->exp2tab[k];
   // neighbour viscous face fluxes from launch 1
   const int e0 = blockIdx.x * G::EPB;
   const R* fb = reinterpret_cast<const R*>(a.fb);
@@ -459,7 +497,7 @@ __global__ void __launch_bounds__(kRT) k_reacting_stage(const ReactArgs a) {
   const int nr = a.mech->nr;
   if (nr > 0) {
     const double T = cpT[1];
-    const double lnT = log(T), invT = 1.0 / T;
+    const double lnT = log(T), invT = rcp64(T);
     const double Z = 1.0e4 * invT, Zi = 1.0e-4 * T, lnZ = a.ln1e4 - lnT, Z2 = Z * Z;
 #pragma unroll
     for (int s2 = 0; s2 < NS; ++s2) X[s2 * kRT + t] = u64[s2] * sp[3 * NS + s2];
@@ -471,7 +509,7 @@ __global__ void __launch_bounds__(kRT) k_reacting_stage(const ReactArgs a) {
       const RxnDev& Rx = a.mech->rx[r];
       const double lkf = fma(Rx.b, lnT, fma(-Rx.Ta, invT, Rx.lnA));
       const double lkc = fma(Rx.kc[0], Zi, fma(Rx.kc[2], lnZ, fma(Rx.kc[3], Z, fma(Rx.kc[4], Z2, Rx.kc[1]))));
-      const double kf = exp(lkf), kb = exp(lkf - lkc);
+      const double kf = exp_tab(lkf, e2tab), kb = exp_tab(lkf - lkc, e2tab);
       const double pf = X[Rx.f[0] * kRT + t] * X[Rx.f[1] * kRT + t] * X[Rx.f[2] * kRT + t];
       const double pb = X[Rx.bk[0] * kRT + t] * X[Rx.bk[1] * kRT + t] * X[Rx.bk[2] * kRT + t];
       const double rate = fma(kf, pf, -kb * pb);
