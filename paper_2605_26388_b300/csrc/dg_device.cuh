@@ -192,17 +192,18 @@ __device__ __forceinline__ void point_flux(const R* u, const Prim<DIM, R>& q, R*
 // (a-b)/(ln a - ln b) with the logarithms la, lb computed once per node.  FP32 evaluates
 // both forms and selects (no divergent branch, one fast reciprocal); FP64 branches (the
 // division is expensive there and the branch is uniform in smooth regions).
+// Arguments: d = a - b, dl = ln a - ln b, s = a + b, f = d / s.
 template <class R>
-__device__ __forceinline__ R log_mean_from(R a, R b, R la, R lb, R s, R f) {
+__device__ __forceinline__ R log_mean_from(R d, R dl, R s, R f) {
   const R u = f * f;
   const R G = R(1) - u * (R(1.0 / 3.0) + u * (R(4.0 / 45.0) + u * (R(44.0 / 945.0) +
                                                                     u * R(0.030194003527336861))));
   if constexpr (sizeof(R) == 4) {
-    const R lg = (a - b) * Ar<R>::rcp(la - lb);
-    return u < R(Ar<R>::kLogMeanSeries) ? R(0.5) * s * G : lg;
+    const R lg = d * Ar<R>::rcp(dl);
+    return u < R(Ar<R>::kLogMeanSeries) ? (R(0.5) * s) * G : lg;
   } else {
-    if (u < R(Ar<R>::kLogMeanSeries)) return R(0.5) * s * G;
-    return Ar<R>::div(a - b, la - lb);
+    if (u < R(Ar<R>::kLogMeanSeries)) return (R(0.5) * s) * G;
+    return Ar<R>::div(d, dl);
   }
 }
 
@@ -213,24 +214,24 @@ template <int DIM, int L, class R>
 __device__ __forceinline__ void ec_flux_prims(R rL, const R* vL, R pdL, R bL, R lrL, R lbL, R rR,
                                               const R* vR, R pdR, R bR, R lrR, R lbR, R igm1,
                                               R p_ref, R* F) {
-  const R sr = rL + rR, sb = bL + bR;
+  const R sr = rL + rR, sb = bL + bR, dr = rL - rR, db = bL - bR;
   const R inv = Ar<R>::rcp(sr * sb);  // one reciprocal serves both f's
-  const R fr = (rL - rR) * (sb * inv);
-  const R fb = (bL - bR) * (sr * inv);
-  const R rho_ln = log_mean_from(rL, rR, lrL, lrR, sr, fr);
-  const R beta_ln = log_mean_from(bL, bR, lbL, lbR, sb, fb);
-  R vavg[DIM];
+  const R fr = dr * (sb * inv);
+  const R fb = db * (sr * inv);
+  const R rho_ln = log_mean_from(dr, lrL - lrR, sr, fr);
+  const R beta_ln = log_mean_from(db, lbL - lbR, sb, fb);
+  R vs[DIM];  // v_L + v_R (the factor 1/2 of the averages is folded into the products)
   R vLvR = R(0);
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
-    vavg[d] = R(0.5) * (vL[d] + vR[d]);
+    vs[d] = vL[d] + vR[d];
     vLvR += vL[d] * vR[d];
   }
-  const R frho = rho_ln * vavg[L];
-  const R pdavg = R(0.5) * (pdL + pdR);
+  const R frho = (R(0.5) * rho_ln) * vs[L];
+  const R hf = R(0.5) * frho;
   F[0] = frho;
 #pragma unroll
-  for (int d = 0; d < DIM; ++d) F[1 + d] = frho * vavg[d] + (d == L ? pdavg : R(0));
+  for (int d = 0; d < DIM; ++d) F[1 + d] = d == L ? hf * vs[d] + R(0.5) * (pdL + pdR) : hf * vs[d];
   F[DIM + 1] = frho * (igm1 * Ar<R>::rcp(beta_ln) + R(0.5) * vLvR) +
                R(0.5) * ((pdL + p_ref) * vR[L] + (pdR + p_ref) * vL[L]);
 }

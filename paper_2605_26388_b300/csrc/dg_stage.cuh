@@ -54,6 +54,13 @@ __device__ __forceinline__ void surface_flux(int kind, const R* uL, const Prim<D
 }
 
 constexpr int cmax(int a, int b) { return a > b ? a : b; }
+constexpr int al4(int n) { return (n + 3) & ~3; }
+
+// Four flux-precision values loaded or stored as one 16-byte (FP32) shared-memory access.
+template <class R>
+struct alignas(4 * sizeof(R)) Q4 {
+  R x, y, z, w;
+};
 
 // the launch scalars in the flux precision (precomputed on the host)
 template <class R>
@@ -86,21 +93,24 @@ struct EulerStage {
   // (i, i+o mod N1) for o = 1..NO, the last offset (o = N1/2 when N1 is even) only for
   // i < N1/2, so that every unordered pair is evaluated exactly once.
   static constexpr int NO = N1 / 2;
-  // per-node staged quantities: EC -- rho, v_1..v_DIM, pd, beta = rho/p, ln rho, ln beta;
-  // strong/weak -- the DIM point fluxes (NV each) and pd
-  static constexpr int NQ = EC ? (DIM + 5) : (DIM * NV + 1);
-  static constexpr int PD = EC ? (DIM + 1) : (DIM * NV);
+  // per-node staged quantities: EC -- two Q4 records per node, QA = (rho, v_1, v_2, v_3 or 0)
+  // and QB = (pd, beta = rho/p, ln rho, ln beta); strong/weak -- the DIM point fluxes (NV
+  // each) and pd
+  static constexpr int NQ = EC ? 8 : (DIM * NV + 1);
+  static constexpr int PD = DIM * NV;  // strong/weak: row of pd
   static constexpr int NXN = EC ? DIM * NO : 0;            // pair slots per node
   // FP64 staging buffer (two of them): own U [EPB][NV][NP], U^n [EPB][NV][NP],
   // neighbour face traces [EPB][NF][NV][NFN]
   static constexpr int ST_U = 0, ST_N = EPB * NV * NP, ST_T = 2 * EPB * NV * NP;
   static constexpr int ST_SIZE = ST_T + EPB * NF * NV * NFN;
   // flux-precision arrays
-  static constexpr int OFF_U = 0;                             // [EPB][NV][NP]
-  static constexpr int OFF_Q = OFF_U + EPB * NV * NP;         // [EPB][NQ][NP]
-  static constexpr int OFF_S = OFF_Q + EPB * NQ * NP;         // [EPB][NF][NFN][NV]
-  static constexpr int OFF_X = OFF_S + EPB * NF * NFN * NV;   // [EPB][DIM][NO][NV][NP]
-  static constexpr int OFF_D = OFF_X + EPB * NXN * NV * NP;   // [N1][N1]
+  // pair slot: XA = F_0..F_3 as Q4 per node, then XB = F_4 per node (3D), padded to 16 bytes
+  static constexpr int XSLOT = 4 * NP + (NV > 4 ? al4(NP) : 0);
+  static constexpr int OFF_U = 0;                                  // [EPB][NV][NP]
+  static constexpr int OFF_Q = al4(OFF_U + EPB * NV * NP);         // EC: [EPB][2][NP] Q4, else [EPB][NQ][NP]
+  static constexpr int OFF_S = al4(OFF_Q + EPB * NQ * NP);         // [EPB][NF][NFN][NV]
+  static constexpr int OFF_X = al4(OFF_S + EPB * NF * NFN * NV);   // [EPB][DIM][NO] pair slots
+  static constexpr int OFF_D = OFF_X + EPB * NXN * XSLOT;          // [N1][N1]
   static constexpr int R_SIZE = OFF_D + N1 * N1;
   static constexpr size_t smem_bytes() {
     return sizeof(double) * 2 * (size_t)ST_SIZE + sizeof(R) * (size_t)R_SIZE +
@@ -120,6 +130,26 @@ struct EulerStage {
     m.sm = reinterpret_cast<R*>(m.st + 2 * ST_SIZE);
     m.nb = reinterpret_cast<int*>(m.sm + R_SIZE);
     return m;
+  }
+
+  // EC records of element slot el: QA[NP] then QB[NP]
+  static __device__ __forceinline__ Q4<R>* qa(R* sm, int el) {
+    return reinterpret_cast<Q4<R>*>(sm + OFF_Q) + el * 2 * NP;
+  }
+  static __device__ __forceinline__ const Q4<R>* qa(const R* sm, int el) {
+    return reinterpret_cast<const Q4<R>*>(sm + OFF_Q) + el * 2 * NP;
+  }
+  // pressure deviation of node nd of element slot el
+  static __device__ __forceinline__ R pd_of(const R* sm, int el, int nd) {
+    if constexpr (EC) return qa(sm, el)[NP + nd].x;
+    else return sm[OFF_Q + (el * NQ + PD) * NP + nd];
+  }
+  // pair slot (direction L, offset o) of element slot el
+  static __device__ __forceinline__ R* xslot(R* sm, int el, int L, int o) {
+    return sm + OFF_X + ((el * DIM + L) * NO + (o - 1)) * XSLOT;
+  }
+  static __device__ __forceinline__ const R* xslot(const R* sm, int el, int L, int o) {
+    return sm + OFF_X + ((el * DIM + L) * NO + (o - 1)) * XSLOT;
   }
 
   template <int L>
@@ -207,31 +237,25 @@ struct EulerStage {
     const int i = node_pos<L>(nd);
     const R s = sv<R>(I, L);
     const R* Dv = sm + OFF_D;
-    const R* Q = sm + OFF_Q + el * NQ * NP;
-    R vi[DIM];
-#pragma unroll
-    for (int d = 0; d < DIM; ++d) vi[d] = Q[(1 + d) * NP + nd];
-    const R ri = Q[nd], pdi = Q[PD * NP + nd], bi = Q[(DIM + 2) * NP + nd];
-    const R lri = Q[(DIM + 3) * NP + nd], lbi = Q[(DIM + 4) * NP + nd];
-    R* X = sm + OFF_X + ((el * DIM + L) * NO) * NV * NP + nd;
+    const Q4<R>* QA = qa(sm, el);
+    const Q4<R> ai = QA[nd], bi = QA[NP + nd];
+    const R vi[3] = {ai.y, ai.z, ai.w};
 #pragma unroll
     for (int o = 1; o <= NO; ++o) {
       if (2 * o == N1 && i >= N1 / 2) break;
       const int j = (i + o < N1) ? i + o : i + o - N1;
       const int nj = nd + (j - i) * S;
-      R vj[DIM];
-#pragma unroll
-      for (int d = 0; d < DIM; ++d) vj[d] = Q[(1 + d) * NP + nj];
+      const Q4<R> aj = QA[nj], bj = QA[NP + nj];
+      const R vj[3] = {aj.y, aj.z, aj.w};
       R F[NV];
-      ec_flux_prims<DIM, L>(ri, vi, pdi, bi, lri, lbi, Q[nj], vj, Q[PD * NP + nj],
-                            Q[(DIM + 2) * NP + nj], Q[(DIM + 3) * NP + nj], Q[(DIM + 4) * NP + nj],
+      ec_flux_prims<DIM, L>(ai.x, vi, bi.x, bi.y, bi.z, bi.w, aj.x, vj, bj.x, bj.y, bj.z, bj.w,
                             igm1, p_ref, F);
       const R c = s * Dv[i * N1 + j];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        acc[v] -= c * F[v];
-        X[((o - 1) * NV + v) * NP] = F[v];
-      }
+      for (int v = 0; v < NV; ++v) acc[v] -= c * F[v];
+      R* X = xslot(sm, el, L, o);
+      reinterpret_cast<Q4<R>*>(X)[nd] = Q4<R>{F[0], F[1], F[2], F[3]};
+      if constexpr (NV > 4) X[4 * NP + nd] = F[4];
     }
   }
 
@@ -243,21 +267,25 @@ struct EulerStage {
     const int i = node_pos<L>(nd);
     const R s = sv<R>(I, L);
     const R* Dv = sm + OFF_D;
-    const R* X = sm + OFF_X + ((el * DIM + L) * NO) * NV * NP;
 #pragma unroll
     for (int o = 1; o <= NO; ++o) {
       const int k = (i - o >= 0) ? i - o : i - o + N1;  // owner of pair (k, i) at offset o
       if (2 * o == N1 && k >= N1 / 2) continue;
       const int nk = nd + (k - i) * S;
       const R c = s * Dv[i * N1 + k];
-#pragma unroll
-      for (int v = 0; v < NV; ++v) acc[v] -= c * X[((o - 1) * NV + v) * NP + nk];
+      const R* X = xslot(sm, el, L, o);
+      const Q4<R> f = reinterpret_cast<const Q4<R>*>(X)[nk];
+      acc[0] -= c * f.x;
+      acc[1] -= c * f.y;
+      acc[2] -= c * f.z;
+      acc[3] -= c * f.w;
+      if constexpr (NV > 4) acc[4] -= c * X[4 * NP + nk];
     }
     if (i == 0 || i == N) {  // diagonal: F#(U_i, U_i) = F(U_i); only the end nodes have D_ii != 0
       R u[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) u[v] = sm[OFF_U + (el * NV + v) * NP + nd];
-      const Prim<DIM, R> qq = prims<DIM>(u, sm[OFF_Q + (el * NQ + PD) * NP + nd], p_ref);
+      const Prim<DIM, R> qq = prims<DIM>(u, pd_of(sm, el, nd), p_ref);
       R F[NV];
       point_flux<DIM, L>(u, qq, F);
       const R c = s * Dv[i * N1 + i];
@@ -326,7 +354,7 @@ struct EulerStage {
       nbr0[v] = Ar<R>::load(n64[v]);
     }
     double rhoe;
-    const R pd_own = sm[OFF_Q + (ej * NQ + PD) * NP + r.ndo];
+    const R pd_own = pd_of(sm, ej, r.ndo);
     const R pd_nbr = pdev<DIM>(n64, nbr0, A.pd.gm1, A.pd.p_ref, rhoe);
     R own[NV], nbr[NV];
     to_face_axes(own0, own, l);
@@ -402,16 +430,13 @@ struct EulerStage {
       // FP64 values by their sign/exponent bits
       if (!(__double2hiint(u64[0]) > 0 && __double2hiint(rhoe) > 0)) atomicOr(A.err, 2u);
       R* Q = sm + OFF_Q + el * NQ * NP;
-      Q[PD * NP + nd] = pd;
       if constexpr (EC) {
-        Q[nd] = q.rho;
-#pragma unroll
-        for (int d = 0; d < DIM; ++d) Q[(1 + d) * NP + nd] = q.v[d];
         const R beta = q.rho * Ar<R>::rcp(q.p);
-        Q[(DIM + 2) * NP + nd] = beta;
-        Q[(DIM + 3) * NP + nd] = Ar<R>::log(q.rho);
-        Q[(DIM + 4) * NP + nd] = Ar<R>::log(beta);
+        Q4<R>* QA = qa(sm, el);
+        QA[nd] = Q4<R>{q.rho, q.v[0], q.v[1], DIM == 3 ? q.v[DIM - 1] : R(0)};
+        QA[NP + nd] = Q4<R>{pd, beta, Ar<R>::log(q.rho), Ar<R>::log(beta)};
       } else {
+        Q[PD * NP + nd] = pd;
         R F[NV];
         point_flux<DIM, 0>(u, q, F);
 #pragma unroll
