@@ -202,21 +202,26 @@ __device__ __forceinline__ void point_flux(const R* u, const Prim<DIM, R>& q, R*
 // where the Taylor series of 1/F is 1 - u/3 - 4u^2/45 - 44u^3/945 - c4 u^4 (c4 =
 // 0.0301940...), used for small u (the Ismail-Roe idea of a series near a = b, here
 // expanded for the reciprocal so that no division is needed); otherwise a^ln =
-// (a-b)/(ln a - ln b) with the logarithms la, lb computed once per node.  FP32 evaluates
-// both forms and selects (no divergent branch, one fast reciprocal); FP64 branches (the
-// division is expensive there and the branch is uniform in smooth regions).
-// Arguments: d = a - b, dl = ln a - ln b, s = a + b, f = d / s.
+// (a-b)/ln(a/b).  FP32 takes the logarithms la, lb computed once per node and evaluates
+// both forms, then selects (no divergent branch, one fast reciprocal); FP64 branches and
+// takes the logarithm of the ratio only on the (rare, in smooth regions) log branch, since
+// an FP64 logarithm costs as much as dozens of FP64 FMAs.
+// Arguments: a, b; d = a - b, la, lb (FP32 only), s = a + b, f = d / s.
 template <class R>
-__device__ __forceinline__ R log_mean_from(R d, R dl, R s, R f) {
+__device__ __forceinline__ R log_mean_from(R a, R b, R d, R la, R lb, R s, R f) {
   const R u = f * f;
-  const R G = R(1) - u * (R(1.0 / 3.0) + u * (R(4.0 / 45.0) + u * (R(44.0 / 945.0) +
-                                                                    u * R(0.030194003527336861))));
   if constexpr (sizeof(R) == 4) {
-    const R lg = d * Ar<R>::rcp(dl);
+    const R G = R(1) - u * (R(1.0 / 3.0) + u * (R(4.0 / 45.0) + u * (R(44.0 / 945.0) +
+                                                                      u * R(0.030194003527336861))));
+    const R lg = d * Ar<R>::rcp(la - lb);
     return u < R(Ar<R>::kLogMeanSeries) ? (R(0.5) * s) * G : lg;
   } else {
-    if (u < R(Ar<R>::kLogMeanSeries)) return (R(0.5) * s) * G;
-    return Ar<R>::div(d, dl);
+    if (u < R(Ar<R>::kLogMeanSeries)) {
+      const R G = R(1) - u * (R(1.0 / 3.0) + u * (R(4.0 / 45.0) + u * (R(44.0 / 945.0) +
+                                                                        u * R(0.030194003527336861))));
+      return (R(0.5) * s) * G;
+    }
+    return Ar<R>::div(d, Ar<R>::log(Ar<R>::div(a, b)));
   }
 }
 
@@ -231,8 +236,8 @@ __device__ __forceinline__ void ec_flux_prims(R rL, const R* vL, R pdL, R bL, R 
   const R inv = Ar<R>::rcp(sr * sb);  // one reciprocal serves both f's
   const R fr = dr * (sb * inv);
   const R fb = db * (sr * inv);
-  const R rho_ln = log_mean_from(dr, lrL - lrR, sr, fr);
-  const R beta_ln = log_mean_from(db, lbL - lbR, sb, fb);
+  const R rho_ln = log_mean_from(rL, rR, dr, lrL, lrR, sr, fr);
+  const R beta_ln = log_mean_from(bL, bR, db, lbL, lbR, sb, fb);
   R vs[DIM];  // v_L + v_R (the factor 1/2 of the averages is folded into the products)
   R vLvR = R(0);
 #pragma unroll
@@ -253,8 +258,10 @@ template <int DIM, int L, class R>
 __device__ __forceinline__ void ec_flux(const Prim<DIM, R>& a, const Prim<DIM, R>& b, R igm1,
                                         R p_ref, R* F) {
   const R ba = a.rho * Ar<R>::rcp(a.p), bb = b.rho * Ar<R>::rcp(b.p);
-  ec_flux_prims<DIM, L>(a.rho, a.v, a.pd, ba, Ar<R>::log(a.rho), Ar<R>::log(ba), b.rho, b.v, b.pd,
-                        bb, Ar<R>::log(b.rho), Ar<R>::log(bb), igm1, p_ref, F);
+  const bool f32 = sizeof(R) == 4;  // the FP64 log mean takes its own logarithm
+  ec_flux_prims<DIM, L>(a.rho, a.v, a.pd, ba, f32 ? Ar<R>::log(a.rho) : R(0), f32 ? Ar<R>::log(ba) : R(0),
+                        b.rho, b.v, b.pd, bb, f32 ? Ar<R>::log(b.rho) : R(0), f32 ? Ar<R>::log(bb) : R(0),
+                        igm1, p_ref, F);
 }
 
 // Local Lax-Friedrichs (Rusanov): F* = (F_L + F_R)/2 - lambda/2 (U_R - U_L),

@@ -434,7 +434,9 @@ struct EulerStage {
         const R beta = q.rho * Ar<R>::rcp(q.p);
         Q4<R>* QA = qa(sm, el);
         QA[nd] = Q4<R>{q.rho, q.v[0], q.v[1], DIM == 3 ? q.v[DIM - 1] : R(0)};
-        QA[NP + nd] = Q4<R>{pd, beta, Ar<R>::log(q.rho), Ar<R>::log(beta)};
+        // logarithms for the FP32 log mean only (the FP64 one branches to its own logarithm)
+        if constexpr (sizeof(R) == 4) QA[NP + nd] = Q4<R>{pd, beta, Ar<R>::log(q.rho), Ar<R>::log(beta)};
+        else QA[NP + nd] = Q4<R>{pd, beta, R(0), R(0)};
       } else {
         Q[PD * NP + nd] = pd;
         R F[NV];
