@@ -44,7 +44,7 @@ P_REF = 1.0 / (GAMMA * MACH ** 2)  # background pressure; the momentum flux carr
 # DRAM bytes per stage launch (mean of stages 1-3) of the current kernel, from the ncu
 # capture summarised in profiles/euler_stage_3d_n4_ec_hllc_tgv.md (32^3 case scaled by the
 # element count to 64^3); None where no capture of the current kernel exists.
-TRAFFIC_PER_LAUNCH = {"fp32_mixed": 3.37e9, "fp64": None}
+TRAFFIC_PER_LAUNCH = {"fp32_mixed": 3.30e9, "fp64": None}
 
 
 def measured_peaks():
