@@ -279,3 +279,65 @@ def test_fp32_hundred_steps_match_oracle(env, orc, reactions):
         assert err <= 1e-5, (g, err)
     # the state moved well beyond the tolerance
     assert np.linalg.norm(ref - U) / np.linalg.norm(U) > 1e-5 if not reactions else True
+
+
+def _state_on(orc, mech, N, nel, L, seed):
+    """A reacting state on a box with an uneven element count per direction: air at 4000-6000 K
+    with a smooth seeded temperature field and a seeded velocity field (|u| <= 100 m/s)."""
+    xi, _ = orc.gll(N)
+    lo, hi = (0.0,) * 3, (L,) * 3
+    X = wl.node_coordinates(3, nel, lo, hi, xi)
+    T = 5000.0 + 1000.0 * wl.fourier_field(seed, X, lo, hi, 2)
+    vel = [100.0 * wl.fourier_field(seed + 1 + d, X, lo, hi, 2) for d in range(3)]
+    Y = np.array([0.70, 0.20, 0.04, 0.03, 0.03])
+    rho = 101325.0 / (float(np.dot(Y, mech["R"])) * T)
+    return wl.perturbed(wl.reacting_conserved([rho * Y[s] for s in range(5)], vel, T, mech), seed + 9, 1e-3)
+
+
+@pytest.mark.parametrize("N,nel", [(1, (3, 1, 2)), (2, (1, 1, 1)), (3, (2, 3, 1)), (4, (1, 2, 2))])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_uneven_and_single_element_meshes(env, orc, N, nel, prec):
+    """Element counts that differ per direction, and a single element that is its own
+    neighbour on every face, in both precisions."""
+    torch, dg = env
+    mech = wl.air5_mechanism()
+    mu = 3e-3
+    L = 0.05
+    S = dg.Solver(dg.Mesh(3, N, nel, (0.0,) * 3, (L,) * 3), equations=dg.DG_NS_REACTING, mu=mu,
+                  prandtl=0.72, mechanism=mech, precision=prec, p_ref=P0 if prec else 0.0)
+    P = orc.Problem(dim=3, N=N, nel=nel, lo=(0.0,) * 3, hi=(L,) * 3, equations=orc.NS_REACTING,
+                    mech=mech, mu=mu, prandtl=0.72)
+    U = _state_on(orc, mech, N, nel, L, 21 + N)
+    ref = orc.rhs(P, U)
+    got = S.rhs(dev(torch, U)).cpu().numpy().reshape(U.shape)
+    S.check()
+    if prec == 0:
+        assert grouped_rel(got, ref, 5) <= 1e-12
+    else:
+        floors = fp32_floor(orc, mech, U, ref, N, max(nel), L)
+        for g, fl in zip(groups(5), floors):
+            err = np.linalg.norm(got[g] - ref[g]) / np.linalg.norm(ref[g])
+            assert err <= 1e-6 + fl, (g, err, fl)
+
+
+def test_several_instances_in_one_context(env, orc):
+    """Two reacting instances of different degree and size in one context: each block of
+    the concatenated state evolves as its own problem."""
+    torch, dg = env
+    mech = wl.air5_mechanism()
+    mu, L, dt = 3e-3, 0.05, 1e-12
+    specs = [(2, (2, 3, 2)), (3, (3, 1, 2))]
+    meshes = [dg.Mesh(3, N, nel, (0.0,) * 3, (L,) * 3) for N, nel in specs]
+    S = dg.Solver(meshes, equations=dg.DG_NS_REACTING, mu=mu, prandtl=0.72, mechanism=mech)
+    parts = [_state_on(orc, mech, N, nel, L, 31 + k) for k, (N, nel) in enumerate(specs)]
+    U = np.ascontiguousarray(np.concatenate([p.reshape(9, -1) for p in parts], axis=1))
+    S.set_state(torch.from_numpy(U).cuda())
+    S.rk_step(dt, 5)
+    S.check()
+    got = S.get_state().cpu().numpy()
+    for (N, nel), part, off in zip(specs, parts, S.offsets):
+        P = orc.Problem(dim=3, N=N, nel=nel, lo=(0.0,) * 3, hi=(L,) * 3, equations=orc.NS_REACTING,
+                        mech=mech, mu=mu, prandtl=0.72)
+        ref = orc.rk3(P, part.copy(), dt, 5)
+        g = got[:, off:off + part[0].size].reshape(part.shape)
+        assert grouped_rel(g, ref, 5) <= 1e-12
