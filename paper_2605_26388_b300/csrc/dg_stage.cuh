@@ -40,6 +40,9 @@ __device__ __forceinline__ void cp_async_commit() {
 __device__ __forceinline__ void cp_async_wait_prev() {  // all but the newest group done
   asm volatile("cp.async.wait_group 1;\n" ::: "memory");
 }
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
 
 template <int DIM, int L, class R>
 __device__ __forceinline__ void surface_flux(int kind, const R* uL, const Prim<DIM, R>& a,
@@ -530,7 +533,10 @@ struct EulerStage {
     for (int k = threadIdx.x; k < N1 * N1; k += blockDim.x) sm[OFF_D + k] = R(Dv[k]);
   }
 
-  // single-instance persistent launch: groups of A.inst, double-buffered
+  // single-instance persistent launch: groups of A.inst, double-buffered, one barrier per
+  // group outside compute().  The neighbour table of a group is filled two iterations ahead
+  // (slot it & 1 holds the table of iteration it's group), so that the barrier that publishes
+  // a group's copies also publishes the next group's table and frees the other buffer.
   static __device__ void run(const StageArgs& A) {
     const Smem M = carve();
     const InstArgs& I = A.inst;
@@ -540,18 +546,19 @@ struct EulerStage {
     const int ng = (I.n_elem + EPB - 1) / EPB;
     int g = blockIdx.x;
     if (g < ng) fill_nb(I, g, M.nb);
+    if (g + (int)gridDim.x < ng) fill_nb(I, g + gridDim.x, M.nb + EPB * NF);
     __syncthreads();
     if (g < ng) issue(A, I, r, g, M.st, M.nb, need_un);
     cp_async_commit();
     for (int it = 0; g < ng; g += gridDim.x, ++it) {
       const int b = it & 1;
-      const int gn = g + gridDim.x;
-      if (gn < ng) fill_nb(I, gn, M.nb + (b ^ 1) * EPB * NF);
-      __syncthreads();  // neighbour table ready; the previous group no longer reads buffer b^1
+      const int gn = g + gridDim.x, gnn = gn + gridDim.x;
+      cp_async_wait_all();
+      __syncthreads();  // group g's copies are visible; every thread has left the previous group,
+                        // so buffer b^1 and neighbour slot b are free
       if (gn < ng) issue(A, I, r, gn, M.st + (b ^ 1) * ST_SIZE, M.nb + (b ^ 1) * EPB * NF, need_un);
       cp_async_commit();
-      cp_async_wait_prev();
-      __syncthreads();  // group g's copies (all threads') are visible
+      if (gnn < ng) fill_nb(I, gnn, M.nb + b * EPB * NF);  // read by the next iteration's issue
       compute(A, I, M.sm, r, g, M.st + b * ST_SIZE, need_un);
     }
   }
