@@ -194,6 +194,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-reacting", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--only", default="both", choices=["both", "fp32", "fp64", "reacting"],
                     help="precision(s) to time, or only the reacting workload (profiling runs)")
     ap.add_argument("--reacting-nel", type=int, default=48,
@@ -290,6 +291,7 @@ def main():
     cpu = None if args.no_cpu_baseline or ws > 1 else oracle_sample()
     batched = None if args.no_batched else run_batched(args)
     reacting = None if args.no_reacting else run_reacting(args)
+    adjoint = None if args.no_adjoint else run_adjoint(args)
     fp64 = None
     if ms64:
         fp64 = {"value": 3 * DOF * fp64_steps * ws / (ms64 * 1e-3), "unit": "DOF-updates/s", "steps": fp64_steps,
@@ -313,6 +315,7 @@ def main():
         "cpu_baseline": cpu,
         "batched": batched,
         "reacting": reacting,
+        "adjoint": adjoint,
     }
     print(json.dumps(line), flush=True)
     if ws > 1:
@@ -420,6 +423,51 @@ def run_reacting(args):
             "fp32_mixed": {"ms_per_step": ms32, "value": 3 * dof / (ms32 * 1e-3), "unit": "DOF-updates/s",
                            "note": "fluxes, gradients, viscous terms in FP32 (momentum flux shifted by "
                                    "p_ref = 101325 Pa); mixture state, Arrhenius source, update FP64"}}
+
+
+def run_adjoint(args):
+    """The differentiable workload: 2D Euler, N = 4, 128^2 elements, strong form + Rusanov,
+    200 SSP-RK3 steps (cfl 0.5) from a seeded acoustic state, checkpoints every 20 steps;
+    gradient of the quadrature-weighted L2 density mismatch to a seeded target with respect
+    to U0 and gamma through the hand-written residual/step adjoint.  Times the forward
+    rollout alone (graph-replayed steps) and forward + backward, in FP64 and FP32-mixed."""
+    import torch
+    from paper_2605_26388_b300 import dgsem, workloads as wl
+    from paper_2605_26388_b300.adjoint import rollout
+    nel, n_deg, steps, every = 128, 4, 200, 20
+    x, w, _ = dgsem.gll(n_deg)
+    U0 = torch.from_numpy(wl.acoustic_2d(nel, x, seed=3).reshape(4, -1)).cuda()
+    target = torch.from_numpy(wl.target_density_2d(nel, x, seed=4).reshape(-1)).cuda()
+    jac = (1.0 / nel / 2.0) ** 2
+    wq = torch.from_numpy(np.tile(np.multiply.outer(w, w).ravel(), nel * nel) * jac).cuda()
+    out = {"workload": "2D Euler N=4 128^2, 200 SSP-RK3 steps, checkpoints every 20, grad of the "
+                       "L2 density mismatch in U0 and gamma", "steps": steps}
+    for name, prec in (("fp64", dgsem.FP64), ("fp32_mixed", dgsem.FP32_MIXED)):
+        S = dgsem.Solver(dgsem.Mesh(2, n_deg, (nel, nel), (0.0, 0.0), (1.0, 1.0)), volume=dgsem.VOL_STRONG,
+                         surface=dgsem.SURF_RUSANOV, precision=prec, gamma=GAMMA)
+        S.set_state(U0)
+        dt = S.max_dt(0.5)
+        S.rk_step(dt, 3)
+        S.check()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        S.set_state(U0)
+        S.rk_step(dt, steps)
+        S.check()
+        t_fwd = time.perf_counter() - t0
+        U = U0.clone().requires_grad_(True)
+        gam = torch.tensor(GAMMA, dtype=torch.float64, requires_grad=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        loss = 0.5 * torch.sum(wq * (rollout(S, U, gam, dt, steps, every)[0] - target) ** 2)
+        loss.backward()
+        torch.cuda.synchronize()
+        t_grad = time.perf_counter() - t0
+        S.close()
+        out[name] = {"forward_ms": 1e3 * t_fwd, "gradient_ms": 1e3 * t_grad,
+                     "gradient_over_forward": t_grad / t_fwd,
+                     "note": "gradient = checkpointed forward + segment recompute + reverse step adjoints"}
+    return out
 
 
 def run_e2e(args, U0, dt, ws, barrier):
