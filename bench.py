@@ -455,12 +455,16 @@ def run_adjoint(args):
         S.rk_step(dt, steps)
         S.check()
         t_fwd = time.perf_counter() - t0
-        U = U0.clone().requires_grad_(True)
-        gam = torch.tensor(GAMMA, dtype=torch.float64, requires_grad=True)
+        def grad(n):
+            U = U0.clone().requires_grad_(True)
+            gam = torch.tensor(GAMMA, dtype=torch.float64, requires_grad=True)
+            loss = 0.5 * torch.sum(wq * (rollout(S, U, gam, dt, n, every)[0] - target) ** 2)
+            loss.backward()
+
+        grad(2 * every)  # warm-up: first use of the adjoint workspace, autograd and loss kernels
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        loss = 0.5 * torch.sum(wq * (rollout(S, U, gam, dt, steps, every)[0] - target) ** 2)
-        loss.backward()
+        grad(steps)
         torch.cuda.synchronize()
         t_grad = time.perf_counter() - t0
         S.close()
