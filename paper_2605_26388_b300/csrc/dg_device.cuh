@@ -67,6 +67,21 @@ __device__ __forceinline__ double f2d(float f) {
   return __hiloint2double((int)hi, (int)lo);
 }
 
+// 1/x in FP64 for |x| between 2^-125 and 2^125: an FP32 reciprocal seed (relative error
+// below 2^-21) refined by two Newton-Raphson steps y <- y + y (1 - x y), each of which
+// squares the error, so the result is within an ulp or two of the quotient.  Four FP64
+// operations instead of a full division (which issues at about a ninth of the FP64 FMA
+// rate on sm_103a); other x, zero, infinities and NaN take the division.
+__device__ __forceinline__ double rcp64(double x) {
+  const uint32_t ah = (uint32_t)__double2hiint(x) & 0x7fffffffu;
+  if (ah - 0x38200000u >= 0x47c00000u - 0x38200000u) return 1.0 / x;
+  double y = f2d(__fdividef(1.0f, d2f_rz(x)));
+  double e = fma(-x, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-x, y, 1.0);
+  return fma(y, e, y);
+}
+
 // Finite test on the exponent bits only (integer pipe).
 __device__ __forceinline__ bool finite64(double x) {
   return (((uint32_t)__double2hiint(x)) & 0x7ff00000u) != 0x7ff00000u;
@@ -74,15 +89,15 @@ __device__ __forceinline__ bool finite64(double x) {
 
 // ---------------------------------------------------------------------------------------
 // Arithmetic traits.  FP32 uses the fast reciprocal/rsqrt unit (a few ulp); FP64 uses
-// correctly rounded division and sqrt.
+// Newton-refined reciprocals (within two ulp) and the correctly rounded sqrt.
 // ---------------------------------------------------------------------------------------
 template <class R> struct Ar;
 
 template <> struct Ar<double> {
   static __device__ __forceinline__ double load(double x) { return x; }
   static __device__ __forceinline__ double widen(double x) { return x; }
-  static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
-  static __device__ __forceinline__ double div(double a, double b) { return a / b; }
+  static __device__ __forceinline__ double rcp(double x) { return rcp64(x); }
+  static __device__ __forceinline__ double div(double a, double b) { return a * rcp64(b); }
   static __device__ __forceinline__ double sqrt(double x) { return ::sqrt(x); }
   static __device__ __forceinline__ double log(double x) { return ::log(x); }
   static __device__ __forceinline__ double fmax(double a, double b) { return ::fmax(a, b); }
@@ -161,7 +176,7 @@ __device__ __forceinline__ float pdev(const double* u64, const float* u, double 
 template <int DIM>
 __device__ __forceinline__ double pdev(const double* u64, const double* u, double gm1,
                                        double p_ref, double& rhoe64) {
-  const double irho = __drcp_rn(u[0]);
+  const double irho = rcp64(u[0]);
   double m2 = __dmul_rn(u[1], u[1]);
 #pragma unroll
   for (int d = 1; d < DIM; ++d) m2 = __fma_rn(u[1 + d], u[1 + d], m2);

@@ -100,20 +100,6 @@ __device__ __forceinline__ double exp_tab(double x, const double* tab) {
   return __hiloint2double(__double2hiint(y) + ((n >> 6) << 20), __double2loint(y));
 }
 
-// 1/x in FP64 for positive x between 2^-125 and 2^125: an FP32 reciprocal seed (relative
-// error below 2^-21) refined by two Newton-Raphson steps y <- y + y (1 - x y), each of which
-// squares the error, so the result is within an ulp or two of the quotient.  Four FP64
-// operations instead of a full division; other x take the division.
-__device__ __forceinline__ double rcp64(double x) {
-  const uint32_t hi = (uint32_t)__double2hiint(x);
-  if (hi - 0x38200000u >= 0x47c00000u - 0x38200000u) return 1.0 / x;
-  double y = f2d(__fdividef(1.0f, d2f_rn(x)));
-  double e = fma(-x, y, 1.0);
-  y = fma(y, e, y);
-  e = fma(-x, y, 1.0);
-  return fma(y, e, y);
-}
-
 template <class T>
 __device__ __forceinline__ T pick3(int l, T a, T b, T c) {
   return l == 0 ? a : (l == 1 ? b : c);
