@@ -41,9 +41,9 @@ BYTES_PER_DOF_UPDATE = (16 + 24 + 24) / 3.0  # stage 1 reads U^n, writes U^1; st
 WORKLOAD = "tgv3d_euler_N4_64cube_ec_hllc_ssprk3"
 P_REF = 1.0 / (GAMMA * MACH ** 2)  # background pressure; the momentum flux carries p - P_REF
 
-# DRAM bytes per stage launch (mean of stages 1-3) of the current kernel, from the ncu
-# capture summarised in profiles/euler_stage_3d_n4_ec_hllc_tgv.md (32^3 case scaled by the
-# element count to 64^3); None where no capture of the current kernel exists.
+# DRAM bytes per stage launch (mean of stages 1-3) of the current kernel, from an ncu capture
+# of the 32^3 case scaled by the element count to 64^3; None where no capture of the current
+# kernel exists.
 TRAFFIC_PER_LAUNCH = {"fp32_mixed": 3.30e9, "fp64": None}
 
 
@@ -116,6 +116,24 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def max_over_ranks(x: float, ws: int) -> float:
+    """The largest x over all ranks of the initialised process group (x itself for one
+    rank); the device of the reduction follows the backend (CUDA for NCCL, host for gloo)."""
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_value(units_per_rank: float, ws: int, seconds: float) -> float:
+    """Whole-job throughput of N independent replicas: all ranks' units / slowest rank's time."""
+    return units_per_rank * ws / seconds
 
 
 def oracle_sample(seconds_hint: float = 10.0):
@@ -250,12 +268,7 @@ def main():
             torch.cuda.synchronize()
             barrier()
         S.check()
-        ms = e0.elapsed_time(e1)
-        if ws > 1:
-            import torch.distributed as dist
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(e0.elapsed_time(e1), ws)
         return S, dt, ms, clk.summary()
 
     fp64_steps = args.fp64_steps or max(3, args.steps // 10)
@@ -277,8 +290,7 @@ def main():
                 "kernel": "k_euler_stage<3,4,EC," + ("float" if prec == "fp32_mixed" else "double") + ">",
                 "avg_launch_ms": launch_ms, "alg_bytes_per_launch": alg}
 
-    total_updates = 3 * DOF * args.steps * ws
-    value = total_updates / (ms32 * 1e-3) if ms32 else None
+    value = weak_value(3 * DOF * args.steps, ws, ms32 * 1e-3) if ms32 else None
     if args.no_e2e or ms32 is None:
         e2e = None
     else:
@@ -294,7 +306,7 @@ def main():
     adjoint = None if args.no_adjoint else run_adjoint(args)
     fp64 = None
     if ms64:
-        fp64 = {"value": 3 * DOF * fp64_steps * ws / (ms64 * 1e-3), "unit": "DOF-updates/s", "steps": fp64_steps,
+        fp64 = {"value": weak_value(3 * DOF * fp64_steps, ws, ms64 * 1e-3), "unit": "DOF-updates/s", "steps": fp64_steps,
                 "ms_per_step": ms64 / fp64_steps, "roofline": roofline(ms64, fp64_steps, "fp64"),
                 "bound_note": "FP64-pipe bound on B300 (measured DFMA rate 475 G/s)", "clocks": clk64}
     line = {
@@ -498,11 +510,11 @@ def run_e2e(args, U0, dt, ws, barrier):
         Se.get_state(host_out)
     Se.check()
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
+    e2e_s = max_over_ranks(time.perf_counter() - t0, ws)
     barrier()
     Se.close()
     nbytes = U0.nbytes
-    return {"value": 3 * DOF * args.e2e_steps * ws / e2e_s, "unit": "DOF-updates/s",
+    return {"value": weak_value(3 * DOF * args.e2e_steps, ws, e2e_s), "unit": "DOF-updates/s",
             "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
             "note": "per step: dg_set_state from pinned host memory, one SSP-RK3 step, dg_get_state to pinned host memory"}
 
