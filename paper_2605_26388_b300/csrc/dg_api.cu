@@ -49,6 +49,11 @@ struct dg_ctx {
   dg::MechDev* d_mech = nullptr;
   double* fb = nullptr;
   std::vector<long long> fb_offs;
+  // primitive caches of the three state buffers and a scratch one (flux-type rows, then the
+  // FP64 temperature), and whether each cache matches its buffer's current contents
+  void* pc[4] = {nullptr, nullptr, nullptr, nullptr};
+  double* pT[4] = {nullptr, nullptr, nullptr, nullptr};
+  bool pvalid[3] = {false, false, false};
 };
 
 namespace {
@@ -270,10 +275,48 @@ void launch_args(const dg_ctx* c, dg::StageArgs& a, const double* U, const doubl
 
 // One fused stage over all instances: mode 0 writes L(U), mode 1 the stage update.  One
 // launch per instance, or one batched launch for all of them.
+// Which context state buffer p is (0..2), or -1 for a caller buffer.
+int buf_index(const dg_ctx* c, const double* p) {
+  for (int b = 0; b < 3; ++b)
+    if (c->buf[b] == p) return b;
+  return -1;
+}
+
+// Fill primitive cache slot k (0..2: a state buffer's, 3: scratch) from state U.
+dg_status fill_prims(dg_ctx* c, const double* U, int k, cudaStream_t s) {
+  const int fp32 = c->phys.precision == DG_FP32_MIXED;
+  for (size_t i = 0; i < c->inst.size(); ++i) {
+    cudaError_t e = dg::launch_react_prims(c->n_species, fp32, U, c->n_nodes_total, c->offs[i],
+                                           n_elem_of(c->inst[i]) * n_p_of(c->inst[i]), c->d_mech,
+                                           c->phys.p_ref, c->pc[k], c->pT[k], c->err, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "primitive cache launch");
+  }
+  return DG_OK;
+}
+
 dg_status run_stage_ns(dg_ctx* c, const double* U, const double* Un, double* out, int mode,
                        double ca, double cb, double dt, cudaStream_t s) {
   dg::ReactArgs a;
   std::memset(&a, 0, sizeof(a));
+  // the input's primitive cache: its buffer's if valid, else computed now
+  const int bin = buf_index(c, U);
+  const int kin = bin >= 0 ? bin : 3;
+  if (bin < 0 || !c->pvalid[bin]) {
+    dg_status st = fill_prims(c, U, kin, s);
+    if (st) return st;
+    if (bin >= 0) c->pvalid[bin] = true;
+  }
+  a.pin = c->pc[kin];
+  a.tin = c->pT[kin];
+  // the output's cache, written by the stage kernel when the output is a context buffer
+  const int bout = buf_index(c, out);
+  if (bout >= 0) {
+    if (mode == 1) {
+      a.pout = c->pc[bout];
+      a.tout = c->pT[bout];
+    }
+    c->pvalid[bout] = (mode == 1);
+  }
   a.U = U;
   a.Un = Un;
   a.out = out;
@@ -556,6 +599,15 @@ dg_status dg_init_mesh(const dg_mesh_desc* inst, int n_inst, const dg_physics* p
       dg_free(c);
       return DG_ENOMEM;
     }
+    const size_t rsz = phys->precision == DG_FP32_MIXED ? sizeof(float) : sizeof(double);
+    for (int k = 0; k < 4; ++k) {
+      if (cudaMalloc(&c->pc[k], 7 * rsz * (size_t)off) != cudaSuccess ||
+          cudaMalloc(&c->pT[k], sizeof(double) * (size_t)off) != cudaSuccess) {
+        cudaGetLastError();
+        dg_free(c);
+        return DG_ENOMEM;
+      }
+    }
     if (cudaMemcpy(c->d_mech, &mech, sizeof(mech), cudaMemcpyHostToDevice) != cudaSuccess) {
       cudaGetLastError();
       dg_free(c);
@@ -609,6 +661,7 @@ dg_status dg_instance_offset(const dg_ctx* c, int i, int64_t* offset) {
 dg_status dg_set_state(dg_ctx* c, const double* U) {
   if (!c) return DG_EINVAL;
   if (!U) return fail(c, DG_EINVAL, "null state pointer");
+  c->pvalid[c->cur] = false;
   const size_t bytes = sizeof(double) * (size_t)c->nv * c->n_nodes_total;
   cudaError_t e = cudaMemcpyAsync(c->buf[c->cur], U, bytes, cudaMemcpyDefault, c->stream);
   return e == cudaSuccess ? DG_OK : cuda_fail(c, e, "dg_set_state");
@@ -654,6 +707,11 @@ dg_status dg_rk_step(dg_ctx* c, double dt, int n_steps) {
   }
   const int triples = n_steps / 3;  // three steps bring the rotation back to buf[0]
   if (triples > 0) {
+    // Navier-Stokes: the graph starts from buf[0] with a valid primitive cache
+    if (c->ns && !c->pvalid[0]) {
+      if ((st = fill_prims(c, c->buf[0], 0, c->stream))) return st;
+      c->pvalid[0] = true;
+    }
     if (!c->gexec || c->g_dt != dt) {
       if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
       cudaGraph_t g;
@@ -665,6 +723,7 @@ dg_status dg_rk_step(dg_ctx* c, double dt, int n_steps) {
           cudaStreamEndCapture(c->cap, &g);
           cudaGetLastError();
           c->cur = saved;
+          for (bool& v : c->pvalid) v = false;
           return st;
         }
       }
@@ -678,7 +737,10 @@ dg_status dg_rk_step(dg_ctx* c, double dt, int n_steps) {
     }
     for (int k = 0; k < triples; ++k) {
       cudaError_t e = cudaGraphLaunch(c->gexec, c->stream);
-      if (e != cudaSuccess) return cuda_fail(c, e, "graph launch");
+      if (e != cudaSuccess) {
+        for (bool& v : c->pvalid) v = false;
+        return cuda_fail(c, e, "graph launch");
+      }
     }
     n_steps -= 3 * triples;
   }
@@ -901,6 +963,10 @@ void dg_free(dg_ctx* c) {
   if (c->gacc) cudaFree(c->gacc);
   if (c->d_mech) cudaFree(c->d_mech);
   if (c->fb) cudaFree(c->fb);
+  for (int k = 0; k < 4; ++k) {
+    if (c->pc[k]) cudaFree(c->pc[k]);
+    if (c->pT[k]) cudaFree(c->pT[k]);
+  }
   delete c;
 }
 

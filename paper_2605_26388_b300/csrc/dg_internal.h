@@ -150,6 +150,10 @@ struct ReactArgs {
   double* out;         // stage output (mode 1) or L(U) (mode 0)
   unsigned* err;       // device error word
   void* fb;            // face buffer of this instance (flux type): [elem][face][4][(N+1)^2]
+  const void* pin;     // primitive cache of U (flux type, 7 rows at `stride`) ...
+  const double* tin;   //   ... and its FP64 temperature
+  void* pout;          // primitive cache of the stage output (mode 1; null: not written)
+  double* tout;
   const MechDev* mech; // device copy of the mechanism
   long long stride;    // per-variable stride of the SoA state
   long long base;      // node offset of the instance
@@ -174,6 +178,11 @@ cudaError_t prepare_reacting(int N, int ns, int fp32);
 // One stage (or residual) over one instance: the BR1 face pass, then the fused stage; fp32
 // selects FP32 flux arithmetic (mixture, source and update stay FP64).
 cudaError_t launch_reacting(int N, int ns, int fp32, const ReactArgs& a, cudaStream_t s);
+// Primitive cache (u, v, w, T, p - p_ref, a, c_p in the flux type; T in FP64) of the nodes
+// [base, base + n_nodes) of a state; flags rho <= 0 or T <= 0 in *err.
+cudaError_t launch_react_prims(int ns, int fp32, const double* U, long long stride, long long base,
+                               long long n_nodes, const MechDev* mech, double p_ref, void* P, double* T64,
+                               unsigned* err, cudaStream_t s);
 // Largest |u| + a (frozen mixture sound speed) and largest 1/rho over one instance,
 // atomically max-ed into out2[0] and out2[1] (bit patterns of non-negative doubles).
 cudaError_t launch_max_speed_mix(int ns, const double* U, long long stride, long long base,

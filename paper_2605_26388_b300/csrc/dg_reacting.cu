@@ -16,6 +16,12 @@
 // The gradient is recomputed in launch 2 from the same inputs by the same code, so the
 // neighbour's face value and the own one come from identical arithmetic.
 //
+// Primitive cache: the mixture state of every node (u, v, w, T, p - p_ref, a, c_p in R and T
+// in FP64) is computed once per stage, by the stage kernel for its output state (or by
+// k_react_prims for a state that did not come from a stage), and both launches of the next
+// stage read it for their own nodes and the neighbours' face traces instead of evaluating
+// the FP64 mixture again (five times per node otherwise).
+//
 // Precision: the mixture state of every node (T, p, sound speed, c_p from the FP64 conserved
 // variables), the Arrhenius source and the stage update are FP64 in both modes; gradients,
 // viscous and inviscid fluxes, the Rusanov flux, the contractions and the lifts run in the
@@ -34,6 +40,7 @@ namespace {
 
 constexpr int kRT = 128;
 constexpr int NPR = 6;  // staged primitives per node: u, v, w, T, p - p_ref, a
+constexpr int NPC = 7;  // cached per node in R: u, v, w, T, p - p_ref, a, c_p (+ T in FP64)
 
 template <int N, int NS, class R>
 struct RG {
@@ -60,9 +67,7 @@ struct RG {
   }
   // gradient kernel, per element (R): primitives and trace primitives
   static constexpr int G_P = 0, G_PT = NPR * NP, G_SIZE = NPR * NP + 6 * NPR * NFN;
-  static constexpr size_t grad_smem() {
-    return sizeof(double) * (size_t)(3 * NS) + sizeof(R) * (size_t)(N1 * N1 + EPB * G_SIZE);
-  }
+  static constexpr size_t grad_smem() { return sizeof(R) * (size_t)(N1 * N1 + EPB * G_SIZE); }
 };
 
 template <int N1>
@@ -139,26 +144,20 @@ __device__ __forceinline__ Mx mixture(const double* u, const double* sp) {
   return m;
 }
 
-// Stage one node: conserved variables (R) and primitives (u, v, w, T, p - p_ref, a) in R;
-// returns the positivity flag (rho > 0 and T > 0, decided in FP64).
+// Mixture state of one node into the primitive cache (R rows u, v, w, T, p - p_ref, a, c_p at
+// stride `stride`, T in FP64); returns the positivity flag (rho > 0 and T > 0, in FP64).
 template <int NS, class R>
-__device__ __forceinline__ unsigned stage_node(const double* u, const double* sp, double p_ref, R* us,
-                                               int us_stride, R* pr, int pr_stride, double* cpT_out) {
+__device__ __forceinline__ unsigned write_prims(const double* u, const double* sp, double p_ref, R* P,
+                                                double* T64, long long stride, long long gi) {
   const Mx m = mixture<NS>(u, sp);
-  if (us) {
-#pragma unroll
-    for (int v = 0; v < NS + 4; ++v) us[v * us_stride] = Ar<R>::load(u[v]);
-  }
-  pr[0] = Ar<R>::load(m.v[0]);
-  pr[pr_stride] = Ar<R>::load(m.v[1]);
-  pr[2 * pr_stride] = Ar<R>::load(m.v[2]);
-  pr[3 * pr_stride] = Ar<R>::load(m.T);
-  pr[4 * pr_stride] = Ar<R>::load(m.p - p_ref);
-  pr[5 * pr_stride] = Ar<R>::load(m.a);
-  if (cpT_out) {
-    cpT_out[0] = m.cp;
-    cpT_out[1] = m.T;
-  }
+  P[gi] = Ar<R>::load(m.v[0]);
+  P[stride + gi] = Ar<R>::load(m.v[1]);
+  P[2 * stride + gi] = Ar<R>::load(m.v[2]);
+  P[3 * stride + gi] = Ar<R>::load(m.T);
+  P[4 * stride + gi] = Ar<R>::load(m.p - p_ref);
+  P[5 * stride + gi] = Ar<R>::load(m.a);
+  P[6 * stride + gi] = Ar<R>::load(m.cp);
+  T64[gi] = m.T;
   return (m.rho > 0.0 && m.T > 0.0) ? 0u : 2u;
 }
 
@@ -250,27 +249,32 @@ struct RS {
   }
 };
 
-// Own primitives (and U in R) of the CTA's elements, and the neighbours' face traces.
-template <int N, int NS, class R, bool KEEP_U>
-__device__ __forceinline__ unsigned load_element(const ReactArgs& a, int e0, R* smem_el, int esz, int off_p,
-                                                 int off_pt, int off_us, int off_ut, const double* sp,
-                                                 double* u_own, double* cpT_own) {
+// Own primitives (and U in R) of the CTA's elements and the neighbours' face traces, from the
+// primitive cache (rows 0..NROW-1) and, with KEEP_U, the FP64 state; the own nodes' FP64
+// state is returned in u_own and c_p, T (FP64) in cpT_own.
+template <int N, int NS, class R, bool KEEP_U, int NROW>
+__device__ __forceinline__ void load_element(const ReactArgs& a, int e0, R* smem_el, int esz, int off_p,
+                                             int off_pt, int off_us, int off_ut, double* u_own, double* cpT_own) {
   using G = RG<N, NS, R>;
-  unsigned flag = 0;
   const int t = threadIdx.x;
+  const R* P = reinterpret_cast<const R*>(a.pin);
   if (t < G::EPB * G::NP) {
     const int el = t / G::NP, q = t % G::NP, e = e0 + el;
     if (e < a.n_elem) {
       R* sm = smem_el + el * esz;
       const long long gi = a.base + (long long)e * G::NP + q;
-      double u[G::NV];
 #pragma unroll
-      for (int v = 0; v < G::NV; ++v) u[v] = a.U[v * a.stride + gi];
-      flag |= stage_node<NS, R>(u, sp, a.p_ref, KEEP_U ? sm + off_us + q : nullptr, G::NP, sm + off_p + q,
-                                G::NP, cpT_own);
-      if (u_own) {
+      for (int c = 0; c < NROW; ++c) sm[off_p + c * G::NP + q] = P[c * a.stride + gi];
+      if (cpT_own) {
+        cpT_own[0] = Ar<R>::widen(P[6 * a.stride + gi]);
+        cpT_own[1] = a.tin[gi];
+      }
+      if (KEEP_U) {
 #pragma unroll
-        for (int v = 0; v < G::NV; ++v) u_own[v] = u[v];
+        for (int v = 0; v < G::NV; ++v) {
+          u_own[v] = a.U[v * a.stride + gi];
+          sm[off_us + v * G::NP + q] = Ar<R>::load(u_own[v]);
+        }
       }
     }
   }
@@ -282,13 +286,13 @@ __device__ __forceinline__ unsigned load_element(const ReactArgs& a, int e0, R* 
     const int l = f >> 1, side = f & 1;
     const int en = neighbour(a.nel, e, l, side ? 1 : -1);
     const long long gi = a.base + (long long)en * G::NP + face_node<G::N1>(l, side ^ 1, jf);
-    double u[G::NV];
 #pragma unroll
-    for (int v = 0; v < G::NV; ++v) u[v] = a.U[v * a.stride + gi];
-    flag |= stage_node<NS, R>(u, sp, a.p_ref, KEEP_U ? sm + off_ut + f * G::NV * G::NFN + jf : nullptr,
-                              G::NFN, sm + off_pt + f * NPR * G::NFN + jf, G::NFN, nullptr);
+    for (int c = 0; c < NROW; ++c) sm[off_pt + (f * NPR + c) * G::NFN + jf] = P[c * a.stride + gi];
+    if (KEEP_U) {
+#pragma unroll
+      for (int v = 0; v < G::NV; ++v) sm[off_ut + (f * G::NV + v) * G::NFN + jf] = Ar<R>::load(a.U[v * a.stride + gi]);
+    }
   }
-  return flag;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -298,17 +302,14 @@ template <int N, int NS, class R>
 __global__ void __launch_bounds__(kRT) k_br1_faces(const ReactArgs a) {
   using G = RG<N, NS, R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* sp = reinterpret_cast<double*>(smem_raw);
-  R* D = reinterpret_cast<R*>(sp + 3 * NS);
+  R* D = reinterpret_cast<R*>(smem_raw);
   R* el_base = D + G::N1 * G::N1;
   const int t = threadIdx.x;
   for (int k = t; k < G::N1 * G::N1; k += kRT) D[k] = Ar<R>::load(a.D[k]);
-  load_species<NS>(a.mech, sp, 3);
-  __syncthreads();
   const RS<R> rs(a);
   const int e0 = blockIdx.x * G::EPB;
   double cpT[2] = {0.0, 0.0};
-  load_element<N, NS, R, false>(a, e0, el_base, G::G_SIZE, G::G_P, G::G_PT, 0, 0, sp, nullptr, cpT);
+  load_element<N, NS, R, false, 4>(a, e0, el_base, G::G_SIZE, G::G_P, G::G_PT, 0, 0, nullptr, cpT);
   __syncthreads();
   if (t >= G::EPB * G::NP) return;
   const int el = t / G::NP, q = t % G::NP, e = e0 + el;
@@ -368,8 +369,8 @@ __global__ void __launch_bounds__(kRT) k_reacting_stage(const ReactArgs a) {
   const RS<R> rs(a);
   double u64[NV];
   double cpT[2] = {0.0, 1.0};
-  unsigned flag = load_element<N, NS, R, true>(a, e0, el_base, G::E_SIZE, G::E_P, G::E_PT, G::E_US, G::E_UT, sp,
-                                               u64, cpT);
+  load_element<N, NS, R, true, NPR>(a, e0, el_base, G::E_SIZE, G::E_P, G::E_PT, G::E_US, G::E_UT, u64, cpT);
+  unsigned flag = 0;
   __syncthreads();
 
   const bool node_thread = t < G::EPB * NP;
@@ -508,18 +509,40 @@ __global__ void __launch_bounds__(kRT) k_reacting_stage(const ReactArgs a) {
 
   const long long gi = a.base + (long long)e * NP + q;
   bool finite = true;
+  double x[NV];
 #pragma unroll
   for (int k = 0; k < NV; ++k) {
-    double x = r64[k];
+    x[k] = r64[k];
     if (a.mode == 1) {
-      x = fma(a.cb, u64[k], a.cbdt * r64[k]);
-      if (a.need_un) x = fma(a.ca, a.Un[k * a.stride + gi], x);
+      x[k] = fma(a.cb, u64[k], a.cbdt * r64[k]);
+      if (a.need_un) x[k] = fma(a.ca, a.Un[k * a.stride + gi], x[k]);
     }
-    finite = finite && finite64(x);
-    a.out[k * a.stride + gi] = x;
+    finite = finite && finite64(x[k]);
+    a.out[k * a.stride + gi] = x[k];
   }
+  // the primitive cache of the new state, read by the next stage
+  if (a.mode == 1 && a.pout) flag |= write_prims<NS, R>(x, sp, a.p_ref, reinterpret_cast<R*>(a.pout), a.tout,
+                                                        a.stride, gi);
   if (!finite) flag |= 1u;
   if (flag) atomicOr(a.err, flag);
+}
+
+// The primitive cache of a state that did not come from a stage launch.
+template <int NS, class R>
+__global__ void k_react_prims(const double* U, long long stride, long long base, long long n,
+                              const MechDev* __restrict__ mech, double p_ref, R* P, double* T64, unsigned* err) {
+  __shared__ double sp[4 * NS];
+  load_species<NS>(mech, sp, 4);
+  __syncthreads();
+  unsigned flag = 0;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
+       q += (long long)gridDim.x * blockDim.x) {
+    double u[NS + 4];
+#pragma unroll
+    for (int v = 0; v < NS + 4; ++v) u[v] = U[v * stride + base + q];
+    flag |= write_prims<NS, R>(u, sp, p_ref, P, T64, stride, base + q);
+  }
+  if (flag) atomicOr(err, flag);
 }
 
 // Largest |u| + a and largest 1/rho over the nodes of one instance.
@@ -609,6 +632,20 @@ cudaError_t launch_reacting(int N, int ns, int fp32, const ReactArgs& a, cudaStr
 #define DG_L(n, sp) (fp32 ? launch_one<n, sp, float>(a, s) : launch_one<n, sp, double>(a, s))
   DG_REACT_DISPATCH(DG_L)
 #undef DG_L
+}
+
+cudaError_t launch_react_prims(int ns, int fp32, const double* U, long long stride, long long base,
+                               long long n_nodes, const MechDev* mech, double p_ref, void* P, double* T64,
+                               unsigned* err, cudaStream_t s) {
+  if (n_nodes <= 0) return cudaSuccess;
+  const long long want = (n_nodes + 255) / 256;
+  const unsigned grid = (unsigned)(want < 148 * 16 ? want : 148 * 16);
+  if (ns == 1 && fp32) k_react_prims<1, float><<<grid, 256, 0, s>>>(U, stride, base, n_nodes, mech, p_ref, (float*)P, T64, err);
+  else if (ns == 1) k_react_prims<1, double><<<grid, 256, 0, s>>>(U, stride, base, n_nodes, mech, p_ref, (double*)P, T64, err);
+  else if (ns == 5 && fp32) k_react_prims<5, float><<<grid, 256, 0, s>>>(U, stride, base, n_nodes, mech, p_ref, (float*)P, T64, err);
+  else if (ns == 5) k_react_prims<5, double><<<grid, 256, 0, s>>>(U, stride, base, n_nodes, mech, p_ref, (double*)P, T64, err);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
 }
 
 cudaError_t launch_max_speed_mix(int ns, const double* U, long long stride, long long base,
