@@ -47,6 +47,27 @@ P_REF = 1.0 / (GAMMA * MACH ** 2)  # background pressure; the momentum flux carr
 TRAFFIC_PER_LAUNCH = {"fp32_mixed": 3.30e9, "fp64": None}
 
 
+# FP64 instructions (thread level) per FP64 stage launch at 64^3, from an ncu capture of the
+# 32^3 case (2.757e9, smsp__sass_thread_inst_executed_op_fp64_pred_on) scaled by the element
+# count; None once the kernel changes.
+FP64_INSTR_PER_LAUNCH = 2.757e9 * 8
+# FP64 peak from the nominal B300 rate (1.25 TFLOP/s dense = 0.625 T FP64 FMA/s).
+FP64_PEAK_GINSTR = 625.0
+
+
+def fp64_pipe(launch_ms):
+    """Executed FP64 instructions per second of the FP64 stage kernel against the nominal
+    FP64 rate (each DFMA counted once)."""
+    if FP64_INSTR_PER_LAUNCH is None:
+        return None
+    ach = FP64_INSTR_PER_LAUNCH / (launch_ms * 1e-3) / 1e9
+    return {"bound": "alu", "unit": "G FP64 instr/s", "achieved": ach, "peak": FP64_PEAK_GINSTR,
+            "frac": ach / FP64_PEAK_GINSTR, "peak_kind": "nominal (1.25 TFLOP/s FP64 / 2)",
+            "instr_per_launch": FP64_INSTR_PER_LAUNCH,
+            "note": "executed FP64 instructions from ncu (not algorithmic flops); ncu reports the FP64 "
+                    "pipe 86% busy"}
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -308,7 +329,8 @@ def main():
     if ms64:
         fp64 = {"value": weak_value(3 * DOF * fp64_steps, ws, ms64 * 1e-3), "unit": "DOF-updates/s", "steps": fp64_steps,
                 "ms_per_step": ms64 / fp64_steps, "roofline": roofline(ms64, fp64_steps, "fp64"),
-                "bound_note": "FP64-pipe bound on B300 (measured DFMA rate 475 G/s)", "clocks": clk64}
+                "bound_note": "FP64-pipe bound on B300",
+                "fp64_pipe": fp64_pipe(ms64 / (3 * fp64_steps)), "clocks": clk64}
     line = {
         "metric": "RK-stage DOF-updates/s (3D Euler DGSEM N=4, TGV Ma 0.1, EC flux differencing + HLLC; FP32-mixed vs FP64)",
         "value": value, "unit": "DOF-updates/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
