@@ -152,6 +152,7 @@ def lib():
         _lib.orc_max_dt.argtypes = [pp, dp, C.c_double, dp]
         _lib.orc_rhs_jvp.argtypes = [pp, dp, dp, C.c_double, dp, dp]
         _lib.orc_rhs_vjp_brute.argtypes = [pp, dp, dp, dp, dp]
+        _lib.orc_rollout_grad.argtypes = [pp, dp, dp, dp, C.c_double, C.c_int, dp, dp]
         _lib.orc_arrhenius.argtypes = [C.POINTER(_Mech), C.c_int, C.c_double, dp, dp]
         _lib.orc_chem_source.argtypes = [pp, dp, dp]
         _lib.orc_mixture.argtypes = [pp, dp, dp, dp]
@@ -282,6 +283,21 @@ def max_dt(P: Problem, U: np.ndarray, cfl: float) -> float:
     c = P._c()
     _check(lib().orc_max_dt(C.byref(c), _ptr(U), cfl, _ptr(out)), "max_dt")
     return float(out[0])
+
+
+def rollout_grad(P: Problem, U0: np.ndarray, target: np.ndarray, wq: np.ndarray, dt: float, n_steps: int):
+    """Gradient of J = 1/2 sum wq (rho_final - target)^2 after n_steps SSP-RK3 steps from U0,
+    with respect to U0 and gamma, by exact forward mode (one dual-number rollout per
+    unknown; tiny meshes).  Built on the pinned dual-number residual."""
+    U0 = np.ascontiguousarray(U0, dtype=np.float64).reshape(P.shape)
+    target = np.ascontiguousarray(target, dtype=np.float64).reshape(P.shape[1:])
+    wq = np.ascontiguousarray(wq, dtype=np.float64).reshape(P.shape[1:])
+    g = np.zeros_like(U0)
+    gg = C.c_double()
+    c = P._c()
+    _check(lib().orc_rollout_grad(C.byref(c), _ptr(U0), _ptr(target), _ptr(wq), dt, n_steps, _ptr(g),
+                                  C.byref(gg)), "rollout_grad")
+    return g, gg.value
 
 
 def arrhenius(mech: dict, r: int, T: float):

@@ -1044,6 +1044,44 @@ int orc_rhs_vjp_brute(const OrcProblem* P, const double* U, const double* lam, d
   return 0;
 }
 
+// Gradient of the rollout loss J = 1/2 sum_e sum_i wq[e][i] (rho_final - target)^2, where
+// rho_final is the density after n_steps SSP-RK3 steps (App. B, Shu-Osher form) of size dt
+// from U0 (strong or weak volume form, Rusanov flux), with respect to every entry of U0
+// (grad, layout of U0) and gamma (*ggam).  Exact forward mode: one dual-number rollout per
+// direction (tiny meshes only); an independent route to what the adjoint computes in reverse.
+int orc_rollout_grad(const OrcProblem* P, const double* U0, const double* target, const double* wq,
+                     double dt, int n_steps, double* grad, double* ggam) {
+  int rc = check_problem(*P);
+  if (rc) return rc;
+  if ((P->volume != ORC_VOL_STRONG && P->volume != ORC_VOL_WEAK) || P->surface != ORC_SURF_RUSANOV ||
+      P->equations != ORC_EULER)
+    return -6;
+  Mesh M(*P);
+  Ops ops(P->N);
+  const size_t stride = (size_t)M.n_elem * M.n_nodes;
+  const size_t n = (size_t)n_vars(*P) * stride;
+  if (n > 4000 || n_steps < 0) return -1;
+  std::vector<Dual> Un(n), U1(n), U2(n), L(n);
+  for (size_t dir = 0; dir <= n; ++dir) {
+    for (size_t q = 0; q < n; ++q) Un[q] = Dual(U0[q], q == dir ? 1.0 : 0.0);
+    const Dual g(P->gamma, dir == n ? 1.0 : 0.0);
+    for (int s = 0; s < n_steps; ++s) {
+      for (int e = 0; e < M.n_elem; ++e) element_residual_t<Dual>(*P, M, ops, Un.data(), g, e, L.data());
+      for (size_t q = 0; q < n; ++q) U1[q] = Un[q] + Dual(dt) * L[q];
+      for (int e = 0; e < M.n_elem; ++e) element_residual_t<Dual>(*P, M, ops, U1.data(), g, e, L.data());
+      for (size_t q = 0; q < n; ++q) U2[q] = Dual(0.75) * Un[q] + Dual(0.25) * (U1[q] + Dual(dt) * L[q]);
+      for (int e = 0; e < M.n_elem; ++e) element_residual_t<Dual>(*P, M, ops, U2.data(), g, e, L.data());
+      for (size_t q = 0; q < n; ++q)
+        Un[q] = Dual(1.0 / 3.0) * Un[q] + Dual(2.0 / 3.0) * (U2[q] + Dual(dt) * L[q]);
+    }
+    double dJ = 0.0;  // dJ = sum wq (rho - target) drho
+    for (size_t q = 0; q < stride; ++q) dJ += wq[q] * (Un[q].v - target[q]) * Un[q].d;
+    if (dir < n) grad[dir] = dJ;
+    else *ggam = dJ;
+  }
+  return 0;
+}
+
 // Convective time-step bound (Sec. 3.1.2 Eq. dt_hyp; App. B):
 //   dt = cfl * dx_min / ((2N+1) lambda_max),  lambda_max = max over nodes of |u| + a.
 // READING: |u| is the speed (vector magnitude); the SSP coefficient of SSP-RK3 is 1, so

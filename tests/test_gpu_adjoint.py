@@ -160,3 +160,29 @@ def test_checkpointed_gradient_vs_finite_differences(env, orc):
     rel = float(torch.linalg.norm(U32.grad - gU) / torch.linalg.norm(gU))
     assert rel <= 1e-4, rel
     assert abs(float(g32.grad) - gG) <= 1e-4 * abs(gG)
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 1e-4)])
+def test_rollout_gradient_matches_oracle(env, orc, prec, tol):
+    """The checkpointed rollout gradient (segments of 3 steps over 10 steps, the last one
+    partial) in U0 and gamma against the oracle's exact forward-mode gradient."""
+    torch, dg = env
+    from paper_2605_26388_b300.adjoint import rollout
+    P, S = make(orc, dg, 2, 2, 2, 0, prec=prec)
+    U0 = state(orc, P, 7)
+    rng = np.random.default_rng(3)
+    target = U0[0] * (1.0 + 0.01 * rng.standard_normal(U0[0].shape))
+    _, w = orc.gll(2)
+    wq = np.tile(np.multiply.outer(w, w).ravel(), (P.n_elem, 1)) * 0.0625
+    dt, steps = 2e-3, 10
+    g_ref, gg_ref = orc.rollout_grad(P, U0, target, wq, dt, steps)
+    U = dev(torch, U0).requires_grad_(True)
+    gam = torch.tensor(GAMMA, dtype=torch.float64, requires_grad=True)
+    tg = torch.from_numpy(target.reshape(-1)).cuda()
+    wqt = torch.from_numpy(wq.reshape(-1)).cuda()
+    UT = rollout(S, U, gam, dt, steps, 3)
+    loss = 0.5 * torch.sum(wqt * (UT[0] - tg) ** 2)
+    loss.backward()
+    got = U.grad.cpu().numpy().reshape(U0.shape)
+    assert np.linalg.norm(got - g_ref) <= tol * np.linalg.norm(g_ref)
+    assert abs(float(gam.grad) - gg_ref) <= tol * abs(gg_ref)

@@ -55,3 +55,33 @@ def test_brute_force_vjp_is_the_transpose(orc):
     assert abs(np.sum(lam * JV) - np.sum(Ub * V)) <= 1e-12 * np.sum(np.abs(lam * JV))
     _, Jg = orc.rhs_jvp(P, U, None, 1.0)
     assert abs(np.sum(lam * Jg) - gb) <= 1e-12 * np.sum(np.abs(lam * Jg))
+
+
+def test_rollout_gradient_against_central_differences(orc):
+    """Exact forward-mode gradient of the rollout loss (U0 and gamma) against central
+    differences of the pinned FP64 rollout."""
+    P = problem(orc, 2, 2, 2, 0)
+    U0 = state(orc, P, 7)
+    rng = np.random.default_rng(3)
+    target = U0[0] * (1.0 + 0.01 * rng.standard_normal(U0[0].shape))
+    _, w = orc.gll(2)
+    wq = np.tile(np.multiply.outer(w, w).ravel(), (P.n_elem, 1)) * 0.0625
+    dt, steps = 2e-3, 7
+
+    def loss(U, gamma):
+        Pg = problem(orc, 2, 2, 2, 0)
+        Pg.gamma = gamma
+        UT = orc.rk3(Pg, U.copy(), dt, steps)
+        return 0.5 * np.sum(wq * (UT[0] - target) ** 2)
+
+    g, gg = orc.rollout_grad(P, U0, target, wq, dt, steps)
+    h = 1e-6
+    for k in [0, 5, 17, 40, 77, U0.size - 1]:
+        E = np.zeros(U0.size)
+        E[k] = h
+        E = E.reshape(U0.shape)
+        fd = (loss(U0 + E, GAMMA) - loss(U0 - E, GAMMA)) / (2 * h)
+        # central differences carry ~1e-12 of rounding noise at h = 1e-6
+        assert abs(fd - g.reshape(-1)[k]) <= 1e-6 * np.max(np.abs(g)), (k, fd, g.reshape(-1)[k])
+    fdg = (loss(U0, GAMMA + h) - loss(U0, GAMMA - h)) / (2 * h)
+    assert abs(fdg - gg) <= 1e-6 * abs(fdg)
