@@ -45,7 +45,7 @@ struct Batched {
   }
 
 template <int DIM, bool EC, class R, int GS>
-__global__ void __launch_bounds__(Batched<DIM, EC, R, GS>::BT, (Batched<DIM, EC, R, GS>::BT <= 128 ? 4 : 2))
+__global__ void __launch_bounds__(Batched<DIM, EC, R, GS>::BT, (Batched<DIM, EC, R, GS>::BT <= 128 ? (sizeof(R) == 4 ? 6 : 4) : 2))
     k_euler_stage_batched(const StageArgs A) {
   using B = Batched<DIM, EC, R, GS>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
