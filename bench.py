@@ -40,6 +40,16 @@ DOF = NEL ** 3 * NP * NV
 BYTES_PER_DOF_UPDATE = (16 + 24 + 24) / 3.0  # stage 1 reads U^n, writes U^1; stages 2-3 read 2, write 1
 WORKLOAD = "tgv3d_euler_N4_64cube_ec_hllc_ssprk3"
 P_REF = 1.0 / (GAMMA * MACH ** 2)  # background pressure; the momentum flux carries p - P_REF
+METRIC = "RK-stage DOF-updates/s (3D Euler DGSEM N=4, TGV Ma 0.1, EC flux differencing + HLLC; FP32-mixed vs FP64)"
+
+
+def workload_config(nel, ws=1):
+    """The `config` object of both arms (the workload, not a model)."""
+    return {"workload": WORKLOAD if nel == 64 else f"{WORKLOAD} (profiling size {nel}^3)",
+            "mesh": f"{nel}^3 periodic on [0,2pi]^3", "N": N, "dof": nel ** 3 * NP * NV,
+            "cfl": CFL, "p_ref": P_REF,
+            "l2": "inputs larger than L2: three state buffers of %.2f GB per replica" % (nel ** 3 * NP * NV * 8 / 1e9),
+            "parallelism": f"replicas x{ws}"}
 
 # DRAM bytes per stage launch (mean of stages 1-3) of the current kernel, from an ncu capture
 # of the 32^3 case scaled by the element count to 64^3; None where no capture of the current
@@ -208,14 +218,14 @@ def run_reference(args):
     t_all = sum(per_step)
     value = 3 * dof * args.steps / t_all
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    line = {"impl": "reference", "metric": "RK-stage DOF-updates/s (3D Euler DGSEM N=4, TGV, EC+HLLC)",
+    line = {"impl": "reference", "metric": METRIC,
             "value": value, "unit": "DOF-updates/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_all / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": f"each step: one SSP-RK3 step on a {nel}^3 sub-mesh "
-                                                        f"of the same problem ({dof} DOF) on the host CPU"},
+            "config": workload_config(NEL, 1),
             "cpu_baseline": {"value": value, "unit": "DOF-updates/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{args.steps} SSP-RK3 steps on a {nel}^3 sub-mesh, FP64"},
+                             "sample": f"each step: one SSP-RK3 step of the same problem on a {nel}^3 "
+                                       f"sub-mesh ({dof} DOF), FP64, on the host cores; {args.steps} steps"},
             "e2e": {"value": value, "unit": "DOF-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -332,15 +342,11 @@ def main():
                 "bound_note": "FP64-pipe bound on B300",
                 "fp64_pipe": fp64_pipe(ms64 / (3 * fp64_steps)), "clocks": clk64}
     line = {
-        "metric": "RK-stage DOF-updates/s (3D Euler DGSEM N=4, TGV Ma 0.1, EC flux differencing + HLLC; FP32-mixed vs FP64)",
+        "metric": METRIC,
         "value": value, "unit": "DOF-updates/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms32 / args.steps if ms32 else None, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 flux / f64 state", "data": "synthetic",
-        "config": {"workload": WORKLOAD if NEL == 64 else f"{WORKLOAD} (profiling size {NEL}^3)",
-                   "mesh": f"{NEL}^3 periodic on [0,2pi]^3", "N": N, "dof": DOF,
-                   "precision": "fp32_mixed", "dt": dt, "cfl": CFL, "p_ref": P_REF,
-                   "l2": "inputs larger than L2: three state buffers of %.2f GB per replica" % (DOF * 8 / 1e9),
-                   "parallelism": f"replicas x{ws}"},
+        "config": dict(workload_config(NEL, ws), precision="fp32_mixed", dt=dt),
         "roofline": roofline(ms32, args.steps, "fp32_mixed") if ms32 else None,
         "fp64": fp64,
         "clocks": clk32 if clk32 else clk64,
