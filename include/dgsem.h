@@ -177,16 +177,24 @@ DG_API dg_status dg_rk_step(dg_ctx* ctx, double dt, int n_steps);
  *   *gammabar += lam . dL/dgamma     (host double)
  * Non-smooth points follow the forward evaluation: the larger Rusanov signal speed (the left
  * one on a tie) carries the derivative, and d|u|/du = sign(u) with sign(0) = 0.  Ubar must not
- * alias U or lam.  Allocates the adjoint workspace on first use; synchronizes the stream. */
+ * alias U or lam.  Allocates the adjoint workspace on first use.  The gamma contribution is
+ * added to a device accumulator of the context; with gammabar != NULL the call synchronizes
+ * the stream, adds the accumulator to *gammabar and resets it; with gammabar == NULL it stays
+ * on the device (no synchronization) until dg_adjoint_gammabar(). */
 DG_API dg_status dg_rhs_vjp(dg_ctx* ctx, const double* U, const double* lam, double* Ubar,
                             double* gammabar);
 
 /* Adjoint of one SSP-RK3 step from Un with step dt (App. B, Shu-Osher form, stages
  * recomputed from Un): on entry lam = dJ/dU^{n+1}, on exit lam = dJ/dU^n; *gammabar (host)
  * += dJ/dgamma through this step.  The positivity floor, if enabled, is not differentiated.
- * lam must not alias Un.  Synchronizes the stream. */
+ * lam must not alias Un.  gammabar as for dg_rhs_vjp: NULL keeps the contribution in the
+ * context's device accumulator and the call stays asynchronous. */
 DG_API dg_status dg_rk_step_vjp(dg_ctx* ctx, const double* Un, double dt, double* lam,
                                 double* gammabar);
+
+/* Synchronize the stream and add the gamma contributions accumulated on the device by
+ * adjoint calls made with gammabar == NULL to *gammabar (host); resets the accumulator. */
+DG_API dg_status dg_adjoint_gammabar(dg_ctx* ctx, double* gammabar);
 
 /* Launch modes for contexts with several instances. */
 enum { DG_LAUNCH_PER_INSTANCE = 0, DG_LAUNCH_BATCHED = 1 };

@@ -21,7 +21,7 @@ class _Rollout(torch.autograd.Function):
         solver.set_state(U0.detach().contiguous())
         done = 0
         while done < n_steps:
-            checkpoints.append(solver.get_state().clone())
+            checkpoints.append(solver.get_state())  # a fresh tensor
             k = min(every, n_steps - done)
             solver.rk_step(dt, k)
             done += k
@@ -35,17 +35,18 @@ class _Rollout(torch.autograd.Function):
     def backward(ctx, gout):
         S, dt, every = ctx.solver, ctx.dt, ctx.every
         lam = gout.detach().contiguous().clone()
-        gbar = 0.0
+        S.adjoint_gammabar()  # start from an empty device accumulator
         n_seg = len(ctx.checkpoints)
         for s in reversed(range(n_seg)):
             k = min(every, ctx.n_steps - s * every)
             S.set_state(ctx.checkpoints[s])
             states = []
             for _ in range(k):  # recompute the segment
-                states.append(S.get_state().clone())
+                states.append(S.get_state())
                 S.rk_step(dt, 1)
             for j in reversed(range(k)):
-                gbar += S.rk_step_vjp(states[j], dt, lam)
+                S.rk_step_vjp(states[j], dt, lam, defer=True)  # gamma stays on the device
+        gbar = S.adjoint_gammabar()
         S.check()
         gg = torch.tensor(gbar, dtype=torch.float64)
         return lam, gg, None, None, None, None

@@ -441,6 +441,10 @@ dg_status ensure_adjoint(dg_ctx* c) {
     cudaGetLastError();
     return fail(c, DG_ENOMEM, "adjoint workspace");
   }
+  if (cudaMemsetAsync(c->gacc, 0, sizeof(double), c->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, DG_ECUDA, "adjoint workspace");
+  }
   return DG_OK;
 }
 
@@ -474,12 +478,16 @@ dg_status run_vjp(dg_ctx* c, const double* U, const double* lam, double* out, in
   return DG_OK;
 }
 
+// Hand the device gamma accumulator to the host: sync, *gammabar += it, reset it.  With a
+// null gammabar nothing happens (the contribution stays on the device for a later call).
 dg_status read_gacc(dg_ctx* c, double* gammabar) {
+  if (!gammabar) return DG_OK;
   double g = 0.0;
   cudaError_t e = cudaMemcpyAsync(&g, c->gacc, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->gacc, 0, sizeof(double), c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "adjoint gamma read");
-  if (gammabar) *gammabar += g;
+  *gammabar += g;
   return DG_OK;
 }
 
@@ -758,8 +766,6 @@ dg_status dg_rhs_vjp(dg_ctx* c, const double* U, const double* lam, double* Ubar
   if (c->ns) return fail(c, DG_EUNSUPPORTED, "the adjoint exists for the Euler equations");
   dg_status st = ensure_adjoint(c);
   if (st) return st;
-  cudaError_t e = cudaMemsetAsync(c->gacc, 0, sizeof(double), c->stream);
-  if (e != cudaSuccess) return cuda_fail(c, e, "dg_rhs_vjp");
   if ((st = run_vjp(c, U, lam, Ubar, 0, 1.0, 0.0, nullptr, nullptr, 0, 0.0, 1.0))) return st;
   return read_gacc(c, gammabar);
 }
@@ -776,13 +782,18 @@ dg_status dg_rk_step_vjp(dg_ctx* c, const double* Un, double dt, double* lam, do
   // recompute the stage states of this step
   if ((st = run_stage(c, Un, Un, W1, 1, kStageA[0], kStageB[0], dt, c->stream))) return st;
   if ((st = run_stage(c, W1, Un, W2, 1, kStageA[1], kStageB[1], dt, c->stream))) return st;
-  cudaError_t e = cudaMemsetAsync(c->gacc, 0, sizeof(double), c->stream);
-  if (e != cudaSuccess) return cuda_fail(c, e, "dg_rk_step_vjp");
   // reverse Shu-Osher: U3 = 1/3 Un + 2/3 (U2 + dt L(U2)), U2 = 3/4 Un + 1/4 (U1 + dt L(U1)),
   // U1 = Un + dt L(Un)
   if ((st = run_vjp(c, W2, lam, T1, 1, kStageB[2], dt, nullptr, T2, 1, kStageA[2], kStageB[2] * dt))) return st;
   if ((st = run_vjp(c, W1, T1, T3, 1, kStageB[1], dt, nullptr, T2, 0, kStageA[1], kStageB[1] * dt))) return st;
   if ((st = run_vjp(c, Un, T3, lam, 1, kStageB[0], dt, T2, nullptr, 0, 0.0, kStageB[0] * dt))) return st;
+  return read_gacc(c, gammabar);
+}
+
+dg_status dg_adjoint_gammabar(dg_ctx* c, double* gammabar) {
+  if (!c) return DG_EINVAL;
+  if (!gammabar) return fail(c, DG_EINVAL, "null gammabar");
+  if (!c->gacc) return DG_OK;  // no adjoint call yet: nothing accumulated
   return read_gacc(c, gammabar);
 }
 

@@ -33,7 +33,7 @@ _STATUS = {0: "DG_OK", -1: "DG_EINVAL", -2: "DG_ENOMEM", -3: "DG_ECUDA", -4: "DG
 EXPORTS = ["dg_init_mesh", "dg_state_size", "dg_instance_offset", "dg_set_state", "dg_get_state",
            "dg_rhs", "dg_rk_stage", "dg_rk_step", "dg_max_dt", "dg_check", "dg_gll",
            "dg_two_point_flux", "dg_max_dt_noalloc", "dg_set_launch", "dg_autotune",
-           "dg_rhs_vjp", "dg_rk_step_vjp",
+           "dg_rhs_vjp", "dg_rk_step_vjp", "dg_adjoint_gammabar",
            "dg_last_error", "dg_free"]
 
 
@@ -113,6 +113,7 @@ def lib():
         L.dg_set_launch.argtypes = [vp, ip, ip, ip, ip]
         L.dg_rhs_vjp.argtypes = [vp, vp, vp, vp, dp]
         L.dg_rk_step_vjp.argtypes = [vp, vp, C.c_double, vp, dp]
+        L.dg_adjoint_gammabar.argtypes = [vp, dp]
         L.dg_autotune.argtypes = [vp, C.c_double, ip, C.POINTER(C.c_int), dp]
         L.dg_last_error.argtypes = [vp]
         L.dg_last_error.restype = C.c_char_p
@@ -265,11 +266,19 @@ class Solver:
                                     C.byref(g)), "dg_rhs_vjp")
         return Ubar, g.value
 
-    def rk_step_vjp(self, Un, dt: float, lam):
-        """In place: lam = dJ/dU^{n+1} -> dJ/dU^n; returns dJ/dgamma through this step."""
+    def rk_step_vjp(self, Un, dt: float, lam, defer: bool = False):
+        """In place: lam = dJ/dU^{n+1} -> dJ/dU^n; returns dJ/dgamma through this step.  With
+        defer=True the gamma contribution stays on the device (no synchronization; returns 0.0)
+        until adjoint_gammabar()."""
         g = C.c_double(0.0)
-        self._call(lib().dg_rk_step_vjp(self._h, self._dev(Un, "Un"), dt, self._dev(lam, "lam"), C.byref(g)),
-                   "dg_rk_step_vjp")
+        self._call(lib().dg_rk_step_vjp(self._h, self._dev(Un, "Un"), dt, self._dev(lam, "lam"),
+                                        None if defer else C.byref(g)), "dg_rk_step_vjp")
+        return g.value
+
+    def adjoint_gammabar(self) -> float:
+        """The gamma contributions of deferred adjoint calls (synchronizes; resets them)."""
+        g = C.c_double(0.0)
+        self._call(lib().dg_adjoint_gammabar(self._h, C.byref(g)), "dg_adjoint_gammabar")
         return g.value
 
     def set_launch(self, mode: int, group_scale: int = 1, ctas_per_sm: int = 0, order: int = 0):

@@ -186,3 +186,22 @@ def test_rollout_gradient_matches_oracle(env, orc, prec, tol):
     got = U.grad.cpu().numpy().reshape(U0.shape)
     assert np.linalg.norm(got - g_ref) <= tol * np.linalg.norm(g_ref)
     assert abs(float(gam.grad) - gg_ref) <= tol * abs(gg_ref)
+
+
+def test_deferred_gamma_accumulates_on_the_device(env, orc):
+    """gammabar == NULL keeps each call's gamma contribution on the device; one
+    dg_adjoint_gammabar call returns their sum and resets it."""
+    torch, dg = env
+    P, S = make(orc, dg, 2, 3, 3, 0)
+    U = dev(torch, state(orc, P, 5))
+    lam0 = dev(torch, wl.uniform(41, U.numel()).reshape(U.shape) - 0.5)
+    dt = 1e-3
+    lam = lam0.clone()
+    g1 = S.rk_step_vjp(U, dt, lam)
+    g2 = S.rk_step_vjp(U, dt, lam)
+    lam = lam0.clone()
+    assert S.rk_step_vjp(U, dt, lam, defer=True) == 0.0
+    S.rk_step_vjp(U, dt, lam, defer=True)
+    g = S.adjoint_gammabar()
+    assert abs(g - (g1 + g2)) <= 1e-12 * (abs(g1) + abs(g2))
+    assert S.adjoint_gammabar() == 0.0
