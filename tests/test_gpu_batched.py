@@ -61,13 +61,16 @@ def test_batched_equals_per_instance_bitwise(env, orc, prec, vol):
                 assert torch.equal(S.get_state(), ref), (gs, cps, order)
 
 
-def test_batched_matches_oracle(env, orc):
+@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 1e-5)])
+def test_batched_matches_oracle(env, orc, prec, tol):
+    """One batched launch per stage over eight uneven instances, 100 SSP-RK3 steps, against
+    the oracle run instance by instance."""
     torch, dg = env
     meshes, U = vortex_set(dg, orc, SPECS)
-    S = dg.Solver(meshes, volume=dg.VOL_STRONG, surface=dg.SURF_RUSANOV, precision=dg.FP64, gamma=GAMMA)
+    S = dg.Solver(meshes, volume=dg.VOL_STRONG, surface=dg.SURF_RUSANOV, precision=prec, gamma=GAMMA)
     S.set_state(torch.from_numpy(U).cuda())
-    dt = 1e-3
-    S.rk_step(dt, 5)
+    dt = 2e-3
+    S.rk_step(dt, 100)
     S.check()
     got = S.get_state().cpu().numpy()
     for k, ((nel, N, c), off) in enumerate(zip(SPECS, S.offsets)):
@@ -75,10 +78,10 @@ def test_batched_matches_oracle(env, orc):
                         gamma=GAMMA)
         n = nel * nel * (N + 1) ** 2
         U0 = U[:, off:off + n].reshape(P.shape)
-        ref = orc.rk3(P, U0, dt, 5)
+        ref = orc.rk3(P, U0, dt, 100)
         g = got[:, off:off + n].reshape(P.shape)
         err = np.linalg.norm(g - ref) / np.linalg.norm(ref)
-        assert err <= 1e-12, (k, err)
+        assert err <= tol, (k, err)
 
 
 def test_batched_rejects_high_degree_and_autotune_keeps_state(env, orc):
