@@ -40,7 +40,6 @@ namespace {
 
 constexpr int kRT = 128;
 constexpr int NPR = 6;  // staged primitives per node: u, v, w, T, p - p_ref, a
-constexpr int NPC = 7;  // cached per node in R: u, v, w, T, p - p_ref, a, c_p (+ T in FP64)
 
 template <int N, int NS, class R>
 struct RG {
