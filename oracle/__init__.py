@@ -1,9 +1,10 @@
 """ORACLE -- test infrastructure only, never part of the product path.
 
-A plain, slow FP64 CPU implementation of the DGSEM residual, numerical fluxes, SSP-RK3
-stage and time-step bound of the paper's method (arXiv 2605.26388, Sec. 2, Sec. 3.1.1,
-App. A, App. B), and of the reacting Navier-Stokes residual (BR1 viscous terms, Sec. 3.1.2;
-Arrhenius source, Sec. 3.1.3 and App. C), written in C++ (``dg_oracle.cpp``) and loaded here with ctypes.  It
+A plain, slow FP64 CPU implementation of the DGSEM residual, numerical fluxes, SSP-RK33
+and SSP-RK54 steps and time-step bound of the paper's method (arXiv 2605.26388, Sec. 2,
+Sec. 3.1.1, App. A, App. B), and of the reacting Navier-Stokes residual (BR1 viscous terms,
+Sec. 3.1.2; Arrhenius source, Sec. 3.1.3 and App. C) with its implicit Strang-split source
+substep (Sec. 3.1.3), written in C++ (``dg_oracle.cpp``) and loaded here with ctypes.  It
 shares no code with the CUDA library.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
 CPU-baseline leg of ``bench.py`` may import it.
 
@@ -156,6 +157,11 @@ def lib():
         _lib.orc_arrhenius.argtypes = [C.POINTER(_Mech), C.c_int, C.c_double, dp, dp]
         _lib.orc_chem_source.argtypes = [pp, dp, dp]
         _lib.orc_mixture.argtypes = [pp, dp, dp, dp]
+        ip = C.POINTER(C.c_int)
+        _lib.orc_ssp_table.argtypes = [C.c_int, dp, dp, ip, dp]
+        _lib.orc_ssp_steps.argtypes = [pp, C.c_int, dp, C.c_double, C.c_int]
+        _lib.orc_source_implicit.argtypes = [pp, dp, C.c_double, C.c_int, C.c_double, ip]
+        _lib.orc_strang_steps.argtypes = [pp, C.c_int, dp, C.c_double, C.c_int, C.c_int, C.c_double, ip]
     return _lib
 
 
@@ -330,3 +336,59 @@ def mixture(P: Problem, u):
     c = P._c()
     _check(lib().orc_mixture(C.byref(c), _ptr(u), C.byref(T), C.byref(p)), "mixture")
     return T.value, p.value
+
+
+SSPRK33, SSPRK54 = 3, 54
+NEWTON_MAX_IT, NEWTON_TOL = 20, 1e-12
+
+
+def ssp_table(scheme: int):
+    """(alpha, beta, s, c): the Shu-Osher table of SSP-RK33 (Shu-Osher 1988) or SSP-RK54
+    (Spiteri-Ruuth 2002) as (s, s) arrays (row i = stage i+1), the stage count and the SSP
+    coefficient min alpha/beta (App. B).  Pinned by the order conditions of the Butcher form
+    (order 3 / 4), the convexity rules and the paper's c ~ 1.508."""
+    a = np.zeros(25)
+    b = np.zeros(25)
+    s, c = C.c_int(), C.c_double()
+    _check(lib().orc_ssp_table(scheme, _ptr(a), _ptr(b), C.byref(s), C.byref(c)), "ssp_table")
+    n = s.value
+    return a.reshape(5, 5)[:n, :n], b.reshape(5, 5)[:n, :n], n, c.value
+
+
+def ssp_steps(P: Problem, scheme: int, U: np.ndarray, dt: float, n_steps: int) -> np.ndarray:
+    """n_steps steps of SSP-RK33 or SSP-RK54 by the Shu-Osher sums (App. B); returns the new
+    state.  Pinned by the temporal convergence order on a smooth problem and, for RK33, by
+    agreement with the separately written rk3()."""
+    U = np.array(U, dtype=np.float64, order="C").reshape(P.shape)
+    c = P._c()
+    _check(lib().orc_ssp_steps(C.byref(c), scheme, _ptr(U), dt, n_steps), "ssp_steps")
+    return U
+
+
+def source_implicit(P: Problem, U: np.ndarray, h: float, max_it: int = NEWTON_MAX_IT,
+                    tol: float = NEWTON_TOL):
+    """One backward-Euler substep of the chemical source of length h at every node (Sec.
+    3.1.3, Eq. source_residual; Newton with a forward-difference Jacobian and Gauss-Jordan
+    solves).  Returns (new state, largest Newton count; -1 = a node did not converge).
+    Pinned by closed-form backward-Euler solutions of first- and second-order reactions, a
+    bisection root of a temperature-coupled reaction, the O(h^2) agreement with an explicit
+    Euler step, and mass and atom conservation."""
+    U = np.array(U, dtype=np.float64, order="C").reshape(P.shape)
+    it = C.c_int()
+    c = P._c()
+    _check(lib().orc_source_implicit(C.byref(c), _ptr(U), h, max_it, tol, C.byref(it)), "source_implicit")
+    return U, it.value
+
+
+def strang_steps(P: Problem, scheme: int, U: np.ndarray, dt: float, n_steps: int,
+                 max_it: int = NEWTON_MAX_IT, tol: float = NEWTON_TOL):
+    """n_steps Strang-split steps S_{dt/2} T_dt S_{dt/2} (Eq. strang_split): T_dt one SSP
+    step of the residual without its source part, S the implicit source substep.  Returns
+    (new state, largest Newton count).  Built from the pinned parts; with the source off it
+    reduces to ssp_steps() on the transport residual (tested)."""
+    U = np.array(U, dtype=np.float64, order="C").reshape(P.shape)
+    it = C.c_int()
+    c = P._c()
+    _check(lib().orc_strang_steps(C.byref(c), scheme, _ptr(U), dt, n_steps, max_it, tol, C.byref(it)),
+           "strang_steps")
+    return U, it.value

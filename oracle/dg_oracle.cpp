@@ -24,6 +24,7 @@
 // run on several OpenMP threads: each element writes only its own residual, so the
 // arithmetic per element is the same on one thread or many.
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -542,24 +543,31 @@ void arrhenius(const OrcMech& m, int r, double T, double& kf, double& Kc) {
                 m.kc[r][4] * Z * Z);
 }
 
-void chem_source(const OrcProblem& P, const double* u, double* S) {
-  const OrcMech& m = *P.mech;
-  const int ns = m.n_species, nv = n_vars(P);
-  for (int v = 0; v < nv; ++v) S[v] = 0.0;
-  Mix q = mixture(P, u);
+// Species production rates omega_s (kg m^-3 s^-1) of the partial densities rho_s at
+// temperature T.
+void species_rates(const OrcMech& m, const double* rho_s, double T, double* w) {
+  const int ns = m.n_species;
+  for (int s = 0; s < ns; ++s) w[s] = 0.0;
   double X[8];
-  for (int s = 0; s < ns; ++s) X[s] = u[s] / m.W[s] * 1.0e-6;
+  for (int s = 0; s < ns; ++s) X[s] = rho_s[s] / m.W[s] * 1.0e-6;
   for (int r = 0; r < m.n_reactions; ++r) {
     double kf, Kc;
-    arrhenius(m, r, q.T, kf, Kc);
+    arrhenius(m, r, T, kf, Kc);
     double pf = 1.0, pb = 1.0;
     for (int s = 0; s < ns; ++s) {
       for (int k = 0; k < m.nu_f[r][s]; ++k) pf *= X[s];
       for (int k = 0; k < m.nu_b[r][s]; ++k) pb *= X[s];
     }
     const double Rr = kf * pf - kf / Kc * pb;
-    for (int s = 0; s < ns; ++s) S[s] += m.W[s] * 1.0e6 * (m.nu_b[r][s] - m.nu_f[r][s]) * Rr;
+    for (int s = 0; s < ns; ++s) w[s] += m.W[s] * 1.0e6 * (m.nu_b[r][s] - m.nu_f[r][s]) * Rr;
   }
+}
+
+void chem_source(const OrcProblem& P, const double* u, double* S) {
+  const int nv = n_vars(P);
+  for (int v = 0; v < nv; ++v) S[v] = 0.0;
+  Mix q = mixture(P, u);
+  species_rates(*P.mech, u, q.T, S);
 }
 
 // BR1 gradient (Sec. 3.1.2 Eq. br1_avg; App. A "Viscous Volume and Interface Fluxes") of
@@ -991,6 +999,252 @@ int orc_rk3(const OrcProblem* P, double* U, double dt, int n_steps) {
     orc_rk3_stage(P, 2, U, U1.data(), dt, U2.data());
     orc_rk3_stage(P, 3, U, U2.data(), dt, U);
   }
+  return 0;
+}
+
+}  // extern "C"
+
+namespace {
+
+// ---------------------------------------------------------------------------------------
+// The s-stage SSP-RK scheme in Shu-Osher form (App. B):
+//   U^(0) = U^n,  U^(i) = sum_{k<i} [alpha_ik U^(k) + dt beta_ik L(U^(k))],  U^{n+1} = U^(s).
+// Two tables: SSP-RK33 of Shu and Osher (J. Comput. Phys. 77, 1988) and SSP-RK54 of
+// Spiteri and Ruuth (SIAM J. Numer. Anal. 40(2), 2002), the paper's production integrator
+// (SSP coefficient about 1.508).  The paper prints neither table; both are the published
+// coefficients (SSP-RK54 to the 15 digits of its publication).  Row i holds stage i+1.
+// ---------------------------------------------------------------------------------------
+struct SspTable {
+  int s;
+  double alpha[5][5], beta[5][5];
+};
+
+SspTable ssp_table(int scheme) {
+  SspTable t;
+  std::memset(&t, 0, sizeof(t));
+  if (scheme == 3) {
+    t.s = 3;
+    t.alpha[0][0] = 1.0;                           t.beta[0][0] = 1.0;
+    t.alpha[1][0] = 0.75; t.alpha[1][1] = 0.25;    t.beta[1][1] = 0.25;
+    t.alpha[2][0] = 1.0 / 3.0; t.alpha[2][2] = 2.0 / 3.0;  t.beta[2][2] = 2.0 / 3.0;
+    return t;
+  }
+  t.s = 5;
+  t.alpha[0][0] = 1.0;
+  t.beta[0][0] = 0.391752226571890;
+  t.alpha[1][0] = 0.444370493651235;
+  t.alpha[1][1] = 0.555629506348765;
+  t.beta[1][1] = 0.368410593050371;
+  t.alpha[2][0] = 0.620101851488403;
+  t.alpha[2][2] = 0.379898148511597;
+  t.beta[2][2] = 0.251891774271694;
+  t.alpha[3][0] = 0.178079954393132;
+  t.alpha[3][3] = 0.821920045606868;
+  t.beta[3][3] = 0.544974750228521;
+  t.alpha[4][2] = 0.517231671970585;
+  t.alpha[4][3] = 0.096059710526147;
+  t.beta[4][3] = 0.063692468666290;
+  t.alpha[4][4] = 0.386708617503269;
+  t.beta[4][4] = 0.226007483236906;
+  return t;
+}
+
+// SSP coefficient min over beta_ik > 0 of alpha_ik / beta_ik (App. B, c~).
+double ssp_coefficient(const SspTable& t) {
+  double c = 1e300;
+  for (int i = 0; i < t.s; ++i)
+    for (int k = 0; k <= i; ++k)
+      if (t.beta[i][k] > 0.0) c = std::fmin(c, t.alpha[i][k] / t.beta[i][k]);
+  return c;
+}
+
+// One step of the table's scheme, in place; every stage state keeps its residual.  The
+// positivity floor (when enabled) follows each stage.
+void ssp_step(const OrcProblem& P, const SspTable& t, double* U, double dt) {
+  Mesh M(P);
+  const size_t n = (size_t)n_vars(P) * M.n_elem * M.n_nodes;
+  std::vector<std::vector<double>> Us(t.s + 1, std::vector<double>(n)), Ls(t.s, std::vector<double>(n));
+  std::memcpy(Us[0].data(), U, n * sizeof(double));
+  for (int i = 1; i <= t.s; ++i) {
+    residual(P, Us[i - 1].data(), Ls[i - 1].data());
+    for (size_t q = 0; q < n; ++q) {
+      double x = 0.0;
+      for (int k = 0; k < i; ++k) x += t.alpha[i - 1][k] * Us[k][q] + dt * t.beta[i - 1][k] * Ls[k][q];
+      Us[i][q] = x;
+    }
+    positivity_floor(P, Us[i].data());
+  }
+  std::memcpy(U, Us[t.s].data(), n * sizeof(double));
+}
+
+// ---------------------------------------------------------------------------------------
+// Implicit source substep S_h of the Strang split (Sec. 3.1.3, Eqs. strang_split and
+// source_residual), single temperature.  Per node, the partial densities Y = (rho_1..rho_ns)
+// advance by one backward-Euler step of length h of the chemical source,
+//   R(Y*) = Y* - Y^n - h omega(Y*) = 0,
+// with rho = sum rho_s, the momentum and E held fixed (the source has no momentum or energy
+// component and sum_s omega_s = 0).  READINGS: with one temperature there is no E_v row and
+// no Landau-Teller term; the temperature of an iterate Y follows in closed form from the
+// fixed internal energy e = E - |rho u|^2 / (2 rho^n) of the calorically perfect species,
+// T(Y) = (e - sum Y_s h0_s) / sum Y_s cv_s (the paper's inner NASA-9 Newton reduces to this).
+// Newton: J = dR/dY by forward differences column by column with
+// eps_k = max(1e-7 |Y_k|, 1e-12); the update solves J d = R by Gauss-Jordan elimination
+// (partial pivoting) and sets Y <- Y - d.  READING: the paper gives no stopping rule; the
+// iteration stops after the first update with max_k |d_k| <= tol * rho, or after max_it
+// updates (then the node counts as not converged).
+// ---------------------------------------------------------------------------------------
+void source_residual(const OrcMech& m, const double* Y, const double* Yn, double e, double h,
+                     double* R) {
+  const int ns = m.n_species;
+  double rcv = 0.0, rh0 = 0.0;
+  for (int s = 0; s < ns; ++s) {
+    rcv += Y[s] * m.cv[s];
+    rh0 += Y[s] * m.h0[s];
+  }
+  const double T = (e - rh0) / rcv;
+  double w[8];
+  species_rates(m, Y, T, w);
+  for (int s = 0; s < ns; ++s) R[s] = Y[s] - Yn[s] - h * w[s];
+}
+
+// Solve A x = b (n x n, row-major, both overwritten) by Gauss-Jordan elimination with
+// partial pivoting; x is returned in b.  Returns false on a zero pivot.
+bool gauss_jordan(int n, double* A, double* b) {
+  for (int k = 0; k < n; ++k) {
+    int piv = k;
+    for (int i = k + 1; i < n; ++i)
+      if (std::fabs(A[i * n + k]) > std::fabs(A[piv * n + k])) piv = i;
+    if (A[piv * n + k] == 0.0) return false;
+    if (piv != k) {
+      for (int j = 0; j < n; ++j) std::swap(A[k * n + j], A[piv * n + j]);
+      std::swap(b[k], b[piv]);
+    }
+    const double d = A[k * n + k];
+    for (int j = 0; j < n; ++j) A[k * n + j] /= d;
+    b[k] /= d;
+    for (int i = 0; i < n; ++i) {
+      if (i == k) continue;
+      const double f = A[i * n + k];
+      for (int j = 0; j < n; ++j) A[i * n + j] -= f * A[k * n + j];
+      b[i] -= f * b[k];
+    }
+  }
+  return true;
+}
+
+// One node: u (all n_vars components) in, the new partial densities written to u.
+// Returns the number of Newton updates taken, or -1 if the iteration did not converge.
+int source_implicit_node(const OrcProblem& P, double* u, double h, int max_it, double tol) {
+  const OrcMech& m = *P.mech;
+  const int ns = m.n_species, dim = P.dim;
+  double Yn[8], Y[8], rho = 0.0, kin = 0.0;
+  for (int s = 0; s < ns; ++s) {
+    Yn[s] = Y[s] = u[s];
+    rho += u[s];
+  }
+  for (int d = 0; d < dim; ++d) kin += u[ns + d] * u[ns + d];
+  const double e = u[ns + dim] - 0.5 * kin / rho;
+  for (int it = 1; it <= max_it; ++it) {
+    double R[8], J[64];
+    source_residual(m, Y, Yn, e, h, R);
+    for (int k = 0; k < ns; ++k) {
+      const double eps = std::fmax(1e-7 * std::fabs(Y[k]), 1e-12);
+      double Yp[8], Rp[8];
+      for (int s = 0; s < ns; ++s) Yp[s] = Y[s];
+      Yp[k] += eps;
+      source_residual(m, Yp, Yn, e, h, Rp);
+      for (int i = 0; i < ns; ++i) J[i * ns + k] = (Rp[i] - R[i]) / eps;
+    }
+    if (!gauss_jordan(ns, J, R)) return -1;
+    double dmax = 0.0;
+    for (int s = 0; s < ns; ++s) {
+      Y[s] -= R[s];
+      dmax = std::fmax(dmax, std::fabs(R[s]));
+    }
+    if (dmax <= tol * rho) {
+      for (int s = 0; s < ns; ++s) u[s] = Y[s];
+      return it;
+    }
+  }
+  for (int s = 0; s < ns; ++s) u[s] = Y[s];
+  return -1;
+}
+
+// S_h over every node of a state, in place; returns the largest iteration count, or -1.
+int source_implicit(const OrcProblem& P, double* U, double h, int max_it, double tol) {
+  Mesh M(P);
+  const int nv = n_vars(P);
+  const size_t stride = (size_t)M.n_elem * M.n_nodes;
+  int worst = 0;
+  for (size_t q = 0; q < stride; ++q) {
+    double u[16];
+    for (int v = 0; v < nv; ++v) u[v] = U[v * stride + q];
+    const int it = source_implicit_node(P, u, h, max_it, tol);
+    worst = (it < 0 || worst < 0) ? -1 : std::max(worst, it);
+    for (int v = 0; v < nv; ++v) U[v * stride + q] = u[v];
+  }
+  return worst;
+}
+
+}  // namespace
+
+extern "C" {
+
+// The Shu-Osher table of an SSP scheme (3: SSP-RK33, 54: SSP-RK54) as 5 x 5 row-major
+// alpha and beta (row i = stage i+1), its stage count and its SSP coefficient.
+int orc_ssp_table(int scheme, double* alpha, double* beta, int* s, double* c) {
+  if (scheme != 3 && scheme != 54) return -1;
+  SspTable t = ssp_table(scheme);
+  for (int i = 0; i < 5; ++i)
+    for (int k = 0; k < 5; ++k) {
+      alpha[i * 5 + k] = t.alpha[i][k];
+      beta[i * 5 + k] = t.beta[i][k];
+    }
+  *s = t.s;
+  *c = ssp_coefficient(t);
+  return 0;
+}
+
+// n_steps steps of the SSP scheme (3 or 54) in place, by the Shu-Osher sums as written.
+int orc_ssp_steps(const OrcProblem* P, int scheme, double* U, double dt, int n_steps) {
+  int rc = check_problem(*P);
+  if (rc) return rc;
+  if (scheme != 3 && scheme != 54) return -1;
+  SspTable t = ssp_table(scheme);
+  for (int k = 0; k < n_steps; ++k) ssp_step(*P, t, U, dt);
+  return 0;
+}
+
+// One implicit source substep S_h over a whole state, in place (reacting problems).
+// *iters receives the largest Newton count over the nodes (-1: some node did not converge).
+int orc_source_implicit(const OrcProblem* P, double* U, double h, int max_it, double tol, int* iters) {
+  int rc = check_problem(*P);
+  if (rc) return rc;
+  if (P->equations != ORC_NS_REACTING || !P->mech) return -1;
+  *iters = source_implicit(*P, U, h, max_it, tol);
+  return 0;
+}
+
+// n_steps Strang-split steps (Eq. strang_split), in place:
+//   U <- S_{dt/2}( T_dt( S_{dt/2}(U) ) ),
+// T_dt one step of the SSP scheme on the residual without its source part.
+int orc_strang_steps(const OrcProblem* P, int scheme, double* U, double dt, int n_steps, int max_it,
+                     double tol, int* iters) {
+  int rc = check_problem(*P);
+  if (rc) return rc;
+  if (P->equations != ORC_NS_REACTING || !P->mech || (scheme != 3 && scheme != 54)) return -1;
+  OrcProblem T = *P;
+  T.parts = (P->parts ? P->parts : 7) & 3;
+  if (T.parts == 0) T.parts = 8;  // no transport part: the residual is zero
+  SspTable t = ssp_table(scheme);
+  int worst = 0;
+  for (int k = 0; k < n_steps; ++k) {
+    const int a = source_implicit(*P, U, 0.5 * dt, max_it, tol);
+    ssp_step(T, t, U, dt);
+    const int b = source_implicit(*P, U, 0.5 * dt, max_it, tol);
+    worst = (a < 0 || b < 0 || worst < 0) ? -1 : std::max(worst, std::max(a, b));
+  }
+  *iters = worst;
   return 0;
 }
 
