@@ -1,20 +1,23 @@
-/* dgsem.h -- C-ABI of the B300 (sm_103a) DGSEM residual and SSP-RK3 stage library.
+/* dgsem.h -- C-ABI of the B300 (sm_103a) DGSEM residual and SSP-RK stage library.
  *
  * The library evaluates the semi-discrete DGSEM residual of the compressible Euler
  * equations, and of the single-temperature reacting Navier-Stokes equations, on periodic
- * Cartesian meshes and advances it with the three-stage SSP-RK scheme, entirely in
+ * Cartesian meshes and advances it with the SSP-RK33 or SSP-RK54 scheme, entirely in
  * hand-written CUDA kernels (one fused kernel per RK stage for Euler; a BR1 gradient pass
- * plus one fused kernel for Navier-Stokes).  The operations follow arXiv 2605.26388:
+ * plus one fused kernel for Navier-Stokes; one per-node kernel for the implicit chemistry
+ * substep of the Strang split).  The operations follow arXiv 2605.26388:
  *   - equations and ideal-gas closure: Sec. 2;
  *   - viscous terms: BR1 lifting (Sec. 3.1.2, Eqs. br1_avg, tau, br1_flux);
  *   - finite-rate chemistry: Arrhenius source (Sec. 3.1.3, Eqs. src_reaction_rate,
- *     src_omega; App. C);
+ *     src_omega; App. C), in the residual or by the Strang split with a per-node
+ *     backward-Euler Newton substep (Sec. 3.1.3, Eqs. strang_split, source_residual);
  *   - element-local DGSEM on (N+1)^d GLL nodes: Sec. 3.1.1 and App. A;
  *   - volume term: Eq. vol_weak (strong form; the weak form is the same operator by the
  *     SBP property) or Eq. vol_split / Eq. split_form_3D (flux differencing with the
  *     Ranocha entropy-conservative two-point flux);
  *   - surface term: Eq. surf_int with a Riemann flux (Sec. 3.1.1 "Surface Fluxes");
- *   - time integration: App. B (SSP-RK, Shu-Osher form) and Eq. dt_hyp (time-step bound).
+ *   - time integration: App. B (SSP-RK33 and SSP-RK54, Shu-Osher form) and Eq. dt_hyp
+ *     (time-step bound).
  *
  * Conventions shared by every entry point:
  *   - State layout (SoA, FP64): U[v * n_nodes_total + node_offset(instance) + e * n_p + q]
@@ -56,7 +59,8 @@ typedef enum {
   DG_ENONFINITE = -4,   /* a kernel produced a non-finite value */
   DG_EPOSITIVITY = -5,  /* a kernel read a state with rho <= 0 or p <= 0 */
   DG_EUNSUPPORTED = -6, /* valid but not implemented (e.g. non-periodic boundaries) */
-  DG_ETOOLARGE = -7     /* more instances than dg_max_dt_noalloc's static scratch holds */
+  DG_ETOOLARGE = -7,    /* more instances than dg_max_dt_noalloc's static scratch holds */
+  DG_ECONVERGENCE = -8  /* a node's implicit-source Newton iteration did not converge */
 } dg_status;
 
 /* Equations.  DG_NAVIER_STOKES is the single-gas, non-dimensional case (R = 1, so T = p/rho,
@@ -75,6 +79,13 @@ enum { DG_SURF_RUSANOV = 0, DG_SURF_HLLC = 1, DG_SURF_HLL = 2, DG_SURF_EC = 3 };
  * state, the RK accumulation, the pressure (from the FP64 total energy) and the
  * positivity decision kept in FP64. */
 enum { DG_FP64 = 0, DG_FP32_MIXED = 1 };
+/* Time integration (App. B): SSP-RK33 of Shu and Osher (SSP coefficient 1) or SSP-RK54 of
+ * Spiteri and Ruuth (five stages, fourth order, SSP coefficient 1.508; the paper's
+ * production integrator, with the coefficients of its publication). */
+enum { DG_SSPRK33 = 0, DG_SSPRK54 = 1 };
+/* Defaults of the implicit source substep's Newton iteration (dg_physics fields <= 0). */
+#define DG_NEWTON_MAX_IT 40
+#define DG_NEWTON_TOL 1e-12
 
 /* One periodic Cartesian mesh instance (Sec. 3.1.1: element-wise affine map of the
  * reference cube; collocation on (N+1)^dim GLL nodes). */
@@ -129,6 +140,13 @@ typedef struct {
   double mu;        /* constant dynamic viscosity (>= 0) */
   double prandtl;   /* Prandtl number (> 0); conductivity k = mu c_p / Pr */
   const dg_mechanism* chem;  /* DG_NS_REACTING: species and reactions (copied at init) */
+  /* Time integration (a zero-filled struct gives SSP-RK33 with the source in the residual): */
+  int time_scheme;  /* DG_SSPRK33 | DG_SSPRK54 */
+  int chem_split;   /* DG_NS_REACTING only: 0 the Arrhenius source is part of L(U); 1 Strang
+                     * split (Eq. strang_split): L(U) has no source and every step is
+                     * S_{dt/2} o T_dt o S_{dt/2}, S the implicit substep of dg_source_step */
+  int newton_max_it;  /* implicit substep: Newton updates per node at most (<= 0: default) */
+  double newton_tol;  /* stop once max_s |dY_s| <= newton_tol * rho (<= 0: default) */
 } dg_physics;
 
 /* Build a context for n_inst instances (all of the same dim) sharing one physics
@@ -153,20 +171,25 @@ DG_API dg_status dg_set_state(dg_ctx* ctx, const double* U);
 DG_API dg_status dg_get_state(const dg_ctx* ctx, double* U);
 
 /* dUdt = L(U) at time t (the residual does not depend on t).  U and dUdt are device
- * pointers of dg_state_size() doubles and must not overlap. */
+ * pointers of dg_state_size() doubles and must not overlap.  Under the Strang split L has
+ * no chemical source. */
 DG_API dg_status dg_rhs(dg_ctx* ctx, const double* U, double* dUdt, double t);
 
 /* One SSP-RK3 stage (App. B, Shu-Osher form) on caller buffers:
  *   stage 1: Uout = Un + dt L(Un)                       (Uprev must equal Un)
  *   stage 2: Uout = 3/4 Un + 1/4 (Uprev + dt L(Uprev))
  *   stage 3: Uout = 1/3 Un + 2/3 (Uprev + dt L(Uprev))
- * followed by the positivity floor when enabled.  Uout must not alias Un or Uprev. */
+ * followed by the positivity floor when enabled.  Uout must not alias Un or Uprev.  The
+ * stage is SSP-RK3's whatever the context's time_scheme. */
 DG_API dg_status dg_rk_stage(dg_ctx* ctx, int stage, const double* Un, const double* Uprev,
                       double dt, double* Uout);
 
-/* n_steps SSP-RK3 steps of size dt on the context-held state (3 fused stage launches per
- * step, replayed from a CUDA graph).  Asynchronous: call dg_check() to synchronize and
- * collect device-side errors. */
+/* n_steps steps of size dt on the context-held state with the context's time_scheme:
+ * SSP-RK33 (3 fused stage launches per step) or SSP-RK54 (5 launches; stage 4 also writes
+ * the running sum a52 U2 + a53 U3 + b53 dt L(U3) of stage 5 into a fourth buffer).  Under
+ * the Strang split each step is wrapped in two implicit source substeps of dt/2.  Steps are
+ * replayed from a CUDA graph.  Asynchronous: call dg_check() to synchronize and collect
+ * device-side errors. */
 DG_API dg_status dg_rk_step(dg_ctx* ctx, double dt, int n_steps);
 
 /* Adjoint of the residual (for differentiable rollouts; the paper has no adjoint -- it is the
@@ -185,7 +208,7 @@ DG_API dg_status dg_rhs_vjp(dg_ctx* ctx, const double* U, const double* lam, dou
                             double* gammabar);
 
 /* Adjoint of one SSP-RK3 step from Un with step dt (App. B, Shu-Osher form, stages
- * recomputed from Un): on entry lam = dJ/dU^{n+1}, on exit lam = dJ/dU^n; *gammabar (host)
+ * recomputed from Un; SSP-RK54 contexts return DG_EUNSUPPORTED): on entry lam = dJ/dU^{n+1}, on exit lam = dJ/dU^n; *gammabar (host)
  * += dJ/dgamma through this step.  The positivity floor, if enabled, is not differentiated.
  * lam must not alias Un.  gammabar as for dg_rhs_vjp: NULL keeps the contribution in the
  * context's device accumulator and the call stays asynchronous. */
@@ -217,11 +240,12 @@ DG_API dg_status dg_set_launch(dg_ctx* ctx, int mode, int group_scale, int ctas_
  * time per step in ms.  Allocates one temporary state copy; synchronizes the stream. */
 DG_API dg_status dg_autotune(dg_ctx* ctx, double dt, int n_reps, int* config_out, double* ms_out);
 
-/* Convective time-step bound of Eq. dt_hyp on the context-held state:
- *   dt = cfl * dx_min / ((2N+1) * max over nodes of (|u| + a)),
+/* Convective time-step bound of Eq. dt_hyp (App. B) on the context-held state:
+ *   dt = c * cfl * dx_min / ((2N+1) * max over nodes of (|u| + a)),
+ * c the SSP coefficient of the context's time_scheme (1 for SSP-RK33, 1.508 for SSP-RK54),
  * taking the minimum over instances.  Navier-Stokes: a is the frozen mixture sound speed and
  * the result is min(dt_C, dt_D) with the diffusive bound of Eq. dt_para,
- *   dt_D = cfl * dx_min^2 / ((2N+1)^2 * max over nodes of max(mu/rho, mu/(rho Pr))).
+ *   dt_D = c * cfl * dx_min^2 / ((2N+1)^2 * max over nodes of max(mu/rho, mu/(rho Pr))).
  * Synchronizes the stream; *dt_out is a host double. */
 DG_API dg_status dg_max_dt(dg_ctx* ctx, double cfl, double* dt_out);
 
@@ -259,6 +283,27 @@ DG_API dg_status dg_two_point_flux(dg_ctx* ctx, int kind, int l, int n, const do
 DG_API dg_status dg_max_dt_noalloc(const dg_mesh_desc* inst, int n_inst, double gamma,
                                    const double* U, double cfl, void* cuda_stream,
                                    double* dt_out, const char** msg);
+
+/* Implicit source substep S_h of the Strang split (Sec. 3.1.3, Eqs. strang_split and
+ * source_residual), DG_NS_REACTING contexts only.  At every node the partial densities
+ * Y = (rho_1..rho_ns) take one backward-Euler step of length h >= 0 of the chemical source,
+ *   Y* - Y - h omega(Y*) = 0,
+ * solved by Newton's method from Y* = Y: the Jacobian by forward differences, column k with
+ * the perturbation eps_k = max(1e-7 |Y*_k|, 1e-12); the update by Gauss-Jordan elimination
+ * with partial pivoting; stop once max_s |dY_s| <= newton_tol * rho.  rho, the momentum and
+ * E stay fixed (the source has no momentum or energy part and sum_s omega_s = 0); the
+ * temperature of an iterate follows from the fixed internal energy E - |rho u|^2 / (2 rho).
+ * U and Uout are device pointers of dg_state_size() doubles; they may be equal (in place)
+ * but must not otherwise overlap.  A node still unconverged after newton_max_it updates
+ * keeps its last iterate and makes dg_check() return DG_ECONVERGENCE.  Asynchronous. */
+DG_API dg_status dg_source_step(dg_ctx* ctx, const double* U, double h, double* Uout);
+
+/* Element-wise device evaluation of n doubles x into y (device pointers), for testing the
+ * library's own math routines against CUDA's: kind 0 the table-driven exp of the reaction
+ * rates (Tang's method, 64-entry table), 1 the Newton-refined reciprocal, 2 CUDA's exp,
+ * 3 CUDA's correctly rounded 1/x.  cuda_stream is a cudaStream_t (NULL = legacy default);
+ * asynchronous.  Needs no context. */
+DG_API dg_status dg_math_fn(int kind, int64_t n, const double* x, double* y, void* cuda_stream);
 
 /* Message of the last error on this context (static string if ctx is NULL). */
 DG_API const char* dg_last_error(const dg_ctx* ctx);

@@ -339,7 +339,7 @@ def mixture(P: Problem, u):
 
 
 SSPRK33, SSPRK54 = 3, 54
-NEWTON_MAX_IT, NEWTON_TOL = 20, 1e-12
+NEWTON_MAX_IT, NEWTON_TOL = 40, 1e-12
 
 
 def ssp_table(scheme: int):

@@ -1089,19 +1089,30 @@ void ssp_step(const OrcProblem& P, const SspTable& t, double* U, double dt) {
 // T(Y) = (e - sum Y_s h0_s) / sum Y_s cv_s (the paper's inner NASA-9 Newton reduces to this).
 // Newton: J = dR/dY by forward differences column by column with
 // eps_k = max(1e-7 |Y_k|, 1e-12); the update solves J d = R by Gauss-Jordan elimination
-// (partial pivoting) and sets Y <- Y - d.  READING: the paper gives no stopping rule; the
-// iteration stops after the first update with max_k |d_k| <= tol * rho, or after max_it
-// updates (then the node counts as not converged).
+// (partial pivoting) and takes the step Y <- Y - lambda d.  READINGS: the paper names no
+// safeguard and no stopping rule.  A full Newton step from the initial composition can
+// overshoot far enough that the next iterate's temperature is negative and its rates are
+// not finite (on the reacting workload once h exceeds about 2e-5 s); so lambda = 1 is halved
+// (at most 30 times) while the temperature of the new iterate lies outside [T/2, 2T].
+// Partial densities are not bounded below: the backward-Euler root itself can hold a
+// slightly negative trace density (seen at 1e-8 of rho near equilibrium), and a positivity
+// limit would stall there.  The iteration stops after the first full step (lambda = 1) with
+// max_k |d_k| <= tol * rho, or after max_it updates (then the node counts as not converged).
 // ---------------------------------------------------------------------------------------
-void source_residual(const OrcMech& m, const double* Y, const double* Yn, double e, double h,
-                     double* R) {
-  const int ns = m.n_species;
+// Temperature of the partial densities Y at the fixed internal energy e.
+double temperature_of(const OrcMech& m, const double* Y, double e) {
   double rcv = 0.0, rh0 = 0.0;
-  for (int s = 0; s < ns; ++s) {
+  for (int s = 0; s < m.n_species; ++s) {
     rcv += Y[s] * m.cv[s];
     rh0 += Y[s] * m.h0[s];
   }
-  const double T = (e - rh0) / rcv;
+  return (e - rh0) / rcv;
+}
+
+void source_residual(const OrcMech& m, const double* Y, const double* Yn, double e, double h,
+                     double* R) {
+  const int ns = m.n_species;
+  const double T = temperature_of(m, Y, e);
   double w[8];
   species_rates(m, Y, T, w);
   for (int s = 0; s < ns; ++s) R[s] = Y[s] - Yn[s] - h * w[s];
@@ -1156,12 +1167,21 @@ int source_implicit_node(const OrcProblem& P, double* u, double h, int max_it, d
       for (int i = 0; i < ns; ++i) J[i * ns + k] = (Rp[i] - R[i]) / eps;
     }
     if (!gauss_jordan(ns, J, R)) return -1;
-    double dmax = 0.0;
-    for (int s = 0; s < ns; ++s) {
-      Y[s] -= R[s];
-      dmax = std::fmax(dmax, std::fabs(R[s]));
+    // the step, halved while the new temperature leaves [T/2, 2T]
+    const double T0 = temperature_of(m, Y, e);
+    double lam = 1.0, Yt[8];
+    for (int k = 0; k < 30; ++k) {
+      for (int s = 0; s < ns; ++s) Yt[s] = Y[s] - lam * R[s];
+      const double Tt = temperature_of(m, Yt, e);
+      if (Tt >= 0.5 * T0 && Tt <= 2.0 * T0) break;
+      lam *= 0.5;
     }
-    if (dmax <= tol * rho) {
+    bool small = lam == 1.0;
+    for (int s = 0; s < ns; ++s) {
+      small = small && std::fabs(R[s]) <= tol * rho;  // false for a non-finite update
+      Y[s] = Yt[s];
+    }
+    if (small) {
       for (int s = 0; s < ns; ++s) u[s] = Y[s];
       return it;
     }

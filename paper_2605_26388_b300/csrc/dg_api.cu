@@ -1,9 +1,9 @@
 // dg_api.cu -- the C-ABI of include/dgsem.h: context lifecycle, operators, launches.
 //
 // Host side only.  The context owns three FP64 state buffers (the current state and two
-// stage buffers, rotated so that no launch writes a buffer it reads), the device error
-// word, a scratch word for the time-step reduction, a private capture stream and the CUDA
-// graph that replays three SSP-RK3 steps (nine fused stage launches).
+// stage buffers, rotated so that no launch writes a buffer it reads; SSP-RK54 adds a fourth),
+// the device error word, a scratch word for the time-step reduction, a private capture stream
+// and the CUDA graph that replays three time steps (nine fused stage launches for SSP-RK3).
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -22,8 +22,10 @@ struct dg_ctx {
   int dim = 0, nv = 0;
   long long n_nodes_total = 0;
   std::vector<long long> offs;       // node offset per instance
-  double* buf[3] = {nullptr, nullptr, nullptr};
+  double* buf[4] = {nullptr, nullptr, nullptr, nullptr};  // buf[3]: SSP-RK54 only
   int cur = 0;                       // index of the buffer holding the current state
+  bool rk54 = false;                 // SSP-RK54 (the state stays in buf[cur]); else SSP-RK3
+  bool split = false;                // Strang-split implicit source (reacting)
   unsigned* err = nullptr;
   unsigned long long* lam = nullptr;
   std::string msg;
@@ -49,11 +51,12 @@ struct dg_ctx {
   dg::MechDev* d_mech = nullptr;
   double* fb = nullptr;
   std::vector<long long> fb_offs;
-  // primitive caches of the three state buffers and a scratch one (flux-type rows, then the
-  // FP64 temperature), and whether each cache matches its buffer's current contents
-  void* pc[4] = {nullptr, nullptr, nullptr, nullptr};
-  double* pT[4] = {nullptr, nullptr, nullptr, nullptr};
-  bool pvalid[3] = {false, false, false};
+  // primitive caches of the state buffers (slot 3 with SSP-RK54) and a scratch one (slot 4)
+  // (flux-type rows, then the FP64 temperature), and whether each cache matches its
+  // buffer's current contents
+  void* pc[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  double* pT[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  bool pvalid[4] = {false, false, false, false};
 };
 
 namespace {
@@ -146,6 +149,11 @@ dg_status check_desc(const dg_mesh_desc& m, int dim0, std::string& why) {
 // The kernels' copy of a mechanism: species data, per-reaction Arrhenius and K_c
 // coefficients, the species of each side's concentration product (at most three molecules;
 // index n_species stands for a factor 1) and the source coefficients W_s 1e6 (nu'' - nu').
+// 2^(j/64), j = 0..63, rounded once from long double: the table of the device exp.
+void fill_exp2_table(double* tab) {
+  for (int j = 0; j < 64; ++j) tab[j] = (double)std::exp2((long double)j / 64.0L);
+}
+
 dg_status pack_mechanism(const dg_mechanism& m, dg::MechDev& d, std::string& why) {
   std::memset(&d, 0, sizeof(d));
   if (m.n_species < 1 || m.n_species > DG_MAX_SPECIES || m.n_reactions < 0 ||
@@ -156,7 +164,7 @@ dg_status pack_mechanism(const dg_mechanism& m, dg::MechDev& d, std::string& why
   const int ns = m.n_species;
   d.ns = ns;
   d.nr = m.n_reactions;
-  for (int j = 0; j < 64; ++j) d.exp2tab[j] = (double)std::exp2((long double)j / 64.0L);
+  fill_exp2_table(d.exp2tab);
   for (int s = 0; s < ns; ++s) {
     if (!(m.W[s] > 0.0) || !(m.R[s] > 0.0) || !(m.cv[s] > 0.0) || !std::isfinite(m.h0[s]) ||
         !std::isfinite(m.W[s]) || !std::isfinite(m.R[s]) || !std::isfinite(m.cv[s])) {
@@ -239,10 +247,19 @@ void inst_args(const dg_ctx* c, int i, dg::InstArgs& I) {
   I.liftf = (float)I.lift;
 }
 
+// Coefficients of one Shu-Osher stage update (App. B), with X = U^n or a running sum:
+//   out = ca X + cb U + bdt L(U)                  (bdt = beta dt)
+//   acc = acc_a acc + acc_b U + acc_bdt L(U)      (only when acc is not null)
+struct StageCoef {
+  double ca = 0.0, cb = 0.0, bdt = 0.0;
+  double* acc = nullptr;
+  double acc_a = 0.0, acc_b = 0.0, acc_bdt = 0.0;
+};
+
 // Launch-wide fields (state pointers, stage coefficients, physics) and the host-precomputed
 // scalars in both precisions.
 void launch_args(const dg_ctx* c, dg::StageArgs& a, const double* U, const double* Un, double* out,
-                 int mode, double ca, double cb, double dt) {
+                 int mode, const StageCoef& k) {
   std::memset(&a, 0, sizeof(a));
   a.U = U;
   a.Un = Un;
@@ -250,9 +267,12 @@ void launch_args(const dg_ctx* c, dg::StageArgs& a, const double* U, const doubl
   a.err = c->err;
   a.stride = c->n_nodes_total;
   a.gamma = c->phys.gamma;
-  a.ca = ca;
-  a.cb = cb;
-  a.dt = dt;
+  a.ca = k.ca;
+  a.cb = k.cb;
+  a.dt = k.bdt;
+  a.acc = k.acc;
+  a.acc_a = k.acc_a;
+  a.acc_b = k.acc_b;
   a.mode = mode;
   a.surface = c->phys.surface;
   a.weak = (c->phys.volume == DG_VOL_WEAK) ? 1 : 0;
@@ -263,24 +283,27 @@ void launch_args(const dg_ctx* c, dg::StageArgs& a, const double* U, const doubl
   a.pd.gm1 = a.gamma - 1.0;
   a.pd.igm1 = 1.0 / (a.gamma - 1.0);
   a.pd.p_ref = a.p_ref;
-  a.pd.cbdt = cb * dt;
+  a.pd.cbdt = k.bdt;
+  a.pd.abdt = k.acc_bdt;
   a.pf.gamma = (float)a.gamma;
   a.pf.gm1 = (float)a.gamma - 1.0f;
   a.pf.igm1 = 1.0f / a.pf.gm1;
   a.pf.p_ref = (float)a.p_ref;
   a.pf.cbdt = (float)a.pd.cbdt;
-  a.need_un = (mode == 1 && ca != 0.0) ? 1 : 0;
+  a.pf.abdt = (float)a.pd.abdt;
+  a.need_un = (mode == 1 && k.ca != 0.0) ? 1 : 0;
   a.floor_on = (a.rho_floor > 0.0 || a.p_floor > 0.0) ? 1 : 0;
 }
 
 // One fused stage over all instances: mode 0 writes L(U), mode 1 the stage update.  One
 // launch per instance, or one batched launch for all of them.
-// Which context state buffer p is (0..2), or -1 for a caller buffer.
+// Which context state buffer p is (0..3), or -1 for a caller buffer.
 int buf_index(const dg_ctx* c, const double* p) {
-  for (int b = 0; b < 3; ++b)
-    if (c->buf[b] == p) return b;
+  for (int b = 0; b < 4; ++b)
+    if (p && c->buf[b] == p) return b;
   return -1;
 }
+constexpr int kScratch = 4;  // primitive cache slot of states that are not context buffers
 
 // Fill primitive cache slot k (0..2: a state buffer's, 3: scratch) from state U.
 dg_status fill_prims(dg_ctx* c, const double* U, int k, cudaStream_t s) {
@@ -295,12 +318,12 @@ dg_status fill_prims(dg_ctx* c, const double* U, int k, cudaStream_t s) {
 }
 
 dg_status run_stage_ns(dg_ctx* c, const double* U, const double* Un, double* out, int mode,
-                       double ca, double cb, double dt, cudaStream_t s) {
+                       const StageCoef& k, cudaStream_t s) {
   dg::ReactArgs a;
   std::memset(&a, 0, sizeof(a));
   // the input's primitive cache: its buffer's if valid, else computed now
   const int bin = buf_index(c, U);
-  const int kin = bin >= 0 ? bin : 3;
+  const int kin = bin >= 0 ? bin : kScratch;
   if (bin < 0 || !c->pvalid[bin]) {
     dg_status st = fill_prims(c, U, kin, s);
     if (st) return st;
@@ -317,6 +340,8 @@ dg_status run_stage_ns(dg_ctx* c, const double* U, const double* Un, double* out
     }
     c->pvalid[bout] = (mode == 1);
   }
+  const int bacc = buf_index(c, k.acc);
+  if (bacc >= 0) c->pvalid[bacc] = false;
   a.U = U;
   a.Un = Un;
   a.out = out;
@@ -324,10 +349,15 @@ dg_status run_stage_ns(dg_ctx* c, const double* U, const double* Un, double* out
   a.mech = c->d_mech;
   a.stride = c->n_nodes_total;
   a.mode = mode;
-  a.need_un = (mode == 1 && ca != 0.0) ? 1 : 0;
-  a.ca = ca;
-  a.cb = cb;
-  a.cbdt = cb * dt;
+  a.need_un = (mode == 1 && k.ca != 0.0) ? 1 : 0;
+  a.src = c->split ? 0 : 1;
+  a.ca = k.ca;
+  a.cb = k.cb;
+  a.cbdt = k.bdt;
+  a.acc = k.acc;
+  a.acc_a = k.acc_a;
+  a.acc_b = k.acc_b;
+  a.acc_bdt = k.acc_bdt;
   a.mu = c->phys.mu;
   a.kfac = c->phys.mu / c->phys.prandtl;
   a.p_ref = c->phys.p_ref;
@@ -357,11 +387,11 @@ dg_status run_stage_ns(dg_ctx* c, const double* U, const double* Un, double* out
 }
 
 dg_status run_stage(dg_ctx* c, const double* U, const double* Un, double* out, int mode,
-                    double ca, double cb, double dt, cudaStream_t s) {
-  if (c->ns) return run_stage_ns(c, U, Un, out, mode, ca, cb, dt, s);
+                    const StageCoef& k, cudaStream_t s) {
+  if (c->ns) return run_stage_ns(c, U, Un, out, mode, k, s);
   const int ec = c->phys.volume == DG_VOL_EC, fp32 = c->phys.precision == DG_FP32_MIXED;
   dg::StageArgs a;
-  launch_args(c, a, U, Un, out, mode, ca, cb, dt);
+  launch_args(c, a, U, Un, out, mode, k);
   if (c->batched) {
     a.insts = c->d_insts;
     a.items = c->d_items;
@@ -499,16 +529,111 @@ void drop_graph(dg_ctx* c) {
 const double kStageA[3] = {0.0, 0.75, 1.0 / 3.0};
 const double kStageB[3] = {1.0, 0.25, 2.0 / 3.0};
 
-// One SSP-RK3 step from buf[cur]; the new state lands in another buffer and cur moves.
+StageCoef rk3_coef(int stage, double dt) {  // stage 0..2
+  StageCoef k;
+  k.ca = kStageA[stage];
+  k.cb = kStageB[stage];
+  k.bdt = kStageB[stage] * dt;
+  return k;
+}
+
+// SSP-RK54 of Spiteri and Ruuth (SIAM J. Numer. Anal. 40(2), 2002), the paper's production
+// integrator (App. B; it names the scheme and its SSP coefficient, not the coefficients),
+// in Shu-Osher form with the published 15-digit values.  Non-zero entries only:
+//   U1 = U0 + b10 dt L(U0)
+//   U2 = a20 U0 + a21 U1 + b21 dt L(U1)
+//   U3 = a30 U0 + a32 U2 + b32 dt L(U2)
+//   U4 = a40 U0 + a43 U3 + b43 dt L(U3)
+//   U5 = a52 U2 + a53 U3 + b53 dt L(U3) + a54 U4 + b54 dt L(U4)
+struct Ssp54 {
+  double b10, a20, a21, b21, a30, a32, b32, a40, a43, b43, a52, a53, b53, a54, b54;
+};
+constexpr Ssp54 kRk54 = {0.391752226571890, 0.444370493651235, 0.555629506348765,
+                         0.368410593050371, 0.620101851488403, 0.379898148511597,
+                         0.251891774271694, 0.178079954393132, 0.821920045606868,
+                         0.544974750228521, 0.517231671970585, 0.096059710526147,
+                         0.063692468666290, 0.386708617503269, 0.226007483236906};
+
+// SSP coefficient (App. B, c~ = min alpha_ik / beta_ik over beta_ik > 0) of the context's scheme.
+double ssp_coefficient(const dg_ctx* c) {
+  if (!c->rk54) return 1.0;
+  const Ssp54& k = kRk54;
+  const double r[6] = {1.0 / k.b10, k.a21 / k.b21, k.a32 / k.b32, k.a43 / k.b43, k.a53 / k.b53,
+                       k.a54 / k.b54};
+  double m = r[0];
+  for (double x : r) m = std::fmin(m, x);
+  return m;
+}
+
+// Implicit source substep S_h (Sec. 3.1.3, Eqs. strang_split, source_residual) from U into
+// out (equal pointers: in place).  Writes the output's primitive cache when out is a
+// context buffer.
+dg_status run_source(dg_ctx* c, const double* U, double* out, double h, cudaStream_t s) {
+  dg::SourceArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.U = U;
+  a.out = out;
+  a.err = c->err;
+  a.mech = c->d_mech;
+  a.stride = c->n_nodes_total;
+  a.h = h;
+  a.max_it = c->phys.newton_max_it > 0 ? c->phys.newton_max_it : DG_NEWTON_MAX_IT;
+  a.tol = c->phys.newton_tol > 0.0 ? c->phys.newton_tol : DG_NEWTON_TOL;
+  a.p_ref = c->phys.p_ref;
+  a.ln1e4 = std::log(1.0e4);
+  a.copy_rest = (U != out) ? 1 : 0;
+  const int bout = buf_index(c, out);
+  if (bout >= 0) {
+    a.pout = c->pc[bout];
+    a.tout = c->pT[bout];
+    c->pvalid[bout] = true;
+  }
+  const int fp32 = c->phys.precision == DG_FP32_MIXED;
+  for (size_t i = 0; i < c->inst.size(); ++i) {
+    a.base = c->offs[i];
+    a.n = n_elem_of(c->inst[i]) * n_p_of(c->inst[i]);
+    cudaError_t e = dg::launch_source_implicit(c->n_species, fp32, a, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "implicit source launch");
+  }
+  return DG_OK;
+}
+
+// One time step from buf[cur]: SSP-RK3 (the new state lands in another buffer and cur
+// moves) or SSP-RK54 (the new state lands in buf[cur] again); under the Strang split
+// (Eq. strang_split) wrapped in two implicit source half steps.
 dg_status one_step(dg_ctx* c, double dt, cudaStream_t s) {
-  double* A = c->buf[c->cur];
-  double* B = c->buf[(c->cur + 1) % 3];
-  double* C = c->buf[(c->cur + 2) % 3];
   dg_status st;
-  if ((st = run_stage(c, A, A, B, 1, kStageA[0], kStageB[0], dt, s))) return st;
-  if ((st = run_stage(c, B, A, C, 1, kStageA[1], kStageB[1], dt, s))) return st;
-  if ((st = run_stage(c, C, A, B, 1, kStageA[2], kStageB[2], dt, s))) return st;
-  c->cur = (c->cur + 1) % 3;
+  if (c->split && (st = run_source(c, c->buf[c->cur], c->buf[c->cur], 0.5 * dt, s))) return st;
+  if (c->rk54) {
+    double* A = c->buf[c->cur];
+    double* B = c->buf[(c->cur + 1) % 4];
+    double* C = c->buf[(c->cur + 2) % 4];
+    double* D = c->buf[(c->cur + 3) % 4];
+    const Ssp54& r = kRk54;
+    StageCoef k;
+    k.cb = 1.0;
+    k.bdt = r.b10 * dt;
+    if ((st = run_stage(c, A, A, B, 1, k, s))) return st;                       // U1 -> B
+    k.ca = r.a20, k.cb = r.a21, k.bdt = r.b21 * dt;
+    if ((st = run_stage(c, B, A, C, 1, k, s))) return st;                       // U2 -> C
+    k.ca = r.a30, k.cb = r.a32, k.bdt = r.b32 * dt;
+    if ((st = run_stage(c, C, A, B, 1, k, s))) return st;                       // U3 -> B
+    k.ca = r.a40, k.cb = r.a43, k.bdt = r.b43 * dt;
+    k.acc = C, k.acc_a = r.a52, k.acc_b = r.a53, k.acc_bdt = r.b53 * dt;       // C: a52 U2 + a53 U3 + b53 dt L(U3)
+    if ((st = run_stage(c, B, A, D, 1, k, s))) return st;                       // U4 -> D
+    StageCoef k5;
+    k5.ca = 1.0, k5.cb = r.a54, k5.bdt = r.b54 * dt;
+    if ((st = run_stage(c, D, C, A, 1, k5, s))) return st;                      // U5 -> A
+  } else {
+    double* A = c->buf[c->cur];
+    double* B = c->buf[(c->cur + 1) % 3];
+    double* C = c->buf[(c->cur + 2) % 3];
+    if ((st = run_stage(c, A, A, B, 1, rk3_coef(0, dt), s))) return st;
+    if ((st = run_stage(c, B, A, C, 1, rk3_coef(1, dt), s))) return st;
+    if ((st = run_stage(c, C, A, B, 1, rk3_coef(2, dt), s))) return st;
+    c->cur = (c->cur + 1) % 3;
+  }
+  if (c->split && (st = run_source(c, c->buf[c->cur], c->buf[c->cur], 0.5 * dt, s))) return st;
   return DG_OK;
 }
 
@@ -532,6 +657,10 @@ dg_status dg_init_mesh(const dg_mesh_desc* inst, int n_inst, const dg_physics* p
   if (phys->precision != DG_FP64 && phys->precision != DG_FP32_MIXED) return DG_EINVAL;
   if (phys->equations != DG_NS_REACTING && !(phys->gamma > 1.0)) return DG_EINVAL;
   if (!std::isfinite(phys->p_ref)) return DG_EINVAL;
+  if (phys->time_scheme != DG_SSPRK33 && phys->time_scheme != DG_SSPRK54) return DG_EINVAL;
+  if (phys->chem_split != 0 && (phys->chem_split != 1 || phys->equations != DG_NS_REACTING))
+    return DG_EINVAL;
+  if (!std::isfinite(phys->newton_tol) || phys->newton_max_it > 1000) return DG_EINVAL;
   const bool navier_stokes = phys->equations != DG_EULER;
   dg::MechDev mech;
   if (navier_stokes) {
@@ -574,8 +703,10 @@ dg_status dg_init_mesh(const dg_mesh_desc* inst, int n_inst, const dg_physics* p
     off += n_elem_of(inst[i]) * n_p_of(inst[i]);
   }
   c->n_nodes_total = off;
+  c->rk54 = phys->time_scheme == DG_SSPRK54;
+  c->split = phys->chem_split == 1;
   const size_t bytes = sizeof(double) * (size_t)c->nv * (size_t)off;
-  for (int b = 0; b < 3; ++b) {
+  for (int b = 0; b < (c->rk54 ? 4 : 3); ++b) {
     if (cudaMalloc(&c->buf[b], bytes) != cudaSuccess) {
       cudaGetLastError();
       dg_free(c);
@@ -608,7 +739,8 @@ dg_status dg_init_mesh(const dg_mesh_desc* inst, int n_inst, const dg_physics* p
       return DG_ENOMEM;
     }
     const size_t rsz = phys->precision == DG_FP32_MIXED ? sizeof(float) : sizeof(double);
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < 5; ++k) {
+      if (k == 3 && !c->rk54) continue;
       if (cudaMalloc(&c->pc[k], 7 * rsz * (size_t)off) != cudaSuccess ||
           cudaMalloc(&c->pT[k], sizeof(double) * (size_t)off) != cudaSuccess) {
         cudaGetLastError();
@@ -689,7 +821,7 @@ dg_status dg_rhs(dg_ctx* c, const double* U, double* dUdt, double t) {
   if (!c) return DG_EINVAL;
   if (!U || !dUdt) return fail(c, DG_EINVAL, "null pointer");
   if (U == dUdt) return fail(c, DG_EINVAL, "U and dUdt must not overlap");
-  return run_stage(c, U, U, dUdt, 0, 0.0, 0.0, 0.0, c->stream);
+  return run_stage(c, U, U, dUdt, 0, StageCoef(), c->stream);
 }
 
 dg_status dg_rk_stage(dg_ctx* c, int stage, const double* Un, const double* Uprev, double dt,
@@ -699,8 +831,7 @@ dg_status dg_rk_stage(dg_ctx* c, int stage, const double* Un, const double* Upre
   if (!Un || !Uprev || !Uout) return fail(c, DG_EINVAL, "null pointer");
   if (Uout == Un || Uout == Uprev) return fail(c, DG_EINVAL, "Uout must not alias an input");
   if (!std::isfinite(dt)) return fail(c, DG_EINVAL, "dt must be finite");
-  return run_stage(c, Uprev, Un, Uout, 1, kStageA[stage - 1], kStageB[stage - 1], dt,
-                   c->stream);
+  return run_stage(c, Uprev, Un, Uout, 1, rk3_coef(stage - 1, dt), c->stream);
 }
 
 dg_status dg_rk_step(dg_ctx* c, double dt, int n_steps) {
@@ -775,13 +906,14 @@ dg_status dg_rk_step_vjp(dg_ctx* c, const double* Un, double dt, double* lam, do
   if (!Un || !lam) return fail(c, DG_EINVAL, "null pointer");
   if (Un == lam) return fail(c, DG_EINVAL, "lam must not alias Un");
   if (c->ns) return fail(c, DG_EUNSUPPORTED, "the adjoint exists for the Euler equations");
+  if (c->rk54) return fail(c, DG_EUNSUPPORTED, "the adjoint step reverses SSP-RK3");
   if (!std::isfinite(dt)) return fail(c, DG_EINVAL, "dt must be finite");
   dg_status st = ensure_adjoint(c);
   if (st) return st;
   double *W1 = c->adj[0], *W2 = c->adj[1], *T1 = c->adj[2], *T2 = c->adj[3], *T3 = c->adj[4];
   // recompute the stage states of this step
-  if ((st = run_stage(c, Un, Un, W1, 1, kStageA[0], kStageB[0], dt, c->stream))) return st;
-  if ((st = run_stage(c, W1, Un, W2, 1, kStageA[1], kStageB[1], dt, c->stream))) return st;
+  if ((st = run_stage(c, Un, Un, W1, 1, rk3_coef(0, dt), c->stream))) return st;
+  if ((st = run_stage(c, W1, Un, W2, 1, rk3_coef(1, dt), c->stream))) return st;
   // reverse Shu-Osher: U3 = 1/3 Un + 2/3 (U2 + dt L(U2)), U2 = 3/4 Un + 1/4 (U1 + dt L(U1)),
   // U1 = Un + dt L(Un)
   if ((st = run_vjp(c, W2, lam, T1, 1, kStageB[2], dt, nullptr, T2, 1, kStageA[2], kStageB[2] * dt))) return st;
@@ -896,8 +1028,9 @@ dg_status dg_max_dt(dg_ctx* c, double cfl, double* dt_out) {
       for (int l = 0; l < m.dim; ++l) dxmin = std::fmin(dxmin, (m.hi[l] - m.lo[l]) / m.nel[l]);
       const double n2 = (2.0 * m.N + 1.0) * (2.0 * m.N + 1.0);
       const double nu = c->phys.mu * irho / std::fmin(1.0, c->phys.prandtl);
-      double dt = cfl * dxmin / ((2 * m.N + 1) * lam);
-      if (nu > 0.0) dt = std::fmin(dt, cfl * dxmin * dxmin / (n2 * nu));
+      const double cs = cfl * ssp_coefficient(c);
+      double dt = cs * dxmin / ((2 * m.N + 1) * lam);
+      if (nu > 0.0) dt = std::fmin(dt, cs * dxmin * dxmin / (n2 * nu));
       best = std::fmin(best, dt);
     }
     *dt_out = best;
@@ -919,7 +1052,7 @@ dg_status dg_max_dt(dg_ctx* c, double cfl, double* dt_out) {
     if (!(lam > 0.0) || !std::isfinite(lam)) return fail(c, DG_ENONFINITE, "no finite signal speed");
     double dxmin = INFINITY;
     for (int l = 0; l < m.dim; ++l) dxmin = std::fmin(dxmin, (m.hi[l] - m.lo[l]) / m.nel[l]);
-    best = std::fmin(best, cfl * dxmin / ((2 * m.N + 1) * lam));
+    best = std::fmin(best, cfl * ssp_coefficient(c) * dxmin / ((2 * m.N + 1) * lam));
   }
   *dt_out = best;
   return DG_OK;
@@ -935,6 +1068,7 @@ dg_status dg_check(dg_ctx* c) {
   if (e != cudaSuccess) return cuda_fail(c, e, "dg_check read");
   if (w & 1u) return fail(c, DG_ENONFINITE, "a kernel produced a non-finite value");
   if (w & 2u) return fail(c, DG_EPOSITIVITY, "a kernel read a state with rho <= 0 or p <= 0");
+  if (w & 4u) return fail(c, DG_ECONVERGENCE, "the implicit source Newton iteration did not converge");
   return DG_OK;
 }
 
@@ -955,12 +1089,33 @@ dg_status dg_two_point_flux(dg_ctx* c, int kind, int l, int n, const double* uL,
   return e == cudaSuccess ? DG_OK : cuda_fail(c, e, "two-point flux launch");
 }
 
+dg_status dg_source_step(dg_ctx* c, const double* U, double h, double* Uout) {
+  if (!c) return DG_EINVAL;
+  if (!U || !Uout) return fail(c, DG_EINVAL, "null pointer");
+  if (c->phys.equations != DG_NS_REACTING)
+    return fail(c, DG_EUNSUPPORTED, "the implicit source step exists for reacting mixtures");
+  if (!std::isfinite(h) || h < 0.0) return fail(c, DG_EINVAL, "h must be finite and >= 0");
+  return run_source(c, U, Uout, h, c->stream);
+}
+
+dg_status dg_math_fn(int kind, int64_t n, const double* x, double* y, void* cuda_stream) {
+  if (kind < 0 || kind > 3 || n < 0 || (n > 0 && (!x || !y))) return DG_EINVAL;
+  dg::MathArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.x = x;
+  a.y = y;
+  a.n = n;
+  a.kind = kind;
+  fill_exp2_table(a.tab);
+  return dg::launch_math_fn(a, (cudaStream_t)cuda_stream) == cudaSuccess ? DG_OK : DG_ECUDA;
+}
+
 const char* dg_last_error(const dg_ctx* c) { return c ? c->msg.c_str() : kNullCtxMsg; }
 
 void dg_free(dg_ctx* c) {
   if (!c) return;
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
-  for (int b = 0; b < 3; ++b)
+  for (int b = 0; b < 4; ++b)
     if (c->buf[b]) cudaFree(c->buf[b]);
   if (c->err) cudaFree(c->err);
   if (c->lam) cudaFree(c->lam);
@@ -974,7 +1129,7 @@ void dg_free(dg_ctx* c) {
   if (c->gacc) cudaFree(c->gacc);
   if (c->d_mech) cudaFree(c->d_mech);
   if (c->fb) cudaFree(c->fb);
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < 5; ++k) {
     if (c->pc[k]) cudaFree(c->pc[k]);
     if (c->pT[k]) cudaFree(c->pT[k]);
   }

@@ -27,7 +27,7 @@ struct InstArgs {
 // sm_103a) or evaluates a double comparison of a uniform flag.
 template <class R>
 struct ScalarsT {
-  R gamma, gm1, igm1, p_ref, cbdt;
+  R gamma, gm1, igm1, p_ref, cbdt, abdt;
 };
 
 // Arguments of one fused stage launch (passed by value).
@@ -38,7 +38,11 @@ struct StageArgs {
   unsigned* err;       // device error word (bit 0 non-finite, bit 1 non-positive)
   long long stride;    // per-variable stride of the SoA state (total nodes)
   double gamma;
-  double ca, cb, dt;   // U^(k) = ca Un + cb (U^(k-1) + dt L)
+  double ca, cb, dt;   // U^(k) = ca Un + cb U^(k-1) + (beta dt) L, beta dt in pd/pf.cbdt
+  // optional second output of a stage update (the running sum of the last SSP-RK54 stage):
+  // acc = acc_a acc + acc_b U^(k-1) + (acc_beta dt) L, acc_beta dt in pd/pf.abdt; null: none
+  double* acc;
+  double acc_a, acc_b;
   int mode;            // 0: out = L(U); 1: RK stage update
   int surface;         // DG_SURF_*
   int weak;            // 1: weak-form volume operator (surface lifts F* only)
@@ -161,9 +165,12 @@ struct ReactArgs {
   int n_elem;
   int mode;            // 0: out = L(U); 1: stage update
   int need_un;
+  int src;             // 1: the Arrhenius source is part of L (0 under the Strang split)
   double s[3];         // 2 / dx_l
   double lift;         // 1 / w_0 = 1 / w_N
-  double ca, cb, cbdt;
+  double ca, cb, cbdt; // out = ca Un + cb U + cbdt L
+  double* acc;         // optional second output: acc = acc_a acc + acc_b U + acc_bdt L
+  double acc_a, acc_b, acc_bdt;
   double mu, kfac;     // viscosity; mu / Pr (conductivity = kfac * c_p)
   double p_ref;        // constant subtracted from the pressure in the momentum flux
   double ln1e4;        // ln 10^4 (for ln Z = ln 10^4 - ln T)
@@ -183,6 +190,34 @@ cudaError_t launch_reacting(int N, int ns, int fp32, const ReactArgs& a, cudaStr
 cudaError_t launch_react_prims(int ns, int fp32, const double* U, long long stride, long long base,
                                long long n_nodes, const MechDev* mech, double p_ref, void* P, double* T64,
                                unsigned* err, cudaStream_t s);
+// Implicit source substep (Strang split) over the nodes [base, base + n) of a state.
+struct SourceArgs {
+  const double* U;     // input state
+  double* out;         // output state (may equal U: each node is read, then written)
+  unsigned* err;       // device error word (bit 2: a node's Newton iteration did not converge)
+  const MechDev* mech;
+  void* pout;          // primitive cache of the output (flux type; null: not written)
+  double* tout;
+  long long stride, base, n;
+  double h;            // substep length
+  double tol;          // stop when max |dY| <= tol * rho
+  double p_ref, ln1e4;
+  int max_it;          // Newton updates per node at most
+  int copy_rest;       // 1: also copy momentum and energy (out != U)
+};
+cudaError_t launch_source_implicit(int ns, int fp32, const SourceArgs& a, cudaStream_t s);
+
+// Element-wise evaluation of a device math routine for the tests: kind 0 the library's
+// table-driven exp, 1 its Newton reciprocal, 2 CUDA's exp, 3 CUDA's 1/x.
+struct MathArgs {
+  const double* x;
+  double* y;
+  long long n;
+  int kind;
+  double tab[64];      // 2^(j/64)
+};
+cudaError_t launch_math_fn(const MathArgs& a, cudaStream_t s);
+
 // Largest |u| + a (frozen mixture sound speed) and largest 1/rho over one instance,
 // atomically max-ed into out2[0] and out2[1] (bit patterns of non-negative doubles).
 cudaError_t launch_max_speed_mix(int ns, const double* U, long long stride, long long base,

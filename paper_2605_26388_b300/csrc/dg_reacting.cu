@@ -1,5 +1,6 @@
-// dg_reacting.cu -- residual and SSP-RK3 stage of the single-temperature reacting
-// Navier-Stokes equations (Sec. 2 reacting system) on periodic 3D Cartesian meshes.
+// dg_reacting.cu -- residual, SSP-RK stage and implicit source substep of the
+// single-temperature reacting Navier-Stokes equations (Sec. 2 reacting system) on periodic
+// 3D Cartesian meshes.
 //
 // One stage is two launches over the elements of an instance:
 //   1. k_br1_faces: BR1 gradients (Sec. 3.1.2, Eq. br1_avg) of W = (u, v, w, T) at every node
@@ -229,6 +230,32 @@ __device__ __forceinline__ void load_species(const MechDev* __restrict__ mech, d
     const int k = t / NS, s = t % NS;
     const double* src = k == 0 ? mech->R : (k == 1 ? mech->cv : (k == 2 ? mech->h0 : mech->scale));
     sp[t] = src[s];
+  }
+}
+
+// Species production rates omega_s of one node (Sec. 3.1.3, Eqs. src_reaction_rate and
+// src_omega; App. C), FP64: k_f = exp(lnA + b ln T - Ta/T), ln K_c from the five-term fit in
+// Z = 1e4/T, R_r = k_f prod [X]^nu' - (k_f / K_c) prod [X]^nu'',
+// omega_s = sum_r W_s 1e6 (nu''_s - nu'_s) R_r.  The concentrations [X_s] sit in this
+// thread's slots X[s * xs] (slot NS holds 1.0, the factor of an empty place in a product).
+template <int NS>
+__device__ __forceinline__ void species_rates(const MechDev* __restrict__ mech, int nr, double T,
+                                              const double* X, int xs, const double* e2tab,
+                                              double ln1e4, double (&om)[NS]) {
+  const double lnT = log(T), invT = rcp64(T);
+  const double Z = 1.0e4 * invT, Zi = 1.0e-4 * T, lnZ = ln1e4 - lnT, Z2 = Z * Z;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) om[s] = 0.0;
+  for (int r = 0; r < nr; ++r) {
+    const RxnDev& Rx = mech->rx[r];
+    const double lkf = fma(Rx.b, lnT, fma(-Rx.Ta, invT, Rx.lnA));
+    const double lkc = fma(Rx.kc[0], Zi, fma(Rx.kc[2], lnZ, fma(Rx.kc[3], Z, fma(Rx.kc[4], Z2, Rx.kc[1]))));
+    const double kf = exp_tab(lkf, e2tab), kb = exp_tab(lkf - lkc, e2tab);
+    const double pf = X[Rx.f[0] * xs] * X[Rx.f[1] * xs] * X[Rx.f[2] * xs];
+    const double pb = X[Rx.bk[0] * xs] * X[Rx.bk[1] * xs] * X[Rx.bk[2] * xs];
+    const double rate = fma(kf, pf, -kb * pb);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) om[s] = fma(Rx.coef[s], rate, om[s]);
   }
 }
 
@@ -476,32 +503,15 @@ __global__ void __launch_bounds__(kRT) k_reacting_stage(const ReactArgs a) {
 #pragma unroll
   for (int k = 0; k < NV; ++k) r64[k] = Ar<R>::widen(res[k]);
 
-  // Arrhenius source (Sec. 3.1.3, Eqs. src_reaction_rate and src_omega; App. C), FP64:
-  // [X_s] = rho_s 1e-6 / W_s, k_f = exp(lnA + b ln T - Ta/T), ln K_c from the five-term fit
-  // in Z = 1e4/T, R_r = k_f prod [X]^nu' - (k_f / K_c) prod [X]^nu'',
-  // omega_s = sum_r W_s 1e6 (nu''_s - nu'_s) R_r.
+  // Arrhenius source (Sec. 3.1.3; App. C), FP64, [X_s] = rho_s 1e-6 / W_s; left out of L
+  // under the Strang split, where the implicit substep takes it
   const int nr = a.mech->nr;
-  if (nr > 0) {
-    const double T = cpT[1];
-    const double lnT = log(T), invT = rcp64(T);
-    const double Z = 1.0e4 * invT, Zi = 1.0e-4 * T, lnZ = a.ln1e4 - lnT, Z2 = Z * Z;
+  if (nr > 0 && a.src) {
 #pragma unroll
     for (int s2 = 0; s2 < NS; ++s2) X[s2 * kRT + t] = u64[s2] * sp[3 * NS + s2];
     X[NS * kRT + t] = 1.0;
     double om[NS];
-#pragma unroll
-    for (int s2 = 0; s2 < NS; ++s2) om[s2] = 0.0;
-    for (int r = 0; r < nr; ++r) {
-      const RxnDev& Rx = a.mech->rx[r];
-      const double lkf = fma(Rx.b, lnT, fma(-Rx.Ta, invT, Rx.lnA));
-      const double lkc = fma(Rx.kc[0], Zi, fma(Rx.kc[2], lnZ, fma(Rx.kc[3], Z, fma(Rx.kc[4], Z2, Rx.kc[1]))));
-      const double kf = exp_tab(lkf, e2tab), kb = exp_tab(lkf - lkc, e2tab);
-      const double pf = X[Rx.f[0] * kRT + t] * X[Rx.f[1] * kRT + t] * X[Rx.f[2] * kRT + t];
-      const double pb = X[Rx.bk[0] * kRT + t] * X[Rx.bk[1] * kRT + t] * X[Rx.bk[2] * kRT + t];
-      const double rate = fma(kf, pf, -kb * pb);
-#pragma unroll
-      for (int s2 = 0; s2 < NS; ++s2) om[s2] = fma(Rx.coef[s2], rate, om[s2]);
-    }
+    species_rates<NS>(a.mech, nr, cpT[1], X + t, kRT, e2tab, a.ln1e4, om);
 #pragma unroll
     for (int s2 = 0; s2 < NS; ++s2) r64[s2] += om[s2];
   }
@@ -515,6 +525,11 @@ __global__ void __launch_bounds__(kRT) k_reacting_stage(const ReactArgs a) {
     if (a.mode == 1) {
       x[k] = fma(a.cb, u64[k], a.cbdt * r64[k]);
       if (a.need_un) x[k] = fma(a.ca, a.Un[k * a.stride + gi], x[k]);
+      if (a.acc) {  // running sum of a later stage (SSP-RK54)
+        double y = fma(a.acc_b, u64[k], a.acc_bdt * r64[k]);
+        if (a.acc_a != 0.0) y = fma(a.acc_a, a.acc[k * a.stride + gi], y);
+        a.acc[k * a.stride + gi] = y;
+      }
     }
     finite = finite && finite64(x[k]);
     a.out[k * a.stride + gi] = x[k];
@@ -542,6 +557,179 @@ __global__ void k_react_prims(const double* U, long long stride, long long base,
     flag |= write_prims<NS, R>(u, sp, p_ref, P, T64, stride, base + q);
   }
   if (flag) atomicOr(err, flag);
+}
+
+// ---------------------------------------------------------------------------------------
+// Implicit source substep of the Strang split (Sec. 3.1.3, Eqs. strang_split and
+// source_residual): one thread per node advances the partial densities Y by one
+// backward-Euler step of length h,  R(Y) = Y - Y^n - h omega(Y) = 0,  by Newton's method
+// with rho, the momentum and E fixed.  Each Newton update takes NS + 1 evaluations of R
+// (at Y and at Y + eps_k e_k, eps_k = max(1e-7 |Y_k|, 1e-12): the forward-difference
+// Jacobian, column by column) and one Gauss-Jordan solve J d = R with partial pivoting, all
+// in registers (the concentrations of the evaluation in a per-thread shared-memory slot
+// table, indexed by the reactions' species lists).  The temperature of an iterate follows
+// from the fixed internal energy e = E - |rho u|^2 / (2 rho): T = (e - sum Y h0) / sum Y cv.
+// The step Y <- Y - lam d is guarded (the paper names no safeguard; a full step can
+// overshoot to a negative temperature and non-finite rates for h above about 2e-5 s on air
+// at 2000-8000 K): lam = 1 is halved (at most 30 times) while the new temperature leaves
+// [T/2, 2T].  The iteration stops after the first full step with max |d| <= tol rho; a node
+// that is still unconverged after max_it updates keeps its last iterate and sets bit 2 of
+// the error word.  FP64 throughout (both precisions); the output's primitive cache is written
+// in the flux type R.
+// ---------------------------------------------------------------------------------------
+constexpr int kCT = 128;  // threads per CTA of the implicit source kernel
+
+// Temperature of the partial densities Y at the fixed internal energy e.
+template <int NS>
+__device__ __forceinline__ double temp_of(const double (&Y)[NS], const double* sp, double e) {
+  double rcv = 0.0, rh0 = 0.0;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    rcv = fma(Y[s], sp[NS + s], rcv);
+    rh0 = fma(Y[s], sp[2 * NS + s], rh0);
+  }
+  return (e - rh0) * rcp64(rcv);
+}
+
+template <int NS>
+__device__ __forceinline__ void be_residual(const MechDev* __restrict__ mech, int nr, const double* sp,
+                                            const double (&Y)[NS], const double (&Yn)[NS], double e,
+                                            double h, double* X, const double* e2tab, double ln1e4,
+                                            double (&R)[NS]) {
+#pragma unroll
+  for (int s = 0; s < NS; ++s) X[s * kCT] = Y[s] * sp[3 * NS + s];
+  const double T = temp_of<NS>(Y, sp, e);
+  double om[NS];
+  species_rates<NS>(mech, nr, T, X, kCT, e2tab, ln1e4, om);
+#pragma unroll
+  for (int s = 0; s < NS; ++s) R[s] = fma(-h, om[s], Y[s] - Yn[s]);
+}
+
+template <int NS, class R>
+__global__ void __launch_bounds__(kCT) k_source_implicit(const SourceArgs a) {
+  __shared__ double sp[4 * NS];
+  __shared__ double e2tab[64];
+  __shared__ double Xs[(NS + 1) * kCT];
+  const int t = threadIdx.x;
+  load_species<NS>(a.mech, sp, 4);
+  for (int k = t; k < 64; k += kCT) e2tab[k] = a.mech->exp2tab[k];
+  double* X = Xs + t;
+  X[NS * kCT] = 1.0;
+  __syncthreads();
+  const long long q = blockIdx.x * (long long)kCT + t;
+  if (q >= a.n) return;
+  const long long gi = a.base + q;
+  const int nr = a.mech->nr;
+  double u[NS + 4];
+#pragma unroll
+  for (int v = 0; v < NS + 4; ++v) u[v] = a.U[v * a.stride + gi];
+  double Yn[NS], Y[NS], rho = 0.0;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    Yn[s] = Y[s] = u[s];
+    rho += u[s];
+  }
+  const double kin = fma(u[NS], u[NS], fma(u[NS + 1], u[NS + 1], u[NS + 2] * u[NS + 2]));
+  const double e = u[NS + 3] - 0.5 * kin * rcp64(rho);
+  const double lim = a.tol * rho;
+  bool done = false;
+  for (int it = 0; it < a.max_it && !done; ++it) {
+    double Rv[NS], J[NS][NS];
+    be_residual<NS>(a.mech, nr, sp, Y, Yn, e, a.h, X, e2tab, a.ln1e4, Rv);
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      double Yp[NS], Rp[NS];
+#pragma unroll
+      for (int s = 0; s < NS; ++s) Yp[s] = Y[s];
+      const double eps = fmax(1e-7 * fabs(Y[k]), 1e-12);
+      Yp[k] += eps;
+      be_residual<NS>(a.mech, nr, sp, Yp, Yn, e, a.h, X, e2tab, a.ln1e4, Rp);
+      const double ie = rcp64(eps);
+#pragma unroll
+      for (int i = 0; i < NS; ++i) J[i][k] = (Rp[i] - Rv[i]) * ie;
+    }
+    // Gauss-Jordan on [J | R] with partial pivoting (row swaps by compare-and-swap, so that
+    // every index stays compile-time and J stays in registers)
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+#pragma unroll
+      for (int i = k + 1; i < NS; ++i) {
+        if (fabs(J[i][k]) > fabs(J[k][k])) {
+#pragma unroll
+          for (int j = 0; j < NS; ++j) {
+            const double tmp = J[i][j];
+            J[i][j] = J[k][j];
+            J[k][j] = tmp;
+          }
+          const double tmp = Rv[i];
+          Rv[i] = Rv[k];
+          Rv[k] = tmp;
+        }
+      }
+      const double d = rcp64(J[k][k]);
+#pragma unroll
+      for (int j = 0; j < NS; ++j) J[k][j] *= d;
+      Rv[k] *= d;
+#pragma unroll
+      for (int i = 0; i < NS; ++i) {
+        if (i == k) continue;
+        const double f = J[i][k];
+#pragma unroll
+        for (int j = 0; j < NS; ++j) J[i][j] = fma(-f, J[k][j], J[i][j]);
+        Rv[i] = fma(-f, Rv[k], Rv[i]);
+      }
+    }
+    // the guarded step
+    const double T0 = temp_of<NS>(Y, sp, e);
+    double lam = 1.0, Yt[NS];
+    for (int k = 0; k < 30; ++k) {
+#pragma unroll
+      for (int s = 0; s < NS; ++s) Yt[s] = fma(-lam, Rv[s], Y[s]);
+      const double Tt = temp_of<NS>(Yt, sp, e);
+      if (Tt >= 0.5 * T0 && Tt <= 2.0 * T0) break;
+      lam *= 0.5;
+    }
+    bool small = lam == 1.0;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      // false for a non-finite update: the node then runs out of updates and is flagged
+      small = small && fabs(Rv[s]) <= lim;
+      Y[s] = Yt[s];
+    }
+    done = small;
+  }
+  unsigned flag = done ? 0u : 4u;
+  bool finite = true;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    u[s] = Y[s];
+    finite = finite && finite64(Y[s]);
+    a.out[s * a.stride + gi] = Y[s];
+  }
+  if (a.copy_rest) {
+#pragma unroll
+    for (int v = NS; v < NS + 4; ++v) a.out[v * a.stride + gi] = u[v];
+  }
+  if (a.pout) flag |= write_prims<NS, R>(u, sp, a.p_ref, reinterpret_cast<R*>(a.pout), a.tout, a.stride, gi);
+  if (!finite) flag |= 1u;
+  if (flag) atomicOr(a.err, flag);
+}
+
+// Element-wise math routines for the tests (see MathArgs).
+__global__ void k_math_fn(const MathArgs a) {
+  __shared__ double tab[64];
+  for (int k = threadIdx.x; k < 64; k += blockDim.x) tab[k] = a.tab[k];
+  __syncthreads();
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < a.n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double x = a.x[i];
+    double y;
+    if (a.kind == 0) y = exp_tab(x, tab);
+    else if (a.kind == 1) y = rcp64(x);
+    else if (a.kind == 2) y = exp(x);
+    else y = 1.0 / x;
+    a.y[i] = y;
+  }
 }
 
 // Largest |u| + a and largest 1/rho over the nodes of one instance.
@@ -644,6 +832,25 @@ cudaError_t launch_react_prims(int ns, int fp32, const double* U, long long stri
   else if (ns == 5 && fp32) k_react_prims<5, float><<<grid, 256, 0, s>>>(U, stride, base, n_nodes, mech, p_ref, (float*)P, T64, err);
   else if (ns == 5) k_react_prims<5, double><<<grid, 256, 0, s>>>(U, stride, base, n_nodes, mech, p_ref, (double*)P, T64, err);
   else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_source_implicit(int ns, int fp32, const SourceArgs& a, cudaStream_t s) {
+  if (a.n <= 0) return cudaSuccess;
+  const unsigned grid = (unsigned)((a.n + kCT - 1) / kCT);
+  if (ns == 1 && fp32) k_source_implicit<1, float><<<grid, kCT, 0, s>>>(a);
+  else if (ns == 1) k_source_implicit<1, double><<<grid, kCT, 0, s>>>(a);
+  else if (ns == 5 && fp32) k_source_implicit<5, float><<<grid, kCT, 0, s>>>(a);
+  else if (ns == 5) k_source_implicit<5, double><<<grid, kCT, 0, s>>>(a);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_math_fn(const MathArgs& a, cudaStream_t s) {
+  if (a.n <= 0) return cudaSuccess;
+  const long long want = (a.n + 255) / 256;
+  const unsigned grid = (unsigned)(want < 148 * 8 ? want : 148 * 8);
+  k_math_fn<<<grid, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 

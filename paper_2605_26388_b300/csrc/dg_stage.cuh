@@ -494,7 +494,7 @@ struct EulerStage {
 #pragma unroll
       for (int v = 0; v < NV; ++v) res[v] = Ar<R>::widen(acc[v]);
     } else {
-      // U^(k) = ca Un + cb (U^(k-1) + dt L), with the increment cb dt L formed in R
+      // U^(k) = ca Un + cb U^(k-1) + beta dt L, with the increment beta dt L formed in R
       const R cbdt = sc<R>(A).cbdt;
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
@@ -502,6 +502,15 @@ struct EulerStage {
         double x = fma(A.cb, SU[(el * NV + v) * NP + nd], inc);
         if (need_un) x = fma(A.ca, SN[(el * NV + v) * NP + nd], x);
         res[v] = x;
+      }
+      if (A.acc) {  // running sum of a later stage: acc = acc_a acc + acc_b U^(k-1) + acc_beta dt L
+        const R abdt = sc<R>(A).abdt;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          double y = fma(A.acc_b, SU[(el * NV + v) * NP + nd], Ar<R>::widen(abdt * acc[v]));
+          if (A.acc_a != 0.0) y = fma(A.acc_a, A.acc[v * A.stride + gi], y);
+          A.acc[v * A.stride + gi] = y;
+        }
       }
       if (A.floor_on) {  // positivity floor (off by default)
         if (A.rho_floor > 0.0 && res[0] < A.rho_floor) res[0] = A.rho_floor;

@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_lib", "libdgsem.so")
 
 DG_OK, DG_EINVAL, DG_ENOMEM, DG_ECUDA, DG_ENONFINITE, DG_EPOSITIVITY, DG_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
-DG_ETOOLARGE = -7
+DG_ETOOLARGE, DG_ECONVERGENCE = -7, -8
 NOALLOC_MAX_INSTANCES = 4096
 DG_EULER, DG_NAVIER_STOKES, DG_NS_REACTING = 0, 1, 2
 MAX_SPECIES, MAX_REACTIONS = 8, 32
@@ -25,15 +25,18 @@ VOL_STRONG, VOL_WEAK, VOL_EC = 0, 1, 2
 SURF_RUSANOV, SURF_HLLC, SURF_HLL, SURF_EC = 0, 1, 2, 3
 FP64, FP32_MIXED = 0, 1
 LAUNCH_PER_INSTANCE, LAUNCH_BATCHED = 0, 1
+SSPRK33, SSPRK54 = 0, 1
+NEWTON_MAX_IT, NEWTON_TOL = 40, 1e-12
+MATH_EXP_TABLE, MATH_RCP_NEWTON, MATH_EXP_CUDA, MATH_RCP_CUDA = 0, 1, 2, 3
 
 _STATUS = {0: "DG_OK", -1: "DG_EINVAL", -2: "DG_ENOMEM", -3: "DG_ECUDA", -4: "DG_ENONFINITE",
-           -5: "DG_EPOSITIVITY", -6: "DG_EUNSUPPORTED", -7: "DG_ETOOLARGE"}
+           -5: "DG_EPOSITIVITY", -6: "DG_EUNSUPPORTED", -7: "DG_ETOOLARGE", -8: "DG_ECONVERGENCE"}
 
 # Every entry point include/dgsem.h declares (checked by the CPU tests).
 EXPORTS = ["dg_init_mesh", "dg_state_size", "dg_instance_offset", "dg_set_state", "dg_get_state",
            "dg_rhs", "dg_rk_stage", "dg_rk_step", "dg_max_dt", "dg_check", "dg_gll",
            "dg_two_point_flux", "dg_max_dt_noalloc", "dg_set_launch", "dg_autotune",
-           "dg_rhs_vjp", "dg_rk_step_vjp", "dg_adjoint_gammabar",
+           "dg_rhs_vjp", "dg_rk_step_vjp", "dg_adjoint_gammabar", "dg_source_step", "dg_math_fn",
            "dg_last_error", "dg_free"]
 
 
@@ -82,7 +85,9 @@ class Physics(C.Structure):
     _fields_ = [("equations", C.c_int), ("volume", C.c_int), ("surface", C.c_int),
                 ("precision", C.c_int), ("gamma", C.c_double), ("rho_floor", C.c_double),
                 ("p_floor", C.c_double), ("p_ref", C.c_double), ("mu", C.c_double),
-                ("prandtl", C.c_double), ("chem", C.POINTER(Mechanism))]
+                ("prandtl", C.c_double), ("chem", C.POINTER(Mechanism)),
+                ("time_scheme", C.c_int), ("chem_split", C.c_int), ("newton_max_it", C.c_int),
+                ("newton_tol", C.c_double)]
 
 
 _lib = None
@@ -115,6 +120,8 @@ def lib():
         L.dg_rk_step_vjp.argtypes = [vp, vp, C.c_double, vp, dp]
         L.dg_adjoint_gammabar.argtypes = [vp, dp]
         L.dg_autotune.argtypes = [vp, C.c_double, ip, C.POINTER(C.c_int), dp]
+        L.dg_source_step.argtypes = [vp, vp, C.c_double, vp]
+        L.dg_math_fn.argtypes = [ip, C.c_int64, vp, vp, vp]
         L.dg_last_error.argtypes = [vp]
         L.dg_last_error.restype = C.c_char_p
         L.dg_free.argtypes = [vp]
@@ -171,7 +178,8 @@ class Solver:
 
     def __init__(self, meshes, volume=VOL_STRONG, surface=SURF_RUSANOV, precision=FP64,
                  gamma=1.4, rho_floor=0.0, p_floor=0.0, p_ref=0.0, stream=None,
-                 equations=DG_EULER, mu=0.0, prandtl=0.72, mechanism=None):
+                 equations=DG_EULER, mu=0.0, prandtl=0.72, mechanism=None,
+                 time_scheme=SSPRK33, chem_split=False, newton_max_it=0, newton_tol=0.0):
         import torch
         if isinstance(meshes, Mesh):
             meshes = [meshes]
@@ -179,7 +187,8 @@ class Solver:
         self.gamma = gamma
         arr = (MeshDesc * len(self.meshes))(*[m.c() for m in self.meshes])
         phys = Physics(equations, volume, surface, precision, gamma, rho_floor, p_floor, p_ref,
-                       mu, prandtl, None)
+                       mu, prandtl, None, time_scheme, 1 if chem_split else 0, newton_max_it,
+                       newton_tol)
         if mechanism is not None:
             mech = mechanism if isinstance(mechanism, Mechanism) else Mechanism.from_dict(mechanism)
             phys.chem = C.pointer(mech)  # copied by dg_init_mesh
@@ -256,6 +265,15 @@ class Solver:
     def rk_step(self, dt: float, n_steps: int = 1):
         self._call(lib().dg_rk_step(self._h, dt, n_steps), "dg_rk_step")
 
+    def source_step(self, U, h: float, out=None):
+        """Implicit source substep S_h (see dg_source_step); out may be U (in place)."""
+        import torch
+        if out is None:
+            out = torch.empty_like(U)
+        self._call(lib().dg_source_step(self._h, self._dev(U, "U"), h, self._dev(out, "Uout")),
+                   "dg_source_step")
+        return out
+
     def rhs_vjp(self, U, lam, Ubar=None):
         """(Ubar + (dL/dU)^T lam, lam . dL/dgamma) -- see dg_rhs_vjp."""
         import torch
@@ -322,3 +340,17 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+def math_fn(kind: int, x, out=None):
+    """The device math routine `kind` (MATH_*) applied element-wise to a float64 CUDA tensor."""
+    import torch
+    if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float64 and x.is_contiguous()):
+        raise TypeError("x must be a contiguous float64 CUDA tensor")
+    if out is None:
+        out = torch.empty_like(x)
+    st = lib().dg_math_fn(kind, x.numel(), C.c_void_p(x.data_ptr()), C.c_void_p(out.data_ptr()),
+                          C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if st != DG_OK:
+        raise DGError(st, "dg_math_fn")
+    return out

@@ -136,8 +136,14 @@ def test_small_steps_agree_with_explicit_euler(orc):
     assert abs(errs[0] / errs[1] - 4.0) < 0.05
 
 
-@pytest.mark.parametrize("h", [1e-12, 1e-9, 1e-6])
+@pytest.mark.parametrize("h", [1e-12, 1e-9, 1e-6, 4e-5])
 def test_conservation_and_convergence_on_the_workload(orc, h):
+    """Up to 4e-5 s (the SSP-RK54 transport step of this mesh is about 1.5e-4 s): every node
+    converges and conserves mass and atoms.  At 4e-5 s unguarded Newton steps overshoot to a
+    negative temperature and non-finite rates at two nodes of this mesh, and the
+    backward-Euler root itself holds trace densities slightly below zero (about -6e-7 rho):
+    backward Euler does not preserve positivity for these rates.  Up to 1e-5 s every density
+    stays positive."""
     m = wl.air5_mechanism()
     xi, _ = orc.gll(3)
     P = orc.Problem(dim=3, N=3, nel=(2, 2, 2), lo=(0.0,) * 3, hi=(2 * math.pi,) * 3,
@@ -152,7 +158,9 @@ def test_conservation_and_convergence_on_the_workload(orc, h):
         a1 = sum(V[s] * atoms[s] / m["W"][s] for s in range(5))
         assert np.abs(a1 - a0).max() <= 1e-13 * a0.max()
     assert np.array_equal(U[5:], V[5:])
-    assert (V[:5] > 0).all()
+    if h <= 1e-5:
+        assert (V[:5] > 0).all()
+    assert (V[:5] > -1e-6 * rho0).all()
     # the result solves the backward-Euler equation with the pinned explicit source
     for e, n in [(0, 0), (3, 21), (7, 63)]:
         S = orc.chem_source(P, V[:, e, n])
