@@ -78,6 +78,14 @@ def fp64_pipe(launch_ms):
                     "pipe 86% busy"}
 
 
+# FP64 instructions (thread level: DFMA + DADD + DMUL) per Newton update of
+# k_source_implicit<5,double>, from an ncu capture of one substep on the 12^3 split workload
+# (2.054e9 instructions over 442003 updates); None once the kernel changes.
+FP64_INSTR_PER_NEWTON_UPDATE = 2.054e9 / 442003
+SPLIT_DT = 1e-5          # the split workload's step (s)
+EXPLICIT_DT = 1e-13      # the explicit source's stable step on the same mechanism (s)
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -244,20 +252,24 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-reacting", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
-    ap.add_argument("--only", default="both", choices=["both", "fp32", "fp64", "reacting"],
+    ap.add_argument("--only", default="both", choices=["both", "fp32", "fp64", "reacting", "split"],
                     help="precision(s) to time, or only the reacting workload (profiling runs)")
     ap.add_argument("--reacting-nel", type=int, default=48,
                     help="elements per direction of the reacting workload (profiling runs)")
+    ap.add_argument("--no-split", action="store_true")
+    ap.add_argument("--split-nel", type=int, default=32,
+                    help="elements per direction of the split (implicit chemistry) workload")
     ap.add_argument("--nel", type=int, default=NEL, help="elements per direction (profiling runs)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         run_reference(args)
         return
-    if args.only == "reacting":
+    if args.only in ("reacting", "split"):
         import torch
         torch.cuda.set_device(dist_env()[2])
-        print(json.dumps({"reacting": run_reacting(args)}), flush=True)
+        fn = run_reacting if args.only == "reacting" else run_split
+        print(json.dumps({args.only: fn(args)}), flush=True)
         return
 
     import torch
@@ -334,6 +346,7 @@ def main():
     cpu = None if args.no_cpu_baseline or ws > 1 else oracle_sample()
     batched = None if args.no_batched else run_batched(args)
     reacting = None if args.no_reacting else run_reacting(args)
+    split = None if args.no_split else run_split(args)
     adjoint = None if args.no_adjoint else run_adjoint(args)
     fp64 = None
     if ms64:
@@ -355,6 +368,7 @@ def main():
         "cpu_baseline": cpu,
         "batched": batched,
         "reacting": reacting,
+        "reacting_split": split,
         "adjoint": adjoint,
     }
     print(json.dumps(line), flush=True)
@@ -463,6 +477,95 @@ def run_reacting(args):
             "fp32_mixed": {"ms_per_step": ms32, "value": 3 * dof / (ms32 * 1e-3), "unit": "DOF-updates/s",
                            "note": "fluxes, gradients, viscous terms in FP32 (momentum flux shifted by "
                                    "p_ref = 101325 Pa); mixture state, Arrhenius source, update FP64"}}
+
+
+def run_split(args):
+    """The stiff-chemistry workload: the reacting workload on 32^3 elements (N = 3, 2.1 M
+    nodes) advanced by the Strang split (Eq. strang_split): SSP-RK54 transport (five BR1 +
+    stage launch pairs, no source in L) between two implicit source substeps of dt/2 (one
+    k_source_implicit launch each), at dt = 1e-5 s.  For comparison, the explicit path (source
+    in L, SSP-RK3) is stable only below about 1e-12 s on this mechanism; it is timed at
+    1e-13 s on the same mesh.  Transport in FP64 and FP32-mixed; chemistry FP64 in both.
+    Steps are timed after three warm-up steps (the first substeps, far from chemical
+    equilibrium, take the most Newton updates); the substep is also timed alone, with the
+    Newton updates it took."""
+    import torch
+    from paper_2605_26388_b300 import dgsem, workloads as wl
+    nel, n_deg = args.split_nel, 3
+    mech = wl.air5_mechanism()
+    mu = wl.reacting_tgv_viscosity(mech)
+    x, _, _ = dgsem.gll(n_deg)
+    U = torch.from_numpy(wl.reacting_tgv_3d(nel, x, mech).reshape(9, -1)).cuda()
+    steps = max(2, args.steps // 20)
+    mesh = dgsem.Mesh(3, n_deg, (nel,) * 3, (0.0,) * 3, (2 * math.pi,) * 3)
+
+    def events():
+        return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed_steps(S, dt, k):
+        e0, e1 = events()
+        torch.cuda.synchronize()
+        e0.record()
+        S.rk_step(dt, k)
+        e1.record()
+        torch.cuda.synchronize()
+        S.check()
+        return e0.elapsed_time(e1) / k
+
+    out = {"workload": f"3D reacting NS, 5-species air, 17 reactions, N=3, {nel}^3, BR1 Re=1600, Rusanov; "
+                       "Strang split: SSP-RK54 transport + implicit backward-Euler chemistry substeps",
+           "dt": SPLIT_DT, "steps": steps}
+    for name, prec in (("fp64", dgsem.FP64), ("fp32_mixed", dgsem.FP32_MIXED)):
+        S = dgsem.Solver(mesh, equations=dgsem.DG_NS_REACTING, mu=mu, prandtl=0.72, mechanism=mech,
+                         precision=prec, p_ref=101325.0 if prec == dgsem.FP32_MIXED else 0.0,
+                         time_scheme=dgsem.SSPRK54, chem_split=True)
+        S.set_state(U)
+        transport_dt = S.max_dt(1.0)
+        S.rk_step(SPLIT_DT, 3)
+        S.check()
+        S.newton_updates()
+        ms = timed_steps(S, SPLIT_DT, steps)
+        upd_steps = S.newton_updates()
+        V = S.get_state()
+        W = torch.empty_like(V)
+        reps, times = 3, []
+        for _ in range(reps):  # the same substep three times: median launch time
+            e0, e1 = events()
+            torch.cuda.synchronize()
+            e0.record()
+            S.source_step(V, 0.5 * SPLIT_DT, W)
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        S.check()
+        chem_ms = sorted(times)[reps // 2]
+        upd = S.newton_updates() // reps
+        nodes = S.n_nodes
+        r = {"ms_per_step": ms, "sim_seconds_per_s": SPLIT_DT / (ms * 1e-3),
+             "transport_dt_bound": transport_dt, "gpu_launches_per_step": 2 * 5 + 2,
+             "newton_updates_per_node_per_substep": upd_steps / (2 * steps * nodes),
+             "source_substep": {"kernel": "k_source_implicit<5,double>", "ms": chem_ms, "nodes": nodes,
+                                "newton_updates": upd, "updates_per_node": upd / nodes,
+                                "share_of_step": 2 * chem_ms / ms}}
+        if FP64_INSTR_PER_NEWTON_UPDATE:
+            ach = upd * FP64_INSTR_PER_NEWTON_UPDATE / (chem_ms * 1e-3) / 1e9
+            r["source_substep"]["roofline"] = {
+                "bound": "alu", "unit": "G FP64 instr/s", "achieved": ach, "peak": FP64_PEAK_GINSTR,
+                "frac": ach / FP64_PEAK_GINSTR, "peak_kind": "nominal (1.25 TFLOP/s FP64 / 2)",
+                "instr_per_update": FP64_INSTR_PER_NEWTON_UPDATE}
+        S.close()
+        out[name] = r
+    # the explicit path on the same mesh: source in L, SSP-RK3, at its stable step
+    S = dgsem.Solver(mesh, equations=dgsem.DG_NS_REACTING, mu=mu, prandtl=0.72, mechanism=mech)
+    S.set_state(U)
+    S.rk_step(EXPLICIT_DT, 3)
+    S.check()
+    ms_exp = timed_steps(S, EXPLICIT_DT, steps)
+    S.close()
+    out["explicit_fp64"] = {"dt": EXPLICIT_DT, "ms_per_step": ms_exp,
+                            "sim_seconds_per_s": EXPLICIT_DT / (ms_exp * 1e-3)}
+    out["speedup_sim_time_fp64"] = out["fp64"]["sim_seconds_per_s"] / out["explicit_fp64"]["sim_seconds_per_s"]
+    return out
 
 
 def run_adjoint(args):

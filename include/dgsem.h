@@ -298,6 +298,12 @@ DG_API dg_status dg_max_dt_noalloc(const dg_mesh_desc* inst, int n_inst, double 
  * keeps its last iterate and makes dg_check() return DG_ECONVERGENCE.  Asynchronous. */
 DG_API dg_status dg_source_step(dg_ctx* ctx, const double* U, double h, double* Uout);
 
+/* Newton updates taken by all nodes in the implicit source substeps (dg_source_step and the
+ * split steps of dg_rk_step) since the previous call, into *count (host); resets the count.
+ * The work of a substep is proportional to it (NS + 1 evaluations of the source per update).
+ * Synchronizes the stream. */
+DG_API dg_status dg_newton_updates(dg_ctx* ctx, int64_t* count);
+
 /* Element-wise device evaluation of n doubles x into y (device pointers), for testing the
  * library's own math routines against CUDA's: kind 0 the table-driven exp of the reaction
  * rates (Tang's method, 64-entry table), 1 the Newton-refined reciprocal, 2 CUDA's exp,

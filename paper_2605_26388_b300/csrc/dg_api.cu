@@ -27,7 +27,7 @@ struct dg_ctx {
   bool rk54 = false;                 // SSP-RK54 (the state stays in buf[cur]); else SSP-RK3
   bool split = false;                // Strang-split implicit source (reacting)
   unsigned* err = nullptr;
-  unsigned long long* lam = nullptr;
+  unsigned long long* lam = nullptr;  // [0..1] time-step reductions, [2] Newton update count
   std::string msg;
   cudaGraphExec_t gexec = nullptr;   // three RK steps starting from buf[0]
   double g_dt = 0.0;
@@ -582,6 +582,7 @@ dg_status run_source(dg_ctx* c, const double* U, double* out, double h, cudaStre
   a.p_ref = c->phys.p_ref;
   a.ln1e4 = std::log(1.0e4);
   a.copy_rest = (U != out) ? 1 : 0;
+  a.updates = c->lam + 2;
   const int bout = buf_index(c, out);
   if (bout >= 0) {
     a.pout = c->pc[bout];
@@ -714,12 +715,13 @@ dg_status dg_init_mesh(const dg_mesh_desc* inst, int n_inst, const dg_physics* p
     }
   }
   if (cudaMalloc(&c->err, sizeof(unsigned)) != cudaSuccess ||
-      cudaMalloc(&c->lam, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+      cudaMalloc(&c->lam, 3 * sizeof(unsigned long long)) != cudaSuccess) {
     cudaGetLastError();
     dg_free(c);
     return DG_ENOMEM;
   }
   if (cudaMemset(c->err, 0, sizeof(unsigned)) != cudaSuccess ||
+      cudaMemset(c->lam, 0, 3 * sizeof(unsigned long long)) != cudaSuccess ||
       cudaMemset(c->buf[0], 0, bytes) != cudaSuccess ||
       cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
@@ -1096,6 +1098,18 @@ dg_status dg_source_step(dg_ctx* c, const double* U, double h, double* Uout) {
     return fail(c, DG_EUNSUPPORTED, "the implicit source step exists for reacting mixtures");
   if (!std::isfinite(h) || h < 0.0) return fail(c, DG_EINVAL, "h must be finite and >= 0");
   return run_source(c, U, Uout, h, c->stream);
+}
+
+dg_status dg_newton_updates(dg_ctx* c, int64_t* count) {
+  if (!c) return DG_EINVAL;
+  if (!count) return fail(c, DG_EINVAL, "null pointer");
+  unsigned long long v = 0;
+  cudaError_t e = cudaMemcpyAsync(&v, c->lam + 2, sizeof(v), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->lam + 2, 0, sizeof(v), c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "dg_newton_updates");
+  *count = (int64_t)v;
+  return DG_OK;
 }
 
 dg_status dg_math_fn(int kind, int64_t n, const double* x, double* y, void* cuda_stream) {

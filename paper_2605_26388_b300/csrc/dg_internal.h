@@ -204,6 +204,7 @@ struct SourceArgs {
   double p_ref, ln1e4;
   int max_it;          // Newton updates per node at most
   int copy_rest;       // 1: also copy momentum and energy (out != U)
+  unsigned long long* updates;  // device counter: Newton updates taken, summed over nodes
 };
 cudaError_t launch_source_implicit(int ns, int fp32, const SourceArgs& a, cudaStream_t s);
 

@@ -633,7 +633,8 @@ __global__ void __launch_bounds__(kCT) k_source_implicit(const SourceArgs a) {
   const double e = u[NS + 3] - 0.5 * kin * rcp64(rho);
   const double lim = a.tol * rho;
   bool done = false;
-  for (int it = 0; it < a.max_it && !done; ++it) {
+  int it = 0;
+  for (; it < a.max_it && !done; ++it) {
     double Rv[NS], J[NS][NS];
     be_residual<NS>(a.mech, nr, sp, Y, Yn, e, a.h, X, e2tab, a.ln1e4, Rv);
 #pragma unroll
@@ -697,6 +698,13 @@ __global__ void __launch_bounds__(kCT) k_source_implicit(const SourceArgs a) {
       Y[s] = Yt[s];
     }
     done = small;
+  }
+  // Newton updates of this node into the launch's counter (one atomic per converged group of
+  // lanes)
+  {
+    const unsigned mask = __activemask();
+    const unsigned sum = __reduce_add_sync(mask, (unsigned)it);
+    if ((threadIdx.x & 31) == __ffs(mask) - 1) atomicAdd(a.updates, (unsigned long long)sum);
   }
   unsigned flag = done ? 0u : 4u;
   bool finite = true;

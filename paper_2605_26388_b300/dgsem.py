@@ -36,7 +36,8 @@ _STATUS = {0: "DG_OK", -1: "DG_EINVAL", -2: "DG_ENOMEM", -3: "DG_ECUDA", -4: "DG
 EXPORTS = ["dg_init_mesh", "dg_state_size", "dg_instance_offset", "dg_set_state", "dg_get_state",
            "dg_rhs", "dg_rk_stage", "dg_rk_step", "dg_max_dt", "dg_check", "dg_gll",
            "dg_two_point_flux", "dg_max_dt_noalloc", "dg_set_launch", "dg_autotune",
-           "dg_rhs_vjp", "dg_rk_step_vjp", "dg_adjoint_gammabar", "dg_source_step", "dg_math_fn",
+           "dg_rhs_vjp", "dg_rk_step_vjp", "dg_adjoint_gammabar", "dg_source_step", "dg_newton_updates",
+           "dg_math_fn",
            "dg_last_error", "dg_free"]
 
 
@@ -121,6 +122,7 @@ def lib():
         L.dg_adjoint_gammabar.argtypes = [vp, dp]
         L.dg_autotune.argtypes = [vp, C.c_double, ip, C.POINTER(C.c_int), dp]
         L.dg_source_step.argtypes = [vp, vp, C.c_double, vp]
+        L.dg_newton_updates.argtypes = [vp, C.POINTER(C.c_int64)]
         L.dg_math_fn.argtypes = [ip, C.c_int64, vp, vp, vp]
         L.dg_last_error.argtypes = [vp]
         L.dg_last_error.restype = C.c_char_p
@@ -273,6 +275,12 @@ class Solver:
         self._call(lib().dg_source_step(self._h, self._dev(U, "U"), h, self._dev(out, "Uout")),
                    "dg_source_step")
         return out
+
+    def newton_updates(self) -> int:
+        """Newton updates of the implicit substeps since the previous call (resets the count)."""
+        n = C.c_int64()
+        self._call(lib().dg_newton_updates(self._h, C.byref(n)), "dg_newton_updates")
+        return int(n.value)
 
     def rhs_vjp(self, U, lam, Ubar=None):
         """(Ubar + (dL/dU)^T lam, lam . dL/dgamma) -- see dg_rhs_vjp."""

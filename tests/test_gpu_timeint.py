@@ -221,6 +221,10 @@ def test_source_step_matches_oracle(env, orc, h, prec):
     S.check()
     ref, it = orc.source_implicit(P, U, h)
     assert it > 0
+    n_nodes = U.shape[1] * U.shape[2]
+    updates = S.newton_updates()
+    assert n_nodes <= updates <= it * n_nodes + n_nodes  # every node takes at least one update
+    assert S.newton_updates() == 0                       # the count was reset
     got = out.cpu().numpy().reshape(U.shape)
     rho = U[:5].sum(axis=0)
     assert np.abs(got[:5] - ref[:5]).max() <= 1e-10 * rho.max()
