@@ -4,7 +4,8 @@ A plain, slow FP64 CPU implementation of the DGSEM residual, numerical fluxes, S
 and SSP-RK54 steps and time-step bound of the paper's method (arXiv 2605.26388, Sec. 2,
 Sec. 3.1.1, App. A, App. B), and of the reacting Navier-Stokes residual (BR1 viscous terms,
 Sec. 3.1.2; Arrhenius source, Sec. 3.1.3 and App. C) with its implicit Strang-split source
-substep (Sec. 3.1.3), written in C++ (``dg_oracle.cpp``) and loaded here with ctypes.  It
+substep (Sec. 3.1.3), and the Hennemann-Gassner DG/FV shock capturing of the Euler residual
+(Sec. 3.1.1, Eq. vol_blend; App. A), written in C++ (``dg_oracle.cpp``) and loaded here with ctypes.  It
 shares no code with the CUDA library.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
 CPU-baseline leg of ``bench.py`` may import it.
 
@@ -14,6 +15,7 @@ Parity status of each function is stated in its docstring ("pinned by ..." or
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import subprocess
 from dataclasses import dataclass, field
@@ -74,6 +76,8 @@ class _Problem(C.Structure):
         ("gamma", C.c_double), ("mu", C.c_double), ("prandtl", C.c_double),
         ("rho_floor", C.c_double), ("p_floor", C.c_double),
         ("mech", C.POINTER(_Mech)), ("parts", C.c_int),
+        ("shock", C.c_int), ("alpha_min", C.c_double), ("alpha_max", C.c_double),
+        ("sharpness", C.c_double),
     ]
 
 
@@ -95,6 +99,10 @@ class Problem:
     p_floor: float = 0.0
     mech: dict = None   # NS_REACTING: mechanism dictionary (species and reactions)
     parts: int = 0      # NS_REACTING: 1 inviscid, 2 viscous, 4 source; 0 = all
+    shock: bool = False  # Euler: Hennemann-Gassner DG/FV blending
+    alpha_min: float = 0.001
+    alpha_max: float = 0.5
+    sharpness: float = math.log(9999.0)
 
     @property
     def nvars(self) -> int:
@@ -125,6 +133,8 @@ class Problem:
                      (C.c_double * 3)(*hi), self.equations, self.volume, self.surface,
                      self.gamma, self.mu, self.prandtl, self.rho_floor, self.p_floor)
         p.parts = self.parts
+        p.shock = 1 if self.shock else 0
+        p.alpha_min, p.alpha_max, p.sharpness = self.alpha_min, self.alpha_max, self.sharpness
         if self.mech is not None:
             p._mech_keep = mechanism(self.mech)  # kept alive with the structure
             p.mech = C.pointer(p._mech_keep)
@@ -158,6 +168,9 @@ def lib():
         _lib.orc_chem_source.argtypes = [pp, dp, dp]
         _lib.orc_mixture.argtypes = [pp, dp, dp, dp]
         ip = C.POINTER(C.c_int)
+        _lib.orc_shock_alpha.argtypes = [pp, dp, dp, dp]
+        _lib.orc_fv_residual.argtypes = [pp, dp, dp]
+        _lib.orc_modes.argtypes = [pp, dp, dp]
         _lib.orc_ssp_table.argtypes = [C.c_int, dp, dp, ip, dp]
         _lib.orc_ssp_steps.argtypes = [pp, C.c_int, dp, C.c_double, C.c_int]
         _lib.orc_source_implicit.argtypes = [pp, dp, C.c_double, C.c_int, C.c_double, ip]
@@ -392,3 +405,40 @@ def strang_steps(P: Problem, scheme: int, U: np.ndarray, dt: float, n_steps: int
     _check(lib().orc_strang_steps(C.byref(c), scheme, _ptr(U), dt, n_steps, max_it, tol, C.byref(it)),
            "strang_steps")
     return U, it.value
+
+
+def shock_alpha(P: Problem, U: np.ndarray):
+    """(alpha_raw, alpha): the Hennemann-Gassner blending coefficient of every element from
+    the modal smoothness of rho p, before and after the face-neighbourhood maximum (Sec.
+    3.1.1 "Shock Indicator and Smoothing"; App. A "Shock Capturing").  Pinned by the modes of
+    known Legendre expansions, the sigmoid's midpoint at E = T, the clipping bounds and the
+    neighbourhood rule."""
+    U = np.ascontiguousarray(U, dtype=np.float64).reshape(P.shape)
+    a = np.zeros(P.n_elem)
+    b = np.zeros(P.n_elem)
+    c = P._c()
+    _check(lib().orc_shock_alpha(C.byref(c), _ptr(U), _ptr(a), _ptr(b)), "shock_alpha")
+    return a, b
+
+
+def fv_residual(P: Problem, U: np.ndarray) -> np.ndarray:
+    """The first-order sub-cell finite-volume residual alone (Eq. vol_blend's R^FV).  Pinned
+    by conservation (sum_i w_i R_i telescopes to the element-face fluxes), free-stream
+    preservation, first-order consistency with -div F, and monotone (no new extrema) steps
+    of a jump."""
+    U = np.ascontiguousarray(U, dtype=np.float64).reshape(P.shape)
+    dU = np.zeros_like(U)
+    c = P._c()
+    _check(lib().orc_fv_residual(C.byref(c), _ptr(U), _ptr(dU)), "fv_residual")
+    return dU
+
+
+def modes(P: Problem, q) -> np.ndarray:
+    """Orthonormal tensor-Legendre coefficients of one element's nodal field (mode index in
+    place of the node index).  Pinned against expansions evaluated with numpy's Legendre
+    module."""
+    q = np.ascontiguousarray(q, dtype=np.float64).reshape(-1)
+    m = np.zeros_like(q)
+    c = P._c()
+    _check(lib().orc_modes(C.byref(c), _ptr(q), _ptr(m)), "modes")
+    return m

@@ -17,6 +17,10 @@
 //                    interface flux (Eq. br1_flux), diffusive time-step bound Delta t_D
 //   Sec. 3.1.3       Arrhenius source (Eqs. src_reaction_rate, src_omega)
 //   App. B           SSP-RK in Shu-Osher form; convective time-step bound Delta t_C
+//   Sec. 3.1.1, App. A  Hennemann-Gassner indicator, neighbourhood maximum and the DG/FV
+//                    sub-cell blend (Eq. vol_blend)
+//   Sec. 3.1.3       implicit source substep and Strang split (Eqs. strang_split,
+//                    source_residual)
 // Readings of passages the paper leaves open are marked READING below.
 //
 // Loops are written per element, per node, per direction, exactly in the order the
@@ -66,6 +70,8 @@ struct OrcProblem {
   double rho_floor, p_floor;  // <= 0 disables the positivity floor
   const OrcMech* mech;        // ORC_NS_REACTING: species and reactions
   int parts;                  // ORC_NS_REACTING: 1 inviscid, 2 viscous, 4 source (0 = all)
+  int shock;                  // Euler: 1 = Hennemann-Gassner DG/FV blending of the residual
+  double alpha_min, alpha_max, sharpness;  // blending bounds and the sigmoid's steepness s
 };
 
 }  // extern "C"
@@ -454,6 +460,172 @@ void euler_element_residual(const OrcProblem& P, const Mesh& M, const Ops& ops,
       dU[((size_t)v * M.n_elem + e) * M.n_nodes + nd] = R[nd * nv + v];
 }
 
+// ---------------------------------------------------------------------------------------
+// Hennemann-Gassner shock capturing (Sec. 3.1.1 "Shock Indicator and Smoothing" and Eq.
+// vol_blend; App. A "Shock Capturing").
+//
+// Modes: the nodal values of the indicator field on the element are the degree-N
+// interpolant's values; its coefficients in the orthonormal tensor Legendre basis
+// P~_j = sqrt((2j+1)/2) P_j follow from m = V^{-1} q along every direction, with the
+// Vandermonde matrix V_ij = P~_j(x_i) on the GLL nodes (inverted by Gauss-Jordan in long
+// double).
+// ---------------------------------------------------------------------------------------
+std::vector<double> modal_matrix(int N) {
+  const int n1 = N + 1;
+  std::vector<long double> x, w;
+  gll_rule(N, x, w);
+  std::vector<long double> A((size_t)n1 * 2 * n1, 0.0L);  // [V | I]
+  for (int i = 0; i < n1; ++i) {
+    for (int j = 0; j < n1; ++j) {
+      long double Pj, Pjm1;
+      legendre(j, x[i], Pj, Pjm1);
+      A[(size_t)i * 2 * n1 + j] = std::sqrt((2.0L * j + 1.0L) / 2.0L) * Pj;
+    }
+    A[(size_t)i * 2 * n1 + n1 + i] = 1.0L;
+  }
+  for (int k = 0; k < n1; ++k) {
+    int piv = k;
+    for (int i = k + 1; i < n1; ++i)
+      if (std::fabs(A[(size_t)i * 2 * n1 + k]) > std::fabs(A[(size_t)piv * 2 * n1 + k])) piv = i;
+    for (int j = 0; j < 2 * n1; ++j) std::swap(A[(size_t)k * 2 * n1 + j], A[(size_t)piv * 2 * n1 + j]);
+    const long double d = A[(size_t)k * 2 * n1 + k];
+    for (int j = 0; j < 2 * n1; ++j) A[(size_t)k * 2 * n1 + j] /= d;
+    for (int i = 0; i < n1; ++i) {
+      if (i == k) continue;
+      const long double f = A[(size_t)i * 2 * n1 + k];
+      for (int j = 0; j < 2 * n1; ++j) A[(size_t)i * 2 * n1 + j] -= f * A[(size_t)k * 2 * n1 + j];
+    }
+  }
+  std::vector<double> Vinv((size_t)n1 * n1);
+  for (int i = 0; i < n1; ++i)
+    for (int j = 0; j < n1; ++j) Vinv[(size_t)i * n1 + j] = (double)A[(size_t)i * 2 * n1 + n1 + j];
+  return Vinv;
+}
+
+// Modal coefficients m[node(i,j,k)] (mode indices in place of node indices) of one
+// element's nodal field q: V^{-1} applied along direction 0, then 1, then 2.
+void to_modes(const Mesh& M, const std::vector<double>& Vinv, const double* q, double* m) {
+  const int n1 = M.n1;
+  std::vector<double> a(q, q + M.n_nodes), b(M.n_nodes);
+  for (int l = 0; l < M.dim; ++l) {
+    for (int nd = 0; nd < M.n_nodes; ++nd) {
+      int ijk[3];
+      M.node_coords(nd, ijk);
+      double acc = 0.0;
+      for (int j = 0; j < n1; ++j) {
+        int jk[3] = {ijk[0], ijk[1], ijk[2]};
+        jk[l] = j;
+        acc += Vinv[(size_t)ijk[l] * n1 + j] * a[M.node(jk)];
+      }
+      b[nd] = acc;
+    }
+    a.swap(b);
+  }
+  for (int nd = 0; nd < M.n_nodes; ++nd) m[nd] = a[nd];
+}
+
+// Smoothness indicator of element e: the field rho p (the paper's choice for its reacting
+// and shock cases), its modes, and
+//   E = max(E_high^(N) / E_tot^(N), E_high^(N-1) / E_tot^(N-1)),
+// E_tot^(K) the energy of the modes with max(i,j,k) <= K, E_high^(K) of those with
+// max(i,j,k) = K.  (A zero total energy gives the ratio 0.)
+double smoothness(const OrcProblem& P, const Mesh& M, const std::vector<double>& Vinv,
+                  const double* U, int e) {
+  const int nv = M.dim + 2, N = M.N;
+  std::vector<double> q(M.n_nodes), m(M.n_nodes);
+  for (int nd = 0; nd < M.n_nodes; ++nd) {
+    double u[8];
+    load_node(M, nv, U, e, nd, u);
+    Prim pr = primitives(M.dim, u, P.gamma);
+    q[nd] = pr.rho * pr.p;
+  }
+  to_modes(M, Vinv, q.data(), m.data());
+  double tot_n = 0.0, tot_nm1 = 0.0, high_n = 0.0, high_nm1 = 0.0;
+  for (int nd = 0; nd < M.n_nodes; ++nd) {
+    int ijk[3];
+    M.node_coords(nd, ijk);
+    int mx = ijk[0];
+    for (int l = 1; l < M.dim; ++l) mx = std::max(mx, ijk[l]);
+    const double e2 = m[nd] * m[nd];
+    tot_n += e2;
+    if (mx <= N - 1) tot_nm1 += e2;
+    if (mx == N) high_n += e2;
+    if (mx == N - 1) high_nm1 += e2;
+  }
+  const double r1 = tot_n > 0.0 ? high_n / tot_n : 0.0;
+  const double r2 = tot_nm1 > 0.0 ? high_nm1 / tot_nm1 : 0.0;
+  return std::fmax(r1, r2);
+}
+
+// Blending coefficients of all elements:
+//   alpha_raw = 1 / (1 + exp(-(s/T)(E - T))),  T = 0.5 * 10^(-1.8 (N+1)^(1/4));
+// READINGS (the paper names alpha_min, alpha_max and s without values): alpha_raw below
+// alpha_min is set to 0 and alpha_raw is capped at alpha_max (Hennemann and Gassner's
+// clipping; defaults 0.001, 0.5 and s = ln(9999), which puts alpha(E = 0) at 1e-4); then the
+// face-neighbourhood maximum alpha_e = max(alpha_raw_e, alpha_raw of the 2 dim face
+// neighbours), taken once over the raw values.
+void shock_alpha(const OrcProblem& P, const double* U, double* alpha_raw, double* alpha) {
+  Mesh M(P);
+  const std::vector<double> Vinv = modal_matrix(M.N);
+  const double T = 0.5 * std::pow(10.0, -1.8 * std::pow(M.N + 1.0, 0.25));
+  for (int e = 0; e < M.n_elem; ++e) {
+    const double E = smoothness(P, M, Vinv, U, e);
+    double a = 1.0 / (1.0 + std::exp(-(P.sharpness / T) * (E - T)));
+    if (a < P.alpha_min) a = 0.0;
+    alpha_raw[e] = std::fmin(a, P.alpha_max);
+  }
+  for (int e = 0; e < M.n_elem; ++e) {
+    double a = alpha_raw[e];
+    for (int l = 0; l < M.dim; ++l)
+      for (int off = -1; off <= 1; off += 2) a = std::fmax(a, alpha_raw[M.neighbour(e, l, off)]);
+    alpha[e] = a;
+  }
+}
+
+// First-order finite-volume residual on the GLL sub-cell grid of element e (Eq. vol_blend's
+// R^FV, App. A "Shock Capturing"): along direction l node i is the centre of a sub-cell of
+// reference width w_i (the sub-cell faces sit at -1 + w_0 + ... + w_{i-1}), so
+//   R_i -= (2/dx_l) / w_i (f_{i+1/2} - f_{i-1/2}),
+// f_{i+1/2} = F*(U_i, U_{i+1}) between nodes of the element and, at the element faces, the
+// DG surface flux with the neighbour's trace (f_{-1/2} = F*(U_nbr,N, U_0),
+// f_{N+1/2} = F*(U_N, U_nbr,0)).  READING: every sub-cell interface uses the context's
+// surface flux ("matching numerical surface flux functions"; Rusanov in the paper's case).
+void fv_element_residual(const OrcProblem& P, const Mesh& M, const Ops& ops, const double* U, int e,
+                         double* dU) {
+  const int dim = M.dim, N = M.N, nv = dim + 2;
+  std::vector<double> R((size_t)M.n_nodes * nv, 0.0);
+  for (int l = 0; l < dim; ++l) {
+    const double s = 2.0 / M.dx[l];
+    for (int nd = 0; nd < M.n_nodes; ++nd) {
+      int ijk[3];
+      M.node_coords(nd, ijk);
+      const int il = ijk[l];
+      double uo[8], ua[8], fm[8], fp[8];
+      load_node(M, nv, U, e, nd, uo);
+      int nk[3] = {ijk[0], ijk[1], ijk[2]};
+      if (il == 0) {
+        nk[l] = N;
+        load_node(M, nv, U, M.neighbour(e, l, -1), M.node(nk), ua);
+      } else {
+        nk[l] = il - 1;
+        load_node(M, nv, U, e, M.node(nk), ua);
+      }
+      surface_flux(P.surface, dim, l, ua, uo, P.gamma, fm);
+      if (il == N) {
+        nk[l] = 0;
+        load_node(M, nv, U, M.neighbour(e, l, +1), M.node(nk), ua);
+      } else {
+        nk[l] = il + 1;
+        load_node(M, nv, U, e, M.node(nk), ua);
+      }
+      surface_flux(P.surface, dim, l, uo, ua, P.gamma, fp);
+      for (int v = 0; v < nv; ++v) R[nd * nv + v] -= s / ops.w[il] * (fp[v] - fm[v]);
+    }
+  }
+  for (int nd = 0; nd < M.n_nodes; ++nd)
+    for (int v = 0; v < nv; ++v) dU[((size_t)v * M.n_elem + e) * M.n_nodes + nd] = R[nd * nv + v];
+}
+
 int n_vars(const OrcProblem& P) {
   return (P.equations == ORC_NS_REACTING) ? P.mech->n_species + P.dim + 1 : P.dim + 2;
 }
@@ -470,9 +642,13 @@ int check_problem(const OrcProblem& P) {
     if (P.volume != ORC_VOL_STRONG || P.surface != ORC_SURF_RUSANOV) return -6;
     if (P.rho_floor > 0.0 || P.p_floor > 0.0) return -6;
     if (P.mu < 0.0 || !(P.prandtl > 0.0)) return -1;
+    if (P.shock) return -6;
     return 0;
   }
   if (P.equations != ORC_EULER) return -6;
+  if (P.shock && (P.N < 2 || !(P.alpha_min >= 0.0) || !(P.alpha_max <= 1.0) ||
+                  !(P.alpha_min <= P.alpha_max) || !(P.sharpness > 0.0)))
+    return -1;
   return 0;
 }
 
@@ -719,6 +895,24 @@ void residual(const OrcProblem& P, const double* U, double* dU) {
   }
 #pragma omp parallel for schedule(static)
   for (int e = 0; e < M.n_elem; ++e) euler_element_residual(P, M, ops, U, e, dU);
+  if (P.shock) {
+    // Eq. vol_blend: R = (1 - alpha_e) R^DG + alpha_e R^FV per element (with the strong-form
+    // DG residual this is the paper's (1 - alpha_e) F(U^-) boundary correction of F*)
+    std::vector<double> araw(M.n_elem), alpha(M.n_elem);
+    shock_alpha(P, U, araw.data(), alpha.data());
+    const int nv = n_vars(P);
+    std::vector<double> fv((size_t)nv * M.n_elem * M.n_nodes, 0.0);
+#pragma omp parallel for schedule(static)
+    for (int e = 0; e < M.n_elem; ++e) {
+      if (alpha[e] == 0.0) continue;
+      fv_element_residual(P, M, ops, U, e, fv.data());
+      for (int v = 0; v < nv; ++v)
+        for (int nd = 0; nd < M.n_nodes; ++nd) {
+          const size_t q = ((size_t)v * M.n_elem + e) * M.n_nodes + nd;
+          dU[q] = (1.0 - alpha[e]) * dU[q] + alpha[e] * fv[q];
+        }
+    }
+  }
 }
 
 // Positivity floor (Sec. 4.1 and 4.2 set-ups: "a per-stage positivity floor enforces
@@ -959,6 +1153,36 @@ int orc_rhs_elements(const OrcProblem* P, const double* U, const int* elems, int
   }
 #pragma omp parallel for schedule(static)
   for (int k = 0; k < n; ++k) euler_element_residual(*P, M, ops, U, elems[k], dU);
+  return 0;
+}
+
+// Hennemann-Gassner blending coefficients of every element (before and after the
+// face-neighbourhood maximum), Euler problems with shock capturing.
+int orc_shock_alpha(const OrcProblem* P, const double* U, double* alpha_raw, double* alpha) {
+  int rc = check_problem(*P);
+  if (rc) return rc;
+  if (!P->shock || P->equations != ORC_EULER) return -1;
+  shock_alpha(*P, U, alpha_raw, alpha);
+  return 0;
+}
+
+// The sub-cell finite-volume residual of every element alone (Euler problems).
+int orc_fv_residual(const OrcProblem* P, const double* U, double* dU) {
+  int rc = check_problem(*P);
+  if (rc) return rc;
+  if (P->equations != ORC_EULER) return -1;
+  Mesh M(*P);
+  Ops ops(P->N);
+  for (int e = 0; e < M.n_elem; ++e) fv_element_residual(*P, M, ops, U, e, dU);
+  return 0;
+}
+
+// Orthonormal tensor-Legendre modes of one element's nodal field q ((N+1)^dim values).
+int orc_modes(const OrcProblem* P, const double* q, double* m) {
+  int rc = check_problem(*P);
+  if (rc) return rc;
+  Mesh M(*P);
+  to_modes(M, modal_matrix(M.N), q, m);
   return 0;
 }
 
@@ -1275,6 +1499,7 @@ int orc_rhs_jvp(const OrcProblem* P, const double* U, const double* V, double gd
                 double* dL) {
   int rc = check_problem(*P);
   if (rc) return rc;
+  if (P->shock) return -6;  // the dual-number residual has no shock capturing
   if ((P->volume != ORC_VOL_STRONG && P->volume != ORC_VOL_WEAK) || P->surface != ORC_SURF_RUSANOV ||
       P->equations != ORC_EULER)
     return -6;
@@ -1299,6 +1524,7 @@ int orc_rhs_vjp_brute(const OrcProblem* P, const double* U, const double* lam, d
                       double* gbar) {
   int rc = check_problem(*P);
   if (rc) return rc;
+  if (P->shock) return -6;  // the dual-number residual has no shock capturing
   Mesh M(*P);
   const size_t n = (size_t)n_vars(*P) * M.n_elem * M.n_nodes;
   if (n > 20000) return -1;
@@ -1327,6 +1553,7 @@ int orc_rollout_grad(const OrcProblem* P, const double* U0, const double* target
                      double dt, int n_steps, double* grad, double* ggam) {
   int rc = check_problem(*P);
   if (rc) return rc;
+  if (P->shock) return -6;  // the dual-number residual has no shock capturing
   if ((P->volume != ORC_VOL_STRONG && P->volume != ORC_VOL_WEAK) || P->surface != ORC_SURF_RUSANOV ||
       P->equations != ORC_EULER)
     return -6;
