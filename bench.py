@@ -252,11 +252,14 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-reacting", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
-    ap.add_argument("--only", default="both", choices=["both", "fp32", "fp64", "reacting", "split"],
+    ap.add_argument("--only", default="both", choices=["both", "fp32", "fp64", "reacting", "split", "shock"],
                     help="precision(s) to time, or only the reacting workload (profiling runs)")
     ap.add_argument("--reacting-nel", type=int, default=48,
                     help="elements per direction of the reacting workload (profiling runs)")
     ap.add_argument("--no-split", action="store_true")
+    ap.add_argument("--no-shock", action="store_true")
+    ap.add_argument("--shock-nel", type=int, default=48,
+                    help="elements per direction of the blast (shock-capturing) workload")
     ap.add_argument("--split-nel", type=int, default=32,
                     help="elements per direction of the split (implicit chemistry) workload")
     ap.add_argument("--nel", type=int, default=NEL, help="elements per direction (profiling runs)")
@@ -265,10 +268,10 @@ def main():
     if args.impl == "reference":
         run_reference(args)
         return
-    if args.only in ("reacting", "split"):
+    if args.only in ("reacting", "split", "shock"):
         import torch
         torch.cuda.set_device(dist_env()[2])
-        fn = run_reacting if args.only == "reacting" else run_split
+        fn = {"reacting": run_reacting, "split": run_split, "shock": run_shock}[args.only]
         print(json.dumps({args.only: fn(args)}), flush=True)
         return
 
@@ -347,6 +350,7 @@ def main():
     batched = None if args.no_batched else run_batched(args)
     reacting = None if args.no_reacting else run_reacting(args)
     split = None if args.no_split else run_split(args)
+    shock = None if args.no_shock else run_shock(args)
     adjoint = None if args.no_adjoint else run_adjoint(args)
     fp64 = None
     if ms64:
@@ -369,6 +373,7 @@ def main():
         "batched": batched,
         "reacting": reacting,
         "reacting_split": split,
+        "shock": shock,
         "adjoint": adjoint,
     }
     print(json.dumps(line), flush=True)
@@ -565,6 +570,56 @@ def run_split(args):
     out["explicit_fp64"] = {"dt": EXPLICIT_DT, "ms_per_step": ms_exp,
                             "sim_seconds_per_s": EXPLICIT_DT / (ms_exp * 1e-3)}
     out["speedup_sim_time_fp64"] = out["fp64"]["sim_seconds_per_s"] / out["explicit_fp64"]["sim_seconds_per_s"]
+    return out
+
+
+def run_shock(args):
+    """The shock-capturing workload: 3D Euler blast (pressure ratio 10, gas at rest) in the
+    periodic box [0, 2]^3, 48^3 elements, N = 3, EC flux differencing + Rusanov, Hennemann-
+    Gassner DG/FV blending in every stage (indicator + neighbourhood maximum, the fused stage
+    with blended elements deferred, the sub-cell FV blend), SSP-RK3 at CFL 0.3, FP32-mixed
+    and FP64.  Steps are timed after three warm-up steps, beside the same steps with shock
+    capturing off (which stays finite for these few steps) for the overhead."""
+    import torch
+    from paper_2605_26388_b300 import dgsem, workloads as wl
+    nel, n_deg = args.shock_nel, 3
+    x, _, _ = dgsem.gll(n_deg)
+    U = torch.from_numpy(wl.blast_wave(3, nel, x).reshape(5, -1)).cuda()
+    steps = max(3, args.steps // 6)
+    mesh = dgsem.Mesh(3, n_deg, (nel,) * 3, (0.0,) * 3, (2.0,) * 3)
+    out = {"workload": f"3D Euler blast (p ratio 10), N=3, {nel}^3, EC + Rusanov, SSP-RK3 CFL 0.3, "
+                       "Hennemann-Gassner DG/FV blending", "steps": steps, "dof": nel ** 3 * 64 * 5}
+    for name, prec in (("fp32_mixed", dgsem.FP32_MIXED), ("fp64", dgsem.FP64)):
+        r = {}
+        for shock in (True, False):
+            S = dgsem.Solver(mesh, volume=dgsem.VOL_EC, surface=dgsem.SURF_RUSANOV, precision=prec,
+                             gamma=GAMMA, shock=shock)
+            S.set_state(U)
+            dt = S.max_dt(0.3)
+            S.rk_step(dt, 3)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            S.rk_step(dt, steps)
+            e1.record()
+            torch.cuda.synchronize()
+            try:
+                S.check()
+                finite = True
+            except dgsem.DGError:
+                if shock:
+                    raise
+                finite = False  # the unblended scheme may leave the physical states: timing only
+            ms = e0.elapsed_time(e1) / steps
+            key = "blended" if shock else "unblended"
+            r[key] = {"ms_per_step": ms, "value": 3 * out["dof"] / (ms * 1e-3), "unit": "DOF-updates/s",
+                      "state_valid": finite}
+            if shock:
+                _, al = S.shock_alpha(S.get_state())
+                r["blended"]["elements_blended"] = float((al > 0).double().mean())
+            S.close()
+        r["overhead"] = r["blended"]["ms_per_step"] / r["unblended"]["ms_per_step"]
+        out[name] = r
     return out
 
 

@@ -83,6 +83,11 @@ enum { DG_FP64 = 0, DG_FP32_MIXED = 1 };
  * Spiteri and Ruuth (five stages, fourth order, SSP coefficient 1.508; the paper's
  * production integrator, with the coefficients of its publication). */
 enum { DG_SSPRK33 = 0, DG_SSPRK54 = 1 };
+/* Defaults of the Hennemann-Gassner blending bounds (dg_physics fields <= 0); the sigmoid's
+ * steepness defaults to ln(9999), which puts the blending of a perfectly smooth element at
+ * 1e-4 before the cut. */
+#define DG_ALPHA_MIN 0.001
+#define DG_ALPHA_MAX 0.5
 /* Defaults of the implicit source substep's Newton iteration (dg_physics fields <= 0). */
 #define DG_NEWTON_MAX_IT 40
 #define DG_NEWTON_TOL 1e-12
@@ -147,6 +152,12 @@ typedef struct {
                      * S_{dt/2} o T_dt o S_{dt/2}, S the implicit substep of dg_source_step */
   int newton_max_it;  /* implicit substep: Newton updates per node at most (<= 0: default) */
   double newton_tol;  /* stop once max_s |dY_s| <= newton_tol * rho (<= 0: default) */
+  /* Shock capturing (Sec. 3.1.1 "Shock Indicator and Smoothing", Eq. vol_blend; App. A):
+   * DG_EULER only, N >= 2 (N <= 7 in 2D, <= 5 in 3D), per-instance launches. */
+  int shock;        /* 1: every stage blends R = (1 - alpha_e) R^DG + alpha_e R^FV per element */
+  double alpha_min; /* blending below this is cut to 0 (<= 0: DG_ALPHA_MIN) */
+  double alpha_max; /* blending is capped here (<= 0: DG_ALPHA_MAX) */
+  double sharpness; /* steepness s of the sigmoid (<= 0: ln 9999) */
 } dg_physics;
 
 /* Build a context for n_inst instances (all of the same dim) sharing one physics
@@ -297,6 +308,18 @@ DG_API dg_status dg_max_dt_noalloc(const dg_mesh_desc* inst, int n_inst, double 
  * but must not otherwise overlap.  A node still unconverged after newton_max_it updates
  * keeps its last iterate and makes dg_check() return DG_ECONVERGENCE.  Asynchronous. */
 DG_API dg_status dg_source_step(dg_ctx* ctx, const double* U, double h, double* Uout);
+
+/* Hennemann-Gassner blending coefficients of every element for the state U (device, SoA as
+ * everywhere), into alpha_raw and alpha (device arrays of the total element count, instances
+ * concatenated; either may be NULL).  Per element: the field rho p at its nodes, its
+ * orthonormal tensor-Legendre modes m, the smoothness
+ *   E = max(E_high^(N) / E_tot^(N), E_high^(N-1) / E_tot^(N-1))
+ * (E_tot^(K): energy of the modes with max index <= K; E_high^(K): with max index = K), then
+ *   alpha_raw = min(alpha_max, sigmoid), sigmoid = 1 / (1 + exp(-(s/T)(E - T))), cut to 0 below
+ * alpha_min, T = 0.5 * 10^(-1.8 (N+1)^(1/4)); alpha = max of alpha_raw over the element and its
+ * face neighbours.  These are the coefficients every shock-captured stage computes from its
+ * input state.  DG_EUNSUPPORTED unless shock capturing is on.  Asynchronous. */
+DG_API dg_status dg_shock_alpha(dg_ctx* ctx, const double* U, double* alpha_raw, double* alpha);
 
 /* Newton updates taken by all nodes in the implicit source substeps (dg_source_step and the
  * split steps of dg_rk_step) since the previous call, into *count (host); resets the count.

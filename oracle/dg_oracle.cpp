@@ -1153,6 +1153,22 @@ int orc_rhs_elements(const OrcProblem* P, const double* U, const int* elems, int
   }
 #pragma omp parallel for schedule(static)
   for (int k = 0; k < n; ++k) euler_element_residual(*P, M, ops, U, elems[k], dU);
+  if (P->shock) {  // Eq. vol_blend on the listed elements (the coefficients need the whole mesh)
+    std::vector<double> araw(M.n_elem), alpha(M.n_elem);
+    shock_alpha(*P, U, araw.data(), alpha.data());
+    const int nv = n_vars(*P);
+    std::vector<double> fv((size_t)nv * M.n_elem * M.n_nodes, 0.0);
+    for (int k = 0; k < n; ++k) {
+      const int e = elems[k];
+      if (alpha[e] == 0.0) continue;
+      fv_element_residual(*P, M, ops, U, e, fv.data());
+      for (int v = 0; v < nv; ++v)
+        for (int nd = 0; nd < M.n_nodes; ++nd) {
+          const size_t q = ((size_t)v * M.n_elem + e) * M.n_nodes + nd;
+          dU[q] = (1.0 - alpha[e]) * dU[q] + alpha[e] * fv[q];
+        }
+    }
+  }
   return 0;
 }
 

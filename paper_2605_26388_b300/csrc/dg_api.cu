@@ -57,6 +57,16 @@ struct dg_ctx {
   void* pc[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   double* pT[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   bool pvalid[4] = {false, false, false, false};
+  // shock capturing (Euler): per-element blending coefficients (raw and smoothed), the list
+  // of blended elements and its length, the DG-residual side buffer, per-instance element
+  // offsets
+  bool shock = false;
+  double* alpha_raw = nullptr;
+  double* alpha = nullptr;
+  int* list = nullptr;
+  int* count = nullptr;
+  double* ldg = nullptr;
+  std::vector<long long> eoffs;
 };
 
 namespace {
@@ -230,6 +240,47 @@ void volume_operator(const dg_ctx* c, int N, double* Dv, double* lift) {
   if (lift) *lift = 1.0 / w[0];
 }
 
+// Nodal -> orthonormal Legendre modes on the GLL nodes (Sec. 3.1.1 "Shock Indicator"; the
+// Hennemann-Gassner indicator's modal decomposition): Vinv = V^{-1}, V_ij = P~_j(x_i),
+// P~_j = sqrt((2j+1)/2) P_j, inverted by Gauss-Jordan in long double.
+void modal_inverse(int N, double* Vinv) {
+  const int n1 = N + 1;
+  double x[dg::kMaxN + 1], w[dg::kMaxN + 1];
+  gll_table(N, x, w, nullptr);
+  long double A[dg::kMaxN + 1][2 * (dg::kMaxN + 1)];
+  for (int i = 0; i < n1; ++i) {
+    long double pm = 1.0L, p = x[i];  // P_0, P_1
+    for (int j = 0; j < n1; ++j) {
+      long double Pj;
+      if (j == 0) Pj = 1.0L;
+      else if (j == 1) Pj = x[i];
+      else {
+        const long double pn = ((2.0L * j - 1.0L) * x[i] * p - (j - 1.0L) * pm) / j;
+        pm = p;
+        p = pn;
+        Pj = pn;
+      }
+      A[i][j] = std::sqrt((2.0L * j + 1.0L) / 2.0L) * Pj;
+      A[i][n1 + j] = (i == j) ? 1.0L : 0.0L;
+    }
+  }
+  for (int k = 0; k < n1; ++k) {
+    int piv = k;
+    for (int i = k + 1; i < n1; ++i)
+      if (std::fabs(A[i][k]) > std::fabs(A[piv][k])) piv = i;
+    for (int j = 0; j < 2 * n1; ++j) std::swap(A[k][j], A[piv][j]);
+    const long double d = A[k][k];
+    for (int j = 0; j < 2 * n1; ++j) A[k][j] /= d;
+    for (int i = 0; i < n1; ++i) {
+      if (i == k) continue;
+      const long double f = A[i][k];
+      for (int j = 0; j < 2 * n1; ++j) A[i][j] -= f * A[k][j];
+    }
+  }
+  for (int i = 0; i < n1; ++i)
+    for (int j = 0; j < n1; ++j) Vinv[i * n1 + j] = (double)A[i][n1 + j];
+}
+
 // The kernels' view of instance i.
 void inst_args(const dg_ctx* c, int i, dg::InstArgs& I) {
   const dg_mesh_desc& m = c->inst[i];
@@ -386,12 +437,82 @@ dg_status run_stage_ns(dg_ctx* c, const double* U, const double* Un, double* out
   return DG_OK;
 }
 
+// Shock-capturing arguments of instance i for one stage (the stage launch's own arguments a
+// supply the precomputed scalars).
+void shock_args(const dg_ctx* c, int i, const dg::StageArgs& a, const StageCoef& k, dg::ShockArgs& sa) {
+  std::memset(&sa, 0, sizeof(sa));
+  const dg_mesh_desc& m = c->inst[i];
+  sa.U = a.U;
+  sa.Un = a.Un;
+  sa.out = a.out;
+  sa.ldg = a.mode == 1 ? c->ldg : a.out;
+  sa.acc = k.acc;
+  sa.acc_a = k.acc_a;
+  sa.acc_b = k.acc_b;
+  sa.acc_bdt = k.acc_bdt;
+  sa.err = c->err;
+  sa.stride = c->n_nodes_total;
+  inst_args(c, i, sa.inst);
+  sa.mode = a.mode;
+  sa.need_un = a.need_un;
+  sa.surface = c->phys.surface;
+  sa.floor_on = a.floor_on;
+  sa.ca = k.ca;
+  sa.cb = k.cb;
+  sa.bdt = k.bdt;
+  sa.gamma = c->phys.gamma;
+  sa.rho_floor = c->phys.rho_floor;
+  sa.p_floor = c->phys.p_floor;
+  sa.pd = a.pd;
+  sa.pf = a.pf;
+  double x[dg::kMaxN + 1], w[dg::kMaxN + 1];
+  gll_table(m.N, x, w, nullptr);
+  for (int j = 0; j <= m.N; ++j) {
+    sa.iw[j] = 1.0 / w[j];
+    sa.iwf[j] = (float)sa.iw[j];
+  }
+  modal_inverse(m.N, sa.Vinv);
+  sa.thr = 0.5 * std::pow(10.0, -1.8 * std::pow(m.N + 1.0, 0.25));
+  sa.sharp = c->phys.sharpness;
+  sa.alpha_min = c->phys.alpha_min;
+  sa.alpha_max = c->phys.alpha_max;
+  sa.alpha_raw = c->alpha_raw + c->eoffs[i];
+  sa.alpha = c->alpha + c->eoffs[i];
+  sa.list = c->list;
+  sa.count = c->count;
+}
+
+// Indicator and neighbourhood maximum of instance i on state U (resets the list).
+dg_status run_indicator(dg_ctx* c, int i, const dg::ShockArgs& sa, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(c->count, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = dg::launch_shock_indicator(c->inst[i].dim, c->inst[i].N, sa, s);
+  return e == cudaSuccess ? DG_OK : cuda_fail(c, e, "shock indicator launch");
+}
+
 dg_status run_stage(dg_ctx* c, const double* U, const double* Un, double* out, int mode,
                     const StageCoef& k, cudaStream_t s) {
   if (c->ns) return run_stage_ns(c, U, Un, out, mode, k, s);
   const int ec = c->phys.volume == DG_VOL_EC, fp32 = c->phys.precision == DG_FP32_MIXED;
   dg::StageArgs a;
   launch_args(c, a, U, Un, out, mode, k);
+  if (c->shock) {
+    // per instance: indicator -> stage (blended elements only write L_DG) -> FV + blend
+    for (size_t i = 0; i < c->inst.size(); ++i) {
+      dg::ShockArgs sa;
+      shock_args(c, (int)i, a, k, sa);
+      dg_status st = run_indicator(c, (int)i, sa, s);
+      if (st) return st;
+      dg::StageArgs b = a;
+      inst_args(c, (int)i, b.inst);
+      volume_operator(c, c->inst[i].N, b.Dv, nullptr);
+      b.alpha = sa.alpha;
+      b.ldg = c->ldg;
+      cudaError_t e = dg::launch_euler_stage(c->inst[i].dim, c->inst[i].N, ec, fp32, b, s);
+      if (e == cudaSuccess) e = dg::launch_shock_blend(c->inst[i].dim, c->inst[i].N, fp32, sa, s);
+      if (e != cudaSuccess) return cuda_fail(c, e, "shock-captured stage launch");
+    }
+    return DG_OK;
+  }
   if (c->batched) {
     a.insts = c->d_insts;
     a.items = c->d_items;
@@ -458,6 +579,7 @@ dg_status build_batch(dg_ctx* c) {
 
 // ---- adjoint ----
 dg_status ensure_adjoint(dg_ctx* c) {
+  if (c->shock) return fail(c, DG_EUNSUPPORTED, "the adjoint has no shock capturing");
   if (c->phys.volume == DG_VOL_EC || c->phys.surface != DG_SURF_RUSANOV)
     return fail(c, DG_EUNSUPPORTED, "the adjoint covers the strong/weak volume form with the Rusanov flux");
   if (c->gacc) return DG_OK;
@@ -662,6 +784,19 @@ dg_status dg_init_mesh(const dg_mesh_desc* inst, int n_inst, const dg_physics* p
   if (phys->chem_split != 0 && (phys->chem_split != 1 || phys->equations != DG_NS_REACTING))
     return DG_EINVAL;
   if (!std::isfinite(phys->newton_tol) || phys->newton_max_it > 1000) return DG_EINVAL;
+  dg_physics ph = *phys;  // with the shock-capturing defaults filled in
+  if (ph.shock) {
+    if (ph.shock != 1) return DG_EINVAL;
+    if (ph.equations != DG_EULER) return DG_EUNSUPPORTED;
+    for (int i = 0; i < n_inst; ++i)
+      if (!dg::have_shock(inst[i].dim, inst[i].N)) return DG_EUNSUPPORTED;
+    if (!(ph.alpha_min > 0.0)) ph.alpha_min = DG_ALPHA_MIN;
+    if (!(ph.alpha_max > 0.0)) ph.alpha_max = DG_ALPHA_MAX;
+    if (!(ph.sharpness > 0.0)) ph.sharpness = std::log(9999.0);
+    if (!std::isfinite(ph.alpha_min) || !std::isfinite(ph.sharpness) || !(ph.alpha_max <= 1.0) ||
+        !(ph.alpha_min <= ph.alpha_max))
+      return DG_EINVAL;
+  }
   const bool navier_stokes = phys->equations != DG_EULER;
   dg::MechDev mech;
   if (navier_stokes) {
@@ -692,7 +827,7 @@ dg_status dg_init_mesh(const dg_mesh_desc* inst, int n_inst, const dg_physics* p
 
   dg_ctx* c = new dg_ctx();
   c->inst.assign(inst, inst + n_inst);
-  c->phys = *phys;
+  c->phys = ph;
   c->stream = (cudaStream_t)cuda_stream;
   c->dim = inst[0].dim;
   c->ns = navier_stokes;
@@ -772,6 +907,25 @@ dg_status dg_init_mesh(const dg_mesh_desc* inst, int n_inst, const dg_physics* p
       dg_free(c);
       return DG_ECUDA;
     }
+  }
+  if (ph.shock) {
+    c->shock = true;
+    long long ne = 0;
+    for (int i = 0; i < n_inst; ++i) {
+      c->eoffs.push_back(ne);
+      ne += n_elem_of(inst[i]);
+    }
+    if (cudaMalloc(&c->alpha_raw, sizeof(double) * ne) != cudaSuccess ||
+        cudaMalloc(&c->alpha, sizeof(double) * ne) != cudaSuccess ||
+        cudaMalloc(&c->list, sizeof(int) * ne) != cudaSuccess ||
+        cudaMalloc(&c->count, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&c->ldg, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      dg_free(c);
+      return DG_ENOMEM;
+    }
+    *out = c;  // shock-captured stages are launched per instance
+    return DG_OK;
   }
   bool batchable = true;
   for (int i = 0; i < n_inst; ++i) batchable = batchable && inst[i].N <= dg::kMaxBatchedN;
@@ -937,6 +1091,8 @@ dg_status dg_set_launch(dg_ctx* c, int mode, int group_scale, int ctas_per_sm, i
     return fail(c, DG_EINVAL, "mode must be DG_LAUNCH_PER_INSTANCE or DG_LAUNCH_BATCHED");
   if (c->ns && mode == DG_LAUNCH_BATCHED)
     return fail(c, DG_EUNSUPPORTED, "the batched launch exists for the Euler equations");
+  if (c->shock && mode == DG_LAUNCH_BATCHED)
+    return fail(c, DG_EUNSUPPORTED, "shock-captured stages are launched per instance");
   if (group_scale != 1 && !(group_scale == 2 && c->dim == 2))
     return fail(c, DG_EINVAL, "group_scale must be 1 (or 2 in 2D)");
   if (ctas_per_sm < 0 || (order != 0 && order != 1))
@@ -1100,6 +1256,27 @@ dg_status dg_source_step(dg_ctx* c, const double* U, double h, double* Uout) {
   return run_source(c, U, Uout, h, c->stream);
 }
 
+dg_status dg_shock_alpha(dg_ctx* c, const double* U, double* alpha_raw, double* alpha) {
+  if (!c) return DG_EINVAL;
+  if (!U) return fail(c, DG_EINVAL, "null pointer");
+  if (!c->shock) return fail(c, DG_EUNSUPPORTED, "shock capturing is off");
+  dg::StageArgs a;
+  launch_args(c, a, U, U, nullptr, 0, StageCoef());
+  long long ne = 0;
+  for (size_t i = 0; i < c->inst.size(); ++i) {
+    dg::ShockArgs sa;
+    shock_args(c, (int)i, a, StageCoef(), sa);
+    dg_status st = run_indicator(c, (int)i, sa, c->stream);
+    if (st) return st;
+    ne += n_elem_of(c->inst[i]);
+  }
+  cudaError_t e = cudaSuccess;
+  if (alpha_raw) e = cudaMemcpyAsync(alpha_raw, c->alpha_raw, sizeof(double) * ne, cudaMemcpyDeviceToDevice, c->stream);
+  if (e == cudaSuccess && alpha)
+    e = cudaMemcpyAsync(alpha, c->alpha, sizeof(double) * ne, cudaMemcpyDeviceToDevice, c->stream);
+  return e == cudaSuccess ? DG_OK : cuda_fail(c, e, "dg_shock_alpha");
+}
+
 dg_status dg_newton_updates(dg_ctx* c, int64_t* count) {
   if (!c) return DG_EINVAL;
   if (!count) return fail(c, DG_EINVAL, "null pointer");
@@ -1143,6 +1320,11 @@ void dg_free(dg_ctx* c) {
   if (c->gacc) cudaFree(c->gacc);
   if (c->d_mech) cudaFree(c->d_mech);
   if (c->fb) cudaFree(c->fb);
+  if (c->alpha_raw) cudaFree(c->alpha_raw);
+  if (c->alpha) cudaFree(c->alpha);
+  if (c->list) cudaFree(c->list);
+  if (c->count) cudaFree(c->count);
+  if (c->ldg) cudaFree(c->ldg);
   for (int k = 0; k < 5; ++k) {
     if (c->pc[k]) cudaFree(c->pc[k]);
     if (c->pT[k]) cudaFree(c->pT[k]);

@@ -52,6 +52,10 @@ struct StageArgs {
   ScalarsT<float> pf;
   int need_un;         // mode == 1 and ca != 0
   int floor_on;        // rho_floor > 0 or p_floor > 0
+  // shock capturing (mode 1): elements with alpha[e] > 0 write their DG residual to ldg and
+  // leave the update to the blending launch; null alpha: no shock capturing
+  const double* alpha; // per element of the instance
+  double* ldg;         // state-shaped side buffer
   // single-instance launch
   InstArgs inst;
   double Dv[(kMaxN + 1) * (kMaxN + 1)];  // volume operator, row-major (N+1)^2
@@ -80,6 +84,39 @@ struct VjpArgs {
   double gamma, dt, bcoef, acoef, gw;
   int mode, weak;
 };
+
+// Hennemann-Gassner shock capturing over one instance (Sec. 3.1.1 "Shock Indicator and
+// Smoothing", Eq. vol_blend): indicator -> alpha_raw, neighbourhood maximum -> alpha and the
+// list of elements with alpha > 0, then (after the stage launch) the sub-cell FV residual,
+// the blend with the DG residual and the stage update of the listed elements.
+struct ShockArgs {
+  const double* U;       // stage input state
+  const double* Un;      // X of the update (need_un)
+  double* out;           // stage output (mode 1) or L (mode 0)
+  const double* ldg;     // DG residual of the listed elements (mode 1: side buffer; mode 0: out)
+  double* acc;           // optional running sum (see StageArgs)
+  double acc_a, acc_b, acc_bdt;
+  unsigned* err;
+  long long stride;
+  InstArgs inst;
+  int mode, need_un, surface, floor_on;
+  double ca, cb, bdt;
+  double gamma, rho_floor, p_floor;
+  ScalarsT<double> pd;
+  ScalarsT<float> pf;
+  double iw[kMaxN + 1];  // 1 / w_i of the GLL rule
+  float iwf[kMaxN + 1];
+  double Vinv[(kMaxN + 1) * (kMaxN + 1)];  // nodal -> orthonormal Legendre modes
+  double thr, sharp, alpha_min, alpha_max;   // threshold T, steepness s, clipping bounds
+  double* alpha_raw;     // per element of the instance
+  double* alpha;
+  int* list;             // elements with alpha > 0 ...
+  int* count;            // ... and their number (device)
+};
+// The three shock-capturing launches; have_shock(dim, N) says whether they exist.
+bool have_shock(int dim, int N);
+cudaError_t launch_shock_indicator(int dim, int N, const ShockArgs& a, cudaStream_t s);
+cudaError_t launch_shock_blend(int dim, int N, int fp32, const ShockArgs& a, cudaStream_t s);
 
 // Launch the adjoint of the residual for one instance, then add the weighted gamma
 // contribution (a deterministic sum of the per-CTA partials) to *gacc (device).

@@ -1,0 +1,344 @@
+// dg_shock.cu -- Hennemann-Gassner shock capturing of the Euler residual (Sec. 3.1.1 "Shock
+// Indicator and Smoothing", Eq. vol_blend; App. A "Shock Capturing").
+//
+// Per stage and instance, around the fused stage launch:
+//   1. k_hg_indicator: per element, the modal smoothness of rho p (FP64: orthonormal tensor
+//      Legendre modes by three line contractions with V^{-1} in shared memory, energies of
+//      the top and next-to-top shells), the sigmoid with threshold T and steepness s, and the
+//      clipping to [alpha_min, alpha_max] -> alpha_raw;
+//   2. k_hg_alpha: alpha_e = max(alpha_raw_e, alpha_raw of the face neighbours); elements with
+//      alpha > 0 are appended to a list (its order does not matter: the elements are
+//      independent);
+//   3. (the stage launch writes the DG residual of the listed elements to a side buffer and
+//      skips their update);
+//   4. k_fv_blend: one CTA per listed element (persistent over the list) computes the
+//      first-order FV residual on the GLL sub-cells -- the interface fluxes F*(U_i, U_{i+1})
+//      and, at the element faces, F* with the neighbour's trace, evaluated exactly as the
+//      stage kernel's face jobs do (same conversions and pressure deviation, same flux call
+//      after the same axis relabelling), so the F* both elements of a face use agree -- and
+//      forms L = (1 - alpha) L_DG + alpha R_FV and the stage update.
+// The decisions (alpha_min cut, alpha > 0) are taken in FP64 in both precisions.
+#include "dg_stage.cuh"
+
+namespace dg {
+namespace {
+
+constexpr int kIT = 128;  // threads of the indicator CTA (more when one element has more nodes)
+
+template <int DIM, int N>
+struct SG {
+  static constexpr int N1 = N + 1;
+  static constexpr int NP = DIM == 2 ? N1 * N1 : N1 * N1 * N1;
+  static constexpr int NV = DIM + 2;
+  static constexpr int EPB = NP >= kIT ? 1 : kIT / NP;          // elements per indicator CTA
+  static constexpr int T = ((EPB * NP + 31) / 32) * 32;          // threads per indicator CTA
+  static constexpr int NLINE = NP / N1;
+  static constexpr int NJ = DIM * NLINE * (N + 2);                // sub-cell interfaces
+  static int stride(int l) { return l == 0 ? 1 : (l == 1 ? N1 : N1 * N1); }
+};
+
+template <int N1>
+__device__ __forceinline__ int dstride(int l) {
+  return l == 0 ? 1 : (l == 1 ? N1 : N1 * N1);
+}
+
+// ---- 1: indicator ----
+template <int DIM, int N>
+__global__ void __launch_bounds__(SG<DIM, N>::T) k_hg_indicator(const ShockArgs a) {
+  using G = SG<DIM, N>;
+  constexpr int N1 = G::N1, NP = G::NP, EPB = G::EPB;
+  __shared__ double qa[EPB * NP], qb[EPB * NP], Vi[N1 * N1];
+  __shared__ double part[EPB * NP][4];
+  const int t = threadIdx.x;
+  for (int k = t; k < N1 * N1; k += blockDim.x) Vi[k] = a.Vinv[k];
+  const int el = t / NP, nd = t - el * NP;
+  const int e = blockIdx.x * EPB + el;
+  const bool active = t < EPB * NP && e < a.inst.n_elem;
+  if (active) {
+    const long long gi = a.inst.base + (long long)e * NP + nd;
+    double u[G::NV];
+#pragma unroll
+    for (int v = 0; v < G::NV; ++v) u[v] = a.U[v * a.stride + gi];
+    double m2 = 0.0;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) m2 = fma(u[1 + d], u[1 + d], m2);
+    const double p = (a.gamma - 1.0) * (u[DIM + 1] - 0.5 * m2 / u[0]);
+    qa[el * NP + nd] = u[0] * p;
+  }
+  __syncthreads();
+  // modes: V^{-1} along direction 0, 1 (, 2)
+  double* src = qa;
+  double* dst = qb;
+#pragma unroll
+  for (int l = 0; l < DIM; ++l) {
+    if (active) {
+      const int S = dstride<N1>(l);
+      const int i = (nd / S) % N1;
+      const double* line = src + el * NP + nd - i * S;
+      double acc = 0.0;
+#pragma unroll
+      for (int j = 0; j < N1; ++j) acc = fma(Vi[i * N1 + j], line[j * S], acc);
+      dst[el * NP + nd] = acc;
+    }
+    __syncthreads();
+    double* tmp = src;
+    src = dst;
+    dst = tmp;
+  }
+  if (active) {
+    const double m = src[el * NP + nd];
+    int mx = nd % N1;
+    if (DIM >= 2) mx = max(mx, (nd / N1) % N1);
+    if (DIM == 3) mx = max(mx, nd / (N1 * N1));
+    const double e2 = m * m;
+    part[el * NP + nd][0] = e2;                      // E_tot^(N)
+    part[el * NP + nd][1] = mx <= N - 1 ? e2 : 0.0;  // E_tot^(N-1)
+    part[el * NP + nd][2] = mx == N ? e2 : 0.0;      // E_high^(N)
+    part[el * NP + nd][3] = mx == N - 1 ? e2 : 0.0;  // E_high^(N-1)
+  }
+  __syncthreads();
+  if (active && nd == 0) {
+    double s4[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int k = 0; k < NP; ++k) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) s4[c] += part[el * NP + k][c];
+    }
+    const double r1 = s4[0] > 0.0 ? s4[2] / s4[0] : 0.0;
+    const double r2 = s4[1] > 0.0 ? s4[3] / s4[1] : 0.0;
+    const double E = fmax(r1, r2);
+    double al = 1.0 / (1.0 + exp(-(a.sharp / a.thr) * (E - a.thr)));
+    if (al < a.alpha_min) al = 0.0;
+    a.alpha_raw[e] = fmin(al, a.alpha_max);
+  }
+}
+
+// ---- 2: neighbourhood maximum and the list of blended elements ----
+template <int DIM>
+__global__ void k_hg_alpha(const ShockArgs a) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= a.inst.n_elem) return;
+  const int* nel = a.inst.nel;
+  const int c[3] = {e % nel[0], (e / nel[0]) % nel[1], DIM == 3 ? e / (nel[0] * nel[1]) : 0};
+  double al = a.alpha_raw[e];
+#pragma unroll
+  for (int l = 0; l < DIM; ++l) {
+#pragma unroll
+    for (int d = -1; d <= 1; d += 2) {
+      int cc[3] = {c[0], c[1], c[2]};
+      cc[l] = (cc[l] + d + nel[l]) % nel[l];
+      al = fmax(al, a.alpha_raw[cc[0] + nel[0] * (cc[1] + nel[1] * cc[2])]);
+    }
+  }
+  a.alpha[e] = al;
+  if (al > 0.0) a.list[atomicAdd(a.count, 1)] = e;
+}
+
+// ---- 4: sub-cell FV residual, blend, stage update ----
+template <int DIM, class R>
+__device__ __forceinline__ void to_axes(const R* in, R* out, int l) {
+  constexpr int NV = DIM + 2;
+  out[0] = in[0];
+  out[NV - 1] = in[NV - 1];
+  if constexpr (DIM == 2) {
+    out[1] = l ? in[2] : in[1];
+    out[2] = l ? in[1] : in[2];
+  } else {
+    out[1] = l == 0 ? in[1] : (l == 1 ? in[2] : in[3]);
+    out[2] = l == 0 ? in[2] : (l == 1 ? in[3] : in[1]);
+    out[3] = l == 0 ? in[3] : (l == 1 ? in[1] : in[2]);
+  }
+}
+template <int DIM, class R>
+__device__ __forceinline__ void from_axes(const R* in, R* out, int l) {
+  constexpr int NV = DIM + 2;
+  out[0] = in[0];
+  out[NV - 1] = in[NV - 1];
+  if constexpr (DIM == 2) {
+    out[1] = l ? in[2] : in[1];
+    out[2] = l ? in[1] : in[2];
+  } else {
+    out[1] = l == 0 ? in[1] : (l == 1 ? in[3] : in[2]);
+    out[2] = l == 0 ? in[2] : (l == 1 ? in[1] : in[3]);
+    out[3] = l == 0 ? in[3] : (l == 1 ? in[2] : in[1]);
+  }
+}
+
+template <class R> __device__ __forceinline__ const ScalarsT<R>& shs(const ShockArgs& a);
+template <> __device__ __forceinline__ const ScalarsT<double>& shs<double>(const ShockArgs& a) { return a.pd; }
+template <> __device__ __forceinline__ const ScalarsT<float>& shs<float>(const ShockArgs& a) { return a.pf; }
+
+// F*(U_L, U_R) in direction l from FP64 states, as the stage kernel's face jobs evaluate it.
+template <int DIM, class R>
+__device__ __forceinline__ void interface_flux(const ShockArgs& a, int l, const double* L64,
+                                               const double* R64, R* F) {
+  constexpr int NV = DIM + 2;
+  R uL0[NV], uR0[NV], uL[NV], uR[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    uL0[v] = Ar<R>::load(L64[v]);
+    uR0[v] = Ar<R>::load(R64[v]);
+  }
+  double rhoe;
+  const R pdL = pdev<DIM>(L64, uL0, a.pd.gm1, a.pd.p_ref, rhoe);
+  const R pdR = pdev<DIM>(R64, uR0, a.pd.gm1, a.pd.p_ref, rhoe);
+  to_axes<DIM>(uL0, uL, l);
+  to_axes<DIM>(uR0, uR, l);
+  const ScalarsT<R>& k = shs<R>(a);
+  const Prim<DIM, R> pa = prims<DIM>(uL, pdL, k.p_ref);
+  const Prim<DIM, R> pb = prims<DIM>(uR, pdR, k.p_ref);
+  R Fs[NV];
+  surface_flux<DIM, 0>(a.surface, uL, pa, uR, pb, k.gamma, k.igm1, k.p_ref, Fs);
+  from_axes<DIM>(Fs, F, l);
+}
+
+__device__ __forceinline__ int nbr_elem(const InstArgs& I, int dim, int e, int l, int d) {
+  int c[3] = {e % I.nel[0], (e / I.nel[0]) % I.nel[1], dim == 3 ? e / (I.nel[0] * I.nel[1]) : 0};
+  c[l] = (c[l] + d + I.nel[l]) % I.nel[l];
+  return c[0] + I.nel[0] * (c[1] + I.nel[1] * c[2]);
+}
+
+template <int DIM, int N, class R>
+__global__ void __launch_bounds__(128) k_fv_blend(const ShockArgs a) {
+  using G = SG<DIM, N>;
+  constexpr int N1 = G::N1, NP = G::NP, NV = G::NV, NLINE = G::NLINE, NJ = G::NJ;
+  __shared__ R Fh[NJ * NV];
+  const int t = threadIdx.x;
+  const InstArgs& I = a.inst;
+  const int n = *a.count;
+  for (int k = blockIdx.x; k < n; k += gridDim.x) {
+    const int e = a.list[k];
+    // interface jobs: direction l, line, interface position i = 0..N+1 (between nodes i-1, i)
+    for (int j = t; j < NJ; j += blockDim.x) {
+      const int l = j / (NLINE * (N + 2));
+      const int r = j - l * NLINE * (N + 2);
+      const int line = r / (N + 2), i = r - line * (N + 2);
+      const int S = dstride<N1>(l);
+      const int base_nd = (line % S) + (line / S) * S * N1;  // node of position 0 on this line
+      int eL = e, iL = i - 1, eR = e, iR = i;
+      if (i == 0) { eL = nbr_elem(I, DIM, e, l, -1); iL = N; }
+      if (i == N + 1) { eR = nbr_elem(I, DIM, e, l, +1); iR = 0; }
+      const long long gL = I.base + (long long)eL * NP + base_nd + iL * S;
+      const long long gR = I.base + (long long)eR * NP + base_nd + iR * S;
+      double L64[NV], R64[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        L64[v] = a.U[v * a.stride + gL];
+        R64[v] = a.U[v * a.stride + gR];
+      }
+      R F[NV];
+      interface_flux<DIM, R>(a, l, L64, R64, F);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Fh[j * NV + v] = F[v];
+    }
+    __syncthreads();
+    const double al = a.alpha[e];
+    for (int nd = t; nd < NP; nd += blockDim.x) {
+      R rfv[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) rfv[v] = R(0);
+#pragma unroll
+      for (int l = 0; l < DIM; ++l) {
+        const int S = dstride<N1>(l);
+        const int i = (nd / S) % N1;
+        const int line = (nd % S) + (nd / (S * N1)) * S;
+        const int j0 = (l * NLINE + line) * (N + 2) + i;  // interface i - 1/2; i + 1/2 is j0 + 1
+        const R c = (sizeof(R) == 4 ? R(I.sf[l]) : R(I.s[l])) *
+                    (sizeof(R) == 4 ? R(a.iwf[i]) : R(a.iw[i]));
+#pragma unroll
+        for (int v = 0; v < NV; ++v) rfv[v] -= c * (Fh[(j0 + 1) * NV + v] - Fh[j0 * NV + v]);
+      }
+      const long long gi = I.base + (long long)e * NP + nd;
+      double res[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const double L = fma(al, Ar<R>::widen(rfv[v]) - a.ldg[v * a.stride + gi], a.ldg[v * a.stride + gi]);
+        if (a.mode == 0) {
+          res[v] = L;
+        } else {
+          const double u = a.U[v * a.stride + gi];
+          double x = fma(a.cb, u, a.bdt * L);
+          if (a.need_un) x = fma(a.ca, a.Un[v * a.stride + gi], x);
+          res[v] = x;
+          if (a.acc) {
+            double y = fma(a.acc_b, u, a.acc_bdt * L);
+            if (a.acc_a != 0.0) y = fma(a.acc_a, a.acc[v * a.stride + gi], y);
+            a.acc[v * a.stride + gi] = y;
+          }
+        }
+      }
+      if (a.mode == 1 && a.floor_on) {  // the stage kernel's positivity floor
+        if (a.rho_floor > 0.0 && res[0] < a.rho_floor) res[0] = a.rho_floor;
+        double kin = 0.0;
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) kin += res[1 + d] * res[1 + d] / res[0];
+        const double p = (a.gamma - 1.0) * (res[DIM + 1] - 0.5 * kin);
+        if (a.p_floor > 0.0 && p < a.p_floor) res[DIM + 1] = a.p_floor / (a.gamma - 1.0) + 0.5 * kin;
+      }
+      bool finite = true;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        finite = finite && finite64(res[v]);
+        a.out[v * a.stride + gi] = res[v];
+      }
+      if (!finite) atomicOr(a.err, 1u);
+    }
+    __syncthreads();
+  }
+}
+
+template <int DIM, int N>
+cudaError_t indicator_dn(const ShockArgs& a, cudaStream_t s) {
+  using G = SG<DIM, N>;
+  if (a.inst.n_elem <= 0) return cudaSuccess;
+  const unsigned grid = (unsigned)((a.inst.n_elem + G::EPB - 1) / G::EPB);
+  k_hg_indicator<DIM, N><<<grid, G::T, 0, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_hg_alpha<DIM><<<(unsigned)((a.inst.n_elem + 127) / 128), 128, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int DIM, int N>
+cudaError_t blend_dn(int fp32, const ShockArgs& a, cudaStream_t s) {
+  if (a.inst.n_elem <= 0) return cudaSuccess;
+  const int want = a.inst.n_elem;
+  const unsigned grid = (unsigned)(want < 148 * 16 ? want : 148 * 16);
+  if (fp32) k_fv_blend<DIM, N, float><<<grid, 128, 0, s>>>(a);
+  else k_fv_blend<DIM, N, double><<<grid, 128, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+#define DG_SHOCK_DISPATCH(CALL)                                                  \
+  switch (dim * 16 + N) {                                                        \
+    case 2 * 16 + 2: return CALL(2, 2);                                          \
+    case 2 * 16 + 3: return CALL(2, 3);                                          \
+    case 2 * 16 + 4: return CALL(2, 4);                                          \
+    case 2 * 16 + 5: return CALL(2, 5);                                          \
+    case 2 * 16 + 6: return CALL(2, 6);                                          \
+    case 2 * 16 + 7: return CALL(2, 7);                                          \
+    case 3 * 16 + 2: return CALL(3, 2);                                          \
+    case 3 * 16 + 3: return CALL(3, 3);                                          \
+    case 3 * 16 + 4: return CALL(3, 4);                                          \
+    case 3 * 16 + 5: return CALL(3, 5);                                          \
+    default: return cudaErrorInvalidValue;                                       \
+  }
+
+}  // namespace
+
+bool have_shock(int dim, int N) {
+  return (dim == 2 && N >= 2 && N <= 7) || (dim == 3 && N >= 2 && N <= 5);
+}
+
+cudaError_t launch_shock_indicator(int dim, int N, const ShockArgs& a, cudaStream_t s) {
+#define DG_I(d, n) indicator_dn<d, n>(a, s)
+  DG_SHOCK_DISPATCH(DG_I)
+#undef DG_I
+}
+
+cudaError_t launch_shock_blend(int dim, int N, int fp32, const ShockArgs& a, cudaStream_t s) {
+#define DG_B(d, n) blend_dn<d, n>(fp32, a, s)
+  DG_SHOCK_DISPATCH(DG_B)
+#undef DG_B
+}
+
+}  // namespace dg

@@ -490,6 +490,13 @@ struct EulerStage {
 
     const long long gi = I.base + (long long)(e0 + el) * NP + nd;
     double res[NV];
+    if (A.mode == 1 && A.alpha && A.alpha[e0 + el] > 0.0) {
+      // shock-flagged element: its DG residual goes to the side buffer, the blending launch
+      // forms the update
+#pragma unroll
+      for (int v = 0; v < NV; ++v) A.ldg[v * A.stride + gi] = Ar<R>::widen(acc[v]);
+      return;
+    }
     if (A.mode == 0) {
 #pragma unroll
       for (int v = 0; v < NV; ++v) res[v] = Ar<R>::widen(acc[v]);

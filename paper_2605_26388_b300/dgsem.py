@@ -36,7 +36,7 @@ _STATUS = {0: "DG_OK", -1: "DG_EINVAL", -2: "DG_ENOMEM", -3: "DG_ECUDA", -4: "DG
 EXPORTS = ["dg_init_mesh", "dg_state_size", "dg_instance_offset", "dg_set_state", "dg_get_state",
            "dg_rhs", "dg_rk_stage", "dg_rk_step", "dg_max_dt", "dg_check", "dg_gll",
            "dg_two_point_flux", "dg_max_dt_noalloc", "dg_set_launch", "dg_autotune",
-           "dg_rhs_vjp", "dg_rk_step_vjp", "dg_adjoint_gammabar", "dg_source_step", "dg_newton_updates",
+           "dg_rhs_vjp", "dg_rk_step_vjp", "dg_adjoint_gammabar", "dg_source_step", "dg_newton_updates", "dg_shock_alpha",
            "dg_math_fn",
            "dg_last_error", "dg_free"]
 
@@ -88,7 +88,8 @@ class Physics(C.Structure):
                 ("p_floor", C.c_double), ("p_ref", C.c_double), ("mu", C.c_double),
                 ("prandtl", C.c_double), ("chem", C.POINTER(Mechanism)),
                 ("time_scheme", C.c_int), ("chem_split", C.c_int), ("newton_max_it", C.c_int),
-                ("newton_tol", C.c_double)]
+                ("newton_tol", C.c_double), ("shock", C.c_int), ("alpha_min", C.c_double),
+                ("alpha_max", C.c_double), ("sharpness", C.c_double)]
 
 
 _lib = None
@@ -123,6 +124,7 @@ def lib():
         L.dg_autotune.argtypes = [vp, C.c_double, ip, C.POINTER(C.c_int), dp]
         L.dg_source_step.argtypes = [vp, vp, C.c_double, vp]
         L.dg_newton_updates.argtypes = [vp, C.POINTER(C.c_int64)]
+        L.dg_shock_alpha.argtypes = [vp, vp, vp, vp]
         L.dg_math_fn.argtypes = [ip, C.c_int64, vp, vp, vp]
         L.dg_last_error.argtypes = [vp]
         L.dg_last_error.restype = C.c_char_p
@@ -181,7 +183,8 @@ class Solver:
     def __init__(self, meshes, volume=VOL_STRONG, surface=SURF_RUSANOV, precision=FP64,
                  gamma=1.4, rho_floor=0.0, p_floor=0.0, p_ref=0.0, stream=None,
                  equations=DG_EULER, mu=0.0, prandtl=0.72, mechanism=None,
-                 time_scheme=SSPRK33, chem_split=False, newton_max_it=0, newton_tol=0.0):
+                 time_scheme=SSPRK33, chem_split=False, newton_max_it=0, newton_tol=0.0,
+                 shock=False, alpha_min=0.0, alpha_max=0.0, sharpness=0.0):
         import torch
         if isinstance(meshes, Mesh):
             meshes = [meshes]
@@ -190,7 +193,8 @@ class Solver:
         arr = (MeshDesc * len(self.meshes))(*[m.c() for m in self.meshes])
         phys = Physics(equations, volume, surface, precision, gamma, rho_floor, p_floor, p_ref,
                        mu, prandtl, None, time_scheme, 1 if chem_split else 0, newton_max_it,
-                       newton_tol)
+                       newton_tol, 1 if shock else 0, alpha_min, alpha_max, sharpness)
+        self.n_elem = sum(m.n_elem for m in self.meshes)
         if mechanism is not None:
             mech = mechanism if isinstance(mechanism, Mechanism) else Mechanism.from_dict(mechanism)
             phys.chem = C.pointer(mech)  # copied by dg_init_mesh
@@ -275,6 +279,15 @@ class Solver:
         self._call(lib().dg_source_step(self._h, self._dev(U, "U"), h, self._dev(out, "Uout")),
                    "dg_source_step")
         return out
+
+    def shock_alpha(self, U):
+        """(alpha_raw, alpha) per element for state U (see dg_shock_alpha)."""
+        import torch
+        a = torch.empty(self.n_elem, dtype=torch.float64, device="cuda")
+        b = torch.empty_like(a)
+        self._call(lib().dg_shock_alpha(self._h, self._dev(U, "U"), C.c_void_p(a.data_ptr()),
+                                        C.c_void_p(b.data_ptr())), "dg_shock_alpha")
+        return a, b
 
     def newton_updates(self) -> int:
         """Newton updates of the implicit substeps since the previous call (resets the count)."""

@@ -201,6 +201,19 @@ def batched_vortex_set(n_inst: int = 256, seed: int = 5, n_range=(8, 96), degree
     return out
 
 
+def blast_wave(dim: int, nel: int, xi: np.ndarray, p_in: float = 10.0, radius: float = 0.4,
+               gamma: float = 1.4, L: float = 2.0) -> np.ndarray:
+    """The shock-capturing workload: a blast in a periodic box [0, L]^dim -- gas at rest,
+    rho = 1, p = p_in inside the ball of the given radius about the box centre and p = 1
+    outside, a discontinuity at the GLL nodes (no smoothing)."""
+    lo, hi = (0.0,) * dim, (L,) * dim
+    X = node_coordinates(dim, (nel,) * dim, lo, hi, xi)
+    r2 = sum((X[l] - 0.5 * L) ** 2 for l in range(dim))
+    p = np.where(r2 < radius * radius, p_in, 1.0)
+    rho = np.ones_like(p)
+    return conserved(rho, [np.zeros_like(p)] * dim, p, gamma)
+
+
 def perturbed(U: np.ndarray, seed: int, rel: float) -> np.ndarray:
     """U times (1 + rel * xi), xi ~ U[-1, 1] seeded per entry (a non-smooth test state)."""
     r = uniform(seed, U.size).reshape(U.shape)
