@@ -476,6 +476,10 @@ void shock_args(const dg_ctx* c, int i, const dg::StageArgs& a, const StageCoef&
   sa.sharp = c->phys.sharpness;
   sa.alpha_min = c->phys.alpha_min;
   sa.alpha_max = c->phys.alpha_max;
+  // sigmoid(E) < alpha_min  <=>  E < T + (T/s) ln(alpha_min / (1 - alpha_min))
+  sa.emin = (sa.alpha_min > 0.0 && sa.alpha_min < 1.0)
+                ? sa.thr + (sa.thr / sa.sharp) * std::log(sa.alpha_min / (1.0 - sa.alpha_min))
+                : -INFINITY;
   sa.alpha_raw = c->alpha_raw + c->eoffs[i];
   sa.alpha = c->alpha + c->eoffs[i];
   sa.list = c->list;

@@ -108,6 +108,7 @@ struct ShockArgs {
   float iwf[kMaxN + 1];
   double Vinv[(kMaxN + 1) * (kMaxN + 1)];  // nodal -> orthonormal Legendre modes
   double thr, sharp, alpha_min, alpha_max;   // threshold T, steepness s, clipping bounds
+  double emin;           // the smoothness below which the sigmoid is under alpha_min
   double* alpha_raw;     // per element of the instance
   double* alpha;
   int* list;             // elements with alpha > 0 ...

@@ -2,10 +2,11 @@
 // Indicator and Smoothing", Eq. vol_blend; App. A "Shock Capturing").
 //
 // Per stage and instance, around the fused stage launch:
-//   1. k_hg_indicator: per element, the modal smoothness of rho p (FP64: orthonormal tensor
+//   1. k_hg_indicator: per element, the modal smoothness of rho p (orthonormal tensor
 //      Legendre modes by three line contractions with V^{-1} in shared memory, energies of
-//      the top and next-to-top shells), the sigmoid with threshold T and steepness s, and the
-//      clipping to [alpha_min, alpha_max] -> alpha_raw;
+//      the top and next-to-top shells; an FP32 filter settles the clearly smooth elements,
+//      the others are evaluated in FP64), the sigmoid with threshold T and steepness s, and
+//      the clipping to [alpha_min, alpha_max] -> alpha_raw;
 //   2. k_hg_alpha: alpha_e = max(alpha_raw_e, alpha_raw of the face neighbours); elements with
 //      alpha > 0 are appended to a list (its order does not matter: the elements are
 //      independent);
@@ -43,73 +44,145 @@ __device__ __forceinline__ int dstride(int l) {
 }
 
 // ---- 1: indicator ----
+// FP32 filter, FP64 decision: the modes, energies and E are first evaluated in FP32; an
+// element whose FP32 E lies below a quarter of E_min -- the E below which the sigmoid is
+// under alpha_min, so that alpha_raw is 0 -- is decided there (the FP32 error of E is many
+// orders of magnitude below that margin).  If any element of the CTA is not, the CTA repeats
+// the evaluation in FP64 exactly as the definition states and decides those elements from
+// it.  Smooth regions thus cost FP32 arithmetic only (B300 issues FP64 at a sixtieth of the
+// FP32 rate); every decision near the threshold is an FP64 one.
 template <int DIM, int N>
-__global__ void __launch_bounds__(SG<DIM, N>::T) k_hg_indicator(const ShockArgs a) {
-  using G = SG<DIM, N>;
-  constexpr int N1 = G::N1, NP = G::NP, EPB = G::EPB;
-  __shared__ double qa[EPB * NP], qb[EPB * NP], Vi[N1 * N1];
-  __shared__ double part[EPB * NP][4];
-  const int t = threadIdx.x;
-  for (int k = t; k < N1 * N1; k += blockDim.x) Vi[k] = a.Vinv[k];
-  const int el = t / NP, nd = t - el * NP;
-  const int e = blockIdx.x * EPB + el;
-  const bool active = t < EPB * NP && e < a.inst.n_elem;
-  if (active) {
-    const long long gi = a.inst.base + (long long)e * NP + nd;
-    double u[G::NV];
-#pragma unroll
-    for (int v = 0; v < G::NV; ++v) u[v] = a.U[v * a.stride + gi];
-    double m2 = 0.0;
-#pragma unroll
-    for (int d = 0; d < DIM; ++d) m2 = fma(u[1 + d], u[1 + d], m2);
-    const double p = (a.gamma - 1.0) * (u[DIM + 1] - 0.5 * m2 / u[0]);
-    qa[el * NP + nd] = u[0] * p;
-  }
-  __syncthreads();
-  // modes: V^{-1} along direction 0, 1 (, 2)
-  double* src = qa;
-  double* dst = qb;
+struct IG {
+  static constexpr int N1 = N + 1;
+  static constexpr int NP = DIM == 2 ? N1 * N1 : N1 * N1 * N1;
+  static constexpr int NPP = NP <= 32 ? 32 : (NP <= 64 ? 64 : (NP <= 128 ? 128 : 256));  // pow2 >= NP
+  static constexpr int EPB = SG<DIM, N>::EPB;
+  static constexpr int T = SG<DIM, N>::T;
+};
+
+// Modes of the EPB element fields in q[0] (ping-pong with q[1]): V^{-1} along each direction.
+// Returns the buffer holding the result.  Every thread of the CTA must call it.
+template <int DIM, int N, class F>
+__device__ __forceinline__ F* to_modes(F* q0, F* q1, const F* V, int el, int nd, bool active) {
+  constexpr int N1 = N + 1, NP = IG<DIM, N>::NP;
+  F* src = q0;
+  F* dst = q1;
 #pragma unroll
   for (int l = 0; l < DIM; ++l) {
     if (active) {
       const int S = dstride<N1>(l);
       const int i = (nd / S) % N1;
-      const double* line = src + el * NP + nd - i * S;
-      double acc = 0.0;
+      const F* line = src + el * NP + nd - i * S;
+      F acc = F(0);
 #pragma unroll
-      for (int j = 0; j < N1; ++j) acc = fma(Vi[i * N1 + j], line[j * S], acc);
+      for (int j = 0; j < N1; ++j) acc = fma(V[i * N1 + j], line[j * S], acc);
       dst[el * NP + nd] = acc;
     }
     __syncthreads();
-    double* tmp = src;
+    F* tmp = src;
     src = dst;
     dst = tmp;
   }
+  return src;
+}
+
+// The four shell energies of every element, by a fixed-order tree in shared memory
+// (deterministic): part[el][0][c] = E_tot^(N), E_tot^(N-1), E_high^(N), E_high^(N-1).
+template <int DIM, int N, class F>
+__device__ __forceinline__ void shell_energies(const F* m, F* part, int el, int nd, bool active) {
+  constexpr int N1 = N + 1, NP = IG<DIM, N>::NP, NPP = IG<DIM, N>::NPP, EPB = IG<DIM, N>::EPB;
+  const int t = threadIdx.x;
+  for (int k = t; k < EPB * NPP * 4; k += blockDim.x) part[k] = F(0);
+  __syncthreads();
   if (active) {
-    const double m = src[el * NP + nd];
+    const F mm = m[el * NP + nd];
     int mx = nd % N1;
-    if (DIM >= 2) mx = max(mx, (nd / N1) % N1);
+    mx = max(mx, (nd / N1) % N1);
     if (DIM == 3) mx = max(mx, nd / (N1 * N1));
-    const double e2 = m * m;
-    part[el * NP + nd][0] = e2;                      // E_tot^(N)
-    part[el * NP + nd][1] = mx <= N - 1 ? e2 : 0.0;  // E_tot^(N-1)
-    part[el * NP + nd][2] = mx == N ? e2 : 0.0;      // E_high^(N)
-    part[el * NP + nd][3] = mx == N - 1 ? e2 : 0.0;  // E_high^(N-1)
+    const F e2 = mm * mm;
+    F* p = part + (el * NPP + nd) * 4;
+    p[0] = e2;
+    p[1] = mx <= N - 1 ? e2 : F(0);
+    p[2] = mx == N ? e2 : F(0);
+    p[3] = mx == N - 1 ? e2 : F(0);
   }
   __syncthreads();
-  if (active && nd == 0) {
-    double s4[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int k = 0; k < NP; ++k) {
-#pragma unroll
-      for (int c = 0; c < 4; ++c) s4[c] += part[el * NP + k][c];
+#pragma unroll 1
+  for (int s = NPP / 2; s >= 1; s >>= 1) {
+    for (int k = t; k < EPB * s * 4; k += blockDim.x) {
+      const int e = k / (s * 4), r = k - e * s * 4, i = r >> 2, c = r & 3;
+      part[(e * NPP + i) * 4 + c] += part[(e * NPP + i + s) * 4 + c];
     }
-    const double r1 = s4[0] > 0.0 ? s4[2] / s4[0] : 0.0;
-    const double r2 = s4[1] > 0.0 ? s4[3] / s4[1] : 0.0;
-    const double E = fmax(r1, r2);
-    double al = 1.0 / (1.0 + exp(-(a.sharp / a.thr) * (E - a.thr)));
-    if (al < a.alpha_min) al = 0.0;
-    a.alpha_raw[e] = fmin(al, a.alpha_max);
+    __syncthreads();
   }
+}
+
+template <int DIM, int N>
+__global__ void __launch_bounds__(IG<DIM, N>::T) k_hg_indicator(const ShockArgs a) {
+  using G = IG<DIM, N>;
+  constexpr int N1 = G::N1, NP = G::NP, NPP = G::NPP, EPB = G::EPB, NV = DIM + 2;
+  __shared__ float qf[2][EPB * NP], Vf[N1 * N1], pf[EPB * NPP * 4];
+  __shared__ double qd[2][EPB * NP], Vd[N1 * N1], pd[EPB * NPP * 4];
+  __shared__ int need[EPB], any;
+  const int t = threadIdx.x;
+  for (int k = t; k < N1 * N1; k += blockDim.x) {
+    Vd[k] = a.Vinv[k];
+    Vf[k] = d2f_rn(a.Vinv[k]);
+  }
+  if (t == 0) any = 0;
+  const int el = t / NP, nd = t - el * NP;
+  const int e = blockIdx.x * EPB + el;
+  const bool active = t < EPB * NP && e < a.inst.n_elem;
+  const long long gi = a.inst.base + (long long)e * NP + nd;
+  if (active) {  // rho p in FP32 for the filter
+    float u[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) u[v] = d2f_rz(a.U[v * a.stride + gi]);
+    float m2 = 0.0f;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) m2 = fmaf(u[1 + d], u[1 + d], m2);
+    const float p = a.pf.gm1 * (u[DIM + 1] - 0.5f * m2 * __fdividef(1.0f, u[0]));
+    qf[0][el * NP + nd] = u[0] * p;
+  }
+  __syncthreads();
+  const float* mf = to_modes<DIM, N, float>(qf[0], qf[1], Vf, el, nd, active);
+  shell_energies<DIM, N, float>(mf, pf, el, nd, active);
+  if (t < EPB) {
+    const int ee = blockIdx.x * EPB + t;
+    const float* s4 = pf + t * NPP * 4;
+    const float r1 = s4[0] > 0.0f ? s4[2] / s4[0] : 0.0f;
+    const float r2 = s4[1] > 0.0f ? s4[3] / s4[1] : 0.0f;
+    const float E = fmaxf(r1, r2);
+    need[t] = ee < a.inst.n_elem && !(E <= 0.25f * (float)a.emin) ? 1 : 0;
+    if (need[t]) atomicOr(&any, 1);
+  }
+  __syncthreads();
+  double al = 0.0;
+  if (any) {  // FP64, as the definition states
+    if (active) {
+      double u[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) u[v] = a.U[v * a.stride + gi];
+      double m2 = 0.0;
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) m2 = fma(u[1 + d], u[1 + d], m2);
+      const double p = (a.gamma - 1.0) * (u[DIM + 1] - 0.5 * m2 / u[0]);
+      qd[0][el * NP + nd] = u[0] * p;
+    }
+    __syncthreads();
+    const double* md = to_modes<DIM, N, double>(qd[0], qd[1], Vd, el, nd, active);
+    shell_energies<DIM, N, double>(md, pd, el, nd, active);
+    if (t < EPB && need[t]) {
+      const double* s4 = pd + t * NPP * 4;
+      const double r1 = s4[0] > 0.0 ? s4[2] / s4[0] : 0.0;
+      const double r2 = s4[1] > 0.0 ? s4[3] / s4[1] : 0.0;
+      const double E = fmax(r1, r2);
+      al = 1.0 / (1.0 + exp(-(a.sharp / a.thr) * (E - a.thr)));
+      if (al < a.alpha_min) al = 0.0;
+      al = fmin(al, a.alpha_max);
+    }
+  }
+  if (t < EPB && blockIdx.x * EPB + t < a.inst.n_elem) a.alpha_raw[blockIdx.x * EPB + t] = al;
 }
 
 // ---- 2: neighbourhood maximum and the list of blended elements ----
@@ -288,7 +361,7 @@ __global__ void __launch_bounds__(128) k_fv_blend(const ShockArgs a) {
 
 template <int DIM, int N>
 cudaError_t indicator_dn(const ShockArgs& a, cudaStream_t s) {
-  using G = SG<DIM, N>;
+  using G = IG<DIM, N>;
   if (a.inst.n_elem <= 0) return cudaSuccess;
   const unsigned grid = (unsigned)((a.inst.n_elem + G::EPB - 1) / G::EPB);
   k_hg_indicator<DIM, N><<<grid, G::T, 0, s>>>(a);

@@ -226,3 +226,36 @@ def test_full_size_blast_sampled(env, orc, prec, tol):
     _, al = S.shock_alpha(Ud)
     assert np.abs(al.cpu().numpy() - oal).max() <= 1e-10
     S.close()
+
+
+def test_decisions_across_the_cut(env, orc):
+    """Forty elements whose smoothness E sweeps 0.05 E_min .. 20 E_min (E_min: the E where the
+    sigmoid reaches alpha_min): the GPU's FP32 filter hands every element near the cut to its
+    FP64 evaluation, so the cut decisions and the coefficients equal the oracle's."""
+    torch, dg = env
+    from numpy.polynomial import legendre as npleg
+    N, n = 3, 40
+    T = 0.5 * 10.0 ** (-1.8 * (N + 1) ** 0.25)
+    s = math.log(9999.0)
+    emin = T + T / s * math.log(0.001 / 0.999)
+    Es = emin * np.geomspace(0.05, 20.0, n)
+    m0 = 2.0  # mode (0, 0) of the constant 1 in 2D
+    amp = m0 * np.sqrt(Es / (1.0 - Es))
+    P = orc.Problem(dim=2, N=N, nel=(n, 1), lo=(0.0, 0.0), hi=(float(n), 1.0), volume=2, surface=0,
+                    gamma=GAMMA, shock=True)
+    S = dg.Solver(dg.Mesh(2, N, (n, 1), (0.0, 0.0), (float(n), 1.0)), volume=2, surface=0, gamma=GAMMA,
+                  shock=True)
+    xi, _ = orc.gll(N)
+    X = wl.node_coordinates(2, P.nel, P.lo, P.hi, xi)
+    e = np.floor(X[0]).astype(int).clip(0, n - 1)
+    ref = 2.0 * (X[0] - e) - 1.0
+    PN = npleg.legval(ref, np.eye(N + 1)[N]) * math.sqrt((2 * N + 1) / 2.0)
+    p = 1.0 + amp[e] / math.sqrt(2.0) * PN
+    U = wl.conserved(np.ones_like(p), [0 * p, 0 * p], p, GAMMA).reshape(P.shape)
+    oraw, _ = orc.shock_alpha(P, U)
+    raw, _ = S.shock_alpha(dev(torch, U))
+    raw = raw.cpu().numpy()
+    assert 0 < np.count_nonzero(oraw) < n
+    assert np.array_equal(raw > 0, oraw > 0)
+    assert np.abs(raw - oraw).max() <= 1e-10
+    S.close()
