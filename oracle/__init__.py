@@ -30,6 +30,7 @@ _LIB = os.path.join(_HERE, "_build", "liboracle.so")
 EULER, NAVIER_STOKES, NS_REACTING = 0, 1, 2
 VOL_STRONG, VOL_WEAK, VOL_EC, VOL_CENTRAL = 0, 1, 2, 3
 SURF_RUSANOV, SURF_HLLC, SURF_HLL, SURF_EC, SURF_CENTRAL = 0, 1, 2, 3, 4
+BC_PERIODIC, BC_SLIP_WALL, BC_INFLOW, BC_OUTFLOW, BC_DIRICHLET = 0, 1, 2, 3, 4
 
 
 def build(force: bool = False) -> str:
@@ -77,7 +78,7 @@ class _Problem(C.Structure):
         ("rho_floor", C.c_double), ("p_floor", C.c_double),
         ("mech", C.POINTER(_Mech)), ("parts", C.c_int),
         ("shock", C.c_int), ("alpha_min", C.c_double), ("alpha_max", C.c_double),
-        ("sharpness", C.c_double),
+        ("sharpness", C.c_double), ("bc", C.c_int * 6), ("bc_state", (C.c_double * 5) * 6),
     ]
 
 
@@ -103,6 +104,8 @@ class Problem:
     alpha_min: float = 0.001
     alpha_max: float = 0.5
     sharpness: float = math.log(9999.0)
+    bc: tuple = (0, 0, 0, 0, 0, 0)  # Euler: per domain face x-, x+, y-, y+, z-, z+; 0 = periodic
+    bc_state: tuple = None          # per face: the exterior conserved state (INFLOW, DIRICHLET)
 
     @property
     def nvars(self) -> int:
@@ -135,6 +138,11 @@ class Problem:
         p.parts = self.parts
         p.shock = 1 if self.shock else 0
         p.alpha_min, p.alpha_max, p.sharpness = self.alpha_min, self.alpha_max, self.sharpness
+        for f in range(6):
+            p.bc[f] = int(self.bc[f])
+            if self.bc_state is not None and self.bc_state[f] is not None:
+                for v, x in enumerate(self.bc_state[f]):
+                    p.bc_state[f][v] = float(x)
         if self.mech is not None:
             p._mech_keep = mechanism(self.mech)  # kept alive with the structure
             p.mech = C.pointer(p._mech_keep)

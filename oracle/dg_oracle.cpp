@@ -43,6 +43,9 @@ enum { ORC_EULER = 0, ORC_NAVIER_STOKES = 1, ORC_NS_REACTING = 2 };
 enum { ORC_VOL_STRONG = 0, ORC_VOL_WEAK = 1, ORC_VOL_EC = 2, ORC_VOL_CENTRAL = 3 };
 enum { ORC_SURF_RUSANOV = 0, ORC_SURF_HLLC = 1, ORC_SURF_HLL = 2, ORC_SURF_EC = 3,
        ORC_SURF_CENTRAL = 4 };
+// boundary condition of a domain face (0 = periodic)
+enum { ORC_BC_PERIODIC = 0, ORC_BC_SLIP_WALL = 1, ORC_BC_INFLOW = 2, ORC_BC_OUTFLOW = 3,
+       ORC_BC_DIRICHLET = 4 };
 
 }  // namespace
 
@@ -72,6 +75,8 @@ struct OrcProblem {
   int parts;                  // ORC_NS_REACTING: 1 inviscid, 2 viscous, 4 source (0 = all)
   int shock;                  // Euler: 1 = Hennemann-Gassner DG/FV blending of the residual
   double alpha_min, alpha_max, sharpness;  // blending bounds and the sigmoid's steepness s
+  int bc[6];                  // Euler: per domain face x-, x+, y-, y+, z-, z+ (0 = periodic)
+  double bc_state[6][5];      // INFLOW / DIRICHLET: the exterior conserved state
 };
 
 }  // extern "C"
@@ -374,6 +379,44 @@ struct Mesh {
   }
 };
 
+// Boundary flux F* in direction l at domain face f (Sec. 3.1.1 "Surface Fluxes": one
+// functor per boundary type; Sec. 4 set-ups: enforced weakly through the numerical flux).
+// own_left: the element's own trace is the left state (upper face).  READINGS: slip wall --
+// the Riemann flux against the mirror state (normal momentum reversed); supersonic inflow --
+// "the flux evaluated directly from" the prescribed state, F^l(U_b); supersonic outflow --
+// the interior state's flux F^l(U-); free-stream Dirichlet -- the Riemann flux against U_b.
+void boundary_flux(const OrcProblem& P, int f, int l, const double* uown, bool own_left, double* F) {
+  const int dim = P.dim, nv = dim + 2;
+  double ub[8];
+  switch (P.bc[f]) {
+    case ORC_BC_SLIP_WALL:
+      for (int v = 0; v < nv; ++v) ub[v] = uown[v];
+      ub[1 + l] = -uown[1 + l];
+      break;
+    case ORC_BC_INFLOW:
+      euler_flux(dim, l, P.bc_state[f], P.gamma, F);
+      return;
+    case ORC_BC_OUTFLOW:
+      euler_flux(dim, l, uown, P.gamma, F);
+      return;
+    default:  // ORC_BC_DIRICHLET
+      for (int v = 0; v < nv; ++v) ub[v] = P.bc_state[f][v];
+      break;
+  }
+  if (own_left) surface_flux(P.surface, dim, l, uown, ub, P.gamma, F);
+  else surface_flux(P.surface, dim, l, ub, uown, P.gamma, F);
+}
+
+// Whether face side (0 lower, 1 upper) of element e in direction l lies on a non-periodic
+// domain face; returns that face's index or -1.
+int boundary_face(const OrcProblem& P, const Mesh& M, int e, int l, int side) {
+  const int f = 2 * l + side;
+  if (P.bc[f] == ORC_BC_PERIODIC) return -1;
+  int c[3];
+  M.elem_coords(e, c);
+  return (side ? c[l] == M.nel[l] - 1 : c[l] == 0) ? f : -1;
+}
+
 void load_node(const Mesh& M, int nv, const double* U, int e, int nd, double* u) {
   for (int v = 0; v < nv; ++v) u[v] = U[((size_t)v * M.n_elem + e) * M.n_nodes + nd];
 }
@@ -439,16 +482,26 @@ void euler_element_residual(const OrcProblem& P, const Mesh& M, const Ops& ops,
       if (ijk[l] == N) {  // upper face: own state is the left state
         int nk[3] = {ijk[0], ijk[1], ijk[2]};
         nk[l] = 0;
-        load_node(M, nv, U, M.neighbour(e, l, +1), M.node(nk), unbr);
-        surface_flux(P.surface, dim, l, uown, unbr, gamma, Fs);
+        const int fb = boundary_face(P, M, e, l, 1);
+        if (fb >= 0) {
+          boundary_flux(P, fb, l, uown, true, Fs);
+        } else {
+          load_node(M, nv, U, M.neighbour(e, l, +1), M.node(nk), unbr);
+          surface_flux(P.surface, dim, l, uown, unbr, gamma, Fs);
+        }
         for (int v = 0; v < nv; ++v)
           R[nd * nv + v] -= s / ops.w[N] * (Fs[v] - (weak ? 0.0 : Fown[v]));
       }
       if (ijk[l] == 0) {  // lower face: own state is the right state
         int nk[3] = {ijk[0], ijk[1], ijk[2]};
         nk[l] = N;
-        load_node(M, nv, U, M.neighbour(e, l, -1), M.node(nk), unbr);
-        surface_flux(P.surface, dim, l, unbr, uown, gamma, Fs);
+        const int fb = boundary_face(P, M, e, l, 0);
+        if (fb >= 0) {
+          boundary_flux(P, fb, l, uown, false, Fs);
+        } else {
+          load_node(M, nv, U, M.neighbour(e, l, -1), M.node(nk), unbr);
+          surface_flux(P.surface, dim, l, unbr, uown, gamma, Fs);
+        }
         for (int v = 0; v < nv; ++v)
           R[nd * nv + v] += s / ops.w[0] * (Fs[v] - (weak ? 0.0 : Fown[v]));
       }
@@ -577,7 +630,9 @@ void shock_alpha(const OrcProblem& P, const double* U, double* alpha_raw, double
   for (int e = 0; e < M.n_elem; ++e) {
     double a = alpha_raw[e];
     for (int l = 0; l < M.dim; ++l)
-      for (int off = -1; off <= 1; off += 2) a = std::fmax(a, alpha_raw[M.neighbour(e, l, off)]);
+      for (int off = -1; off <= 1; off += 2)
+        if (boundary_face(P, M, e, l, off > 0 ? 1 : 0) < 0)  // no neighbour across a boundary
+          a = std::fmax(a, alpha_raw[M.neighbour(e, l, off)]);
     alpha[e] = a;
   }
 }
@@ -603,22 +658,32 @@ void fv_element_residual(const OrcProblem& P, const Mesh& M, const Ops& ops, con
       double uo[8], ua[8], fm[8], fp[8];
       load_node(M, nv, U, e, nd, uo);
       int nk[3] = {ijk[0], ijk[1], ijk[2]};
-      if (il == 0) {
-        nk[l] = N;
-        load_node(M, nv, U, M.neighbour(e, l, -1), M.node(nk), ua);
+      const int fl = il == 0 ? boundary_face(P, M, e, l, 0) : -1;
+      if (fl >= 0) {
+        boundary_flux(P, fl, l, uo, false, fm);
       } else {
-        nk[l] = il - 1;
-        load_node(M, nv, U, e, M.node(nk), ua);
+        if (il == 0) {
+          nk[l] = N;
+          load_node(M, nv, U, M.neighbour(e, l, -1), M.node(nk), ua);
+        } else {
+          nk[l] = il - 1;
+          load_node(M, nv, U, e, M.node(nk), ua);
+        }
+        surface_flux(P.surface, dim, l, ua, uo, P.gamma, fm);
       }
-      surface_flux(P.surface, dim, l, ua, uo, P.gamma, fm);
-      if (il == N) {
-        nk[l] = 0;
-        load_node(M, nv, U, M.neighbour(e, l, +1), M.node(nk), ua);
+      const int fu = il == N ? boundary_face(P, M, e, l, 1) : -1;
+      if (fu >= 0) {
+        boundary_flux(P, fu, l, uo, true, fp);
       } else {
-        nk[l] = il + 1;
-        load_node(M, nv, U, e, M.node(nk), ua);
+        if (il == N) {
+          nk[l] = 0;
+          load_node(M, nv, U, M.neighbour(e, l, +1), M.node(nk), ua);
+        } else {
+          nk[l] = il + 1;
+          load_node(M, nv, U, e, M.node(nk), ua);
+        }
+        surface_flux(P.surface, dim, l, uo, ua, P.gamma, fp);
       }
-      surface_flux(P.surface, dim, l, uo, ua, P.gamma, fp);
       for (int v = 0; v < nv; ++v) R[nd * nv + v] -= s / ops.w[il] * (fp[v] - fm[v]);
     }
   }
@@ -643,9 +708,19 @@ int check_problem(const OrcProblem& P) {
     if (P.rho_floor > 0.0 || P.p_floor > 0.0) return -6;
     if (P.mu < 0.0 || !(P.prandtl > 0.0)) return -1;
     if (P.shock) return -6;
+    for (int f = 0; f < 6; ++f)
+      if (P.bc[f] != ORC_BC_PERIODIC) return -6;
     return 0;
   }
   if (P.equations != ORC_EULER) return -6;
+  for (int f = 0; f < 2 * P.dim; ++f) {
+    if (P.bc[f] < ORC_BC_PERIODIC || P.bc[f] > ORC_BC_DIRICHLET) return -1;
+    if ((P.bc[f] == ORC_BC_PERIODIC) != (P.bc[f ^ 1] == ORC_BC_PERIODIC)) return -1;  // pairs
+    if (P.bc[f] == ORC_BC_INFLOW || P.bc[f] == ORC_BC_DIRICHLET) {
+      Prim q = primitives(P.dim, P.bc_state[f], P.gamma);
+      if (!(q.rho > 0.0) || !(q.p > 0.0)) return -1;
+    }
+  }
   if (P.shock && (P.N < 2 || !(P.alpha_min >= 0.0) || !(P.alpha_max <= 1.0) ||
                   !(P.alpha_min <= P.alpha_max) || !(P.sharpness > 0.0)))
     return -1;
@@ -1515,7 +1590,8 @@ int orc_rhs_jvp(const OrcProblem* P, const double* U, const double* V, double gd
                 double* dL) {
   int rc = check_problem(*P);
   if (rc) return rc;
-  if (P->shock) return -6;  // the dual-number residual has no shock capturing
+  // the dual-number residual has no shock capturing and periodic boundaries only
+  if (P->shock || P->bc[0] || P->bc[1] || P->bc[2] || P->bc[3] || P->bc[4] || P->bc[5]) return -6;
   if ((P->volume != ORC_VOL_STRONG && P->volume != ORC_VOL_WEAK) || P->surface != ORC_SURF_RUSANOV ||
       P->equations != ORC_EULER)
     return -6;
@@ -1540,7 +1616,8 @@ int orc_rhs_vjp_brute(const OrcProblem* P, const double* U, const double* lam, d
                       double* gbar) {
   int rc = check_problem(*P);
   if (rc) return rc;
-  if (P->shock) return -6;  // the dual-number residual has no shock capturing
+  // the dual-number residual has no shock capturing and periodic boundaries only
+  if (P->shock || P->bc[0] || P->bc[1] || P->bc[2] || P->bc[3] || P->bc[4] || P->bc[5]) return -6;
   Mesh M(*P);
   const size_t n = (size_t)n_vars(*P) * M.n_elem * M.n_nodes;
   if (n > 20000) return -1;
@@ -1569,7 +1646,8 @@ int orc_rollout_grad(const OrcProblem* P, const double* U0, const double* target
                      double dt, int n_steps, double* grad, double* ggam) {
   int rc = check_problem(*P);
   if (rc) return rc;
-  if (P->shock) return -6;  // the dual-number residual has no shock capturing
+  // the dual-number residual has no shock capturing and periodic boundaries only
+  if (P->shock || P->bc[0] || P->bc[1] || P->bc[2] || P->bc[3] || P->bc[4] || P->bc[5]) return -6;
   if ((P->volume != ORC_VOL_STRONG && P->volume != ORC_VOL_WEAK) || P->surface != ORC_SURF_RUSANOV ||
       P->equations != ORC_EULER)
     return -6;
