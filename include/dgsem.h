@@ -92,15 +92,27 @@ enum { DG_SSPRK33 = 0, DG_SSPRK54 = 1 };
 #define DG_NEWTON_MAX_IT 40
 #define DG_NEWTON_TOL 1e-12
 
-/* One periodic Cartesian mesh instance (Sec. 3.1.1: element-wise affine map of the
- * reference cube; collocation on (N+1)^dim GLL nodes). */
+/* Boundary conditions of a non-periodic domain face (Sec. 3.1.1 "Surface Fluxes": one
+ * functor per boundary type; enforced weakly through the numerical flux, Sec. 4 set-ups):
+ *   DG_BC_SLIP_WALL  the Riemann flux against the mirror state (normal momentum reversed);
+ *   DG_BC_INFLOW     supersonic inflow: the flux F^l(U_b) of the prescribed state;
+ *   DG_BC_OUTFLOW    supersonic outflow: the flux F^l(U-) of the interior state;
+ *   DG_BC_DIRICHLET  free stream: the Riemann flux against the prescribed state U_b. */
+enum { DG_BC_SLIP_WALL = 1, DG_BC_INFLOW = 2, DG_BC_OUTFLOW = 3, DG_BC_DIRICHLET = 4 };
+
+/* One Cartesian mesh instance (Sec. 3.1.1: element-wise affine map of the reference cube;
+ * collocation on (N+1)^dim GLL nodes). */
 typedef struct {
   int dim;          /* 2 or 3 */
   int N;            /* polynomial degree: 1..7 in 2D, 1..5 in 3D (Navier-Stokes: 1..4) */
   int nel[3];       /* elements per direction (nel[2] ignored in 2D) */
   double lo[3];     /* box lower corner */
   double hi[3];     /* box upper corner */
-  int periodic[3];  /* must be 1 in every used direction, else DG_EUNSUPPORTED */
+  int periodic[3];  /* 1: periodic in that direction; 0: the faces bc[2l] (lower) and bc[2l+1]
+                     * (upper) carry boundary conditions (DG_EULER only, else DG_EUNSUPPORTED) */
+  int bc[6];        /* DG_BC_* per face x-, x+, y-, y+, z-, z+ of a non-periodic direction */
+  double bc_state[6][5];  /* DG_BC_INFLOW / DG_BC_DIRICHLET: the conserved state U_b
+                           * (rho, rho u, rho v[, rho w], E) of that face, rho > 0, p > 0 */
 } dg_mesh_desc;
 
 /* Species and reactions of a reacting mixture (Sec. 2 thermochemistry, single temperature;

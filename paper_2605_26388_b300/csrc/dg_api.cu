@@ -149,7 +149,20 @@ dg_status check_desc(const dg_mesh_desc& m, int dim0, std::string& why) {
   for (int l = 0; l < m.dim; ++l) {
     if (m.nel[l] < 1) { why = "nel must be >= 1"; return DG_EINVAL; }
     if (!(m.hi[l] > m.lo[l])) { why = "hi must exceed lo"; return DG_EINVAL; }
-    if (m.periodic[l] != 1) { why = "only periodic meshes are supported"; return DG_EUNSUPPORTED; }
+    if (m.periodic[l] != 1 && m.periodic[l] != 0) { why = "periodic must be 0 or 1"; return DG_EINVAL; }
+    if (m.periodic[l] == 1) continue;
+    for (int side = 0; side < 2; ++side) {
+      const int f = 2 * l + side;
+      if (m.bc[f] < DG_BC_SLIP_WALL || m.bc[f] > DG_BC_DIRICHLET) { why = "bad boundary type"; return DG_EINVAL; }
+      if (m.bc[f] == DG_BC_INFLOW || m.bc[f] == DG_BC_DIRICHLET) {
+        const double* b = m.bc_state[f];
+        double m2 = 0.0;
+        for (int d = 0; d < m.dim; ++d) m2 += b[1 + d] * b[1 + d];
+        bool ok = b[0] > 0.0 && std::isfinite(b[0]) && std::isfinite(m2) && std::isfinite(b[m.dim + 1]);
+        ok = ok && b[m.dim + 1] - 0.5 * m2 / b[0] > 0.0;
+        if (!ok) { why = "boundary state must have rho > 0 and p > 0"; return DG_EINVAL; }
+      }
+    }
   }
   const long long ne = (long long)m.nel[0] * m.nel[1] * (m.dim == 3 ? m.nel[2] : 1);
   if (ne > (1LL << 31) - 1) { why = "too many elements"; return DG_EINVAL; }
@@ -286,6 +299,15 @@ void inst_args(const dg_ctx* c, int i, dg::InstArgs& I) {
   const dg_mesh_desc& m = c->inst[i];
   std::memset(&I, 0, sizeof(I));
   I.base = c->offs[i];
+  for (int l = 0; l < m.dim; ++l) {
+    if (m.periodic[l] == 1) continue;
+    for (int side = 0; side < 2; ++side) {
+      const int f = 2 * l + side;
+      I.bc[f] = m.bc[f];
+      for (int v = 0; v < 5; ++v) I.bcs[f][v] = m.bc_state[f][v];
+    }
+    I.nonper = 1;
+  }
   for (int l = 0; l < 3; ++l) {
     I.nel[l] = (l < m.dim) ? m.nel[l] : 1;
     I.s[l] = (l < m.dim) ? 2.0 / ((m.hi[l] - m.lo[l]) / m.nel[l]) : 0.0;
@@ -584,6 +606,9 @@ dg_status build_batch(dg_ctx* c) {
 // ---- adjoint ----
 dg_status ensure_adjoint(dg_ctx* c) {
   if (c->shock) return fail(c, DG_EUNSUPPORTED, "the adjoint has no shock capturing");
+  for (const dg_mesh_desc& m : c->inst)
+    for (int l = 0; l < m.dim; ++l)
+      if (m.periodic[l] != 1) return fail(c, DG_EUNSUPPORTED, "the adjoint covers periodic meshes");
   if (c->phys.volume == DG_VOL_EC || c->phys.surface != DG_SURF_RUSANOV)
     return fail(c, DG_EUNSUPPORTED, "the adjoint covers the strong/weak volume form with the Rusanov flux");
   if (c->gacc) return DG_OK;
@@ -822,8 +847,11 @@ dg_status dg_init_mesh(const dg_mesh_desc* inst, int n_inst, const dg_physics* p
       if (st) return st;
     }
     if (inst[0].dim != 3) return DG_EUNSUPPORTED;
-    for (int i = 0; i < n_inst; ++i)
+    for (int i = 0; i < n_inst; ++i) {
       if (!dg::have_reacting(inst[i].N, mech.ns)) return DG_EUNSUPPORTED;
+      for (int l = 0; l < 3; ++l)
+        if (inst[i].periodic[l] != 1) return DG_EUNSUPPORTED;  // boundary kernels: Euler only
+    }
     if (phys->volume != DG_VOL_STRONG || phys->surface != DG_SURF_RUSANOV ||
         phys->rho_floor > 0.0 || phys->p_floor > 0.0)
       return DG_EUNSUPPORTED;

@@ -20,6 +20,9 @@ struct InstArgs {
   float sf[3];
   double lift;         // 1 / w_0 (= 1 / w_N) of the GLL rule
   float liftf;
+  int nonper;          // 1: some direction is not periodic
+  int bc[6];           // boundary type per domain face (0: periodic)
+  double bcs[6][5];    // prescribed boundary states (conserved, FP64)
 };
 
 // Launch-wide scalars in one precision, precomputed on the host so that no thread converts

@@ -197,6 +197,7 @@ __global__ void k_hg_alpha(const ShockArgs a) {
   for (int l = 0; l < DIM; ++l) {
 #pragma unroll
     for (int d = -1; d <= 1; d += 2) {
+      if (a.inst.nonper && boundary_face(a.inst, DIM, e, l, d > 0 ? 1 : 0) >= 0) continue;  // no neighbour
       int cc[3] = {c[0], c[1], c[2]};
       cc[l] = (cc[l] + d + nel[l]) % nel[l];
       al = fmax(al, a.alpha_raw[cc[0] + nel[0] * (cc[1] + nel[1] * cc[2])]);
@@ -207,35 +208,6 @@ __global__ void k_hg_alpha(const ShockArgs a) {
 }
 
 // ---- 4: sub-cell FV residual, blend, stage update ----
-template <int DIM, class R>
-__device__ __forceinline__ void to_axes(const R* in, R* out, int l) {
-  constexpr int NV = DIM + 2;
-  out[0] = in[0];
-  out[NV - 1] = in[NV - 1];
-  if constexpr (DIM == 2) {
-    out[1] = l ? in[2] : in[1];
-    out[2] = l ? in[1] : in[2];
-  } else {
-    out[1] = l == 0 ? in[1] : (l == 1 ? in[2] : in[3]);
-    out[2] = l == 0 ? in[2] : (l == 1 ? in[3] : in[1]);
-    out[3] = l == 0 ? in[3] : (l == 1 ? in[1] : in[2]);
-  }
-}
-template <int DIM, class R>
-__device__ __forceinline__ void from_axes(const R* in, R* out, int l) {
-  constexpr int NV = DIM + 2;
-  out[0] = in[0];
-  out[NV - 1] = in[NV - 1];
-  if constexpr (DIM == 2) {
-    out[1] = l ? in[2] : in[1];
-    out[2] = l ? in[1] : in[2];
-  } else {
-    out[1] = l == 0 ? in[1] : (l == 1 ? in[3] : in[2]);
-    out[2] = l == 0 ? in[2] : (l == 1 ? in[1] : in[3]);
-    out[3] = l == 0 ? in[3] : (l == 1 ? in[2] : in[1]);
-  }
-}
-
 template <class R> __device__ __forceinline__ const ScalarsT<R>& shs(const ShockArgs& a);
 template <> __device__ __forceinline__ const ScalarsT<double>& shs<double>(const ShockArgs& a) { return a.pd; }
 template <> __device__ __forceinline__ const ScalarsT<float>& shs<float>(const ShockArgs& a) { return a.pf; }
@@ -254,14 +226,34 @@ __device__ __forceinline__ void interface_flux(const ShockArgs& a, int l, const 
   double rhoe;
   const R pdL = pdev<DIM>(L64, uL0, a.pd.gm1, a.pd.p_ref, rhoe);
   const R pdR = pdev<DIM>(R64, uR0, a.pd.gm1, a.pd.p_ref, rhoe);
-  to_axes<DIM>(uL0, uL, l);
-  to_axes<DIM>(uR0, uR, l);
+  to_face_axes<DIM>(uL0, uL, l);
+  to_face_axes<DIM>(uR0, uR, l);
   const ScalarsT<R>& k = shs<R>(a);
   const Prim<DIM, R> pa = prims<DIM>(uL, pdL, k.p_ref);
   const Prim<DIM, R> pb = prims<DIM>(uR, pdR, k.p_ref);
   R Fs[NV];
   surface_flux<DIM, 0>(a.surface, uL, pa, uR, pb, k.gamma, k.igm1, k.p_ref, Fs);
-  from_axes<DIM>(Fs, F, l);
+  from_face_axes<DIM>(Fs, F, l);
+}
+
+// Flux at domain face fb (boundary condition) from the interior node's FP64 state, as the
+// stage kernel's face jobs evaluate it; side = 1 when the interior is the left state.
+template <int DIM, class R>
+__device__ __forceinline__ void domain_face_flux(const ShockArgs& a, int fb, int l, int side,
+                                                 const double* own64, R* F) {
+  constexpr int NV = DIM + 2;
+  R own0[NV], own[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) own0[v] = Ar<R>::load(own64[v]);
+  double rhoe;
+  const R pd = pdev<DIM>(own64, own0, a.pd.gm1, a.pd.p_ref, rhoe);
+  to_face_axes<DIM>(own0, own, l);
+  const ScalarsT<R>& k = shs<R>(a);
+  const Prim<DIM, R> po = prims<DIM>(own, pd, k.p_ref);
+  R Fs[NV];
+  boundary_flux<DIM, R>(a.inst, fb, l, side, own, po, a.surface, k.gamma, k.igm1, k.p_ref, a.pd.gm1,
+                        a.pd.p_ref, Fs);
+  from_face_axes<DIM>(Fs, F, l);
 }
 
 __device__ __forceinline__ int nbr_elem(const InstArgs& I, int dim, int e, int l, int d) {
@@ -287,19 +279,28 @@ __global__ void __launch_bounds__(128) k_fv_blend(const ShockArgs a) {
       const int line = r / (N + 2), i = r - line * (N + 2);
       const int S = dstride<N1>(l);
       const int base_nd = (line % S) + (line / S) * S * N1;  // node of position 0 on this line
-      int eL = e, iL = i - 1, eR = e, iR = i;
-      if (i == 0) { eL = nbr_elem(I, DIM, e, l, -1); iL = N; }
-      if (i == N + 1) { eR = nbr_elem(I, DIM, e, l, +1); iR = 0; }
-      const long long gL = I.base + (long long)eL * NP + base_nd + iL * S;
-      const long long gR = I.base + (long long)eR * NP + base_nd + iR * S;
-      double L64[NV], R64[NV];
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        L64[v] = a.U[v * a.stride + gL];
-        R64[v] = a.U[v * a.stride + gR];
-      }
+      const int fb = (i == 0 || i == N + 1) && I.nonper ? boundary_face(I, DIM, e, l, i == N + 1 ? 1 : 0) : -1;
       R F[NV];
-      interface_flux<DIM, R>(a, l, L64, R64, F);
+      if (fb >= 0) {  // element face on a domain boundary: the boundary functor
+        const long long go = I.base + (long long)e * NP + base_nd + (i == 0 ? 0 : N) * S;
+        double own64[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) own64[v] = a.U[v * a.stride + go];
+        domain_face_flux<DIM, R>(a, fb, l, i == 0 ? 0 : 1, own64, F);
+      } else {
+        int eL = e, iL = i - 1, eR = e, iR = i;
+        if (i == 0) { eL = nbr_elem(I, DIM, e, l, -1); iL = N; }
+        if (i == N + 1) { eR = nbr_elem(I, DIM, e, l, +1); iR = 0; }
+        const long long gL = I.base + (long long)eL * NP + base_nd + iL * S;
+        const long long gR = I.base + (long long)eR * NP + base_nd + iR * S;
+        double L64[NV], R64[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          L64[v] = a.U[v * a.stride + gL];
+          R64[v] = a.U[v * a.stride + gR];
+        }
+        interface_flux<DIM, R>(a, l, L64, R64, F);
+      }
 #pragma unroll
       for (int v = 0; v < NV; ++v) Fh[j * NV + v] = F[v];
     }

@@ -56,6 +56,91 @@ __device__ __forceinline__ void surface_flux(int kind, const R* uL, const Prim<D
   }
 }
 
+// Cyclic relabelling of the axes that makes direction l the first one (and back): the Euler
+// fluxes are unchanged by a relabelling of the axes, so every face flux is evaluated with one
+// instantiation (normal along axis 0).
+template <int DIM, class R>
+__device__ __forceinline__ void to_face_axes(const R* in, R* out, int l) {
+  constexpr int NV = DIM + 2;
+  out[0] = in[0];
+  out[NV - 1] = in[NV - 1];
+  if constexpr (DIM == 2) {
+    out[1] = l ? in[2] : in[1];
+    out[2] = l ? in[1] : in[2];
+  } else {
+    out[1] = l == 0 ? in[1] : (l == 1 ? in[2] : in[3]);
+    out[2] = l == 0 ? in[2] : (l == 1 ? in[3] : in[1]);
+    out[3] = l == 0 ? in[3] : (l == 1 ? in[1] : in[2]);
+  }
+}
+template <int DIM, class R>
+__device__ __forceinline__ void from_face_axes(const R* in, R* out, int l) {
+  constexpr int NV = DIM + 2;
+  out[0] = in[0];
+  out[NV - 1] = in[NV - 1];
+  if constexpr (DIM == 2) {
+    out[1] = l ? in[2] : in[1];
+    out[2] = l ? in[1] : in[2];
+  } else {
+    out[1] = l == 0 ? in[1] : (l == 1 ? in[3] : in[2]);
+    out[2] = l == 0 ? in[2] : (l == 1 ? in[1] : in[3]);
+    out[3] = l == 0 ? in[3] : (l == 1 ? in[2] : in[1]);
+  }
+}
+
+// Domain face of face `side` (0 lower, 1 upper) in direction l of element e, if that face
+// carries a boundary condition; else -1.
+__device__ __forceinline__ int boundary_face(const InstArgs& I, int dim, int e, int l, int side) {
+  const int f = 2 * l + side;
+  if (I.bc[f] == 0) return -1;
+  const int c = l == 0 ? e % I.nel[0] : (l == 1 ? (e / I.nel[0]) % I.nel[1] : e / (I.nel[0] * I.nel[1]));
+  (void)dim;
+  return (side ? c == I.nel[l] - 1 : c == 0) ? f : -1;
+}
+
+// Boundary flux at domain face fb in face axes (Sec. 3.1.1 "Surface Fluxes", one functor per
+// boundary type): own / po the interior trace and its primitives in face axes, side = 1 when
+// the interior is the left state (upper face).  Slip wall: Riemann flux against the mirror
+// state; supersonic inflow: F(U_b); supersonic outflow: F(U-); Dirichlet: Riemann flux
+// against U_b.  The prescribed state is converted exactly as a neighbour trace is.
+template <int DIM, class R>
+__device__ __forceinline__ void boundary_flux(const InstArgs& I, int fb, int l, int side, const R* own,
+                                              const Prim<DIM, R>& po, int kind, R gamma, R igm1,
+                                              R p_ref, double gm1_64, double p_ref_64, R* Fs) {
+  constexpr int NV = DIM + 2;
+  const int type = I.bc[fb];
+  if (type == 3) {  // outflow
+    point_flux<DIM, 0>(own, po, Fs);
+    return;
+  }
+  R ext[NV];
+  Prim<DIM, R> pe;
+  if (type == 1) {  // slip wall: the mirror state
+#pragma unroll
+    for (int v = 0; v < NV; ++v) ext[v] = own[v];
+    ext[1] = -own[1];
+    pe = prims<DIM>(ext, po.pd, p_ref);
+  } else {  // inflow, Dirichlet: the prescribed state
+    double b64[NV];
+    R b0[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      b64[v] = I.bcs[fb][v];
+      b0[v] = Ar<R>::load(b64[v]);
+    }
+    double rhoe;
+    const R pd = pdev<DIM>(b64, b0, gm1_64, p_ref_64, rhoe);
+    to_face_axes<DIM>(b0, ext, l);
+    pe = prims<DIM>(ext, pd, p_ref);
+    if (type == 2) {  // inflow
+      point_flux<DIM, 0>(ext, pe, Fs);
+      return;
+    }
+  }
+  if (side) surface_flux<DIM, 0>(kind, own, po, ext, pe, gamma, igm1, p_ref, Fs);
+  else surface_flux<DIM, 0>(kind, ext, pe, own, po, gamma, igm1, p_ref, Fs);
+}
+
 constexpr int cmax(int a, int b) { return a > b ? a : b; }
 constexpr int al4(int n) { return (n + 3) & ~3; }
 
@@ -345,35 +430,43 @@ struct EulerStage {
 
   // ---- phase 3: one face node (face r.face of element r.jel) ----
   static __device__ __forceinline__ void face_job(R* sm, const double* trace, const StageArgs& A,
-                                                  const InstArgs& I, const Role& r, R gamma, R igm1,
-                                                  R p_ref) {
+                                                  const InstArgs& I, const Role& r, int e, R gamma,
+                                                  R igm1, R p_ref) {
     const int ej = r.jel, side = r.face & 1, l = r.face >> 1;
-    R own0[NV], nbr0[NV];
-    double n64[NV];
+    R own0[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      own0[v] = sm[OFF_U + (ej * NV + v) * NP + r.ndo];
-      n64[v] = trace[((ej * NF + r.face) * NV + v) * NFN + r.f];
-      nbr0[v] = Ar<R>::load(n64[v]);
-    }
-    double rhoe;
+    for (int v = 0; v < NV; ++v) own0[v] = sm[OFF_U + (ej * NV + v) * NP + r.ndo];
     const R pd_own = pd_of(sm, ej, r.ndo);
-    const R pd_nbr = pdev<DIM>(n64, nbr0, A.pd.gm1, A.pd.p_ref, rhoe);
-    R own[NV], nbr[NV];
+    R own[NV];
     to_face_axes(own0, own, l);
-    to_face_axes(nbr0, nbr, l);
     const Prim<DIM, R> po = prims<DIM>(own, pd_own, p_ref);
-    const Prim<DIM, R> pn = prims<DIM>(nbr, pd_nbr, p_ref);
-    R uL[NV], uR[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      uL[v] = side ? own[v] : nbr[v];
-      uR[v] = side ? nbr[v] : own[v];
-    }
-    const Prim<DIM, R>& a = side ? po : pn;
-    const Prim<DIM, R>& b = side ? pn : po;
     R Fs[NV];
-    surface_flux<DIM, 0>(A.surface, uL, a, uR, b, gamma, igm1, p_ref, Fs);  // the single call site
+    const int fb = I.nonper ? boundary_face(I, DIM, e, l, side) : -1;
+    if (fb >= 0) {  // a domain face with a boundary condition
+      boundary_flux<DIM, R>(I, fb, l, side, own, po, A.surface, gamma, igm1, p_ref, A.pd.gm1, A.pd.p_ref, Fs);
+    } else {
+      R nbr0[NV];
+      double n64[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        n64[v] = trace[((ej * NF + r.face) * NV + v) * NFN + r.f];
+        nbr0[v] = Ar<R>::load(n64[v]);
+      }
+      double rhoe;
+      const R pd_nbr = pdev<DIM>(n64, nbr0, A.pd.gm1, A.pd.p_ref, rhoe);
+      R nbr[NV];
+      to_face_axes(nbr0, nbr, l);
+      const Prim<DIM, R> pn = prims<DIM>(nbr, pd_nbr, p_ref);
+      R uL[NV], uR[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        uL[v] = side ? own[v] : nbr[v];
+        uR[v] = side ? nbr[v] : own[v];
+      }
+      const Prim<DIM, R>& a = side ? po : pn;
+      const Prim<DIM, R>& b = side ? pn : po;
+      surface_flux<DIM, 0>(A.surface, uL, a, uR, b, gamma, igm1, p_ref, Fs);  // the single call site
+    }
     if (!A.weak) {
       R Fo[NV];
       point_flux<DIM, 0>(own, po, Fo);
@@ -470,7 +563,7 @@ struct EulerStage {
       }
     }
     // phase 3: face jobs
-    if (t < NJS && e0 + r.jel < I.n_elem) face_job(sm, TR, A, I, r, gamma, igm1, p_ref);
+    if (t < NJS && e0 + r.jel < I.n_elem) face_job(sm, TR, A, I, r, e0 + r.jel, gamma, igm1, p_ref);
     __syncthreads();
 
     // phase 4: gather, then L or the stage update

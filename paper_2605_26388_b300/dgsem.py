@@ -25,6 +25,7 @@ VOL_STRONG, VOL_WEAK, VOL_EC = 0, 1, 2
 SURF_RUSANOV, SURF_HLLC, SURF_HLL, SURF_EC = 0, 1, 2, 3
 FP64, FP32_MIXED = 0, 1
 LAUNCH_PER_INSTANCE, LAUNCH_BATCHED = 0, 1
+BC_PERIODIC, BC_SLIP_WALL, BC_INFLOW, BC_OUTFLOW, BC_DIRICHLET = 0, 1, 2, 3, 4
 SSPRK33, SSPRK54 = 0, 1
 NEWTON_MAX_IT, NEWTON_TOL = 40, 1e-12
 MATH_EXP_TABLE, MATH_RCP_NEWTON, MATH_EXP_CUDA, MATH_RCP_CUDA = 0, 1, 2, 3
@@ -49,7 +50,8 @@ class DGError(RuntimeError):
 
 class MeshDesc(C.Structure):
     _fields_ = [("dim", C.c_int), ("N", C.c_int), ("nel", C.c_int * 3), ("lo", C.c_double * 3),
-                ("hi", C.c_double * 3), ("periodic", C.c_int * 3)]
+                ("hi", C.c_double * 3), ("periodic", C.c_int * 3), ("bc", C.c_int * 6),
+                ("bc_state", (C.c_double * 5) * 6)]
 
 
 class Mechanism(C.Structure):
@@ -151,19 +153,30 @@ def gll(N: int):
 
 @dataclass
 class Mesh:
-    """One periodic Cartesian instance."""
+    """One Cartesian instance: periodic, or with boundary conditions bc[f] (BC_*) on the
+    faces x-, x+, y-, y+, z-, z+ of a direction whose two faces are both non-periodic;
+    bc_state[f] is the prescribed conserved state of an inflow or Dirichlet face."""
     dim: int
     N: int
     nel: Sequence[int]
     lo: Sequence[float]
     hi: Sequence[float]
+    bc: Sequence[int] = (0, 0, 0, 0, 0, 0)
+    bc_state: Sequence = None
 
     def c(self) -> MeshDesc:
         nel = list(self.nel) + [1] * (3 - len(self.nel))
         lo = list(self.lo) + [0.0] * (3 - len(self.lo))
         hi = list(self.hi) + [1.0] * (3 - len(self.hi))
-        return MeshDesc(self.dim, self.N, (C.c_int * 3)(*nel), (C.c_double * 3)(*lo),
-                        (C.c_double * 3)(*hi), (C.c_int * 3)(1, 1, 1))
+        per = [1 if self.bc[2 * l] == 0 and self.bc[2 * l + 1] == 0 else 0 for l in range(3)]
+        d = MeshDesc(self.dim, self.N, (C.c_int * 3)(*nel), (C.c_double * 3)(*lo),
+                     (C.c_double * 3)(*hi), (C.c_int * 3)(*per))
+        for f in range(6):
+            d.bc[f] = int(self.bc[f])
+            if self.bc_state is not None and self.bc_state[f] is not None:
+                for v, x in enumerate(self.bc_state[f]):
+                    d.bc_state[f][v] = float(x)
+        return d
 
     @property
     def n_elem(self) -> int:

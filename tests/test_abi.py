@@ -65,8 +65,14 @@ def test_init_rejects_bad_descriptions(dg):
     bad = dg.Mesh(3, 6, (4, 4, 4), (0.0,) * 3, (1.0,) * 3).c()
     assert _init(dg, bad)[0] == dg.DG_EUNSUPPORTED
     np_ = dg.Mesh(2, 3, (4, 4), (0.0, 0.0), (1.0, 1.0)).c()
-    np_.periodic[1] = 0
-    assert _init(dg, np_)[0] == dg.DG_EUNSUPPORTED
+    np_.periodic[1] = 0  # non-periodic without boundary types
+    assert _init(dg, np_)[0] == dg.DG_EINVAL
+    np_.bc[2], np_.bc[3] = dg.BC_SLIP_WALL, 9
+    assert _init(dg, np_)[0] == dg.DG_EINVAL
+    np_.bc[3] = dg.BC_DIRICHLET  # prescribed state with rho = 0
+    assert _init(dg, np_)[0] == dg.DG_EINVAL
+    np_.periodic[1] = 2
+    assert _init(dg, np_)[0] == dg.DG_EINVAL
     assert _init(dg, m, gamma=1.0)[0] == dg.DG_EINVAL
     assert _init(dg, m, volume=7)[0] == dg.DG_EINVAL
     assert _init(dg, m, precision=3)[0] == dg.DG_EINVAL
