@@ -84,8 +84,8 @@ struct OrcProblem {
 namespace {
 
 // ---------------------------------------------------------------------------------------
-// Legendre polynomials and the Gauss-Lobatto-Legendre rule (Sec. 3.1.1: "collocated at
-// the (P+1)^d tensor-product GLL nodes with weights w_i").  Nodes are -1, +1 and the
+// Legendre polynomials and the Gauss-Lobatto-Legendre rule (Sec. 3.1.1: the solution lives
+// on the tensor-product GLL nodes, weights w_i).  Nodes are -1, +1 and the
 // roots of P_N'; weights w_i = 2 / (N (N+1) P_N(x_i)^2).  Newton iteration in long
 // double on q(x) = P_{N+1}(x) - P_{N-1}(x), which vanishes exactly at the GLL nodes.
 // ---------------------------------------------------------------------------------------
@@ -129,8 +129,8 @@ void gll_rule(int N, std::vector<long double>& x, std::vector<long double>& w) {
   }
 }
 
-// Lagrange differentiation matrix D_ij = l_j'(x_i) on the GLL nodes (Sec. 3.1.1: "the
-// one-dimensional GLL differentiation matrix D"), from barycentric weights
+// Lagrange differentiation matrix D_ij = l_j'(x_i) on the GLL nodes (Sec. 3.1.1: the 1D
+// GLL derivative matrix D), from barycentric weights
 // lambda_j = 1 / prod_{k != j} (x_j - x_k):  D_ij = (lambda_j / lambda_i) / (x_i - x_j)
 // for i != j, and the diagonal by the negative row sum (derivative of a constant is 0).
 void diff_matrix(int N, const std::vector<long double>& x, std::vector<long double>& D) {
@@ -383,7 +383,7 @@ struct Mesh {
 // functor per boundary type; Sec. 4 set-ups: enforced weakly through the numerical flux).
 // own_left: the element's own trace is the left state (upper face).  READINGS: slip wall --
 // the Riemann flux against the mirror state (normal momentum reversed); supersonic inflow --
-// "the flux evaluated directly from" the prescribed state, F^l(U_b); supersonic outflow --
+// the flux of the prescribed state itself, F^l(U_b); supersonic outflow --
 // the interior state's flux F^l(U-); free-stream Dirichlet -- the Riemann flux against U_b.
 void boundary_flux(const OrcProblem& P, int f, int l, const double* uown, bool own_left, double* F) {
   const int dim = P.dim, nv = dim + 2;
@@ -644,7 +644,8 @@ void shock_alpha(const OrcProblem& P, const double* U, double* alpha_raw, double
 // f_{i+1/2} = F*(U_i, U_{i+1}) between nodes of the element and, at the element faces, the
 // DG surface flux with the neighbour's trace (f_{-1/2} = F*(U_nbr,N, U_0),
 // f_{N+1/2} = F*(U_N, U_nbr,0)).  READING: every sub-cell interface uses the context's
-// surface flux ("matching numerical surface flux functions"; Rusanov in the paper's case).
+// surface flux (the paper asks for the same numerical flux functions as the DG surface;
+// Rusanov in its cases).
 void fv_element_residual(const OrcProblem& P, const Mesh& M, const Ops& ops, const double* U, int e,
                          double* dU) {
   const int dim = M.dim, N = M.N, nv = dim + 2;
@@ -990,8 +991,8 @@ void residual(const OrcProblem& P, const double* U, double* dU) {
   }
 }
 
-// Positivity floor (Sec. 4.1 and 4.2 set-ups: "a per-stage positivity floor enforces
-// rho >= ..., p >= ...").  READING: the paper does not say how; here rho is raised to
+// Positivity floor (Sec. 4.1 and 4.2 set-ups: lower bounds on rho and p are applied after
+// every stage).  READING: the paper does not say how; here rho is raised to
 // rho_floor (momentum kept), then E is reset so that p = p_floor where p < p_floor.
 void positivity_floor(const OrcProblem& P, double* U) {
   if (!(P.rho_floor > 0.0) && !(P.p_floor > 0.0)) return;
