@@ -79,6 +79,7 @@ class _Problem(C.Structure):
         ("mech", C.POINTER(_Mech)), ("parts", C.c_int),
         ("shock", C.c_int), ("alpha_min", C.c_double), ("alpha_max", C.c_double),
         ("sharpness", C.c_double), ("bc", C.c_int * 6), ("bc_state", (C.c_double * 5) * 6),
+        ("coords", C.POINTER(C.c_double)),
     ]
 
 
@@ -106,6 +107,7 @@ class Problem:
     sharpness: float = math.log(9999.0)
     bc: tuple = (0, 0, 0, 0, 0, 0)  # Euler: per domain face x-, x+, y-, y+, z-, z+; 0 = periodic
     bc_state: tuple = None          # per face: the exterior conserved state (INFLOW, DIRICHLET)
+    coords: np.ndarray = None       # Euler: node coordinates (dim, n_elem, n_nodes) of a curved mesh
 
     @property
     def nvars(self) -> int:
@@ -138,6 +140,9 @@ class Problem:
         p.parts = self.parts
         p.shock = 1 if self.shock else 0
         p.alpha_min, p.alpha_max, p.sharpness = self.alpha_min, self.alpha_max, self.sharpness
+        if self.coords is not None:
+            p._coords_keep = np.ascontiguousarray(self.coords, dtype=np.float64)
+            p.coords = p._coords_keep.ctypes.data_as(C.POINTER(C.c_double))
         for f in range(6):
             p.bc[f] = int(self.bc[f])
             if self.bc_state is not None and self.bc_state[f] is not None:
@@ -179,6 +184,7 @@ def lib():
         _lib.orc_shock_alpha.argtypes = [pp, dp, dp, dp]
         _lib.orc_fv_residual.argtypes = [pp, dp, dp]
         _lib.orc_modes.argtypes = [pp, dp, dp]
+        _lib.orc_metrics.argtypes = [pp, dp, dp]
         _lib.orc_ssp_table.argtypes = [C.c_int, dp, dp, ip, dp]
         _lib.orc_ssp_steps.argtypes = [pp, C.c_int, dp, C.c_double, C.c_int]
         _lib.orc_source_implicit.argtypes = [pp, dp, C.c_double, C.c_int, C.c_double, ip]
@@ -450,3 +456,15 @@ def modes(P: Problem, q) -> np.ndarray:
     c = P._c()
     _check(lib().orc_modes(C.byref(c), _ptr(q), _ptr(m)), "modes")
     return m
+
+
+def metrics(P: Problem):
+    """(Ja, J) of a curved mesh: Ja[elem, node, l, d] (the contravariant vectors, 3 x 3 per
+    node, 2D in the leading 2 x 2) and J[elem, node] (Sec. 3.1.1: 2D cross-derivative form,
+    3D conservative curl form).  Pinned by the discrete GCL, the affine case and free-stream
+    preservation."""
+    Ja = np.zeros(P.n_elem * P.n_nodes * 9)
+    J = np.zeros(P.n_elem * P.n_nodes)
+    c = P._c()
+    _check(lib().orc_metrics(C.byref(c), _ptr(Ja), _ptr(J)), "metrics")
+    return Ja.reshape(P.n_elem, P.n_nodes, 3, 3), J.reshape(P.n_elem, P.n_nodes)

@@ -77,6 +77,8 @@ struct OrcProblem {
   double alpha_min, alpha_max, sharpness;  // blending bounds and the sigmoid's steepness s
   int bc[6];                  // Euler: per domain face x-, x+, y-, y+, z-, z+ (0 = periodic)
   double bc_state[6][5];      // INFLOW / DIRICHLET: the exterior conserved state
+  const double* coords;       // Euler, periodic: node coordinates [d][elem][node] of a curved
+                              // mesh on the same element topology (null: the Cartesian box)
 };
 
 }  // extern "C"
@@ -692,6 +694,205 @@ void fv_element_residual(const OrcProblem& P, const Mesh& M, const Ops& ops, con
     for (int v = 0; v < nv; ++v) dU[((size_t)v * M.n_elem + e) * M.n_nodes + nd] = R[nd * nv + v];
 }
 
+// ---------------------------------------------------------------------------------------
+// Curvilinear elements (Sec. 3.1.1: element maps x = X(xi), Jacobian J_dm = dx_d/dxi_m,
+// J = det, contravariant vectors Ja^l satisfying the discrete GCL sum_l d_xi_l Ja^l = 0).
+// The map is the degree-N interpolant of the given node coordinates.  Metric terms:
+//   2D  Ja^1 = (y_eta, -x_eta), Ja^2 = (-y_xi, x_xi);
+//   3D  the conservative curl form Ja^i_n = -1/2 [curl_xi (X_l grad_xi X_m - X_m grad_xi X_l)]_i,
+//       (n, m, l) cyclic,
+// derivatives by D along the lines; J = x_xi y_eta - x_eta y_xi (2D) or the determinant of
+// dx/dxi (3D).  With these, d_xi-divergences of Ja^l vanish to rounding (the D's commute).
+// ---------------------------------------------------------------------------------------
+struct Metrics {
+  std::vector<double> Ja;  // [elem][node][l][d]
+  std::vector<double> J;   // [elem][node]
+};
+
+Metrics curved_metrics(const OrcProblem& P, const Mesh& M, const Ops& ops) {
+  const int dim = M.dim, n1 = M.n1, np = M.n_nodes;
+  Metrics G;
+  G.Ja.assign((size_t)M.n_elem * np * 9, 0.0);
+  G.J.assign((size_t)M.n_elem * np, 0.0);
+  auto X = [&](int d, int e, int nd) { return P.coords[((size_t)d * M.n_elem + e) * np + nd]; };
+  // derivative along reference direction k of a nodal field f at node nd
+  auto deriv = [&](const std::vector<double>& f, int k, int nd) {
+    int ijk[3];
+    M.node_coords(nd, ijk);
+    double acc = 0.0;
+    for (int m = 0; m < n1; ++m) {
+      int mk[3] = {ijk[0], ijk[1], ijk[2]};
+      mk[k] = m;
+      acc += ops.D[ijk[k] * n1 + m] * f[M.node(mk)];
+    }
+    return acc;
+  };
+  for (int e = 0; e < M.n_elem; ++e) {
+    std::vector<std::vector<double>> x(dim, std::vector<double>(np));
+    for (int d = 0; d < dim; ++d)
+      for (int nd = 0; nd < np; ++nd) x[d][nd] = X(d, e, nd);
+    // dx_d / dxi_k at every node
+    std::vector<double> dx((size_t)np * 9);
+    for (int nd = 0; nd < np; ++nd)
+      for (int d = 0; d < dim; ++d)
+        for (int k = 0; k < dim; ++k) dx[(size_t)nd * 9 + d * 3 + k] = deriv(x[d], k, nd);
+    double* Ja = &G.Ja[(size_t)e * np * 9];
+    if (dim == 2) {
+      for (int nd = 0; nd < np; ++nd) {
+        const double* g = &dx[(size_t)nd * 9];  // g[d*3+k] = dx_d/dxi_k
+        Ja[nd * 9 + 0 * 3 + 0] = g[1 * 3 + 1];   // Ja^1 = ( y_eta, -x_eta)
+        Ja[nd * 9 + 0 * 3 + 1] = -g[0 * 3 + 1];
+        Ja[nd * 9 + 1 * 3 + 0] = -g[1 * 3 + 0];  // Ja^2 = (-y_xi,  x_xi)
+        Ja[nd * 9 + 1 * 3 + 1] = g[0 * 3 + 0];
+        G.J[(size_t)e * np + nd] = g[0] * g[4] - g[1] * g[3];
+      }
+    } else {
+      for (int n = 0; n < 3; ++n) {
+        const int m = (n + 1) % 3, l = (n + 2) % 3;
+        // V_k = X_l d_k X_m - X_m d_k X_l at the nodes
+        std::vector<std::vector<double>> V(3, std::vector<double>(np));
+        for (int nd = 0; nd < np; ++nd)
+          for (int k = 0; k < 3; ++k)
+            V[k][nd] = x[l][nd] * dx[(size_t)nd * 9 + m * 3 + k] - x[m][nd] * dx[(size_t)nd * 9 + l * 3 + k];
+        for (int nd = 0; nd < np; ++nd)
+          for (int i = 0; i < 3; ++i) {
+            const int i1 = (i + 1) % 3, i2 = (i + 2) % 3;
+            const double curl = deriv(V[i2], i1, nd) - deriv(V[i1], i2, nd);
+            Ja[nd * 9 + i * 3 + n] = -0.5 * curl;
+          }
+      }
+      for (int nd = 0; nd < np; ++nd) {
+        const double* g = &dx[(size_t)nd * 9];
+        G.J[(size_t)e * np + nd] = g[0] * (g[4] * g[8] - g[5] * g[7]) - g[1] * (g[3] * g[8] - g[5] * g[6]) +
+                                   g[2] * (g[3] * g[7] - g[4] * g[6]);
+      }
+    }
+  }
+  return G;
+}
+
+// Riemann flux in the unit direction n: the states' momenta are expressed in an orthonormal
+// frame (n, t1[, t2]), the flux of direction 0 is evaluated there and its momentum rotated
+// back (rotational invariance of the Euler equations).
+void normal_frame(int dim, const double* n, double t[2][3]) {
+  if (dim == 2) {
+    t[0][0] = -n[1]; t[0][1] = n[0]; t[0][2] = 0.0;
+    return;
+  }
+  // t1: the unit vector orthogonal to n built from the axis least aligned with n
+  int a = 0;
+  if (std::fabs(n[1]) < std::fabs(n[a])) a = 1;
+  if (std::fabs(n[2]) < std::fabs(n[a])) a = 2;
+  double e[3] = {0.0, 0.0, 0.0};
+  e[a] = 1.0;
+  double c[3] = {n[1] * e[2] - n[2] * e[1], n[2] * e[0] - n[0] * e[2], n[0] * e[1] - n[1] * e[0]};
+  const double cn = std::sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+  for (int d = 0; d < 3; ++d) t[0][d] = c[d] / cn;
+  t[1][0] = n[1] * t[0][2] - n[2] * t[0][1];
+  t[1][1] = n[2] * t[0][0] - n[0] * t[0][2];
+  t[1][2] = n[0] * t[0][1] - n[1] * t[0][0];
+}
+
+void normal_riemann(int kind, int dim, const double* n, const double* uL, const double* uR, double gamma,
+                    double* F) {
+  const int nv = dim + 2;
+  double t[2][3];
+  normal_frame(dim, n, t);
+  double rL[8], rR[8], Fr[8];
+  rL[0] = uL[0];
+  rR[0] = uR[0];
+  rL[nv - 1] = uL[nv - 1];
+  rR[nv - 1] = uR[nv - 1];
+  for (int c = 0; c < dim; ++c) {
+    const double* b = c == 0 ? n : t[c - 1];
+    rL[1 + c] = 0.0;
+    rR[1 + c] = 0.0;
+    for (int d = 0; d < dim; ++d) {
+      rL[1 + c] += uL[1 + d] * b[d];
+      rR[1 + c] += uR[1 + d] * b[d];
+    }
+  }
+  surface_flux(kind, dim, 0, rL, rR, gamma, Fr);
+  F[0] = Fr[0];
+  F[nv - 1] = Fr[nv - 1];
+  for (int d = 0; d < dim; ++d) {
+    F[1 + d] = Fr[1] * n[d];
+    for (int c = 1; c < dim; ++c) F[1 + d] += Fr[1 + c] * t[c - 1][d];
+  }
+}
+
+// Residual of element e on a curved mesh (Sec. 3.1.1, Eqs. vol_weak and vol_split with the
+// metric terms; Eq. surf_int):
+//   strong:    R_i = -(1/J_i) sum_l sum_m D_{i_l m} Ja^l(m) . F(U_m)
+//   two-point: R_i = -(2/J_i) sum_l sum_m D_{i_l m} {{Ja^l}}_{im} . F#(U_i, U_m)
+//   surface:   R_i -/+ (1/(J_i w)) (|Ja^l| F*(U_L, U_R; n) - Ja^l . F(U_i)),  n = Ja^l / |Ja^l|
+// on the upper / lower face of direction l, Ja^l taken at the own face node (the neighbour's
+// is the same: it depends only on the face's nodes).
+void curved_element_residual(const OrcProblem& P, const Mesh& M, const Ops& ops, const Metrics& G,
+                             const double* U, int e, double* dU) {
+  const int dim = M.dim, n1 = M.n1, N = M.N, nv = dim + 2, np = M.n_nodes;
+  std::vector<double> R((size_t)np * nv, 0.0);
+  auto Ja = [&](int el, int nd, int l, int d) { return G.Ja[(((size_t)el * np + nd) * 3 + l) * 3 + d]; };
+  for (int nd = 0; nd < np; ++nd) {
+    int ijk[3];
+    M.node_coords(nd, ijk);
+    double ui[8], um[8], F[8];
+    load_node(M, nv, U, e, nd, ui);
+    const double iJ = 1.0 / G.J[(size_t)e * np + nd];
+    for (int l = 0; l < dim; ++l) {
+      for (int m = 0; m < n1; ++m) {
+        int mk[3] = {ijk[0], ijk[1], ijk[2]};
+        mk[l] = m;
+        const int nm = M.node(mk);
+        load_node(M, nv, U, e, nm, um);
+        const double Dim = ops.D[ijk[l] * n1 + m];
+        for (int d = 0; d < dim; ++d) {
+          if (P.volume == ORC_VOL_STRONG) {
+            euler_flux(dim, d, um, P.gamma, F);
+            for (int v = 0; v < nv; ++v) R[nd * nv + v] -= iJ * Dim * Ja(e, nm, l, d) * F[v];
+          } else {
+            ec_flux(dim, d, ui, um, P.gamma, F);
+            const double a = 0.5 * (Ja(e, nd, l, d) + Ja(e, nm, l, d));
+            for (int v = 0; v < nv; ++v) R[nd * nv + v] -= 2.0 * iJ * Dim * a * F[v];
+          }
+        }
+      }
+    }
+  }
+  for (int l = 0; l < dim; ++l) {
+    for (int nd = 0; nd < np; ++nd) {
+      int ijk[3];
+      M.node_coords(nd, ijk);
+      if (ijk[l] != 0 && ijk[l] != N) continue;
+      const double iJ = 1.0 / G.J[(size_t)e * np + nd];
+      double uown[8], unbr[8], Fs[8], Fo[8], Fd[8], n[3] = {0.0, 0.0, 0.0};
+      load_node(M, nv, U, e, nd, uown);
+      double s2 = 0.0;
+      for (int d = 0; d < dim; ++d) s2 += Ja(e, nd, l, d) * Ja(e, nd, l, d);
+      const double s = std::sqrt(s2);
+      for (int d = 0; d < dim; ++d) n[d] = Ja(e, nd, l, d) / s;
+      for (int v = 0; v < nv; ++v) Fo[v] = 0.0;
+      for (int d = 0; d < dim; ++d) {
+        euler_flux(dim, d, uown, P.gamma, Fd);
+        for (int v = 0; v < nv; ++v) Fo[v] += Ja(e, nd, l, d) * Fd[v];
+      }
+      for (int side = 0; side < 2; ++side) {
+        if (side == 1 && ijk[l] != N) continue;
+        if (side == 0 && ijk[l] != 0) continue;
+        int nk[3] = {ijk[0], ijk[1], ijk[2]};
+        nk[l] = side ? 0 : N;
+        load_node(M, nv, U, M.neighbour(e, l, side ? +1 : -1), M.node(nk), unbr);
+        if (side) normal_riemann(P.surface, dim, n, uown, unbr, P.gamma, Fs);
+        else normal_riemann(P.surface, dim, n, unbr, uown, P.gamma, Fs);
+        const double c = (side ? -1.0 : 1.0) * iJ / ops.w[side ? N : 0];
+        for (int v = 0; v < nv; ++v) R[nd * nv + v] += c * (s * Fs[v] - Fo[v]);
+      }
+    }
+  }
+  for (int nd = 0; nd < np; ++nd)
+    for (int v = 0; v < nv; ++v) dU[((size_t)v * M.n_elem + e) * M.n_nodes + nd] = R[nd * nv + v];
+}
+
 int n_vars(const OrcProblem& P) {
   return (P.equations == ORC_NS_REACTING) ? P.mech->n_species + P.dim + 1 : P.dim + 2;
 }
@@ -721,6 +922,12 @@ int check_problem(const OrcProblem& P) {
       Prim q = primitives(P.dim, P.bc_state[f], P.gamma);
       if (!(q.rho > 0.0) || !(q.p > 0.0)) return -1;
     }
+  }
+  if (P.coords) {  // curved meshes: periodic, strong or two-point volume form, no blending
+    for (int f = 0; f < 6; ++f)
+      if (P.bc[f]) return -6;
+    if (P.shock || P.rho_floor > 0.0 || P.p_floor > 0.0) return -6;
+    if (P.volume != ORC_VOL_STRONG && P.volume != ORC_VOL_EC) return -6;
   }
   if (P.shock && (P.N < 2 || !(P.alpha_min >= 0.0) || !(P.alpha_max <= 1.0) ||
                   !(P.alpha_min <= P.alpha_max) || !(P.sharpness > 0.0)))
@@ -967,6 +1174,12 @@ void residual(const OrcProblem& P, const double* U, double* dU) {
     }
 #pragma omp parallel for schedule(static)
     for (int e = 0; e < M.n_elem; ++e) reacting_element_residual(P, M, ops, U, G.data(), e, dU);
+    return;
+  }
+  if (P.coords) {  // curved mesh
+    const Metrics G = curved_metrics(P, M, ops);
+#pragma omp parallel for schedule(static)
+    for (int e = 0; e < M.n_elem; ++e) curved_element_residual(P, M, ops, G, U, e, dU);
     return;
   }
 #pragma omp parallel for schedule(static)
@@ -1227,6 +1440,12 @@ int orc_rhs_elements(const OrcProblem* P, const double* U, const int* elems, int
     for (int k = 0; k < n; ++k) reacting_element_residual(*P, M, ops, U, G.data(), elems[k], dU);
     return 0;
   }
+  if (P->coords) {
+    const Metrics G = curved_metrics(*P, M, ops);
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < n; ++k) curved_element_residual(*P, M, ops, G, U, elems[k], dU);
+    return 0;
+  }
 #pragma omp parallel for schedule(static)
   for (int k = 0; k < n; ++k) euler_element_residual(*P, M, ops, U, elems[k], dU);
   if (P->shock) {  // Eq. vol_blend on the listed elements (the coefficients need the whole mesh)
@@ -1262,10 +1481,23 @@ int orc_shock_alpha(const OrcProblem* P, const double* U, double* alpha_raw, dou
 int orc_fv_residual(const OrcProblem* P, const double* U, double* dU) {
   int rc = check_problem(*P);
   if (rc) return rc;
-  if (P->equations != ORC_EULER) return -1;
+  if (P->equations != ORC_EULER || P->coords) return -1;
   Mesh M(*P);
   Ops ops(P->N);
   for (int e = 0; e < M.n_elem; ++e) fv_element_residual(*P, M, ops, U, e, dU);
+  return 0;
+}
+
+// Metric terms of a curved mesh: Ja[elem][node][l][d] (3 x 3 per node) and J[elem][node].
+int orc_metrics(const OrcProblem* P, double* Ja, double* J) {
+  int rc = check_problem(*P);
+  if (rc) return rc;
+  if (!P->coords) return -1;
+  Mesh M(*P);
+  Ops ops(P->N);
+  const Metrics G = curved_metrics(*P, M, ops);
+  std::memcpy(Ja, G.Ja.data(), G.Ja.size() * sizeof(double));
+  std::memcpy(J, G.J.data(), G.J.size() * sizeof(double));
   return 0;
 }
 
@@ -1591,8 +1823,8 @@ int orc_rhs_jvp(const OrcProblem* P, const double* U, const double* V, double gd
                 double* dL) {
   int rc = check_problem(*P);
   if (rc) return rc;
-  // the dual-number residual has no shock capturing and periodic boundaries only
-  if (P->shock || P->bc[0] || P->bc[1] || P->bc[2] || P->bc[3] || P->bc[4] || P->bc[5]) return -6;
+  // the dual-number residual has no shock capturing, periodic boundaries and Cartesian boxes only
+  if (P->shock || P->coords || P->bc[0] || P->bc[1] || P->bc[2] || P->bc[3] || P->bc[4] || P->bc[5]) return -6;
   if ((P->volume != ORC_VOL_STRONG && P->volume != ORC_VOL_WEAK) || P->surface != ORC_SURF_RUSANOV ||
       P->equations != ORC_EULER)
     return -6;
@@ -1617,8 +1849,8 @@ int orc_rhs_vjp_brute(const OrcProblem* P, const double* U, const double* lam, d
                       double* gbar) {
   int rc = check_problem(*P);
   if (rc) return rc;
-  // the dual-number residual has no shock capturing and periodic boundaries only
-  if (P->shock || P->bc[0] || P->bc[1] || P->bc[2] || P->bc[3] || P->bc[4] || P->bc[5]) return -6;
+  // the dual-number residual has no shock capturing, periodic boundaries and Cartesian boxes only
+  if (P->shock || P->coords || P->bc[0] || P->bc[1] || P->bc[2] || P->bc[3] || P->bc[4] || P->bc[5]) return -6;
   Mesh M(*P);
   const size_t n = (size_t)n_vars(*P) * M.n_elem * M.n_nodes;
   if (n > 20000) return -1;
@@ -1647,8 +1879,8 @@ int orc_rollout_grad(const OrcProblem* P, const double* U0, const double* target
                      double dt, int n_steps, double* grad, double* ggam) {
   int rc = check_problem(*P);
   if (rc) return rc;
-  // the dual-number residual has no shock capturing and periodic boundaries only
-  if (P->shock || P->bc[0] || P->bc[1] || P->bc[2] || P->bc[3] || P->bc[4] || P->bc[5]) return -6;
+  // the dual-number residual has no shock capturing, periodic boundaries and Cartesian boxes only
+  if (P->shock || P->coords || P->bc[0] || P->bc[1] || P->bc[2] || P->bc[3] || P->bc[4] || P->bc[5]) return -6;
   if ((P->volume != ORC_VOL_STRONG && P->volume != ORC_VOL_WEAK) || P->surface != ORC_SURF_RUSANOV ||
       P->equations != ORC_EULER)
     return -6;
@@ -1721,6 +1953,19 @@ int orc_max_dt(const OrcProblem* P, const double* U, double cfl, double* dt) {
   }
   double dxmin = M.dx[0];
   for (int l = 1; l < dim; ++l) dxmin = std::fmin(dxmin, M.dx[l]);
+  if (P->coords) {
+    // READING (curved meshes): the element size in direction l is 2 J / |Ja^l| (the physical
+    // length of the reference interval; dx_l on the affine box), minimised over the nodes
+    Ops ops(P->N);
+    const Metrics G = curved_metrics(*P, M, ops);
+    dxmin = 1e300;
+    for (size_t q = 0; q < stride; ++q)
+      for (int l = 0; l < dim; ++l) {
+        double s2 = 0.0;
+        for (int d = 0; d < dim; ++d) s2 += G.Ja[(q * 3 + l) * 3 + d] * G.Ja[(q * 3 + l) * 3 + d];
+        dxmin = std::fmin(dxmin, 2.0 * G.J[q] / std::sqrt(s2));
+      }
+  }
   *dt = cfl * dxmin / ((2 * P->N + 1) * lam);
   return 0;
 }

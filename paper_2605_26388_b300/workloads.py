@@ -201,6 +201,21 @@ def batched_vortex_set(n_inst: int = 256, seed: int = 5, n_range=(8, 96), degree
     return out
 
 
+def warped_coordinates(dim: int, nel, xi: np.ndarray, lo, hi, amp: float = 0.05) -> np.ndarray:
+    """Node coordinates (dim, n_elem, n_nodes) of a curved periodic mesh on the box: the
+    Cartesian nodes displaced by amp * L_d * prod_k sin(2 pi (x_k - lo_k) / L_k) (a phase
+    per component), a periodic smooth warp of the element grid."""
+    X = node_coordinates(dim, nel, lo, hi, xi)
+    L = [hi[d] - lo[d] for d in range(dim)]
+    Y = X.copy()
+    for d in range(dim):
+        w = np.ones_like(X[0])
+        for k in range(dim):
+            w = w * np.sin(2.0 * np.pi * (X[k] - lo[k]) / L[k] + 0.3 * d * (k == d))
+        Y[d] = X[d] + amp * L[d] * w
+    return Y
+
+
 def blast_wave(dim: int, nel: int, xi: np.ndarray, p_in: float = 10.0, radius: float = 0.4,
                gamma: float = 1.4, L: float = 2.0) -> np.ndarray:
     """The shock-capturing workload: a blast in a periodic box [0, L]^dim -- gas at rest,
