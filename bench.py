@@ -252,12 +252,13 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-reacting", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
-    ap.add_argument("--only", default="both", choices=["both", "fp32", "fp64", "reacting", "split", "shock"],
+    ap.add_argument("--only", default="both", choices=["both", "fp32", "fp64", "reacting", "split", "shock", "curved"],
                     help="precision(s) to time, or only the reacting workload (profiling runs)")
     ap.add_argument("--reacting-nel", type=int, default=48,
                     help="elements per direction of the reacting workload (profiling runs)")
     ap.add_argument("--no-split", action="store_true")
     ap.add_argument("--no-shock", action="store_true")
+    ap.add_argument("--no-curved", action="store_true")
     ap.add_argument("--shock-nel", type=int, default=48,
                     help="elements per direction of the blast (shock-capturing) workload")
     ap.add_argument("--split-nel", type=int, default=32,
@@ -268,10 +269,10 @@ def main():
     if args.impl == "reference":
         run_reference(args)
         return
-    if args.only in ("reacting", "split", "shock"):
+    if args.only in ("reacting", "split", "shock", "curved"):
         import torch
         torch.cuda.set_device(dist_env()[2])
-        fn = {"reacting": run_reacting, "split": run_split, "shock": run_shock}[args.only]
+        fn = {"reacting": run_reacting, "split": run_split, "shock": run_shock, "curved": run_curved}[args.only]
         print(json.dumps({args.only: fn(args)}), flush=True)
         return
 
@@ -351,6 +352,7 @@ def main():
     reacting = None if args.no_reacting else run_reacting(args)
     split = None if args.no_split else run_split(args)
     shock = None if args.no_shock else run_shock(args)
+    curved = None if args.no_curved else run_curved(args)
     adjoint = None if args.no_adjoint else run_adjoint(args)
     fp64 = None
     if ms64:
@@ -374,6 +376,7 @@ def main():
         "reacting": reacting,
         "reacting_split": split,
         "shock": shock,
+        "curved": curved,
         "adjoint": adjoint,
     }
     print(json.dumps(line), flush=True)
@@ -619,6 +622,47 @@ def run_shock(args):
                 r["blended"]["elements_blended"] = float((al > 0).double().mean())
             S.close()
         r["overhead"] = r["blended"]["ms_per_step"] / r["unblended"]["ms_per_step"]
+        out[name] = r
+    return out
+
+
+def run_curved(args):
+    """The curved-mesh workload: the 3D Taylor-Green vortex (Ma 0.1, N = 4, EC flux
+    differencing + HLLC) on a periodically warped 32^3 mesh (node displacement 5% of the box
+    times a product of sines), SSP-RK3 at CFL 0.25, FP32-mixed and FP64, timed beside the
+    affine Cartesian kernel on the same 32^3 problem."""
+    import torch
+    from paper_2605_26388_b300 import dgsem, workloads as wl
+    nel = 32
+    x, _, _ = dgsem.gll(N)
+    lo, hi = (0.0,) * 3, (2 * math.pi,) * 3
+    X = wl.warped_coordinates(3, (nel,) * 3, x, lo, hi, 0.05)
+    U0 = wl.taylor_green_3d(nel, x, MACH, GAMMA).reshape(NV, -1)
+    U = torch.from_numpy(U0).cuda()
+    dof = nel ** 3 * NP * NV
+    steps = max(3, args.steps // 6)
+    out = {"workload": f"3D Euler TGV Ma 0.1, N=4, {nel}^3 warped periodic mesh, EC + HLLC, SSP-RK3",
+           "dof": dof, "steps": steps}
+    for name, prec in (("fp32_mixed", dgsem.FP32_MIXED), ("fp64", dgsem.FP64)):
+        r = {}
+        for key, coords in (("curved", X), ("cartesian", None)):
+            S = dgsem.Solver(dgsem.Mesh(3, N, (nel,) * 3, lo, hi, coords=coords), volume=dgsem.VOL_EC,
+                             surface=dgsem.SURF_HLLC, precision=prec, gamma=GAMMA, p_ref=P_REF)
+            S.set_state(U)
+            dt = S.max_dt(CFL)
+            S.rk_step(dt, 3)
+            S.check()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            S.rk_step(dt, steps)
+            e1.record()
+            torch.cuda.synchronize()
+            S.check()
+            ms = e0.elapsed_time(e1) / steps
+            r[key] = {"ms_per_step": ms, "value": 3 * dof / (ms * 1e-3), "unit": "DOF-updates/s"}
+            S.close()
+        r["cost_ratio"] = r["curved"]["ms_per_step"] / r["cartesian"]["ms_per_step"]
         out[name] = r
     return out
 

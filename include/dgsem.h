@@ -113,6 +113,13 @@ typedef struct {
   int bc[6];        /* DG_BC_* per face x-, x+, y-, y+, z-, z+ of a non-periodic direction */
   double bc_state[6][5];  /* DG_BC_INFLOW / DG_BC_DIRICHLET: the conserved state U_b
                            * (rho, rho u, rho v[, rho w], E) of that face, rho > 0, p > 0 */
+  const double* coords;   /* NULL: the affine box.  Else a curved mesh on the same (periodic)
+                           * element topology (Sec. 3.1.1: element maps, metric terms Ja^l with
+                           * the discrete GCL): host array of the node coordinates,
+                           * coords[d * n_elem * n_p + e * n_p + q], copied at dg_init_mesh.
+                           * DG_EULER only, all directions periodic, strong or two-point volume
+                           * form, no shock capturing, no positivity floor (else
+                           * DG_EUNSUPPORTED); every element must have J > 0 (else DG_EINVAL). */
 } dg_mesh_desc;
 
 /* Species and reactions of a reacting mixture (Sec. 2 thermochemistry, single temperature;

@@ -60,6 +60,11 @@ struct dg_ctx {
   // shock capturing (Euler): per-element blending coefficients (raw and smoothed), the list
   // of blended elements and its length, the DG-residual side buffer, per-instance element
   // offsets
+  // curved meshes: metric terms [dim*dim + 1][n_nodes_total] on the device, which instances
+  // are curved, and their smallest element size for the time-step bound
+  double* met = nullptr;
+  std::vector<char> curved;
+  std::vector<double> curved_dx;
   bool shock = false;
   double* alpha_raw = nullptr;
   double* alpha = nullptr;
@@ -292,6 +297,80 @@ void modal_inverse(int N, double* Vinv) {
   }
   for (int i = 0; i < n1; ++i)
     for (int j = 0; j < n1; ++j) Vinv[i * n1 + j] = (double)A[i][n1 + j];
+}
+
+// Metric terms of a curved instance (Sec. 3.1.1: element maps interpolating the node
+// coordinates, contravariant vectors Ja^l with the discrete GCL): 2D Ja^1 = (y_eta, -x_eta),
+// Ja^2 = (-y_xi, x_xi); 3D the conservative curl form
+// Ja^i_n = -1/2 [curl_xi (X_l grad_xi X_m - X_m grad_xi X_l)]_i, (n, m, l) cyclic; derivatives
+// by D along the lines; J the determinant of dx/dxi.  Writes met[c][base + node] (c = l*dim + d,
+// then 1/J at c = dim*dim) with the given node stride; returns false if some J <= 0, and the
+// smallest 2 J / |Ja^l| over nodes and directions in dxmin.
+bool curved_metrics_host(const dg_mesh_desc& m, double* met, long long stride, long long base,
+                         double& dxmin) {
+  const int dim = m.dim, N = m.N, n1 = N + 1;
+  const int np = dim == 2 ? n1 * n1 : n1 * n1 * n1;
+  const long long ne = n_elem_of(m);
+  double x[dg::kMaxN + 1], w[dg::kMaxN + 1], D[(dg::kMaxN + 1) * (dg::kMaxN + 1)];
+  gll_table(N, x, w, D);
+  auto pos = [&](int q, int k) { return k == 0 ? q % n1 : (k == 1 ? (q / n1) % n1 : q / (n1 * n1)); };
+  auto strd = [&](int k) { return k == 0 ? 1 : (k == 1 ? n1 : n1 * n1); };
+  auto deriv = [&](const std::vector<double>& f, int k, int q) {
+    const int i = pos(q, k), S = strd(k), b = q - i * S;
+    double acc = 0.0;
+    for (int j = 0; j < n1; ++j) acc += D[i * n1 + j] * f[b + j * S];
+    return acc;
+  };
+  dxmin = INFINITY;
+  for (long long e = 0; e < ne; ++e) {
+    std::vector<std::vector<double>> X(dim, std::vector<double>(np));
+    for (int d = 0; d < dim; ++d)
+      for (int q = 0; q < np; ++q) X[d][q] = m.coords[((size_t)d * ne + e) * np + q];
+    std::vector<double> g((size_t)np * 9, 0.0), Ja((size_t)np * 9, 0.0);  // g[q][d][k] = dx_d/dxi_k
+    for (int q = 0; q < np; ++q)
+      for (int d = 0; d < dim; ++d)
+        for (int k = 0; k < dim; ++k) g[(size_t)q * 9 + d * 3 + k] = deriv(X[d], k, q);
+    if (dim == 2) {
+      for (int q = 0; q < np; ++q) {
+        const double* G = &g[(size_t)q * 9];
+        Ja[q * 9 + 0] = G[4];   // l = 0: ( y_eta, -x_eta)
+        Ja[q * 9 + 1] = -G[1];
+        Ja[q * 9 + 3] = -G[3];  // l = 1: (-y_xi,  x_xi)
+        Ja[q * 9 + 4] = G[0];
+      }
+    } else {
+      for (int n = 0; n < 3; ++n) {
+        const int mm = (n + 1) % 3, ll = (n + 2) % 3;
+        std::vector<std::vector<double>> V(3, std::vector<double>(np));
+        for (int q = 0; q < np; ++q)
+          for (int k = 0; k < 3; ++k)
+            V[k][q] = X[ll][q] * g[(size_t)q * 9 + mm * 3 + k] - X[mm][q] * g[(size_t)q * 9 + ll * 3 + k];
+        for (int q = 0; q < np; ++q)
+          for (int i = 0; i < 3; ++i) {
+            const int i1 = (i + 1) % 3, i2 = (i + 2) % 3;
+            Ja[q * 9 + i * 3 + n] = -0.5 * (deriv(V[i2], i1, q) - deriv(V[i1], i2, q));
+          }
+      }
+    }
+    for (int q = 0; q < np; ++q) {
+      const double* G = &g[(size_t)q * 9];
+      const double J = dim == 2 ? G[0] * G[4] - G[1] * G[3]
+                                : G[0] * (G[4] * G[8] - G[5] * G[7]) - G[1] * (G[3] * G[8] - G[5] * G[6]) +
+                                      G[2] * (G[3] * G[7] - G[4] * G[6]);
+      if (!(J > 0.0)) return false;
+      const long long gi = base + e * np + q;
+      for (int l = 0; l < dim; ++l) {
+        double s2 = 0.0;
+        for (int d = 0; d < dim; ++d) {
+          met[(size_t)(l * dim + d) * stride + gi] = Ja[q * 9 + l * 3 + d];
+          s2 += Ja[q * 9 + l * 3 + d] * Ja[q * 9 + l * 3 + d];
+        }
+        dxmin = std::fmin(dxmin, 2.0 * J / std::sqrt(s2));
+      }
+      met[(size_t)dim * dim * stride + gi] = 1.0 / J;
+    }
+  }
+  return true;
 }
 
 // The kernels' view of instance i.
@@ -550,8 +629,15 @@ dg_status run_stage(dg_ctx* c, const double* U, const double* Un, double* out, i
   }
   for (size_t i = 0; i < c->inst.size(); ++i) {
     inst_args(c, (int)i, a.inst);
-    volume_operator(c, c->inst[i].N, a.Dv, nullptr);
-    cudaError_t e = dg::launch_euler_stage(c->inst[i].dim, c->inst[i].N, ec, fp32, a, s);
+    cudaError_t e;
+    if (!c->curved.empty() && c->curved[i]) {  // curved instance: plain D, metric terms
+      double x[dg::kMaxN + 1], w[dg::kMaxN + 1];
+      gll_table(c->inst[i].N, x, w, a.Dv);
+      e = dg::launch_curved(c->inst[i].dim, c->inst[i].N, ec, fp32, &a, c->met, s);
+    } else {
+      volume_operator(c, c->inst[i].N, a.Dv, nullptr);
+      e = dg::launch_euler_stage(c->inst[i].dim, c->inst[i].N, ec, fp32, a, s);
+    }
     if (e != cudaSuccess) return cuda_fail(c, e, "stage launch");
   }
   return DG_OK;
@@ -606,9 +692,11 @@ dg_status build_batch(dg_ctx* c) {
 // ---- adjoint ----
 dg_status ensure_adjoint(dg_ctx* c) {
   if (c->shock) return fail(c, DG_EUNSUPPORTED, "the adjoint has no shock capturing");
-  for (const dg_mesh_desc& m : c->inst)
+  for (const dg_mesh_desc& m : c->inst) {
+    if (m.coords) return fail(c, DG_EUNSUPPORTED, "the adjoint covers affine meshes");
     for (int l = 0; l < m.dim; ++l)
       if (m.periodic[l] != 1) return fail(c, DG_EUNSUPPORTED, "the adjoint covers periodic meshes");
+  }
   if (c->phys.volume == DG_VOL_EC || c->phys.surface != DG_SURF_RUSANOV)
     return fail(c, DG_EUNSUPPORTED, "the adjoint covers the strong/weak volume form with the Rusanov flux");
   if (c->gacc) return DG_OK;
@@ -813,6 +901,17 @@ dg_status dg_init_mesh(const dg_mesh_desc* inst, int n_inst, const dg_physics* p
   if (phys->chem_split != 0 && (phys->chem_split != 1 || phys->equations != DG_NS_REACTING))
     return DG_EINVAL;
   if (!std::isfinite(phys->newton_tol) || phys->newton_max_it > 1000) return DG_EINVAL;
+  bool any_curved = false;
+  for (int i = 0; i < n_inst; ++i) {
+    if (!inst[i].coords) continue;
+    any_curved = true;
+    if (phys->equations != DG_EULER || phys->shock || phys->rho_floor > 0.0 || phys->p_floor > 0.0 ||
+        (phys->volume != DG_VOL_STRONG && phys->volume != DG_VOL_EC) ||
+        !dg::have_curved(inst[i].dim, inst[i].N))
+      return DG_EUNSUPPORTED;
+    for (int l = 0; l < inst[i].dim; ++l)
+      if (inst[i].periodic[l] != 1) return DG_EUNSUPPORTED;
+  }
   dg_physics ph = *phys;  // with the shock-capturing defaults filled in
   if (ph.shock) {
     if (ph.shock != 1) return DG_EINVAL;
@@ -939,6 +1038,38 @@ dg_status dg_init_mesh(const dg_mesh_desc* inst, int n_inst, const dg_physics* p
       dg_free(c);
       return DG_ECUDA;
     }
+  }
+  if (any_curved) {
+    const int nm = c->dim * c->dim + 1;
+    std::vector<double> met((size_t)nm * off, 0.0);
+    c->curved.assign(n_inst, 0);
+    c->curved_dx.assign(n_inst, 0.0);
+    for (int i = 0; i < n_inst; ++i) {
+      if (!inst[i].coords) continue;
+      c->curved[i] = 1;
+      if (!curved_metrics_host(inst[i], met.data(), off, c->offs[i], c->curved_dx[i])) {
+        dg_free(c);
+        return DG_EINVAL;  // an element with J <= 0
+      }
+      if (dg::launch_curved(inst[i].dim, inst[i].N, phys->volume == DG_VOL_EC,
+                            phys->precision == DG_FP32_MIXED, nullptr, nullptr, nullptr) != cudaSuccess) {
+        cudaGetLastError();
+        dg_free(c);
+        return DG_ECUDA;
+      }
+    }
+    if (cudaMalloc(&c->met, sizeof(double) * met.size()) != cudaSuccess) {
+      cudaGetLastError();
+      dg_free(c);
+      return DG_ENOMEM;
+    }
+    if (cudaMemcpy(c->met, met.data(), sizeof(double) * met.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaGetLastError();
+      dg_free(c);
+      return DG_ECUDA;
+    }
+    *out = c;  // curved instances are launched per instance
+    return DG_OK;
   }
   if (ph.shock) {
     c->shock = true;
@@ -1125,6 +1256,8 @@ dg_status dg_set_launch(dg_ctx* c, int mode, int group_scale, int ctas_per_sm, i
     return fail(c, DG_EUNSUPPORTED, "the batched launch exists for the Euler equations");
   if (c->shock && mode == DG_LAUNCH_BATCHED)
     return fail(c, DG_EUNSUPPORTED, "shock-captured stages are launched per instance");
+  if (c->met && mode == DG_LAUNCH_BATCHED)
+    return fail(c, DG_EUNSUPPORTED, "curved instances are launched per instance");
   if (group_scale != 1 && !(group_scale == 2 && c->dim == 2))
     return fail(c, DG_EINVAL, "group_scale must be 1 (or 2 in 2D)");
   if (ctas_per_sm < 0 || (order != 0 && order != 1))
@@ -1242,6 +1375,7 @@ dg_status dg_max_dt(dg_ctx* c, double cfl, double* dt_out) {
     if (!(lam > 0.0) || !std::isfinite(lam)) return fail(c, DG_ENONFINITE, "no finite signal speed");
     double dxmin = INFINITY;
     for (int l = 0; l < m.dim; ++l) dxmin = std::fmin(dxmin, (m.hi[l] - m.lo[l]) / m.nel[l]);
+    if (!c->curved.empty() && c->curved[i]) dxmin = c->curved_dx[i];  // 2 J / |Ja^l| on curved meshes
     best = std::fmin(best, cfl * ssp_coefficient(c) * dxmin / ((2 * m.N + 1) * lam));
   }
   *dt_out = best;
@@ -1352,6 +1486,7 @@ void dg_free(dg_ctx* c) {
   if (c->gacc) cudaFree(c->gacc);
   if (c->d_mech) cudaFree(c->d_mech);
   if (c->fb) cudaFree(c->fb);
+  if (c->met) cudaFree(c->met);
   if (c->alpha_raw) cudaFree(c->alpha_raw);
   if (c->alpha) cudaFree(c->alpha);
   if (c->list) cudaFree(c->list);

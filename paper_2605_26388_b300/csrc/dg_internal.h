@@ -161,6 +161,13 @@ int batched_group(int dim, int N, int group_scale);
 // Threads per CTA and dynamic shared memory of the batched kernel.
 cudaError_t prepare_euler_stage_batched(int dim, int ec, int fp32, int group_scale);
 
+// Curved meshes: one CTA per element; met = the metric terms [DIM*DIM][nodes] (Ja^l_d at
+// index l*DIM+d) then 1/J [nodes], at the state's node stride; a->Dv holds the plain D.
+// a == null sets the kernel attributes (before the first launch, outside capture).
+bool have_curved(int dim, int N);
+cudaError_t launch_curved(int dim, int N, int ec, int fp32, const StageArgs* a, const double* met,
+                          cudaStream_t s);
+
 // Whether (dim, N) has compiled kernels.
 bool have_kernels(int dim, int N);
 

@@ -51,7 +51,7 @@ class DGError(RuntimeError):
 class MeshDesc(C.Structure):
     _fields_ = [("dim", C.c_int), ("N", C.c_int), ("nel", C.c_int * 3), ("lo", C.c_double * 3),
                 ("hi", C.c_double * 3), ("periodic", C.c_int * 3), ("bc", C.c_int * 6),
-                ("bc_state", (C.c_double * 5) * 6)]
+                ("bc_state", (C.c_double * 5) * 6), ("coords", C.POINTER(C.c_double))]
 
 
 class Mechanism(C.Structure):
@@ -163,6 +163,7 @@ class Mesh:
     hi: Sequence[float]
     bc: Sequence[int] = (0, 0, 0, 0, 0, 0)
     bc_state: Sequence = None
+    coords: np.ndarray = None  # node coordinates (dim, n_elem, n_p) of a curved mesh
 
     def c(self) -> MeshDesc:
         nel = list(self.nel) + [1] * (3 - len(self.nel))
@@ -176,6 +177,11 @@ class Mesh:
             if self.bc_state is not None and self.bc_state[f] is not None:
                 for v, x in enumerate(self.bc_state[f]):
                     d.bc_state[f][v] = float(x)
+        if self.coords is not None:
+            self._coords_c = np.ascontiguousarray(self.coords, dtype=np.float64)  # read by dg_init_mesh
+            if self._coords_c.size != self.dim * self.n_elem * self.n_nodes:
+                raise ValueError("coords must hold dim * n_elem * n_p values")
+            d.coords = self._coords_c.ctypes.data_as(C.POINTER(C.c_double))
         return d
 
     @property
