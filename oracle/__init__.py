@@ -31,6 +31,7 @@ EULER, NAVIER_STOKES, NS_REACTING = 0, 1, 2
 VOL_STRONG, VOL_WEAK, VOL_EC, VOL_CENTRAL = 0, 1, 2, 3
 SURF_RUSANOV, SURF_HLLC, SURF_HLL, SURF_EC, SURF_CENTRAL = 0, 1, 2, 3, 4
 BC_PERIODIC, BC_SLIP_WALL, BC_INFLOW, BC_OUTFLOW, BC_DIRICHLET = 0, 1, 2, 3, 4
+BC_NOSLIP_ADIABATIC, BC_NOSLIP_ISOTHERMAL = 5, 6  # NS_REACTING only
 
 
 def build(force: bool = False) -> str:
@@ -78,7 +79,7 @@ class _Problem(C.Structure):
         ("rho_floor", C.c_double), ("p_floor", C.c_double),
         ("mech", C.POINTER(_Mech)), ("parts", C.c_int),
         ("shock", C.c_int), ("alpha_min", C.c_double), ("alpha_max", C.c_double),
-        ("sharpness", C.c_double), ("bc", C.c_int * 6), ("bc_state", (C.c_double * 5) * 6),
+        ("sharpness", C.c_double), ("bc", C.c_int * 6), ("bc_state", (C.c_double * 12) * 6),
         ("coords", C.POINTER(C.c_double)),
     ]
 
@@ -105,8 +106,9 @@ class Problem:
     alpha_min: float = 0.001
     alpha_max: float = 0.5
     sharpness: float = math.log(9999.0)
-    bc: tuple = (0, 0, 0, 0, 0, 0)  # Euler: per domain face x-, x+, y-, y+, z-, z+; 0 = periodic
-    bc_state: tuple = None          # per face: the exterior conserved state (INFLOW, DIRICHLET)
+    bc: tuple = (0, 0, 0, 0, 0, 0)  # per domain face x-, x+, y-, y+, z-, z+; 0 = periodic
+    bc_state: tuple = None          # per face: the exterior conserved state (INFLOW, DIRICHLET);
+                                    # (T_wall,) for NOSLIP_ISOTHERMAL
     coords: np.ndarray = None       # Euler: node coordinates (dim, n_elem, n_nodes) of a curved mesh
 
     @property

@@ -45,7 +45,8 @@ enum { ORC_SURF_RUSANOV = 0, ORC_SURF_HLLC = 1, ORC_SURF_HLL = 2, ORC_SURF_EC = 
        ORC_SURF_CENTRAL = 4 };
 // boundary condition of a domain face (0 = periodic)
 enum { ORC_BC_PERIODIC = 0, ORC_BC_SLIP_WALL = 1, ORC_BC_INFLOW = 2, ORC_BC_OUTFLOW = 3,
-       ORC_BC_DIRICHLET = 4 };
+       ORC_BC_DIRICHLET = 4, ORC_BC_NOSLIP_ADIABATIC = 5, ORC_BC_NOSLIP_ISOTHERMAL = 6 };
+constexpr int ORC_MAX_VARS = 12;  // 8 species + 3 momenta + energy
 
 }  // namespace
 
@@ -75,8 +76,10 @@ struct OrcProblem {
   int parts;                  // ORC_NS_REACTING: 1 inviscid, 2 viscous, 4 source (0 = all)
   int shock;                  // Euler: 1 = Hennemann-Gassner DG/FV blending of the residual
   double alpha_min, alpha_max, sharpness;  // blending bounds and the sigmoid's steepness s
-  int bc[6];                  // Euler: per domain face x-, x+, y-, y+, z-, z+ (0 = periodic)
-  double bc_state[6][5];      // INFLOW / DIRICHLET: the exterior conserved state
+  int bc[6];                  // per domain face x-, x+, y-, y+, z-, z+ (0 = periodic); the
+                              // no-slip walls (5, 6) exist for ORC_NS_REACTING only
+  double bc_state[6][12];     // INFLOW / DIRICHLET: the exterior conserved state (n_vars
+                              // values); NOSLIP_ISOTHERMAL: [0] = the wall temperature
   const double* coords;       // Euler, periodic: node coordinates [d][elem][node] of a curved
                               // mesh on the same element topology (null: the Cartesian box)
 };
@@ -897,6 +900,8 @@ int n_vars(const OrcProblem& P) {
   return (P.equations == ORC_NS_REACTING) ? P.mech->n_species + P.dim + 1 : P.dim + 2;
 }
 
+int check_reacting_bc(const OrcProblem& P);
+
 int check_problem(const OrcProblem& P) {
   if (P.dim != 2 && P.dim != 3) return -1;
   if (P.N < 1 || P.N > 15) return -1;
@@ -909,14 +914,12 @@ int check_problem(const OrcProblem& P) {
     if (P.volume != ORC_VOL_STRONG || P.surface != ORC_SURF_RUSANOV) return -6;
     if (P.rho_floor > 0.0 || P.p_floor > 0.0) return -6;
     if (P.mu < 0.0 || !(P.prandtl > 0.0)) return -1;
-    if (P.shock) return -6;
-    for (int f = 0; f < 6; ++f)
-      if (P.bc[f] != ORC_BC_PERIODIC) return -6;
-    return 0;
+    if (P.shock || P.coords) return -6;
+    return check_reacting_bc(P);
   }
   if (P.equations != ORC_EULER) return -6;
   for (int f = 0; f < 2 * P.dim; ++f) {
-    if (P.bc[f] < ORC_BC_PERIODIC || P.bc[f] > ORC_BC_DIRICHLET) return -1;
+    if (P.bc[f] < ORC_BC_PERIODIC || P.bc[f] > ORC_BC_DIRICHLET) return -1;  // no viscosity: no no-slip
     if ((P.bc[f] == ORC_BC_PERIODIC) != (P.bc[f ^ 1] == ORC_BC_PERIODIC)) return -1;  // pairs
     if (P.bc[f] == ORC_BC_INFLOW || P.bc[f] == ORC_BC_DIRICHLET) {
       Prim q = primitives(P.dim, P.bc_state[f], P.gamma);
@@ -1029,9 +1032,135 @@ void chem_source(const OrcProblem& P, const double* u, double* S) {
   species_rates(*P.mech, u, q.T, S);
 }
 
+// ---------------------------------------------------------------------------------------
+// Boundary conditions of the reacting Navier-Stokes system (Sec. 3.1.1 boundary functors for
+// the inviscid flux; Sec. 3.1.2 "BR1 Gradient" boundary kernels for the viscous part; the
+// set-up of Sec. 4's wing case: a wall is a slip wall for the inviscid flux and a no-slip
+// wall for the viscous terms; every condition acts weakly, through the numerical fluxes).
+// ---------------------------------------------------------------------------------------
+int check_reacting_bc(const OrcProblem& P) {
+  const int nv = n_vars(P);
+  for (int f = 0; f < 2 * P.dim; ++f) {
+    if (P.bc[f] < ORC_BC_PERIODIC || P.bc[f] > ORC_BC_NOSLIP_ISOTHERMAL) return -1;
+    if ((P.bc[f] == ORC_BC_PERIODIC) != (P.bc[f ^ 1] == ORC_BC_PERIODIC)) return -1;  // pairs
+    if (P.bc[f] == ORC_BC_INFLOW || P.bc[f] == ORC_BC_DIRICHLET) {
+      for (int v = 0; v < nv; ++v)
+        if (!std::isfinite(P.bc_state[f][v])) return -1;
+      Mix q = mixture(P, P.bc_state[f]);
+      if (!(q.rho > 0.0) || !(q.T > 0.0)) return -1;
+    }
+    if (P.bc[f] == ORC_BC_NOSLIP_ISOTHERMAL &&
+        !(P.bc_state[f][0] > 0.0 && std::isfinite(P.bc_state[f][0])))
+      return -1;
+  }
+  return 0;
+}
+
+// Inviscid flux F* in direction l at domain face f of the reacting system; own_left: the
+// element's trace is the left state (upper face).  Every wall (slip or no-slip) is the slip
+// wall here: the Rusanov flux against the mirror state (normal momentum reversed, species
+// densities and energy kept); supersonic inflow: F^l(U_b); supersonic outflow: F^l(U-);
+// Dirichlet: the Rusanov flux against U_b.
+void mix_boundary_flux(const OrcProblem& P, int f, int l, const double* uown, bool own_left,
+                       double* F) {
+  const int ns = P.mech->n_species, nv = n_vars(P);
+  double ub[16];
+  switch (P.bc[f]) {
+    case ORC_BC_INFLOW:
+      mix_flux(P, l, P.bc_state[f], F);
+      return;
+    case ORC_BC_OUTFLOW:
+      mix_flux(P, l, uown, F);
+      return;
+    case ORC_BC_DIRICHLET:
+      for (int v = 0; v < nv; ++v) ub[v] = P.bc_state[f][v];
+      break;
+    default:  // slip and no-slip walls
+      for (int v = 0; v < nv; ++v) ub[v] = uown[v];
+      ub[ns + l] = -uown[ns + l];
+      break;
+  }
+  if (own_left) mix_rusanov(P, l, uown, ub, F);
+  else mix_rusanov(P, l, ub, uown, F);
+}
+
+// BR1 trace W^ of W = (u, v, w, T) at domain face f with normal axis l, from the element's
+// own trace Wo (Sec. 3.1.2: at a no-slip adiabatic wall the velocity is zero and (rho, T)
+// come from the interior; an isothermal wall also fixes T; a slip wall mirrors the velocity
+// across the wall).  READINGS: the trace is the boundary's value of W itself; at a slip
+// wall, the BR1 average of the interior trace and its mirror image (normal velocity 0,
+// tangential velocity and T kept); inflow and Dirichlet: W of the prescribed state (the
+// far-field Dirichlet condition); outflow: the interior trace (no gradient lift).
+void wall_trace(const OrcProblem& P, int f, int l, const double* Wo, double* Wh) {
+  switch (P.bc[f]) {
+    case ORC_BC_SLIP_WALL: {
+      double Wm[4] = {Wo[0], Wo[1], Wo[2], Wo[3]};
+      Wm[l] = -Wo[l];
+      for (int q = 0; q < 4; ++q) Wh[q] = 0.5 * (Wo[q] + Wm[q]);
+      return;
+    }
+    case ORC_BC_NOSLIP_ADIABATIC:
+      Wh[0] = Wh[1] = Wh[2] = 0.0;
+      Wh[3] = Wo[3];
+      return;
+    case ORC_BC_NOSLIP_ISOTHERMAL:
+      Wh[0] = Wh[1] = Wh[2] = 0.0;
+      Wh[3] = P.bc_state[f][0];
+      return;
+    case ORC_BC_OUTFLOW:
+      for (int q = 0; q < 4; ++q) Wh[q] = Wo[q];
+      return;
+    default: {  // inflow, Dirichlet
+      Mix b = mixture(P, P.bc_state[f]);
+      Wh[0] = b.v[0];
+      Wh[1] = b.v[1];
+      Wh[2] = b.v[2];
+      Wh[3] = b.T;
+    }
+  }
+}
+
+void viscous_flux(const OrcProblem& P, int l, const double* u, const double* g, double* F);
+
+// Viscous numerical flux (F_v^l)* at domain face f with normal axis l, from the element's own
+// node u and its gradient g (Sec. 3.1.2 boundary kernels: the viscous operator of a wall
+// enforces no slip and, adiabatic, no heat flux).  READINGS: slip wall: the BR1 average of
+// the interior flux and its mirror image -- the normal-momentum row (tau_ll) kept, the
+// tangential rows and the energy row 0; no-slip adiabatic wall: the interior stress rows,
+// energy 0 (a wall at rest does no work and passes no heat); no-slip isothermal wall: the
+// interior stress rows, energy k dT/dx_l (heat conducted through the wall, no work); inflow,
+// outflow, Dirichlet: the interior flux (no viscous lift).
+void viscous_boundary_flux(const OrcProblem& P, int f, int l, const double* u, const double* g,
+                           double* F) {
+  const int ns = P.mech->n_species, dim = P.dim, nv = n_vars(P);
+  double Fo[16];
+  viscous_flux(P, l, u, g, Fo);
+  for (int v = 0; v < nv; ++v) F[v] = Fo[v];
+  switch (P.bc[f]) {
+    case ORC_BC_SLIP_WALL: {
+      double Fm[16];
+      for (int v = 0; v < nv; ++v) Fm[v] = -Fo[v];
+      Fm[ns + l] = Fo[ns + l];
+      for (int v = 0; v < nv; ++v) F[v] = 0.5 * (Fo[v] + Fm[v]);
+      return;
+    }
+    case ORC_BC_NOSLIP_ADIABATIC:
+      F[ns + dim] = 0.0;
+      return;
+    case ORC_BC_NOSLIP_ISOTHERMAL: {
+      Mix q = mixture(P, u);
+      F[ns + dim] = P.mu * q.cp / P.prandtl * g[3 * 3 + l];
+      return;
+    }
+    default:
+      return;
+  }
+}
+
 // BR1 gradient (Sec. 3.1.2 Eq. br1_avg; App. A "Viscous Volume and Interface Fluxes") of
 // W = (u, v, w, T) on element e: S_l = (2/dx_l) [D W + (upper face) (W^ - W_N)/w_N
-// - (lower face) (W^ - W_0)/w_0], W^ = (W_L + W_R)/2.  Layout G[(node * 4 + q) * 3 + l].
+// - (lower face) (W^ - W_0)/w_0], W^ = (W_L + W_R)/2 (at a domain face: wall_trace).
+// Layout G[(node * 4 + q) * 3 + l].
 void br1_gradient(const OrcProblem& P, const Mesh& M, const Ops& ops, const double* U, int e,
                   double* G) {
   const int dim = M.dim, n1 = M.n1, N = M.N, nv = n_vars(P);
@@ -1055,19 +1184,31 @@ void br1_gradient(const OrcProblem& P, const Mesh& M, const Ops& ops, const doub
         prim(e, M.node(mk), Wm);
         for (int q = 0; q < 4; ++q) acc[q] += ops.D[ijk[l] * n1 + m] * Wm[q];
       }
-      double Wo[4], Wn[4];
+      double Wo[4], Wn[4], Wh[4];
       prim(e, nd, Wo);
       if (ijk[l] == N) {
-        int nk[3] = {ijk[0], ijk[1], ijk[2]};
-        nk[l] = 0;
-        prim(M.neighbour(e, l, +1), M.node(nk), Wn);
-        for (int q = 0; q < 4; ++q) acc[q] += (0.5 * (Wo[q] + Wn[q]) - Wo[q]) / ops.w[N];
+        const int fb = boundary_face(P, M, e, l, 1);
+        if (fb >= 0) {
+          wall_trace(P, fb, l, Wo, Wh);
+        } else {
+          int nk[3] = {ijk[0], ijk[1], ijk[2]};
+          nk[l] = 0;
+          prim(M.neighbour(e, l, +1), M.node(nk), Wn);
+          for (int q = 0; q < 4; ++q) Wh[q] = 0.5 * (Wo[q] + Wn[q]);
+        }
+        for (int q = 0; q < 4; ++q) acc[q] += (Wh[q] - Wo[q]) / ops.w[N];
       }
       if (ijk[l] == 0) {
-        int nk[3] = {ijk[0], ijk[1], ijk[2]};
-        nk[l] = N;
-        prim(M.neighbour(e, l, -1), M.node(nk), Wn);
-        for (int q = 0; q < 4; ++q) acc[q] -= (0.5 * (Wn[q] + Wo[q]) - Wo[q]) / ops.w[0];
+        const int fb = boundary_face(P, M, e, l, 0);
+        if (fb >= 0) {
+          wall_trace(P, fb, l, Wo, Wh);
+        } else {
+          int nk[3] = {ijk[0], ijk[1], ijk[2]};
+          nk[l] = N;
+          prim(M.neighbour(e, l, -1), M.node(nk), Wn);
+          for (int q = 0; q < 4; ++q) Wh[q] = 0.5 * (Wn[q] + Wo[q]);
+        }
+        for (int q = 0; q < 4; ++q) acc[q] -= (Wh[q] - Wo[q]) / ops.w[0];
       }
       for (int q = 0; q < 4; ++q) G[((size_t)(e * M.n_nodes + nd) * 4 + q) * 3 + l] = s * acc[q];
     }
@@ -1133,20 +1274,26 @@ void reacting_element_residual(const OrcProblem& P, const Mesh& M, const Ops& op
         if ((side == 1 && ijk[l] != N) || (side == 0 && ijk[l] != 0)) continue;
         int nk[3] = {ijk[0], ijk[1], ijk[2]};
         nk[l] = side ? 0 : N;
+        const int fb = boundary_face(P, M, e, l, side);
         const int en = M.neighbour(e, l, side ? +1 : -1), nn = M.node(nk);
         load_node(M, nv, U, en, nn, unbr);
         const double lift = s / ops.w[side ? N : 0];
         if (parts & 1) {
-          if (side) mix_rusanov(P, l, uown, unbr, Fs);
+          if (fb >= 0) mix_boundary_flux(P, fb, l, uown, side == 1, Fs);
+          else if (side) mix_rusanov(P, l, uown, unbr, Fs);
           else mix_rusanov(P, l, unbr, uown, Fs);
           mix_flux(P, l, uown, Fo);
           for (int v = 0; v < nv; ++v) R[nd * nv + v] += (side ? -lift : lift) * (Fs[v] - Fo[v]);
         }
         if (parts & 2) {  // BR1 central viscous flux (Eq. br1_flux)
           viscous_flux(P, l, uown, grad(e, nd), Fvo);
-          viscous_flux(P, l, unbr, grad(en, nn), Fvn);
-          for (int v = 0; v < nv; ++v)
-            R[nd * nv + v] += (side ? lift : -lift) * (0.5 * (Fvo[v] + Fvn[v]) - Fvo[v]);
+          if (fb >= 0) {
+            viscous_boundary_flux(P, fb, l, uown, grad(e, nd), Fs);
+          } else {
+            viscous_flux(P, l, unbr, grad(en, nn), Fvn);
+            for (int v = 0; v < nv; ++v) Fs[v] = 0.5 * (Fvo[v] + Fvn[v]);
+          }
+          for (int v = 0; v < nv; ++v) R[nd * nv + v] += (side ? lift : -lift) * (Fs[v] - Fvo[v]);
         }
       }
     }
