@@ -451,8 +451,8 @@ def run_reacting(args):
     dt = 1e-13
     steps = max(3, args.steps // 10)
 
-    def timed(precision):
-        S = dgsem.Solver(dgsem.Mesh(3, n_deg, (nel,) * 3, (0.0,) * 3, (2 * math.pi,) * 3),
+    def timed(precision, bc=(0,) * 6, bc_state=None):
+        S = dgsem.Solver(dgsem.Mesh(3, n_deg, (nel,) * 3, (0.0,) * 3, (2 * math.pi,) * 3, bc=bc, bc_state=bc_state),
                          equations=dgsem.DG_NS_REACTING, mu=mu, prandtl=0.72, mechanism=mech,
                          precision=precision, p_ref=101325.0 if precision == dgsem.FP32_MIXED else 0.0)
         S.set_state(U)
@@ -471,6 +471,11 @@ def run_reacting(args):
 
     ms, dof = timed(dgsem.FP64)
     ms32, _ = timed(dgsem.FP32_MIXED)
+    # the same workload in a closed box: slip, no-slip adiabatic and isothermal walls
+    walls = (dgsem.BC_SLIP_WALL, dgsem.BC_NOSLIP_ISOTHERMAL, dgsem.BC_NOSLIP_ADIABATIC,
+             dgsem.BC_NOSLIP_ADIABATIC, dgsem.BC_NOSLIP_ISOTHERMAL, dgsem.BC_SLIP_WALL)
+    wall_T = (None, (6200.0,), None, None, (4300.0,), None)
+    msw, _ = timed(dgsem.FP64, walls, wall_T)
     state_bytes = dof * 8
     alg = (16 + 24 + 24) / 3.0 * dof  # stage update bytes per average stage, as for Euler
     peak, kind = measured_peaks()
@@ -484,7 +489,11 @@ def run_reacting(args):
             "state_gb": state_bytes / 1e9,
             "fp32_mixed": {"ms_per_step": ms32, "value": 3 * dof / (ms32 * 1e-3), "unit": "DOF-updates/s",
                            "note": "fluxes, gradients, viscous terms in FP32 (momentum flux shifted by "
-                                   "p_ref = 101325 Pa); mixture state, Arrhenius source, update FP64"}}
+                                   "p_ref = 101325 Pa); mixture state, Arrhenius source, update FP64"},
+            "closed_box": {"ms_per_step": msw, "value": 3 * dof / (msw * 1e-3), "unit": "DOF-updates/s",
+                           "cost_ratio": msw / ms,
+                           "note": "FP64; x: slip / isothermal 6200 K, y: no-slip adiabatic, z: isothermal "
+                                   "4300 K / slip (boundary functors in the BR1 pass and the stage)"}}
 
 
 def run_split(args):

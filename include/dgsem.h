@@ -1,8 +1,9 @@
 /* dgsem.h -- C-ABI of the B300 (sm_103a) DGSEM residual and SSP-RK stage library.
  *
  * The library evaluates the semi-discrete DGSEM residual of the compressible Euler
- * equations, and of the single-temperature reacting Navier-Stokes equations, on periodic
- * Cartesian meshes and advances it with the SSP-RK33 or SSP-RK54 scheme, entirely in
+ * equations, and of the single-temperature reacting Navier-Stokes equations, on Cartesian
+ * meshes (periodic, or with per-face boundary conditions; Euler also on curved periodic
+ * meshes) and advances it with the SSP-RK33 or SSP-RK54 scheme, entirely in
  * hand-written CUDA kernels (one fused kernel per RK stage for Euler; a BR1 gradient pass
  * plus one fused kernel for Navier-Stokes; one per-node kernel for the implicit chemistry
  * substep of the Strang split).  The operations follow arXiv 2605.26388:
@@ -65,8 +66,9 @@ typedef enum {
 
 /* Equations.  DG_NAVIER_STOKES is the single-gas, non-dimensional case (R = 1, so T = p/rho,
  * cv = 1/(gamma-1), conductivity k = gamma mu / ((gamma-1) Pr)); DG_NS_REACTING takes its
- * species and reactions from dg_physics.chem (SI units).  Both: 3D, strong volume form,
- * Rusanov surface flux, FP64, no positivity floor; others return DG_EUNSUPPORTED. */
+ * species and reactions from dg_physics.chem (SI units).  Both: 3D, Cartesian, strong volume
+ * form, Rusanov surface flux, no positivity floor, no shock capturing; others return
+ * DG_EUNSUPPORTED. */
 enum { DG_EULER = 0, DG_NAVIER_STOKES = 1, DG_NS_REACTING = 2 };
 /* Volume term: strong form (Eq. vol_weak), weak form (integrated by parts; equal to the
  * strong form by SBP), or two-point flux differencing with Ranocha's EC flux
@@ -93,12 +95,28 @@ enum { DG_SSPRK33 = 0, DG_SSPRK54 = 1 };
 #define DG_NEWTON_TOL 1e-12
 
 /* Boundary conditions of a non-periodic domain face (Sec. 3.1.1 "Surface Fluxes": one
- * functor per boundary type; enforced weakly through the numerical flux, Sec. 4 set-ups):
+ * functor per boundary type; enforced weakly through the numerical flux, Sec. 4 set-ups).
+ * Inviscid flux:
  *   DG_BC_SLIP_WALL  the Riemann flux against the mirror state (normal momentum reversed);
  *   DG_BC_INFLOW     supersonic inflow: the flux F^l(U_b) of the prescribed state;
  *   DG_BC_OUTFLOW    supersonic outflow: the flux F^l(U-) of the interior state;
- *   DG_BC_DIRICHLET  free stream: the Riemann flux against the prescribed state U_b. */
-enum { DG_BC_SLIP_WALL = 1, DG_BC_INFLOW = 2, DG_BC_OUTFLOW = 3, DG_BC_DIRICHLET = 4 };
+ *   DG_BC_DIRICHLET  free stream: the Riemann flux against the prescribed state U_b;
+ *   DG_BC_NOSLIP_*   as DG_BC_SLIP_WALL (Sec. 4: walls are slip walls for the inviscid flux).
+ * Viscous terms (DG_NAVIER_STOKES, DG_NS_REACTING; Sec. 3.1.2 boundary kernels), the BR1
+ * trace of (u, v, w, T) and the viscous numerical flux (F_v^l)* at the face:
+ *   DG_BC_SLIP_WALL           trace: velocity with its normal part removed, T inherited;
+ *                             flux: the normal-stress row tau_ll only (no shear, no heat);
+ *   DG_BC_NOSLIP_ADIABATIC    trace: velocity 0, T inherited; flux: the interior stress
+ *                             rows, energy 0 (no work, no heat through the wall);
+ *   DG_BC_NOSLIP_ISOTHERMAL   trace: velocity 0, T = T_wall; flux: the interior stress rows,
+ *                             energy k dT/dx_l (conduction through the wall, no work);
+ *   DG_BC_INFLOW, DG_BC_DIRICHLET  trace: (u, v, w, T) of U_b; flux: the interior flux;
+ *   DG_BC_OUTFLOW             trace and flux: the interior ones (no viscous lift).
+ * The no-slip walls need viscous equations (DG_EULER: DG_EINVAL). */
+enum { DG_BC_SLIP_WALL = 1, DG_BC_INFLOW = 2, DG_BC_OUTFLOW = 3, DG_BC_DIRICHLET = 4,
+       DG_BC_NOSLIP_ADIABATIC = 5, DG_BC_NOSLIP_ISOTHERMAL = 6 };
+/* Conserved variables of one node at most: 8 species, 3 momenta, energy. */
+#define DG_MAX_VARS 12
 
 /* One Cartesian mesh instance (Sec. 3.1.1: element-wise affine map of the reference cube;
  * collocation on (N+1)^dim GLL nodes). */
@@ -109,10 +127,15 @@ typedef struct {
   double lo[3];     /* box lower corner */
   double hi[3];     /* box upper corner */
   int periodic[3];  /* 1: periodic in that direction; 0: the faces bc[2l] (lower) and bc[2l+1]
-                     * (upper) carry boundary conditions (DG_EULER only, else DG_EUNSUPPORTED) */
+                     * (upper) carry boundary conditions */
   int bc[6];        /* DG_BC_* per face x-, x+, y-, y+, z-, z+ of a non-periodic direction */
-  double bc_state[6][5];  /* DG_BC_INFLOW / DG_BC_DIRICHLET: the conserved state U_b
-                           * (rho, rho u, rho v[, rho w], E) of that face, rho > 0, p > 0 */
+  double bc_state[6][DG_MAX_VARS];  /* DG_BC_INFLOW / DG_BC_DIRICHLET: the conserved state U_b
+                           * of that face in the state's variable order -- (rho, rho u, rho v
+                           * [, rho w], E) for DG_EULER, (rho_1..rho_ns, rho u, rho v, rho w, E)
+                           * for the viscous equations -- with rho > 0 and p > 0 (Euler) or
+                           * T > 0 (viscous); DG_BC_NOSLIP_ISOTHERMAL: bc_state[f][0] = T_wall
+                           * > 0 (the non-dimensional T = p/rho for DG_NAVIER_STOKES, K for
+                           * DG_NS_REACTING).  Else DG_EINVAL. */
   const double* coords;   /* NULL: the affine box.  Else a curved mesh on the same (periodic)
                            * element topology (Sec. 3.1.1: element maps, metric terms Ja^l with
                            * the discrete GCL): host array of the node coordinates,
@@ -182,8 +205,10 @@ typedef struct {
 /* Build a context for n_inst instances (all of the same dim) sharing one physics
  * description.  Allocates the context-held state and stage buffers on the current CUDA
  * device.  `cuda_stream` is a cudaStream_t (NULL = legacy default stream).
- * Returns DG_EINVAL on a bad description, DG_EUNSUPPORTED on non-periodic meshes or an
- * unsupported (dim, N), DG_ENOMEM if allocation fails.  *out is NULL on failure. */
+ * Returns DG_EINVAL on a bad description (including a boundary type the equations do not
+ * have or a bad boundary state), DG_EUNSUPPORTED on an unsupported combination (dim, N,
+ * options; boundary conditions with the batched launch, curved meshes or the adjoint),
+ * DG_ENOMEM if allocation fails.  *out is NULL on failure. */
 DG_API dg_status dg_init_mesh(const dg_mesh_desc* inst, int n_inst, const dg_physics* phys,
                        void* cuda_stream, dg_ctx** out);
 

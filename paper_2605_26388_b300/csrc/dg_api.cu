@@ -51,6 +51,7 @@ struct dg_ctx {
   dg::MechDev* d_mech = nullptr;
   double* fb = nullptr;
   std::vector<long long> fb_offs;
+  std::vector<dg::ReactBC> rbc;      // boundary conditions per instance (viscous equations)
   // primitive caches of the state buffers (slot 3 with SSP-RK54) and a scratch one (slot 4)
   // (flux-type rows, then the FP64 temperature), and whether each cache matches its
   // buffer's current contents
@@ -146,7 +147,8 @@ void gll_table(int N, double* x, double* w, double* D) {
   }
 }
 
-dg_status check_desc(const dg_mesh_desc& m, int dim0, std::string& why) {
+dg_status check_desc(const dg_mesh_desc& m, int dim0, int equations, std::string& why) {
+  const bool viscous = equations != DG_EULER;
   if (m.dim != 2 && m.dim != 3) { why = "dim must be 2 or 3"; return DG_EINVAL; }
   if (m.dim != dim0) { why = "all instances must have the same dim"; return DG_EINVAL; }
   if (m.N < 1) { why = "N must be >= 1"; return DG_EINVAL; }
@@ -158,7 +160,16 @@ dg_status check_desc(const dg_mesh_desc& m, int dim0, std::string& why) {
     if (m.periodic[l] == 1) continue;
     for (int side = 0; side < 2; ++side) {
       const int f = 2 * l + side;
-      if (m.bc[f] < DG_BC_SLIP_WALL || m.bc[f] > DG_BC_DIRICHLET) { why = "bad boundary type"; return DG_EINVAL; }
+      const int top = viscous ? DG_BC_NOSLIP_ISOTHERMAL : DG_BC_DIRICHLET;
+      if (m.bc[f] < DG_BC_SLIP_WALL || m.bc[f] > top) { why = "bad boundary type"; return DG_EINVAL; }
+      if (viscous) {  // the prescribed states are checked against the mixture later
+        if (m.bc[f] == DG_BC_NOSLIP_ISOTHERMAL &&
+            !(m.bc_state[f][0] > 0.0 && std::isfinite(m.bc_state[f][0]))) {
+          why = "the wall temperature must be > 0";
+          return DG_EINVAL;
+        }
+        continue;
+      }
       if (m.bc[f] == DG_BC_INFLOW || m.bc[f] == DG_BC_DIRICHLET) {
         const double* b = m.bc_state[f];
         double m2 = 0.0;
@@ -373,6 +384,57 @@ bool curved_metrics_host(const dg_mesh_desc& m, double* met, long long stride, l
   return true;
 }
 
+// The kernels' copy of instance m's boundary conditions for the viscous equations: the
+// prescribed states of inflow and Dirichlet faces with their (u, v, w, T, p - p_ref, a) from
+// the mixture of `mech` (the kernels' closure), the wall temperature of isothermal walls.
+// False (why set) when a prescribed state is not finite or has rho <= 0 or T <= 0.
+bool react_bc(const dg_mesh_desc& m, const dg::MechDev& mech, double p_ref, dg::ReactBC& b,
+              std::string& why) {
+  std::memset(&b, 0, sizeof(b));
+  const int ns = mech.ns;
+  for (int l = 0; l < 3; ++l) {
+    if (m.periodic[l] == 1) continue;
+    b.nonper = 1;
+    for (int side = 0; side < 2; ++side) {
+      const int f = 2 * l + side;
+      b.bc[f] = m.bc[f];
+      if (m.bc[f] == DG_BC_NOSLIP_ISOTHERMAL) b.bcw[f][3] = m.bc_state[f][0];
+      if (m.bc[f] != DG_BC_INFLOW && m.bc[f] != DG_BC_DIRICHLET) continue;
+      const double* u = m.bc_state[f];
+      bool ok = true;
+      for (int v = 0; v < ns + 4; ++v) {
+        b.bcu[f][v] = u[v];
+        ok = ok && std::isfinite(u[v]);
+      }
+      double rho = 0.0, rR = 0.0, rcv = 0.0, rh0 = 0.0;
+      for (int s = 0; s < ns; ++s) {
+        rho += u[s];
+        rR += u[s] * mech.R[s];
+        rcv += u[s] * mech.cv[s];
+        rh0 += u[s] * mech.h0[s];
+      }
+      ok = ok && rho > 0.0 && rcv > 0.0;
+      if (ok) {
+        double kin = 0.0;
+        for (int d = 0; d < 3; ++d) {
+          b.bcw[f][d] = u[ns + d] / rho;
+          kin += u[ns + d] * b.bcw[f][d];
+        }
+        const double T = (u[ns + 3] - 0.5 * kin - rh0) / rcv, p = rR * T;
+        ok = T > 0.0 && std::isfinite(T);
+        b.bcw[f][3] = T;
+        b.bcw[f][4] = p - p_ref;
+        b.bcw[f][5] = std::sqrt((1.0 + rR / rcv) * p / rho);
+      }
+      if (!ok) {
+        why = "boundary state must be finite with rho > 0 and T > 0";
+        return false;
+      }
+    }
+  }
+  return true;
+}
+
 // The kernels' view of instance i.
 void inst_args(const dg_ctx* c, int i, dg::InstArgs& I) {
   const dg_mesh_desc& m = c->inst[i];
@@ -522,6 +584,7 @@ dg_status run_stage_ns(dg_ctx* c, const double* U, const double* Un, double* out
     const dg_mesh_desc& m = c->inst[i];
     a.base = c->offs[i];
     a.fb = c->fb + c->fb_offs[i];
+    a.bnd = c->rbc[i];
     for (int l = 0; l < 3; ++l) {
       a.nel[l] = m.nel[l];
       a.s[l] = 2.0 / ((m.hi[l] - m.lo[l]) / m.nel[l]);
@@ -888,7 +951,7 @@ dg_status dg_init_mesh(const dg_mesh_desc* inst, int n_inst, const dg_physics* p
   if (!inst || n_inst < 1 || !phys) return DG_EINVAL;
   std::string why;
   for (int i = 0; i < n_inst; ++i) {
-    dg_status s = check_desc(inst[i], inst[0].dim, why);
+    dg_status s = check_desc(inst[i], inst[0].dim, phys->equations, why);
     if (s) return s;
   }
   if (phys->equations < DG_EULER || phys->equations > DG_NS_REACTING) return DG_EINVAL;
@@ -927,6 +990,7 @@ dg_status dg_init_mesh(const dg_mesh_desc* inst, int n_inst, const dg_physics* p
   }
   const bool navier_stokes = phys->equations != DG_EULER;
   dg::MechDev mech;
+  std::vector<dg::ReactBC> rbc;
   if (navier_stokes) {
     if (!(phys->mu >= 0.0) || !std::isfinite(phys->mu) || !(phys->prandtl > 0.0) ||
         !std::isfinite(phys->prandtl))
@@ -946,11 +1010,11 @@ dg_status dg_init_mesh(const dg_mesh_desc* inst, int n_inst, const dg_physics* p
       if (st) return st;
     }
     if (inst[0].dim != 3) return DG_EUNSUPPORTED;
-    for (int i = 0; i < n_inst; ++i) {
+    for (int i = 0; i < n_inst; ++i)
       if (!dg::have_reacting(inst[i].N, mech.ns)) return DG_EUNSUPPORTED;
-      for (int l = 0; l < 3; ++l)
-        if (inst[i].periodic[l] != 1) return DG_EUNSUPPORTED;  // boundary kernels: Euler only
-    }
+    rbc.resize(n_inst);
+    for (int i = 0; i < n_inst; ++i)
+      if (!react_bc(inst[i], mech, phys->p_ref, rbc[i], why)) return DG_EINVAL;
     if (phys->volume != DG_VOL_STRONG || phys->surface != DG_SURF_RUSANOV ||
         phys->rho_floor > 0.0 || phys->p_floor > 0.0)
       return DG_EUNSUPPORTED;
@@ -958,6 +1022,7 @@ dg_status dg_init_mesh(const dg_mesh_desc* inst, int n_inst, const dg_physics* p
 
   dg_ctx* c = new dg_ctx();
   c->inst.assign(inst, inst + n_inst);
+  c->rbc = rbc;
   c->phys = ph;
   c->stream = (cudaStream_t)cuda_stream;
   c->dim = inst[0].dim;

@@ -195,6 +195,15 @@ struct MechDev {
   RxnDev rx[kMaxReactions];
 };
 
+// Boundary conditions of one reacting / Navier-Stokes instance (host-filled).
+struct ReactBC {
+  int nonper;            // 1: some direction carries boundary conditions
+  int bc[6];             // boundary type per domain face (0: periodic)
+  double bcu[6][12];     // prescribed conserved state U_b (inflow, Dirichlet)
+  double bcw[6][6];      // (u, v, w, T, p - p_ref, a) of U_b (inflow, Dirichlet), or
+                         // (0, 0, 0, T_wall, 0, 0) (isothermal wall)
+};
+
 // Arguments of the two reacting launches of one stage over one instance.
 struct ReactArgs {
   const double* U;     // input state (or the residual's input)
@@ -224,6 +233,7 @@ struct ReactArgs {
   double ln1e4;        // ln 10^4 (for ln Z = ln 10^4 - ln T)
   float sf[3], liftf, muf, kfacf, p_reff;  // the same scalars for the FP32 flux arithmetic
   double D[(kMaxReactingN + 1) * (kMaxReactingN + 1)];
+  ReactBC bnd;          // boundary conditions of the instance
 };
 
 // Whether the reacting kernels exist for degree N and n_species.

@@ -1,6 +1,8 @@
 // dg_reacting.cu -- residual, SSP-RK stage and implicit source substep of the
-// single-temperature reacting Navier-Stokes equations (Sec. 2 reacting system) on periodic
-// 3D Cartesian meshes.
+// single-temperature reacting Navier-Stokes equations (Sec. 2 reacting system) on 3D
+// Cartesian meshes, periodic or with per-face boundary conditions (slip, no-slip adiabatic and
+// isothermal walls, supersonic inflow and outflow, Dirichlet: Sec. 3.1.1 boundary functors for
+// the inviscid flux, Sec. 3.1.2 boundary kernels for the BR1 trace and the viscous flux).
 //
 // One stage is two launches over the elements of an instance:
 //   1. k_br1_faces: BR1 gradients (Sec. 3.1.2, Eq. br1_avg) of W = (u, v, w, T) at every node
@@ -82,6 +84,15 @@ __device__ __forceinline__ int neighbour(const int* nel, int e, int l, int dir) 
   for (int d = 0; d < 3; ++d)
     if (d == l) c[d] = (c[d] + dir + nel[d]) % nel[d];
   return c[0] + nel[0] * (c[1] + nel[1] * c[2]);
+}
+
+// Domain face (2 l + side) that side `side` (0 lower, 1 upper) of element e in direction l
+// lies on when that face carries a boundary condition, else -1.
+__device__ __forceinline__ int wall_face(const ReactArgs& a, int e, int l, int side) {
+  const int f = 2 * l + side;
+  if (a.bnd.bc[f] == 0) return -1;
+  const int c = l == 0 ? e % a.nel[0] : (l == 1 ? (e / a.nel[0]) % a.nel[1] : e / (a.nel[0] * a.nel[1]));
+  return (side ? c == a.nel[l] - 1 : c == 0) ? f : -1;
 }
 
 // exp(x) for the Arrhenius rates, after Tang's table-driven method (P. T. P. Tang, ACM TOMS
@@ -224,6 +235,27 @@ __device__ __forceinline__ void br1_gradient(int q, const R* W, const R* Wt, con
   }
 }
 
+// Ghost neighbour value of the viscous face flux (momentum rows, energy) at a domain face
+// with normal axis L, from the element's own flux Fv and its conduction part heat = k dT/dx_L,
+// such that the BR1 average (Fv + gh)/2 is the boundary's viscous flux (Sec. 3.1.2 boundary
+// kernels): slip wall -- only the normal-stress row survives; no-slip adiabatic -- stress
+// rows kept, energy 0; no-slip isothermal -- stress rows kept, energy = heat; inflow,
+// outflow, Dirichlet -- the interior flux itself.
+template <int L, class R>
+__device__ __forceinline__ void ghost_viscous_flux(int type, const R* Fv, R heat, R* gh) {
+#pragma unroll
+  for (int c = 0; c < 4; ++c) gh[c] = Fv[c];
+  if (type == 1) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+      if (c != L) gh[c] = -Fv[c];
+  } else if (type == 5) {
+    gh[3] = -Fv[3];
+  } else if (type == 6) {
+    gh[3] = R(2) * heat - Fv[3];
+  }
+}
+
 template <int NS>
 __device__ __forceinline__ void load_species(const MechDev* __restrict__ mech, double* sp, int n) {
   for (int t = threadIdx.x; t < n * NS; t += blockDim.x) {
@@ -310,6 +342,37 @@ __device__ __forceinline__ void load_element(const ReactArgs& a, int e0, R* smem
     if (e >= a.n_elem) continue;
     R* sm = smem_el + el * esz;
     const int l = f >> 1, side = f & 1;
+    const int fw = a.bnd.nonper ? wall_face(a, e, l, side) : -1;
+    if (fw >= 0) {
+      // a domain face: a ghost trace W+ whose BR1 average (W + W+)/2 is the boundary's
+      // trace of (u, v, w, T) (Sec. 3.1.2 boundary kernels); the other rows and U are the
+      // element's own (the face job computes the inviscid boundary flux from them)
+      const long long go = a.base + (long long)e * G::NP + face_node<G::N1>(l, side, jf);
+      const int type = a.bnd.bc[fw];
+      R w[NROW];
+#pragma unroll
+      for (int c = 0; c < NROW; ++c) w[c] = P[c * a.stride + go];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        R g = w[c];
+        if (type == 1) {                        // slip wall: the mirror image
+          if (c == l) g = -g;
+        } else if (type == 5 || type == 6) {    // no-slip walls: velocity 0 on the wall
+          if (c < 3) g = -g;
+          else if (type == 6) g = R(2) * Ar<R>::load(a.bnd.bcw[fw][3]) - g;  // T = T_wall
+        } else if (type == 2 || type == 4) {    // inflow, Dirichlet: W of U_b
+          g = R(2) * Ar<R>::load(a.bnd.bcw[fw][c]) - g;
+        }                                       // outflow: the interior trace
+        sm[off_pt + (f * NPR + c) * G::NFN + jf] = g;
+      }
+#pragma unroll
+      for (int c = 4; c < NROW; ++c) sm[off_pt + (f * NPR + c) * G::NFN + jf] = w[c];
+      if (KEEP_U) {
+#pragma unroll
+        for (int v = 0; v < G::NV; ++v) sm[off_ut + (f * G::NV + v) * G::NFN + jf] = Ar<R>::load(a.U[v * a.stride + go]);
+      }
+      continue;
+    }
     const int en = neighbour(a.nel, e, l, side ? 1 : -1);
     const long long gi = a.base + (long long)en * G::NP + face_node<G::N1>(l, side ^ 1, jf);
 #pragma unroll
@@ -429,8 +492,16 @@ __global__ void __launch_bounds__(kRT) k_reacting_stage(const ReactArgs a) {
       if (ijk[L] == 0 || ijk[L] == N) {                                                       \
         const int jf = L == 0 ? ijk[1] + N1 * ijk[2]                                          \
                               : (L == 1 ? ijk[0] + N1 * ijk[2] : ijk[0] + N1 * ijk[1]);        \
-        R* dst = sm + G::E_FO + (2 * L + (ijk[L] == N ? 1 : 0)) * 4 * NFN + jf;               \
+        const int side = ijk[L] == N ? 1 : 0;                                                 \
+        R* dst = sm + G::E_FO + (2 * L + side) * 4 * NFN + jf;                                \
         _Pragma("unroll") for (int c = 0; c < 4; ++c) dst[c * NFN] = Fv[c];                   \
+        const int fw = a.bnd.nonper ? wall_face(a, e, L, side) : -1;                          \
+        if (fw >= 0) { /* ghost neighbour flux: (F_v + ghost)/2 is the boundary flux */       \
+          R gh[4];                                                                            \
+          ghost_viscous_flux<L, R>(a.bnd.bc[fw], Fv, kcond * S[3][L], gh);                    \
+          R* gd = sm + G::E_FT + (2 * L + side) * 4 * NFN + jf;                               \
+          _Pragma("unroll") for (int c = 0; c < 4; ++c) gd[c * NFN] = gh[c];                  \
+        }                                                                                     \
       }                                                                                       \
     }                                                                                         \
     __syncthreads();                                                                          \
@@ -471,14 +542,52 @@ __global__ void __launch_bounds__(kRT) k_reacting_stage(const ReactArgs a) {
     const R* pn = fs + G::E_PT + f * NPR * NFN + jf;
     R Fo[NV], Fn[NV];
     inv_flux<NS, R>(l, uo, po[0], po[NP], po[2 * NP], po[4 * NP], rs.p_ref, Fo);
-    inv_flux<NS, R>(l, un, pn[0], pn[NFN], pn[2 * NFN], pn[4 * NFN], rs.p_ref, Fn);
-    const R vlo = pick3(l, po[0], po[NP], po[2 * NP]), vln = pick3(l, pn[0], pn[NFN], pn[2 * NFN]);
-    const R lam = Ar<R>::fmax(Ar<R>::abs(vlo) + po[5 * NP], Ar<R>::abs(vln) + pn[5 * NFN]);
+    // the exterior state: the neighbour's trace, or at a domain face the boundary functor's
+    // (Sec. 3.1.1): walls -- the mirror state; Dirichlet -- U_b; inflow -- F* = F(U_b);
+    // outflow -- F* = F(U-)
+    R vn[3] = {pn[0], pn[NFN], pn[2 * NFN]}, pdn = pn[4 * NFN], an = pn[5 * NFN];
+    const int fw = a.bnd.nonper ? wall_face(a, e0 + fel, l, side) : -1;
+    const int type = fw >= 0 ? a.bnd.bc[fw] : 0;
+    if (fw >= 0) {
+      if (type == 2 || type == 4) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) un[k] = Ar<R>::load(a.bnd.bcu[fw][k]);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) vn[d] = Ar<R>::load(a.bnd.bcw[fw][d]);
+        pdn = Ar<R>::load(a.bnd.bcw[fw][4]);
+        an = Ar<R>::load(a.bnd.bcw[fw][5]);
+      } else {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) un[k] = uo[k];
+        vn[0] = po[0];
+        vn[1] = po[NP];
+        vn[2] = po[2 * NP];
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+          if (d == l) {
+            un[NS + d] = -uo[NS + d];
+            vn[d] = -vn[d];
+          }
+        pdn = po[4 * NP];
+        an = po[5 * NP];
+      }
+    }
+    inv_flux<NS, R>(l, un, vn[0], vn[1], vn[2], pdn, rs.p_ref, Fn);
+    const R vlo = pick3(l, po[0], po[NP], po[2 * NP]), vln = pick3(l, vn[0], vn[1], vn[2]);
+    const R lam = Ar<R>::fmax(Ar<R>::abs(vlo) + po[5 * NP], Ar<R>::abs(vln) + an);
     // F* = (F_L + F_R)/2 - lam (U_R - U_L)/2; with L/R the lower/upper side of the face
     const R hl = side ? R(0.5) * lam : R(-0.5) * lam;  // lam/2 (U_R - U_L) = hl (un - uo)
     R dlt[NV];
+    if (type == 2) {  // supersonic inflow: F* = F(U_b)
 #pragma unroll
-    for (int k = 0; k < NV; ++k) dlt[k] = R(0.5) * (Fn[k] - Fo[k]) - hl * (un[k] - uo[k]);
+      for (int k = 0; k < NV; ++k) dlt[k] = Fn[k] - Fo[k];
+    } else if (type == 3) {  // supersonic outflow: F* = F(U-)
+#pragma unroll
+      for (int k = 0; k < NV; ++k) dlt[k] = R(0);
+    } else {
+#pragma unroll
+      for (int k = 0; k < NV; ++k) dlt[k] = R(0.5) * (Fn[k] - Fo[k]) - hl * (un[k] - uo[k]);
+    }
 #pragma unroll
     for (int c = 0; c < 4; ++c)
       dlt[NS + c] = dlt[NS + c] - R(0.5) * (fs[G::E_FT + f * 4 * NFN + c * NFN + jf] -

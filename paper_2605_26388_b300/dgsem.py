@@ -26,6 +26,8 @@ SURF_RUSANOV, SURF_HLLC, SURF_HLL, SURF_EC = 0, 1, 2, 3
 FP64, FP32_MIXED = 0, 1
 LAUNCH_PER_INSTANCE, LAUNCH_BATCHED = 0, 1
 BC_PERIODIC, BC_SLIP_WALL, BC_INFLOW, BC_OUTFLOW, BC_DIRICHLET = 0, 1, 2, 3, 4
+BC_NOSLIP_ADIABATIC, BC_NOSLIP_ISOTHERMAL = 5, 6
+MAX_VARS = 12
 SSPRK33, SSPRK54 = 0, 1
 NEWTON_MAX_IT, NEWTON_TOL = 40, 1e-12
 MATH_EXP_TABLE, MATH_RCP_NEWTON, MATH_EXP_CUDA, MATH_RCP_CUDA = 0, 1, 2, 3
@@ -51,7 +53,7 @@ class DGError(RuntimeError):
 class MeshDesc(C.Structure):
     _fields_ = [("dim", C.c_int), ("N", C.c_int), ("nel", C.c_int * 3), ("lo", C.c_double * 3),
                 ("hi", C.c_double * 3), ("periodic", C.c_int * 3), ("bc", C.c_int * 6),
-                ("bc_state", (C.c_double * 5) * 6), ("coords", C.POINTER(C.c_double))]
+                ("bc_state", (C.c_double * MAX_VARS) * 6), ("coords", C.POINTER(C.c_double))]
 
 
 class Mechanism(C.Structure):
@@ -155,7 +157,8 @@ def gll(N: int):
 class Mesh:
     """One Cartesian instance: periodic, or with boundary conditions bc[f] (BC_*) on the
     faces x-, x+, y-, y+, z-, z+ of a direction whose two faces are both non-periodic;
-    bc_state[f] is the prescribed conserved state of an inflow or Dirichlet face."""
+    bc_state[f] is the prescribed conserved state of an inflow or Dirichlet face, or
+    (T_wall,) of an isothermal no-slip wall."""
     dim: int
     N: int
     nel: Sequence[int]

@@ -94,3 +94,32 @@ def test_product_path_has_no_fallback(dg, monkeypatch):
     monkeypatch.setattr(dg, "_lib", None)
     with pytest.raises(OSError):
         dg.lib()
+
+
+def _init_ns(dg, mesh):
+    phys = dg.Physics(dg.DG_NAVIER_STOKES, 0, 0, 0, 1.4, 0.0, 0.0, 0.0, 0.01, 0.72)
+    arr = (dg.MeshDesc * 1)(mesh)
+    h = C.c_void_p()
+    return dg.lib().dg_init_mesh(arr, 1, C.byref(phys), None, C.byref(h))
+
+
+def test_init_rejects_bad_wall_descriptions(dg):
+    """No-slip walls need viscous equations; a wall temperature must be positive; a viscous
+    far-field state must have rho > 0 and T > 0 under the mixture closure."""
+    euler = dg.Mesh(2, 3, (4, 4), (0.0, 0.0), (1.0, 1.0), bc=(5, 5, 0, 0, 0, 0)).c()
+    assert _init(dg, euler)[0] == dg.DG_EINVAL
+    euler = dg.Mesh(2, 3, (4, 4), (0.0, 0.0), (1.0, 1.0), bc=(6, 6, 0, 0, 0, 0),
+                    bc_state=((1.0,), (1.0,), None, None, None, None)).c()
+    assert _init(dg, euler)[0] == dg.DG_EINVAL
+    box = dict(dim=3, N=3, nel=(2, 2, 2), lo=(0.0,) * 3, hi=(1.0,) * 3)
+    cold = dg.Mesh(**box, bc=(0, 0, 6, 6, 0, 0), bc_state=(None, None, (0.0,), (1.0,), None, None)).c()
+    assert _init_ns(dg, cold) == dg.DG_EINVAL
+    nan = dg.Mesh(**box, bc=(0, 0, 6, 6, 0, 0), bc_state=(None, None, (1.0,), (float("nan"),), None, None)).c()
+    assert _init_ns(dg, nan) == dg.DG_EINVAL
+    # E below the kinetic energy: T < 0
+    neg = dg.Mesh(**box, bc=(4, 4, 0, 0, 0, 0),
+                  bc_state=((1.0, 2.0, 0.0, 0.0, 1.0), (1.0, 0.0, 0.0, 0.0, 2.5), None, None, None, None)).c()
+    assert _init_ns(dg, neg) == dg.DG_EINVAL
+    assert _init_ns(dg, dg.Mesh(**box, bc=(7, 7, 0, 0, 0, 0)).c()) == dg.DG_EINVAL
+    unpaired = dg.Mesh(**box, bc=(5, 0, 0, 0, 0, 0)).c()
+    assert _init_ns(dg, unpaired) == dg.DG_EINVAL
