@@ -49,12 +49,14 @@ class _Mech(C.Structure):
         ("W", C.c_double * 8), ("R", C.c_double * 8), ("cv", C.c_double * 8), ("h0", C.c_double * 8),
         ("lnA", C.c_double * 32), ("b", C.c_double * 32), ("Ta", C.c_double * 32),
         ("kc", (C.c_double * 5) * 32), ("nu_f", (C.c_int * 8) * 32), ("nu_b", (C.c_int * 8) * 32),
+        ("theta_v", C.c_double * 8), ("ta_mode", C.c_int * 32),
     ]
 
 
 def mechanism(m: dict) -> _Mech:
-    """Pack a mechanism dictionary (species data W, R, cv, h0; per-reaction lnA, b, Ta, kc,
-    nu_f, nu_b) into the oracle's own structure."""
+    """Pack a mechanism dictionary (species data W, R, cv, h0 and, for the two-temperature
+    model, theta_v; per-reaction lnA, b, Ta, kc, nu_f, nu_b and ta_mode) into the oracle's own
+    structure."""
     c = _Mech()
     ns, nr = int(m["n_species"]), int(m["n_reactions"])
     c.n_species, c.n_reactions = ns, nr
@@ -67,6 +69,9 @@ def mechanism(m: dict) -> _Mech:
         for s in range(ns):
             c.nu_f[r][s] = int(m["nu_f"][r][s])
             c.nu_b[r][s] = int(m["nu_b"][r][s])
+        c.ta_mode[r] = int(m.get("ta_mode", [0] * nr)[r])
+    for s in range(ns):
+        c.theta_v[s] = float(m.get("theta_v", [0.0] * ns)[s])
     return c
 
 
@@ -80,7 +85,7 @@ class _Problem(C.Structure):
         ("mech", C.POINTER(_Mech)), ("parts", C.c_int),
         ("shock", C.c_int), ("alpha_min", C.c_double), ("alpha_max", C.c_double),
         ("sharpness", C.c_double), ("bc", C.c_int * 6), ("bc_state", (C.c_double * 12) * 6),
-        ("coords", C.POINTER(C.c_double)),
+        ("coords", C.POINTER(C.c_double)), ("two_temperature", C.c_int),
     ]
 
 
@@ -110,11 +115,12 @@ class Problem:
     bc_state: tuple = None          # per face: the exterior conserved state (INFLOW, DIRICHLET);
                                     # (T_wall,) for NOSLIP_ISOTHERMAL
     coords: np.ndarray = None       # Euler: node coordinates (dim, n_elem, n_nodes) of a curved mesh
+    two_temperature: bool = False   # NS_REACTING: E_v appended to the state (periodic meshes)
 
     @property
     def nvars(self) -> int:
         if self.equations == NS_REACTING:
-            return int(self.mech["n_species"]) + self.dim + 1
+            return int(self.mech["n_species"]) + self.dim + 1 + (1 if self.two_temperature else 0)
         return self.dim + 2
 
     @property
@@ -140,6 +146,7 @@ class Problem:
                      (C.c_double * 3)(*hi), self.equations, self.volume, self.surface,
                      self.gamma, self.mu, self.prandtl, self.rho_floor, self.p_floor)
         p.parts = self.parts
+        p.two_temperature = 1 if self.two_temperature else 0
         p.shock = 1 if self.shock else 0
         p.alpha_min, p.alpha_max, p.sharpness = self.alpha_min, self.alpha_max, self.sharpness
         if self.coords is not None:
@@ -181,7 +188,8 @@ def lib():
         _lib.orc_rollout_grad.argtypes = [pp, dp, dp, dp, C.c_double, C.c_int, dp, dp]
         _lib.orc_arrhenius.argtypes = [C.POINTER(_Mech), C.c_int, C.c_double, dp, dp]
         _lib.orc_chem_source.argtypes = [pp, dp, dp]
-        _lib.orc_mixture.argtypes = [pp, dp, dp, dp]
+        _lib.orc_mixture.argtypes = [pp, dp, dp, dp, dp]
+        _lib.orc_relaxation_time.argtypes = [C.POINTER(_Mech), C.c_int, dp, C.c_double, C.c_double, dp]
         ip = C.POINTER(C.c_int)
         _lib.orc_shock_alpha.argtypes = [pp, dp, dp, dp]
         _lib.orc_fv_residual.argtypes = [pp, dp, dp]
@@ -360,11 +368,28 @@ def chem_source(P: Problem, u) -> np.ndarray:
 def mixture(P: Problem, u):
     """Temperature and pressure of one reacting node state (calorically perfect species,
     Sec. 2 closure). Pinned by inverting the state constructor of the reacting workload."""
+    T, p, _ = mixture_tt(P, u)
+    return T, p
+
+
+def mixture_tt(P: Problem, u):
+    """(T, p, T_v) of one reacting node state; T_v = T in the single-temperature model.
+    Pinned by inverting the two-temperature state constructor."""
     u = np.ascontiguousarray(u, dtype=np.float64)
-    T, p = C.c_double(), C.c_double()
+    T, p, Tv = C.c_double(), C.c_double(), C.c_double()
     c = P._c()
-    _check(lib().orc_mixture(C.byref(c), _ptr(u), C.byref(T), C.byref(p)), "mixture")
-    return T.value, p.value
+    _check(lib().orc_mixture(C.byref(c), _ptr(u), C.byref(T), C.byref(p), C.byref(Tv)), "mixture")
+    return T.value, p.value, Tv.value
+
+
+def relaxation_time(mech: dict, s: int, X, T: float, p: float) -> float:
+    """Vibrational relaxation time (s) of molecular species s, Millikan-White with Park's
+    correction (Sec. 3.1.3), for mole fractions X at temperature T (K) and pressure p (Pa)."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    m = mechanism(mech)
+    tau = C.c_double()
+    _check(lib().orc_relaxation_time(C.byref(m), s, _ptr(X), T, p, C.byref(tau)), "relaxation_time")
+    return tau.value
 
 
 SSPRK33, SSPRK54 = 3, 54

@@ -59,6 +59,10 @@ struct OrcMech {
   double lnA[32], b[32], Ta[32];          // k_f = exp(lnA + b ln T - Ta/T), cm-mol-s
   double kc[32][5];                       // ln K_c = a0/Z + a1 + a2 ln Z + a3 Z + a4 Z^2, Z = 1e4/T
   int nu_f[32][8], nu_b[32][8];           // stoichiometric coefficients nu', nu''
+  double theta_v[8];                      // two-temperature: characteristic vibrational
+                                          // temperature (K) of each species, 0 for atoms
+  int ta_mode[32];                        // two-temperature: 1 -- the reaction's controlling
+                                          // temperature is sqrt(T Tv) (dissociation), 0 -- T
 };
 
 struct OrcProblem {
@@ -82,6 +86,8 @@ struct OrcProblem {
                               // values); NOSLIP_ISOTHERMAL: [0] = the wall temperature
   const double* coords;       // Euler, periodic: node coordinates [d][elem][node] of a curved
                               // mesh on the same element topology (null: the Cartesian box)
+  int two_temperature;        // ORC_NS_REACTING: 1 -- the two-temperature model (E_v appended
+                              // to the state), periodic meshes, residual only
 };
 
 }  // extern "C"
@@ -897,7 +903,8 @@ void curved_element_residual(const OrcProblem& P, const Mesh& M, const Ops& ops,
 }
 
 int n_vars(const OrcProblem& P) {
-  return (P.equations == ORC_NS_REACTING) ? P.mech->n_species + P.dim + 1 : P.dim + 2;
+  if (P.equations == ORC_NS_REACTING) return P.mech->n_species + P.dim + 1 + (P.two_temperature ? 1 : 0);
+  return P.dim + 2;
 }
 
 int check_reacting_bc(const OrcProblem& P);
@@ -915,9 +922,16 @@ int check_problem(const OrcProblem& P) {
     if (P.rho_floor > 0.0 || P.p_floor > 0.0) return -6;
     if (P.mu < 0.0 || !(P.prandtl > 0.0)) return -1;
     if (P.shock || P.coords) return -6;
+    if (P.two_temperature) {  // periodic meshes only
+      if (P.two_temperature != 1) return -1;
+      for (int f = 0; f < 6; ++f)
+        if (P.bc[f]) return -6;
+      for (int s = 0; s < P.mech->n_species; ++s)
+        if (!(P.mech->theta_v[s] >= 0.0)) return -1;
+    }
     return check_reacting_bc(P);
   }
-  if (P.equations != ORC_EULER) return -6;
+  if (P.equations != ORC_EULER || P.two_temperature) return -6;
   for (int f = 0; f < 2 * P.dim; ++f) {
     if (P.bc[f] < ORC_BC_PERIODIC || P.bc[f] > ORC_BC_DIRICHLET) return -1;  // no viscosity: no no-slip
     if ((P.bc[f] == ORC_BC_PERIODIC) != (P.bc[f ^ 1] == ORC_BC_PERIODIC)) return -1;  // pairs
@@ -944,10 +958,53 @@ int check_problem(const OrcProblem& P) {
 // (Sec. 2 closure), E = sum rho_s (cv_s T + h0_s) + rho |u|^2 / 2, p = sum rho_s R_s T;
 // frozen sound speed a^2 = (1 + sum rho_s R_s / sum rho_s cv_s) p / rho; no species
 // diffusion; constant viscosity mu; conductivity k = mu c_p / Pr with the mixture c_p.
+// Two-temperature model (Sec. 2 "Thermal nonequilibrium coupling", "Total energy and
+// closure"; Sec. 3.1.3 Eqs. src_vector, src_landau_teller): E_v appended to U, cv_s the
+// translational-rotational heat capacity, E_v = sum rho_s e_v,s(T_v) with harmonic
+// oscillators; the vibrational mode is frozen in the sound speed; READING: conductivity of
+// the vibrational mode k_v = mu c_v,v / Pr with c_v,v = (1/rho) dE_v/dT_v (the same
+// Eucken-type ratio as k), and the total-energy flux carries both heat fluxes (E contains E_v).
 // ---------------------------------------------------------------------------------------
 struct Mix {
   double rho, v[3], T, p, a, cp, rcv;  // rcv = sum rho_s cv_s
+  double Tv, Ev, cvv;                  // two-temperature: T_v, E_v, (1/rho) dE_v/dT_v
 };
+
+// Vibrational energy per unit mass of a harmonic oscillator with characteristic temperature
+// theta at temperature T (Sec. 3.1.3, below Eq. src_landau_teller):
+// e_v = R theta / (exp(theta / T) - 1); 0 for an atom (theta = 0).
+double vib_energy(double R, double theta, double T) {
+  if (theta <= 0.0) return 0.0;
+  return R * theta / std::expm1(theta / T);
+}
+
+// d e_v / dT of the same oscillator.
+double vib_heat(double R, double theta, double T) {
+  if (theta <= 0.0) return 0.0;
+  const double x = theta / T, em = std::expm1(x);
+  return R * x * x * (em + 1.0) / (em * em);
+}
+
+// E_v of the partial densities rho_s at vibrational temperature T.
+double vib_energy_density(const OrcMech& m, const double* rho_s, double T) {
+  double Ev = 0.0;
+  for (int s = 0; s < m.n_species; ++s) Ev += rho_s[s] * vib_energy(m.R[s], m.theta_v[s], T);
+  return Ev;
+}
+
+// The vibrational temperature with E_v(T_v) = Ev: E_v grows strictly with T_v, so bisection
+// on [1e-3, 1e7] K to the last bit finds the root (NaN when no species vibrates or Ev <= 0).
+double vib_temperature(const OrcMech& m, const double* rho_s, double Ev) {
+  double lo = 1e-3, hi = 1e7;
+  if (!(Ev > 0.0) || !(vib_energy_density(m, rho_s, hi) > Ev)) return std::nan("");
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (vib_energy_density(m, rho_s, mid) < Ev) lo = mid;
+    else hi = mid;
+  }
+  return 0.5 * (lo + hi);
+}
 
 Mix mixture(const OrcProblem& P, const double* u) {
   const OrcMech& m = *P.mech;
@@ -967,11 +1024,21 @@ Mix mixture(const OrcProblem& P, const double* u) {
     q.v[d] = u[ns + d] / q.rho;
     kin += u[ns + d] * q.v[d];
   }
-  q.T = (u[ns + dim] - 0.5 * kin - rh0) / rcv;
+  // two-temperature closure (Sec. 2 "Total energy and closure"): E = sum rho_s (cv_s T +
+  // h0_s) + E_v + rho |u|^2 / 2 with cv_s the translational-rotational heat capacity
+  q.Ev = P.two_temperature ? u[ns + dim + 1] : 0.0;
+  q.T = (u[ns + dim] - q.Ev - 0.5 * kin - rh0) / rcv;
   q.p = rR * q.T;
   q.a = std::sqrt((1.0 + rR / rcv) * q.p / q.rho);
   q.cp = (rcv + rR) / q.rho;
   q.rcv = rcv;
+  q.Tv = q.T;
+  q.cvv = 0.0;
+  if (P.two_temperature) {
+    q.Tv = vib_temperature(m, u, q.Ev);
+    for (int s = 0; s < ns; ++s) q.cvv += u[s] * vib_heat(m.R[s], m.theta_v[s], q.Tv);
+    q.cvv /= q.rho;
+  }
   return q;
 }
 
@@ -982,6 +1049,7 @@ void mix_flux(const OrcProblem& P, int l, const double* u, double* F) {
   for (int s = 0; s < ns; ++s) F[s] = u[s] * q.v[l];
   for (int d = 0; d < dim; ++d) F[ns + d] = u[ns + l] * q.v[d] + (d == l ? q.p : 0.0);
   F[ns + dim] = (u[ns + dim] + q.p) * q.v[l];
+  if (P.two_temperature) F[ns + dim + 1] = u[ns + dim + 1] * q.v[l];  // E_v u_l
 }
 
 void mix_rusanov(const OrcProblem& P, int l, const double* uL, const double* uR, double* F) {
@@ -1006,15 +1074,18 @@ void arrhenius(const OrcMech& m, int r, double T, double& kf, double& Kc) {
 }
 
 // Species production rates omega_s (kg m^-3 s^-1) of the partial densities rho_s at
-// temperature T.
-void species_rates(const OrcMech& m, const double* rho_s, double T, double* w) {
+// translational temperature T and vibrational temperature Tv: each reaction's rates are
+// evaluated at its controlling temperature T_a (Sec. 3.1.3: sqrt(T Tv) for dissociation,
+// ta_mode 1; T otherwise), k_b = k_f / K_c(T_a).  Single temperature: Tv = T.
+void species_rates(const OrcMech& m, const double* rho_s, double T, double Tv, double* w) {
   const int ns = m.n_species;
   for (int s = 0; s < ns; ++s) w[s] = 0.0;
   double X[8];
   for (int s = 0; s < ns; ++s) X[s] = rho_s[s] / m.W[s] * 1.0e-6;
   for (int r = 0; r < m.n_reactions; ++r) {
+    const double Ta = (m.ta_mode[r] && Tv != T) ? std::sqrt(T * Tv) : T;
     double kf, Kc;
-    arrhenius(m, r, T, kf, Kc);
+    arrhenius(m, r, Ta, kf, Kc);
     double pf = 1.0, pb = 1.0;
     for (int s = 0; s < ns; ++s) {
       for (int k = 0; k < m.nu_f[r][s]; ++k) pf *= X[s];
@@ -1025,11 +1096,62 @@ void species_rates(const OrcMech& m, const double* rho_s, double T, double* w) {
   }
 }
 
+// Vibrational relaxation time tau_s (s) of molecular species s (Sec. 3.1.3, below Eq.
+// src_landau_teller: the Millikan-White correlation with Park's high-temperature
+// correction), at translational temperature T and pressure p (Pa) for mole fractions X.
+// Millikan and White (J. Chem. Phys. 39, 1963): p tau_sr = exp(A_sr (T^-1/3 - B_sr) - 18.42)
+// atm s with A_sr = 1.16e-3 mu_sr^1/2 theta_s^4/3, B_sr = 0.015 mu_sr^1/4, mu_sr the reduced
+// molar mass in g/mol, and the mixture rule tau_MW = sum_r X_r / sum_r (X_r / tau_sr).
+// Park (J. Thermophys. Heat Transfer 7, 1993): tau_P = 1 / (n sigma_v c_s), n = p / (k_B T)
+// the number density, c_s = sqrt(8 R_s T / pi) the mean molecular speed,
+// sigma_v = 1e-21 (50000 / T)^2 m^2.  READING: tau_s = tau_MW + tau_P, n the mixture's.
+double relaxation_time(const OrcMech& m, int s, const double* X, double T, double p) {
+  const double katm = 101325.0, kB = 1.380649e-23;
+  double num = 0.0, den = 0.0;
+  for (int r = 0; r < m.n_species; ++r) {
+    const double Ws = m.W[s] * 1.0e3, Wr = m.W[r] * 1.0e3;  // g/mol
+    const double mu = Ws * Wr / (Ws + Wr);
+    const double A = 1.16e-3 * std::sqrt(mu) * std::pow(m.theta_v[s], 4.0 / 3.0);
+    const double B = 0.015 * std::pow(mu, 0.25);
+    const double tau_sr = std::exp(A * (std::pow(T, -1.0 / 3.0) - B) - 18.42) * katm / p;
+    num += X[r];
+    den += X[r] / tau_sr;
+  }
+  const double tau_mw = num / den;
+  const double n = p / (kB * T);
+  const double sigma = 1.0e-21 * (50000.0 / T) * (50000.0 / T);
+  const double c = std::sqrt(8.0 * m.R[s] * T / M_PI);
+  return tau_mw + 1.0 / (n * sigma * c);
+}
+
+// Landau-Teller exchange (Sec. 3.1.3 Eq. src_landau_teller):
+// Q_T-v = sum over molecules rho_s (e_v,s(T) - e_v,s(Tv)) / tau_s(T, p).
+double landau_teller(const OrcMech& m, const double* rho_s, const Mix& q) {
+  double X[8], sum = 0.0;
+  for (int s = 0; s < m.n_species; ++s) sum += (X[s] = rho_s[s] / m.W[s]);
+  for (int s = 0; s < m.n_species; ++s) X[s] /= sum;
+  double Q = 0.0;
+  for (int s = 0; s < m.n_species; ++s) {
+    if (m.theta_v[s] <= 0.0) continue;
+    const double tau = relaxation_time(m, s, X, q.T, q.p);
+    Q += rho_s[s] * (vib_energy(m.R[s], m.theta_v[s], q.T) - vib_energy(m.R[s], m.theta_v[s], q.Tv)) / tau;
+  }
+  return Q;
+}
+
+// Source vector (Sec. 3.1.3 Eq. src_vector): omega_s, no momentum or total-energy source;
+// two-temperature: the E_v row Q_T-v + sum_s omega_s e_v,s(Tv).
 void chem_source(const OrcProblem& P, const double* u, double* S) {
   const int nv = n_vars(P);
   for (int v = 0; v < nv; ++v) S[v] = 0.0;
   Mix q = mixture(P, u);
-  species_rates(*P.mech, u, q.T, S);
+  species_rates(*P.mech, u, q.T, q.Tv, S);
+  if (P.two_temperature) {
+    const OrcMech& m = *P.mech;
+    double Sv = landau_teller(m, u, q);
+    for (int s = 0; s < m.n_species; ++s) Sv += S[s] * vib_energy(m.R[s], m.theta_v[s], q.Tv);
+    S[nv - 1] = Sv;
+  }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1158,9 +1280,10 @@ void viscous_boundary_flux(const OrcProblem& P, int f, int l, const double* u, c
 }
 
 // BR1 gradient (Sec. 3.1.2 Eq. br1_avg; App. A "Viscous Volume and Interface Fluxes") of
-// W = (u, v, w, T) on element e: S_l = (2/dx_l) [D W + (upper face) (W^ - W_N)/w_N
-// - (lower face) (W^ - W_0)/w_0], W^ = (W_L + W_R)/2 (at a domain face: wall_trace).
-// Layout G[(node * 4 + q) * 3 + l].
+// W = (u, v, w, T, T_v) on element e: S_l = (2/dx_l) [D W + (upper face) (W^ - W_N)/w_N
+// - (lower face) (W^ - W_0)/w_0], W^ = (W_L + W_R)/2 (at a domain face: wall_trace; the
+// two-temperature model has no boundary conditions, so W^'s T_v row is never a wall's).
+// Layout G[(node * 5 + q) * 3 + l]; T_v = T in the single-temperature model.
 void br1_gradient(const OrcProblem& P, const Mesh& M, const Ops& ops, const double* U, int e,
                   double* G) {
   const int dim = M.dim, n1 = M.n1, N = M.N, nv = n_vars(P);
@@ -1168,55 +1291,58 @@ void br1_gradient(const OrcProblem& P, const Mesh& M, const Ops& ops, const doub
     double u[16];
     load_node(M, nv, U, el, nd, u);
     Mix q = mixture(P, u);
-    W[0] = q.v[0]; W[1] = q.v[1]; W[2] = q.v[2]; W[3] = q.T;
+    W[0] = q.v[0]; W[1] = q.v[1]; W[2] = q.v[2]; W[3] = q.T; W[4] = q.Tv;
   };
   for (int nd = 0; nd < M.n_nodes; ++nd) {
     int ijk[3];
     M.node_coords(nd, ijk);
-    for (int q = 0; q < 4; ++q)
-      for (int l = 0; l < 3; ++l) G[((size_t)(e * M.n_nodes + nd) * 4 + q) * 3 + l] = 0.0;
+    for (int q = 0; q < 5; ++q)
+      for (int l = 0; l < 3; ++l) G[((size_t)(e * M.n_nodes + nd) * 5 + q) * 3 + l] = 0.0;
     for (int l = 0; l < dim; ++l) {
       const double s = 2.0 / M.dx[l];
-      double acc[4] = {0, 0, 0, 0}, Wm[4];
+      double acc[5] = {0, 0, 0, 0, 0}, Wm[5];
       for (int m = 0; m < n1; ++m) {
         int mk[3] = {ijk[0], ijk[1], ijk[2]};
         mk[l] = m;
         prim(e, M.node(mk), Wm);
-        for (int q = 0; q < 4; ++q) acc[q] += ops.D[ijk[l] * n1 + m] * Wm[q];
+        for (int q = 0; q < 5; ++q) acc[q] += ops.D[ijk[l] * n1 + m] * Wm[q];
       }
-      double Wo[4], Wn[4], Wh[4];
+      double Wo[5], Wn[5], Wh[5];
       prim(e, nd, Wo);
       if (ijk[l] == N) {
         const int fb = boundary_face(P, M, e, l, 1);
         if (fb >= 0) {
           wall_trace(P, fb, l, Wo, Wh);
+          Wh[4] = Wh[3];
         } else {
           int nk[3] = {ijk[0], ijk[1], ijk[2]};
           nk[l] = 0;
           prim(M.neighbour(e, l, +1), M.node(nk), Wn);
-          for (int q = 0; q < 4; ++q) Wh[q] = 0.5 * (Wo[q] + Wn[q]);
+          for (int q = 0; q < 5; ++q) Wh[q] = 0.5 * (Wo[q] + Wn[q]);
         }
-        for (int q = 0; q < 4; ++q) acc[q] += (Wh[q] - Wo[q]) / ops.w[N];
+        for (int q = 0; q < 5; ++q) acc[q] += (Wh[q] - Wo[q]) / ops.w[N];
       }
       if (ijk[l] == 0) {
         const int fb = boundary_face(P, M, e, l, 0);
         if (fb >= 0) {
           wall_trace(P, fb, l, Wo, Wh);
+          Wh[4] = Wh[3];
         } else {
           int nk[3] = {ijk[0], ijk[1], ijk[2]};
           nk[l] = N;
           prim(M.neighbour(e, l, -1), M.node(nk), Wn);
-          for (int q = 0; q < 4; ++q) Wh[q] = 0.5 * (Wn[q] + Wo[q]);
+          for (int q = 0; q < 5; ++q) Wh[q] = 0.5 * (Wn[q] + Wo[q]);
         }
-        for (int q = 0; q < 4; ++q) acc[q] -= (Wh[q] - Wo[q]) / ops.w[0];
+        for (int q = 0; q < 5; ++q) acc[q] -= (Wh[q] - Wo[q]) / ops.w[0];
       }
-      for (int q = 0; q < 4; ++q) G[((size_t)(e * M.n_nodes + nd) * 4 + q) * 3 + l] = s * acc[q];
+      for (int q = 0; q < 5; ++q) G[((size_t)(e * M.n_nodes + nd) * 5 + q) * 3 + l] = s * acc[q];
     }
   }
 }
 
 // viscous flux in direction l (Sec. 2 F_v; Sec. 3.1.2 Eq. tau; q = -k grad T):
-// (0 for species, tau_{.l}, u . tau_{.l} + k dT/dx_l)
+// (0 for species, tau_{.l}, u . tau_{.l} + k dT/dx_l); two-temperature: the energy row adds
+// k_v dT_v/dx_l and the E_v row is k_v dT_v/dx_l (q_v = -k_v grad T_v).
 void viscous_flux(const OrcProblem& P, int l, const double* u, const double* g, double* F) {
   const int ns = P.mech->n_species, dim = P.dim, nv = n_vars(P);
   Mix q = mixture(P, u);
@@ -1231,6 +1357,11 @@ void viscous_flux(const OrcProblem& P, int l, const double* u, const double* g, 
     work += q.v[j] * tau;
   }
   F[ns + dim] = work + k * g[3 * 3 + l];
+  if (P.two_temperature) {
+    const double kv = mu * q.cvv / P.prandtl;
+    F[ns + dim] += kv * g[4 * 3 + l];
+    F[ns + dim + 1] = kv * g[4 * 3 + l];
+  }
 }
 
 void reacting_element_residual(const OrcProblem& P, const Mesh& M, const Ops& ops, const double* U,
@@ -1238,7 +1369,7 @@ void reacting_element_residual(const OrcProblem& P, const Mesh& M, const Ops& op
   const int dim = M.dim, n1 = M.n1, N = M.N, nv = n_vars(P);
   const int parts = P.parts ? P.parts : 7;
   std::vector<double> R((size_t)M.n_nodes * nv, 0.0);
-  auto grad = [&](int el, int nd) { return G + (size_t)(el * M.n_nodes + nd) * 12; };
+  auto grad = [&](int el, int nd) { return G + (size_t)(el * M.n_nodes + nd) * 15; };
   double um[16], F[16];
   for (int nd = 0; nd < M.n_nodes; ++nd) {
     int ijk[3];
@@ -1313,7 +1444,7 @@ void residual(const OrcProblem& P, const double* U, double* dU) {
   Mesh M(P);
   Ops ops(P.N);
   if (P.equations == ORC_NS_REACTING) {
-    std::vector<double> G((size_t)M.n_elem * M.n_nodes * 12, 0.0);
+    std::vector<double> G((size_t)M.n_elem * M.n_nodes * 15, 0.0);
     const int parts = P.parts ? P.parts : 7;
     if (parts & 2) {
 #pragma omp parallel for schedule(static)
@@ -1540,12 +1671,22 @@ int orc_chem_source(const OrcProblem* P, const double* u, double* S) {
   return 0;
 }
 
-// Temperature and pressure of one node state (reacting problems).
-int orc_mixture(const OrcProblem* P, const double* u, double* T, double* p) {
+// Temperature, pressure and vibrational temperature (T for the single-temperature model) of
+// one node state (reacting problems).
+int orc_mixture(const OrcProblem* P, const double* u, double* T, double* p, double* Tv) {
   if (P->equations != ORC_NS_REACTING || !P->mech) return -1;
   Mix q = mixture(*P, u);
   *T = q.T;
   *p = q.p;
+  if (Tv) *Tv = q.Tv;
+  return 0;
+}
+
+// Vibrational relaxation time of species s (two-temperature model) for mole fractions X at
+// temperature T (K) and pressure p (Pa).
+int orc_relaxation_time(const OrcMech* m, int s, const double* X, double T, double p, double* tau) {
+  if (!m || s < 0 || s >= m->n_species || !(m->theta_v[s] > 0.0)) return -1;
+  *tau = relaxation_time(*m, s, X, T, p);
   return 0;
 }
 
@@ -1569,7 +1710,7 @@ int orc_rhs_elements(const OrcProblem* P, const double* U, const int* elems, int
   }
   if (P->equations == ORC_NS_REACTING) {
     // gradients are needed on the listed elements and their face neighbours only
-    std::vector<double> G((size_t)M.n_elem * M.n_nodes * 12, 0.0);
+    std::vector<double> G((size_t)M.n_elem * M.n_nodes * 15, 0.0);
     std::vector<int> need;
     std::vector<char> mark(M.n_elem, 0);
     for (int k = 0; k < n; ++k) {
@@ -1809,7 +1950,7 @@ void source_residual(const OrcMech& m, const double* Y, const double* Yn, double
   const int ns = m.n_species;
   const double T = temperature_of(m, Y, e);
   double w[8];
-  species_rates(m, Y, T, w);
+  species_rates(m, Y, T, T, w);
   for (int s = 0; s < ns; ++s) R[s] = Y[s] - Yn[s] - h * w[s];
 }
 
@@ -1933,6 +2074,7 @@ int orc_ssp_steps(const OrcProblem* P, int scheme, double* U, double dt, int n_s
 // One implicit source substep S_h over a whole state, in place (reacting problems).
 // *iters receives the largest Newton count over the nodes (-1: some node did not converge).
 int orc_source_implicit(const OrcProblem* P, double* U, double h, int max_it, double tol, int* iters) {
+  if (P->two_temperature) return -6;  // the implicit substep is single-temperature
   int rc = check_problem(*P);
   if (rc) return rc;
   if (P->equations != ORC_NS_REACTING || !P->mech) return -1;
@@ -1945,6 +2087,7 @@ int orc_source_implicit(const OrcProblem* P, double* U, double h, int max_it, do
 // T_dt one step of the SSP scheme on the residual without its source part.
 int orc_strang_steps(const OrcProblem* P, int scheme, double* U, double dt, int n_steps, int max_it,
                      double tol, int* iters) {
+  if (P->two_temperature) return -6;  // the implicit substep is single-temperature
   int rc = check_problem(*P);
   if (rc) return rc;
   if (P->equations != ORC_NS_REACTING || !P->mech || (scheme != 3 && scheme != 54)) return -1;

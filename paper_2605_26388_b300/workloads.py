@@ -245,6 +245,9 @@ MOLAR_MASS = (2 * _W_N, 2 * _W_O, _W_N + _W_O, _W_N, _W_O)
 DIATOMIC = (True, True, True, False, False)
 # formation enthalpies per mole (J/mol; N2 and O2 are the references), per kg below
 _H0_MOLAR = (0.0, 0.0, 90291.0, 472680.0, 249175.0)
+# characteristic vibrational temperatures (K) of N2, O2, NO (harmonic oscillators; atoms 0),
+# the standard values of Park's air model
+THETA_V = (3395.0, 2239.0, 2817.0, 0.0, 0.0)
 ATOMS_N = (2, 0, 1, 1, 0)
 ATOMS_O = (0, 2, 1, 0, 1)
 
@@ -284,18 +287,23 @@ def air5_mechanism(seed: int = 1, lg10A=(12.0, 22.0), b=(-1.6, 0.0), Ta=(2.0e4, 
         ta.append(Ta[0] + (Ta[1] - Ta[0]) * r[8 * i + 2])
         kc.append([-1.0 + 2.0 * r[8 * i + 3], -5.0 + 10.0 * r[8 * i + 4], -1.0 + 2.0 * r[8 * i + 5],
                    -5.0 * r[8 * i + 6], -0.2 + 0.4 * r[8 * i + 7]])
+    # two-temperature data: vibrational temperatures, and the controlling temperature of each
+    # reaction -- sqrt(T Tv) for the 15 dissociations, T for the two exchanges
     return {"n_species": ns, "n_reactions": nr, "W": list(MOLAR_MASS), "R": Rs, "cv": cv, "h0": h0,
-            "lnA": lnA, "b": bb, "Ta": ta, "kc": kc, "nu_f": nu_f, "nu_b": nu_b}
+            "lnA": lnA, "b": bb, "Ta": ta, "kc": kc, "nu_f": nu_f, "nu_b": nu_b,
+            "theta_v": list(THETA_V), "ta_mode": [1] * 15 + [0, 0]}
 
 
-def reacting_conserved(rho_s, vel, T, mech: dict) -> np.ndarray:
+def reacting_conserved(rho_s, vel, T, mech: dict, Tv=None) -> np.ndarray:
     """Conserved reacting state (rho_1..rho_ns, rho u, ..., E) from partial densities, velocity
     components and temperature of calorically perfect species:
-    E = sum_s rho_s (cv_s T + h0_s) + rho |u|^2 / 2."""
+    E = sum_s rho_s (cv_s T + h0_s) + rho |u|^2 / 2.  With a vibrational temperature Tv
+    (two-temperature state): E_v = sum_s rho_s R_s theta_s / (exp(theta_s / Tv) - 1) is
+    appended and added to E."""
     ns = int(mech["n_species"])
     rho = sum(np.asarray(rho_s[s], dtype=np.float64) for s in range(ns))
     shape = np.shape(rho)
-    U = np.zeros((ns + len(vel) + 1,) + shape)
+    U = np.zeros((ns + len(vel) + 1 + (0 if Tv is None else 1),) + shape)
     e = np.zeros(shape)
     for s in range(ns):
         U[s] = rho_s[s]
@@ -305,16 +313,27 @@ def reacting_conserved(rho_s, vel, T, mech: dict) -> np.ndarray:
         U[ns + d] = rho * v
         kin = kin + v * v
     U[ns + len(vel)] = e + 0.5 * rho * kin
+    if Tv is not None:
+        Ev = np.zeros(shape)
+        for s in range(ns):
+            th = mech["theta_v"][s]
+            if th > 0.0:
+                Ev = Ev + U[s] * mech["R"][s] * th / np.expm1(th / Tv)
+        U[ns + len(vel)] += Ev
+        U[ns + len(vel) + 1] = Ev
     return U
 
 
 def reacting_tgv_3d(nel: int, xi: np.ndarray, mech: dict, seed: int = 2, U0: float = 100.0,
-                    p0: float = 101325.0, lo=(0.0, 0.0, 0.0), hi=None):
+                    p0: float = 101325.0, lo=(0.0, 0.0, 0.0), hi=None, two_temperature: bool = False):
     """The reacting workload's state (9 conserved variables rho_s, rho u, rho v, rho w, E):
     Taylor-Green velocity of amplitude U0 on [0, 2 pi]^3 m, uniform p0, temperature
     T = 5000 + 3000 phi/max|phi| K with phi a seeded Fourier sum (|k| <= 3), air mass
     fractions Y = (0.767, 0.233, 1e-10, 1e-10, 1e-10) normalised.  E from the calorically
-    perfect mixture: E = sum_s rho_s (cv_s T + h0_s) + rho |u|^2 / 2, p = sum_s rho_s R_s T."""
+    perfect mixture: E = sum_s rho_s (cv_s T + h0_s) + rho |u|^2 / 2, p = sum_s rho_s R_s T.
+    two_temperature: a tenth variable E_v at a lagging vibrational temperature
+    Tv = T (0.6 + 0.3 psi), psi a second seeded Fourier sum scaled to [-1, 1] (seed + 7), so
+    Tv spans 0.3 T to 0.9 T (vibration behind the translational mode, as behind a shock)."""
     if hi is None:
         hi = (2 * math.pi,) * 3
     X = node_coordinates(3, (nel, nel, nel), lo, hi, xi)
@@ -327,7 +346,10 @@ def reacting_tgv_3d(nel: int, xi: np.ndarray, mech: dict, seed: int = 2, U0: flo
     u = U0 * np.sin(x) * np.cos(y) * np.cos(z)
     v = -U0 * np.cos(x) * np.sin(y) * np.cos(z)
     w = np.zeros_like(x)
-    return reacting_conserved([rho * Y[s] for s in range(5)], [u, v, w], T, mech)
+    Tv = None
+    if two_temperature:
+        Tv = T * (0.6 + 0.3 * fourier_field_3d_tensor(seed + 7, (nel, nel, nel), xi, lo, hi, 3))
+    return reacting_conserved([rho * Y[s] for s in range(5)], [u, v, w], T, mech, Tv=Tv)
 
 
 AIR_Y = (0.767, 0.233, 1e-10, 1e-10, 1e-10)
