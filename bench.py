@@ -451,11 +451,12 @@ def run_reacting(args):
     dt = 1e-13
     steps = max(3, args.steps // 10)
 
-    def timed(precision, bc=(0,) * 6, bc_state=None):
+    def timed(precision, bc=(0,) * 6, bc_state=None, tt=False):
         S = dgsem.Solver(dgsem.Mesh(3, n_deg, (nel,) * 3, (0.0,) * 3, (2 * math.pi,) * 3, bc=bc, bc_state=bc_state),
                          equations=dgsem.DG_NS_REACTING, mu=mu, prandtl=0.72, mechanism=mech,
-                         precision=precision, p_ref=101325.0 if precision == dgsem.FP32_MIXED else 0.0)
-        S.set_state(U)
+                         precision=precision, p_ref=101325.0 if precision == dgsem.FP32_MIXED else 0.0,
+                         two_temperature=tt)
+        S.set_state(U_tt if tt else U)
         S.rk_step(dt, 3)
         S.check()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -476,6 +477,12 @@ def run_reacting(args):
              dgsem.BC_NOSLIP_ADIABATIC, dgsem.BC_NOSLIP_ISOTHERMAL, dgsem.BC_SLIP_WALL)
     wall_T = (None, (6200.0,), None, None, (4300.0,), None)
     msw, _ = timed(dgsem.FP64, walls, wall_T)
+    # the two-temperature model on the same workload: E_v at a lagging T_v, Landau-Teller
+    # exchange, dissociation at sqrt(T T_v)
+    U_tt = torch.from_numpy(wl.reacting_tgv_3d(nel, x, mech, two_temperature=True).reshape(10, -1)).cuda()
+    ms_tt, dof_tt = timed(dgsem.FP64, tt=True)
+    ms_tt32, _ = timed(dgsem.FP32_MIXED, tt=True)
+    del U_tt
     state_bytes = dof * 8
     alg = (16 + 24 + 24) / 3.0 * dof  # stage update bytes per average stage, as for Euler
     peak, kind = measured_peaks()
@@ -490,6 +497,12 @@ def run_reacting(args):
             "fp32_mixed": {"ms_per_step": ms32, "value": 3 * dof / (ms32 * 1e-3), "unit": "DOF-updates/s",
                            "note": "fluxes, gradients, viscous terms in FP32 (momentum flux shifted by "
                                    "p_ref = 101325 Pa); mixture state, Arrhenius source, update FP64"},
+            "two_temperature": {"dof": dof_tt, "ms_per_step": ms_tt, "value": 3 * dof_tt / (ms_tt * 1e-3),
+                                "unit": "DOF-updates/s", "cost_ratio": ms_tt / ms,
+                                "fp32_mixed": {"ms_per_step": ms_tt32, "value": 3 * dof_tt / (ms_tt32 * 1e-3)},
+                                "note": "10 variables (E_v); T_v by Newton per node per stage, Landau-Teller "
+                                        "with Millikan-White + Park, 15 dissociations at sqrt(T T_v); FP64 "
+                                        "and FP32-mixed"},
             "closed_box": {"ms_per_step": msw, "value": 3 * dof / (msw * 1e-3), "unit": "DOF-updates/s",
                            "cost_ratio": msw / ms,
                            "note": "FP64; x: slip / isothermal 6200 K, y: no-slip adiabatic, z: isothermal "

@@ -61,7 +61,8 @@ typedef enum {
   DG_EPOSITIVITY = -5,  /* a kernel read a state with rho <= 0 or p <= 0 */
   DG_EUNSUPPORTED = -6, /* valid but not implemented (e.g. non-periodic boundaries) */
   DG_ETOOLARGE = -7,    /* more instances than dg_max_dt_noalloc's static scratch holds */
-  DG_ECONVERGENCE = -8  /* a node's implicit-source Newton iteration did not converge */
+  DG_ECONVERGENCE = -8  /* a node's Newton iteration (implicit source, or the vibrational
+                        * temperature of the two-temperature model) did not converge */
 } dg_status;
 
 /* Equations.  DG_NAVIER_STOKES is the single-gas, non-dimensional case (R = 1, so T = p/rho,
@@ -168,6 +169,11 @@ typedef struct dg_mechanism {
   double kc[DG_MAX_REACTIONS][5];
   int nu_f[DG_MAX_REACTIONS][DG_MAX_SPECIES];
   int nu_b[DG_MAX_REACTIONS][DG_MAX_SPECIES];
+  /* Two-temperature model only (dg_physics.two_temperature; ignored otherwise): */
+  double theta_v[DG_MAX_SPECIES];     /* characteristic vibrational temperature, K (>= 0; 0 for
+                                       * atoms): e_v,s(T) = R_s theta / (exp(theta / T) - 1) */
+  int ta_mode[DG_MAX_REACTIONS];      /* 1: the reaction's controlling temperature is
+                                       * T_a = sqrt(T T_v) (dissociation), 0: T_a = T */
 } dg_mechanism;
 
 typedef struct {
@@ -200,6 +206,19 @@ typedef struct {
   double alpha_min; /* blending below this is cut to 0 (<= 0: DG_ALPHA_MIN) */
   double alpha_max; /* blending is capped here (<= 0: DG_ALPHA_MAX) */
   double sharpness; /* steepness s of the sigmoid (<= 0: ln 9999) */
+  /* Two-temperature model (Sec. 2 "Thermal nonequilibrium coupling" and "Total energy and
+   * closure"; Sec. 3.1.3 Eqs. src_vector, src_reaction_rate, src_landau_teller): DG_NS_REACTING
+   * with 5 species, periodic meshes, no Strang split (else DG_EUNSUPPORTED).  The state gains
+   * E_v, U = (rho_1..rho_ns, rho u, rho v, rho w, E, E_v); cv_s is the translational-rotational
+   * heat capacity and E = sum rho_s (cv_s T + h0_s) + E_v + rho|u|^2/2; T_v solves
+   * E_v = sum rho_s e_v,s(T_v) (harmonic oscillators of chem->theta_v); the E_v flux is E_v u,
+   * the vibrational heat flux -k_v grad T_v (k_v = mu c_v,v / Pr, c_v,v = dE_v/dT_v / rho)
+   * enters the E and E_v rows; reaction r runs at its controlling temperature (ta_mode) with
+   * k_b = k_f / K_c(T_a); the E_v source is Q_T-v + sum_s omega_s e_v,s(T_v) with the
+   * Landau-Teller Q_T-v = sum rho_s (e_v,s(T) - e_v,s(T_v)) / tau_s, tau_s the Millikan-White
+   * relaxation time plus Park's high-temperature term.  A node whose T_v iteration does not
+   * converge sets DG_ECONVERGENCE. */
+  int two_temperature;  /* 0: single temperature; 1: two-temperature */
 } dg_physics;
 
 /* Build a context for n_inst instances (all of the same dim) sharing one physics
@@ -340,7 +359,8 @@ DG_API dg_status dg_max_dt_noalloc(const dg_mesh_desc* inst, int n_inst, double 
                                    double* dt_out, const char** msg);
 
 /* Implicit source substep S_h of the Strang split (Sec. 3.1.3, Eqs. strang_split and
- * source_residual), DG_NS_REACTING contexts only.  At every node the partial densities
+ * source_residual), single-temperature DG_NS_REACTING contexts only (else DG_EUNSUPPORTED).
+ * At every node the partial densities
  * Y = (rho_1..rho_ns) take one backward-Euler step of length h >= 0 of the chemical source,
  *   Y* - Y - h omega(Y*) = 0,
  * solved by Newton's method from Y* = Y: the Jacobian by forward differences, column k with

@@ -26,6 +26,7 @@ struct dg_ctx {
   int cur = 0;                       // index of the buffer holding the current state
   bool rk54 = false;                 // SSP-RK54 (the state stays in buf[cur]); else SSP-RK3
   bool split = false;                // Strang-split implicit source (reacting)
+  int tt = 0;                        // two-temperature model (reacting)
   unsigned* err = nullptr;
   unsigned long long* lam = nullptr;  // [0..1] time-step reductions, [2] Newton update count
   std::string msg;
@@ -193,7 +194,12 @@ void fill_exp2_table(double* tab) {
   for (int j = 0; j < 64; ++j) tab[j] = (double)std::exp2((long double)j / 64.0L);
 }
 
-dg_status pack_mechanism(const dg_mechanism& m, dg::MechDev& d, std::string& why) {
+// tt: the two-temperature model -- vibrational temperatures (>= 0, one at least > 0), each
+// reaction's controlling-temperature flag, and the Millikan-White coefficients of every
+// (vibrating species s, collision partner r) pair: A_sr = 1.16e-3 mu_sr^1/2 theta_s^4/3,
+// B_sr = 0.015 mu_sr^1/4 (mu_sr the reduced molar mass in g/mol), stored as A_sr and
+// C_sr = A_sr B_sr + 18.42 (Millikan and White, J. Chem. Phys. 39, 1963).
+dg_status pack_mechanism(const dg_mechanism& m, dg::MechDev& d, int tt, std::string& why) {
   std::memset(&d, 0, sizeof(d));
   if (m.n_species < 1 || m.n_species > DG_MAX_SPECIES || m.n_reactions < 0 ||
       m.n_reactions > DG_MAX_REACTIONS) {
@@ -240,6 +246,28 @@ dg_status pack_mechanism(const dg_mechanism& m, dg::MechDev& d, std::string& why
       }
       x.coef[s] = m.W[s] * 1.0e6 * (double)(m.nu_b[r][s] - m.nu_f[r][s]);
     }
+    if (tt) {
+      if (m.ta_mode[r] != 0 && m.ta_mode[r] != 1) { why = "ta_mode must be 0 or 1"; return DG_EINVAL; }
+      x.ta = m.ta_mode[r];
+    }
+  }
+  if (tt) {
+    bool any = false;
+    for (int s = 0; s < ns; ++s) {
+      if (!(m.theta_v[s] >= 0.0) || !std::isfinite(m.theta_v[s])) { why = "theta_v must be finite and >= 0"; return DG_EINVAL; }
+      d.theta[s] = m.theta_v[s];
+      any = any || m.theta_v[s] > 0.0;
+    }
+    if (!any) { why = "the two-temperature model needs a vibrating species"; return DG_EINVAL; }
+    for (int s = 0; s < ns; ++s)
+      for (int r = 0; r < ns; ++r) {
+        if (!(d.theta[s] > 0.0)) continue;
+        const double Ws = m.W[s] * 1.0e3, Wr = m.W[r] * 1.0e3;
+        const double mu = Ws * Wr / (Ws + Wr);
+        const double A = 1.16e-3 * std::sqrt(mu) * std::pow(d.theta[s], 4.0 / 3.0);
+        d.mwA[s][r] = A;
+        d.mwC[s][r] = A * 0.015 * std::pow(mu, 0.25) + 18.42;
+      }
   }
   return DG_OK;
 }
@@ -523,7 +551,7 @@ constexpr int kScratch = 4;  // primitive cache slot of states that are not cont
 dg_status fill_prims(dg_ctx* c, const double* U, int k, cudaStream_t s) {
   const int fp32 = c->phys.precision == DG_FP32_MIXED;
   for (size_t i = 0; i < c->inst.size(); ++i) {
-    cudaError_t e = dg::launch_react_prims(c->n_species, fp32, U, c->n_nodes_total, c->offs[i],
+    cudaError_t e = dg::launch_react_prims(c->n_species, c->tt, fp32, U, c->n_nodes_total, c->offs[i],
                                            n_elem_of(c->inst[i]) * n_p_of(c->inst[i]), c->d_mech,
                                            c->phys.p_ref, c->pc[k], c->pT[k], c->err, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "primitive cache launch");
@@ -595,7 +623,7 @@ dg_status run_stage_ns(dg_ctx* c, const double* U, const double* Un, double* out
     gll_table(m.N, x, w, a.D);
     a.lift = 1.0 / w[0];
     a.liftf = (float)a.lift;
-    cudaError_t e = dg::launch_reacting(m.N, c->n_species, fp32, a, s);
+    cudaError_t e = dg::launch_reacting(m.N, c->n_species, c->tt, fp32, a, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "Navier-Stokes stage launch");
   }
   return DG_OK;
@@ -989,6 +1017,14 @@ dg_status dg_init_mesh(const dg_mesh_desc* inst, int n_inst, const dg_physics* p
       return DG_EINVAL;
   }
   const bool navier_stokes = phys->equations != DG_EULER;
+  const int tt = phys->two_temperature;
+  if (tt != 0 && tt != 1) return DG_EINVAL;
+  if (tt) {  // two-temperature: reacting air on periodic meshes, source in the residual
+    if (phys->equations != DG_NS_REACTING || phys->chem_split) return DG_EUNSUPPORTED;
+    for (int i = 0; i < n_inst; ++i)
+      for (int l = 0; l < 3; ++l)
+        if (inst[i].periodic[l] != 1) return DG_EUNSUPPORTED;
+  }
   dg::MechDev mech;
   std::vector<dg::ReactBC> rbc;
   if (navier_stokes) {
@@ -997,7 +1033,7 @@ dg_status dg_init_mesh(const dg_mesh_desc* inst, int n_inst, const dg_physics* p
       return DG_EINVAL;
     if (phys->equations == DG_NS_REACTING) {
       if (!phys->chem) return DG_EINVAL;
-      dg_status st = pack_mechanism(*phys->chem, mech, why);
+      dg_status st = pack_mechanism(*phys->chem, mech, tt, why);
       if (st) return st;
     } else {
       dg_mechanism one;
@@ -1006,12 +1042,12 @@ dg_status dg_init_mesh(const dg_mesh_desc* inst, int n_inst, const dg_physics* p
       one.W[0] = 1.0;
       one.R[0] = 1.0;
       one.cv[0] = 1.0 / (phys->gamma - 1.0);
-      dg_status st = pack_mechanism(one, mech, why);
+      dg_status st = pack_mechanism(one, mech, 0, why);
       if (st) return st;
     }
     if (inst[0].dim != 3) return DG_EUNSUPPORTED;
     for (int i = 0; i < n_inst; ++i)
-      if (!dg::have_reacting(inst[i].N, mech.ns)) return DG_EUNSUPPORTED;
+      if (!dg::have_reacting(inst[i].N, mech.ns, tt)) return DG_EUNSUPPORTED;
     rbc.resize(n_inst);
     for (int i = 0; i < n_inst; ++i)
       if (!react_bc(inst[i], mech, phys->p_ref, rbc[i], why)) return DG_EINVAL;
@@ -1028,7 +1064,8 @@ dg_status dg_init_mesh(const dg_mesh_desc* inst, int n_inst, const dg_physics* p
   c->dim = inst[0].dim;
   c->ns = navier_stokes;
   c->n_species = navier_stokes ? mech.ns : 0;
-  c->nv = navier_stokes ? mech.ns + 4 : c->dim + 2;
+  c->nv = navier_stokes ? mech.ns + 4 + tt : c->dim + 2;
+  c->tt = tt;
   long long off = 0;
   for (int i = 0; i < n_inst; ++i) {
     c->offs.push_back(off);
@@ -1063,7 +1100,7 @@ dg_status dg_init_mesh(const dg_mesh_desc* inst, int n_inst, const dg_physics* p
     long long nfb = 0;
     for (int i = 0; i < n_inst; ++i) {
       c->fb_offs.push_back(nfb);
-      nfb += n_elem_of(inst[i]) * 6 * 4 * (long long)(inst[i].N + 1) * (inst[i].N + 1);
+      nfb += n_elem_of(inst[i]) * 6 * (4 + tt) * (long long)(inst[i].N + 1) * (inst[i].N + 1);
     }
     if (cudaMalloc(&c->d_mech, sizeof(dg::MechDev)) != cudaSuccess ||
         cudaMalloc(&c->fb, sizeof(double) * (size_t)nfb) != cudaSuccess) {
@@ -1074,8 +1111,8 @@ dg_status dg_init_mesh(const dg_mesh_desc* inst, int n_inst, const dg_physics* p
     const size_t rsz = phys->precision == DG_FP32_MIXED ? sizeof(float) : sizeof(double);
     for (int k = 0; k < 5; ++k) {
       if (k == 3 && !c->rk54) continue;
-      if (cudaMalloc(&c->pc[k], 7 * rsz * (size_t)off) != cudaSuccess ||
-          cudaMalloc(&c->pT[k], sizeof(double) * (size_t)off) != cudaSuccess) {
+      if (cudaMalloc(&c->pc[k], dg::react_cache_rows(tt) * rsz * (size_t)off) != cudaSuccess ||
+          cudaMalloc(&c->pT[k], dg::react_t64_rows(tt) * sizeof(double) * (size_t)off) != cudaSuccess) {
         cudaGetLastError();
         dg_free(c);
         return DG_ENOMEM;
@@ -1087,7 +1124,7 @@ dg_status dg_init_mesh(const dg_mesh_desc* inst, int n_inst, const dg_physics* p
       return DG_ECUDA;
     }
     for (int i = 0; i < n_inst; ++i) {
-      if (dg::prepare_reacting(inst[i].N, mech.ns, phys->precision == DG_FP32_MIXED) != cudaSuccess) {
+      if (dg::prepare_reacting(inst[i].N, mech.ns, tt, phys->precision == DG_FP32_MIXED) != cudaSuccess) {
         cudaGetLastError();
         dg_free(c);
         return DG_ECUDA;
@@ -1400,7 +1437,7 @@ dg_status dg_max_dt(dg_ctx* c, double cfl, double* dt_out) {
       const dg_mesh_desc& m = c->inst[i];
       cudaError_t e = cudaMemsetAsync(c->lam, 0, 2 * sizeof(unsigned long long), c->stream);
       if (e == cudaSuccess)
-        e = dg::launch_max_speed_mix(c->n_species, c->buf[c->cur], c->n_nodes_total, c->offs[i],
+        e = dg::launch_max_speed_mix(c->n_species, c->tt, c->buf[c->cur], c->n_nodes_total, c->offs[i],
                                      n_elem_of(m) * n_p_of(m), c->d_mech, c->lam, c->stream);
       unsigned long long bits[2] = {0, 0};
       if (e == cudaSuccess)
@@ -1483,6 +1520,7 @@ dg_status dg_source_step(dg_ctx* c, const double* U, double h, double* Uout) {
   if (!U || !Uout) return fail(c, DG_EINVAL, "null pointer");
   if (c->phys.equations != DG_NS_REACTING)
     return fail(c, DG_EUNSUPPORTED, "the implicit source step exists for reacting mixtures");
+  if (c->tt) return fail(c, DG_EUNSUPPORTED, "the implicit source step is single-temperature");
   if (!std::isfinite(h) || h < 0.0) return fail(c, DG_EINVAL, "h must be finite and >= 0");
   return run_source(c, U, Uout, h, c->stream);
 }

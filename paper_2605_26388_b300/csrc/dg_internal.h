@@ -183,7 +183,9 @@ struct RxnDev {
   double kc[5];                // ln K_c = kc0 / Z + kc1 + kc2 ln Z + kc3 Z + kc4 Z^2
   double coef[kMaxSpecies];    // W_s * 1e6 * (nu''_s - nu'_s): mol/(cm^3 s) -> kg/(m^3 s)
   int f[3], bk[3];             // species of the forward / backward concentration products;
-  int pad[2];                  //   index n_species stands for the factor 1
+                               //   index n_species stands for the factor 1
+  int ta;                      // two-temperature: 1 -- rates at T_a = sqrt(T Tv), 0 -- at T
+  int pad;
 };
 
 struct MechDev {
@@ -191,6 +193,9 @@ struct MechDev {
   int pad[2];
   double R[kMaxSpecies], cv[kMaxSpecies], h0[kMaxSpecies];
   double scale[kMaxSpecies];   // 1e-6 / W_s: rho_s (kg/m^3) -> [X_s] (mol/cm^3)
+  double theta[kMaxSpecies];   // two-temperature: vibrational temperature (0: atom)
+  // two-temperature, Millikan-White: 1 / tau_sr = (p / 1 atm) exp(mwC[s][r] - mwA[s][r] T^-1/3)
+  double mwA[kMaxSpecies][kMaxSpecies], mwC[kMaxSpecies][kMaxSpecies];
   double exp2tab[64];          // 2^(j/64), j = 0..63, for the table-driven exp of the rates
   RxnDev rx[kMaxReactions];
 };
@@ -236,16 +241,21 @@ struct ReactArgs {
   ReactBC bnd;          // boundary conditions of the instance
 };
 
-// Whether the reacting kernels exist for degree N and n_species.
-bool have_reacting(int N, int ns);
+// Whether the reacting kernels exist for degree N, n_species and the temperature model
+// (tt = 1: two-temperature).
+bool have_reacting(int N, int ns, int tt);
 // Kernel attributes (dynamic shared memory); call before the first launch, outside capture.
-cudaError_t prepare_reacting(int N, int ns, int fp32);
+cudaError_t prepare_reacting(int N, int ns, int tt, int fp32);
 // One stage (or residual) over one instance: the BR1 face pass, then the fused stage; fp32
 // selects FP32 flux arithmetic (mixture, source and update stay FP64).
-cudaError_t launch_reacting(int N, int ns, int fp32, const ReactArgs& a, cudaStream_t s);
-// Primitive cache (u, v, w, T, p - p_ref, a, c_p in the flux type; T in FP64) of the nodes
-// [base, base + n_nodes) of a state; flags rho <= 0 or T <= 0 in *err.
-cudaError_t launch_react_prims(int ns, int fp32, const double* U, long long stride, long long base,
+cudaError_t launch_reacting(int N, int ns, int tt, int fp32, const ReactArgs& a, cudaStream_t s);
+// Rows of the primitive cache (flux type): u, v, w, T, p - p_ref, a, c_p; two-temperature:
+// u, v, w, T, T_v, p - p_ref, a, c_p, c_v,v.  FP64 rows: T (and T_v).
+inline int react_cache_rows(int tt) { return tt ? 9 : 7; }
+inline int react_t64_rows(int tt) { return tt ? 2 : 1; }
+// Primitive cache of the nodes [base, base + n_nodes) of a state; flags rho <= 0 or T <= 0
+// (bit 1) and an unconverged T_v iteration (bit 2) in *err.
+cudaError_t launch_react_prims(int ns, int tt, int fp32, const double* U, long long stride, long long base,
                                long long n_nodes, const MechDev* mech, double p_ref, void* P, double* T64,
                                unsigned* err, cudaStream_t s);
 // Implicit source substep (Strang split) over the nodes [base, base + n) of a state.
@@ -279,7 +289,7 @@ cudaError_t launch_math_fn(const MathArgs& a, cudaStream_t s);
 
 // Largest |u| + a (frozen mixture sound speed) and largest 1/rho over one instance,
 // atomically max-ed into out2[0] and out2[1] (bit patterns of non-negative doubles).
-cudaError_t launch_max_speed_mix(int ns, const double* U, long long stride, long long base,
+cudaError_t launch_max_speed_mix(int ns, int tt, const double* U, long long stride, long long base,
                                  long long n_nodes, const MechDev* mech,
                                  unsigned long long* out2, cudaStream_t s);
 

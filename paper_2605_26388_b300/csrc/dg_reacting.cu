@@ -42,11 +42,18 @@ namespace dg {
 namespace {
 
 constexpr int kRT = 128;
-constexpr int NPR = 6;  // staged primitives per node: u, v, w, T, p - p_ref, a
 
-template <int N, int NS, class R>
+// Per-launch geometry.  TT: the two-temperature model (E_v appended to the state, T_v a
+// gradient variable, E_v a viscous flux row).
+template <int N, int NS, bool TT, class R>
 struct RG {
-  static constexpr int N1 = N + 1, NP = N1 * N1 * N1, NFN = N1 * N1, NV = NS + 4;
+  static constexpr int N1 = N + 1, NP = N1 * N1 * N1, NFN = N1 * N1;
+  static constexpr int NV = NS + 4 + (TT ? 1 : 0);
+  static constexpr int NW = TT ? 5 : 4;    // gradient variables: u, v, w, T (, T_v)
+  static constexpr int NFV = NW;           // viscous face flux rows: 3 momenta, E (, E_v)
+  static constexpr int NPR = NW + 2;       // staged primitives: u, v, w, T (, T_v), p - p_ref, a
+  static constexpr int RPD = NW, RA = NW + 1, RCP = NW + 2, RCV = NW + 3;  // cache rows
+  static constexpr int NSP = TT ? 5 : 4;   // species table rows: R, cv, h0, 1e-6/W (, theta)
   static constexpr int EPB = kRT / NP;
   static constexpr int NFJ = 6 * NFN;  // face nodes of one element
   static constexpr int NSL = NS + 1;   // concentration slots (last one holds 1.0)
@@ -55,13 +62,14 @@ struct RG {
   static constexpr int E_UT = E_US + NV * NP;           // nbr U traces [6][NV][NFN] -> lifts
   static constexpr int E_P = E_UT + 6 * NV * NFN;       // primitives   [NPR][NP]
   static constexpr int E_PT = E_P + NPR * NP;           // nbr prims    [6][NPR][NFN]
-  static constexpr int E_FT = E_PT + 6 * NPR * NFN;     // nbr F_v      [6][4][NFN]
-  static constexpr int E_FO = E_FT + 24 * NFN;          // own F_v      [6][4][NFN]
-  static constexpr int E_H = E_FO + 24 * NFN;           // F^l - F_v^l  [NV][NP]
+  static constexpr int E_FT = E_PT + 6 * NPR * NFN;     // nbr F_v      [6][NFV][NFN]
+  static constexpr int E_FO = E_FT + 6 * NFV * NFN;     // own F_v      [6][NFV][NFN]
+  static constexpr int E_H = E_FO + 6 * NFV * NFN;      // F^l - F_v^l  [NV][NP]
   static constexpr int E_SIZE = E_H + NV * NP;
   // stage kernel, per CTA: species table, exp table, concentration slots (double), D (R)
-  static constexpr int C_SP = 0;                        // R, cv, h0, scale [4][NS]
-  static constexpr int C_E2 = C_SP + 4 * NS;            // 2^(j/64) [64]
+  static constexpr int C_SP = 0;                        // species table [NSP][NS]
+  static constexpr int C_MW = C_SP + 5 * 8;             // TT: Millikan-White A, C [2][NS][NS]
+  static constexpr int C_E2 = C_MW + 2 * 8 * 8;         // 2^(j/64) [64]
   static constexpr int C_X = C_E2 + 64;                 // [NSL][kRT]
   static constexpr int C_DBL = C_X + NSL * kRT;
   static constexpr size_t stage_smem() {
@@ -121,15 +129,70 @@ __device__ __forceinline__ T pick3(int l, T a, T b, T c) {
   return l == 0 ? a : (l == 1 ? b : c);
 }
 
-// Mixture state of one node, FP64 (calorically perfect species, single temperature):
-// T = (E - rho|u|^2/2 - sum rho_s h0_s) / sum rho_s cv_s, p = T sum rho_s R_s,
-// frozen sound speed a^2 = (1 + sum rho_s R_s / sum rho_s cv_s) p / rho, c_p of the mixture.
+// Mixture state of one node, FP64 (calorically perfect species):
+// T = (E - E_v - rho|u|^2/2 - sum rho_s h0_s) / sum rho_s cv_s (E_v = 0 for one temperature),
+// p = T sum rho_s R_s, frozen sound speed a^2 = (1 + sum rho_s R_s / sum rho_s cv_s) p / rho,
+// c_p of the mixture; two-temperature: T_v with E_v(T_v) = E_v and c_v,v = dE_v/dT_v / rho.
 struct Mx {
-  double rho, v[3], T, p, a, cp;
+  double rho, v[3], T, p, a, cp, Tv, cvv;
+  bool conv;  // the T_v iteration converged
 };
 
+// Two-temperature: the vibrational temperature of the partial densities u[0..NS) with
+// E_v(T_v) = sum rho_s R_s theta_s / (exp(theta_s / T_v) - 1) = Ev (harmonic oscillators;
+// sp: species table, row 0 R_s, row 4 theta_s), by Newton's method from x0 (the node's T_v of
+// the previous stage when known; else the exact inverse for the (rho R)-weighted mean theta);
+// steps are limited to a factor 2 either way (E_v grows strictly with T_v, so the iterate
+// stays positive and approaches the single root); stops after a step |dT_v| <= 1e-13 T_v, at
+// most 50 updates.  Also returns rho c_v,v = dE_v/dT_v (at the last iterate but one, within
+// 1e-13 relative of the root's).  exp by the table-driven exp_tab (e2tab).
 template <int NS>
-__device__ __forceinline__ Mx mixture(const double* u, const double* sp) {
+__device__ __forceinline__ double vib_temperature(const double* u, const double* sp, double Ev, double x0,
+                                                  const double* e2tab, double& dEv, bool& conv) {
+  double x = x0;
+  if (!(x0 > 0.0)) {
+    double rR = 0.0, rRt = 0.0;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      const double th = sp[4 * NS + s];
+      if (th > 0.0) {
+        rR = fma(u[s], sp[s], rR);
+        rRt = fma(u[s] * sp[s], th, rRt);
+      }
+    }
+    x = rRt * rcp64(rR) / log1p(rRt / Ev);
+  }
+  conv = false;
+  dEv = 0.0;
+  for (int it = 0; it < 50; ++it) {
+    double f = -Ev, df = 0.0;
+    const double ix = rcp64(x);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      const double th = sp[4 * NS + s];
+      if (th > 0.0) {
+        const double y = th * ix, ey = exp_tab(y, e2tab), iem = rcp64(ey - 1.0);
+        const double e = u[s] * sp[s] * th * iem;
+        f += e;
+        df = fma(e * y * ix, ey * iem, df);
+      }
+    }
+    dEv = df;
+    double xn = fma(-f, rcp64(df), x);
+    xn = fmin(fmax(xn, 0.5 * x), 2.0 * x);
+    const bool done = fabs(xn - x) <= 1e-13 * x;
+    x = xn;
+    if (done) {
+      conv = true;
+      break;
+    }
+  }
+  return x;
+}
+
+template <int NS, bool TT>
+__device__ __forceinline__ Mx mixture(const double* u, const double* sp, double tv_guess = 0.0,
+                                      const double* e2tab = nullptr) {
   double rho = 0.0, rR = 0.0, rcv = 0.0, rh0 = 0.0;
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
@@ -148,33 +211,51 @@ __device__ __forceinline__ Mx mixture(const double* u, const double* sp) {
     kin = fma(u[NS + d], m.v[d], kin);
   }
   const double ircv = rcp64(rcv);
-  m.T = (u[NS + 3] - 0.5 * kin - rh0) * ircv;
+  const double Ev = TT ? u[NS + 4] : 0.0;
+  m.T = (u[NS + 3] - Ev - 0.5 * kin - rh0) * ircv;
   m.p = rR * m.T;
   m.a = sqrt(fma(rR, ircv, 1.0) * m.p * irho);
   m.cp = (rcv + rR) * irho;
+  m.Tv = m.T;
+  m.cvv = 0.0;
+  m.conv = true;
+  if constexpr (TT) {
+    double dEv;
+    m.Tv = vib_temperature<NS>(u, sp, Ev, tv_guess, e2tab, dEv, m.conv);
+    m.cvv = dEv * irho;
+  }
   return m;
 }
 
-// Mixture state of one node into the primitive cache (R rows u, v, w, T, p - p_ref, a, c_p at
-// stride `stride`, T in FP64); returns the positivity flag (rho > 0 and T > 0, in FP64).
-template <int NS, class R>
+// Mixture state of one node into the primitive cache (R rows u, v, w, T (, T_v), p - p_ref,
+// a, c_p (, c_v,v) at stride `stride`; T (and T_v) in FP64); returns the flags: 2 -- rho <= 0
+// or T <= 0 (or T_v <= 0), in FP64; 4 -- the T_v iteration did not converge.
+template <int NS, bool TT, class R>
 __device__ __forceinline__ unsigned write_prims(const double* u, const double* sp, double p_ref, R* P,
-                                                double* T64, long long stride, long long gi) {
-  const Mx m = mixture<NS>(u, sp);
+                                                double* T64, long long stride, long long gi,
+                                                double tv_guess = 0.0, const double* e2tab = nullptr) {
+  const Mx m = mixture<NS, TT>(u, sp, tv_guess, e2tab);
+  constexpr int W = TT ? 5 : 4;
   P[gi] = Ar<R>::load(m.v[0]);
   P[stride + gi] = Ar<R>::load(m.v[1]);
   P[2 * stride + gi] = Ar<R>::load(m.v[2]);
   P[3 * stride + gi] = Ar<R>::load(m.T);
-  P[4 * stride + gi] = Ar<R>::load(m.p - p_ref);
-  P[5 * stride + gi] = Ar<R>::load(m.a);
-  P[6 * stride + gi] = Ar<R>::load(m.cp);
+  if (TT) P[4 * stride + gi] = Ar<R>::load(m.Tv);
+  P[W * stride + gi] = Ar<R>::load(m.p - p_ref);
+  P[(W + 1) * stride + gi] = Ar<R>::load(m.a);
+  P[(W + 2) * stride + gi] = Ar<R>::load(m.cp);
+  if (TT) P[(W + 3) * stride + gi] = Ar<R>::load(m.cvv);
   T64[gi] = m.T;
-  return (m.rho > 0.0 && m.T > 0.0) ? 0u : 2u;
+  if (TT) T64[stride + gi] = m.Tv;
+  unsigned flag = (m.rho > 0.0 && m.T > 0.0 && m.Tv > 0.0) ? 0u : 2u;
+  if (!m.conv) flag |= 4u;
+  return flag;
 }
 
 // Inviscid flux in direction l (runtime l: no dynamic register indexing); the momentum rows
-// carry pd = p - p_ref, the energy row (E + p) v_l with p = pd + p_ref.
-template <int NS, class R>
+// carry pd = p - p_ref, the energy row (E + p) v_l with p = pd + p_ref; two-temperature: the
+// E_v row E_v v_l.
+template <int NS, bool TT, class R>
 __device__ __forceinline__ void inv_flux(int l, const R* u, R v0, R v1, R v2, R pd, R p_ref, R* F) {
   const R vl = pick3(l, v0, v1, v2);
 #pragma unroll
@@ -183,12 +264,14 @@ __device__ __forceinline__ void inv_flux(int l, const R* u, R v0, R v1, R v2, R 
   F[NS + 1] = u[NS + 1] * vl + (l == 1 ? pd : R(0));
   F[NS + 2] = u[NS + 2] * vl + (l == 2 ? pd : R(0));
   F[NS + 3] = (u[NS + 3] + (pd + p_ref)) * vl;
+  if constexpr (TT) F[NS + 4] = u[NS + 4] * vl;
 }
 
-// Viscous flux in direction L (compile-time) from the gradient S[q][l] of (u, v, w, T):
-// tau_jL = mu (d_L u_j + d_j u_L) - (2/3) mu (div u) delta_jL, energy u . tau_L + k d_L T.
-template <int L, class R>
-__device__ __forceinline__ void visc_flux(const R (&S)[4][3], const R* v, R mu, R kcond, R* Fv) {
+// Viscous flux in direction L (compile-time) from the gradient S[q][l] of (u, v, w, T (, T_v)):
+// tau_jL = mu (d_L u_j + d_j u_L) - (2/3) mu (div u) delta_jL, energy u . tau_L + k d_L T;
+// two-temperature: + k_v d_L T_v in the energy row and the E_v row k_v d_L T_v.
+template <int L, int NW, class R>
+__device__ __forceinline__ void visc_flux(const R (&S)[NW][3], const R* v, R mu, R kcond, R kvib, R* Fv) {
   const R div = S[0][0] + S[1][1] + S[2][2];
   R work = R(0);
 #pragma unroll
@@ -199,15 +282,21 @@ __device__ __forceinline__ void visc_flux(const R (&S)[4][3], const R* v, R mu, 
     work = work + v[j] * t;
   }
   Fv[3] = work + kcond * S[3][L];
+  if constexpr (NW == 5) {
+    const R qv = kvib * S[4][L];
+    Fv[3] = Fv[3] + qv;
+    Fv[4] = qv;
+  }
+  (void)kvib;
 }
 
 // BR1 gradient of W at node q (Eq. br1_avg): for each direction l,
 // (2/dx_l) [ sum_m D_{i_l m} W_m + (upper) (W^ - W_N)/w_N - (lower) (W^ - W_0)/w_0 ],
-// W^ = (W_own + W_nbr)/2.  W: rows c = 0..3 of the element's primitives (row stride NP),
+// W^ = (W_own + W_nbr)/2.  W: rows c = 0..NW-1 of the element's primitives (row stride NP),
 // Wt: the neighbours' face-trace primitives [6][NPR][NFN].
-template <int N, class R>
+template <int N, int NW, int NPR, class R>
 __device__ __forceinline__ void br1_gradient(int q, const R* W, const R* Wt, const R* D, const R* s,
-                                             R lift, R (&S)[4][3]) {
+                                             R lift, R (&S)[NW][3]) {
   constexpr int N1 = N + 1, NFN = N1 * N1, NP = N1 * NFN;
   const int ijk[3] = {q % N1, (q / N1) % N1, q / NFN};
   constexpr int stride_l[3] = {1, N1, NFN};
@@ -215,12 +304,14 @@ __device__ __forceinline__ void br1_gradient(int q, const R* W, const R* Wt, con
   for (int l = 0; l < 3; ++l) {
     const int il = ijk[l];
     const int q0 = q - il * stride_l[l];
-    R acc[4] = {R(0), R(0), R(0), R(0)};
+    R acc[NW];
+#pragma unroll
+    for (int c = 0; c < NW; ++c) acc[c] = R(0);
 #pragma unroll
     for (int m = 0; m < N1; ++m) {
       const R d = D[il * N1 + m];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) acc[c] = acc[c] + d * W[c * NP + q0 + m * stride_l[l]];
+      for (int c = 0; c < NW; ++c) acc[c] = acc[c] + d * W[c * NP + q0 + m * stride_l[l]];
     }
     if (il == N || il == 0) {
       const int side = il == N ? 1 : 0;
@@ -228,10 +319,10 @@ __device__ __forceinline__ void br1_gradient(int q, const R* W, const R* Wt, con
       const R* wt = Wt + (2 * l + side) * NPR * NFN + jf;
       const R h = side ? R(0.5) * lift : R(-0.5) * lift;
 #pragma unroll
-      for (int c = 0; c < 4; ++c) acc[c] = acc[c] + h * (wt[c * NFN] - W[c * NP + q]);
+      for (int c = 0; c < NW; ++c) acc[c] = acc[c] + h * (wt[c * NFN] - W[c * NP + q]);
     }
 #pragma unroll
-    for (int c = 0; c < 4; ++c) S[c][l] = s[l] * acc[c];
+    for (int c = 0; c < NW; ++c) S[c][l] = s[l] * acc[c];
   }
 }
 
@@ -240,11 +331,12 @@ __device__ __forceinline__ void br1_gradient(int q, const R* W, const R* Wt, con
 // such that the BR1 average (Fv + gh)/2 is the boundary's viscous flux (Sec. 3.1.2 boundary
 // kernels): slip wall -- only the normal-stress row survives; no-slip adiabatic -- stress
 // rows kept, energy 0; no-slip isothermal -- stress rows kept, energy = heat; inflow,
-// outflow, Dirichlet -- the interior flux itself.
-template <int L, class R>
+// outflow, Dirichlet -- the interior flux itself.  (Two-temperature meshes are periodic: the
+// E_v row, NFV = 5, never reaches a domain face.)
+template <int L, int NFV, class R>
 __device__ __forceinline__ void ghost_viscous_flux(int type, const R* Fv, R heat, R* gh) {
 #pragma unroll
-  for (int c = 0; c < 4; ++c) gh[c] = Fv[c];
+  for (int c = 0; c < NFV; ++c) gh[c] = Fv[c];
   if (type == 1) {
 #pragma unroll
     for (int c = 0; c < 4; ++c)
@@ -256,32 +348,48 @@ __device__ __forceinline__ void ghost_viscous_flux(int type, const R* Fv, R heat
   }
 }
 
+// Species table rows: R, cv, h0, 1e-6/W (, theta_v).
 template <int NS>
 __device__ __forceinline__ void load_species(const MechDev* __restrict__ mech, double* sp, int n) {
   for (int t = threadIdx.x; t < n * NS; t += blockDim.x) {
     const int k = t / NS, s = t % NS;
-    const double* src = k == 0 ? mech->R : (k == 1 ? mech->cv : (k == 2 ? mech->h0 : mech->scale));
+    const double* src = k == 0 ? mech->R : (k == 1 ? mech->cv : (k == 2 ? mech->h0 : (k == 3 ? mech->scale : mech->theta)));
     sp[t] = src[s];
   }
 }
 
 // Species production rates omega_s of one node (Sec. 3.1.3, Eqs. src_reaction_rate and
-// src_omega; App. C), FP64: k_f = exp(lnA + b ln T - Ta/T), ln K_c from the five-term fit in
-// Z = 1e4/T, R_r = k_f prod [X]^nu' - (k_f / K_c) prod [X]^nu'',
-// omega_s = sum_r W_s 1e6 (nu''_s - nu'_s) R_r.  The concentrations [X_s] sit in this
-// thread's slots X[s * xs] (slot NS holds 1.0, the factor of an empty place in a product).
-template <int NS>
-__device__ __forceinline__ void species_rates(const MechDev* __restrict__ mech, int nr, double T,
+// src_omega; App. C), FP64: k_f = exp(lnA + b ln T_a - Ta/T_a), ln K_c from the five-term fit
+// in Z = 1e4/T_a, R_r = k_f prod [X]^nu' - (k_f / K_c) prod [X]^nu'',
+// omega_s = sum_r W_s 1e6 (nu''_s - nu'_s) R_r, with T_a = T, or (two-temperature, reactions
+// flagged ta) T_a = sqrt(T T_v).  The concentrations [X_s] sit in this thread's slots
+// X[s * xs] (slot NS holds 1.0, the factor of an empty place in a product).
+template <int NS, bool TT>
+__device__ __forceinline__ void species_rates(const MechDev* __restrict__ mech, int nr, double T, double Tv,
                                               const double* X, int xs, const double* e2tab,
                                               double ln1e4, double (&om)[NS]) {
   const double lnT = log(T), invT = rcp64(T);
   const double Z = 1.0e4 * invT, Zi = 1.0e-4 * T, lnZ = ln1e4 - lnT, Z2 = Z * Z;
+  double lnTa = lnT, invTa = invT, Za = Z, Zia = Zi, lnZa = lnZ, Za2 = Z2;
+  if constexpr (TT) {
+    const double Ta = sqrt(T * Tv);
+    lnTa = 0.5 * (lnT + log(Tv));
+    invTa = rcp64(Ta);
+    Za = 1.0e4 * invTa;
+    Zia = 1.0e-4 * Ta;
+    lnZa = ln1e4 - lnTa;
+    Za2 = Za * Za;
+  }
+  (void)Tv;
 #pragma unroll
   for (int s = 0; s < NS; ++s) om[s] = 0.0;
   for (int r = 0; r < nr; ++r) {
     const RxnDev& Rx = mech->rx[r];
-    const double lkf = fma(Rx.b, lnT, fma(-Rx.Ta, invT, Rx.lnA));
-    const double lkc = fma(Rx.kc[0], Zi, fma(Rx.kc[2], lnZ, fma(Rx.kc[3], Z, fma(Rx.kc[4], Z2, Rx.kc[1]))));
+    const bool ta = TT && Rx.ta;  // uniform across the launch
+    const double lt = ta ? lnTa : lnT, it = ta ? invTa : invT;
+    const double z = ta ? Za : Z, zi = ta ? Zia : Zi, lz = ta ? lnZa : lnZ, z2 = ta ? Za2 : Z2;
+    const double lkf = fma(Rx.b, lt, fma(-Rx.Ta, it, Rx.lnA));
+    const double lkc = fma(Rx.kc[0], zi, fma(Rx.kc[2], lz, fma(Rx.kc[3], z, fma(Rx.kc[4], z2, Rx.kc[1]))));
     const double kf = exp_tab(lkf, e2tab), kb = exp_tab(lkf - lkc, e2tab);
     const double pf = X[Rx.f[0] * xs] * X[Rx.f[1] * xs] * X[Rx.f[2] * xs];
     const double pb = X[Rx.bk[0] * xs] * X[Rx.bk[1] * xs] * X[Rx.bk[2] * xs];
@@ -289,6 +397,47 @@ __device__ __forceinline__ void species_rates(const MechDev* __restrict__ mech, 
 #pragma unroll
     for (int s = 0; s < NS; ++s) om[s] = fma(Rx.coef[s], rate, om[s]);
   }
+}
+
+// Two-temperature E_v source of one node (Sec. 3.1.3 Eqs. src_vector, src_landau_teller),
+// FP64: Q_T-v + sum_s omega_s e_v,s(T_v) with Q_T-v = sum rho_s (e_v,s(T) - e_v,s(T_v)) / tau_s
+// over the vibrating species, tau_s = tau_MW + tau_P:
+//   1 / tau_MW = (p / 1 atm) sum_r X_r exp(C_sr - A_sr T^-1/3)       (Millikan and White)
+//   tau_P = k_B T / (p sigma_v c_s), sigma_v = 1e-21 (5e4 / T)^2 m^2, c_s = (8 R_s T / pi)^1/2
+// (Park), X_r the mole fractions, A_sr and C_sr = A_sr B_sr + 18.42 precomputed on the host.
+// sp: species table (rows R, cv, h0, 1e-6/W, theta); mw: [2][NS][NS] (A, then C).
+template <int NS>
+__device__ __forceinline__ double vib_source(const double* u, const double* sp, const double* mw, double T,
+                                             double Tv, const double (&om)[NS], const double* e2tab) {
+  double X[NS], sum = 0.0, rR = 0.0;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    X[s] = u[s] * sp[3 * NS + s];
+    sum += X[s];
+    rR = fma(u[s], sp[s], rR);
+  }
+  const double ix = rcp64(sum), invT = rcp64(T), invTv = rcp64(Tv);
+  const double p = rR * T;
+  const double t13 = exp_tab(-log(T) * (1.0 / 3.0), e2tab);  // T^-1/3
+  const double patm = p * (1.0 / 101325.0);
+  const double r5 = 5.0e4 * invT;
+  const double park = 1.380649e-23 * T / (p * 1.0e-21 * r5 * r5);  // k_B T / (p sigma_v)
+  double out = 0.0;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    const double th = sp[4 * NS + s];
+    if (th <= 0.0) continue;
+    double r = 0.0;
+#pragma unroll
+    for (int q = 0; q < NS; ++q) r = fma(X[q], exp_tab(fma(-mw[s * NS + q], t13, mw[NS * NS + s * NS + q]), e2tab), r);
+    const double tau = rcp64(patm * r * ix) + park * rsqrt(8.0 * sp[s] * T * (1.0 / 3.141592653589793));
+    const double Rth = sp[s] * th;
+    const double eT = Rth * rcp64(exp_tab(th * invT, e2tab) - 1.0);
+    const double eTv = Rth * rcp64(exp_tab(th * invTv, e2tab) - 1.0);
+    out = fma(u[s], (eT - eTv) * rcp64(tau), out);
+    out = fma(om[s], eTv, out);
+  }
+  return out;
 }
 
 // Launch scalars in the flux precision.
@@ -309,11 +458,13 @@ struct RS {
 
 // Own primitives (and U in R) of the CTA's elements and the neighbours' face traces, from the
 // primitive cache (rows 0..NROW-1) and, with KEEP_U, the FP64 state; the own nodes' FP64
-// state is returned in u_own and c_p, T (FP64) in cpT_own.
-template <int N, int NS, class R, bool KEEP_U, int NROW>
+// state is returned in u_own and (c_p, T, c_v,v, T_v) (FP64; the last two two-temperature
+// only) in cpT_own.
+template <int N, int NS, bool TT, class R, bool KEEP_U, int NROW>
 __device__ __forceinline__ void load_element(const ReactArgs& a, int e0, R* smem_el, int esz, int off_p,
                                              int off_pt, int off_us, int off_ut, double* u_own, double* cpT_own) {
-  using G = RG<N, NS, R>;
+  using G = RG<N, NS, TT, R>;
+  constexpr int NPR = G::NPR;
   const int t = threadIdx.x;
   const R* P = reinterpret_cast<const R*>(a.pin);
   if (t < G::EPB * G::NP) {
@@ -324,8 +475,12 @@ __device__ __forceinline__ void load_element(const ReactArgs& a, int e0, R* smem
 #pragma unroll
       for (int c = 0; c < NROW; ++c) sm[off_p + c * G::NP + q] = P[c * a.stride + gi];
       if (cpT_own) {
-        cpT_own[0] = Ar<R>::widen(P[6 * a.stride + gi]);
+        cpT_own[0] = Ar<R>::widen(P[G::RCP * a.stride + gi]);
         cpT_own[1] = a.tin[gi];
+        if (TT) {
+          cpT_own[2] = Ar<R>::widen(P[G::RCV * a.stride + gi]);
+          cpT_own[3] = a.tin[a.stride + gi];
+        }
       }
       if (KEEP_U) {
 #pragma unroll
@@ -387,9 +542,9 @@ __device__ __forceinline__ void load_element(const ReactArgs& a, int e0, R* smem
 // ---------------------------------------------------------------------------------------
 // Launch 1: BR1 gradients and the element's own viscous flux on its faces.
 // ---------------------------------------------------------------------------------------
-template <int N, int NS, class R>
+template <int N, int NS, bool TT, class R>
 __global__ void __launch_bounds__(kRT) k_br1_faces(const ReactArgs a) {
-  using G = RG<N, NS, R>;
+  using G = RG<N, NS, TT, R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* D = reinterpret_cast<R*>(smem_raw);
   R* el_base = D + G::N1 * G::N1;
@@ -397,8 +552,8 @@ __global__ void __launch_bounds__(kRT) k_br1_faces(const ReactArgs a) {
   for (int k = t; k < G::N1 * G::N1; k += kRT) D[k] = Ar<R>::load(a.D[k]);
   const RS<R> rs(a);
   const int e0 = blockIdx.x * G::EPB;
-  double cpT[2] = {0.0, 0.0};
-  load_element<N, NS, R, false, 4>(a, e0, el_base, G::G_SIZE, G::G_P, G::G_PT, 0, 0, nullptr, cpT);
+  double cpT[4] = {0.0, 0.0, 0.0, 0.0};
+  load_element<N, NS, TT, R, false, G::NW>(a, e0, el_base, G::G_SIZE, G::G_P, G::G_PT, 0, 0, nullptr, cpT);
   __syncthreads();
   if (t >= G::EPB * G::NP) return;
   const int el = t / G::NP, q = t % G::NP, e = e0 + el;
@@ -406,19 +561,20 @@ __global__ void __launch_bounds__(kRT) k_br1_faces(const ReactArgs a) {
   const int ijk[3] = {q % G::N1, (q / G::N1) % G::N1, q / G::NFN};
   if (ijk[0] != 0 && ijk[0] != N && ijk[1] != 0 && ijk[1] != N && ijk[2] != 0 && ijk[2] != N) return;
   const R* sm = el_base + el * G::G_SIZE;
-  R S[4][3];
-  br1_gradient<N, R>(q, sm + G::G_P, sm + G::G_PT, D, rs.s, rs.lift, S);
+  R S[G::NW][3];
+  br1_gradient<N, G::NW, G::NPR, R>(q, sm + G::G_P, sm + G::G_PT, D, rs.s, rs.lift, S);
   const R v[3] = {sm[G::G_P + q], sm[G::G_P + G::NP + q], sm[G::G_P + 2 * G::NP + q]};
   const R kcond = rs.kfac * Ar<R>::load(cpT[0]);
-  R* fbe = reinterpret_cast<R*>(a.fb) + (size_t)e * 6 * 4 * G::NFN;
-  R Fv[4];
+  const R kvib = rs.kfac * Ar<R>::load(cpT[2]);
+  R* fbe = reinterpret_cast<R*>(a.fb) + (size_t)e * 6 * G::NFV * G::NFN;
+  R Fv[G::NFV];
 #define DG_FACE_OUT(L)                                                                       \
   if (ijk[L] == 0 || ijk[L] == N) {                                                          \
-    visc_flux<L, R>(S, v, rs.mu, kcond, Fv);                                                 \
+    visc_flux<L, G::NW, R>(S, v, rs.mu, kcond, kvib, Fv);                                    \
     const int jf = L == 0 ? ijk[1] + G::N1 * ijk[2]                                          \
                           : (L == 1 ? ijk[0] + G::N1 * ijk[2] : ijk[0] + G::N1 * ijk[1]);     \
-    R* dst = fbe + (2 * L + (ijk[L] == N ? 1 : 0)) * 4 * G::NFN + jf;                        \
-    for (int c = 0; c < 4; ++c) dst[c * G::NFN] = Fv[c];                                     \
+    R* dst = fbe + (2 * L + (ijk[L] == N ? 1 : 0)) * G::NFV * G::NFN + jf;                   \
+    for (int c = 0; c < G::NFV; ++c) dst[c * G::NFN] = Fv[c];                               \
   }
   DG_FACE_OUT(0)
   DG_FACE_OUT(1)
@@ -429,36 +585,43 @@ __global__ void __launch_bounds__(kRT) k_br1_faces(const ReactArgs a) {
 // ---------------------------------------------------------------------------------------
 // Launch 2: the fused stage.
 // ---------------------------------------------------------------------------------------
-template <int N, int NS, class R>
+template <int N, int NS, bool TT, class R>
 __global__ void __launch_bounds__(kRT) k_reacting_stage(const ReactArgs a) {
-  using G = RG<N, NS, R>;
-  constexpr int N1 = G::N1, NP = G::NP, NFN = G::NFN, NV = G::NV;
+  using G = RG<N, NS, TT, R>;
+  constexpr int N1 = G::N1, NP = G::NP, NFN = G::NFN, NV = G::NV, NFV = G::NFV, NPR = G::NPR;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* sp = reinterpret_cast<double*>(smem_raw) + G::C_SP;
   double* X = reinterpret_cast<double*>(smem_raw) + G::C_X;
   double* e2tab = reinterpret_cast<double*>(smem_raw) + G::C_E2;
+  double* mw = reinterpret_cast<double*>(smem_raw) + G::C_MW;
   R* D = reinterpret_cast<R*>(reinterpret_cast<double*>(smem_raw) + G::C_DBL);
   R* el_base = D + N1 * N1;
   const int t = threadIdx.x;
   for (int k = t; k < N1 * N1; k += kRT) D[k] = Ar<R>::load(a.D[k]);
-  load_species<NS>(a.mech, sp, 4);
+  load_species<NS>(a.mech, sp, G::NSP);
   for (int k = t; k < 64; k += kRT) e2tab[k] = a.mech->exp2tab[k];
+  if (TT) {  // Millikan-White coefficients [A | C][s][r]
+    for (int k = t; k < 2 * NS * NS; k += kRT) {
+      const int w = k / (NS * NS), s2 = (k / NS) % NS, r2 = k % NS;
+      mw[k] = w ? a.mech->mwC[s2][r2] : a.mech->mwA[s2][r2];
+    }
+  }
   // neighbour viscous face fluxes from launch 1
   const int e0 = blockIdx.x * G::EPB;
   const R* fb = reinterpret_cast<const R*>(a.fb);
-  for (int idx = t; idx < G::EPB * 24 * NFN; idx += kRT) {
-    const int el = idx / (24 * NFN), r = idx % (24 * NFN), f = r / (4 * NFN), cj = r % (4 * NFN);
+  for (int idx = t; idx < G::EPB * 6 * NFV * NFN; idx += kRT) {
+    const int el = idx / (6 * NFV * NFN), r = idx % (6 * NFV * NFN), f = r / (NFV * NFN), cj = r % (NFV * NFN);
     const int e = e0 + el;
     if (e >= a.n_elem) continue;
     const int l = f >> 1, side = f & 1;
     const int en = neighbour(a.nel, e, l, side ? 1 : -1);
-    el_base[el * G::E_SIZE + G::E_FT + r] = fb[((size_t)en * 6 + (2 * l + (side ^ 1))) * 4 * NFN + cj];
+    el_base[el * G::E_SIZE + G::E_FT + r] = fb[((size_t)en * 6 + (2 * l + (side ^ 1))) * NFV * NFN + cj];
   }
   __syncthreads();
   const RS<R> rs(a);
   double u64[NV];
-  double cpT[2] = {0.0, 1.0};
-  load_element<N, NS, R, true, NPR>(a, e0, el_base, G::E_SIZE, G::E_P, G::E_PT, G::E_US, G::E_UT, u64, cpT);
+  double cpT[4] = {0.0, 1.0, 0.0, 1.0};
+  load_element<N, NS, TT, R, true, NPR>(a, e0, el_base, G::E_SIZE, G::E_P, G::E_PT, G::E_US, G::E_UT, u64, cpT);
   unsigned flag = 0;
   __syncthreads();
 
@@ -467,8 +630,8 @@ __global__ void __launch_bounds__(kRT) k_reacting_stage(const ReactArgs a) {
   const bool active = node_thread && e < a.n_elem;
   R* sm = el_base + el * G::E_SIZE;
   const int ijk[3] = {q % N1, (q / N1) % N1, q / NFN};
-  R u[NV], res[NV], v[3], pd = R(0), kcond = R(0);
-  R S[4][3];
+  R u[NV], res[NV], v[3], pd = R(0), kcond = R(0), kvib = R(0);
+  R S[G::NW][3];
 #pragma unroll
   for (int k = 0; k < NV; ++k) res[k] = R(0);
   if (active) {
@@ -476,31 +639,32 @@ __global__ void __launch_bounds__(kRT) k_reacting_stage(const ReactArgs a) {
     for (int k = 0; k < NV; ++k) u[k] = sm[G::E_US + k * NP + q];
 #pragma unroll
     for (int d = 0; d < 3; ++d) v[d] = sm[G::E_P + d * NP + q];
-    pd = sm[G::E_P + 4 * NP + q];
+    pd = sm[G::E_P + G::RPD * NP + q];
     kcond = rs.kfac * Ar<R>::load(cpT[0]);
-    br1_gradient<N, R>(q, sm + G::E_P, sm + G::E_PT, D, rs.s, rs.lift, S);
+    kvib = rs.kfac * Ar<R>::load(cpT[2]);
+    br1_gradient<N, G::NW, NPR, R>(q, sm + G::E_P, sm + G::E_PT, D, rs.s, rs.lift, S);
   }
   // volume term, one direction at a time through the H buffer
 #define DG_VOLUME_DIR(L)                                                                      \
   {                                                                                           \
     if (active) {                                                                             \
-      R F[NV], Fv[4];                                                                         \
-      inv_flux<NS, R>(L, u, v[0], v[1], v[2], pd, rs.p_ref, F);                               \
-      visc_flux<L, R>(S, v, rs.mu, kcond, Fv);                                                \
-      _Pragma("unroll") for (int c = 0; c < 4; ++c) F[NS + c] -= Fv[c];                       \
+      R F[NV], Fv[NFV];                                                                       \
+      inv_flux<NS, TT, R>(L, u, v[0], v[1], v[2], pd, rs.p_ref, F);                           \
+      visc_flux<L, G::NW, R>(S, v, rs.mu, kcond, kvib, Fv);                                   \
+      _Pragma("unroll") for (int c = 0; c < NFV; ++c) F[NS + c] -= Fv[c];                     \
       _Pragma("unroll") for (int k = 0; k < NV; ++k) sm[G::E_H + k * NP + q] = F[k];          \
       if (ijk[L] == 0 || ijk[L] == N) {                                                       \
         const int jf = L == 0 ? ijk[1] + N1 * ijk[2]                                          \
                               : (L == 1 ? ijk[0] + N1 * ijk[2] : ijk[0] + N1 * ijk[1]);        \
         const int side = ijk[L] == N ? 1 : 0;                                                 \
-        R* dst = sm + G::E_FO + (2 * L + side) * 4 * NFN + jf;                                \
-        _Pragma("unroll") for (int c = 0; c < 4; ++c) dst[c * NFN] = Fv[c];                   \
+        R* dst = sm + G::E_FO + (2 * L + side) * NFV * NFN + jf;                              \
+        _Pragma("unroll") for (int c = 0; c < NFV; ++c) dst[c * NFN] = Fv[c];                 \
         const int fw = a.bnd.nonper ? wall_face(a, e, L, side) : -1;                          \
         if (fw >= 0) { /* ghost neighbour flux: (F_v + ghost)/2 is the boundary flux */       \
-          R gh[4];                                                                            \
-          ghost_viscous_flux<L, R>(a.bnd.bc[fw], Fv, kcond * S[3][L], gh);                    \
-          R* gd = sm + G::E_FT + (2 * L + side) * 4 * NFN + jf;                               \
-          _Pragma("unroll") for (int c = 0; c < 4; ++c) gd[c * NFN] = gh[c];                  \
+          R gh[NFV];                                                                          \
+          ghost_viscous_flux<L, NFV, R>(a.bnd.bc[fw], Fv, kcond * S[3][L], gh);               \
+          R* gd = sm + G::E_FT + (2 * L + side) * NFV * NFN + jf;                             \
+          _Pragma("unroll") for (int c = 0; c < NFV; ++c) gd[c * NFN] = gh[c];                \
         }                                                                                     \
       }                                                                                       \
     }                                                                                         \
@@ -541,11 +705,11 @@ __global__ void __launch_bounds__(kRT) k_reacting_stage(const ReactArgs a) {
     const R* po = fs + G::E_P + qo;
     const R* pn = fs + G::E_PT + f * NPR * NFN + jf;
     R Fo[NV], Fn[NV];
-    inv_flux<NS, R>(l, uo, po[0], po[NP], po[2 * NP], po[4 * NP], rs.p_ref, Fo);
+    inv_flux<NS, TT, R>(l, uo, po[0], po[NP], po[2 * NP], po[G::RPD * NP], rs.p_ref, Fo);
     // the exterior state: the neighbour's trace, or at a domain face the boundary functor's
     // (Sec. 3.1.1): walls -- the mirror state; Dirichlet -- U_b; inflow -- F* = F(U_b);
     // outflow -- F* = F(U-)
-    R vn[3] = {pn[0], pn[NFN], pn[2 * NFN]}, pdn = pn[4 * NFN], an = pn[5 * NFN];
+    R vn[3] = {pn[0], pn[NFN], pn[2 * NFN]}, pdn = pn[G::RPD * NFN], an = pn[G::RA * NFN];
     const int fw = a.bnd.nonper ? wall_face(a, e0 + fel, l, side) : -1;
     const int type = fw >= 0 ? a.bnd.bc[fw] : 0;
     if (fw >= 0) {
@@ -568,13 +732,13 @@ __global__ void __launch_bounds__(kRT) k_reacting_stage(const ReactArgs a) {
             un[NS + d] = -uo[NS + d];
             vn[d] = -vn[d];
           }
-        pdn = po[4 * NP];
-        an = po[5 * NP];
+        pdn = po[G::RPD * NP];
+        an = po[G::RA * NP];
       }
     }
-    inv_flux<NS, R>(l, un, vn[0], vn[1], vn[2], pdn, rs.p_ref, Fn);
+    inv_flux<NS, TT, R>(l, un, vn[0], vn[1], vn[2], pdn, rs.p_ref, Fn);
     const R vlo = pick3(l, po[0], po[NP], po[2 * NP]), vln = pick3(l, vn[0], vn[1], vn[2]);
-    const R lam = Ar<R>::fmax(Ar<R>::abs(vlo) + po[5 * NP], Ar<R>::abs(vln) + an);
+    const R lam = Ar<R>::fmax(Ar<R>::abs(vlo) + po[G::RA * NP], Ar<R>::abs(vln) + an);
     // F* = (F_L + F_R)/2 - lam (U_R - U_L)/2; with L/R the lower/upper side of the face
     const R hl = side ? R(0.5) * lam : R(-0.5) * lam;  // lam/2 (U_R - U_L) = hl (un - uo)
     R dlt[NV];
@@ -589,9 +753,9 @@ __global__ void __launch_bounds__(kRT) k_reacting_stage(const ReactArgs a) {
       for (int k = 0; k < NV; ++k) dlt[k] = R(0.5) * (Fn[k] - Fo[k]) - hl * (un[k] - uo[k]);
     }
 #pragma unroll
-    for (int c = 0; c < 4; ++c)
-      dlt[NS + c] = dlt[NS + c] - R(0.5) * (fs[G::E_FT + f * 4 * NFN + c * NFN + jf] -
-                                            fs[G::E_FO + f * 4 * NFN + c * NFN + jf]);
+    for (int c = 0; c < NFV; ++c)
+      dlt[NS + c] = dlt[NS + c] - R(0.5) * (fs[G::E_FT + f * NFV * NFN + c * NFN + jf] -
+                                            fs[G::E_FO + f * NFV * NFN + c * NFN + jf]);
 #pragma unroll
     for (int k = 0; k < NV; ++k) fs[G::E_UT + (f * NV + k) * NFN + jf] = dlt[k];
   }
@@ -615,14 +779,21 @@ __global__ void __launch_bounds__(kRT) k_reacting_stage(const ReactArgs a) {
   // Arrhenius source (Sec. 3.1.3; App. C), FP64, [X_s] = rho_s 1e-6 / W_s; left out of L
   // under the Strang split, where the implicit substep takes it
   const int nr = a.mech->nr;
-  if (nr > 0 && a.src) {
-#pragma unroll
-    for (int s2 = 0; s2 < NS; ++s2) X[s2 * kRT + t] = u64[s2] * sp[3 * NS + s2];
-    X[NS * kRT + t] = 1.0;
+  if (a.src && (nr > 0 || TT)) {
     double om[NS];
-    species_rates<NS>(a.mech, nr, cpT[1], X + t, kRT, e2tab, a.ln1e4, om);
 #pragma unroll
-    for (int s2 = 0; s2 < NS; ++s2) r64[s2] += om[s2];
+    for (int s2 = 0; s2 < NS; ++s2) om[s2] = 0.0;
+    if (nr > 0) {
+#pragma unroll
+      for (int s2 = 0; s2 < NS; ++s2) X[s2 * kRT + t] = u64[s2] * sp[3 * NS + s2];
+      X[NS * kRT + t] = 1.0;
+      species_rates<NS, TT>(a.mech, nr, cpT[1], cpT[3], X + t, kRT, e2tab, a.ln1e4, om);
+#pragma unroll
+      for (int s2 = 0; s2 < NS; ++s2) r64[s2] += om[s2];
+    }
+    // two-temperature: the E_v source (Landau-Teller and the vibrational energy that
+    // chemistry carries)
+    if constexpr (TT) r64[NS + 4] += vib_source<NS>(u64, sp, mw, cpT[1], cpT[3], om, e2tab);
   }
 
   const long long gi = a.base + (long long)e * NP + q;
@@ -644,26 +815,27 @@ __global__ void __launch_bounds__(kRT) k_reacting_stage(const ReactArgs a) {
     a.out[k * a.stride + gi] = x[k];
   }
   // the primitive cache of the new state, read by the next stage
-  if (a.mode == 1 && a.pout) flag |= write_prims<NS, R>(x, sp, a.p_ref, reinterpret_cast<R*>(a.pout), a.tout,
-                                                        a.stride, gi);
+  if (a.mode == 1 && a.pout) flag |= write_prims<NS, TT, R>(x, sp, a.p_ref, reinterpret_cast<R*>(a.pout), a.tout,
+                                                            a.stride, gi, cpT[3], e2tab);
   if (!finite) flag |= 1u;
   if (flag) atomicOr(a.err, flag);
 }
 
 // The primitive cache of a state that did not come from a stage launch.
-template <int NS, class R>
+template <int NS, bool TT, class R>
 __global__ void k_react_prims(const double* U, long long stride, long long base, long long n,
                               const MechDev* __restrict__ mech, double p_ref, R* P, double* T64, unsigned* err) {
-  __shared__ double sp[4 * NS];
-  load_species<NS>(mech, sp, 4);
+  constexpr int NV = NS + 4 + (TT ? 1 : 0);
+  __shared__ double sp[5 * NS];
+  load_species<NS>(mech, sp, TT ? 5 : 4);
   __syncthreads();
   unsigned flag = 0;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
        q += (long long)gridDim.x * blockDim.x) {
-    double u[NS + 4];
+    double u[NV];
 #pragma unroll
-    for (int v = 0; v < NS + 4; ++v) u[v] = U[v * stride + base + q];
-    flag |= write_prims<NS, R>(u, sp, p_ref, P, T64, stride, base + q);
+    for (int v = 0; v < NV; ++v) u[v] = U[v * stride + base + q];
+    flag |= write_prims<NS, TT, R>(u, sp, p_ref, P, T64, stride, base + q, 0.0, mech->exp2tab);
   }
   if (flag) atomicOr(err, flag);
 }
@@ -709,7 +881,7 @@ __device__ __forceinline__ void be_residual(const MechDev* __restrict__ mech, in
   for (int s = 0; s < NS; ++s) X[s * kCT] = Y[s] * sp[3 * NS + s];
   const double T = temp_of<NS>(Y, sp, e);
   double om[NS];
-  species_rates<NS>(mech, nr, T, X, kCT, e2tab, ln1e4, om);
+  species_rates<NS, false>(mech, nr, T, T, X, kCT, e2tab, ln1e4, om);
 #pragma unroll
   for (int s = 0; s < NS; ++s) R[s] = fma(-h, om[s], Y[s] - Yn[s]);
 }
@@ -827,7 +999,7 @@ __global__ void __launch_bounds__(kCT) k_source_implicit(const SourceArgs a) {
 #pragma unroll
     for (int v = NS; v < NS + 4; ++v) a.out[v * a.stride + gi] = u[v];
   }
-  if (a.pout) flag |= write_prims<NS, R>(u, sp, a.p_ref, reinterpret_cast<R*>(a.pout), a.tout, a.stride, gi);
+  if (a.pout) flag |= write_prims<NS, false, R>(u, sp, a.p_ref, reinterpret_cast<R*>(a.pout), a.tout, a.stride, gi);
   if (!finite) flag |= 1u;
   if (flag) atomicOr(a.err, flag);
 }
@@ -850,19 +1022,21 @@ __global__ void k_math_fn(const MathArgs a) {
 }
 
 // Largest |u| + a and largest 1/rho over the nodes of one instance.
-template <int NS>
+template <int NS, bool TT>
 __global__ void k_max_speed_mix(const double* U, long long stride, long long base, long long n,
                                 const MechDev* __restrict__ mech, unsigned long long* out2) {
+  constexpr int NV = NS + 4 + (TT ? 1 : 0);
   __shared__ double sp[4 * NS];
   load_species<NS>(mech, sp, 4);
   __syncthreads();
   double lam = 0.0, irho = 0.0;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
        q += (long long)gridDim.x * blockDim.x) {
-    double u[NS + 4];
+    double u[NV];
 #pragma unroll
-    for (int v = 0; v < NS + 4; ++v) u[v] = U[v * stride + base + q];
-    const Mx m = mixture<NS>(u, sp);
+    for (int v = 0; v < NV; ++v) u[v] = U[v * stride + base + q];
+    if (TT) u[NS + 3] -= u[NV - 1];  // the frozen sound speed needs T only: E - E_v
+    const Mx m = mixture<NS, false>(u, sp);
     lam = fmax(lam, sqrt(m.v[0] * m.v[0] + m.v[1] * m.v[1] + m.v[2] * m.v[2]) + m.a);
     irho = fmax(irho, 1.0 / m.rho);
   }
@@ -886,69 +1060,82 @@ __global__ void k_max_speed_mix(const double* U, long long stride, long long bas
   }
 }
 
-template <int N, int NS, class R>
+template <int N, int NS, bool TT, class R>
 cudaError_t prepare_one() {
-  using G = RG<N, NS, R>;
-  cudaError_t e = cudaFuncSetAttribute(k_reacting_stage<N, NS, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  using G = RG<N, NS, TT, R>;
+  cudaError_t e = cudaFuncSetAttribute(k_reacting_stage<N, NS, TT, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)G::stage_smem());
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_br1_faces<N, NS, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(k_br1_faces<N, NS, TT, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)G::grad_smem());
   return e;
 }
 
-template <int N, int NS, class R>
+template <int N, int NS, bool TT, class R>
 cudaError_t launch_one(const ReactArgs& a, cudaStream_t s) {
-  using G = RG<N, NS, R>;
+  using G = RG<N, NS, TT, R>;
   if (a.n_elem <= 0) return cudaSuccess;
   const unsigned grid = (unsigned)((a.n_elem + G::EPB - 1) / G::EPB);
-  k_br1_faces<N, NS, R><<<grid, kRT, G::grad_smem(), s>>>(a);
+  k_br1_faces<N, NS, TT, R><<<grid, kRT, G::grad_smem(), s>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_reacting_stage<N, NS, R><<<grid, kRT, G::stage_smem(), s>>>(a);
+  k_reacting_stage<N, NS, TT, R><<<grid, kRT, G::stage_smem(), s>>>(a);
   return cudaGetLastError();
 }
 
+// (N, n_species, two-temperature) instantiations: one species (the non-dimensional single
+// gas) and five (air), N = 1..4; the two-temperature model for air.
 #define DG_REACT_DISPATCH(CALL)                          \
-  switch (ns * 16 + N) {                                 \
-    case 1 * 16 + 1: return CALL(1, 1);                  \
-    case 1 * 16 + 2: return CALL(2, 1);                  \
-    case 1 * 16 + 3: return CALL(3, 1);                  \
-    case 1 * 16 + 4: return CALL(4, 1);                  \
-    case 5 * 16 + 1: return CALL(1, 5);                  \
-    case 5 * 16 + 2: return CALL(2, 5);                  \
-    case 5 * 16 + 3: return CALL(3, 5);                  \
-    case 5 * 16 + 4: return CALL(4, 5);                  \
+  switch ((tt ? 256 : 0) + ns * 16 + N) {                \
+    case 1 * 16 + 1: return CALL(1, 1, false);           \
+    case 1 * 16 + 2: return CALL(2, 1, false);           \
+    case 1 * 16 + 3: return CALL(3, 1, false);           \
+    case 1 * 16 + 4: return CALL(4, 1, false);           \
+    case 5 * 16 + 1: return CALL(1, 5, false);           \
+    case 5 * 16 + 2: return CALL(2, 5, false);           \
+    case 5 * 16 + 3: return CALL(3, 5, false);           \
+    case 5 * 16 + 4: return CALL(4, 5, false);           \
+    case 256 + 5 * 16 + 1: return CALL(1, 5, true);      \
+    case 256 + 5 * 16 + 2: return CALL(2, 5, true);      \
+    case 256 + 5 * 16 + 3: return CALL(3, 5, true);      \
+    case 256 + 5 * 16 + 4: return CALL(4, 5, true);      \
     default: return cudaErrorInvalidValue;               \
   }
 
 }  // namespace
 
-bool have_reacting(int N, int ns) { return (ns == 1 || ns == 5) && N >= 1 && N <= kMaxReactingN; }
+bool have_reacting(int N, int ns, int tt) {
+  return (tt ? ns == 5 : (ns == 1 || ns == 5)) && N >= 1 && N <= kMaxReactingN;
+}
 
-cudaError_t prepare_reacting(int N, int ns, int fp32) {
-#define DG_P(n, s) (fp32 ? prepare_one<n, s, float>() : prepare_one<n, s, double>())
+cudaError_t prepare_reacting(int N, int ns, int tt, int fp32) {
+#define DG_P(n, s, t) (fp32 ? prepare_one<n, s, t, float>() : prepare_one<n, s, t, double>())
   DG_REACT_DISPATCH(DG_P)
 #undef DG_P
 }
 
-cudaError_t launch_reacting(int N, int ns, int fp32, const ReactArgs& a, cudaStream_t s) {
-#define DG_L(n, sp) (fp32 ? launch_one<n, sp, float>(a, s) : launch_one<n, sp, double>(a, s))
+cudaError_t launch_reacting(int N, int ns, int tt, int fp32, const ReactArgs& a, cudaStream_t s) {
+#define DG_L(n, sp, t) (fp32 ? launch_one<n, sp, t, float>(a, s) : launch_one<n, sp, t, double>(a, s))
   DG_REACT_DISPATCH(DG_L)
 #undef DG_L
 }
 
-cudaError_t launch_react_prims(int ns, int fp32, const double* U, long long stride, long long base,
+cudaError_t launch_react_prims(int ns, int tt, int fp32, const double* U, long long stride, long long base,
                                long long n_nodes, const MechDev* mech, double p_ref, void* P, double* T64,
                                unsigned* err, cudaStream_t s) {
   if (n_nodes <= 0) return cudaSuccess;
   const long long want = (n_nodes + 255) / 256;
   const unsigned grid = (unsigned)(want < 148 * 16 ? want : 148 * 16);
-  if (ns == 1 && fp32) k_react_prims<1, float><<<grid, 256, 0, s>>>(U, stride, base, n_nodes, mech, p_ref, (float*)P, T64, err);
-  else if (ns == 1) k_react_prims<1, double><<<grid, 256, 0, s>>>(U, stride, base, n_nodes, mech, p_ref, (double*)P, T64, err);
-  else if (ns == 5 && fp32) k_react_prims<5, float><<<grid, 256, 0, s>>>(U, stride, base, n_nodes, mech, p_ref, (float*)P, T64, err);
-  else if (ns == 5) k_react_prims<5, double><<<grid, 256, 0, s>>>(U, stride, base, n_nodes, mech, p_ref, (double*)P, T64, err);
+#define DG_RP(S2, T2, R2) k_react_prims<S2, T2, R2><<<grid, 256, 0, s>>>(U, stride, base, n_nodes, mech, p_ref, (R2*)P, T64, err)
+  if (tt && ns == 5 && fp32) DG_RP(5, true, float);
+  else if (tt && ns == 5) DG_RP(5, true, double);
+  else if (tt) return cudaErrorInvalidValue;
+  else if (ns == 1 && fp32) DG_RP(1, false, float);
+  else if (ns == 1) DG_RP(1, false, double);
+  else if (ns == 5 && fp32) DG_RP(5, false, float);
+  else if (ns == 5) DG_RP(5, false, double);
   else return cudaErrorInvalidValue;
+#undef DG_RP
   return cudaGetLastError();
 }
 
@@ -971,14 +1158,16 @@ cudaError_t launch_math_fn(const MathArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_max_speed_mix(int ns, const double* U, long long stride, long long base,
+cudaError_t launch_max_speed_mix(int ns, int tt, const double* U, long long stride, long long base,
                                  long long n_nodes, const MechDev* mech,
                                  unsigned long long* out2, cudaStream_t s) {
   if (n_nodes <= 0) return cudaSuccess;
   const long long want = (n_nodes + 255) / 256;
   const unsigned grid = (unsigned)(want < 148 * 16 ? want : 148 * 16);
-  if (ns == 1) k_max_speed_mix<1><<<grid, 256, 0, s>>>(U, stride, base, n_nodes, mech, out2);
-  else if (ns == 5) k_max_speed_mix<5><<<grid, 256, 0, s>>>(U, stride, base, n_nodes, mech, out2);
+  if (tt && ns == 5) k_max_speed_mix<5, true><<<grid, 256, 0, s>>>(U, stride, base, n_nodes, mech, out2);
+  else if (tt) return cudaErrorInvalidValue;
+  else if (ns == 1) k_max_speed_mix<1, false><<<grid, 256, 0, s>>>(U, stride, base, n_nodes, mech, out2);
+  else if (ns == 5) k_max_speed_mix<5, false><<<grid, 256, 0, s>>>(U, stride, base, n_nodes, mech, out2);
   else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }

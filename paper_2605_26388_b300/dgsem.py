@@ -64,12 +64,14 @@ class Mechanism(C.Structure):
                 ("lnA", C.c_double * MAX_REACTIONS), ("b", C.c_double * MAX_REACTIONS),
                 ("Ta", C.c_double * MAX_REACTIONS), ("kc", (C.c_double * 5) * MAX_REACTIONS),
                 ("nu_f", (C.c_int * MAX_SPECIES) * MAX_REACTIONS),
-                ("nu_b", (C.c_int * MAX_SPECIES) * MAX_REACTIONS)]
+                ("nu_b", (C.c_int * MAX_SPECIES) * MAX_REACTIONS),
+                ("theta_v", C.c_double * MAX_SPECIES), ("ta_mode", C.c_int * MAX_REACTIONS)]
 
     @classmethod
     def from_dict(cls, m: dict) -> "Mechanism":
         """Pack a mechanism given as a dict of plain numbers (keys n_species, n_reactions, W, R,
-        cv, h0 per species; lnA, b, Ta, kc (5 each), nu_f, nu_b per reaction)."""
+        cv, h0 and, for the two-temperature model, theta_v per species; lnA, b, Ta, kc (5
+        each), nu_f, nu_b and ta_mode per reaction)."""
         c = cls()
         ns, nr = int(m["n_species"]), int(m["n_reactions"])
         if not (1 <= ns <= MAX_SPECIES and 0 <= nr <= MAX_REACTIONS):
@@ -83,6 +85,9 @@ class Mechanism(C.Structure):
                 c.kc[r][k] = m["kc"][r][k]
             for s in range(ns):
                 c.nu_f[r][s], c.nu_b[r][s] = int(m["nu_f"][r][s]), int(m["nu_b"][r][s])
+            c.ta_mode[r] = int(m.get("ta_mode", [0] * nr)[r])
+        for s in range(ns):
+            c.theta_v[s] = float(m.get("theta_v", [0.0] * ns)[s])
         return c
 
 
@@ -93,7 +98,7 @@ class Physics(C.Structure):
                 ("prandtl", C.c_double), ("chem", C.POINTER(Mechanism)),
                 ("time_scheme", C.c_int), ("chem_split", C.c_int), ("newton_max_it", C.c_int),
                 ("newton_tol", C.c_double), ("shock", C.c_int), ("alpha_min", C.c_double),
-                ("alpha_max", C.c_double), ("sharpness", C.c_double)]
+                ("alpha_max", C.c_double), ("sharpness", C.c_double), ("two_temperature", C.c_int)]
 
 
 _lib = None
@@ -206,7 +211,7 @@ class Solver:
                  gamma=1.4, rho_floor=0.0, p_floor=0.0, p_ref=0.0, stream=None,
                  equations=DG_EULER, mu=0.0, prandtl=0.72, mechanism=None,
                  time_scheme=SSPRK33, chem_split=False, newton_max_it=0, newton_tol=0.0,
-                 shock=False, alpha_min=0.0, alpha_max=0.0, sharpness=0.0):
+                 shock=False, alpha_min=0.0, alpha_max=0.0, sharpness=0.0, two_temperature=False):
         import torch
         if isinstance(meshes, Mesh):
             meshes = [meshes]
@@ -215,7 +220,8 @@ class Solver:
         arr = (MeshDesc * len(self.meshes))(*[m.c() for m in self.meshes])
         phys = Physics(equations, volume, surface, precision, gamma, rho_floor, p_floor, p_ref,
                        mu, prandtl, None, time_scheme, 1 if chem_split else 0, newton_max_it,
-                       newton_tol, 1 if shock else 0, alpha_min, alpha_max, sharpness)
+                       newton_tol, 1 if shock else 0, alpha_min, alpha_max, sharpness,
+                       1 if two_temperature else 0)
         self.n_elem = sum(m.n_elem for m in self.meshes)
         if mechanism is not None:
             mech = mechanism if isinstance(mechanism, Mechanism) else Mechanism.from_dict(mechanism)

@@ -123,3 +123,34 @@ def test_init_rejects_bad_wall_descriptions(dg):
     assert _init_ns(dg, dg.Mesh(**box, bc=(7, 7, 0, 0, 0, 0)).c()) == dg.DG_EINVAL
     unpaired = dg.Mesh(**box, bc=(5, 0, 0, 0, 0, 0)).c()
     assert _init_ns(dg, unpaired) == dg.DG_EINVAL
+
+
+def _init_tt(dg, mesh, mech=None, **kw):
+    from paper_2605_26388_b300 import workloads as wl
+    m = dg.Mechanism.from_dict(mech or wl.air5_mechanism())
+    phys = dg.Physics()
+    phys.equations = kw.get("equations", dg.DG_NS_REACTING)
+    phys.gamma, phys.mu, phys.prandtl = 1.4, 1e-3, 0.72
+    phys.chem = C.pointer(m)
+    phys.two_temperature = kw.get("tt", 1)
+    phys.chem_split = kw.get("split", 0)
+    arr = (dg.MeshDesc * 1)(mesh)
+    h = C.c_void_p()
+    return dg.lib().dg_init_mesh(arr, 1, C.byref(phys), None, C.byref(h))
+
+
+def test_init_rejects_bad_two_temperature_setups(dg):
+    """The two-temperature model is reacting, periodic, unsplit, with a vibrating species."""
+    from paper_2605_26388_b300 import workloads as wl
+    box = dict(dim=3, N=3, nel=(2, 2, 2), lo=(0.0,) * 3, hi=(1.0,) * 3)
+    periodic = dg.Mesh(**box).c()
+    assert _init_tt(dg, periodic, tt=2) == dg.DG_EINVAL
+    assert _init_tt(dg, periodic, equations=dg.DG_NAVIER_STOKES) == dg.DG_EUNSUPPORTED
+    assert _init_tt(dg, periodic, split=1) == dg.DG_EUNSUPPORTED
+    assert _init_tt(dg, dg.Mesh(**box, bc=(1, 1, 0, 0, 0, 0)).c()) == dg.DG_EUNSUPPORTED
+    frozen = wl.air5_mechanism()
+    frozen["theta_v"] = [0.0] * 5
+    assert _init_tt(dg, periodic, mech=frozen) == dg.DG_EINVAL
+    bad = wl.air5_mechanism()
+    bad["ta_mode"] = [2] * 17
+    assert _init_tt(dg, periodic, mech=bad) == dg.DG_EINVAL
