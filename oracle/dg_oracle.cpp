@@ -1979,18 +1979,89 @@ bool gauss_jordan(int n, double* A, double* b) {
   return true;
 }
 
-// One node: u (all n_vars components) in, the new partial densities written to u.
-// Returns the number of Newton updates taken, or -1 if the iteration did not converge.
+// Two-temperature backward-Euler residual of the unknowns y = (Y_1..Y_ns, E_v) (Sec. 3.1.3:
+// the implicit substep takes the full source vector, Eq. src_vector, whose E_v row is
+// Q_T-v + sum omega_s e_v,s(T_v)): T from the fixed internal energy e (E minus the kinetic
+// energy) less E_v, T_v from E_v; R = y - y^n - h S(y).  Returns false when T or T_v is not
+// positive and finite.
+bool source_residual_tt(const OrcProblem& P, const double* y, const double* yn, double e, double h,
+                        double* R, double* T_out, double* Tv_out) {
+  const OrcMech& m = *P.mech;
+  const int ns = m.n_species;
+  const double T = temperature_of(m, y, e - y[ns]);
+  const double Tv = vib_temperature(m, y, y[ns]);
+  if (T_out) *T_out = T;
+  if (Tv_out) *Tv_out = Tv;
+  if (!(T > 0.0) || !(Tv > 0.0) || !std::isfinite(T) || !std::isfinite(Tv)) return false;
+  double w[8];
+  species_rates(m, y, T, Tv, w);
+  Mix q;
+  double rR = 0.0;
+  for (int s = 0; s < ns; ++s) rR += y[s] * m.R[s];
+  q.T = T;
+  q.Tv = Tv;
+  q.p = rR * T;
+  double Sv = landau_teller(m, y, q);
+  for (int s = 0; s < ns; ++s) Sv += w[s] * vib_energy(m.R[s], m.theta_v[s], Tv);
+  for (int s = 0; s < ns; ++s) R[s] = y[s] - yn[s] - h * w[s];
+  R[ns] = y[ns] - yn[ns] - h * Sv;
+  return true;
+}
+
+// One node: u (all n_vars components) in, the new partial densities (and, two-temperature,
+// E_v) written to u.  Single temperature: Newton on R(Y) = Y - Y^n - h omega(Y) with T from
+// the fixed internal energy.  Two-temperature: Newton on the unknowns (Y, E_v) of
+// source_residual_tt; the step guard also keeps T_v within [T_v/2, 2 T_v], and convergence
+// also asks |dE_v| <= tol e (e the internal energy density).  Returns the number of Newton
+// updates taken, or -1 if the iteration did not converge.
 int source_implicit_node(const OrcProblem& P, double* u, double h, int max_it, double tol) {
   const OrcMech& m = *P.mech;
   const int ns = m.n_species, dim = P.dim;
-  double Yn[8], Y[8], rho = 0.0, kin = 0.0;
+  double Yn[9], Y[9], rho = 0.0, kin = 0.0;
   for (int s = 0; s < ns; ++s) {
     Yn[s] = Y[s] = u[s];
     rho += u[s];
   }
   for (int d = 0; d < dim; ++d) kin += u[ns + d] * u[ns + d];
   const double e = u[ns + dim] - 0.5 * kin / rho;
+  if (P.two_temperature) {
+    const int n = ns + 1;
+    Yn[ns] = Y[ns] = u[ns + dim + 1];
+    for (int it = 1; it <= max_it; ++it) {
+      double R[9], J[81], T0, Tv0;
+      if (!source_residual_tt(P, Y, Yn, e, h, R, &T0, &Tv0)) break;
+      for (int k = 0; k < n; ++k) {
+        const double eps = std::fmax(1e-7 * std::fabs(Y[k]), 1e-12);
+        double Yp[9], Rp[9];
+        for (int s = 0; s < n; ++s) Yp[s] = Y[s];
+        Yp[k] += eps;
+        if (!source_residual_tt(P, Yp, Yn, e, h, Rp, nullptr, nullptr)) return -1;
+        for (int i = 0; i < n; ++i) J[i * n + k] = (Rp[i] - R[i]) / eps;
+      }
+      if (!gauss_jordan(n, J, R)) return -1;
+      double lam = 1.0, Yt[9];
+      for (int k = 0; k < 30; ++k) {
+        for (int s = 0; s < n; ++s) Yt[s] = Y[s] - lam * R[s];
+        const double Tt = temperature_of(m, Yt, e - Yt[ns]);
+        const double Tvt = vib_temperature(m, Yt, Yt[ns]);
+        if (Tt >= 0.5 * T0 && Tt <= 2.0 * T0 && Tvt >= 0.5 * Tv0 && Tvt <= 2.0 * Tv0) break;
+        lam *= 0.5;
+      }
+      bool small = lam == 1.0 && std::fabs(R[ns]) <= tol * e;
+      for (int s = 0; s < n; ++s) {
+        if (s < ns) small = small && std::fabs(R[s]) <= tol * rho;
+        Y[s] = Yt[s];
+      }
+      if (small) {
+        for (int s = 0; s < ns; ++s) u[s] = Y[s];
+        u[ns + dim + 1] = Y[ns];
+        return it;
+      }
+    }
+    for (int s = 0; s < ns; ++s) u[s] = Y[s];
+    u[ns + dim + 1] = Y[ns];
+    return -1;
+  }
   for (int it = 1; it <= max_it; ++it) {
     double R[8], J[64];
     source_residual(m, Y, Yn, e, h, R);
@@ -2074,7 +2145,6 @@ int orc_ssp_steps(const OrcProblem* P, int scheme, double* U, double dt, int n_s
 // One implicit source substep S_h over a whole state, in place (reacting problems).
 // *iters receives the largest Newton count over the nodes (-1: some node did not converge).
 int orc_source_implicit(const OrcProblem* P, double* U, double h, int max_it, double tol, int* iters) {
-  if (P->two_temperature) return -6;  // the implicit substep is single-temperature
   int rc = check_problem(*P);
   if (rc) return rc;
   if (P->equations != ORC_NS_REACTING || !P->mech) return -1;
@@ -2087,7 +2157,6 @@ int orc_source_implicit(const OrcProblem* P, double* U, double h, int max_it, do
 // T_dt one step of the SSP scheme on the residual without its source part.
 int orc_strang_steps(const OrcProblem* P, int scheme, double* U, double dt, int n_steps, int max_it,
                      double tol, int* iters) {
-  if (P->two_temperature) return -6;  // the implicit substep is single-temperature
   int rc = check_problem(*P);
   if (rc) return rc;
   if (P->equations != ORC_NS_REACTING || !P->mech || (scheme != 3 && scheme != 54)) return -1;

@@ -257,6 +257,84 @@ def test_refused(orc):
                     mech=m, mu=0.0, two_temperature=True, bc=(1, 1, 0, 0, 0, 0))
     with pytest.raises(Exception):
         orc.rhs(P, np.ones(P.shape))
-    P = problem(orc, m)
-    with pytest.raises(Exception):
-        orc.source_implicit(P, np.ones(P.shape), 1e-6)
+
+
+# ---------------------------------------------------------------------------------------
+# the implicit substep with the E_v row (Sec. 3.1.3: the backward-Euler step takes the full
+# source vector, Eq. src_vector)
+# ---------------------------------------------------------------------------------------
+def one_node_problem(orc, mech):
+    return orc.Problem(dim=3, N=1, nel=(1, 1, 1), lo=(0.0,) * 3, hi=(1.0,) * 3, equations=orc.NS_REACTING,
+                       mech=mech, mu=0.0, two_temperature=True)
+
+
+def as_state(P, u):
+    return np.repeat(np.asarray(u, dtype=np.float64)[:, None, None], P.n_nodes, axis=2)
+
+
+def test_implicit_substep_matches_the_source_for_small_h(orc):
+    m = air()
+    rs = air_rho(T=3000.0)  # the seeded rates' time scale here is ~5e-10 s: h well below it
+    u = node(m, rs, 3000.0, 2000.0, vel=(50.0, 0.0, -20.0))
+    P = one_node_problem(orc, m)
+    S = orc.chem_source(P, u)
+    errs = []
+    for h in (1e-12, 1e-13):
+        U, it = orc.source_implicit(P, as_state(P, u), h)
+        d = (U[:, 0, 0] - u) / h
+        errs.append(max(np.abs(d[:5] - S[:5]).max() / np.abs(S[:5]).max(), abs(d[9] - S[9]) / abs(S[9])))
+        assert np.all(U[5:9, 0, 0] == u[5:9])  # momentum and E fixed
+    assert errs[1] < 2e-3 and errs[1] < errs[0] / 5, errs  # O(h) agreement
+
+
+def test_implicit_substep_solves_the_scalar_relaxation_equation(orc):
+    """Inert gas: only E_v changes; the step's E_v is the root of
+    x - E_v^n - h S_Ev(x), found here by bisection on the oracle's source."""
+    m = inert(air())
+    rs = air_rho(T=5000.0, p=2 * 101325.0)
+    u = node(m, rs, 5000.0, 1800.0)
+    P = one_node_problem(orc, m)
+    h = 3e-6
+
+    def g(x):
+        w = u.copy()
+        w[9] = x  # E fixed: the translational temperature follows from E - x
+        return x - u[9] - h * orc.chem_source(P, w)[9]
+
+    # bracket: E_v^n and the equilibrium E_v(T_eq) of the fixed energy, where S_Ev = 0
+    e_int = u[8] - sum(r * hh for r, hh in zip(rs, m["h0"]))
+    rcv = sum(r * c for r, c in zip(rs, m["cv"]))
+    a, b = 1000.0, 6000.0
+    for _ in range(200):
+        mid = 0.5 * (a + b)
+        a, b = (mid, b) if rcv * mid + sum(rs[k] * ev(m, k, mid) for k in range(5)) < e_int else (a, mid)
+    lo, hi = u[9], sum(rs[k] * ev(m, k, 0.5 * (a + b)) for k in range(5))
+    assert g(lo) < 0 < g(hi)
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        lo, hi = (mid, hi) if g(mid) < 0 else (lo, mid)
+    U, it = orc.source_implicit(P, as_state(P, u), h)
+    assert abs(U[9, 0, 0] - 0.5 * (lo + hi)) <= 1e-9 * u[9]
+    assert np.all(U[:5, 0, 0] == u[:5])
+
+
+def test_implicit_substep_conserves_and_reaches_equilibrium(orc):
+    m = air()
+    rs = air_rho(T=7000.0)
+    u = node(m, rs, 7000.0, 3000.0)
+    P = one_node_problem(orc, m)
+    U, it = orc.source_implicit(P, as_state(P, u), 2e-6)
+    v = U[:, 0, 0]
+    assert abs(sum(v[:5]) - sum(u[:5])) <= 1e-13 * sum(u[:5])
+    W = m["W"]
+    for atoms in ((2, 0, 1, 1, 0), (0, 2, 1, 0, 1)):  # N and O per molecule of N2, O2, NO, N, O
+        a0 = sum(k * u[s] / W[s] for s, k in enumerate(atoms))
+        a1 = sum(k * v[s] / W[s] for s, k in enumerate(atoms))
+        assert abs(a1 - a0) <= 1e-12 * a0
+    # inert gas and a step far beyond the relaxation time: T = T_v = the energy-fixed T_eq
+    mi = inert(air())
+    Pi = one_node_problem(orc, mi)
+    ui = node(mi, rs, 5000.0, 1500.0)
+    Ui, _ = orc.source_implicit(Pi, as_state(Pi, ui), 10.0)
+    T, _, Tv = orc.mixture_tt(Pi, Ui[:, 0, 0])
+    assert abs(T - Tv) <= 1e-6 * T
