@@ -526,6 +526,7 @@ def run_split(args):
     mu = wl.reacting_tgv_viscosity(mech)
     x, _, _ = dgsem.gll(n_deg)
     U = torch.from_numpy(wl.reacting_tgv_3d(nel, x, mech).reshape(9, -1)).cuda()
+    U_tt = torch.from_numpy(wl.reacting_tgv_3d(nel, x, mech, two_temperature=True).reshape(10, -1)).cuda()
     steps = max(2, args.steps // 20)
     mesh = dgsem.Mesh(3, n_deg, (nel,) * 3, (0.0,) * 3, (2 * math.pi,) * 3)
 
@@ -545,11 +546,12 @@ def run_split(args):
     out = {"workload": f"3D reacting NS, 5-species air, 17 reactions, N=3, {nel}^3, BR1 Re=1600, Rusanov; "
                        "Strang split: SSP-RK54 transport + implicit backward-Euler chemistry substeps",
            "dt": SPLIT_DT, "steps": steps}
-    for name, prec in (("fp64", dgsem.FP64), ("fp32_mixed", dgsem.FP32_MIXED)):
+    for name, prec, tt in (("fp64", dgsem.FP64, False), ("fp32_mixed", dgsem.FP32_MIXED, False),
+                           ("two_temperature_fp64", dgsem.FP64, True)):
         S = dgsem.Solver(mesh, equations=dgsem.DG_NS_REACTING, mu=mu, prandtl=0.72, mechanism=mech,
                          precision=prec, p_ref=101325.0 if prec == dgsem.FP32_MIXED else 0.0,
-                         time_scheme=dgsem.SSPRK54, chem_split=True)
-        S.set_state(U)
+                         time_scheme=dgsem.SSPRK54, chem_split=True, two_temperature=tt)
+        S.set_state(U_tt if tt else U)
         transport_dt = S.max_dt(1.0)
         S.rk_step(SPLIT_DT, 3)
         S.check()
@@ -574,10 +576,11 @@ def run_split(args):
         r = {"ms_per_step": ms, "sim_seconds_per_s": SPLIT_DT / (ms * 1e-3),
              "transport_dt_bound": transport_dt, "gpu_launches_per_step": 2 * 5 + 2,
              "newton_updates_per_node_per_substep": upd_steps / (2 * steps * nodes),
-             "source_substep": {"kernel": "k_source_implicit<5,double>", "ms": chem_ms, "nodes": nodes,
+             "source_substep": {"kernel": "k_source_implicit_tt<5,double>" if tt else "k_source_implicit<5,double>",
+                                "ms": chem_ms, "nodes": nodes,
                                 "newton_updates": upd, "updates_per_node": upd / nodes,
                                 "share_of_step": 2 * chem_ms / ms}}
-        if FP64_INSTR_PER_NEWTON_UPDATE:
+        if FP64_INSTR_PER_NEWTON_UPDATE and not tt:
             ach = upd * FP64_INSTR_PER_NEWTON_UPDATE / (chem_ms * 1e-3) / 1e9
             r["source_substep"]["roofline"] = {
                 "bound": "alu", "unit": "G FP64 instr/s", "achieved": ach, "peak": FP64_PEAK_GINSTR,

@@ -208,7 +208,7 @@ typedef struct {
   double sharpness; /* steepness s of the sigmoid (<= 0: ln 9999) */
   /* Two-temperature model (Sec. 2 "Thermal nonequilibrium coupling" and "Total energy and
    * closure"; Sec. 3.1.3 Eqs. src_vector, src_reaction_rate, src_landau_teller): DG_NS_REACTING
-   * with 5 species, periodic meshes, no Strang split (else DG_EUNSUPPORTED).  The state gains
+   * with 5 species, periodic meshes (else DG_EUNSUPPORTED).  The state gains
    * E_v, U = (rho_1..rho_ns, rho u, rho v, rho w, E, E_v); cv_s is the translational-rotational
    * heat capacity and E = sum rho_s (cv_s T + h0_s) + E_v + rho|u|^2/2; T_v solves
    * E_v = sum rho_s e_v,s(T_v) (harmonic oscillators of chem->theta_v); the E_v flux is E_v u,
@@ -359,8 +359,7 @@ DG_API dg_status dg_max_dt_noalloc(const dg_mesh_desc* inst, int n_inst, double 
                                    double* dt_out, const char** msg);
 
 /* Implicit source substep S_h of the Strang split (Sec. 3.1.3, Eqs. strang_split and
- * source_residual), single-temperature DG_NS_REACTING contexts only (else DG_EUNSUPPORTED).
- * At every node the partial densities
+ * source_residual), DG_NS_REACTING contexts only.  At every node the partial densities
  * Y = (rho_1..rho_ns) take one backward-Euler step of length h >= 0 of the chemical source,
  *   Y* - Y - h omega(Y*) = 0,
  * solved by Newton's method from Y* = Y: the Jacobian by forward differences, column k with
@@ -370,7 +369,13 @@ DG_API dg_status dg_max_dt_noalloc(const dg_mesh_desc* inst, int n_inst, double 
  * temperature of an iterate follows from the fixed internal energy E - |rho u|^2 / (2 rho).
  * U and Uout are device pointers of dg_state_size() doubles; they may be equal (in place)
  * but must not otherwise overlap.  A node still unconverged after newton_max_it updates
- * keeps its last iterate and makes dg_check() return DG_ECONVERGENCE.  Asynchronous. */
+ * keeps its last iterate and makes dg_check() return DG_ECONVERGENCE.  Two-temperature
+ * contexts: the unknowns are (Y, E_v) and the source is the full vector of Eq. src_vector
+ * (omega_s at the controlling temperatures; E_v row Q_T-v + sum omega_s e_v,s(T_v)); T follows
+ * from the fixed internal energy less E_v, T_v from E_v (by Newton's method inside each
+ * evaluation); the Jacobian is (ns+1)^2; the step is also halved while T_v leaves
+ * [T_v/2, 2 T_v]; convergence also needs |dE_v| <= newton_tol * (E - |rho u|^2/(2 rho)).
+ * Asynchronous. */
 DG_API dg_status dg_source_step(dg_ctx* ctx, const double* U, double h, double* Uout);
 
 /* Hennemann-Gassner blending coefficients of every element for the state U (device, SoA as

@@ -913,6 +913,8 @@ dg_status run_source(dg_ctx* c, const double* U, double* out, double h, cudaStre
   a.ln1e4 = std::log(1.0e4);
   a.copy_rest = (U != out) ? 1 : 0;
   a.updates = c->lam + 2;
+  const int bin = buf_index(c, U);
+  if (c->tt && bin >= 0 && c->pvalid[bin]) a.tin = c->pT[bin];  // warm start of T_v
   const int bout = buf_index(c, out);
   if (bout >= 0) {
     a.pout = c->pc[bout];
@@ -923,7 +925,7 @@ dg_status run_source(dg_ctx* c, const double* U, double* out, double h, cudaStre
   for (size_t i = 0; i < c->inst.size(); ++i) {
     a.base = c->offs[i];
     a.n = n_elem_of(c->inst[i]) * n_p_of(c->inst[i]);
-    cudaError_t e = dg::launch_source_implicit(c->n_species, fp32, a, s);
+    cudaError_t e = dg::launch_source_implicit(c->n_species, c->tt, fp32, a, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "implicit source launch");
   }
   return DG_OK;
@@ -1019,8 +1021,8 @@ dg_status dg_init_mesh(const dg_mesh_desc* inst, int n_inst, const dg_physics* p
   const bool navier_stokes = phys->equations != DG_EULER;
   const int tt = phys->two_temperature;
   if (tt != 0 && tt != 1) return DG_EINVAL;
-  if (tt) {  // two-temperature: reacting air on periodic meshes, source in the residual
-    if (phys->equations != DG_NS_REACTING || phys->chem_split) return DG_EUNSUPPORTED;
+  if (tt) {  // two-temperature: reacting air on periodic meshes
+    if (phys->equations != DG_NS_REACTING) return DG_EUNSUPPORTED;
     for (int i = 0; i < n_inst; ++i)
       for (int l = 0; l < 3; ++l)
         if (inst[i].periodic[l] != 1) return DG_EUNSUPPORTED;
@@ -1520,7 +1522,6 @@ dg_status dg_source_step(dg_ctx* c, const double* U, double h, double* Uout) {
   if (!U || !Uout) return fail(c, DG_EINVAL, "null pointer");
   if (c->phys.equations != DG_NS_REACTING)
     return fail(c, DG_EUNSUPPORTED, "the implicit source step exists for reacting mixtures");
-  if (c->tt) return fail(c, DG_EUNSUPPORTED, "the implicit source step is single-temperature");
   if (!std::isfinite(h) || h < 0.0) return fail(c, DG_EINVAL, "h must be finite and >= 0");
   return run_source(c, U, Uout, h, c->stream);
 }

@@ -266,6 +266,8 @@ struct SourceArgs {
   const MechDev* mech;
   void* pout;          // primitive cache of the output (flux type; null: not written)
   double* tout;
+  const double* tin;   // two-temperature: the FP64 cache rows of the input (T, T_v) or null;
+                       //   its T_v starts the node's T_v iterations
   long long stride, base, n;
   double h;            // substep length
   double tol;          // stop when max |dY| <= tol * rho
@@ -274,7 +276,7 @@ struct SourceArgs {
   int copy_rest;       // 1: also copy momentum and energy (out != U)
   unsigned long long* updates;  // device counter: Newton updates taken, summed over nodes
 };
-cudaError_t launch_source_implicit(int ns, int fp32, const SourceArgs& a, cudaStream_t s);
+cudaError_t launch_source_implicit(int ns, int tt, int fp32, const SourceArgs& a, cudaStream_t s);
 
 // Element-wise evaluation of a device math routine for the tests: kind 0 the library's
 // table-driven exp, 1 its Newton reciprocal, 2 CUDA's exp, 3 CUDA's 1/x.

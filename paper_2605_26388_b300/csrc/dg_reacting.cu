@@ -862,7 +862,7 @@ constexpr int kCT = 128;  // threads per CTA of the implicit source kernel
 
 // Temperature of the partial densities Y at the fixed internal energy e.
 template <int NS>
-__device__ __forceinline__ double temp_of(const double (&Y)[NS], const double* sp, double e) {
+__device__ __forceinline__ double temp_of(const double* Y, const double* sp, double e) {
   double rcv = 0.0, rh0 = 0.0;
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
@@ -884,6 +884,168 @@ __device__ __forceinline__ void be_residual(const MechDev* __restrict__ mech, in
   species_rates<NS, false>(mech, nr, T, T, X, kCT, e2tab, ln1e4, om);
 #pragma unroll
   for (int s = 0; s < NS; ++s) R[s] = fma(-h, om[s], Y[s] - Yn[s]);
+}
+
+// Two-temperature residual of the unknowns y = (Y, E_v) (Sec. 3.1.3: the substep takes the
+// full source vector, Eq. src_vector): T from the fixed internal energy e less E_v, T_v by
+// vib_temperature from tv (updated in place: the warm start of the next evaluation),
+// R = y - y^n - h (omega, Q_T-v + sum omega_s e_v,s(T_v)).  Returns T; false in ok when T or
+// T_v is not positive or the T_v iteration did not converge.
+template <int NS>
+__device__ __forceinline__ double be_residual_tt(const MechDev* __restrict__ mech, int nr, const double* sp,
+                                                 const double* mw, const double (&y)[NS + 1],
+                                                 const double (&yn)[NS + 1], double e, double h, double* X,
+                                                 const double* e2tab, double ln1e4, double& tv,
+                                                 double (&R)[NS + 1], bool& ok) {
+  const double T = temp_of<NS>(y, sp, e - y[NS]);
+  double dEv;
+  bool conv;
+  tv = vib_temperature<NS>(y, sp, y[NS], tv, e2tab, dEv, conv);
+  ok = conv && T > 0.0 && tv > 0.0;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) X[s * kCT] = y[s] * sp[3 * NS + s];
+  double om[NS];
+  species_rates<NS, true>(mech, nr, T, tv, X, kCT, e2tab, ln1e4, om);
+  const double Sv = vib_source<NS>(y, sp, mw, T, tv, om, e2tab);
+#pragma unroll
+  for (int s = 0; s < NS; ++s) R[s] = fma(-h, om[s], y[s] - yn[s]);
+  R[NS] = fma(-h, Sv, y[NS] - yn[NS]);
+  return T;
+}
+
+// Two-temperature implicit substep: Newton on (Y, E_v) as in k_source_implicit, the forward-
+// difference Jacobian (NS + 2 residual evaluations per update), Gauss-Jordan on the
+// (NS+1)^2 system, the guarded step also keeping T_v within [T_v/2, 2 T_v], convergence once
+// a full step has max_s |dY_s| <= tol rho and |dE_v| <= tol e.
+template <int NS, class R>
+__global__ void __launch_bounds__(kCT) k_source_implicit_tt(const SourceArgs a) {
+  constexpr int NU = NS + 1;
+  __shared__ double sp[5 * NS];
+  __shared__ double mw[2 * NS * NS];
+  __shared__ double e2tab[64];
+  __shared__ double Xs[(NS + 1) * kCT];
+  const int t = threadIdx.x;
+  load_species<NS>(a.mech, sp, 5);
+  for (int k = t; k < 64; k += kCT) e2tab[k] = a.mech->exp2tab[k];
+  for (int k = t; k < 2 * NS * NS; k += kCT) {
+    const int w = k / (NS * NS), s2 = (k / NS) % NS, r2 = k % NS;
+    mw[k] = w ? a.mech->mwC[s2][r2] : a.mech->mwA[s2][r2];
+  }
+  double* X = Xs + t;
+  X[NS * kCT] = 1.0;
+  __syncthreads();
+  const long long q = blockIdx.x * (long long)kCT + t;
+  if (q >= a.n) return;
+  const long long gi = a.base + q;
+  const int nr = a.mech->nr;
+  double u[NS + 5];
+#pragma unroll
+  for (int v = 0; v < NS + 5; ++v) u[v] = a.U[v * a.stride + gi];
+  double yn[NU], y[NU], rho = 0.0;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    yn[s] = y[s] = u[s];
+    rho += u[s];
+  }
+  yn[NS] = y[NS] = u[NS + 4];
+  const double kin = fma(u[NS], u[NS], fma(u[NS + 1], u[NS + 1], u[NS + 2] * u[NS + 2]));
+  const double e = u[NS + 3] - 0.5 * kin * rcp64(rho);
+  const double lim = a.tol * rho, lim_v = a.tol * e;
+  double tv = a.tin ? a.tin[a.stride + gi] : 0.0;  // T_v of the input state when cached
+  bool done = false;
+  int it = 0;
+  for (; it < a.max_it && !done; ++it) {
+    double Rv[NU], J[NU][NU];
+    bool ok;
+    const double T0 = be_residual_tt<NS>(a.mech, nr, sp, mw, y, yn, e, a.h, X, e2tab, a.ln1e4, tv, Rv, ok);
+    if (!ok) break;
+    const double tv0 = tv;
+#pragma unroll
+    for (int k = 0; k < NU; ++k) {
+      double yp[NU], Rp[NU];
+#pragma unroll
+      for (int s = 0; s < NU; ++s) yp[s] = y[s];
+      const double eps = fmax(1e-7 * fabs(y[k]), 1e-12);
+      yp[k] += eps;
+      double tvp = tv0;
+      bool okp;
+      be_residual_tt<NS>(a.mech, nr, sp, mw, yp, yn, e, a.h, X, e2tab, a.ln1e4, tvp, Rp, okp);
+      const double ie = rcp64(eps);
+#pragma unroll
+      for (int i = 0; i < NU; ++i) J[i][k] = (Rp[i] - Rv[i]) * ie;
+    }
+#pragma unroll
+    for (int k = 0; k < NU; ++k) {
+#pragma unroll
+      for (int i = k + 1; i < NU; ++i) {
+        if (fabs(J[i][k]) > fabs(J[k][k])) {
+#pragma unroll
+          for (int j = 0; j < NU; ++j) {
+            const double tmp = J[i][j];
+            J[i][j] = J[k][j];
+            J[k][j] = tmp;
+          }
+          const double tmp = Rv[i];
+          Rv[i] = Rv[k];
+          Rv[k] = tmp;
+        }
+      }
+      const double d = rcp64(J[k][k]);
+#pragma unroll
+      for (int j = 0; j < NU; ++j) J[k][j] *= d;
+      Rv[k] *= d;
+#pragma unroll
+      for (int i = 0; i < NU; ++i) {
+        if (i == k) continue;
+        const double f = J[i][k];
+#pragma unroll
+        for (int j = 0; j < NU; ++j) J[i][j] = fma(-f, J[k][j], J[i][j]);
+        Rv[i] = fma(-f, Rv[k], Rv[i]);
+      }
+    }
+    double lam = 1.0, yt[NU];
+    for (int k = 0; k < 30; ++k) {
+#pragma unroll
+      for (int s = 0; s < NU; ++s) yt[s] = fma(-lam, Rv[s], y[s]);
+      const double Tt = temp_of<NS>(yt, sp, e - yt[NS]);
+      double dEv, tvt = tv0;
+      bool conv;
+      tvt = vib_temperature<NS>(yt, sp, yt[NS], tvt, e2tab, dEv, conv);
+      if (Tt >= 0.5 * T0 && Tt <= 2.0 * T0 && tvt >= 0.5 * tv0 && tvt <= 2.0 * tv0) break;
+      lam *= 0.5;
+    }
+    bool small = lam == 1.0 && fabs(Rv[NS]) <= lim_v;
+#pragma unroll
+    for (int s = 0; s < NU; ++s) {
+      if (s < NS) small = small && fabs(Rv[s]) <= lim;
+      y[s] = yt[s];
+    }
+    done = small;
+  }
+  {
+    const unsigned mask = __activemask();
+    const unsigned sum = __reduce_add_sync(mask, (unsigned)it);
+    if ((threadIdx.x & 31) == __ffs(mask) - 1) atomicAdd(a.updates, (unsigned long long)sum);
+  }
+  unsigned flag = done ? 0u : 4u;
+  bool finite = true;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    u[s] = y[s];
+    finite = finite && finite64(y[s]);
+    a.out[s * a.stride + gi] = y[s];
+  }
+  u[NS + 4] = y[NS];
+  finite = finite && finite64(y[NS]);
+  a.out[(NS + 4) * a.stride + gi] = y[NS];
+  if (a.copy_rest) {
+#pragma unroll
+    for (int v = NS; v < NS + 4; ++v) a.out[v * a.stride + gi] = u[v];
+  }
+  if (a.pout) flag |= write_prims<NS, true, R>(u, sp, a.p_ref, reinterpret_cast<R*>(a.pout), a.tout, a.stride, gi,
+                                               tv, e2tab);
+  if (!finite) flag |= 1u;
+  if (flag) atomicOr(a.err, flag);
 }
 
 template <int NS, class R>
@@ -1139,10 +1301,13 @@ cudaError_t launch_react_prims(int ns, int tt, int fp32, const double* U, long l
   return cudaGetLastError();
 }
 
-cudaError_t launch_source_implicit(int ns, int fp32, const SourceArgs& a, cudaStream_t s) {
+cudaError_t launch_source_implicit(int ns, int tt, int fp32, const SourceArgs& a, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
   const unsigned grid = (unsigned)((a.n + kCT - 1) / kCT);
-  if (ns == 1 && fp32) k_source_implicit<1, float><<<grid, kCT, 0, s>>>(a);
+  if (tt && ns == 5 && fp32) k_source_implicit_tt<5, float><<<grid, kCT, 0, s>>>(a);
+  else if (tt && ns == 5) k_source_implicit_tt<5, double><<<grid, kCT, 0, s>>>(a);
+  else if (tt) return cudaErrorInvalidValue;
+  else if (ns == 1 && fp32) k_source_implicit<1, float><<<grid, kCT, 0, s>>>(a);
   else if (ns == 1) k_source_implicit<1, double><<<grid, kCT, 0, s>>>(a);
   else if (ns == 5 && fp32) k_source_implicit<5, float><<<grid, kCT, 0, s>>>(a);
   else if (ns == 5) k_source_implicit<5, double><<<grid, kCT, 0, s>>>(a);

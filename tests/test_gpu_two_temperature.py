@@ -208,3 +208,38 @@ def test_full_size_sampled(env, orc):
         floor = 16 * 2.2e-16 * (2.0 / (TWO_PI / nel)) * dabs * np.linalg.norm(F) / np.linalg.norm(ref[g])
         assert err <= 1e-12 + floor, (g, err, floor)
     S.close()
+
+
+# ---------------------------------------------------------------------------------------
+# the implicit substep with the E_v row and the Strang split
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("h", [1e-9, 1e-7])
+def test_source_step_matches_oracle(env, orc, h):
+    torch, dg = env
+    mech = wl.air5_mechanism()
+    S, P = setup(orc, dg, 3, 3, mech, wl.reacting_tgv_viscosity(mech), chem_split=True, time_scheme=dg.SSPRK54)
+    U = state(orc, 3, 3, rel=0.0)
+    ref, it = orc.source_implicit(P, U.copy(), h)
+    assert it > 0
+    got = S.source_step(dev(torch, U), h).cpu().numpy().reshape(U.shape)
+    S.check()
+    rho = U[:5].sum(axis=0)
+    assert np.abs(got[:5] - ref[:5]).max() / rho.max() <= 1e-10
+    assert np.abs(got[9] - ref[9]).max() <= 1e-10 * np.abs(ref[9]).max()
+    assert np.all(got[5:9] == U[5:9])
+    assert S.newton_updates() > 0
+    S.close()
+
+
+def test_strang_split_steps_match_oracle(env, orc):
+    torch, dg = env
+    mech = wl.air5_mechanism()
+    S, P = setup(orc, dg, 2, 3, mech, wl.reacting_tgv_viscosity(mech), chem_split=True, time_scheme=dg.SSPRK54)
+    U = state(orc, 2, 3, rel=0.0)
+    dt = 1e-7
+    S.set_state(dev(torch, U))
+    S.rk_step(dt, 3)
+    S.check()
+    got = S.get_state().cpu().numpy().reshape(U.shape)
+    ref, _ = orc.strang_steps(P, orc.SSPRK54, U.copy(), dt, 3)
+    assert grouped_rel(got, ref) <= 1e-9
