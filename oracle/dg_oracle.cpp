@@ -87,7 +87,7 @@ struct OrcProblem {
   const double* coords;       // Euler, periodic: node coordinates [d][elem][node] of a curved
                               // mesh on the same element topology (null: the Cartesian box)
   int two_temperature;        // ORC_NS_REACTING: 1 -- the two-temperature model (E_v appended
-                              // to the state), periodic meshes, residual only
+                              // to the state)
 };
 
 }  // extern "C"
@@ -922,10 +922,8 @@ int check_problem(const OrcProblem& P) {
     if (P.rho_floor > 0.0 || P.p_floor > 0.0) return -6;
     if (P.mu < 0.0 || !(P.prandtl > 0.0)) return -1;
     if (P.shock || P.coords) return -6;
-    if (P.two_temperature) {  // periodic meshes only
+    if (P.two_temperature) {
       if (P.two_temperature != 1) return -1;
-      for (int f = 0; f < 6; ++f)
-        if (P.bc[f]) return -6;
       for (int s = 0; s < P.mech->n_species; ++s)
         if (!(P.mech->theta_v[s] >= 0.0)) return -1;
     }
@@ -1169,7 +1167,7 @@ int check_reacting_bc(const OrcProblem& P) {
       for (int v = 0; v < nv; ++v)
         if (!std::isfinite(P.bc_state[f][v])) return -1;
       Mix q = mixture(P, P.bc_state[f]);
-      if (!(q.rho > 0.0) || !(q.T > 0.0)) return -1;
+      if (!(q.rho > 0.0) || !(q.T > 0.0) || !(q.Tv > 0.0)) return -1;
     }
     if (P.bc[f] == ORC_BC_NOSLIP_ISOTHERMAL &&
         !(P.bc_state[f][0] > 0.0 && std::isfinite(P.bc_state[f][0])))
@@ -1206,31 +1204,34 @@ void mix_boundary_flux(const OrcProblem& P, int f, int l, const double* uown, bo
   else mix_rusanov(P, l, ub, uown, F);
 }
 
-// BR1 trace W^ of W = (u, v, w, T) at domain face f with normal axis l, from the element's
-// own trace Wo (Sec. 3.1.2: at a no-slip adiabatic wall the velocity is zero and (rho, T)
-// come from the interior; an isothermal wall also fixes T; a slip wall mirrors the velocity
-// across the wall).  READINGS: the trace is the boundary's value of W itself; at a slip
-// wall, the BR1 average of the interior trace and its mirror image (normal velocity 0,
-// tangential velocity and T kept); inflow and Dirichlet: W of the prescribed state (the
-// far-field Dirichlet condition); outflow: the interior trace (no gradient lift).
+// BR1 trace W^ of W = (u, v, w, T, T_v) at domain face f with normal axis l, from the
+// element's own trace Wo (Sec. 3.1.2: at a no-slip adiabatic wall the velocity is zero and
+// (rho, T) come from the interior; an isothermal wall also fixes T; a slip wall mirrors the
+// velocity across the wall).  READINGS: the trace is the boundary's value of W itself; at a
+// slip wall, the BR1 average of the interior trace and its mirror image (normal velocity 0,
+// tangential velocity, T and T_v kept); an isothermal wall holds both modes at T_wall
+// (T_v = T_wall), an adiabatic one keeps the interior T_v; inflow and Dirichlet: W of the
+// prescribed state (the far-field Dirichlet condition); outflow: the interior trace (no
+// gradient lift).  Single temperature: T_v = T throughout.
 void wall_trace(const OrcProblem& P, int f, int l, const double* Wo, double* Wh) {
   switch (P.bc[f]) {
     case ORC_BC_SLIP_WALL: {
-      double Wm[4] = {Wo[0], Wo[1], Wo[2], Wo[3]};
+      double Wm[5] = {Wo[0], Wo[1], Wo[2], Wo[3], Wo[4]};
       Wm[l] = -Wo[l];
-      for (int q = 0; q < 4; ++q) Wh[q] = 0.5 * (Wo[q] + Wm[q]);
+      for (int q = 0; q < 5; ++q) Wh[q] = 0.5 * (Wo[q] + Wm[q]);
       return;
     }
     case ORC_BC_NOSLIP_ADIABATIC:
       Wh[0] = Wh[1] = Wh[2] = 0.0;
       Wh[3] = Wo[3];
+      Wh[4] = Wo[4];
       return;
     case ORC_BC_NOSLIP_ISOTHERMAL:
       Wh[0] = Wh[1] = Wh[2] = 0.0;
-      Wh[3] = P.bc_state[f][0];
+      Wh[3] = Wh[4] = P.bc_state[f][0];
       return;
     case ORC_BC_OUTFLOW:
-      for (int q = 0; q < 4; ++q) Wh[q] = Wo[q];
+      for (int q = 0; q < 5; ++q) Wh[q] = Wo[q];
       return;
     default: {  // inflow, Dirichlet
       Mix b = mixture(P, P.bc_state[f]);
@@ -1238,6 +1239,7 @@ void wall_trace(const OrcProblem& P, int f, int l, const double* Wo, double* Wh)
       Wh[1] = b.v[1];
       Wh[2] = b.v[2];
       Wh[3] = b.T;
+      Wh[4] = b.Tv;
     }
   }
 }
@@ -1248,9 +1250,10 @@ void viscous_flux(const OrcProblem& P, int l, const double* u, const double* g, 
 // node u and its gradient g (Sec. 3.1.2 boundary kernels: the viscous operator of a wall
 // enforces no slip and, adiabatic, no heat flux).  READINGS: slip wall: the BR1 average of
 // the interior flux and its mirror image -- the normal-momentum row (tau_ll) kept, the
-// tangential rows and the energy row 0; no-slip adiabatic wall: the interior stress rows,
-// energy 0 (a wall at rest does no work and passes no heat); no-slip isothermal wall: the
-// interior stress rows, energy k dT/dx_l (heat conducted through the wall, no work); inflow,
+// tangential rows and the energy (and E_v) rows 0; no-slip adiabatic wall: the interior
+// stress rows, energy and E_v rows 0 (a wall at rest does no work and passes no heat);
+// no-slip isothermal wall: the interior stress rows, energy k dT/dx_l + k_v dT_v/dx_l and
+// E_v row k_v dT_v/dx_l (heat of both modes conducted through the wall, no work); inflow,
 // outflow, Dirichlet: the interior flux (no viscous lift).
 void viscous_boundary_flux(const OrcProblem& P, int f, int l, const double* u, const double* g,
                            double* F) {
@@ -1267,11 +1270,16 @@ void viscous_boundary_flux(const OrcProblem& P, int f, int l, const double* u, c
       return;
     }
     case ORC_BC_NOSLIP_ADIABATIC:
-      F[ns + dim] = 0.0;
+      for (int v = ns + dim; v < nv; ++v) F[v] = 0.0;
       return;
     case ORC_BC_NOSLIP_ISOTHERMAL: {
       Mix q = mixture(P, u);
       F[ns + dim] = P.mu * q.cp / P.prandtl * g[3 * 3 + l];
+      if (P.two_temperature) {
+        const double qv = P.mu * q.cvv / P.prandtl * g[4 * 3 + l];
+        F[ns + dim] += qv;
+        F[ns + dim + 1] = qv;
+      }
       return;
     }
     default:
@@ -1281,8 +1289,7 @@ void viscous_boundary_flux(const OrcProblem& P, int f, int l, const double* u, c
 
 // BR1 gradient (Sec. 3.1.2 Eq. br1_avg; App. A "Viscous Volume and Interface Fluxes") of
 // W = (u, v, w, T, T_v) on element e: S_l = (2/dx_l) [D W + (upper face) (W^ - W_N)/w_N
-// - (lower face) (W^ - W_0)/w_0], W^ = (W_L + W_R)/2 (at a domain face: wall_trace; the
-// two-temperature model has no boundary conditions, so W^'s T_v row is never a wall's).
+// - (lower face) (W^ - W_0)/w_0], W^ = (W_L + W_R)/2 (at a domain face: wall_trace).
 // Layout G[(node * 5 + q) * 3 + l]; T_v = T in the single-temperature model.
 void br1_gradient(const OrcProblem& P, const Mesh& M, const Ops& ops, const double* U, int e,
                   double* G) {
@@ -1313,7 +1320,6 @@ void br1_gradient(const OrcProblem& P, const Mesh& M, const Ops& ops, const doub
         const int fb = boundary_face(P, M, e, l, 1);
         if (fb >= 0) {
           wall_trace(P, fb, l, Wo, Wh);
-          Wh[4] = Wh[3];
         } else {
           int nk[3] = {ijk[0], ijk[1], ijk[2]};
           nk[l] = 0;
@@ -1326,7 +1332,6 @@ void br1_gradient(const OrcProblem& P, const Mesh& M, const Ops& ops, const doub
         const int fb = boundary_face(P, M, e, l, 0);
         if (fb >= 0) {
           wall_trace(P, fb, l, Wo, Wh);
-          Wh[4] = Wh[3];
         } else {
           int nk[3] = {ijk[0], ijk[1], ijk[2]};
           nk[l] = N;

@@ -252,11 +252,120 @@ def test_vibrational_conduction_converges(orc):
 
 
 def test_refused(orc):
+    """A far-field state must have a vibrational temperature (E_v > 0)."""
     m = air()
+    ub = node(m, air_rho(T=4000.0), 4000.0, 3000.0)
+    ub[9] = 0.0
     P = orc.Problem(dim=3, N=2, nel=(2, 2, 2), lo=(0.0,) * 3, hi=(1.0,) * 3, equations=orc.NS_REACTING,
-                    mech=m, mu=0.0, two_temperature=True, bc=(1, 1, 0, 0, 0, 0))
+                    mech=m, mu=0.0, two_temperature=True, bc=(4, 4, 0, 0, 0, 0), bc_state=(ub, ub, None, None, None, None))
     with pytest.raises(Exception):
         orc.rhs(P, np.ones(P.shape))
+
+
+# ---------------------------------------------------------------------------------------
+# walls (Sec. 3.1.2 boundary kernels with the vibrational mode)
+# ---------------------------------------------------------------------------------------
+def test_isothermal_walls_heat_both_modes(orc):
+    """Inert gas at rest in equilibrium (T = T_v = T0) between isothermal walls at T_w: the
+    BR1 traces of T and T_v both take T_w, so the energy row is -/+ s^2 (k + k_v) D (T_w - T0)/w
+    and the E_v row -/+ s^2 k_v D (T_w - T0)/w along wall-normal lines (no Landau-Teller
+    exchange at equilibrium)."""
+    m = inert(air())
+    N, nel, L, mu, T0 = 3, (2, 3, 2), 1.0, 2e-3, 3000.0
+    Tw = (3600.0, 2500.0)
+    rs = air_rho(T=T0, p=1.0e4)
+    rho = sum(rs)
+    _, w = orc.gll(N)
+    D = orc.dmat(N)
+    s = 2.0 / (L / nel[1])
+    P = orc.Problem(dim=3, N=N, nel=nel, lo=(0.0,) * 3, hi=(L,) * 3, equations=orc.NS_REACTING, mech=m, mu=mu,
+                    prandtl=0.72, two_temperature=True, bc=(0, 0, 6, 6, 0, 0),
+                    bc_state=(None, None, (Tw[0],), (Tw[1],), None, None))
+    one = np.ones((P.n_elem, P.n_nodes))
+    U = wl.reacting_conserved([r * one for r in rs], [0 * one] * 3, T0 * one, m, Tv=T0 * one)
+    R = orc.rhs(P, U.reshape(P.shape))
+    k = mu * sum(rs[q] * (m["cv"][q] + m["R"][q]) for q in range(5)) / rho / 0.72
+    cvv = 0.0
+    for q in range(5):
+        th = m["theta_v"][q]
+        if th > 0:
+            x = th / T0
+            cvv += rs[q] * m["R"][q] * x * x * math.exp(x) / math.expm1(x) ** 2
+    kv = mu * cvv / rho / 0.72
+    n1, nx, ny = N + 1, nel[0], nel[1]
+    want_e = np.zeros((P.n_elem, P.n_nodes))
+    want_v = np.zeros_like(want_e)
+    for e in range(P.n_elem):
+        cy = (e // nx) % ny
+        for nd in range(P.n_nodes):
+            j = (nd // n1) % n1
+            for kk, out in ((k + kv, want_e), (kv, want_v)):
+                if cy == 0:
+                    out[e, nd] += -s * s * kk * D[j, 0] * (Tw[0] - T0) / w[0]
+                if cy == ny - 1:
+                    out[e, nd] += s * s * kk * D[j, N] * (Tw[1] - T0) / w[N]
+    scale = np.abs(want_e).max()
+    assert np.abs(R[8] - want_e).max() <= 1e-10 * scale
+    assert np.abs(R[9] - want_v).max() <= 1e-10 * scale
+    assert np.abs(R[:8]).max() <= 1e-10 * scale
+
+
+@pytest.mark.parametrize("parts", [0, 2])
+def test_slip_walls_are_mirrors_with_two_temperatures(orc, parts):
+    m = air()
+    N, nx, ny, mu = 3, 3, 2, 2e-3
+    xi, _ = orc.gll(N)
+
+    def prob(nel, lo, bc):
+        return orc.Problem(dim=2, N=N, nel=nel, lo=lo, hi=(1.0, 1.0), equations=orc.NS_REACTING, mech=m, mu=mu,
+                           prandtl=0.72, parts=parts, two_temperature=True, bc=bc)
+
+    def fields(X):
+        x, y = X
+        rho_s = [0.01 * (1.0 + 0.2 * np.cos(np.pi * x) * (1.0 + 0.3 * np.sin(2 * np.pi * y + q))) for q in range(5)]
+        u = 300.0 * np.cos(2.0 * x + 0.4)
+        v = 180.0 * np.cos(np.pi * x) * np.sin(2 * np.pi * y)
+        T = 5000.0 * (1.0 + 0.1 * np.cos(np.pi * x) * np.cos(2 * np.pi * y))
+        Tv = 3500.0 * (1.0 + 0.1 * np.cos(np.pi * x) * np.sin(2 * np.pi * y))
+        return rho_s, u, v, T, Tv
+
+    Pw = prob((nx, ny), (0.0, 0.0), (1, 1, 0, 0, 0, 0))
+    Pm = prob((2 * nx, ny), (-1.0, 0.0), (0,) * 6)
+    Xw = wl.node_coordinates(2, Pw.nel, Pw.lo, Pw.hi, xi)
+    Xm = wl.node_coordinates(2, Pm.nel, Pm.lo, Pm.hi, xi)
+    rho_s, u, v, T, Tv = fields(Xw)
+    Uw = wl.reacting_conserved(rho_s, [u, v], T, m, Tv=Tv).reshape(Pw.shape)
+    left = (np.arange(Pm.n_elem) % (2 * nx)) < nx
+    xs = np.where(left[:, None], -Xm[0], Xm[0])
+    rho_s, u, v, T, Tv = fields(np.stack([xs, Xm[1]]))
+    u = np.where(left[:, None], -u, u)
+    Um = wl.reacting_conserved(rho_s, [u, v], T, m, Tv=Tv).reshape(Pm.shape)
+    Rw, Rm = orc.rhs(Pw, Uw), orc.rhs(Pm, Um)
+    right = np.array([(nx + i) + 2 * nx * j for j in range(ny) for i in range(nx)])
+    for g in ([5, 6], [7], [8]):
+        scale = np.abs(Rm[g]).max()
+        assert scale > 0
+        assert np.abs(Rw[g] - Rm[g][:, right, :]).max() <= 1e-11 * scale, g
+
+
+def test_adiabatic_box_conserves_mass_and_energy_with_two_temperatures(orc):
+    m = air()
+    N, nel = 3, (3, 2)
+    xi, w = orc.gll(N)
+    P = orc.Problem(dim=2, N=N, nel=nel, lo=(0.0, 0.0), hi=(1.0, 1.5), equations=orc.NS_REACTING, mech=m,
+                    mu=2e-3, prandtl=0.72, two_temperature=True, bc=(5, 5, 1, 5, 0, 0))
+    X = wl.node_coordinates(2, P.nel, P.lo, P.hi, xi)
+    x, y = X
+    rho_s = [0.01 * (1.0 + 0.1 * np.sin(2 * np.pi * x + q) * np.cos(np.pi * y)) for q in range(5)]
+    U = wl.reacting_conserved(rho_s, [200.0 * np.sin(np.pi * y), 100.0 * np.cos(2 * np.pi * x)],
+                              5000.0 + 500.0 * np.cos(np.pi * x), m, Tv=3000.0 + 300.0 * np.sin(np.pi * y))
+    R = orc.rhs(P, U.reshape(P.shape))
+    W = np.multiply.outer(w, w).ravel()
+    mass = R[:5].sum(axis=0)  # species exchange mass through reactions; the mixture does not
+    assert abs(np.sum(mass * W)) <= 1e-12 * np.sum(np.abs(R[:5]).sum(axis=0) * W)
+    assert abs(np.sum(R[7] * W)) <= 1e-12 * np.sum(np.abs(R[7]) * W)
+    assert abs(np.sum(R[8] * W)) > 1e-6 * np.sum(np.abs(R[8]) * W)  # relaxation and chemistry move E_v
+
 
 
 # ---------------------------------------------------------------------------------------
@@ -338,3 +447,73 @@ def test_implicit_substep_conserves_and_reaches_equilibrium(orc):
     Ui, _ = orc.source_implicit(Pi, as_state(Pi, ui), 10.0)
     T, _, Tv = orc.mixture_tt(Pi, Ui[:, 0, 0])
     assert abs(T - Tv) <= 1e-6 * T
+
+
+def test_adiabatic_walls_pass_no_vibrational_energy(orc):
+    """Inert gas in local equilibrium (T_v = T at every node, so no Landau-Teller exchange)
+    in a box of adiabatic walls: no E_v crosses the boundary, so its weighted residual sums
+    to zero although T_v varies toward the walls."""
+    m = inert(air())
+    N, nel = 3, (3, 2)
+    xi, w = orc.gll(N)
+    P = orc.Problem(dim=2, N=N, nel=nel, lo=(0.0, 0.0), hi=(1.0, 1.5), equations=orc.NS_REACTING, mech=m,
+                    mu=2e-3, prandtl=0.72, two_temperature=True, bc=(5, 5, 5, 5, 0, 0))
+    X = wl.node_coordinates(2, P.nel, P.lo, P.hi, xi)
+    x, y = X
+    T = 4000.0 + 500.0 * np.cos(np.pi * x + 0.3) * np.cos(np.pi * y / 1.5 + 0.2)
+    rho_s = [0.01 * (1.0 + 0.1 * np.sin(2 * np.pi * x + q)) for q in range(5)]
+    U = wl.reacting_conserved(rho_s, [60.0 * np.sin(np.pi * y), 40.0 * np.cos(np.pi * x)], T, m, Tv=T)
+    R = orc.rhs(P, U.reshape(P.shape))
+    W = np.multiply.outer(w, w).ravel()
+    assert abs(np.sum(R[8] * W)) <= 1e-12 * np.sum(np.abs(R[8]) * W)
+
+
+def test_far_field_face_sets_both_temperatures(orc):
+    """Inert gas at rest in equilibrium at T0 beside Dirichlet faces holding a gas at rest at
+    (T_b, T_vb), same pressure: the E_v row is -/+ s^2 k_v D (T_vb - T0)/w along wall-normal
+    lines plus the Rusanov lift (s/w) lambda/2 (E_v,b - E_v,0) at the wall node (lambda the
+    larger frozen sound speed)."""
+    m = inert(air())
+    N, nel, L, mu, T0, Tb, Tvb = 3, (1, 3, 1), 1.0, 2e-3, 3000.0, 3300.0, 2600.0
+    rs = air_rho(T=T0, p=1.0e4)
+    rb = air_rho(T=Tb, p=1.0e4)
+    ub = node(m, rb, Tb, Tvb)
+    _, w = orc.gll(N)
+    D = orc.dmat(N)
+    s = 2.0 / (L / nel[1])
+    P = orc.Problem(dim=3, N=N, nel=nel, lo=(0.0,) * 3, hi=(L,) * 3, equations=orc.NS_REACTING, mech=m, mu=mu,
+                    prandtl=0.72, two_temperature=True, bc=(0, 0, 4, 4, 0, 0), bc_state=(None, None, ub, ub, None, None))
+    one = np.ones((P.n_elem, P.n_nodes))
+    U = wl.reacting_conserved([r * one for r in rs], [0 * one] * 3, T0 * one, m, Tv=T0 * one)
+    u0 = U[:, 0, 0]
+    R = orc.rhs(P, U.reshape(P.shape))
+    rho = sum(rs)
+    cvv = 0.0
+    for q in range(5):
+        th = m["theta_v"][q]
+        if th > 0:
+            x = th / T0
+            cvv += rs[q] * m["R"][q] * x * x * math.exp(x) / math.expm1(x) ** 2
+    kv = mu * cvv / rho / 0.72
+
+    def speed(r, T):
+        rR = sum(a * b for a, b in zip(r, m["R"]))
+        rcv = sum(a * b for a, b in zip(r, m["cv"]))
+        return math.sqrt((1.0 + rR / rcv) * rR * T / sum(r))
+
+    lam = max(speed(rs, T0), speed(rb, Tb))
+    n1 = N + 1
+    want = np.zeros((P.n_elem, P.n_nodes))
+    for e in range(P.n_elem):
+        cy = e % 3
+        for nd in range(P.n_nodes):
+            j = (nd // n1) % n1
+            if cy == 0:
+                want[e, nd] += -s * s * kv * D[j, 0] * (Tvb - T0) / w[0]
+                if j == 0:
+                    want[e, nd] += s / w[0] * 0.5 * lam * (ub[9] - u0[9])
+            if cy == 2:
+                want[e, nd] += s * s * kv * D[j, N] * (Tvb - T0) / w[N]
+                if j == N:
+                    want[e, nd] += s / w[N] * 0.5 * lam * (ub[9] - u0[9])
+    assert np.abs(R[9] - want).max() <= 1e-10 * np.abs(want).max()
