@@ -113,6 +113,10 @@ enum { DG_SSPRK33 = 0, DG_SSPRK54 = 1 };
  *                             energy k dT/dx_l (conduction through the wall, no work);
  *   DG_BC_INFLOW, DG_BC_DIRICHLET  trace: (u, v, w, T) of U_b; flux: the interior flux;
  *   DG_BC_OUTFLOW             trace and flux: the interior ones (no viscous lift).
+ * Two-temperature model: the T_v trace is the interior's at slip and adiabatic walls and at
+ * outflow faces, T_wall at isothermal walls, U_b's at inflow and Dirichlet faces; the E_v
+ * flux row is 0 at slip and adiabatic walls, k_v dT_v/dx_l at isothermal walls (whose energy
+ * row then carries k dT/dx_l + k_v dT_v/dx_l), the interior flux at far-field faces.
  * The no-slip walls need viscous equations (DG_EULER: DG_EINVAL). */
 enum { DG_BC_SLIP_WALL = 1, DG_BC_INFLOW = 2, DG_BC_OUTFLOW = 3, DG_BC_DIRICHLET = 4,
        DG_BC_NOSLIP_ADIABATIC = 5, DG_BC_NOSLIP_ISOTHERMAL = 6 };
@@ -208,7 +212,7 @@ typedef struct {
   double sharpness; /* steepness s of the sigmoid (<= 0: ln 9999) */
   /* Two-temperature model (Sec. 2 "Thermal nonequilibrium coupling" and "Total energy and
    * closure"; Sec. 3.1.3 Eqs. src_vector, src_reaction_rate, src_landau_teller): DG_NS_REACTING
-   * with 5 species, periodic meshes (else DG_EUNSUPPORTED).  The state gains
+   * with 5 species (else DG_EUNSUPPORTED).  The state gains
    * E_v, U = (rho_1..rho_ns, rho u, rho v, rho w, E, E_v); cv_s is the translational-rotational
    * heat capacity and E = sum rho_s (cv_s T + h0_s) + E_v + rho|u|^2/2; T_v solves
    * E_v = sum rho_s e_v,s(T_v) (harmonic oscillators of chem->theta_v); the E_v flux is E_v u,

@@ -415,8 +415,11 @@ bool curved_metrics_host(const dg_mesh_desc& m, double* met, long long stride, l
 // The kernels' copy of instance m's boundary conditions for the viscous equations: the
 // prescribed states of inflow and Dirichlet faces with their (u, v, w, T, p - p_ref, a) from
 // the mixture of `mech` (the kernels' closure), the wall temperature of isothermal walls.
-// False (why set) when a prescribed state is not finite or has rho <= 0 or T <= 0.
-bool react_bc(const dg_mesh_desc& m, const dg::MechDev& mech, double p_ref, dg::ReactBC& b,
+// Two-temperature (tt): the prescribed state carries E_v, T excludes it, and T_v solves
+// E_v = sum rho_s e_v,s(T_v) (bisection to the last bit; E_v grows strictly with T_v); the
+// isothermal wall holds T_v at T_wall.
+// False (why set) when a prescribed state is not finite or has rho <= 0 or T <= 0 (or T_v).
+bool react_bc(const dg_mesh_desc& m, const dg::MechDev& mech, double p_ref, int tt, dg::ReactBC& b,
               std::string& why) {
   std::memset(&b, 0, sizeof(b));
   const int ns = mech.ns;
@@ -426,11 +429,11 @@ bool react_bc(const dg_mesh_desc& m, const dg::MechDev& mech, double p_ref, dg::
     for (int side = 0; side < 2; ++side) {
       const int f = 2 * l + side;
       b.bc[f] = m.bc[f];
-      if (m.bc[f] == DG_BC_NOSLIP_ISOTHERMAL) b.bcw[f][3] = m.bc_state[f][0];
+      if (m.bc[f] == DG_BC_NOSLIP_ISOTHERMAL) b.bcw[f][3] = b.bcw[f][6] = m.bc_state[f][0];
       if (m.bc[f] != DG_BC_INFLOW && m.bc[f] != DG_BC_DIRICHLET) continue;
       const double* u = m.bc_state[f];
       bool ok = true;
-      for (int v = 0; v < ns + 4; ++v) {
+      for (int v = 0; v < ns + 4 + tt; ++v) {
         b.bcu[f][v] = u[v];
         ok = ok && std::isfinite(u[v]);
       }
@@ -448,11 +451,30 @@ bool react_bc(const dg_mesh_desc& m, const dg::MechDev& mech, double p_ref, dg::
           b.bcw[f][d] = u[ns + d] / rho;
           kin += u[ns + d] * b.bcw[f][d];
         }
-        const double T = (u[ns + 3] - 0.5 * kin - rh0) / rcv, p = rR * T;
+        const double Ev = tt ? u[ns + 4] : 0.0;
+        const double T = (u[ns + 3] - Ev - 0.5 * kin - rh0) / rcv, p = rR * T;
         ok = T > 0.0 && std::isfinite(T);
         b.bcw[f][3] = T;
         b.bcw[f][4] = p - p_ref;
         b.bcw[f][5] = std::sqrt((1.0 + rR / rcv) * p / rho);
+        b.bcw[f][6] = T;
+        if (tt) {
+          auto ev = [&](double x) {
+            double e = 0.0;
+            for (int s = 0; s < ns; ++s)
+              if (mech.theta[s] > 0.0) e += u[s] * mech.R[s] * mech.theta[s] / std::expm1(mech.theta[s] / x);
+            return e;
+          };
+          double lo = 1e-3, hi = 1e7;
+          ok = ok && Ev > 0.0 && ev(hi) > Ev;
+          for (int it = 0; ok && it < 200; ++it) {
+            const double mid = 0.5 * (lo + hi);
+            if (mid <= lo || mid >= hi) break;
+            if (ev(mid) < Ev) lo = mid;
+            else hi = mid;
+          }
+          b.bcw[f][6] = 0.5 * (lo + hi);
+        }
       }
       if (!ok) {
         why = "boundary state must be finite with rho > 0 and T > 0";
@@ -1021,12 +1043,7 @@ dg_status dg_init_mesh(const dg_mesh_desc* inst, int n_inst, const dg_physics* p
   const bool navier_stokes = phys->equations != DG_EULER;
   const int tt = phys->two_temperature;
   if (tt != 0 && tt != 1) return DG_EINVAL;
-  if (tt) {  // two-temperature: reacting air on periodic meshes
-    if (phys->equations != DG_NS_REACTING) return DG_EUNSUPPORTED;
-    for (int i = 0; i < n_inst; ++i)
-      for (int l = 0; l < 3; ++l)
-        if (inst[i].periodic[l] != 1) return DG_EUNSUPPORTED;
-  }
+  if (tt && phys->equations != DG_NS_REACTING) return DG_EUNSUPPORTED;  // reacting air only
   dg::MechDev mech;
   std::vector<dg::ReactBC> rbc;
   if (navier_stokes) {
@@ -1052,7 +1069,7 @@ dg_status dg_init_mesh(const dg_mesh_desc* inst, int n_inst, const dg_physics* p
       if (!dg::have_reacting(inst[i].N, mech.ns, tt)) return DG_EUNSUPPORTED;
     rbc.resize(n_inst);
     for (int i = 0; i < n_inst; ++i)
-      if (!react_bc(inst[i], mech, phys->p_ref, rbc[i], why)) return DG_EINVAL;
+      if (!react_bc(inst[i], mech, phys->p_ref, tt, rbc[i], why)) return DG_EINVAL;
     if (phys->volume != DG_VOL_STRONG || phys->surface != DG_SURF_RUSANOV ||
         phys->rho_floor > 0.0 || phys->p_floor > 0.0)
       return DG_EUNSUPPORTED;

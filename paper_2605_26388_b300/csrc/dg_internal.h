@@ -205,8 +205,9 @@ struct ReactBC {
   int nonper;            // 1: some direction carries boundary conditions
   int bc[6];             // boundary type per domain face (0: periodic)
   double bcu[6][12];     // prescribed conserved state U_b (inflow, Dirichlet)
-  double bcw[6][6];      // (u, v, w, T, p - p_ref, a) of U_b (inflow, Dirichlet), or
-                         // (0, 0, 0, T_wall, 0, 0) (isothermal wall)
+  double bcw[6][7];      // (u, v, w, T, p - p_ref, a, T_v) of U_b (inflow, Dirichlet), or
+                         // (0, 0, 0, T_wall, 0, 0, T_wall) (isothermal wall); T_v = T for
+                         // one temperature
 };
 
 // Arguments of the two reacting launches of one stage over one instance.

@@ -331,20 +331,23 @@ __device__ __forceinline__ void br1_gradient(int q, const R* W, const R* Wt, con
 // such that the BR1 average (Fv + gh)/2 is the boundary's viscous flux (Sec. 3.1.2 boundary
 // kernels): slip wall -- only the normal-stress row survives; no-slip adiabatic -- stress
 // rows kept, energy 0; no-slip isothermal -- stress rows kept, energy = heat; inflow,
-// outflow, Dirichlet -- the interior flux itself.  (Two-temperature meshes are periodic: the
-// E_v row, NFV = 5, never reaches a domain face.)
+// outflow, Dirichlet -- the interior flux itself.  Two-temperature (NFV = 5): heat_v =
+// k_v dT_v/dx_L; the E_v row is 0 at slip and adiabatic walls and heat_v at isothermal ones,
+// whose energy row is heat + heat_v.
 template <int L, int NFV, class R>
-__device__ __forceinline__ void ghost_viscous_flux(int type, const R* Fv, R heat, R* gh) {
+__device__ __forceinline__ void ghost_viscous_flux(int type, const R* Fv, R heat, R heat_v, R* gh) {
 #pragma unroll
   for (int c = 0; c < NFV; ++c) gh[c] = Fv[c];
   if (type == 1) {
 #pragma unroll
-    for (int c = 0; c < 4; ++c)
+    for (int c = 0; c < NFV; ++c)
       if (c != L) gh[c] = -Fv[c];
   } else if (type == 5) {
-    gh[3] = -Fv[3];
+#pragma unroll
+    for (int c = 3; c < NFV; ++c) gh[c] = -Fv[c];
   } else if (type == 6) {
-    gh[3] = R(2) * heat - Fv[3];
+    gh[3] = R(2) * (heat + heat_v) - Fv[3];
+    if (NFV > 4) gh[NFV - 1] = R(2) * heat_v - Fv[NFV - 1];
   }
 }
 
@@ -522,6 +525,11 @@ __device__ __forceinline__ void load_element(const ReactArgs& a, int e0, R* smem
       }
 #pragma unroll
       for (int c = 4; c < NROW; ++c) sm[off_pt + (f * NPR + c) * G::NFN + jf] = w[c];
+      if (TT && NROW > 4) {  // T_v: the wall temperature at isothermal walls, U_b's at far-field
+                             // faces, the interior T_v otherwise
+        if (type == 2 || type == 4 || type == 6)
+          sm[off_pt + (f * NPR + 4) * G::NFN + jf] = R(2) * Ar<R>::load(a.bnd.bcw[fw][6]) - w[4];
+      }
       if (KEEP_U) {
 #pragma unroll
         for (int v = 0; v < G::NV; ++v) sm[off_ut + (f * G::NV + v) * G::NFN + jf] = Ar<R>::load(a.U[v * a.stride + go]);
@@ -662,7 +670,8 @@ __global__ void __launch_bounds__(kRT) k_reacting_stage(const ReactArgs a) {
         const int fw = a.bnd.nonper ? wall_face(a, e, L, side) : -1;                          \
         if (fw >= 0) { /* ghost neighbour flux: (F_v + ghost)/2 is the boundary flux */       \
           R gh[NFV];                                                                          \
-          ghost_viscous_flux<L, NFV, R>(a.bnd.bc[fw], Fv, kcond * S[3][L], gh);               \
+          ghost_viscous_flux<L, NFV, R>(a.bnd.bc[fw], Fv, kcond * S[3][L],                    \
+                                        TT ? kvib * S[G::NW - 1][L] : R(0), gh);              \
           R* gd = sm + G::E_FT + (2 * L + side) * NFV * NFN + jf;                             \
           _Pragma("unroll") for (int c = 0; c < NFV; ++c) gd[c * NFN] = gh[c];                \
         }                                                                                     \

@@ -243,3 +243,73 @@ def test_strang_split_steps_match_oracle(env, orc):
     got = S.get_state().cpu().numpy().reshape(U.shape)
     ref, _ = orc.strang_steps(P, orc.SSPRK54, U.copy(), dt, 3)
     assert grouped_rel(got, ref) <= 1e-9
+
+
+# ---------------------------------------------------------------------------------------
+# boundary conditions with the vibrational mode
+# ---------------------------------------------------------------------------------------
+def wall_configs():
+    mech = wl.air5_mechanism()
+    rs = [0.03 * y for y in (0.74, 0.22, 0.02, 0.01, 0.01)]
+    ub = wl.reacting_conserved([np.array(r) for r in rs], [np.array(80.0), np.array(-30.0), np.array(10.0)],
+                               np.array(5200.0), mech, Tv=np.array(3900.0)).reshape(-1)
+    sup = wl.reacting_conserved([np.array(r) for r in rs], [np.array(4000.0), np.array(0.0), np.array(0.0)],
+                                np.array(5000.0), mech, Tv=np.array(4200.0)).reshape(-1)
+    return {
+        "walls": ((1, 1, 5, 6, 0, 0), (None, None, None, (4300.0,), None, None)),
+        "farfield": ((2, 3, 4, 4, 6, 5), (sup, None, ub, ub, (6200.0,), None)),
+        "closed": ((1, 6, 5, 5, 6, 1), (None, (6200.0,), None, None, (4300.0,), None)),
+    }
+
+
+def wall_setup(orc, dg, N, nel, cfg, precision=0, p_ref=0.0, **kw):
+    mech = wl.air5_mechanism()
+    mu = wl.reacting_tgv_viscosity(mech)
+    bc, st = wall_configs()[cfg]
+    lo, hi = (0.0,) * 3, (TWO_PI,) * 3
+    S = dg.Solver(dg.Mesh(3, N, (nel,) * 3, lo, hi, bc=bc, bc_state=st), equations=dg.DG_NS_REACTING, mu=mu,
+                  prandtl=0.72, mechanism=mech, precision=precision, p_ref=p_ref, two_temperature=True, **kw)
+    P = orc.Problem(dim=3, N=N, nel=(nel,) * 3, lo=lo, hi=hi, equations=orc.NS_REACTING, mech=mech, mu=mu,
+                    prandtl=0.72, two_temperature=True, bc=bc, bc_state=st)
+    return S, P
+
+
+@pytest.mark.parametrize("N,nel", [(2, 3), (3, 3)])
+@pytest.mark.parametrize("cfg", ["walls", "farfield", "closed"])
+def test_residual_with_boundaries_matches_oracle(env, orc, N, nel, cfg):
+    torch, dg = env
+    S, P = wall_setup(orc, dg, N, nel, cfg)
+    U = state(orc, N, nel)
+    ref = orc.rhs(P, U)
+    got = S.rhs(dev(torch, U)).cpu().numpy().reshape(U.shape)
+    S.check()
+    assert grouped_rel(got, ref) <= 1e-12
+    S.close()
+
+
+@pytest.mark.parametrize("cfg", ["walls", "closed"])
+def test_fp32_residual_with_boundaries_matches_oracle(env, orc, cfg):
+    torch, dg = env
+    N, nel = 3, 3
+    S, P = wall_setup(orc, dg, N, nel, cfg, precision=dg.FP32_MIXED, p_ref=P0)
+    U = state(orc, N, nel)
+    ref = orc.rhs(P, U)
+    got = S.rhs(dev(torch, U)).cpu().numpy().reshape(U.shape)
+    S.check()
+    for g, fl in zip(GROUPS, fp32_floor(orc, U, ref, N, nel)):
+        err = np.linalg.norm(got[g] - ref[g]) / np.linalg.norm(ref[g])
+        assert err <= 1e-6 + 4 * fl, (g, err, fl)
+    S.close()
+
+
+def test_closed_box_steps_match_oracle(env, orc):
+    torch, dg = env
+    S, P = wall_setup(orc, dg, 2, 3, "closed", time_scheme=dg.SSPRK54)
+    U = state(orc, 2, 3, rel=0.0)
+    S.set_state(dev(torch, U))
+    S.rk_step(1e-12, 20)
+    S.check()
+    got = S.get_state().cpu().numpy().reshape(U.shape)
+    ref = orc.ssp_steps(P, orc.SSPRK54, U.copy(), 1e-12, 20)
+    assert grouped_rel(got, ref) <= 1e-11
+    S.close()
