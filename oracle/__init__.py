@@ -85,7 +85,7 @@ class _Problem(C.Structure):
         ("mech", C.POINTER(_Mech)), ("parts", C.c_int),
         ("shock", C.c_int), ("alpha_min", C.c_double), ("alpha_max", C.c_double),
         ("sharpness", C.c_double), ("bc", C.c_int * 6), ("bc_state", (C.c_double * 12) * 6),
-        ("coords", C.POINTER(C.c_double)), ("two_temperature", C.c_int),
+        ("coords", C.POINTER(C.c_double)), ("two_temperature", C.c_int), ("species_limiter", C.c_int),
     ]
 
 
@@ -115,7 +115,8 @@ class Problem:
     bc_state: tuple = None          # per face: the exterior conserved state (INFLOW, DIRICHLET);
                                     # (T_wall,) for NOSLIP_ISOTHERMAL
     coords: np.ndarray = None       # Euler: node coordinates (dim, n_elem, n_nodes) of a curved mesh
-    two_temperature: bool = False   # NS_REACTING: E_v appended to the state (periodic meshes)
+    two_temperature: bool = False   # NS_REACTING: E_v appended to the state
+    species_limiter: bool = False   # NS_REACTING: Zhang-Shu limiter of rho_s after every RK stage
 
     @property
     def nvars(self) -> int:
@@ -147,6 +148,7 @@ class Problem:
                      self.gamma, self.mu, self.prandtl, self.rho_floor, self.p_floor)
         p.parts = self.parts
         p.two_temperature = 1 if self.two_temperature else 0
+        p.species_limiter = 1 if self.species_limiter else 0
         p.shock = 1 if self.shock else 0
         p.alpha_min, p.alpha_max, p.sharpness = self.alpha_min, self.alpha_max, self.sharpness
         if self.coords is not None:
@@ -189,6 +191,7 @@ def lib():
         _lib.orc_arrhenius.argtypes = [C.POINTER(_Mech), C.c_int, C.c_double, dp, dp]
         _lib.orc_chem_source.argtypes = [pp, dp, dp]
         _lib.orc_mixture.argtypes = [pp, dp, dp, dp, dp]
+        _lib.orc_species_limiter.argtypes = [pp, dp]
         _lib.orc_relaxation_time.argtypes = [C.POINTER(_Mech), C.c_int, dp, C.c_double, C.c_double, dp]
         ip = C.POINTER(C.c_int)
         _lib.orc_shock_alpha.argtypes = [pp, dp, dp, dp]
@@ -380,6 +383,15 @@ def mixture_tt(P: Problem, u):
     c = P._c()
     _check(lib().orc_mixture(C.byref(c), _ptr(u), C.byref(T), C.byref(p), C.byref(Tv)), "mixture")
     return T.value, p.value, Tv.value
+
+
+def species_limiter(P: Problem, U: np.ndarray) -> np.ndarray:
+    """The Zhang-Shu limiter of the partial densities applied once to U (a copy is returned).
+    Pinned by element means, the zero minimum, identity on non-negative states."""
+    U = np.array(U, dtype=np.float64, order="C").reshape(P.shape)
+    c = P._c()
+    _check(lib().orc_species_limiter(C.byref(c), _ptr(U)), "species_limiter")
+    return U
 
 
 def relaxation_time(mech: dict, s: int, X, T: float, p: float) -> float:

@@ -88,6 +88,8 @@ struct OrcProblem {
                               // mesh on the same element topology (null: the Cartesian box)
   int two_temperature;        // ORC_NS_REACTING: 1 -- the two-temperature model (E_v appended
                               // to the state)
+  int species_limiter;        // ORC_NS_REACTING: 1 -- the Zhang-Shu limiter of the partial
+                              // densities after every RK stage
 };
 
 }  // extern "C"
@@ -1490,6 +1492,9 @@ void residual(const OrcProblem& P, const double* U, double* dU) {
 // Positivity floor (Sec. 4.1 and 4.2 set-ups: lower bounds on rho and p are applied after
 // every stage).  READING: the paper does not say how; here rho is raised to
 // rho_floor (momentum kept), then E is reset so that p = p_floor where p < p_floor.
+void after_stage(const OrcProblem& P, double* U);
+void species_limiter(const OrcProblem& P, double* U);
+
 void positivity_floor(const OrcProblem& P, double* U) {
   if (!(P.rho_floor > 0.0) && !(P.p_floor > 0.0)) return;
   Mesh M(P);
@@ -1687,6 +1692,17 @@ int orc_mixture(const OrcProblem* P, const double* u, double* T, double* p, doub
   return 0;
 }
 
+// The species limiter alone, in place (test access).
+int orc_species_limiter(const OrcProblem* P, double* U) {
+  int rc = check_problem(*P);
+  if (rc) return rc;
+  if (P->equations != ORC_NS_REACTING) return -1;
+  OrcProblem Q = *P;
+  Q.species_limiter = 1;
+  species_limiter(Q, U);
+  return 0;
+}
+
 // Vibrational relaxation time of species s (two-temperature model) for mole fractions X at
 // temperature T (K) and pressure p (Pa).
 int orc_relaxation_time(const OrcMech* m, int s, const double* X, double T, double p, double* tau) {
@@ -1809,7 +1825,7 @@ int orc_modes(const OrcProblem* P, const double* q, double* m) {
 //   stage 1: U1 = Un + dt L(Un)
 //   stage 2: U2 = 3/4 Un + 1/4 (U1 + dt L(U1))
 //   stage 3: U3 = 1/3 Un + 2/3 (U2 + dt L(U2))
-// followed by the positivity floor when it is enabled.
+// followed by the positivity floor and the species limiter when they are enabled.
 int orc_rk3_stage(const OrcProblem* P, int stage, const double* Un, const double* Uprev,
                   double dt, double* Uout) {
   int rc = check_problem(*P);
@@ -1824,7 +1840,7 @@ int orc_rk3_stage(const OrcProblem* P, int stage, const double* Un, const double
     else if (stage == 2) Uout[q] = 0.75 * Un[q] + 0.25 * (Uprev[q] + dt * L[q]);
     else Uout[q] = (1.0 / 3.0) * Un[q] + (2.0 / 3.0) * (Uprev[q] + dt * L[q]);
   }
-  positivity_floor(*P, Uout);
+  after_stage(*P, Uout);
   return 0;
 }
 
@@ -1899,8 +1915,52 @@ double ssp_coefficient(const SspTable& t) {
   return c;
 }
 
+// Zhang-Shu positivity limiter of the partial densities (Sec. 4 reacting blast set-up: the
+// limiter keeps rho_s >= 0 per species; X. Zhang and C.-W. Shu, J. Comput. Phys. 229, 2010):
+// per element and species, with the GLL-weighted element mean m and the nodal minimum
+// lo, when lo < 0 every nodal value is contracted toward the mean,
+//   rho_s <- m + theta (rho_s - m),  theta = m / (m - lo)  (the new minimum is 0),
+// and theta = 0 (the element mean everywhere) when the mean itself is not positive.  The
+// element mean of every species is unchanged; momentum and energy are untouched.
+// READINGS: bound 0 (the paper states rho_s >= 0), applied after every RK stage.
+void species_limiter(const OrcProblem& P, double* U) {
+  if (P.equations != ORC_NS_REACTING || !P.species_limiter) return;
+  Mesh M(P);
+  Ops ops(P.N);
+  const int ns = P.mech->n_species;
+  std::vector<double> W(M.n_nodes);
+  for (int nd = 0; nd < M.n_nodes; ++nd) {
+    int ijk[3];
+    M.node_coords(nd, ijk);
+    W[nd] = 1.0;
+    for (int l = 0; l < M.dim; ++l) W[nd] *= ops.w[ijk[l]];
+  }
+  double wsum = 0.0;
+  for (int nd = 0; nd < M.n_nodes; ++nd) wsum += W[nd];
+  for (int e = 0; e < M.n_elem; ++e)
+    for (int s = 0; s < ns; ++s) {
+      double* r = U + ((size_t)s * M.n_elem + e) * M.n_nodes;
+      double mean = 0.0, lo = r[0];
+      for (int nd = 0; nd < M.n_nodes; ++nd) {
+        mean += W[nd] * r[nd];
+        lo = std::fmin(lo, r[nd]);
+      }
+      mean /= wsum;
+      if (!(lo < 0.0)) continue;
+      const double theta = mean > 0.0 ? mean / (mean - lo) : 0.0;
+      for (int nd = 0; nd < M.n_nodes; ++nd) r[nd] = mean + theta * (r[nd] - mean);
+    }
+}
+
+// What follows every RK stage: the Euler positivity floor and the species limiter (each only
+// when enabled).
+void after_stage(const OrcProblem& P, double* U) {
+  positivity_floor(P, U);
+  species_limiter(P, U);
+}
+
 // One step of the table's scheme, in place; every stage state keeps its residual.  The
-// positivity floor (when enabled) follows each stage.
+// positivity floor and the species limiter (when enabled) follow each stage.
 void ssp_step(const OrcProblem& P, const SspTable& t, double* U, double dt) {
   Mesh M(P);
   const size_t n = (size_t)n_vars(P) * M.n_elem * M.n_nodes;
@@ -1913,7 +1973,7 @@ void ssp_step(const OrcProblem& P, const SspTable& t, double* U, double dt) {
       for (int k = 0; k < i; ++k) x += t.alpha[i - 1][k] * Us[k][q] + dt * t.beta[i - 1][k] * Ls[k][q];
       Us[i][q] = x;
     }
-    positivity_floor(P, Us[i].data());
+    after_stage(P, Us[i].data());
   }
   std::memcpy(U, Us[t.s].data(), n * sizeof(double));
 }
