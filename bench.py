@@ -451,11 +451,11 @@ def run_reacting(args):
     dt = 1e-13
     steps = max(3, args.steps // 10)
 
-    def timed(precision, bc=(0,) * 6, bc_state=None, tt=False):
+    def timed(precision, bc=(0,) * 6, bc_state=None, tt=False, limiter=False):
         S = dgsem.Solver(dgsem.Mesh(3, n_deg, (nel,) * 3, (0.0,) * 3, (2 * math.pi,) * 3, bc=bc, bc_state=bc_state),
                          equations=dgsem.DG_NS_REACTING, mu=mu, prandtl=0.72, mechanism=mech,
                          precision=precision, p_ref=101325.0 if precision == dgsem.FP32_MIXED else 0.0,
-                         two_temperature=tt)
+                         two_temperature=tt, species_limiter=limiter)
         S.set_state(U_tt if tt else U)
         S.rk_step(dt, 3)
         S.check()
@@ -477,6 +477,7 @@ def run_reacting(args):
              dgsem.BC_NOSLIP_ADIABATIC, dgsem.BC_NOSLIP_ISOTHERMAL, dgsem.BC_SLIP_WALL)
     wall_T = (None, (6200.0,), None, None, (4300.0,), None)
     msw, _ = timed(dgsem.FP64, walls, wall_T)
+    ms_lim, _ = timed(dgsem.FP64, limiter=True)
     # the two-temperature model on the same workload: E_v at a lagging T_v, Landau-Teller
     # exchange, dissociation at sqrt(T T_v)
     U_tt = torch.from_numpy(wl.reacting_tgv_3d(nel, x, mech, two_temperature=True).reshape(10, -1)).cuda()
@@ -503,6 +504,9 @@ def run_reacting(args):
                                 "note": "10 variables (E_v); T_v by Newton per node per stage, Landau-Teller "
                                         "with Millikan-White + Park, 15 dissociations at sqrt(T T_v); FP64 "
                                         "and FP32-mixed"},
+            "species_limiter": {"ms_per_step": ms_lim, "cost_ratio": ms_lim / ms,
+                                "note": "FP64; Zhang-Shu limiter of the partial densities after every stage "
+                                        "(one warp per element, one more launch per stage)"},
             "closed_box": {"ms_per_step": msw, "value": 3 * dof / (msw * 1e-3), "unit": "DOF-updates/s",
                            "cost_ratio": msw / ms,
                            "note": "FP64; x: slip / isothermal 6200 K, y: no-slip adiabatic, z: isothermal "

@@ -223,6 +223,13 @@ typedef struct {
    * relaxation time plus Park's high-temperature term.  A node whose T_v iteration does not
    * converge sets DG_ECONVERGENCE. */
   int two_temperature;  /* 0: single temperature; 1: two-temperature */
+  /* Zhang-Shu positivity limiter of the partial densities (Sec. 4 reacting blast set-up:
+   * rho_s >= 0 per species; DG_NAVIER_STOKES and DG_NS_REACTING, else DG_EINVAL): after every
+   * RK stage, per element and species with a negative nodal value, the nodal values contract
+   * toward the GLL-weighted element mean m, rho_s <- m + theta (rho_s - m), theta =
+   * m / (m - min rho_s) (the mean itself when m <= 0); element means are kept, momentum and
+   * energy are untouched.  One extra launch per stage. */
+  int species_limiter;  /* 0: off; 1: on */
 } dg_physics;
 
 /* Build a context for n_inst instances (all of the same dim) sharing one physics

@@ -647,6 +647,29 @@ dg_status run_stage_ns(dg_ctx* c, const double* U, const double* Un, double* out
     a.liftf = (float)a.lift;
     cudaError_t e = dg::launch_reacting(m.N, c->n_species, c->tt, fp32, a, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "Navier-Stokes stage launch");
+    if (mode == 1 && c->phys.species_limiter) {  // Zhang-Shu limiter of the stage's output
+      dg::LimiterArgs la;
+      std::memset(&la, 0, sizeof(la));
+      la.U = out;
+      la.pout = a.pout;
+      la.tout = a.tout;
+      la.err = c->err;
+      la.mech = c->d_mech;
+      la.stride = a.stride;
+      la.base = a.base;
+      la.n_elem = a.n_elem;
+      la.np = n_p_of(m);
+      la.p_ref = c->phys.p_ref;
+      double wsum = 0.0;
+      for (int q = 0; q < la.np; ++q) {
+        const int i = q % (m.N + 1), j = (q / (m.N + 1)) % (m.N + 1), kk = q / ((m.N + 1) * (m.N + 1));
+        la.wq[q] = w[i] * w[j] * w[kk];
+        wsum += la.wq[q];
+      }
+      for (int q = 0; q < la.np; ++q) la.wq[q] /= wsum;
+      e = dg::launch_species_limiter(c->n_species, c->tt, fp32, la, s);
+      if (e != cudaSuccess) return cuda_fail(c, e, "species limiter launch");
+    }
   }
   return DG_OK;
 }
@@ -1044,6 +1067,8 @@ dg_status dg_init_mesh(const dg_mesh_desc* inst, int n_inst, const dg_physics* p
   const int tt = phys->two_temperature;
   if (tt != 0 && tt != 1) return DG_EINVAL;
   if (tt && phys->equations != DG_NS_REACTING) return DG_EUNSUPPORTED;  // reacting air only
+  if (phys->species_limiter != 0 && (phys->species_limiter != 1 || phys->equations == DG_EULER))
+    return DG_EINVAL;  // partial densities exist for the viscous equations
   dg::MechDev mech;
   std::vector<dg::ReactBC> rbc;
   if (navier_stokes) {

@@ -279,6 +279,21 @@ struct SourceArgs {
 };
 cudaError_t launch_source_implicit(int ns, int tt, int fp32, const SourceArgs& a, cudaStream_t s);
 
+// Zhang-Shu limiter of the partial densities of one instance's elements, in place, with the
+// primitive cache of the changed nodes rewritten (pout/tout, when not null).
+struct LimiterArgs {
+  double* U;           // state (SoA), limited in place
+  void* pout;          // its primitive cache (flux type) or null
+  double* tout;
+  unsigned* err;
+  const MechDev* mech;
+  long long stride, base;
+  int n_elem, np;      // elements of the instance, nodes per element
+  double p_ref;
+  double wq[(kMaxReactingN + 1) * (kMaxReactingN + 1) * (kMaxReactingN + 1)];  // GLL weights / sum
+};
+cudaError_t launch_species_limiter(int ns, int tt, int fp32, const LimiterArgs& a, cudaStream_t s);
+
 // Element-wise evaluation of a device math routine for the tests: kind 0 the library's
 // table-driven exp, 1 its Newton reciprocal, 2 CUDA's exp, 3 CUDA's 1/x.
 struct MathArgs {

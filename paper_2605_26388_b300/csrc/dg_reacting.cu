@@ -1175,6 +1175,76 @@ __global__ void __launch_bounds__(kCT) k_source_implicit(const SourceArgs a) {
   if (flag) atomicOr(a.err, flag);
 }
 
+// Zhang-Shu limiter of the partial densities after a stage (Sec. 4 reacting blast set-up:
+// rho_s >= 0 per species; X. Zhang and C.-W. Shu, J. Comput. Phys. 229, 2010): one warp per
+// element; the lanes stride over its nodes and reduce, per species, the GLL-weighted mean
+// and the minimum by shuffles; where a minimum is negative the nodal values contract toward
+// the mean, rho_s <- m + theta (rho_s - m) with theta = m / (m - min) (the mean itself when it
+// is not positive), and the changed nodes' primitive cache is rewritten.
+constexpr int kLT = 128;  // threads per CTA of the limiter: four elements
+template <int NS, bool TT, class R>
+__global__ void __launch_bounds__(kLT) k_species_limiter(const LimiterArgs a) {
+  constexpr int NV = NS + 4 + (TT ? 1 : 0);
+  __shared__ double sp[5 * NS];
+  __shared__ double e2tab[64];
+  load_species<NS>(a.mech, sp, TT ? 5 : 4);
+  for (int k = threadIdx.x; k < 64; k += kLT) e2tab[k] = a.mech->exp2tab[k];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int e = blockIdx.x * (kLT / 32) + (threadIdx.x >> 5);
+  if (e >= a.n_elem) return;
+  const long long g0 = a.base + (long long)e * a.np;
+  double mean[NS], lo[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    mean[s] = 0.0;
+    lo[s] = 1e300;
+  }
+  for (int q = lane; q < a.np; q += 32) {
+    const double w = a.wq[q];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      const double r = a.U[s * a.stride + g0 + q];
+      mean[s] = fma(w, r, mean[s]);
+      lo[s] = fmin(lo[s], r);
+    }
+  }
+  bool any = false;
+  double theta[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    for (int o = 16; o > 0; o >>= 1) {
+      mean[s] += __shfl_xor_sync(0xffffffffu, mean[s], o);
+      lo[s] = fmin(lo[s], __shfl_xor_sync(0xffffffffu, lo[s], o));
+    }
+    theta[s] = 1.0;
+    if (lo[s] < 0.0) {
+      theta[s] = mean[s] > 0.0 ? mean[s] / (mean[s] - lo[s]) : 0.0;
+      any = true;
+    }
+  }
+  if (!any) return;  // warp-uniform
+  unsigned flag = 0;
+  for (int q = lane; q < a.np; q += 32) {
+    const long long gi = g0 + q;
+    double u[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) u[v] = a.U[v * a.stride + gi];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      if (theta[s] < 1.0) {
+        u[s] = fma(theta[s], u[s] - mean[s], mean[s]);
+        a.U[s * a.stride + gi] = u[s];
+      }
+    }
+    if (a.pout) {
+      const double tv = TT ? a.tout[a.stride + gi] : 0.0;
+      flag |= write_prims<NS, TT, R>(u, sp, a.p_ref, reinterpret_cast<R*>(a.pout), a.tout, a.stride, gi, tv, e2tab);
+    }
+  }
+  if (flag) atomicOr(a.err, flag);
+}
+
 // Element-wise math routines for the tests (see MathArgs).
 __global__ void k_math_fn(const MathArgs a) {
   __shared__ double tab[64];
@@ -1320,6 +1390,20 @@ cudaError_t launch_source_implicit(int ns, int tt, int fp32, const SourceArgs& a
   else if (ns == 1) k_source_implicit<1, double><<<grid, kCT, 0, s>>>(a);
   else if (ns == 5 && fp32) k_source_implicit<5, float><<<grid, kCT, 0, s>>>(a);
   else if (ns == 5) k_source_implicit<5, double><<<grid, kCT, 0, s>>>(a);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_species_limiter(int ns, int tt, int fp32, const LimiterArgs& a, cudaStream_t s) {
+  if (a.n_elem <= 0) return cudaSuccess;
+  const unsigned grid = (unsigned)((a.n_elem + kLT / 32 - 1) / (kLT / 32));
+  if (tt && ns == 5 && fp32) k_species_limiter<5, true, float><<<grid, kLT, 0, s>>>(a);
+  else if (tt && ns == 5) k_species_limiter<5, true, double><<<grid, kLT, 0, s>>>(a);
+  else if (tt) return cudaErrorInvalidValue;
+  else if (ns == 1 && fp32) k_species_limiter<1, false, float><<<grid, kLT, 0, s>>>(a);
+  else if (ns == 1) k_species_limiter<1, false, double><<<grid, kLT, 0, s>>>(a);
+  else if (ns == 5 && fp32) k_species_limiter<5, false, float><<<grid, kLT, 0, s>>>(a);
+  else if (ns == 5) k_species_limiter<5, false, double><<<grid, kLT, 0, s>>>(a);
   else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }

@@ -98,7 +98,8 @@ class Physics(C.Structure):
                 ("prandtl", C.c_double), ("chem", C.POINTER(Mechanism)),
                 ("time_scheme", C.c_int), ("chem_split", C.c_int), ("newton_max_it", C.c_int),
                 ("newton_tol", C.c_double), ("shock", C.c_int), ("alpha_min", C.c_double),
-                ("alpha_max", C.c_double), ("sharpness", C.c_double), ("two_temperature", C.c_int)]
+                ("alpha_max", C.c_double), ("sharpness", C.c_double), ("two_temperature", C.c_int),
+                ("species_limiter", C.c_int)]
 
 
 _lib = None
@@ -211,7 +212,8 @@ class Solver:
                  gamma=1.4, rho_floor=0.0, p_floor=0.0, p_ref=0.0, stream=None,
                  equations=DG_EULER, mu=0.0, prandtl=0.72, mechanism=None,
                  time_scheme=SSPRK33, chem_split=False, newton_max_it=0, newton_tol=0.0,
-                 shock=False, alpha_min=0.0, alpha_max=0.0, sharpness=0.0, two_temperature=False):
+                 shock=False, alpha_min=0.0, alpha_max=0.0, sharpness=0.0, two_temperature=False,
+                 species_limiter=False):
         import torch
         if isinstance(meshes, Mesh):
             meshes = [meshes]
@@ -221,7 +223,7 @@ class Solver:
         phys = Physics(equations, volume, surface, precision, gamma, rho_floor, p_floor, p_ref,
                        mu, prandtl, None, time_scheme, 1 if chem_split else 0, newton_max_it,
                        newton_tol, 1 if shock else 0, alpha_min, alpha_max, sharpness,
-                       1 if two_temperature else 0)
+                       1 if two_temperature else 0, 1 if species_limiter else 0)
         self.n_elem = sum(m.n_elem for m in self.meshes)
         if mechanism is not None:
             mech = mechanism if isinstance(mechanism, Mechanism) else Mechanism.from_dict(mechanism)

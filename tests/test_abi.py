@@ -152,3 +152,15 @@ def test_init_rejects_bad_two_temperature_setups(dg):
     bad = wl.air5_mechanism()
     bad["ta_mode"] = [2] * 17
     assert _init_tt(dg, periodic, mech=bad) == dg.DG_EINVAL
+
+
+def test_species_limiter_needs_partial_densities(dg):
+    m = dg.Mesh(2, 3, (4, 4), (0.0, 0.0), (1.0, 1.0)).c()
+    phys = dg.Physics()
+    phys.equations, phys.gamma, phys.species_limiter = dg.DG_EULER, 1.4, 1
+    arr = (dg.MeshDesc * 1)(m)
+    h = C.c_void_p()
+    assert dg.lib().dg_init_mesh(arr, 1, C.byref(phys), None, C.byref(h)) == dg.DG_EINVAL
+    phys.equations, phys.species_limiter = dg.DG_NAVIER_STOKES, 2
+    phys.mu, phys.prandtl = 1e-3, 0.72
+    assert dg.lib().dg_init_mesh(arr, 1, C.byref(phys), None, C.byref(h)) == dg.DG_EINVAL
