@@ -84,8 +84,8 @@ struct OrcProblem {
                               // no-slip walls (5, 6) exist for ORC_NS_REACTING only
   double bc_state[6][12];     // INFLOW / DIRICHLET: the exterior conserved state (n_vars
                               // values); NOSLIP_ISOTHERMAL: [0] = the wall temperature
-  const double* coords;       // Euler, periodic: node coordinates [d][elem][node] of a curved
-                              // mesh on the same element topology (null: the Cartesian box)
+  const double* coords;       // Euler: node coordinates [d][elem][node] of a curved mesh on the
+                              // same element topology (null: the Cartesian box)
   int two_temperature;        // ORC_NS_REACTING: 1 -- the two-temperature model (E_v appended
                               // to the state)
   int species_limiter;        // ORC_NS_REACTING: 1 -- the Zhang-Shu limiter of the partial
@@ -832,6 +832,42 @@ void normal_riemann(int kind, int dim, const double* n, const double* uL, const 
   }
 }
 
+// Boundary flux along the contravariant normal n at domain face f of a curved mesh (the
+// functors of boundary_flux, Sec. 3.1.1, in the face's frame): slip wall -- the Riemann flux
+// against the mirror state, the velocity reflected across the wall, m - 2 (m . n) n;
+// supersonic inflow -- the flux of U_b along n; supersonic outflow -- the interior flux along
+// n; Dirichlet -- the Riemann flux against U_b.  own_left: the element's trace is the state
+// on the lower side of the face.
+void curved_boundary_flux(const OrcProblem& P, int f, const double* n, const double* uown, bool own_left,
+                          double* F) {
+  const int dim = P.dim, nv = dim + 2;
+  double ub[8], Fd[8];
+  switch (P.bc[f]) {
+    case ORC_BC_INFLOW:
+    case ORC_BC_OUTFLOW: {
+      const double* u = P.bc[f] == ORC_BC_INFLOW ? P.bc_state[f] : uown;
+      for (int v = 0; v < nv; ++v) F[v] = 0.0;
+      for (int d = 0; d < dim; ++d) {
+        euler_flux(dim, d, u, P.gamma, Fd);
+        for (int v = 0; v < nv; ++v) F[v] += n[d] * Fd[v];
+      }
+      return;
+    }
+    case ORC_BC_SLIP_WALL: {
+      double mn = 0.0;
+      for (int d = 0; d < dim; ++d) mn += uown[1 + d] * n[d];
+      for (int v = 0; v < nv; ++v) ub[v] = uown[v];
+      for (int d = 0; d < dim; ++d) ub[1 + d] = uown[1 + d] - 2.0 * mn * n[d];
+      break;
+    }
+    default:  // Dirichlet
+      for (int v = 0; v < nv; ++v) ub[v] = P.bc_state[f][v];
+      break;
+  }
+  if (own_left) normal_riemann(P.surface, dim, n, uown, ub, P.gamma, F);
+  else normal_riemann(P.surface, dim, n, ub, uown, P.gamma, F);
+}
+
 // Residual of element e on a curved mesh (Sec. 3.1.1, Eqs. vol_weak and vol_split with the
 // metric terms; Eq. surf_int):
 //   strong:    R_i = -(1/J_i) sum_l sum_m D_{i_l m} Ja^l(m) . F(U_m)
@@ -890,11 +926,16 @@ void curved_element_residual(const OrcProblem& P, const Mesh& M, const Ops& ops,
       for (int side = 0; side < 2; ++side) {
         if (side == 1 && ijk[l] != N) continue;
         if (side == 0 && ijk[l] != 0) continue;
-        int nk[3] = {ijk[0], ijk[1], ijk[2]};
-        nk[l] = side ? 0 : N;
-        load_node(M, nv, U, M.neighbour(e, l, side ? +1 : -1), M.node(nk), unbr);
-        if (side) normal_riemann(P.surface, dim, n, uown, unbr, P.gamma, Fs);
-        else normal_riemann(P.surface, dim, n, unbr, uown, P.gamma, Fs);
+        const int fb = boundary_face(P, M, e, l, side);
+        if (fb >= 0) {
+          curved_boundary_flux(P, fb, n, uown, side == 1, Fs);
+        } else {
+          int nk[3] = {ijk[0], ijk[1], ijk[2]};
+          nk[l] = side ? 0 : N;
+          load_node(M, nv, U, M.neighbour(e, l, side ? +1 : -1), M.node(nk), unbr);
+          if (side) normal_riemann(P.surface, dim, n, uown, unbr, P.gamma, Fs);
+          else normal_riemann(P.surface, dim, n, unbr, uown, P.gamma, Fs);
+        }
         const double c = (side ? -1.0 : 1.0) * iJ / ops.w[side ? N : 0];
         for (int v = 0; v < nv; ++v) R[nd * nv + v] += c * (s * Fs[v] - Fo[v]);
       }
@@ -940,9 +981,7 @@ int check_problem(const OrcProblem& P) {
       if (!(q.rho > 0.0) || !(q.p > 0.0)) return -1;
     }
   }
-  if (P.coords) {  // curved meshes: periodic, strong or two-point volume form, no blending
-    for (int f = 0; f < 6; ++f)
-      if (P.bc[f]) return -6;
+  if (P.coords) {  // curved meshes: strong or two-point volume form, no blending
     if (P.shock || P.rho_floor > 0.0 || P.p_floor > 0.0) return -6;
     if (P.volume != ORC_VOL_STRONG && P.volume != ORC_VOL_EC) return -6;
   }
