@@ -141,13 +141,16 @@ typedef struct {
                            * T > 0 (viscous); DG_BC_NOSLIP_ISOTHERMAL: bc_state[f][0] = T_wall
                            * > 0 (the non-dimensional T = p/rho for DG_NAVIER_STOKES, K for
                            * DG_NS_REACTING).  Else DG_EINVAL. */
-  const double* coords;   /* NULL: the affine box.  Else a curved mesh on the same (periodic)
-                           * element topology (Sec. 3.1.1: element maps, metric terms Ja^l with
-                           * the discrete GCL): host array of the node coordinates,
+  const double* coords;   /* NULL: the affine box.  Else a curved mesh on the same element
+                           * topology (Sec. 3.1.1: element maps, metric terms Ja^l with the
+                           * discrete GCL): host array of the node coordinates,
                            * coords[d * n_elem * n_p + e * n_p + q], copied at dg_init_mesh.
-                           * DG_EULER only, all directions periodic, strong or two-point volume
-                           * form, no shock capturing, no positivity floor (else
-                           * DG_EUNSUPPORTED); every element must have J > 0 (else DG_EINVAL). */
+                           * Periodic directions must map periodically; a non-periodic direction
+                           * takes its boundary conditions along the faces' contravariant normal
+                           * (the slip wall mirrors the velocity across it).  DG_EULER only,
+                           * strong or two-point volume form, no shock capturing, no positivity
+                           * floor (else DG_EUNSUPPORTED); every element must have J > 0 (else
+                           * DG_EINVAL). */
 } dg_mesh_desc;
 
 /* Species and reactions of a reacting mixture (Sec. 2 thermochemistry, single temperature;

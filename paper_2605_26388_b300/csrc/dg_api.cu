@@ -1047,8 +1047,6 @@ dg_status dg_init_mesh(const dg_mesh_desc* inst, int n_inst, const dg_physics* p
         (phys->volume != DG_VOL_STRONG && phys->volume != DG_VOL_EC) ||
         !dg::have_curved(inst[i].dim, inst[i].N))
       return DG_EUNSUPPORTED;
-    for (int l = 0; l < inst[i].dim; ++l)
-      if (inst[i].periodic[l] != 1) return DG_EUNSUPPORTED;
   }
   dg_physics ph = *phys;  // with the shock-capturing defaults filled in
   if (ph.shock) {

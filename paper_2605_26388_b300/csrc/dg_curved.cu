@@ -10,7 +10,8 @@
 //   2. one thread per face node: both traces expressed in the orthonormal frame (n, t1, t2) of
 //      the face's contravariant normal n = Ja^l / |Ja^l| (taken at the own node: it depends
 //      only on the face's nodes, so both elements of a face use the same one), the Riemann flux
-//      of direction 0 there, rotated back and scaled by |Ja^l|; minus Ja^l . F(U_own); lifted by
+//      of direction 0 there (at a domain face with a boundary condition: the functor's flux in
+//      the same frame), rotated back and scaled by |Ja^l|; minus Ja^l . F(U_own); lifted by
 //      1 / (J w);
 //   3. one thread per node: the volume term -(1/J) sum_l sum_m D_im Ja^l(m) . F(U_m) (strong) or
 //      -(2/J) sum_l sum_m D_im {{Ja^l}} . F#(U_i, U_m) (two-point, F# in all DIM Cartesian
@@ -157,20 +158,6 @@ __global__ void __launch_bounds__(CG<DIM, N, EC, R>::T) k_euler_curved(const Sta
 #pragma unroll
     for (int v = 0; v < NV; ++v) own[v] = sm[G::O_U + v * NP + nd];
     const R pd_own = sm[G::O_PD + nd];
-    // the neighbour's trace (periodic topology)
-    int c[3] = {e % I.nel[0], (e / I.nel[0]) % I.nel[1], DIM == 3 ? e / (I.nel[0] * I.nel[1]) : 0};
-    c[l] = (c[l] + (side ? 1 : -1) + I.nel[l]) % I.nel[l];
-    const int en = c[0] + I.nel[0] * (c[1] + I.nel[1] * c[2]);
-    const long long gn = I.base + (long long)en * NP + line_nd + (side ? 0 : N) * S;
-    double n64[NV];
-    R nbr[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      n64[v] = A.U[v * stride + gn];
-      nbr[v] = Ar<R>::load(n64[v]);
-    }
-    double rhoe;
-    const R pd_nbr = pdev<DIM>(n64, nbr, A.pd.gm1, A.pd.p_ref, rhoe);
     R ja[DIM], s2 = R(0);
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
@@ -185,11 +172,43 @@ __global__ void __launch_bounds__(CG<DIM, N, EC, R>::T) k_euler_curved(const Sta
     frame<DIM>(n, tv);
     R ro[NV], rn[NV];
     to_frame<DIM>(own, n, tv, ro);
-    to_frame<DIM>(nbr, n, tv, rn);
     const Prim<DIM, R> po = prims<DIM>(ro, pd_own, p_ref);
-    const Prim<DIM, R> pn = prims<DIM>(rn, pd_nbr, p_ref);
+    // the exterior state in the frame: the neighbour's trace, or at a domain face the
+    // boundary functor's (Sec. 3.1.1): slip wall -- the mirror state (normal momentum, the
+    // frame's first momentum row, reversed); Dirichlet -- U_b; inflow -- F* = F(U_b) . n;
+    // outflow -- F* = F(U-) . n
+    const int fb = I.nonper ? boundary_face(I, DIM, e, l, side) : -1;
+    const int type = fb >= 0 ? I.bc[fb] : 0;
+    R pd_ext = pd_own;
+    if (fb < 0 || type == 2 || type == 4) {
+      double n64[NV];
+      R ext[NV];
+      if (fb < 0) {  // the neighbour's trace
+        int c[3] = {e % I.nel[0], (e / I.nel[0]) % I.nel[1], DIM == 3 ? e / (I.nel[0] * I.nel[1]) : 0};
+        c[l] = (c[l] + (side ? 1 : -1) + I.nel[l]) % I.nel[l];
+        const int en = c[0] + I.nel[0] * (c[1] + I.nel[1] * c[2]);
+        const long long gn = I.base + (long long)en * NP + line_nd + (side ? 0 : N) * S;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) n64[v] = A.U[v * stride + gn];
+      } else {  // the prescribed state
+#pragma unroll
+        for (int v = 0; v < NV; ++v) n64[v] = I.bcs[fb][v];
+      }
+#pragma unroll
+      for (int v = 0; v < NV; ++v) ext[v] = Ar<R>::load(n64[v]);
+      double rhoe;
+      pd_ext = pdev<DIM>(n64, ext, A.pd.gm1, A.pd.p_ref, rhoe);
+      to_frame<DIM>(ext, n, tv, rn);
+    } else {  // slip wall (mirror) or outflow (the own trace)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) rn[v] = ro[v];
+      if (type == 1) rn[1] = -ro[1];
+    }
+    const Prim<DIM, R> pn = prims<DIM>(rn, pd_ext, p_ref);
     R Fr[NV];
-    if (side) surface_flux<DIM, 0>(A.surface, ro, po, rn, pn, gamma, igm1, p_ref, Fr);
+    if (type == 2) point_flux<DIM, 0>(rn, pn, Fr);       // supersonic inflow
+    else if (type == 3) point_flux<DIM, 0>(ro, po, Fr);  // supersonic outflow
+    else if (side) surface_flux<DIM, 0>(A.surface, ro, po, rn, pn, gamma, igm1, p_ref, Fr);
     else surface_flux<DIM, 0>(A.surface, rn, pn, ro, po, gamma, igm1, p_ref, Fr);
     // back to Cartesian components, scaled by |Ja^l|; minus the own contravariant flux
     R Fs[NV];

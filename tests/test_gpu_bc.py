@@ -227,11 +227,6 @@ def test_shock_capturing_in_a_closed_box(env, orc, prec, tol):
 
 def test_boundaries_refused_where_not_built(env, orc):
     torch, dg = env
-    xi, _ = orc.gll(3)
-    X = wl.warped_coordinates(2, (4, 4), xi, (0.0, 0.0), (1.0, 1.0), 0.05)
-    with pytest.raises(dg.DGError) as ei:  # curved meshes are periodic
-        dg.Solver(dg.Mesh(2, 3, (4, 4), (0.0, 0.0), (1.0, 1.0), bc=(1, 1, 0, 0, 0, 0), coords=X), gamma=GAMMA)
-    assert ei.value.status == dg.DG_EUNSUPPORTED
     S = dg.Solver(dg.Mesh(2, 3, (4, 4), (0.0, 0.0), (1.0, 1.0), bc=(1, 1, 0, 0, 0, 0)), gamma=GAMMA)
     U = torch.ones(S.shape, dtype=torch.float64, device="cuda")
     with pytest.raises(dg.DGError) as ei:
