@@ -1177,8 +1177,9 @@ __global__ void __launch_bounds__(kCT) k_source_implicit(const SourceArgs a) {
 
 // Zhang-Shu limiter of the partial densities after a stage (Sec. 4 reacting blast set-up:
 // rho_s >= 0 per species; X. Zhang and C.-W. Shu, J. Comput. Phys. 229, 2010): one warp per
-// element; the lanes stride over its nodes and reduce, per species, the GLL-weighted mean
-// and the minimum by shuffles; where a minimum is negative the nodal values contract toward
+// element; an element with no negative nodal density (sign bits) is left at once; otherwise
+// the lanes stride over its nodes and reduce, per species, the GLL-weighted mean and the
+// minimum by shuffles; where a minimum is negative the nodal values contract toward
 // the mean, rho_s <- m + theta (rho_s - m) with theta = m / (m - min) (the mean itself when it
 // is not positive), and the changed nodes' primitive cache is rewritten.
 constexpr int kLT = 128;  // threads per CTA of the limiter: four elements
@@ -1187,13 +1188,24 @@ __global__ void __launch_bounds__(kLT) k_species_limiter(const LimiterArgs a) {
   constexpr int NV = NS + 4 + (TT ? 1 : 0);
   __shared__ double sp[5 * NS];
   __shared__ double e2tab[64];
+  __shared__ double wq[(kMaxReactingN + 1) * (kMaxReactingN + 1) * (kMaxReactingN + 1)];
   load_species<NS>(a.mech, sp, TT ? 5 : 4);
   for (int k = threadIdx.x; k < 64; k += kLT) e2tab[k] = a.mech->exp2tab[k];
+  // the weights once per CTA (lanes reading different parameter words serialize)
+  for (int k = threadIdx.x; k < a.np; k += kLT) wq[k] = a.wq[k];
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int e = blockIdx.x * (kLT / 32) + (threadIdx.x >> 5);
   if (e >= a.n_elem) return;
   const long long g0 = a.base + (long long)e * a.np;
+  // a sign-bit test first (integer operations only): most elements have no negative density
+  // and leave before any FP64 reduction (the FP64 pipe runs at a 64th of the FP32 rate)
+  bool neg = false;
+  for (int q = lane; q < a.np; q += 32) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s) neg = neg || __double2hiint(a.U[s * a.stride + g0 + q]) < 0;
+  }
+  if (!__any_sync(0xffffffffu, neg)) return;
   double mean[NS], lo[NS];
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
@@ -1201,7 +1213,7 @@ __global__ void __launch_bounds__(kLT) k_species_limiter(const LimiterArgs a) {
     lo[s] = 1e300;
   }
   for (int q = lane; q < a.np; q += 32) {
-    const double w = a.wq[q];
+    const double w = wq[q];
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
       const double r = a.U[s * a.stride + g0 + q];
