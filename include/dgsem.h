@@ -282,8 +282,9 @@ DG_API dg_status dg_rk_step(dg_ctx* ctx, double dt, int n_steps);
 
 /* Adjoint of the residual (for differentiable rollouts; the paper has no adjoint -- it is the
  * exact transpose of the semi-discrete operator of Eq. vol_weak + Eq. surf_int with the
- * Rusanov flux, strong or weak volume form, Euler equations; other choices return
- * DG_EUNSUPPORTED):
+ * Rusanov flux, strong or weak volume form, Euler equations, affine meshes, periodic or with
+ * boundary conditions (the functors' exterior states differentiated with the own trace:
+ * the slip wall's mirror state, U_b fixed); other choices return DG_EUNSUPPORTED):
  *   Ubar += (dL/dU)^T lam            (device arrays of dg_state_size() doubles)
  *   *gammabar += lam . dL/dgamma     (host double)
  * Non-smooth points follow the forward evaluation: the larger Rusanov signal speed (the left

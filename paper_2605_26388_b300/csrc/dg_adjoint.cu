@@ -1,7 +1,9 @@
 // dg_adjoint.cu -- hand-written adjoint (vector-Jacobian product) of the DGSEM residual.
 //
 // For the strong or weak volume form (Eq. vol_weak) with the Rusanov surface flux
-// (Eq. surf_int, Sec. 3.1.1), given a co-state lam this computes, element by element,
+// (Eq. surf_int, Sec. 3.1.1), on periodic meshes or with the boundary functors of the forward
+// pass (slip wall, supersonic inflow and outflow, Dirichlet), given a co-state lam this
+// computes, element by element,
 //   w = (dL/dU)^T lam      and      g = lam . dL/dgamma,
 // without atomics: the volume part contracts lam with the transposed volume operator along
 // each line and applies the transposed Euler flux Jacobian; every face node combines its own
@@ -100,6 +102,15 @@ __device__ __forceinline__ NodeState<DIM, R> node_state(const double* u64, R gam
   return s;
 }
 
+// Domain face (2 l + side) that side `side` of element e in direction l lies on when that face
+// carries a boundary condition, else -1.
+__device__ __forceinline__ int wall_face(const InstArgs& I, int e, int l, int side) {
+  const int f = 2 * l + side;
+  if (I.bc[f] == 0) return -1;
+  const int c = l == 0 ? e % I.nel[0] : (l == 1 ? (e / I.nel[0]) % I.nel[1] : e / (I.nel[0] * I.nel[1]));
+  return (side ? c == I.nel[l] - 1 : c == 0) ? f : -1;
+}
+
 template <int DIM, int N, class R>
 struct Vjp {
   using G = Geo<DIM, N>;
@@ -194,18 +205,38 @@ struct Vjp {
       if (e0 + ej >= I.n_elem) continue;
       const int l = face >> 1, side = face & 1;
       const int ndo = line_node(l, f, side ? N : 0);
-      const int en = neighbour(I, e0 + ej, face);
-      const int ndn = line_node(l, f, side ? 0 : N);
       const long long go = I.base + (long long)(e0 + ej) * NP + ndo;
-      const long long gn = I.base + (long long)en * NP + ndn;
+      // a domain face with a boundary condition: the exterior state of its functor (slip wall:
+      // the mirror state; inflow, Dirichlet: U_b; outflow: the own state) and no neighbour
+      // residual (its co-state is 0)
+      const int fb = I.nonper ? wall_face(I, e0 + ej, l, side) : -1;
+      const int type = fb >= 0 ? I.bc[fb] : 0;
       double uo[NV], un[NV];
       R lo[NV], ln[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         uo[v] = A.U[v * A.stride + go];
-        un[v] = A.U[v * A.stride + gn];
         lo[v] = sm[OFF_L + (ej * NV + v) * NP + ndo];
-        ln[v] = Ar<R>::load(A.lam[v * A.stride + gn]);
+      }
+      if (fb < 0) {
+        const int en = neighbour(I, e0 + ej, face);
+        const long long gn = I.base + (long long)en * NP + line_node(l, f, side ? 0 : N);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          un[v] = A.U[v * A.stride + gn];
+          ln[v] = Ar<R>::load(A.lam[v * A.stride + gn]);
+        }
+      } else {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          un[v] = (type == 2 || type == 4) ? I.bcs[fb][v] : uo[v];
+          ln[v] = R(0);
+        }
+        if (type == 1) {
+#pragma unroll
+          for (int d = 0; d < DIM; ++d)
+            if (d == l) un[1 + d] = -uo[1 + d];
+        }
       }
       const NodeState<DIM, R> so = node_state<DIM, R>(uo, gamma), sn = node_state<DIM, R>(un, gamma);
       const NodeState<DIM, R>& sL = side ? so : sn;
@@ -231,14 +262,36 @@ struct Vjp {
       speed_grad<DIM, R>(l, so.v, so.rho, so.p, so.c, gamma, g, dsdg);
       const R sgn_l = side ? R(1) : R(-1);  // d F*/dU_own: +lmax/2 on the left, -lmax/2 on the right
       R ao[NV];
-      if (!A.weak) flux_jac_t<DIM, R>(l, so.v, so.H, gm1, lo, ao);
+      if (!A.weak || type == 3) flux_jac_t<DIM, R>(l, so.v, so.H, gm1, lo, ao);
       const R s = s_of<R>(I, l);
       const R c = (side ? R(-1) : R(1)) * s * lift_of<R>(I);
+      // slip wall: the exterior state M U_own also depends on U_own; its part of dF*/dU_own is
+      // M (dF*/dU_ext)^T lam (M negates the normal momentum; the signal speeds tie, so the
+      // left state carries the speed derivative)
+      R ext[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) ext[v] = R(0);
+      if (type == 1) {
+        R ae[NV], ge[NV], dsdge;
+        flux_jac_t<DIM, R>(l, sn.v, sn.H, gm1, lo, ae);
+        speed_grad<DIM, R>(l, sn.v, sn.rho, sn.p, sn.c, gamma, ge, dsdge);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          ext[v] = R(0.5) * ae[v] - sgn_l * R(0.5) * lmax * lo[v];
+          if (!own_sel) ext[v] -= R(0.5) * dUm * ge[v];
+        }
+#pragma unroll
+        for (int d = 0; d < DIM; ++d)
+          if (d == l) ext[1 + d] = -ext[1 + d];
+      }
       R contrib[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         R jt = R(0.5) * a[v] + sgn_l * R(0.5) * lmax * mu[v];
         if (own_sel) jt -= R(0.5) * dUm * g[v];
+        jt += ext[v];
+        if (type == 2) jt = R(0);      // supersonic inflow: F* = F(U_b) does not see U_own
+        if (type == 3) jt = ao[v];     // supersonic outflow: F* = F(U_own)
         contrib[v] = c * (jt - (A.weak ? R(0) : ao[v]));
       }
       R* S = sm + OFF_S + ((ej * NF + face) * NFN + f) * NV;
@@ -257,7 +310,9 @@ struct Vjp {
         speed_grad<DIM, R>(l, ssel.v, ssel.rho, ssel.p, ssel.c, gamma, gs, dsdg_sel);
         dsel = dsdg_sel;
       }
-      const R dFs = R(0.5) * (dFL + dFR) - R(0.5) * dsel * dUl;
+      R dFs = R(0.5) * (dFL + dFR) - R(0.5) * dsel * dUl;
+      if (type == 2) dFs = side ? dFR : dFL;  // the flux of U_b, the exterior state
+      if (type == 3) dFs = side ? dFL : dFR;  // the own flux
       const R dFo = A.weak ? R(0) : so.rhoe * (mlo + lo[DIM + 1] * vlo);
       gacc += (double)(c * (dFs - dFo));
     }

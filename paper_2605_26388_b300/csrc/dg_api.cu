@@ -830,8 +830,6 @@ dg_status ensure_adjoint(dg_ctx* c) {
   if (c->shock) return fail(c, DG_EUNSUPPORTED, "the adjoint has no shock capturing");
   for (const dg_mesh_desc& m : c->inst) {
     if (m.coords) return fail(c, DG_EUNSUPPORTED, "the adjoint covers affine meshes");
-    for (int l = 0; l < m.dim; ++l)
-      if (m.periodic[l] != 1) return fail(c, DG_EUNSUPPORTED, "the adjoint covers periodic meshes");
   }
   if (c->phys.volume == DG_VOL_EC || c->phys.surface != DG_SURF_RUSANOV)
     return fail(c, DG_EUNSUPPORTED, "the adjoint covers the strong/weak volume form with the Rusanov flux");

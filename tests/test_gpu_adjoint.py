@@ -205,3 +205,44 @@ def test_deferred_gamma_accumulates_on_the_device(env, orc):
     g = S.adjoint_gammabar()
     assert abs(g - (g1 + g2)) <= 1e-12 * (abs(g1) + abs(g2))
     assert S.adjoint_gammabar() == 0.0
+
+
+# ---------------------------------------------------------------------------------------
+# boundary conditions: the transpose against central differences of the oracle's residual
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("bc", [(1, 1, 0, 0, 0, 0), (2, 3, 1, 1, 0, 0), (4, 4, 1, 1, 0, 0), (1, 3, 4, 2, 0, 0)])
+@pytest.mark.parametrize("vol", [0, 1])
+def test_rhs_vjp_with_boundaries_against_oracle_differences(env, orc, bc, vol):
+    """lam . (L(U + eps V) - L(U - eps V)) / (2 eps) of the oracle equals ((dL/dU)^T lam) . V of
+    the GPU, and likewise for gamma: the transposed boundary functors (slip wall, supersonic
+    inflow and outflow, Dirichlet) are the derivatives of the oracle's."""
+    torch, dg = env
+    N, nel = 3, (3, 2)
+    xi, _ = orc.gll(N)
+    lo, hi = (0.0, 0.0), (2.0, 1.0)
+    st = wl.conserved(np.array(1.1), [np.array(2.6), np.array(0.1)], np.array(0.9), GAMMA).reshape(-1)
+    bs = tuple(st if b in (2, 4) else None for b in bc)
+    X = wl.node_coordinates(2, nel, lo, hi, xi)
+    rho = 1.0 + 0.2 * np.cos(np.pi * X[0]) * np.sin(2 * np.pi * X[1] + 0.3)
+    U = wl.conserved(rho, [2.2 + 0.3 * np.sin(np.pi * X[1]), 0.2 * np.cos(np.pi * X[0])], 1.0 + 0.1 * rho,
+                     GAMMA).reshape(4, 6, -1)
+    rng = np.random.default_rng(4)
+    lam = rng.standard_normal(U.shape)
+    V = rng.standard_normal(U.shape) * np.abs(U)
+    S = dg.Solver(dg.Mesh(2, N, nel, lo, hi, bc=bc, bc_state=bs), volume=vol, gamma=GAMMA)
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a.reshape(4, -1))).cuda()
+    Ubar, gbar = S.rhs_vjp(d(U), d(lam))
+    S.check()
+    got = float(np.sum(Ubar.cpu().numpy().reshape(U.shape) * V))
+
+    def res(Ux, g=GAMMA):
+        P = orc.Problem(dim=2, N=N, nel=nel, lo=lo, hi=hi, volume=vol, surface=0, gamma=g, bc=bc, bc_state=bs)
+        return orc.rhs(P, Ux)
+
+    eps = 1e-6
+    want = float(np.sum(lam * (res(U + eps * V) - res(U - eps * V)) / (2 * eps)))
+    assert abs(got - want) <= 1e-6 * max(abs(want), 1.0), (got, want)
+    geps = 1e-6
+    gwant = float(np.sum(lam * (res(U, GAMMA + geps) - res(U, GAMMA - geps)) / (2 * geps)))
+    assert abs(gbar - gwant) <= 1e-6 * max(abs(gwant), 1.0), (gbar, gwant)
+    S.close()
