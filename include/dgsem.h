@@ -296,8 +296,10 @@ DG_API dg_status dg_rk_step(dg_ctx* ctx, double dt, int n_steps);
 DG_API dg_status dg_rhs_vjp(dg_ctx* ctx, const double* U, const double* lam, double* Ubar,
                             double* gammabar);
 
-/* Adjoint of one SSP-RK3 step from Un with step dt (App. B, Shu-Osher form, stages
- * recomputed from Un; SSP-RK54 contexts return DG_EUNSUPPORTED): on entry lam = dJ/dU^{n+1}, on exit lam = dJ/dU^n; *gammabar (host)
+/* Adjoint of one SSP step from Un with step dt (App. B, Shu-Osher form, the context's scheme,
+ * stages recomputed from Un; SSP-RK54 reverses its five stages through the table,
+ * lam^(k) = sum_i alpha_ik lam^(i) + dt (dL/dU(U^(k)))^T sum_i beta_ik lam^(i)): on entry
+ * lam = dJ/dU^{n+1}, on exit lam = dJ/dU^n; *gammabar (host)
  * += dJ/dgamma through this step.  The positivity floor, if enabled, is not differentiated.
  * lam must not alias Un.  gammabar as for dg_rhs_vjp: NULL keeps the contribution in the
  * context's device accumulator and the call stays asynchronous. */

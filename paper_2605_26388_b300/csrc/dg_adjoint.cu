@@ -430,4 +430,21 @@ cudaError_t launch_rhs_vjp(int dim, int N, int fp32, const VjpArgs& a, double* g
   return cudaGetLastError();
 }
 
+__global__ void k_combine(const CombineArgs a) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < a.n;
+       i += (long long)gridDim.x * blockDim.x) {
+    double y = 0.0;
+    for (int j = 0; j < a.m; ++j) y = fma(a.c[j], a.x[j][i], y);
+    a.y[i] = y;
+  }
+}
+
+cudaError_t launch_combine(const CombineArgs& a, cudaStream_t s) {
+  if (a.n <= 0) return cudaSuccess;
+  const long long want = (a.n + 255) / 256;
+  const unsigned grid = (unsigned)(want < 148 * 8 ? want : 148 * 8);
+  k_combine<<<grid, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
 }  // namespace dg

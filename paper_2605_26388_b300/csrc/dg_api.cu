@@ -42,7 +42,7 @@ struct dg_ctx {
   double* d_dv = nullptr;
   // adjoint workspace (allocated on the first adjoint call): recomputed stage states W1, W2,
   // co-state temporaries T1..T3, per-CTA gamma partials and their device accumulator
-  double* adj[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  double* adj[10] = {};               // adjoint workspace (SSP-RK54: all ten)
   double* gpart = nullptr;
   double* gacc = nullptr;
   // Navier-Stokes: mechanism (device copy), face buffer of the BR1 pass and its per-instance
@@ -837,7 +837,7 @@ dg_status ensure_adjoint(dg_ctx* c) {
   const size_t bytes = sizeof(double) * (size_t)c->nv * c->n_nodes_total;
   int maxb = 1;
   for (const dg_mesh_desc& m : c->inst) maxb = std::max(maxb, dg::vjp_blocks(m.dim, m.N, n_elem_of(m)));
-  for (int k = 0; k < 5; ++k)
+  for (int k = 0; k < (c->rk54 ? 10 : 5); ++k)
     if (cudaMalloc(&c->adj[k], bytes) != cudaSuccess) { cudaGetLastError(); return fail(c, DG_ENOMEM, "adjoint workspace"); }
   if (cudaMalloc(&c->gpart, sizeof(double) * maxb) != cudaSuccess ||
       cudaMalloc(&c->gacc, sizeof(double)) != cudaSuccess) {
@@ -1362,15 +1362,81 @@ dg_status dg_rhs_vjp(dg_ctx* c, const double* U, const double* lam, double* Ubar
   return read_gacc(c, gammabar);
 }
 
+}  // extern "C"
+
+namespace {
+
+// Adjoint of one SSP-RK54 step (App. B, Shu-Osher form U^(i) = sum_k alpha_ik U^(k) +
+// dt beta_ik L(U^(k)), U^(5) = U^{n+1}): the stages U^(1..4) are recomputed from Un, then, with
+// lam^(5) = lam, for k = 4..0
+//   mu_k = sum_{i>k} beta_ik lam^(i),   lam^(k) = sum_{i>k} alpha_ik lam^(i) + dt (dL/dU(U^(k)))^T mu_k
+// (one VJP launch with co-state mu_k, bcoef 1 and accin = sum alpha_ik lam^(i) - mu_k, the two
+// sums formed by the combination kernel), and gammabar += dt mu_k . dL/dgamma(U^(k)).
+dg_status rk54_step_vjp(dg_ctx* c, const double* Un, double dt, double* lam, double* gammabar) {
+  const Ssp54& k = kRk54;
+  double* Us[5] = {const_cast<double*>(Un), c->adj[0], c->adj[1], c->adj[2], c->adj[3]};
+  double* Lm[5] = {nullptr, c->adj[4], c->adj[5], c->adj[6], c->adj[7]};  // lam^(1..4)
+  double *mu = c->adj[8], *acc = c->adj[9];
+  // forward stages 1..4: U^(i) = alpha_i0 U^n + alpha_i,i-1 U^(i-1) + beta_i,i-1 dt L(U^(i-1))
+  const double a_i0[5] = {0.0, 0.0, k.a20, k.a30, k.a40};
+  const double a_ip[5] = {0.0, 1.0, k.a21, k.a32, k.a43};
+  const double b_ip[5] = {0.0, k.b10, k.b21, k.b32, k.b43};
+  dg_status st;
+  for (int i = 1; i <= 4; ++i) {
+    StageCoef sc;
+    sc.ca = a_i0[i];
+    sc.cb = a_ip[i];
+    sc.bdt = b_ip[i] * dt;
+    if ((st = run_stage(c, Us[i - 1], Un, Us[i], 1, sc, c->stream))) return st;
+  }
+  // the table's nonzero entries (i, k): alpha and beta
+  double A[6][5] = {}, B[6][5] = {};
+  A[1][0] = 1.0;        B[1][0] = k.b10;
+  A[2][0] = k.a20;      A[2][1] = k.a21;  B[2][1] = k.b21;
+  A[3][0] = k.a30;      A[3][2] = k.a32;  B[3][2] = k.b32;
+  A[4][0] = k.a40;      A[4][3] = k.a43;  B[4][3] = k.b43;
+  A[5][2] = k.a52;      A[5][3] = k.a53;  B[5][3] = k.b53;  A[5][4] = k.a54;  B[5][4] = k.b54;
+  const long long n = (long long)c->nv * c->n_nodes_total;
+  auto lam_of = [&](int i) -> const double* { return i == 5 ? lam : Lm[i]; };
+  for (int kk = 4; kk >= 0; --kk) {
+    dg::CombineArgs cm, ca;
+    std::memset(&cm, 0, sizeof(cm));
+    std::memset(&ca, 0, sizeof(ca));
+    cm.y = mu;
+    ca.y = acc;
+    cm.n = ca.n = n;
+    for (int i = kk + 1; i <= 5; ++i) {
+      if (B[i][kk] != 0.0) {
+        cm.x[cm.m] = lam_of(i);
+        cm.c[cm.m++] = B[i][kk];
+      }
+      if (A[i][kk] != 0.0 || B[i][kk] != 0.0) {
+        ca.x[ca.m] = lam_of(i);
+        ca.c[ca.m++] = A[i][kk] - B[i][kk];
+      }
+    }
+    cudaError_t e = dg::launch_combine(cm, c->stream);
+    if (e == cudaSuccess) e = dg::launch_combine(ca, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "adjoint combination");
+    double* out = kk == 0 ? lam : Lm[kk];
+    if ((st = run_vjp(c, Us[kk], mu, out, 1, 1.0, dt, acc, nullptr, 0, 0.0, dt))) return st;
+  }
+  return read_gacc(c, gammabar);
+}
+
+}  // namespace
+
+extern "C" {
+
 dg_status dg_rk_step_vjp(dg_ctx* c, const double* Un, double dt, double* lam, double* gammabar) {
   if (!c) return DG_EINVAL;
   if (!Un || !lam) return fail(c, DG_EINVAL, "null pointer");
   if (Un == lam) return fail(c, DG_EINVAL, "lam must not alias Un");
   if (c->ns) return fail(c, DG_EUNSUPPORTED, "the adjoint exists for the Euler equations");
-  if (c->rk54) return fail(c, DG_EUNSUPPORTED, "the adjoint step reverses SSP-RK3");
   if (!std::isfinite(dt)) return fail(c, DG_EINVAL, "dt must be finite");
   dg_status st = ensure_adjoint(c);
   if (st) return st;
+  if (c->rk54) return rk54_step_vjp(c, Un, dt, lam, gammabar);
   double *W1 = c->adj[0], *W2 = c->adj[1], *T1 = c->adj[2], *T2 = c->adj[3], *T3 = c->adj[4];
   // recompute the stage states of this step
   if ((st = run_stage(c, Un, Un, W1, 1, rk3_coef(0, dt), c->stream))) return st;
@@ -1622,7 +1688,7 @@ void dg_free(dg_ctx* c) {
   if (c->d_insts) cudaFree(c->d_insts);
   if (c->d_items) cudaFree(c->d_items);
   if (c->d_dv) cudaFree(c->d_dv);
-  for (int k = 0; k < 5; ++k)
+  for (int k = 0; k < 10; ++k)
     if (c->adj[k]) cudaFree(c->adj[k]);
   if (c->gpart) cudaFree(c->gpart);
   if (c->gacc) cudaFree(c->gacc);

@@ -88,6 +88,17 @@ struct VjpArgs {
   int mode, weak;
 };
 
+// y = sum_j c[j] x[j] over n doubles (m <= 5 terms; y may not alias any x): the reverse
+// Shu-Osher combinations of the adjoint step.
+struct CombineArgs {
+  double* y;
+  const double* x[5];
+  double c[5];
+  long long n;
+  int m;
+};
+cudaError_t launch_combine(const CombineArgs& a, cudaStream_t s);
+
 // Hennemann-Gassner shock capturing over one instance (Sec. 3.1.1 "Shock Indicator and
 // Smoothing", Eq. vol_blend): indicator -> alpha_raw, neighbourhood maximum -> alpha and the
 // list of elements with alpha > 0, then (after the stage launch) the sub-cell FV residual,

@@ -3,7 +3,8 @@ differences.
 
 - residual adjoint vs the oracle's brute-force transpose (one dual-number JVP per unknown);
 - dot-product test <lam, J V> = <J^T lam, V>, J V from the oracle's dual numbers;
-- step adjoint vs chained oracle JVPs through the three SSP-RK3 stages;
+- step adjoint vs chained oracle JVPs through the three SSP-RK3 stages and the five
+  SSP-RK54 stages;
 - the differentiable workload (2D Euler, N=4, 128^2, 200 steps, checkpoints every 20):
   gradient of the density-mismatch loss in U0 and gamma vs central differences (FP64,
   rel <= 1e-6), and the FP32-mixed gradient vs the FP64 one.
@@ -245,4 +246,37 @@ def test_rhs_vjp_with_boundaries_against_oracle_differences(env, orc, bc, vol):
     geps = 1e-6
     gwant = float(np.sum(lam * (res(U, GAMMA + geps) - res(U, GAMMA - geps)) / (2 * geps)))
     assert abs(gbar - gwant) <= 1e-6 * max(abs(gwant), 1.0), (gbar, gwant)
+    S.close()
+
+
+def test_rk54_step_vjp_against_chained_oracle_jvps(env, orc):
+    """The SSP-RK54 step adjoint: lam . (dU^{n+1}/dU^n) V from forward-mode oracle JVPs chained
+    through the five Shu-Osher stages, against (VJP lam) . V; likewise for gamma."""
+    torch, dg = env
+    N, nel, vol = 3, 5, 0
+    P = orc.Problem(dim=2, N=N, nel=(nel, nel), lo=(0.0, 0.0), hi=(1.0, 1.0), volume=vol,
+                    surface=orc.SURF_RUSANOV, gamma=GAMMA)
+    S = dg.Solver(dg.Mesh(2, N, (nel, nel), (0.0, 0.0), (1.0, 1.0)), volume=vol,
+                  surface=dg.SURF_RUSANOV, gamma=GAMMA, time_scheme=dg.SSPRK54)
+    U = state(orc, P, 31)
+    V = wl.uniform(37, U.size).reshape(U.shape) - 0.5
+    lam = wl.uniform(41, U.size).reshape(U.shape) - 0.5
+    dt = 2e-3
+    alpha, beta, s, _ = orc.ssp_table(orc.SSPRK54)
+    Us, Vs, Ws, Ls, dLs, gLs = [U], [V], [np.zeros_like(U)], [], [], []
+    for i in range(1, s + 1):
+        L, dL = orc.rhs_jvp(P, Us[i - 1], Vs[i - 1], 0.0)
+        _, gL = orc.rhs_jvp(P, Us[i - 1], Ws[i - 1], 1.0)
+        Ls.append(L); dLs.append(dL); gLs.append(gL)
+        Ui = sum(alpha[i - 1][k] * Us[k] + dt * beta[i - 1][k] * Ls[k] for k in range(i))
+        Vi = sum(alpha[i - 1][k] * Vs[k] + dt * beta[i - 1][k] * dLs[k] for k in range(i))
+        Wi = sum(alpha[i - 1][k] * Ws[k] + dt * beta[i - 1][k] * gLs[k] for k in range(i))
+        Us.append(Ui); Vs.append(Vi); Ws.append(Wi)
+    lam_d = dev(torch, lam)
+    gb = S.rk_step_vjp(dev(torch, U), dt, lam_d)
+    S.check()
+    lhs = float(np.sum(lam * Vs[s]))
+    rhs = float(np.sum(lam_d.cpu().numpy().reshape(U.shape) * V))
+    assert abs(lhs - rhs) <= 1e-12 * float(np.sum(np.abs(lam * Vs[s])))
+    assert abs(gb - float(np.sum(lam * Ws[s]))) <= 1e-12 * float(np.sum(np.abs(lam * Ws[s])))
     S.close()
