@@ -182,6 +182,8 @@ def lib():
         _lib.orc_two_point_flux.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, dp, dp, dp]
         _lib.orc_rhs.argtypes = [pp, dp, dp]
         _lib.orc_rhs_elements.argtypes = [pp, dp, C.POINTER(C.c_int), C.c_int, dp]
+        _lib.orc_br1_gradients.argtypes = [pp, dp, C.POINTER(C.c_int), C.c_int, dp]
+        _lib.orc_rhs_elements_given_gradient.argtypes = [pp, dp, dp, C.POINTER(C.c_int), C.c_int, dp]
         _lib.orc_rk3_stage.argtypes = [pp, C.c_int, dp, dp, C.c_double, dp]
         _lib.orc_rk3.argtypes = [pp, dp, C.c_double, C.c_int]
         _lib.orc_max_dt.argtypes = [pp, dp, C.c_double, dp]
@@ -273,6 +275,35 @@ def rhs_elements(P: Problem, U: np.ndarray, elems) -> np.ndarray:
     c = P._c()
     _check(lib().orc_rhs_elements(C.byref(c), _ptr(U), el.ctypes.data_as(C.POINTER(C.c_int)), len(el),
                                   _ptr(dU)), "rhs_elements")
+    return dU[:, el, :]
+
+
+def br1_gradients(P: Problem, U: np.ndarray, elems, G=None) -> np.ndarray:
+    """BR1 gradients (Sec. 3.1.2) of W = (u, v, w, T, T_v) on the listed elements, written
+    into G of shape (n_elem, n_nodes, 5, 3) (a new zero array unless given); other elements'
+    rows are left as they are."""
+    U = np.ascontiguousarray(U, dtype=np.float64).reshape(P.shape)
+    el = np.ascontiguousarray(elems, dtype=np.int32)
+    if G is None:
+        G = np.zeros((P.n_elem, P.n_nodes, 5, 3))
+    assert G.flags.c_contiguous and G.shape == (P.n_elem, P.n_nodes, 5, 3)
+    c = P._c()
+    _check(lib().orc_br1_gradients(C.byref(c), _ptr(U), el.ctypes.data_as(C.POINTER(C.c_int)), len(el),
+                                   _ptr(G)), "br1_gradients")
+    return G
+
+
+def rhs_elements_given_gradient(P: Problem, U: np.ndarray, G: np.ndarray, elems) -> np.ndarray:
+    """The Navier-Stokes residual on the listed elements from U and the BR1 gradients G
+    (shape (n_elem, n_nodes, 5, 3)); returns (n_vars, len(elems), n_nodes)."""
+    U = np.ascontiguousarray(U, dtype=np.float64).reshape(P.shape)
+    G = np.ascontiguousarray(G, dtype=np.float64)
+    el = np.ascontiguousarray(elems, dtype=np.int32)
+    dU = np.zeros_like(U)
+    c = P._c()
+    _check(lib().orc_rhs_elements_given_gradient(C.byref(c), _ptr(U), _ptr(G),
+                                                 el.ctypes.data_as(C.POINTER(C.c_int)), len(el), _ptr(dU)),
+           "rhs_elements_given_gradient")
     return dU[:, el, :]
 
 

@@ -1750,6 +1750,38 @@ int orc_relaxation_time(const OrcMech* m, int s, const double* X, double T, doub
   return 0;
 }
 
+// The two phases of the Navier-Stokes residual (Sec. 3.1.2), exposed so that a partitioned
+// mesh can exchange the BR1 gradients of its partition faces between them (Sec. 5, face-only
+// exchange): orc_br1_gradients writes the BR1 gradient of W on the listed elements into G
+// (layout G[((e * n_nodes + node) * 5 + q) * 3 + l], n_elem * n_nodes * 15 doubles; rows of
+// other elements untouched); orc_rhs_elements_given_gradient evaluates the residual of the
+// listed elements from U and a caller-supplied G, in which the face neighbours' gradients
+// must be valid at least on the shared faces' nodes.
+int orc_br1_gradients(const OrcProblem* P, const double* U, const int* elems, int n, double* G) {
+  int rc = check_problem(*P);
+  if (rc) return rc;
+  if (P->equations != ORC_NS_REACTING) return -1;
+  Mesh M(*P);
+  Ops ops(P->N);
+  for (int k = 0; k < n; ++k)
+    if (elems[k] < 0 || elems[k] >= M.n_elem) return -1;
+  for (int k = 0; k < n; ++k) br1_gradient(*P, M, ops, U, elems[k], G);
+  return 0;
+}
+
+int orc_rhs_elements_given_gradient(const OrcProblem* P, const double* U, const double* G,
+                                    const int* elems, int n, double* dU) {
+  int rc = check_problem(*P);
+  if (rc) return rc;
+  if (P->equations != ORC_NS_REACTING) return -1;
+  Mesh M(*P);
+  Ops ops(P->N);
+  for (int k = 0; k < n; ++k)
+    if (elems[k] < 0 || elems[k] >= M.n_elem) return -1;
+  for (int k = 0; k < n; ++k) reacting_element_residual(*P, M, ops, U, G, elems[k], dU);
+  return 0;
+}
+
 // dU/dt = L(U) (Appendix B, Eq. for the semi-discrete system).
 int orc_rhs(const OrcProblem* P, const double* U, double* dU) {
   int rc = check_problem(*P);
