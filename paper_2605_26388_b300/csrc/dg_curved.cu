@@ -257,28 +257,14 @@ __global__ void __launch_bounds__(CG<DIM, N, EC, R>::T) k_euler_curved(const Sta
         const R* Q = sm + G::O_Q;
         const R vi[3] = {Q[1 * NP + nd], Q[2 * NP + nd], Q[3 * NP + nd]};
         const R vm[3] = {Q[1 * NP + nm], Q[2 * NP + nm], Q[3 * NP + nm]};
+        R a[DIM];
+#pragma unroll
+        for (int d = 0; d < DIM; ++d)
+          a[d] = R(0.5) * (sm[G::O_JA + (l * DIM + d) * NP + nd] + sm[G::O_JA + (l * DIM + d) * NP + nm]);
         R Fsum[NV];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) Fsum[v] = R(0);
-#pragma unroll
-        for (int d = 0; d < DIM; ++d) {
-          R F[NV];
-          if (d == 0)
-            ec_flux_prims<DIM, 0>(Q[nd], vi, Q[4 * NP + nd], Q[5 * NP + nd], Q[6 * NP + nd], Q[7 * NP + nd],
-                                  Q[nm], vm, Q[4 * NP + nm], Q[5 * NP + nm], Q[6 * NP + nm], Q[7 * NP + nm],
-                                  igm1, p_ref, F);
-          else if (d == 1)
-            ec_flux_prims<DIM, 1>(Q[nd], vi, Q[4 * NP + nd], Q[5 * NP + nd], Q[6 * NP + nd], Q[7 * NP + nd],
-                                  Q[nm], vm, Q[4 * NP + nm], Q[5 * NP + nm], Q[6 * NP + nm], Q[7 * NP + nm],
-                                  igm1, p_ref, F);
-          else
-            ec_flux_prims<DIM, DIM - 1>(Q[nd], vi, Q[4 * NP + nd], Q[5 * NP + nd], Q[6 * NP + nd],
-                                        Q[7 * NP + nd], Q[nm], vm, Q[4 * NP + nm], Q[5 * NP + nm],
-                                        Q[6 * NP + nm], Q[7 * NP + nm], igm1, p_ref, F);
-          const R a = R(0.5) * (sm[G::O_JA + (l * DIM + d) * NP + nd] + sm[G::O_JA + (l * DIM + d) * NP + nm]);
-#pragma unroll
-          for (int v = 0; v < NV; ++v) Fsum[v] += a * F[v];
-        }
+        ec_flux_prims_n<DIM>(Q[nd], vi, Q[4 * NP + nd], Q[5 * NP + nd], Q[6 * NP + nd], Q[7 * NP + nd], Q[nm],
+                             vm, Q[4 * NP + nm], Q[5 * NP + nm], Q[6 * NP + nm], Q[7 * NP + nm], igm1, p_ref,
+                             a, Fsum);
         const R cm = R(2) * jinv * Dim;
 #pragma unroll
         for (int v = 0; v < NV; ++v) acc[v] -= cm * Fsum[v];

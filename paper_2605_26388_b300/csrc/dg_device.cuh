@@ -269,6 +269,40 @@ __device__ __forceinline__ void ec_flux_prims(R rL, const R* vL, R pdL, R bL, R 
                R(0.5) * ((pdL + p_ref) * vR[L] + (pdR + p_ref) * vL[L]);
 }
 
+// The same two-point flux contracted with a direction n, sum_d n_d F#_d (curved elements:
+// the contravariant volume flux with the metric terms averaged over the pair, Sec. 3.1.1
+// Eq. vol_split with Ja^l): the log means and the velocity products do not depend on the
+// direction, so one evaluation replaces DIM of them.
+template <int DIM, class R>
+__device__ __forceinline__ void ec_flux_prims_n(R rL, const R* vL, R pdL, R bL, R lrL, R lbL, R rR,
+                                                const R* vR, R pdR, R bR, R lrR, R lbR, R igm1,
+                                                R p_ref, const R* n, R* F) {
+  const R sr = rL + rR, sb = bL + bR, dr = rL - rR, db = bL - bR;
+  const R inv = Ar<R>::rcp(sr * sb);
+  const R fr = dr * (sb * inv);
+  const R fb = db * (sr * inv);
+  const R rho_ln = log_mean_from(rL, rR, dr, lrL, lrR, sr, fr);
+  const R beta_ln = log_mean_from(bL, bR, db, lbL, lbR, sb, fb);
+  R vs[DIM];
+  R vLvR = R(0), vsn = R(0), vLn = R(0), vRn = R(0);
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    vs[d] = vL[d] + vR[d];
+    vLvR += vL[d] * vR[d];
+    vsn += n[d] * vs[d];
+    vLn += n[d] * vL[d];
+    vRn += n[d] * vR[d];
+  }
+  const R frho = (R(0.5) * rho_ln) * vsn;
+  const R hf = R(0.5) * frho;
+  const R pa = R(0.5) * (pdL + pdR);
+  F[0] = frho;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) F[1 + d] = hf * vs[d] + pa * n[d];
+  F[DIM + 1] = frho * (igm1 * Ar<R>::rcp(beta_ln) + R(0.5) * vLvR) +
+               R(0.5) * ((pdL + p_ref) * vRn + (pdR + p_ref) * vLn);
+}
+
 template <int DIM, int L, class R>
 __device__ __forceinline__ void ec_flux(const Prim<DIM, R>& a, const Prim<DIM, R>& b, R igm1,
                                         R p_ref, R* F) {
