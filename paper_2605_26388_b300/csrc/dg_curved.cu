@@ -34,11 +34,15 @@ struct CG {
   static constexpr int NJ = NF * NFN;
   static constexpr int T = ((cmax(NP, NJ) + 31) / 32) * 32;
   static constexpr int NQ = EC ? 8 : DIM * NV;  // per node: prims (EC) or contravariant fluxes
+  // two-point pairs along a line: every node owns KO = (N1-1)/2 of them (partner i+k mod N1,
+  // k = 1..KO) and, on a line of even length, the lower half owns the k = N1/2 pair too
+  static constexpr int KO = (N1 - 1) / 2, KM = N1 / 2;
   // shared layout (R): U [NV][NP], Q [NQ][NP], pd [NP], Ja [DIM*DIM][NP], jinv [NP],
-  // S [NF][NFN][NV], D [N1*N1]
+  // S [NF][NFN][NV], D [N1*N1], pair fluxes of one direction P [NP][KM][NV] (EC)
   static constexpr int O_U = 0, O_Q = O_U + NV * NP, O_PD = O_Q + NQ * NP, O_JA = O_PD + NP;
   static constexpr int O_JI = O_JA + DIM * DIM * NP, O_S = O_JI + NP, O_D = O_S + NF * NFN * NV;
-  static constexpr int SIZE = O_D + N1 * N1;
+  static constexpr int O_P = O_D + N1 * N1;
+  static constexpr int SIZE = O_P + (EC ? NP * KM * NV : 0);
   static constexpr size_t smem() { return sizeof(R) * (size_t)SIZE; }
 };
 
@@ -236,45 +240,15 @@ __global__ void __launch_bounds__(CG<DIM, N, EC, R>::T) k_euler_curved(const Sta
     for (int v = 0; v < NV; ++v) sm[G::O_S + (face * NFN + j) * NV + v] = cf * Fs[v];
   }
   __syncthreads();
-  // phase 3
-  if (t >= NP) return;
-  const int nd = t;
+  // phase 3: volume terms and lifted face terms per node
+  const bool node = t < NP;
+  const int nd = node ? t : 0;
   R acc[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) acc[v] = R(0);
   const R jinv = sm[G::O_JI + nd];
   const R* Dv = sm + G::O_D;
-#pragma unroll
-  for (int l = 0; l < DIM; ++l) {
-    const int S = cstride<N1>(l);
-    const int i = (nd / S) % N1;
-    const int base = nd - i * S;
-#pragma unroll
-    for (int m = 0; m < N1; ++m) {
-      const int nm = base + m * S;
-      const R Dim = Dv[i * N1 + m];
-      if constexpr (EC) {
-        const R* Q = sm + G::O_Q;
-        const R vi[3] = {Q[1 * NP + nd], Q[2 * NP + nd], Q[3 * NP + nd]};
-        const R vm[3] = {Q[1 * NP + nm], Q[2 * NP + nm], Q[3 * NP + nm]};
-        R a[DIM];
-#pragma unroll
-        for (int d = 0; d < DIM; ++d)
-          a[d] = R(0.5) * (sm[G::O_JA + (l * DIM + d) * NP + nd] + sm[G::O_JA + (l * DIM + d) * NP + nm]);
-        R Fsum[NV];
-        ec_flux_prims_n<DIM>(Q[nd], vi, Q[4 * NP + nd], Q[5 * NP + nd], Q[6 * NP + nd], Q[7 * NP + nd], Q[nm],
-                             vm, Q[4 * NP + nm], Q[5 * NP + nm], Q[6 * NP + nm], Q[7 * NP + nm], igm1, p_ref,
-                             a, Fsum);
-        const R cm = R(2) * jinv * Dim;
-#pragma unroll
-        for (int v = 0; v < NV; ++v) acc[v] -= cm * Fsum[v];
-      } else {
-        const R cm = jinv * Dim;
-#pragma unroll
-        for (int v = 0; v < NV; ++v) acc[v] -= cm * sm[G::O_Q + (l * NV + v) * NP + nm];
-      }
-    }
-    // lifted face terms of this direction
+  auto lifted = [&](int l, int S, int i) {
     const int jf = (nd % S) + (nd / (S * N1)) * S;
     if (i == 0)
 #pragma unroll
@@ -282,6 +256,80 @@ __global__ void __launch_bounds__(CG<DIM, N, EC, R>::T) k_euler_curved(const Sta
     if (i == N)
 #pragma unroll
       for (int v = 0; v < NV; ++v) acc[v] += sm[G::O_S + ((2 * l + 1) * NFN + jf) * NV + v];
+  };
+  if constexpr (EC) {
+    // The contracted two-point flux of a pair (i, m) is symmetric (the metric average too), so
+    // each pair is evaluated once: its owner adds 2/J_i D_im F and stores F; after the barrier
+    // the partner adds 2/J_m D_mi F.  The diagonal pair is the node's own.
+    const R* Q = sm + G::O_Q;
+    R* Pf = sm + G::O_P;
+    auto pair_flux = [&](int l, int na, int nb, R* F) {
+      const R va[3] = {Q[1 * NP + na], Q[2 * NP + na], Q[3 * NP + na]};
+      const R vb[3] = {Q[1 * NP + nb], Q[2 * NP + nb], Q[3 * NP + nb]};
+      R a[DIM];
+#pragma unroll
+      for (int d = 0; d < DIM; ++d)
+        a[d] = R(0.5) * (sm[G::O_JA + (l * DIM + d) * NP + na] + sm[G::O_JA + (l * DIM + d) * NP + nb]);
+      ec_flux_prims_n<DIM>(Q[na], va, Q[4 * NP + na], Q[5 * NP + na], Q[6 * NP + na], Q[7 * NP + na], Q[nb],
+                           vb, Q[4 * NP + nb], Q[5 * NP + nb], Q[6 * NP + nb], Q[7 * NP + nb], igm1, p_ref, a,
+                           F);
+    };
+    const R two_jinv = R(2) * jinv;
+#pragma unroll 1
+    for (int l = 0; l < DIM; ++l) {
+      const int S = cstride<N1>(l);
+      const int i = (nd / S) % N1;
+      const int base = nd - i * S;
+      if (node) {
+        R F[NV];
+        pair_flux(l, nd, nd, F);
+        const R cd = two_jinv * Dv[i * N1 + i];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) acc[v] -= cd * F[v];
+#pragma unroll
+        for (int k = 1; k <= G::KM; ++k) {
+          if (k > G::KO && i >= G::KM) continue;  // the half-way pair of an even line: lower node
+          const int m = i + k < N1 ? i + k : i + k - N1;
+          pair_flux(l, nd, base + m * S, F);
+          const R cm = two_jinv * Dv[i * N1 + m];
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            acc[v] -= cm * F[v];
+            Pf[(nd * G::KM + (k - 1)) * NV + v] = F[v];
+          }
+        }
+      }
+      __syncthreads();
+      if (node) {
+#pragma unroll
+        for (int k = 1; k <= G::KM; ++k) {
+          const int j = i - k >= 0 ? i - k : i - k + N1;  // the owner of pair (j, j + k = i)
+          if (k > G::KO && j >= G::KM) continue;
+          const R cm = two_jinv * Dv[i * N1 + j];
+          const int nj = base + j * S;
+#pragma unroll
+          for (int v = 0; v < NV; ++v) acc[v] -= cm * Pf[(nj * G::KM + (k - 1)) * NV + v];
+        }
+        lifted(l, S, i);
+      }
+      if (l + 1 < DIM) __syncthreads();  // the next direction reuses the pair buffer
+    }
+    if (!node) return;
+  } else {
+    if (!node) return;
+#pragma unroll
+    for (int l = 0; l < DIM; ++l) {
+      const int S = cstride<N1>(l);
+      const int i = (nd / S) % N1;
+      const int base = nd - i * S;
+#pragma unroll
+      for (int m = 0; m < N1; ++m) {
+        const R cm = jinv * Dv[i * N1 + m];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) acc[v] -= cm * sm[G::O_Q + (l * NV + v) * NP + base + m * S];
+      }
+      lifted(l, S, i);
+    }
   }
   const long long gi = I.base + (long long)e * NP + nd;
   double res[NV];
