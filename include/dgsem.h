@@ -59,7 +59,7 @@ typedef enum {
   DG_ECUDA = -3,        /* a CUDA runtime call failed */
   DG_ENONFINITE = -4,   /* a kernel produced a non-finite value */
   DG_EPOSITIVITY = -5,  /* a kernel read a state with rho <= 0 or p <= 0 */
-  DG_EUNSUPPORTED = -6, /* valid but not implemented (e.g. non-periodic boundaries) */
+  DG_EUNSUPPORTED = -6, /* valid but not implemented (e.g. the adjoint of the two-point form) */
   DG_ETOOLARGE = -7,    /* more instances than dg_max_dt_noalloc's static scratch holds */
   DG_ECONVERGENCE = -8  /* a node's Newton iteration (implicit source, or the vibrational
                         * temperature of the two-temperature model) did not converge */
@@ -419,6 +419,16 @@ DG_API dg_status dg_newton_updates(dg_ctx* ctx, int64_t* count);
  * 3 CUDA's correctly rounded 1/x.  cuda_stream is a cudaStream_t (NULL = legacy default);
  * asynchronous.  Needs no context. */
 DG_API dg_status dg_math_fn(int kind, int64_t n, const double* x, double* y, void* cuda_stream);
+
+/* Measured throughput of one arithmetic instruction class on the current device, for the
+ * rooflines of the stage kernels (no counterpart in the paper: a measurement utility).
+ * kind: 0 FP64 fused multiply-add, 1 FP64 add, 2 FP32 fused multiply-add, 3 packed FP32x2
+ * fused multiply-add (both lanes counted), 4 FP32 approximate reciprocal, 5 FP32 add.
+ * *ops_per_s receives thread-level operations per second: independent dependency chains on
+ * 8 CTAs of 256 threads per SM, best of three launches timed with CUDA events after a
+ * warm-up launch, on the legacy default stream.  Synchronizes the device; no clock or other
+ * device setting is changed.  DG_EINVAL for an unknown kind. */
+DG_API dg_status dg_alu_rate(int kind, double* ops_per_s);
 
 /* Message of the last error on this context (static string if ctx is NULL). */
 DG_API const char* dg_last_error(const dg_ctx* ctx);

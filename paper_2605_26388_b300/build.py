@@ -14,7 +14,8 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libdgsem.so")
 SOURCES = ["dg_api.cu", "dg_kernels.cu", "dg_stage2d.cu", "dg_stage3d.cu", "dg_batched2d.cu",
-           "dg_batched3d.cu", "dg_adjoint.cu", "dg_noalloc.cu", "dg_reacting.cu", "dg_shock.cu", "dg_curved.cu"]
+           "dg_batched3d.cu", "dg_adjoint.cu", "dg_noalloc.cu", "dg_reacting.cu", "dg_shock.cu", "dg_curved.cu",
+           "dg_peaks.cu"]
 HEADERS = ["dg_device.cuh", "dg_internal.h", "dg_stage.cuh", "dg_batched.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -42,10 +43,16 @@ def build_library(force: bool = False, verbose: bool = False) -> str:
     if verbose:
         flags.append("-Xptxas=-v")
     procs, objs = [], []
+    hdr_t = max(os.path.getmtime(d) for d in [os.path.join(CSRC, h) for h in HEADERS] +
+                [os.path.join(os.path.dirname(HERE), "include", "dgsem.h")])
     for f in SOURCES:
         obj = os.path.join(objdir, f.replace(".cu", ".o"))
         objs.append(obj)
-        procs.append((f, subprocess.Popen([nvcc, *flags, "-c", os.path.join(CSRC, f), "-o", obj])))
+        src = os.path.join(CSRC, f)
+        # recompile an object older than its source or than any shared header
+        if not force and os.path.exists(obj) and os.path.getmtime(obj) > max(os.path.getmtime(src), hdr_t):
+            continue
+        procs.append((f, subprocess.Popen([nvcc, *flags, "-c", src, "-o", obj])))
     failed = [f for f, p in procs if p.wait() != 0]
     if failed:
         raise subprocess.CalledProcessError(1, f"nvcc {failed}")

@@ -543,18 +543,7 @@ void launch_args(const dg_ctx* c, dg::StageArgs& a, const double* U, const doubl
   a.rho_floor = c->phys.rho_floor;
   a.p_floor = c->phys.p_floor;
   a.p_ref = c->phys.p_ref;
-  a.pd.gamma = a.gamma;
-  a.pd.gm1 = a.gamma - 1.0;
-  a.pd.igm1 = 1.0 / (a.gamma - 1.0);
-  a.pd.p_ref = a.p_ref;
-  a.pd.cbdt = k.bdt;
-  a.pd.abdt = k.acc_bdt;
-  a.pf.gamma = (float)a.gamma;
-  a.pf.gm1 = (float)a.gamma - 1.0f;
-  a.pf.igm1 = 1.0f / a.pf.gm1;
-  a.pf.p_ref = (float)a.p_ref;
-  a.pf.cbdt = (float)a.pd.cbdt;
-  a.pf.abdt = (float)a.pd.abdt;
+  dg::fill_scalars(a.pd, a.pf, a.gamma, a.p_ref, k.bdt, k.acc_bdt);
   a.need_un = (mode == 1 && k.ca != 0.0) ? 1 : 0;
   a.floor_on = (a.rho_floor > 0.0 || a.p_floor > 0.0) ? 1 : 0;
 }

@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(Batched<DIM, EC, R, GS>::BT, (Batched<DIM, EC,
     cp_async_wait_keep<P - 1>();
     const int2 item = A.items[k];
     const InstArgs& I = A.insts[item.x];
-    DG_ON_DEGREE(I.N, K::load_ops(sm, A.dv_table + I.N * (kMaxN + 1) * (kMaxN + 1)));
+    DG_ON_DEGREE(I.N, K::load_ops(sm, A.dv_table + I.N * (kMaxN + 1) * (kMaxN + 1), I));
     __syncthreads();  // item k's copies and operators are visible
     DG_ON_DEGREE(I.N, K::compute(A, I, sm, K::role(), item.y, st + b * B::MST, need_un));
   }

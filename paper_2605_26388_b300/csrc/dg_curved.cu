@@ -51,7 +51,10 @@ __device__ __forceinline__ int cstride(int l) {
   return l == 0 ? 1 : (l == 1 ? N1 : N1 * N1);
 }
 
-// Orthonormal frame of the unit vector n: t1 (and t2 in 3D), as the oracle builds it.
+// Orthonormal frame of the unit vector n: t1 (and t2 in 3D).  3D: t1 is n x e_a normalised,
+// e_a the unit axis of the smallest |n_a| (the best-conditioned cross product), t2 = n x t1.
+// The rotated Riemann flux does not depend on the choice of tangents (rotational invariance
+// of the Euler fluxes), so any orthonormal completion gives the same F* . n.
 template <int DIM, class R>
 __device__ __forceinline__ void frame(const R* n, R (&t)[2][3]) {
   if constexpr (DIM == 2) {
@@ -113,9 +116,8 @@ __global__ void __launch_bounds__(CG<DIM, N, EC, R>::T) k_euler_curved(const Sta
       u[v] = Ar<R>::load(u64[v]);
       sm[G::O_U + v * NP + t] = u[v];
     }
-    double rhoe;
-    const R pd = pdev<DIM>(u64, u, A.pd.gm1, A.pd.p_ref, rhoe);
-    if (!(__double2hiint(u64[0]) > 0 && __double2hiint(rhoe) > 0)) atomicOr(A.err, 2u);
+    const R pd = pdev<DIM>(u64, u, A.pd.gm1, A.pd.p_ref, k.hgm1);
+    if (!positive<DIM>(u64, u, pd, p_ref, k.margin_e, k.margin_0, A.pd.gm1)) atomicOr(A.err, 2u);
     sm[G::O_PD + t] = pd;
     R ja[DIM * DIM];
 #pragma unroll
@@ -200,8 +202,7 @@ __global__ void __launch_bounds__(CG<DIM, N, EC, R>::T) k_euler_curved(const Sta
       }
 #pragma unroll
       for (int v = 0; v < NV; ++v) ext[v] = Ar<R>::load(n64[v]);
-      double rhoe;
-      pd_ext = pdev<DIM>(n64, ext, A.pd.gm1, A.pd.p_ref, rhoe);
+      pd_ext = pdev<DIM>(n64, ext, A.pd.gm1, A.pd.p_ref, k.hgm1);
       to_frame<DIM>(ext, n, tv, rn);
     } else {  // slip wall (mirror) or outflow (the own trace)
 #pragma unroll

@@ -67,6 +67,18 @@ __device__ __forceinline__ double f2d(float f) {
   return __hiloint2double((int)hi, (int)lo);
 }
 
+// FP32 -> FP64 widening of the flux-precision results (the residual and its increments):
+// normal floats are exact; zero and subnormals give a signed zero, infinities and NaN a NaN
+// (so that a non-finite result stays non-finite).  Nine integer operations.
+__device__ __forceinline__ double f2d_w(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const uint32_t a = b & 0x7fffffffu;
+  uint32_t hi = (a >> 3) + 0x38000000u;   // rebias the exponent 127 -> 1023
+  hi = a < 0x00800000u ? 0u : hi;
+  hi = a >= 0x7f800000u ? 0x7ff80000u : hi;
+  return __hiloint2double((int)(hi | (b & 0x80000000u)), (int)(b << 29));
+}
+
 // 1/x in FP64 for |x| between 2^-125 and 2^125: an FP32 reciprocal seed (relative error
 // below 2^-21) refined by two Newton-Raphson steps y <- y + y (1 - x y), each of which
 // squares the error, so the result is within an ulp or two of the quotient.  Four FP64
@@ -109,7 +121,7 @@ template <> struct Ar<double> {
 
 template <> struct Ar<float> {
   static __device__ __forceinline__ float load(double x) { return d2f_rz(x); }
-  static __device__ __forceinline__ double widen(float x) { return f2d(x); }
+  static __device__ __forceinline__ double widen(float x) { return f2d_w(x); }
   static __device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
   static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
   static __device__ __forceinline__ float sqrt(float x) { return x * rsqrtf(x); }
@@ -156,34 +168,63 @@ template <int DIM, int N> struct Geo {
 // the momentum fluxes use pd, everything else p = pd + p_ref.  A constant added to the
 // momentum flux leaves the discrete operator unchanged in exact arithmetic (the rows of D
 // sum to zero, and F* - F(U_own) is invariant), and at low Mach number it keeps the
-// pressure gradient out of FP32 cancellation.  pd itself is evaluated from the FP64 total
-// energy (the ideal-gas closure of Sec. 2): pd = (gamma-1)(E - |m|^2/(2 rho)) - p_ref, with
-// the kinetic energy formed in R.  Explicit-rounding intrinsics make every call site
-// produce the same bits, so the two elements sharing a face see the same pd.
+// pressure gradient out of FP32 cancellation.  pd is taken from the FP64 total energy (the
+// ideal-gas closure of Sec. 2), pd = g - (gamma-1)/2 |m|^2/rho with g = (gamma-1) E - p_ref:
+// g is one FP64 fused multiply-add (the only FP64 operation of a node's primitives), then
+// rounded to R; the kinetic part, which carries no cancellation, is formed in R.  Explicit
+// rounding intrinsics make every call site produce the same bits, so the two elements
+// sharing a face see the same pd.  irho = 1/rho is passed in (Ar<R>::rcp(u[0]) at every
+// call site), so that one reciprocal serves pd and the velocities.
 // ---------------------------------------------------------------------------------------
+// hgm1 = (gamma-1)/2 in R (host-precomputed).
 template <int DIM>
-__device__ __forceinline__ float pdev(const double* u64, const float* u, double gm1,
-                                      double p_ref, double& rhoe64) {
-  const float irho = __fdividef(1.0f, u[0]);
+__device__ __forceinline__ float pdev_i(const double* u64, const float* u, float irho, double gm1,
+                                        double p_ref, float hgm1) {
   float m2 = __fmul_rn(u[1], u[1]);
 #pragma unroll
   for (int d = 1; d < DIM; ++d) m2 = __fmaf_rn(u[1 + d], u[1 + d], m2);
-  const float ke = __fmul_rn(__fmul_rn(0.5f, m2), irho);
-  rhoe64 = __dsub_rn(u64[DIM + 1], f2d(ke));  // internal energy density, FP64
-  return d2f_rz(__fma_rn(gm1, rhoe64, -p_ref));
+  const float g = d2f_rz(__fma_rn(gm1, u64[DIM + 1], -p_ref));
+  return __fmaf_rn(-hgm1, __fmul_rn(m2, irho), g);
 }
 
 template <int DIM>
-__device__ __forceinline__ double pdev(const double* u64, const double* u, double gm1,
-                                       double p_ref, double& rhoe64) {
-  const double irho = rcp64(u[0]);
+__device__ __forceinline__ double pdev_i(const double* u64, const double* u, double irho, double gm1,
+                                         double p_ref, double hgm1) {
+  (void)u64;
   double m2 = __dmul_rn(u[1], u[1]);
 #pragma unroll
   for (int d = 1; d < DIM; ++d) m2 = __fma_rn(u[1 + d], u[1 + d], m2);
-  const double ke = __dmul_rn(__dmul_rn(0.5, m2), irho);
-  (void)u64;
-  rhoe64 = __dsub_rn(u[DIM + 1], ke);
-  return __fma_rn(gm1, rhoe64, -p_ref);
+  const double g = __fma_rn(gm1, u[DIM + 1], -p_ref);
+  return __fma_rn(-hgm1, __dmul_rn(m2, irho), g);
+}
+
+// pd of a node from its FP64 state u64 and its flux-precision copy u
+template <int DIM, class R>
+__device__ __forceinline__ R pdev(const double* u64, const R* u, double gm1, double p_ref, R hgm1) {
+  return pdev_i<DIM>(u64, u, Ar<R>::rcp(u[0]), gm1, p_ref, hgm1);
+}
+
+// Positivity of a node's state, rho > 0 and p > 0 (equivalently rho e > 0), decided on the
+// FP64 values.  FP32: the pressure pd + p_ref formed in FP32 is accepted when it exceeds a
+// margin of 2^-18 ((gamma-1)|E| + |p_ref|), which bounds its rounding error; below the
+// margin (near vacuum, never in smooth flow) the decision is taken again in FP64 from the
+// FP64 state.  FP64: the sign of pd + p_ref.  A NaN density passes (the finite checks of
+// the stage outputs catch it).
+template <int DIM>
+__device__ __forceinline__ bool positive(const double* u64, const float* u, float pd, float p_ref,
+                                         float margin_e, float margin_0, double gm1) {
+  if (__double2hiint(u64[0]) <= 0) return false;
+  if (pd + p_ref > __fmaf_rn(margin_e, fabsf(u[DIM + 1]), margin_0)) return true;
+  double m2 = u64[1] * u64[1];
+#pragma unroll
+  for (int d = 1; d < DIM; ++d) m2 = fma(u64[1 + d], u64[1 + d], m2);
+  return gm1 * (u64[DIM + 1] - 0.5 * m2 / u64[0]) > 0.0;
+}
+template <int DIM>
+__device__ __forceinline__ bool positive(const double* u64, const double* u, double pd, double p_ref,
+                                         double, double, double) {
+  (void)u;
+  return __double2hiint(u64[0]) > 0 && pd + p_ref > 0.0;
 }
 
 template <int DIM, class R> struct Prim {
@@ -191,15 +232,20 @@ template <int DIM, class R> struct Prim {
 };
 
 template <int DIM, class R>
-__device__ __forceinline__ Prim<DIM, R> prims(const R* u, R pd, R p_ref) {
+__device__ __forceinline__ Prim<DIM, R> prims_i(const R* u, R irho, R pd, R p_ref) {
   Prim<DIM, R> q;
   q.rho = u[0];
-  q.irho = Ar<R>::rcp(u[0]);
+  q.irho = irho;
 #pragma unroll
   for (int d = 0; d < DIM; ++d) q.v[d] = u[1 + d] * q.irho;
   q.pd = pd;
   q.p = pd + p_ref;
   return q;
+}
+
+template <int DIM, class R>
+__device__ __forceinline__ Prim<DIM, R> prims(const R* u, R pd, R p_ref) {
+  return prims_i<DIM>(u, Ar<R>::rcp(u[0]), pd, p_ref);
 }
 
 // Cartesian flux F^L(U) in direction L (compile-time); momentum carries pd.
@@ -212,16 +258,121 @@ __device__ __forceinline__ void point_flux(const R* u, const Prim<DIM, R>& q, R*
   F[DIM + 1] = (u[DIM + 1] + q.p) * q.v[L];
 }
 
-// Logarithmic mean for Ranocha's flux (App. A): with s = a+b, f = (a-b)/s, u = f^2,
-//   a^ln = (s/2) G(u),  G = 1/F,  F(u) = sum_k u^k/(2k+1) = atanh(f)/f,
-// where the Taylor series of 1/F is 1 - u/3 - 4u^2/45 - 44u^3/945 - c4 u^4 (c4 =
-// 0.0301940...), used for small u (the Ismail-Roe idea of a series near a = b, here
-// expanded for the reciprocal so that no division is needed); otherwise a^ln =
-// (a-b)/ln(a/b).  FP32 takes the logarithms la, lb computed once per node and evaluates
-// both forms, then selects (no divergent branch, one fast reciprocal); FP64 branches and
-// takes the logarithm of the ratio only on the (rare, in smooth regions) log branch, since
-// an FP64 logarithm costs as much as dozens of FP64 FMAs.
-// Arguments: a, b; d = a - b, la, lb (FP32 only), s = a + b, f = d / s.
+// Four flux-precision values loaded or stored as one 16-byte (FP32) shared-memory access.
+template <class R>
+struct alignas(4 * sizeof(R)) Q4 {
+  R x, y, z, w;
+};
+
+// Per-node records of Ranocha's two-point flux (App. A), built once per node:
+//   A = (rho, beta = rho/p, 2 ln rho, ln beta)      (FP64: the logarithms are not used)
+//   B = (v_1, v_2, v_3 (0 in 2D), pd = p - p_ref)
+template <int DIM, class R>
+__device__ __forceinline__ void ec_records(const Prim<DIM, R>& q, Q4<R>& A, Q4<R>& B) {
+  const R beta = q.rho * Ar<R>::rcp(q.p);
+  if constexpr (sizeof(R) == 4) A = Q4<R>{q.rho, beta, R(2) * Ar<R>::log(q.rho), Ar<R>::log(beta)};
+  else A = Q4<R>{q.rho, beta, R(0), R(0)};
+  B = Q4<R>{q.v[0], q.v[1], DIM == 3 ? q.v[DIM - 1] : R(0), q.pd};
+}
+
+// Ranocha's EC two-point flux in direction L from two records (App. A; energy component in
+// the published consistent form
+//   f_rho = rho^ln {{v_L}},  f_m = f_rho {{v}} + {{p}} e_L,
+//   f_E = f_rho (1/((gamma-1) beta^ln) + v_a.v_b/2) + (p_a v_b,L + p_b v_a,L)/2,
+// where beta = rho/p and {{.}} is the arithmetic mean; {{p}} e_L is carried by pd).
+// Logarithmic means: with s = a + b, f = (a - b)/s, u = f^2, a^ln = (s/2)/Fs(u) where
+// Fs(u) = atanh(f)/f = 1 + u/3 + u^2/5 + u^3/7 + ... .  For small u (the Ismail-Roe idea of
+// a series near a = b) rho^ln/2 = (s/4) G(u), G = 1/Fs = 1 - u/3 - 4u^2/45 - 44u^3/945 -
+// c4 u^4, and 1/beta^ln = 2 Fs(u)/s, so that beta^ln is never inverted; otherwise
+// rho^ln/2 = (a - b)/(2 ln a - 2 ln b) and 1/beta^ln = (ln a - ln b)/(a - b).  FP32 takes
+// the per-node logarithms of the records and evaluates both forms, then selects (no
+// divergent branch); the two means share one reciprocal of s_rho s_beta and run as packed
+// FP32x2 operations.  FP64 branches and takes the logarithm of the ratio only on the (rare,
+// in smooth regions) log branch.  The energy pressure term is split as
+// (pd_a v_b,L + pd_b v_a,L)/2 + p_ref {{v_L}}.
+template <int DIM, int L>
+__device__ __forceinline__ void ec_flux_rec(const Q4<float>& a, const Q4<float>& av, const Q4<float>& b,
+                                            const Q4<float>& bv, float igm1, float p_ref, float* F) {
+  const float2 ra = make_float2(a.x, a.y), rb = make_float2(b.x, b.y);  // (rho, beta)
+  const float2 s = __fadd2_rn(ra, rb);
+  const float2 d = __ffma2_rn(rb, make_float2(-1.0f, -1.0f), ra);
+  float inv;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(inv) : "f"(s.x * s.y));
+  const float2 is = make_float2(s.y * inv, s.x * inv);                  // (1/s_rho, 1/s_beta)
+  const float2 f = __fmul2_rn(d, is);
+  const float2 u = __fmul2_rn(f, f);
+  // (G/4, 2 Fs) by Horner's rule on both lanes
+  float2 P = __ffma2_rn(make_float2(-0.25f * 0.030194003527336861f, 2.0f / 9.0f), u,
+                        make_float2(-0.25f * 44.0f / 945.0f, 2.0f / 7.0f));
+  P = __ffma2_rn(P, u, make_float2(-0.25f * 4.0f / 45.0f, 2.0f / 5.0f));
+  P = __ffma2_rn(P, u, make_float2(-0.25f / 3.0f, 2.0f / 3.0f));
+  P = __ffma2_rn(P, u, make_float2(0.25f, 2.0f));
+  const float2 ser = __fmul2_rn(P, make_float2(s.x, is.y));              // (rho^ln/2, 1/beta^ln)
+  const float2 dl = __ffma2_rn(make_float2(b.z, b.w), make_float2(-1.0f, -1.0f), make_float2(a.z, a.w));
+  float r0, r1;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"(dl.x));
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r1) : "f"(d.y));
+  const float hr = u.x < Ar<float>::kLogMeanSeries ? ser.x : d.x * r0;  // rho^ln / 2
+  const float ib = u.y < Ar<float>::kLogMeanSeries ? ser.y : dl.y * r1; // 1 / beta^ln
+  const float2 vs01 = __fadd2_rn(make_float2(av.x, av.y), make_float2(bv.x, bv.y));
+  const float vs2 = av.z + bv.z;
+  const float2 pv = __fmul2_rn(make_float2(av.x, av.y), make_float2(bv.x, bv.y));
+  const float vab = __fmaf_rn(av.z, bv.z, pv.x + pv.y);
+  const float vsl = L == 0 ? vs01.x : (L == 1 ? vs01.y : vs2);
+  const float val = L == 0 ? av.x : (L == 1 ? av.y : av.z);
+  const float vbl = L == 0 ? bv.x : (L == 1 ? bv.y : bv.z);
+  const float frho = hr * vsl;
+  const float hf = 0.5f * frho;
+  F[0] = frho;
+  const float2 fm = __fmul2_rn(make_float2(hf, hf), vs01);
+  F[1] = fm.x;
+  F[2] = fm.y;
+  if constexpr (DIM == 3) F[3] = hf * vs2;
+  F[1 + L] = __fmaf_rn(0.5f, av.w + bv.w, F[1 + L]);
+  const float e1 = frho * __fmaf_rn(0.5f, vab, igm1 * ib);
+  const float pt = __fmaf_rn(av.w, vbl, bv.w * val);
+  F[DIM + 1] = __fmaf_rn(0.5f, __fmaf_rn(p_ref, vsl, pt), e1);
+}
+
+template <int DIM, int L>
+__device__ __forceinline__ void ec_flux_rec(const Q4<double>& a, const Q4<double>& av, const Q4<double>& b,
+                                            const Q4<double>& bv, double igm1, double p_ref, double* F) {
+  const double sr = a.x + b.x, sb = a.y + b.y, dr = a.x - b.x, db = a.y - b.y;
+  const double inv = rcp64(sr * sb);
+  const double isr = sb * inv, isb = sr * inv;
+  const double fr = dr * isr, fb = db * isb;
+  const double ur = fr * fr, ub = fb * fb;
+  double hr, ib;
+  if (ur < Ar<double>::kLogMeanSeries) {
+    const double G = 0.25 + ur * (-0.25 / 3.0 + ur * (-0.25 * 4.0 / 45.0 + ur * (-0.25 * 44.0 / 945.0 +
+                                                                                 ur * (-0.25 * 0.030194003527336861))));
+    hr = sr * G;
+  } else {
+    hr = 0.5 * dr * rcp64(::log(a.x * rcp64(b.x)));
+  }
+  if (ub < Ar<double>::kLogMeanSeries) {
+    const double Fs = 2.0 + ub * (2.0 / 3.0 + ub * (2.0 / 5.0 + ub * (2.0 / 7.0 + ub * (2.0 / 9.0))));
+    ib = isb * Fs;
+  } else {
+    ib = ::log(a.y * rcp64(b.y)) * rcp64(db);
+  }
+  const double vs[3] = {av.x + bv.x, av.y + bv.y, av.z + bv.z};
+  const double vab = av.x * bv.x + av.y * bv.y + av.z * bv.z;
+  const double va[3] = {av.x, av.y, av.z}, vb[3] = {bv.x, bv.y, bv.z};
+  const double frho = hr * vs[L];
+  const double hf = 0.5 * frho;
+  F[0] = frho;
+#pragma unroll
+  for (int dd = 0; dd < DIM; ++dd) F[1 + dd] = hf * vs[dd];
+  F[1 + L] += 0.5 * (av.w + bv.w);
+  F[DIM + 1] = frho * (igm1 * ib + 0.5 * vab) + 0.5 * (av.w * vb[L] + bv.w * va[L] + p_ref * vs[L]);
+}
+
+// Log mean a^ln with its series branch (the curved kernel's contracted flux below): with
+// s = a+b, f = (a-b)/s, u = f^2, a^ln = (s/2) G(u), G = 1/Fs as above; otherwise
+// (a-b)/ln(a/b).  FP32 takes the logarithms la, lb computed once per node and evaluates both
+// forms, then selects; FP64 branches.  Arguments: a, b; d = a - b, la, lb (FP32 only),
+// s = a + b, f = d / s.
 template <class R>
 __device__ __forceinline__ R log_mean_from(R a, R b, R d, R la, R lb, R s, R f) {
   const R u = f * f;
@@ -238,35 +389,6 @@ __device__ __forceinline__ R log_mean_from(R a, R b, R d, R la, R lb, R s, R f) 
     }
     return Ar<R>::div(d, Ar<R>::log(Ar<R>::div(a, b)));
   }
-}
-
-// Ranocha's EC two-point flux in direction L (App. A; energy component in the published
-// consistent form f_E = f_rho (1/((gamma-1) beta^ln) + u_L.u_R/2) + (p_L u_R + p_R u_L)/2,
-// beta = rho/p).  Inputs are per-node rho, v, pd and beta = rho/p.
-template <int DIM, int L, class R>
-__device__ __forceinline__ void ec_flux_prims(R rL, const R* vL, R pdL, R bL, R lrL, R lbL, R rR,
-                                              const R* vR, R pdR, R bR, R lrR, R lbR, R igm1,
-                                              R p_ref, R* F) {
-  const R sr = rL + rR, sb = bL + bR, dr = rL - rR, db = bL - bR;
-  const R inv = Ar<R>::rcp(sr * sb);  // one reciprocal serves both f's
-  const R fr = dr * (sb * inv);
-  const R fb = db * (sr * inv);
-  const R rho_ln = log_mean_from(rL, rR, dr, lrL, lrR, sr, fr);
-  const R beta_ln = log_mean_from(bL, bR, db, lbL, lbR, sb, fb);
-  R vs[DIM];  // v_L + v_R (the factor 1/2 of the averages is folded into the products)
-  R vLvR = R(0);
-#pragma unroll
-  for (int d = 0; d < DIM; ++d) {
-    vs[d] = vL[d] + vR[d];
-    vLvR += vL[d] * vR[d];
-  }
-  const R frho = (R(0.5) * rho_ln) * vs[L];
-  const R hf = R(0.5) * frho;
-  F[0] = frho;
-#pragma unroll
-  for (int d = 0; d < DIM; ++d) F[1 + d] = d == L ? hf * vs[d] + R(0.5) * (pdL + pdR) : hf * vs[d];
-  F[DIM + 1] = frho * (igm1 * Ar<R>::rcp(beta_ln) + R(0.5) * vLvR) +
-               R(0.5) * ((pdL + p_ref) * vR[L] + (pdR + p_ref) * vL[L]);
 }
 
 // The same two-point flux contracted with a direction n, sum_d n_d F#_d (curved elements:
@@ -306,11 +428,10 @@ __device__ __forceinline__ void ec_flux_prims_n(R rL, const R* vL, R pdL, R bL, 
 template <int DIM, int L, class R>
 __device__ __forceinline__ void ec_flux(const Prim<DIM, R>& a, const Prim<DIM, R>& b, R igm1,
                                         R p_ref, R* F) {
-  const R ba = a.rho * Ar<R>::rcp(a.p), bb = b.rho * Ar<R>::rcp(b.p);
-  const bool f32 = sizeof(R) == 4;  // the FP64 log mean takes its own logarithm
-  ec_flux_prims<DIM, L>(a.rho, a.v, a.pd, ba, f32 ? Ar<R>::log(a.rho) : R(0), f32 ? Ar<R>::log(ba) : R(0),
-                        b.rho, b.v, b.pd, bb, f32 ? Ar<R>::log(b.rho) : R(0), f32 ? Ar<R>::log(bb) : R(0),
-                        igm1, p_ref, F);
+  Q4<R> aA, aB, bA, bB;
+  ec_records<DIM>(a, aA, aB);
+  ec_records<DIM>(b, bA, bB);
+  ec_flux_rec<DIM, L>(aA, aB, bA, bB, igm1, p_ref, F);
 }
 
 // Local Lax-Friedrichs (Rusanov): F* = (F_L + F_R)/2 - lambda/2 (U_R - U_L),

@@ -31,7 +31,32 @@ struct InstArgs {
 template <class R>
 struct ScalarsT {
   R gamma, gm1, igm1, p_ref, cbdt, abdt;
+  R hgm1;                // (gamma - 1) / 2
+  R margin_e, margin_0;  // positivity margin 2^-18 ((gamma - 1)|E| + |p_ref|) = margin_e |E| + margin_0
 };
+// Fill both precisions of the launch scalars (host).
+inline void fill_scalars(ScalarsT<double>& d, ScalarsT<float>& f, double gamma, double p_ref, double cbdt,
+                         double abdt) {
+  const double gm1 = gamma - 1.0, s = 1.0 / 262144.0;  // 2^-18
+  d.gamma = gamma;
+  d.gm1 = gm1;
+  d.igm1 = 1.0 / gm1;
+  d.p_ref = p_ref;
+  d.cbdt = cbdt;
+  d.abdt = abdt;
+  d.hgm1 = 0.5 * gm1;
+  d.margin_e = s * gm1;
+  d.margin_0 = s * (p_ref < 0.0 ? -p_ref : p_ref);
+  f.gamma = (float)gamma;
+  f.gm1 = (float)gamma - 1.0f;
+  f.igm1 = 1.0f / f.gm1;
+  f.p_ref = (float)p_ref;
+  f.cbdt = (float)cbdt;
+  f.abdt = (float)abdt;
+  f.hgm1 = (float)d.hgm1;
+  f.margin_e = (float)d.margin_e;
+  f.margin_0 = (float)d.margin_0;
+}
 
 // Arguments of one fused stage launch (passed by value).
 struct StageArgs {

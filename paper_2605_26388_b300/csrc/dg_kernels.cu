@@ -111,10 +111,10 @@ __device__ void two_point_one(int kind, const double* uL, const double* uR, doub
     a[v] = Ar<R>::load(a64[v]);
     b[v] = Ar<R>::load(b64[v]);
   }
-  double ea, eb;
   const R pr = R(p_ref), gm = R(gamma), igm1 = R(1) / (gm - R(1));
-  const Prim<DIM, R> pa = prims<DIM>(a, pdev<DIM>(a64, a, gamma - 1.0, p_ref, ea), pr);
-  const Prim<DIM, R> pb = prims<DIM>(b, pdev<DIM>(b64, b, gamma - 1.0, p_ref, eb), pr);
+  const R hgm1 = R(0.5 * (gamma - 1.0));
+  const Prim<DIM, R> pa = prims<DIM>(a, pdev<DIM>(a64, a, gamma - 1.0, p_ref, hgm1), pr);
+  const Prim<DIM, R> pb = prims<DIM>(b, pdev<DIM>(b64, b, gamma - 1.0, p_ref, hgm1), pr);
   if (kind < 0) ec_flux<DIM, L>(pa, pb, igm1, pr, f);
   else surface_flux<DIM, L>(kind, a, pa, b, pb, gm, igm1, pr, f);
 #pragma unroll

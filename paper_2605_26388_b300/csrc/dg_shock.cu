@@ -223,12 +223,11 @@ __device__ __forceinline__ void interface_flux(const ShockArgs& a, int l, const 
     uL0[v] = Ar<R>::load(L64[v]);
     uR0[v] = Ar<R>::load(R64[v]);
   }
-  double rhoe;
-  const R pdL = pdev<DIM>(L64, uL0, a.pd.gm1, a.pd.p_ref, rhoe);
-  const R pdR = pdev<DIM>(R64, uR0, a.pd.gm1, a.pd.p_ref, rhoe);
+  const ScalarsT<R>& k = shs<R>(a);
+  const R pdL = pdev<DIM>(L64, uL0, a.pd.gm1, a.pd.p_ref, k.hgm1);
+  const R pdR = pdev<DIM>(R64, uR0, a.pd.gm1, a.pd.p_ref, k.hgm1);
   to_face_axes<DIM>(uL0, uL, l);
   to_face_axes<DIM>(uR0, uR, l);
-  const ScalarsT<R>& k = shs<R>(a);
   const Prim<DIM, R> pa = prims<DIM>(uL, pdL, k.p_ref);
   const Prim<DIM, R> pb = prims<DIM>(uR, pdR, k.p_ref);
   R Fs[NV];
@@ -245,14 +244,13 @@ __device__ __forceinline__ void domain_face_flux(const ShockArgs& a, int fb, int
   R own0[NV], own[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) own0[v] = Ar<R>::load(own64[v]);
-  double rhoe;
-  const R pd = pdev<DIM>(own64, own0, a.pd.gm1, a.pd.p_ref, rhoe);
-  to_face_axes<DIM>(own0, own, l);
   const ScalarsT<R>& k = shs<R>(a);
+  const R pd = pdev<DIM>(own64, own0, a.pd.gm1, a.pd.p_ref, k.hgm1);
+  to_face_axes<DIM>(own0, own, l);
   const Prim<DIM, R> po = prims<DIM>(own, pd, k.p_ref);
   R Fs[NV];
   boundary_flux<DIM, R>(a.inst, fb, l, side, own, po, a.surface, k.gamma, k.igm1, k.p_ref, a.pd.gm1,
-                        a.pd.p_ref, Fs);
+                        a.pd.p_ref, k.hgm1, Fs);
   from_face_axes<DIM>(Fs, F, l);
 }
 

@@ -106,7 +106,7 @@ __device__ __forceinline__ int boundary_face(const InstArgs& I, int dim, int e, 
 template <int DIM, class R>
 __device__ __forceinline__ void boundary_flux(const InstArgs& I, int fb, int l, int side, const R* own,
                                               const Prim<DIM, R>& po, int kind, R gamma, R igm1,
-                                              R p_ref, double gm1_64, double p_ref_64, R* Fs) {
+                                              R p_ref, double gm1_64, double p_ref_64, R hgm1, R* Fs) {
   constexpr int NV = DIM + 2;
   const int type = I.bc[fb];
   if (type == 3) {  // outflow
@@ -128,8 +128,7 @@ __device__ __forceinline__ void boundary_flux(const InstArgs& I, int fb, int l, 
       b64[v] = I.bcs[fb][v];
       b0[v] = Ar<R>::load(b64[v]);
     }
-    double rhoe;
-    const R pd = pdev<DIM>(b64, b0, gm1_64, p_ref_64, rhoe);
+    const R pd = pdev<DIM>(b64, b0, gm1_64, p_ref_64, hgm1);
     to_face_axes<DIM>(b0, ext, l);
     pe = prims<DIM>(ext, pd, p_ref);
     if (type == 2) {  // inflow
@@ -143,12 +142,6 @@ __device__ __forceinline__ void boundary_flux(const InstArgs& I, int fb, int l, 
 
 constexpr int cmax(int a, int b) { return a > b ? a : b; }
 constexpr int al4(int n) { return (n + 3) & ~3; }
-
-// Four flux-precision values loaded or stored as one 16-byte (FP32) shared-memory access.
-template <class R>
-struct alignas(4 * sizeof(R)) Q4 {
-  R x, y, z, w;
-};
 
 // the launch scalars in the flux precision (precomputed on the host)
 template <class R>
@@ -168,6 +161,9 @@ template <> __device__ __forceinline__ float sv<float>(const InstArgs& I, int l)
 template <class R> __device__ __forceinline__ R liftv(const InstArgs& I);
 template <> __device__ __forceinline__ double liftv<double>(const InstArgs& I) { return I.lift; }
 template <> __device__ __forceinline__ float liftv<float>(const InstArgs& I) { return I.liftf; }
+template <class R> __device__ __forceinline__ R from64(double x);
+template <> __device__ __forceinline__ double from64<double>(double x) { return x; }
+template <> __device__ __forceinline__ float from64<float>(double x) { return d2f_rn(x); }
 
 template <int DIM, int N, bool EC, class R, int GS = 1>
 struct EulerStage {
@@ -181,9 +177,8 @@ struct EulerStage {
   // (i, i+o mod N1) for o = 1..NO, the last offset (o = N1/2 when N1 is even) only for
   // i < N1/2, so that every unordered pair is evaluated exactly once.
   static constexpr int NO = N1 / 2;
-  // per-node staged quantities: EC -- two Q4 records per node, QA = (rho, v_1, v_2, v_3 or 0)
-  // and QB = (pd, beta = rho/p, ln rho, ln beta); strong/weak -- the DIM point fluxes (NV
-  // each) and pd
+  // per-node staged quantities: EC -- the two Q4 records of the two-point flux (A, B); strong/
+  // weak -- the DIM point fluxes (NV each) and pd
   static constexpr int NQ = EC ? 8 : (DIM * NV + 1);
   static constexpr int PD = DIM * NV;  // strong/weak: row of pd
   static constexpr int NXN = EC ? DIM * NO : 0;            // pair slots per node
@@ -192,14 +187,17 @@ struct EulerStage {
   static constexpr int ST_U = 0, ST_N = EPB * NV * NP, ST_T = 2 * EPB * NV * NP;
   static constexpr int ST_SIZE = ST_T + EPB * NF * NV * NFN;
   // flux-precision arrays
-  // pair slot: XA = F_0..F_3 as Q4 per node, then XB = F_4 per node (3D), padded to 16 bytes
+  // pair slot: F_0..F_3 as Q4 per node, then F_4 per node (3D), padded to 16 bytes
   static constexpr int XSLOT = 4 * NP + (NV > 4 ? al4(NP) : 0);
   static constexpr int OFF_U = 0;                                  // [EPB][NV][NP]
   static constexpr int OFF_Q = al4(OFF_U + EPB * NV * NP);         // EC: [EPB][2][NP] Q4, else [EPB][NQ][NP]
   static constexpr int OFF_S = al4(OFF_Q + EPB * NQ * NP);         // [EPB][NF][NFN][NV]
   static constexpr int OFF_X = al4(OFF_S + EPB * NF * NFN * NV);   // [EPB][DIM][NO] pair slots
-  static constexpr int OFF_D = OFF_X + EPB * NXN * XSLOT;          // [N1][N1]
-  static constexpr int R_SIZE = OFF_D + N1 * N1;
+  // coefficient tables, scaled by 2/dx_l: EC -- own [DIM][N1][NO] (s_l Dv_ij, j = i+o) then
+  // partner [DIM][N1][NO] (s_l Dv_ik, k = i-o); strong/weak -- [DIM][N1][N1] (s_l Dv)
+  static constexpr int OFF_D = OFF_X + EPB * NXN * XSLOT;
+  static constexpr int ND = EC ? 2 * DIM * N1 * NO : DIM * N1 * N1;
+  static constexpr int R_SIZE = OFF_D + ND;
   static constexpr size_t smem_bytes() {
     return sizeof(double) * 2 * (size_t)ST_SIZE + sizeof(R) * (size_t)R_SIZE +
            sizeof(int) * (size_t)(2 * EPB * NF + 4);
@@ -220,7 +218,7 @@ struct EulerStage {
     return m;
   }
 
-  // EC records of element slot el: QA[NP] then QB[NP]
+  // EC records of element slot el: A[NP] then B[NP]
   static __device__ __forceinline__ Q4<R>* qa(R* sm, int el) {
     return reinterpret_cast<Q4<R>*>(sm + OFF_Q) + el * 2 * NP;
   }
@@ -229,7 +227,7 @@ struct EulerStage {
   }
   // pressure deviation of node nd of element slot el
   static __device__ __forceinline__ R pd_of(const R* sm, int el, int nd) {
-    if constexpr (EC) return qa(sm, el)[NP + nd].x;
+    if constexpr (EC) return qa(sm, el)[NP + nd].w;
     else return sm[OFF_Q + (el * NQ + PD) * NP + nd];
   }
   // pair slot (direction L, offset o) of element slot el
@@ -250,10 +248,6 @@ struct EulerStage {
     constexpr int S = G::stride(L);
     return (nd % S) + (nd / (S * N1)) * S;
   }
-  template <int L>
-  static __device__ __forceinline__ int node_pos(int nd) {
-    return (nd / G::stride(L)) % N1;
-  }
 
   // neighbour element of face `face` (direction face/2, side face%2) of element e
   static __device__ __forceinline__ int neighbour(const InstArgs& A, int e, int face) {
@@ -271,8 +265,10 @@ struct EulerStage {
   // Per-thread roles, decoded once per launch.
   struct Role {
     int el, nd;             // node role (t < EPB*NP)
+    int pos[3];             // position of the node along each direction
     int jel, face, f, ndn;  // face-job role (t < NJS): element, face, face node, neighbour node
     int ndo;                // own node of the face job
+    int pm[3];              // face axes -> Cartesian variable index of the momentum components
   };
 
   static __device__ __forceinline__ Role role() {
@@ -280,6 +276,9 @@ struct EulerStage {
     const int t = threadIdx.x;
     r.el = t / NP;
     r.nd = t - r.el * NP;
+    r.pos[0] = r.nd % N1;
+    r.pos[1] = (r.nd / N1) % N1;
+    r.pos[2] = DIM == 3 ? r.nd / (N1 * N1) : 0;
     r.jel = t / (NF * NFN);
     const int q = t - r.jel * (NF * NFN);
     r.face = q / NFN;
@@ -288,6 +287,8 @@ struct EulerStage {
     if (l == 0) { r.ndn = line_node<0>(r.f, side ? 0 : N); r.ndo = line_node<0>(r.f, side ? N : 0); }
     else if (l == 1) { r.ndn = line_node<1>(r.f, side ? 0 : N); r.ndo = line_node<1>(r.f, side ? N : 0); }
     else { r.ndn = line_node<DIM - 1>(r.f, side ? 0 : N); r.ndo = line_node<DIM - 1>(r.f, side ? N : 0); }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) r.pm[k] = 1 + (l + k) % DIM;
     return r;
   }
 
@@ -319,26 +320,20 @@ struct EulerStage {
 
   // ---- phase 2 (EC): this node's own pairs in direction L ----
   template <int L>
-  static __device__ __forceinline__ void own_pairs(R* sm, const InstArgs& I, int el, int nd,
-                                                   R igm1, R p_ref, R* acc) {
+  static __device__ __forceinline__ void own_pairs(R* sm, const Role& r, int el, R igm1, R p_ref, R* acc) {
     constexpr int S = G::stride(L);
-    const int i = node_pos<L>(nd);
-    const R s = sv<R>(I, L);
-    const R* Dv = sm + OFF_D;
+    const int nd = r.nd, i = r.pos[L];
+    const R* C = sm + OFF_D + (L * N1 + i) * NO;
     const Q4<R>* QA = qa(sm, el);
     const Q4<R> ai = QA[nd], bi = QA[NP + nd];
-    const R vi[3] = {ai.y, ai.z, ai.w};
 #pragma unroll
     for (int o = 1; o <= NO; ++o) {
       if (2 * o == N1 && i >= N1 / 2) break;
-      const int j = (i + o < N1) ? i + o : i + o - N1;
-      const int nj = nd + (j - i) * S;
+      const int nj = (i + o < N1) ? nd + o * S : nd + (o - N1) * S;
       const Q4<R> aj = QA[nj], bj = QA[NP + nj];
-      const R vj[3] = {aj.y, aj.z, aj.w};
       R F[NV];
-      ec_flux_prims<DIM, L>(ai.x, vi, bi.x, bi.y, bi.z, bi.w, aj.x, vj, bj.x, bj.y, bj.z, bj.w,
-                            igm1, p_ref, F);
-      const R c = s * Dv[i * N1 + j];
+      ec_flux_rec<DIM, L>(ai, bi, aj, bj, igm1, p_ref, F);
+      const R c = C[o - 1];
 #pragma unroll
       for (int v = 0; v < NV; ++v) acc[v] -= c * F[v];
       R* X = xslot(sm, el, L, o);
@@ -347,20 +342,18 @@ struct EulerStage {
     }
   }
 
-  // ---- phase 4 (EC): the pairs other nodes evaluated for this node, and D_ii F(U_i) ----
+  // ---- phase 4 (EC): the pairs other nodes evaluated for this node ----
   template <int L>
-  static __device__ __forceinline__ void partner_pairs(const R* sm, const InstArgs& I, int el,
-                                                       int nd, R p_ref, R* acc) {
+  static __device__ __forceinline__ void partner_pairs(const R* sm, const Role& r, int el, R* acc) {
     constexpr int S = G::stride(L);
-    const int i = node_pos<L>(nd);
-    const R s = sv<R>(I, L);
-    const R* Dv = sm + OFF_D;
+    const int nd = r.nd, i = r.pos[L];
+    const R* C = sm + OFF_D + DIM * N1 * NO + (L * N1 + i) * NO;
 #pragma unroll
     for (int o = 1; o <= NO; ++o) {
-      const int k = (i - o >= 0) ? i - o : i - o + N1;  // owner of pair (k, i) at offset o
-      if (2 * o == N1 && k >= N1 / 2) continue;
-      const int nk = nd + (k - i) * S;
-      const R c = s * Dv[i * N1 + k];
+      // owner k = i - o (mod N1) of pair (k, i) at offset o
+      if (2 * o == N1 && (i >= o ? i - o : i - o + N1) >= N1 / 2) continue;
+      const int nk = (i >= o) ? nd - o * S : nd + (N1 - o) * S;
+      const R c = C[o - 1];
       const R* X = xslot(sm, el, L, o);
       const Q4<R> f = reinterpret_cast<const Q4<R>*>(X)[nk];
       acc[0] -= c * f.x;
@@ -369,31 +362,18 @@ struct EulerStage {
       acc[3] -= c * f.w;
       if constexpr (NV > 4) acc[4] -= c * X[4 * NP + nk];
     }
-    if (i == 0 || i == N) {  // diagonal: F#(U_i, U_i) = F(U_i); only the end nodes have D_ii != 0
-      R u[NV];
-#pragma unroll
-      for (int v = 0; v < NV; ++v) u[v] = sm[OFF_U + (el * NV + v) * NP + nd];
-      const Prim<DIM, R> qq = prims<DIM>(u, pd_of(sm, el, nd), p_ref);
-      R F[NV];
-      point_flux<DIM, L>(u, qq, F);
-      const R c = s * Dv[i * N1 + i];
-#pragma unroll
-      for (int v = 0; v < NV; ++v) acc[v] -= c * F[v];
-    }
   }
 
   // ---- phase 4 (strong/weak): contract the volume operator with the staged point fluxes ----
   template <int L>
-  static __device__ __forceinline__ void contract(const R* sm, const InstArgs& I, int el, int nd,
-                                                  R* acc) {
+  static __device__ __forceinline__ void contract(const R* sm, const Role& r, int el, R* acc) {
     constexpr int S = G::stride(L);
-    const int i = node_pos<L>(nd);
-    const R s = sv<R>(I, L);
-    const R* Dv = sm + OFF_D;
+    const int nd = r.nd, i = r.pos[L];
+    const R* Dl = sm + OFF_D + (L * N1 + i) * N1;
     const R* Fq = sm + OFF_Q + (el * NQ + L * NV) * NP + nd - i * S;
 #pragma unroll
     for (int m = 0; m < N1; ++m) {
-      const R c = s * Dv[i * N1 + m];
+      const R c = Dl[m];
 #pragma unroll
       for (int v = 0; v < NV; ++v) acc[v] -= c * Fq[v * NP + m * S];
     }
@@ -415,35 +395,29 @@ struct EulerStage {
       out[3] = l == 0 ? in[3] : (l == 1 ? in[1] : in[2]);
     }
   }
-  static __device__ __forceinline__ void from_face_axes(const R* in, R* out, int l) {
-    out[0] = in[0];
-    out[NV - 1] = in[NV - 1];
-    if constexpr (DIM == 2) {
-      out[1] = l ? in[2] : in[1];
-      out[2] = l ? in[1] : in[2];
-    } else {
-      out[1] = l == 0 ? in[1] : (l == 1 ? in[3] : in[2]);
-      out[2] = l == 0 ? in[2] : (l == 1 ? in[1] : in[3]);
-      out[3] = l == 0 ? in[3] : (l == 1 ? in[2] : in[1]);
-    }
-  }
 
   // ---- phase 3: one face node (face r.face of element r.jel) ----
+  // The own trace is read in face axes (permuted shared-memory offsets); the neighbour's
+  // FP64 trace is converted and its pressure deviation formed in Cartesian order (as the
+  // neighbour's own phase 1 does, so that both elements see the same bits), then relabelled.
+  // The result is stored back to Cartesian components by permuted offsets.
   static __device__ __forceinline__ void face_job(R* sm, const double* trace, const StageArgs& A,
                                                   const InstArgs& I, const Role& r, int e, R gamma,
                                                   R igm1, R p_ref) {
     const int ej = r.jel, side = r.face & 1, l = r.face >> 1;
-    R own0[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) own0[v] = sm[OFF_U + (ej * NV + v) * NP + r.ndo];
-    const R pd_own = pd_of(sm, ej, r.ndo);
+    const ScalarsT<R>& k = sc<R>(A);
+    const R* Uo = sm + OFF_U + ej * NV * NP + r.ndo;
     R own[NV];
-    to_face_axes(own0, own, l);
-    const Prim<DIM, R> po = prims<DIM>(own, pd_own, p_ref);
+    own[0] = Uo[0];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) own[1 + d] = Uo[r.pm[d] * NP];
+    own[NV - 1] = Uo[(NV - 1) * NP];
+    const Prim<DIM, R> po = prims_i<DIM>(own, Ar<R>::rcp(own[0]), pd_of(sm, ej, r.ndo), p_ref);
     R Fs[NV];
     const int fb = I.nonper ? boundary_face(I, DIM, e, l, side) : -1;
     if (fb >= 0) {  // a domain face with a boundary condition
-      boundary_flux<DIM, R>(I, fb, l, side, own, po, A.surface, gamma, igm1, p_ref, A.pd.gm1, A.pd.p_ref, Fs);
+      boundary_flux<DIM, R>(I, fb, l, side, own, po, A.surface, gamma, igm1, p_ref, A.pd.gm1, A.pd.p_ref,
+                            k.hgm1, Fs);
     } else {
       R nbr0[NV];
       double n64[NV];
@@ -452,11 +426,11 @@ struct EulerStage {
         n64[v] = trace[((ej * NF + r.face) * NV + v) * NFN + r.f];
         nbr0[v] = Ar<R>::load(n64[v]);
       }
-      double rhoe;
-      const R pd_nbr = pdev<DIM>(n64, nbr0, A.pd.gm1, A.pd.p_ref, rhoe);
+      const R irn = Ar<R>::rcp(nbr0[0]);
+      const R pd_nbr = pdev_i<DIM>(n64, nbr0, irn, A.pd.gm1, A.pd.p_ref, k.hgm1);
       R nbr[NV];
       to_face_axes(nbr0, nbr, l);
-      const Prim<DIM, R> pn = prims<DIM>(nbr, pd_nbr, p_ref);
+      const Prim<DIM, R> pn = prims_i<DIM>(nbr, irn, pd_nbr, p_ref);
       R uL[NV], uR[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
@@ -467,23 +441,23 @@ struct EulerStage {
       const Prim<DIM, R>& b = side ? pn : po;
       surface_flux<DIM, 0>(A.surface, uL, a, uR, b, gamma, igm1, p_ref, Fs);  // the single call site
     }
-    if (!A.weak) {
+    if (!EC && !A.weak) {  // strong form: F* - F(U_own) (the two-point form's diagonal cancels it)
       R Fo[NV];
       point_flux<DIM, 0>(own, po, Fo);
 #pragma unroll
       for (int v = 0; v < NV; ++v) Fs[v] -= Fo[v];
     }
-    R Fj[NV];
-    from_face_axes(Fs, Fj, l);
     const R lf = (side ? R(-1) : R(1)) * sv<R>(I, l) * liftv<R>(I);
     R* Sx = sm + OFF_S + ((ej * NF + r.face) * NFN + r.f) * NV;
+    Sx[0] = lf * Fs[0];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) Sx[v] = lf * Fj[v];
+    for (int d = 0; d < DIM; ++d) Sx[r.pm[d]] = lf * Fs[1 + d];
+    Sx[NV - 1] = lf * Fs[NV - 1];
   }
 
   template <int L>
-  static __device__ __forceinline__ void gather_faces(const R* sm, int el, int nd, R* acc) {
-    const int i = node_pos<L>(nd), f = node_line<L>(nd);
+  static __device__ __forceinline__ void gather_faces(const R* sm, const Role& r, int el, R* acc) {
+    const int i = r.pos[L], f = node_line<L>(r.nd);
     if (i == 0) {
       const R* Sx = sm + OFF_S + ((el * NF + 2 * L) * NFN + f) * NV;
 #pragma unroll
@@ -505,7 +479,8 @@ struct EulerStage {
     const double* SN = S + ST_N;
     const double* TR = S + ST_T;
     const int e0 = g * EPB;
-    const R gamma = sc<R>(A).gamma, igm1 = sc<R>(A).igm1, p_ref = sc<R>(A).p_ref;
+    const ScalarsT<R>& k = sc<R>(A);
+    const R gamma = k.gamma, igm1 = k.igm1, p_ref = k.p_ref;
     const int el = r.el, nd = r.nd;
     const bool active = (t < EPB * NP) && (e0 + el < I.n_elem);
 
@@ -519,21 +494,17 @@ struct EulerStage {
         u[v] = Ar<R>::load(u64[v]);
         sm[OFF_U + (el * NV + v) * NP + nd] = u[v];
       }
-      double rhoe;
-      const R pd = pdev<DIM>(u64, u, A.pd.gm1, A.pd.p_ref, rhoe);
-      const Prim<DIM, R> q = prims<DIM>(u, pd, p_ref);
+      const R irho = Ar<R>::rcp(u[0]);
+      const R pd = pdev_i<DIM>(u64, u, irho, A.pd.gm1, A.pd.p_ref, k.hgm1);
       // positivity of the state this stage reads (rho > 0 and rho e > 0), decided on the
-      // FP64 values by their sign/exponent bits
-      if (!(__double2hiint(u64[0]) > 0 && __double2hiint(rhoe) > 0)) atomicOr(A.err, 2u);
-      R* Q = sm + OFF_Q + el * NQ * NP;
+      // FP64 values
+      if (!positive<DIM>(u64, u, pd, p_ref, k.margin_e, k.margin_0, A.pd.gm1)) atomicOr(A.err, 2u);
+      const Prim<DIM, R> q = prims_i<DIM>(u, irho, pd, p_ref);
       if constexpr (EC) {
-        const R beta = q.rho * Ar<R>::rcp(q.p);
         Q4<R>* QA = qa(sm, el);
-        QA[nd] = Q4<R>{q.rho, q.v[0], q.v[1], DIM == 3 ? q.v[DIM - 1] : R(0)};
-        // logarithms for the FP32 log mean only (the FP64 one branches to its own logarithm)
-        if constexpr (sizeof(R) == 4) QA[NP + nd] = Q4<R>{pd, beta, Ar<R>::log(q.rho), Ar<R>::log(beta)};
-        else QA[NP + nd] = Q4<R>{pd, beta, R(0), R(0)};
+        ec_records<DIM>(q, QA[nd], QA[NP + nd]);
       } else {
+        R* Q = sm + OFF_Q + el * NQ * NP;
         Q[PD * NP + nd] = pd;
         R F[NV];
         point_flux<DIM, 0>(u, q, F);
@@ -557,9 +528,9 @@ struct EulerStage {
     for (int v = 0; v < NV; ++v) acc[v] = R(0);
     if constexpr (EC) {
       if (active) {
-        own_pairs<0>(sm, I, el, nd, igm1, p_ref, acc);
-        own_pairs<1>(sm, I, el, nd, igm1, p_ref, acc);
-        if constexpr (DIM == 3) own_pairs<2>(sm, I, el, nd, igm1, p_ref, acc);
+        own_pairs<0>(sm, r, el, igm1, p_ref, acc);
+        own_pairs<1>(sm, r, el, igm1, p_ref, acc);
+        if constexpr (DIM == 3) own_pairs<2>(sm, r, el, igm1, p_ref, acc);
       }
     }
     // phase 3: face jobs
@@ -569,17 +540,17 @@ struct EulerStage {
     // phase 4: gather, then L or the stage update
     if (!active) return;
     if constexpr (EC) {
-      partner_pairs<0>(sm, I, el, nd, p_ref, acc);
-      partner_pairs<1>(sm, I, el, nd, p_ref, acc);
-      if constexpr (DIM == 3) partner_pairs<2>(sm, I, el, nd, p_ref, acc);
+      partner_pairs<0>(sm, r, el, acc);
+      partner_pairs<1>(sm, r, el, acc);
+      if constexpr (DIM == 3) partner_pairs<2>(sm, r, el, acc);
     } else {
-      contract<0>(sm, I, el, nd, acc);
-      contract<1>(sm, I, el, nd, acc);
-      if constexpr (DIM == 3) contract<2>(sm, I, el, nd, acc);
+      contract<0>(sm, r, el, acc);
+      contract<1>(sm, r, el, acc);
+      if constexpr (DIM == 3) contract<2>(sm, r, el, acc);
     }
-    gather_faces<0>(sm, el, nd, acc);
-    gather_faces<1>(sm, el, nd, acc);
-    if constexpr (DIM == 3) gather_faces<2>(sm, el, nd, acc);
+    gather_faces<0>(sm, r, el, acc);
+    gather_faces<1>(sm, r, el, acc);
+    if constexpr (DIM == 3) gather_faces<2>(sm, r, el, acc);
 
     const long long gi = I.base + (long long)(e0 + el) * NP + nd;
     double res[NV];
@@ -595,7 +566,7 @@ struct EulerStage {
       for (int v = 0; v < NV; ++v) res[v] = Ar<R>::widen(acc[v]);
     } else {
       // U^(k) = ca Un + cb U^(k-1) + beta dt L, with the increment beta dt L formed in R
-      const R cbdt = sc<R>(A).cbdt;
+      const R cbdt = k.cbdt;
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         const double inc = Ar<R>::widen(cbdt * acc[v]);
@@ -604,7 +575,7 @@ struct EulerStage {
         res[v] = x;
       }
       if (A.acc) {  // running sum of a later stage: acc = acc_a acc + acc_b U^(k-1) + acc_beta dt L
-        const R abdt = sc<R>(A).abdt;
+        const R abdt = k.abdt;
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
           double y = fma(A.acc_b, SU[(el * NV + v) * NP + nd], Ar<R>::widen(abdt * acc[v]));
@@ -638,8 +609,21 @@ struct EulerStage {
     }
   }
 
-  static __device__ __forceinline__ void load_ops(R* sm, const double* Dv) {
-    for (int k = threadIdx.x; k < N1 * N1; k += blockDim.x) sm[OFF_D + k] = R(Dv[k]);
+  // coefficient tables of instance I (volume operator Dv, row-major (N+1)^2), scaled by 2/dx_l
+  static __device__ __forceinline__ void load_ops(R* sm, const double* Dv, const InstArgs& I) {
+    for (int q = threadIdx.x; q < ND; q += blockDim.x) {
+      double c;
+      if constexpr (EC) {
+        const int part = q / (DIM * N1 * NO), rem = q - part * (DIM * N1 * NO);
+        const int L = rem / (N1 * NO), i = (rem / NO) % N1, o = rem % NO + 1;
+        const int j = part ? (i - o + N1) % N1 : (i + o) % N1;
+        c = I.s[L] * Dv[i * N1 + j];
+      } else {
+        const int L = q / (N1 * N1), rem = q - L * N1 * N1;
+        c = I.s[L] * Dv[rem];
+      }
+      sm[OFF_D + q] = from64<R>(c);
+    }
   }
 
   // single-instance persistent launch: groups of A.inst, double-buffered, one barrier per
@@ -650,7 +634,7 @@ struct EulerStage {
     const Smem M = carve();
     const InstArgs& I = A.inst;
     const Role r = role();
-    load_ops(M.sm, A.Dv);
+    load_ops(M.sm, A.Dv, I);
     const bool need_un = A.need_un != 0;
     const int ng = (I.n_elem + EPB - 1) / EPB;
     int g = blockIdx.x;

@@ -40,7 +40,7 @@ EXPORTS = ["dg_init_mesh", "dg_state_size", "dg_instance_offset", "dg_set_state"
            "dg_rhs", "dg_rk_stage", "dg_rk_step", "dg_max_dt", "dg_check", "dg_gll",
            "dg_two_point_flux", "dg_max_dt_noalloc", "dg_set_launch", "dg_autotune",
            "dg_rhs_vjp", "dg_rk_step_vjp", "dg_adjoint_gammabar", "dg_source_step", "dg_newton_updates", "dg_shock_alpha",
-           "dg_math_fn",
+           "dg_math_fn", "dg_alu_rate",
            "dg_last_error", "dg_free"]
 
 
@@ -136,6 +136,7 @@ def lib():
         L.dg_newton_updates.argtypes = [vp, C.POINTER(C.c_int64)]
         L.dg_shock_alpha.argtypes = [vp, vp, vp, vp]
         L.dg_math_fn.argtypes = [ip, C.c_int64, vp, vp, vp]
+        L.dg_alu_rate.argtypes = [ip, dp]
         L.dg_last_error.argtypes = [vp]
         L.dg_last_error.restype = C.c_char_p
         L.dg_free.argtypes = [vp]
