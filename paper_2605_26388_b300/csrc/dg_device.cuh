@@ -248,6 +248,16 @@ __device__ __forceinline__ Prim<DIM, R> prims(const R* u, R pd, R p_ref) {
   return prims_i<DIM>(u, Ar<R>::rcp(u[0]), pd, p_ref);
 }
 
+// The trace of a node as the Riemann fluxes see it: the momentum rebuilt as rho v from the
+// primitives.  Every kernel that evaluates a face flux forms its inputs this one way, from
+// values each side derives identically from the FP64 state, so that F* gets the same bits
+// wherever it is evaluated (both elements of a face, the shock-capturing blend).
+template <int DIM, class R>
+__device__ __forceinline__ void trace_momentum(const Prim<DIM, R>& q, R* u) {
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) u[1 + d] = q.rho * q.v[d];
+}
+
 // Cartesian flux F^L(U) in direction L (compile-time); momentum carries pd.
 template <int DIM, int L, class R>
 __device__ __forceinline__ void point_flux(const R* u, const Prim<DIM, R>& q, R* F) {
@@ -290,30 +300,41 @@ __device__ __forceinline__ void ec_records(const Prim<DIM, R>& q, Q4<R>& A, Q4<R
 // FP32x2 operations.  FP64 branches and takes the logarithm of the ratio only on the (rare,
 // in smooth regions) log branch.  The energy pressure term is split as
 // (pd_a v_b,L + pd_b v_a,L)/2 + p_ref {{v_L}}.
+// a - b on both lanes (packed FP32x2)
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  unsigned long long ra, rb, rd;
+  ra = (unsigned long long)__float_as_uint(a.x) | ((unsigned long long)__float_as_uint(a.y) << 32);
+  rb = (unsigned long long)__float_as_uint(b.x) | ((unsigned long long)__float_as_uint(b.y) << 32);
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
+  return make_float2(__uint_as_float((unsigned)rd), __uint_as_float((unsigned)(rd >> 32)));
+}
+
 template <int DIM, int L>
 __device__ __forceinline__ void ec_flux_rec(const Q4<float>& a, const Q4<float>& av, const Q4<float>& b,
                                             const Q4<float>& bv, float igm1, float p_ref, float* F) {
   const float2 ra = make_float2(a.x, a.y), rb = make_float2(b.x, b.y);  // (rho, beta)
   const float2 s = __fadd2_rn(ra, rb);
-  const float2 d = __ffma2_rn(rb, make_float2(-1.0f, -1.0f), ra);
+  const float2 d = sub2(ra, rb);
   float inv;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(inv) : "f"(s.x * s.y));
   const float2 is = make_float2(s.y * inv, s.x * inv);                  // (1/s_rho, 1/s_beta)
   const float2 f = __fmul2_rn(d, is);
   const float2 u = __fmul2_rn(f, f);
-  // (G/4, 2 Fs) by Horner's rule on both lanes
-  float2 P = __ffma2_rn(make_float2(-0.25f * 0.030194003527336861f, 2.0f / 9.0f), u,
-                        make_float2(-0.25f * 44.0f / 945.0f, 2.0f / 7.0f));
-  P = __ffma2_rn(P, u, make_float2(-0.25f * 4.0f / 45.0f, 2.0f / 5.0f));
-  P = __ffma2_rn(P, u, make_float2(-0.25f / 3.0f, 2.0f / 3.0f));
-  P = __ffma2_rn(P, u, make_float2(0.25f, 2.0f));
-  const float2 ser = __fmul2_rn(P, make_float2(s.x, is.y));              // (rho^ln/2, 1/beta^ln)
-  const float2 dl = __ffma2_rn(make_float2(b.z, b.w), make_float2(-1.0f, -1.0f), make_float2(a.z, a.w));
+  // G/4 and 2 Fs by Horner's rule (immediate coefficients)
+  float G = __fmaf_rn(-0.25f * 0.030194003527336861f, u.x, -0.25f * 44.0f / 945.0f);
+  G = __fmaf_rn(G, u.x, -0.25f * 4.0f / 45.0f);
+  G = __fmaf_rn(G, u.x, -0.25f / 3.0f);
+  G = __fmaf_rn(G, u.x, 0.25f);
+  float Fs = __fmaf_rn(2.0f / 9.0f, u.y, 2.0f / 7.0f);
+  Fs = __fmaf_rn(Fs, u.y, 2.0f / 5.0f);
+  Fs = __fmaf_rn(Fs, u.y, 2.0f / 3.0f);
+  Fs = __fmaf_rn(Fs, u.y, 2.0f);
+  const float2 dl = sub2(make_float2(a.z, a.w), make_float2(b.z, b.w));
   float r0, r1;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"(dl.x));
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r1) : "f"(d.y));
-  const float hr = u.x < Ar<float>::kLogMeanSeries ? ser.x : d.x * r0;  // rho^ln / 2
-  const float ib = u.y < Ar<float>::kLogMeanSeries ? ser.y : dl.y * r1; // 1 / beta^ln
+  const float hr = u.x < Ar<float>::kLogMeanSeries ? s.x * G : d.x * r0;     // rho^ln / 2
+  const float ib = u.y < Ar<float>::kLogMeanSeries ? is.y * Fs : dl.y * r1;  // 1 / beta^ln
   const float2 vs01 = __fadd2_rn(make_float2(av.x, av.y), make_float2(bv.x, bv.y));
   const float vs2 = av.z + bv.z;
   const float2 pv = __fmul2_rn(make_float2(av.x, av.y), make_float2(bv.x, bv.y));

@@ -230,6 +230,8 @@ __device__ __forceinline__ void interface_flux(const ShockArgs& a, int l, const 
   to_face_axes<DIM>(uR0, uR, l);
   const Prim<DIM, R> pa = prims<DIM>(uL, pdL, k.p_ref);
   const Prim<DIM, R> pb = prims<DIM>(uR, pdR, k.p_ref);
+  trace_momentum<DIM>(pa, uL);
+  trace_momentum<DIM>(pb, uR);
   R Fs[NV];
   surface_flux<DIM, 0>(a.surface, uL, pa, uR, pb, k.gamma, k.igm1, k.p_ref, Fs);
   from_face_axes<DIM>(Fs, F, l);
@@ -248,6 +250,7 @@ __device__ __forceinline__ void domain_face_flux(const ShockArgs& a, int fb, int
   const R pd = pdev<DIM>(own64, own0, a.pd.gm1, a.pd.p_ref, k.hgm1);
   to_face_axes<DIM>(own0, own, l);
   const Prim<DIM, R> po = prims<DIM>(own, pd, k.p_ref);
+  trace_momentum<DIM>(po, own);
   R Fs[NV];
   boundary_flux<DIM, R>(a.inst, fb, l, side, own, po, a.surface, k.gamma, k.igm1, k.p_ref, a.pd.gm1,
                         a.pd.p_ref, k.hgm1, Fs);

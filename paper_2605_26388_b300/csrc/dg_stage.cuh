@@ -141,6 +141,7 @@ __device__ __forceinline__ void boundary_flux(const InstArgs& I, int fb, int l, 
 }
 
 constexpr int cmax(int a, int b) { return a > b ? a : b; }
+constexpr int cmin(int a, int b) { return a < b ? a : b; }
 constexpr int al4(int n) { return (n + 3) & ~3; }
 
 // the launch scalars in the flux precision (precomputed on the host)
@@ -413,6 +414,7 @@ struct EulerStage {
     for (int d = 0; d < DIM; ++d) own[1 + d] = Uo[r.pm[d] * NP];
     own[NV - 1] = Uo[(NV - 1) * NP];
     const Prim<DIM, R> po = prims_i<DIM>(own, Ar<R>::rcp(own[0]), pd_of(sm, ej, r.ndo), p_ref);
+    trace_momentum<DIM>(po, own);
     R Fs[NV];
     const int fb = I.nonper ? boundary_face(I, DIM, e, l, side) : -1;
     if (fb >= 0) {  // a domain face with a boundary condition
@@ -431,6 +433,7 @@ struct EulerStage {
       R nbr[NV];
       to_face_axes(nbr0, nbr, l);
       const Prim<DIM, R> pn = prims_i<DIM>(nbr, irn, pd_nbr, p_ref);
+      trace_momentum<DIM>(pn, nbr);
       R uL[NV], uR[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) {

@@ -1,5 +1,5 @@
 // dg_stage3d.cu -- single-instance launches of the fused stage kernel, 3D degrees.
-#include "dg_stage.cuh"
+#include "dg_stage_ec3.cuh"
 
 namespace dg {
 
@@ -41,13 +41,57 @@ static cudaError_t launch_one(const StageArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// The two-point form of elements with 64 or more nodes: the run-walking kernel (EC3).
+template <int N, class R>
+struct EC3Grid {
+  static int ctas;
+};
+template <int N, class R>
+int EC3Grid<N, R>::ctas = 0;
+
+template <int N, class R>
+static cudaError_t prepare_ec3() {
+  using K = EC3<N, R>;
+  cudaError_t e = cudaFuncSetAttribute(k_euler_ec3<N, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)K::smem_bytes());
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_euler_ec3<N, R>, K::T, K::smem_bytes());
+  if (e != cudaSuccess) return e;
+  EC3Grid<N, R>::ctas = sms * (per_sm > 0 ? per_sm : 1);
+  return cudaSuccess;
+}
+
+template <int N, class R>
+static cudaError_t launch_ec3(const StageArgs& a, cudaStream_t s) {
+  using K = EC3<N, R>;
+  const int runs = (a.inst.n_elem + K::KRUN - 1) / K::KRUN;
+  if (runs == 0) return cudaSuccess;
+  if (EC3Grid<N, R>::ctas == 0) {
+    cudaError_t e = prepare_ec3<N, R>();
+    if (e != cudaSuccess) return e;
+  }
+  const int blocks = runs < EC3Grid<N, R>::ctas ? runs : EC3Grid<N, R>::ctas;
+  k_euler_ec3<N, R><<<blocks, K::T, K::smem_bytes(), s>>>(a);
+  return cudaGetLastError();
+}
+
 template <int DIM, int N>
 static cudaError_t launch_dn(int ec, int fp32, const StageArgs* a, cudaStream_t s) {
+  constexpr bool kEC3 = DIM == 3 && N >= 3;
   if (!a) {
-    if (ec) return fp32 ? prepare_one<DIM, N, true, float>() : prepare_one<DIM, N, true, double>();
+    if (ec) {
+      if constexpr (kEC3) return fp32 ? prepare_ec3<N, float>() : prepare_ec3<N, double>();
+      return fp32 ? prepare_one<DIM, N, true, float>() : prepare_one<DIM, N, true, double>();
+    }
     return fp32 ? prepare_one<DIM, N, false, float>() : prepare_one<DIM, N, false, double>();
   }
-  if (ec) return fp32 ? launch_one<DIM, N, true, float>(*a, s) : launch_one<DIM, N, true, double>(*a, s);
+  if (ec) {
+    if constexpr (kEC3) return fp32 ? launch_ec3<N, float>(*a, s) : launch_ec3<N, double>(*a, s);
+    return fp32 ? launch_one<DIM, N, true, float>(*a, s) : launch_one<DIM, N, true, double>(*a, s);
+  }
   return fp32 ? launch_one<DIM, N, false, float>(*a, s) : launch_one<DIM, N, false, double>(*a, s);
 }
 
