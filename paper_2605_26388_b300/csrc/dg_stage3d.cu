@@ -67,13 +67,14 @@ static cudaError_t prepare_ec3() {
 template <int N, class R>
 static cudaError_t launch_ec3(const StageArgs& a, cudaStream_t s) {
   using K = EC3<N, R>;
-  const int runs = (a.inst.n_elem + K::KRUN - 1) / K::KRUN;
-  if (runs == 0) return cudaSuccess;
+  const int nseg = (a.inst.nel[0] + K::KRUN - 1) / K::KRUN;
+  const long long runs = (long long)nseg * a.inst.nel[1] * a.inst.nel[2];
+  if (a.inst.n_elem == 0) return cudaSuccess;
   if (EC3Grid<N, R>::ctas == 0) {
     cudaError_t e = prepare_ec3<N, R>();
     if (e != cudaSuccess) return e;
   }
-  const int blocks = runs < EC3Grid<N, R>::ctas ? runs : EC3Grid<N, R>::ctas;
+  const int blocks = runs < EC3Grid<N, R>::ctas ? (int)runs : EC3Grid<N, R>::ctas;
   k_euler_ec3<N, R><<<blocks, K::T, K::smem_bytes(), s>>>(a);
   return cudaGetLastError();
 }

@@ -4,16 +4,18 @@
 //
 // Same operator as EulerStage (Sec. 3.1.1, Eq. vol_split with Ranocha's flux of App. A,
 // Eq. surf_int, the Shu-Osher update of App. B), organised for the hot 3D case:
-//   * each CTA walks runs of KRUN consecutive elements along x; the x-face between two
+//   * each CTA walks runs of up to KRUN consecutive elements along x; the x-face between two
 //     consecutive elements of a run is evaluated once -- by the first element as its x+ face
 //     -- and carried in shared memory to the second as its x- face, so a run of KRUN elements
 //     evaluates 5 + 1/KRUN faces per element instead of 6, and every thread holds one node
-//     and one face job (no face-only warp).  The runs are dealt to the CTAs cyclically, so
-//     the elements in flight at any time stay within a band of the mesh and the neighbours'
-//     face traces are served by L2;
-//   * the element's FP64 state and the five neighbour traces it needs are double-buffered
-//     in shared memory with cp.async; U^n is read in the update only, straight from global
-//     memory (one coalesced 8-byte load per variable);
+//     and one face job (no face-only warp);
+//   * the runs are dealt to the CTAs cyclically in the element order, so that the elements
+//     in flight stay within a band of the mesh and most neighbours' face traces are served
+//     by L2;
+//   * the element's FP64 state and the five neighbour traces it needs are copied into shared
+//     memory with cp.async one iteration ahead (two buffers); U^n is read in the update only,
+//     straight from global memory (one coalesced 8-byte load per variable, issued before the
+//     gathers of the partners' pairs and the face terms, which cover its latency);
 //   * per node two 16-byte records of the two-point flux and the FP32 total energy; a face
 //     job rebuilds its own trace from them (momentum as rho v on both sides of the face, so
 //     the two elements of a face still feed identical bits to the single Riemann-flux call
@@ -29,11 +31,11 @@ struct EC3 {
   using G = Geo<3, N>;
   static constexpr int NV = 5, NP = G::NP, N1 = G::N1, NFN = G::NFN;
   static constexpr int NF = 6;
-  static constexpr int KRUN = 8;                 // consecutive elements along x per run
+  static constexpr int KRUN = 16;                // consecutive elements along x per run
   static constexpr int NJ = 5 * NFN;             // standard face jobs: x+, y-, y+, z-, z+
   static constexpr int T = ((cmax(NP, NJ) + 31) / 32) * 32;
   static constexpr int NO = N1 / 2;              // pair offsets per direction (cyclic ownership)
-  // FP64 staging (two buffers): U [NV][NP], traces of faces 1..5 [5][NV][NFN]
+  // FP64 staging, two buffers of: U [NV][NP], traces of faces 1..5 [5][NV][NFN]
   static constexpr int ST_T = NV * NP;
   static constexpr int ST_SIZE = ST_T + 5 * NV * NFN;
   // flux-precision arrays
@@ -49,15 +51,14 @@ struct EC3 {
   static constexpr size_t smem_bytes() {
     return sizeof(double) * 2 * (size_t)ST_SIZE + sizeof(R) * (size_t)R_SIZE + sizeof(int) * 2 * NF;
   }
-  // FP32: the CTAs per SM that the shared memory allows (228 KB per SM, 1 KB reserved per
-  // CTA), the register budget the compiler is held to; FP64 (bound by the FP64 pipe): free
+  // The CTAs per SM that the shared memory allows (228 KB per SM, 1 KB reserved per CTA),
+  // the register budget the compiler is held to; FP64 (bound by the FP64 pipe) at most 3
   static constexpr int MINB =
-      sizeof(R) == 4 ? cmax(1, cmin(8, (int)(233472 / (smem_bytes() + 1024)))) : 1;
+      cmax(1, cmin(sizeof(R) == 4 ? 8 : 3, (int)(233472 / (smem_bytes() + 1024))));
 
   struct Role {
     int nd, pos[3];           // node
     int face, f, ndo, ndn;    // standard face job (face 1..5)
-    int pm[3];                // face axes -> Cartesian momentum index (1..3)
     int ndo_m, ndn_m;         // x- face job (thread < NFN): own node (i = 0), neighbour node (i = N)
   };
 
@@ -81,8 +82,6 @@ struct EC3 {
     if (l == 0) { r.ndn = line_node<0>(r.f, side ? 0 : N); r.ndo = line_node<0>(r.f, side ? N : 0); }
     else if (l == 1) { r.ndn = line_node<1>(r.f, side ? 0 : N); r.ndo = line_node<1>(r.f, side ? N : 0); }
     else { r.ndn = line_node<2>(r.f, side ? 0 : N); r.ndo = line_node<2>(r.f, side ? N : 0); }
-#pragma unroll
-    for (int k = 0; k < 3; ++k) r.pm[k] = 1 + (l + k) % 3;
     const int fm = t < NFN ? t : 0;
     r.ndo_m = line_node<0>(fm, 0);
     r.ndn_m = line_node<0>(fm, N);
@@ -98,12 +97,46 @@ struct EC3 {
     return c[0] + I.nel[0] * (c[1] + I.nel[1] * c[2]);
   }
 
-  // group (element) of iteration it of this CTA: runs of KRUN dealt cyclically
-  static __device__ __forceinline__ int elem_of(int it) {
-    const int q = it / KRUN, m = it - q * KRUN;
-    return (blockIdx.x + q * (int)gridDim.x) * KRUN + m;
+  // Runs: each row of elements along x (rows in element order) splits into nseg =
+  // ceil(nx / KRUN) runs.  Run q starts at element *e0 and holds *len elements; returns false
+  // past the last run.
+  static __device__ __forceinline__ bool run_of(const InstArgs& I, int q, int* e0, int* len) {
+    const int nx = I.nel[0];
+    const int nseg = (nx + KRUN - 1) / KRUN;
+    const int row = q / nseg, seg = q - row * nseg;
+    if (row >= I.nel[1] * I.nel[2]) return false;
+    const int x0 = seg * KRUN;
+    *e0 = x0 + nx * row;
+    *len = min(KRUN, nx - x0);
+    return true;
   }
 
+  // A CTA's walk: runs blockIdx.x, blockIdx.x + gridDim.x, ...; position m within the run.
+  struct Walk {
+    int run, m, e0, len;
+    bool ok;
+    __device__ __forceinline__ int elem() const { return ok ? e0 + m : -1; }
+  };
+  static __device__ __forceinline__ Walk walk_start(const InstArgs& I) {
+    Walk w;
+    w.run = blockIdx.x;
+    w.m = 0;
+    w.ok = run_of(I, w.run, &w.e0, &w.len);
+    return w;
+  }
+  static __device__ __forceinline__ Walk walk_next(const InstArgs& I, Walk w) {
+    if (!w.ok) return w;
+    if (w.m + 1 < w.len) {
+      ++w.m;
+      return w;
+    }
+    w.run += gridDim.x;
+    w.m = 0;
+    w.ok = run_of(I, w.run, &w.e0, &w.len);
+    return w;
+  }
+
+  // start the copies of element e's inputs into staging buffer S
   static __device__ __forceinline__ void issue(const StageArgs& A, const InstArgs& I, const Role& r,
                                                int e, double* S, const int* nb) {
     const int t = threadIdx.x;
@@ -134,12 +167,32 @@ struct EC3 {
     return sm + OFF_X + (L * NO + o - 1) * XSLOT;
   }
 
+  // the NO coefficients of one (direction, position) row of a table, as one vector load when
+  // NO = 2 (the row starts at an even index)
+  static __device__ __forceinline__ void coefs(const R* C, R* c) {
+    if constexpr (NO == 2) {
+      if constexpr (sizeof(R) == 4) {
+        const float2 v = *reinterpret_cast<const float2*>(C);
+        c[0] = v.x;
+        c[1] = v.y;
+      } else {
+        const double2 v = *reinterpret_cast<const double2*>(C);
+        c[0] = v.x;
+        c[1] = v.y;
+      }
+    } else {
+#pragma unroll
+      for (int o = 0; o < NO; ++o) c[o] = C[o];
+    }
+  }
+
   template <int L>
   static __device__ __forceinline__ void own_pairs(R* sm, const Role& r, const Q4<R>& ai, const Q4<R>& bi,
                                                    R igm1, R p_ref, R* acc) {
     constexpr int S = G::stride(L);
     const int nd = r.nd, i = r.pos[L];
-    const R* C = sm + OFF_D + (L * N1 + i) * NO;
+    R c[NO];
+    coefs(sm + OFF_D + (L * N1 + i) * NO, c);
     const Q4<R>* Q = rec(sm);
 #pragma unroll
     for (int o = 1; o <= NO; ++o) {
@@ -148,9 +201,8 @@ struct EC3 {
       const Q4<R> aj = Q[nj], bj = Q[NP + nj];
       R F[NV];
       ec_flux_rec<3, L>(ai, bi, aj, bj, igm1, p_ref, F);
-      const R c = C[o - 1];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) acc[v] -= c * F[v];
+      for (int v = 0; v < NV; ++v) acc[v] -= c[o - 1] * F[v];
       R* X = xslot(sm, L, o);
       reinterpret_cast<Q4<R>*>(X)[nd] = Q4<R>{F[0], F[1], F[2], F[3]};
       X[4 * NP + nd] = F[4];
@@ -161,12 +213,13 @@ struct EC3 {
   static __device__ __forceinline__ void partner_pairs(const R* sm, const Role& r, R* acc) {
     constexpr int S = G::stride(L);
     const int nd = r.nd, i = r.pos[L];
-    const R* C = sm + OFF_D + 3 * N1 * NO + (L * N1 + i) * NO;
+    R cc[NO];
+    coefs(sm + OFF_D + 3 * N1 * NO + (L * N1 + i) * NO, cc);
 #pragma unroll
     for (int o = 1; o <= NO; ++o) {
       if (2 * o == N1 && (i >= o ? i - o : i - o + N1) >= N1 / 2) continue;
       const int nk = (i >= o) ? nd - o * S : nd + (N1 - o) * S;
-      const R c = C[o - 1];
+      const R c = cc[o - 1];
       const R* X = xslot(sm, L, o);
       const Q4<R> f = reinterpret_cast<const Q4<R>*>(X)[nk];
       acc[0] -= c * f.x;
@@ -181,19 +234,19 @@ struct EC3 {
   // F* of face (l, side) at face node f with own node ndo, the neighbour's FP64 trace in n64
   // (Cartesian); lifted by lf and stored to face slot `slot` in Cartesian components.
   static __device__ __forceinline__ void face_flux(R* sm, const StageArgs& A, const InstArgs& I, int e, int l,
-                                                   int side, int ndo, const int* pm, const double* n64,
-                                                   int slot, int f) {
+                                                   int side, int ndo, const double* n64, int slot, int f) {
     const ScalarsT<R>& k = sc<R>(A);
     const R gamma = k.gamma, igm1 = k.igm1, p_ref = k.p_ref;
     const Q4<R>* Q = rec(sm);
-    const R* Bo = reinterpret_cast<const R*>(Q + NP + ndo);  // (v_1, v_2, v_3, pd)
+    const Q4<R> Ao = Q[ndo], Bo = Q[NP + ndo];  // (rho, ...), (v_1, v_2, v_3, pd)
     R own[NV];
     Prim<3, R> po;
-    po.rho = Q[ndo].x;
+    po.rho = Ao.x;
     po.irho = Ar<R>::rcp(po.rho);
-#pragma unroll
-    for (int d = 0; d < 3; ++d) po.v[d] = Bo[pm[d] - 1];
-    po.pd = Bo[3];
+    po.v[0] = l == 0 ? Bo.x : (l == 1 ? Bo.y : Bo.z);
+    po.v[1] = l == 0 ? Bo.y : (l == 1 ? Bo.z : Bo.x);
+    po.v[2] = l == 0 ? Bo.z : (l == 1 ? Bo.x : Bo.y);
+    po.pd = Bo.w;
     po.p = po.pd + p_ref;
     own[0] = po.rho;
     trace_momentum<3>(po, own);
@@ -232,10 +285,11 @@ struct EC3 {
       surface_flux<3, 0>(A.surface, uL, a, uR, b, gamma, igm1, p_ref, Fs);  // the single call site
     }
     const R lf = (side ? R(-1) : R(1)) * sv<R>(I, l) * liftv<R>(I);
-    R* Sq = sm + OFF_SQ + (slot * NFN + f) * 4;
-    Sq[0] = lf * Fs[0];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) Sq[pm[d]] = lf * Fs[1 + d];
+    // back to Cartesian components: face axis k is Cartesian direction (l + k) mod 3
+    const R fx = l == 0 ? Fs[1] : (l == 1 ? Fs[3] : Fs[2]);
+    const R fy = l == 0 ? Fs[2] : (l == 1 ? Fs[1] : Fs[3]);
+    const R fz = l == 0 ? Fs[3] : (l == 1 ? Fs[2] : Fs[1]);
+    reinterpret_cast<Q4<R>*>(sm + OFF_SQ)[slot * NFN + f] = Q4<R>{lf * Fs[0], lf * fx, lf * fy, lf * fz};
     sm[OFF_SE + slot * NFN + f] = lf * Fs[4];
   }
 
@@ -261,6 +315,7 @@ struct EC3 {
   // ---- one element ----
   // xp: slot of this element's x+ face; xm: slot its x- face is read from (sgn: its sign) --
   // the previous element's x+ slot (carry, sgn -1) or slot 0 (computed here, sgn +1)
+  // S: this element's staging buffer (copies complete)
   static __device__ __forceinline__ void compute(const StageArgs& A, const InstArgs& I, R* sm, const Role& r,
                                                  int e, const double* S, bool carry, int xp, bool need_un) {
     const int t = threadIdx.x, nd = r.nd;
@@ -302,15 +357,14 @@ struct EC3 {
 #pragma unroll
       for (int v = 0; v < NV; ++v) n64[v] = tr[v * NFN];
       const int slot = r.face == 1 ? xp : r.face;
-      face_flux(sm, A, I, e, r.face >> 1, r.face & 1, r.ndo, r.pm, n64, slot, r.f);
+      face_flux(sm, A, I, e, r.face >> 1, r.face & 1, r.ndo, n64, slot, r.f);
     }
     if (!carry && t < NFN) {  // the x- face (start of a run or of an x line): its own job
       const double* pt = A.U + I.base + (long long)neighbour(I, e, 0) * NP + r.ndn_m;
       double n64[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) n64[v] = __ldg(pt + v * A.stride);
-      const int pm0[3] = {1, 2, 3};
-      face_flux(sm, A, I, e, 0, 0, r.ndo_m, pm0, n64, 0, t);
+      face_flux(sm, A, I, e, 0, 0, r.ndo_m, n64, 0, t);
     }
     __syncthreads();
     // phase 4: partners' pairs, lifted faces, update
@@ -376,10 +430,10 @@ struct EC3 {
     if (!finite) atomicOr(A.err, 1u);
   }
 
-  // Persistent walk: iteration it handles element elem_of(it); its inputs were copied during
-  // iteration it-1 into buffer it & 1, with its neighbour table in slot it & 1 (filled two
-  // iterations ahead).  The x+ face slot alternates between 1 and 6, so that the next element
-  // of the run reads the carried face while this one's slots are rewritten.
+  // Persistent walk: iteration it handles the walk's it-th element; its inputs were copied
+  // during iteration it-1 into buffer it & 1, with its neighbour table in slot it & 1 (filled
+  // two iterations ahead).  The x+ face slot alternates between 1 and 6, so that the next
+  // element of the run reads the carried face while this one's slots are rewritten.
   static __device__ void run(const StageArgs& A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double* st = reinterpret_cast<double*>(smem_raw);
@@ -389,26 +443,28 @@ struct EC3 {
     const Role r = role();
     load_ops(sm, A.Dv, I);
     const bool need_un = A.need_un != 0;
-    const int ne = I.n_elem;
-    int e = elem_of(0);
-    if (e < ne) fill_nb(I, e, nb);
-    if (elem_of(1) < ne) fill_nb(I, elem_of(1), nb + NF);
+    Walk w = walk_start(I);
+    Walk wn = walk_next(I, w);
+    Walk wnn = walk_next(I, wn);
+    if (w.ok) fill_nb(I, w.elem(), nb);
+    if (wn.ok) fill_nb(I, wn.elem(), nb + NF);
     __syncthreads();
-    if (e < ne) issue(A, I, r, e, st, nb);
+    if (w.ok) issue(A, I, r, w.elem(), st, nb);
     cp_async_commit();
-    for (int it = 0; e < ne; ++it) {
+    for (int it = 0; w.ok; ++it) {
       const int b = it & 1;
-      const int en = elem_of(it + 1), enn = elem_of(it + 2);
       cp_async_wait_all();
-      __syncthreads();
-      if (en < ne) issue(A, I, r, en, st + (b ^ 1) * ST_SIZE, nb + (b ^ 1) * NF);
+      __syncthreads();  // this element's copies are in; every thread has left the previous
+                        // element, so buffer b^1 and neighbour slot b are free
+      if (wn.ok) issue(A, I, r, wn.elem(), st + (b ^ 1) * ST_SIZE, nb + (b ^ 1) * NF);
       cp_async_commit();
-      if (enn < ne) fill_nb(I, enn, nb + b * NF);  // read by the next iteration's issue
-      // the x- face is carried when the previous iteration handled element e - 1 of the same
-      // x line
-      const bool carry = (it % KRUN) != 0 && (e % I.nel[0]) != 0;
-      compute(A, I, sm, r, e, st + b * ST_SIZE, carry, b ? NF : 1, need_un);
-      e = en;
+      if (wnn.ok) fill_nb(I, wnn.elem(), nb + b * NF);  // read by the next iteration's issue
+      // the x- face is carried from the previous iteration, which handled element e - 1 of
+      // the same run
+      compute(A, I, sm, r, w.elem(), st + b * ST_SIZE, w.m != 0, b ? NF : 1, need_un);
+      w = wn;
+      wn = wnn;
+      wnn = walk_next(I, wnn);
     }
   }
 };
