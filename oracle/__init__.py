@@ -194,6 +194,7 @@ def lib():
         _lib.orc_chem_source.argtypes = [pp, dp, dp]
         _lib.orc_mixture.argtypes = [pp, dp, dp, dp, dp]
         _lib.orc_species_limiter.argtypes = [pp, dp]
+        _lib.orc_positivity_floor.argtypes = [pp, dp]
         _lib.orc_relaxation_time.argtypes = [C.POINTER(_Mech), C.c_int, dp, C.c_double, C.c_double, dp]
         ip = C.POINTER(C.c_int)
         _lib.orc_shock_alpha.argtypes = [pp, dp, dp, dp]
@@ -422,6 +423,16 @@ def species_limiter(P: Problem, U: np.ndarray) -> np.ndarray:
     U = np.array(U, dtype=np.float64, order="C").reshape(P.shape)
     c = P._c()
     _check(lib().orc_species_limiter(C.byref(c), _ptr(U)), "species_limiter")
+    return U
+
+
+def positivity_floor(P: Problem, U: np.ndarray) -> np.ndarray:
+    """The Euler positivity floor applied once to U (a copy is returned): rho raised to
+    rho_floor, then E reset so that p = p_floor where p < p_floor (momentum kept).  Pinned by
+    the exact floor values, untouched unfloored nodes and idempotence."""
+    U = np.array(U, dtype=np.float64, order="C").reshape(P.shape)
+    c = P._c()
+    _check(lib().orc_positivity_floor(C.byref(c), _ptr(U)), "positivity_floor")
     return U
 
 

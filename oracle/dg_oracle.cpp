@@ -1742,6 +1742,15 @@ int orc_species_limiter(const OrcProblem* P, double* U) {
   return 0;
 }
 
+// The Euler positivity floor alone, in place (test access).
+int orc_positivity_floor(const OrcProblem* P, double* U) {
+  int rc = check_problem(*P);
+  if (rc) return rc;
+  if (P->equations != ORC_EULER) return -1;
+  positivity_floor(*P, U);
+  return 0;
+}
+
 // Vibrational relaxation time of species s (two-temperature model) for mole fractions X at
 // temperature T (K) and pressure p (Pa).
 int orc_relaxation_time(const OrcMech* m, int s, const double* X, double T, double p, double* tau) {
