@@ -100,6 +100,63 @@ __device__ __forceinline__ bool finite64(double x) {
 }
 
 // ---------------------------------------------------------------------------------------
+// Signal-speed reductions (the Eq. dt_hyp bound) over 64-bit patterns.  A node contributes
+// its speed |u| + a >= 0 as a bit pattern, a quiet NaN if one of its inputs is not finite, or
+// +infinity if it has rho <= 0 or p <= 0.  Non-negative doubles order like their unsigned bit
+// patterns and the quiet NaN lies above +infinity, so one unsigned maximum keeps the worst
+// case of a whole state: non-finite > non-positive > the largest speed (a floating-point
+// maximum would drop the NaN and return a finite bound for a broken state).
+// ---------------------------------------------------------------------------------------
+constexpr unsigned long long kSpeedNonFinite = 0x7ff8000000000000ull;
+constexpr unsigned long long kSpeedNonPositive = 0x7ff0000000000000ull;
+
+__device__ __forceinline__ unsigned long long speed_bits(double sp, bool finite_in, bool positive) {
+  if (!finite_in) return kSpeedNonFinite;
+  if (!positive) return kSpeedNonPositive;
+  return (unsigned long long)__double_as_longlong(sp);
+}
+
+// unsigned maximum over a block (blockDim.x a multiple of 32, at most 1024); the result is
+// valid in thread 0
+__device__ __forceinline__ unsigned long long block_max_u64(unsigned long long x) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long y = __shfl_xor_sync(0xffffffffu, x, o);
+    x = y > x ? y : x;
+  }
+  __shared__ unsigned long long red[32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = x;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    x = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0ull;
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long y = __shfl_xor_sync(0xffffffffu, x, o);
+      x = y > x ? y : x;
+    }
+  }
+  return x;
+}
+
+// the Euler signal speed of one node (FP64), as a reduction code
+template <int DIM>
+__device__ __forceinline__ unsigned long long euler_speed_bits(const double* U, long long stride, long long i,
+                                                               double gamma) {
+  const double rho = U[i];
+  bool fin = isfinite(rho);
+  double m2 = 0.0;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    const double m = U[(1 + d) * stride + i];
+    fin = fin && isfinite(m);
+    m2 += m * m;
+  }
+  const double E = U[(DIM + 1) * stride + i];
+  fin = fin && isfinite(E);
+  const double p = (gamma - 1.0) * (E - 0.5 * m2 / rho);
+  const bool pos = rho > 0.0 && p > 0.0;
+  return speed_bits(pos ? sqrt(m2) / rho + sqrt(gamma * p / rho) : 0.0, fin, pos);
+}
+
+// ---------------------------------------------------------------------------------------
 // Arithmetic traits.  FP32 uses the fast reciprocal/rsqrt unit (a few ulp); FP64 uses
 // Newton-refined reciprocals (within two ulp) and the correctly rounded sqrt.
 // ---------------------------------------------------------------------------------------
@@ -513,7 +570,14 @@ __device__ __forceinline__ void hll(const R* uL, const Prim<DIM, R>& a, const R*
 
 // HLLC (Toro, Spruce and Speares): branches S_L >= 0 -> F_L; S* >= 0 -> F*_L; S_R > 0 ->
 // F*_R; else F_R.  Star state U*_K = rho_K (S_K - u_K)/(S_K - S*) (1, S* e_L + tangential,
-// E_K/rho_K + (S* - u_K)(S* + p_K/(rho_K (S_K - u_K)))).  p_R - p_L is taken as pd_R - pd_L.
+// E_K/rho_K + (S* - u_K)(S* + p_K/(rho_K (S_K - u_K)))); p_R - p_L is taken as pd_R - pd_L.
+// Written in jump form, identical in exact arithmetic: with m_K = rho_K (S_K - u_K),
+//   S* - u_L = (dp - m_R du)/(m_L - m_R),  S* - u_R = (dp - m_L du)/(m_L - m_R),
+// dp = p_R - p_L, du = u_R - u_L, and delta = (S* - u_K)/(S_K - S*),
+//   F*_K = F_K + S_K delta (rho_K, rho_K S_K e_L + rho_K tangential, E_K + p_K + m_K S*).
+// The star correction U*_K - U_K is formed from the jumps instead of as a difference of two
+// full states, which for the small jumps of smooth flow keeps its FP32 rounding down to that
+// of the jumps.
 template <int DIM, int L, class R>
 __device__ __forceinline__ void hllc(const R* uL, const Prim<DIM, R>& a, const R* uR,
                                      const Prim<DIM, R>& b, R gamma, R* F) {
@@ -523,7 +587,10 @@ __device__ __forceinline__ void hllc(const R* uL, const Prim<DIM, R>& a, const R
   point_flux<DIM, L>(uL, a, FL);
   point_flux<DIM, L>(uR, b, FR);
   const R mL = a.rho * (SL - a.v[L]), mR = b.rho * (SR - b.v[L]);
-  const R Ss = Ar<R>::div(b.pd - a.pd + a.v[L] * mL - b.v[L] * mR, mL - mR);
+  const R dp = b.pd - a.pd, du = b.v[L] - a.v[L];
+  const R iden = Ar<R>::rcp(mL - mR);
+  const R dL = (dp - mR * du) * iden;  // S* - u_L
+  const R Ss = a.v[L] + dL;
   if (SL >= R(0)) {
 #pragma unroll
     for (int v = 0; v < DIM + 2; ++v) F[v] = FL[v];
@@ -535,22 +602,23 @@ __device__ __forceinline__ void hllc(const R* uL, const Prim<DIM, R>& a, const R
     // registers)
     const bool left = (Ss >= R(0));
     const R SK = left ? SL : SR;
-    const R mK = left ? mL : mR;  // rho_K (S_K - u_K)
-    const R irK = left ? a.irho : b.irho;
+    const R mK = left ? mL : mR;
+    const R rK = left ? a.rho : b.rho;
     const R pK = left ? a.p : b.p;
-    const R vnK = left ? a.v[L] : b.v[L];
-    const R fac = Ar<R>::div(mK, SK - Ss);
-    R Us[DIM + 2];
-    Us[0] = fac;
-#pragma unroll
-    for (int d = 0; d < DIM; ++d) Us[1 + d] = fac * (d == L ? Ss : (left ? a.v[d] : b.v[d]));
+    const R dK = left ? dL : (dp - mL * du) * iden;  // S* - u_K
+    const R sK = SK - (left ? a.v[L] : b.v[L]);      // S_K - u_K
+    const R sd = SK * Ar<R>::div(dK, sK - dK);       // S_K delta
+    const R rs = rK * sd;
     const R EK = left ? uL[DIM + 1] : uR[DIM + 1];
-    Us[DIM + 1] = fac * (EK * irK + (Ss - vnK) * (Ss + Ar<R>::div(pK, mK)));
 #pragma unroll
     for (int v = 0; v < DIM + 2; ++v) {
-      const R uKv = left ? uL[v] : uR[v];
       const R FKv = left ? FL[v] : FR[v];
-      F[v] = FKv + SK * (Us[v] - uKv);
+      R w;
+      if (v == 0) w = rs;
+      else if (v == DIM + 1) w = sd * (EK + pK + mK * Ss);
+      else if (v == 1 + L) w = rs * SK;
+      else w = rs * (left ? a.v[v - 1] : b.v[v - 1]);
+      F[v] = FKv + w;
     }
   }
 }

@@ -32,6 +32,26 @@ def dg():
     return dgsem
 
 
+def rel_l2_groups(a, b):
+    """Relative L2 error of each conserved group: mass, momentum (one vector), energy."""
+    a = np.asarray(a).reshape(a.shape[0], -1)
+    b = np.asarray(b).reshape(b.shape[0], -1)
+    nv = a.shape[0]
+    return [float(np.linalg.norm(a[g] - b[g]) / np.linalg.norm(b[g]))
+            for g in ([0], list(range(1, nv - 1)), [nv - 1])]
+
+
+# Per-group bars of the FP32-mixed 3D Taylor-Green path at Ma 0.1, about 3x the levels
+# measured on B300 (mass, momentum, energy).  The mass and energy residuals are divergences
+# that nearly cancel (O(Ma^2) flow): the energy flux is ~250 times the mass flux, whose FP32
+# rounding it inherits at that scale, so FP32 flux arithmetic keeps three to four digits of
+# them on 4^3 and fewer on 64^3, where the residual is smaller still; momentum keeps five.
+# A 1% error in any group fails the 4^3 bars.  FP64 keeps about eleven digits of every group.
+TGV_FP32_INCREMENT = (5e-4, 7e-6, 2.5e-4)   # U_T - U_0 after 100 steps on 4^3
+TGV_FP32_RESIDUAL = (1e-3, 1e-5, 2e-3)      # L(U_0) on 4^3
+TGV_FP32_RESIDUAL_64 = (2e-4, 5e-2)         # momentum, energy of L(U_0) on 64^3 (sampled)
+
+
 def rel_l2(a, b):
     """Relative L2 error per conserved quantity -- mass, momentum (the DIM components as one
     vector) and energy -- and the largest of the three.  A momentum component that starts at
@@ -138,6 +158,25 @@ def test_tgv_reduced_100_steps(orc, dg, torch, prec):
     got = S.get_state().cpu().numpy().reshape(ref.shape)
     tol = 1e-12 if prec == 0 else 1e-5
     assert rel_l2(got, ref) <= tol, rel_l2(got, ref)
+    # the increment per conserved group: the state bar alone hardly sees the energy residual
+    # (E ~ 178 changes by ~1e-2 over the run)
+    inc = rel_l2_groups(got - U0, ref - U0)
+    bars = (1e-10,) * 3 if prec == 0 else TGV_FP32_INCREMENT
+    assert all(e <= b for e, b in zip(inc, bars)), inc
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_tgv_reduced_residual_per_group(orc, dg, torch, prec):
+    """The residual of the Taylor-Green state on 4^3, per conserved group."""
+    P, S = setup(orc, dg, torch, 3, 4, 4, 2, 1, prec, lo=(0.0,) * 3, hi=(2 * math.pi,) * 3, p_ref=P_TGV)
+    xi, _ = orc.gll(4)
+    U0 = wl.taylor_green_3d(4, xi, 0.1, GAMMA)
+    ref = orc.rhs(P, U0)
+    got = S.rhs(to_dev(torch, U0)).cpu().numpy().reshape(ref.shape)
+    S.check()
+    err = rel_l2_groups(got, ref)
+    bars = (1e-10,) * 3 if prec == 0 else TGV_FP32_RESIDUAL
+    assert all(e <= b for e, b in zip(err, bars)), err
 
 
 @pytest.mark.parametrize("prec", [0, 1])
@@ -168,8 +207,13 @@ def test_tgv_full_size_sampled_stage(orc, dg, torch, prec):
     # carries the parity bar.
     Lg = S.rhs(Ud).cpu().numpy().reshape(U0.shape)[:, elems, :]
     S.check()
-    err = np.linalg.norm(Lg - L) / np.linalg.norm(L)
-    assert err <= (1e-10 if prec == 0 else 5e-2), err
+    err = rel_l2_groups(Lg, L)
+    # momentum and energy per group; the mass residual of this state vanishes analytically
+    # (rho = 1, div u = 0), so at 64^3 it is rounding noise of both evaluations and its
+    # relative difference carries no information (the 4^3 tests bar it, where the
+    # discretization error keeps it away from zero)
+    bars = (1e-10, 1e-10) if prec == 0 else TGV_FP32_RESIDUAL_64
+    assert all(e <= b for e, b in zip(err[1:], bars)), err
 
 
 @pytest.mark.parametrize("kind", [-1, 0, 1, 2])
