@@ -337,7 +337,9 @@ DG_API dg_status dg_autotune(dg_ctx* ctx, double dt, int n_reps, int* config_out
  * taking the minimum over instances.  Navier-Stokes: a is the frozen mixture sound speed and
  * the result is min(dt_C, dt_D) with the diffusive bound of Eq. dt_para,
  *   dt_D = c * cfl * dx_min^2 / ((2N+1)^2 * max over nodes of max(mu/rho, mu/(rho Pr))).
- * Synchronizes the stream; *dt_out is a host double. */
+ * A state with a non-finite value at any node returns DG_ENONFINITE, one with rho <= 0 or
+ * p <= 0 (T <= 0 for Navier-Stokes) at any node DG_EPOSITIVITY; no bound is taken from the
+ * other nodes.  Synchronizes the stream; *dt_out is a host double. */
 DG_API dg_status dg_max_dt(dg_ctx* ctx, double cfl, double* dt_out);
 
 /* Synchronize the context's stream, then read and clear the device error word:
@@ -361,7 +363,11 @@ DG_API dg_status dg_two_point_flux(dg_ctx* ctx, int kind, int l, int n, const do
  * the caller passes the instance descriptions (as for dg_init_mesh), gamma, a device
  * pointer U to a state in the library's SoA layout (instances concatenated in the order
  * given), cfl, and a cudaStream_t (NULL = legacy default stream).  *dt_out (host) receives
- * min over instances of cfl * dx_min / ((2N+1) * max(|u| + a)).  If msg is not NULL it
+ * min over instances of cfl * dx_min / ((2N+1) * max(|u| + a)): the bound dg_max_dt gives a
+ * Cartesian SSP-RK33 context (SSP coefficient 1; SSP-RK54 callers scale cfl by its
+ * coefficient 1.508 themselves).  Curved instances (coords != NULL) return DG_EUNSUPPORTED:
+ * the bound here uses the box spacing.  A non-finite value at any node returns
+ * DG_ENONFINITE, rho <= 0 or p <= 0 at any node DG_EPOSITIVITY.  If msg is not NULL it
  * receives a static description of any error.
  * It calls no cudaMalloc/cudaFree: the per-instance reduction scratch is a static device
  * array of DG_NOALLOC_MAX_INSTANCES 64-bit slots inside the library, held by every GPU that

@@ -1539,11 +1539,11 @@ dg_status dg_max_dt(dg_ctx* c, double cfl, double* dt_out) {
         e = cudaMemcpyAsync(bits, c->lam, sizeof(bits), cudaMemcpyDeviceToHost, c->stream);
       if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
       if (e != cudaSuccess) return cuda_fail(c, e, "dg_max_dt");
-      double lam, irho;
-      std::memcpy(&lam, &bits[0], sizeof(lam));
-      std::memcpy(&irho, &bits[1], sizeof(irho));
-      if (!(lam > 0.0) || !std::isfinite(lam) || !std::isfinite(irho))
-        return fail(c, DG_ENONFINITE, "no finite signal speed");
+      double lam = 0.0, irho = 0.0;
+      const int k0 = dg::decode_speed(bits[0], &lam), k1 = dg::decode_speed(bits[1], &irho);
+      if (k0 == 1 || k1 == 1) return fail(c, DG_ENONFINITE, "the state holds a non-finite value");
+      if (k0 == 2 || k1 == 2) return fail(c, DG_EPOSITIVITY, "the state has a node with rho <= 0 or T <= 0");
+      if (!(lam > 0.0)) return fail(c, DG_ENONFINITE, "no positive signal speed");
       double dxmin = INFINITY;
       for (int l = 0; l < m.dim; ++l) dxmin = std::fmin(dxmin, (m.hi[l] - m.lo[l]) / m.nel[l]);
       const double n2 = (2.0 * m.N + 1.0) * (2.0 * m.N + 1.0);
@@ -1567,9 +1567,11 @@ dg_status dg_max_dt(dg_ctx* c, double cfl, double* dt_out) {
       e = cudaMemcpyAsync(&bits, c->lam, sizeof(bits), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "dg_max_dt");
-    double lam;
-    std::memcpy(&lam, &bits, sizeof(lam));
-    if (!(lam > 0.0) || !std::isfinite(lam)) return fail(c, DG_ENONFINITE, "no finite signal speed");
+    double lam = 0.0;
+    const int k = dg::decode_speed(bits, &lam);
+    if (k == 1) return fail(c, DG_ENONFINITE, "the state holds a non-finite value");
+    if (k == 2) return fail(c, DG_EPOSITIVITY, "the state has a node with rho <= 0 or p <= 0");
+    if (!(lam > 0.0)) return fail(c, DG_ENONFINITE, "no positive signal speed");
     double dxmin = INFINITY;
     for (int l = 0; l < m.dim; ++l) dxmin = std::fmin(dxmin, (m.hi[l] - m.lo[l]) / m.nel[l]);
     if (!c->curved.empty() && c->curved[i]) dxmin = c->curved_dx[i];  // 2 J / |Ja^l| on curved meshes

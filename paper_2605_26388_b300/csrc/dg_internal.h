@@ -179,8 +179,20 @@ cudaError_t launch_euler_stage(int dim, int N, int ec, int fp32, const StageArgs
 // first launch and outside stream capture.
 cudaError_t prepare_euler_stage(int dim, int N, int ec, int fp32);
 
+// A grid-stride kernel's CTA count cap: 16 CTAs per SM of the current device.
+int grid_cap();
+
+// Decode a signal-speed reduction code (see speed_bits in dg_device.cuh): 0 and *lam the
+// speed; 1 a node with a non-finite value; 2 a node with rho <= 0 or p <= 0.
+inline int decode_speed(unsigned long long bits, double* lam) {
+  if (bits >= 0x7ff8000000000000ull) return 1;
+  if (bits >= 0x7ff0000000000000ull) return 2;
+  __builtin_memcpy(lam, &bits, sizeof(*lam));
+  return 0;
+}
+
 // Largest signal speed |u| + a over the nodes of one instance, atomically max-ed into
-// *lam_bits (the bit pattern of a non-negative double).
+// *lam_bits as a reduction code (speed_bits).
 cudaError_t launch_max_speed(int dim, const double* U, long long stride, long long base,
                              long long n_nodes, double gamma, unsigned long long* lam_bits,
                              cudaStream_t s);

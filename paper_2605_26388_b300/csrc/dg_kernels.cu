@@ -4,6 +4,18 @@
 
 namespace dg {
 
+int grid_cap() {
+  static int cap[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148 * 16;
+  if (!cap[dev]) {
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 148;
+    cap[dev] = 16 * sms;
+  }
+  return cap[dev];
+}
+
 cudaError_t dispatch_stage_2d(int N, int ec, int fp32, const StageArgs* a, cudaStream_t s);
 cudaError_t dispatch_stage_3d(int N, int ec, int fp32, const StageArgs* a, cudaStream_t s);
 cudaError_t dispatch_batched_2d(int group_scale, int ec, int fp32, int ctas_per_sm, const StageArgs* a,
@@ -53,36 +65,20 @@ cudaError_t prepare_euler_stage(int dim, int N, int ec, int fp32) {
 }
 
 // ---------------------------------------------------------------------------------------
-// Largest signal speed |u| + a (Eq. dt_hyp), FP64, block max then one atomicMax on the
-// bit pattern (non-negative doubles order like their unsigned bit patterns).
+// Largest signal speed |u| + a (Eq. dt_hyp), FP64, as a reduction code (speed_bits): block
+// maximum, then one atomicMax on the unsigned pattern.
 // ---------------------------------------------------------------------------------------
 template <int DIM>
 __global__ void k_max_speed(const double* U, long long stride, long long base, long long n,
                             double gamma, unsigned long long* out) {
-  double lam = 0.0;
+  unsigned long long lam = 0ull;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
        q += (long long)gridDim.x * blockDim.x) {
-    const double rho = U[base + q];
-    double m2 = 0.0;
-#pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-      const double m = U[(1 + d) * stride + base + q];
-      m2 += m * m;
-    }
-    const double E = U[(DIM + 1) * stride + base + q];
-    const double p = (gamma - 1.0) * (E - 0.5 * m2 / rho);
-    const double sp = sqrt(m2) / rho + sqrt(gamma * p / rho);
-    lam = fmax(lam, sp);
+    const unsigned long long b = euler_speed_bits<DIM>(U, stride, base + q, gamma);
+    lam = b > lam ? b : lam;
   }
-  for (int o = 16; o > 0; o >>= 1) lam = fmax(lam, __shfl_xor_sync(0xffffffffu, lam, o));
-  __shared__ double red[32];
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = lam;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    lam = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) lam = fmax(lam, __shfl_xor_sync(0xffffffffu, lam, o));
-    if (threadIdx.x == 0) atomicMax(out, (unsigned long long)__double_as_longlong(lam));
-  }
+  lam = block_max_u64(lam);
+  if (threadIdx.x == 0) atomicMax(out, lam);
 }
 
 cudaError_t launch_max_speed(int dim, const double* U, long long stride, long long base,
@@ -90,7 +86,8 @@ cudaError_t launch_max_speed(int dim, const double* U, long long stride, long lo
                              cudaStream_t s) {
   if (n_nodes <= 0) return cudaSuccess;
   long long blocks = (n_nodes + 255) / 256;
-  if (blocks > 148 * 16) blocks = 148 * 16;
+  const int cap = grid_cap();
+  if (blocks > cap) blocks = cap;
   if (dim == 2) k_max_speed<2><<<(int)blocks, 256, 0, s>>>(U, stride, base, n_nodes, gamma, lam_bits);
   else k_max_speed<3><<<(int)blocks, 256, 0, s>>>(U, stride, base, n_nodes, gamma, lam_bits);
   return cudaGetLastError();

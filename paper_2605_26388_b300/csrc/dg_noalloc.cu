@@ -16,6 +16,7 @@
 #include <mutex>
 
 #include "../../include/dgsem.h"
+#include "dg_device.cuh"
 
 static __device__ __align__(256) unsigned long long g_speed_slots[DG_NOALLOC_MAX_INSTANCES];
 
@@ -25,35 +26,20 @@ constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
 unsigned long long* g_slots_addr[kMaxDevices] = {};  // device address, per device
 
-// Largest |u| + a over the nodes of one instance (the Eq. dt_hyp signal speed), reduced
-// per block and merged into *slot with one atomicMax on the bit pattern (non-negative
-// doubles order like their unsigned bit patterns).
+// Largest |u| + a over the nodes of one instance (the Eq. dt_hyp signal speed), as the
+// reduction code of dg_device.cuh (a non-finite node, or one with rho <= 0 or p <= 0, makes
+// the slot report it), reduced per block and merged into *slot with one atomicMax.
 template <int DIM>
 __global__ void k_max_speed_slots(const double* U, long long stride, long long base, long long n,
                                   double gamma, unsigned long long* slot) {
-  double lam = 0.0;
+  unsigned long long lam = 0ull;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
        q += (long long)gridDim.x * blockDim.x) {
-    const double rho = U[base + q];
-    double m2 = 0.0;
-#pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-      const double m = U[(1 + d) * stride + base + q];
-      m2 += m * m;
-    }
-    const double E = U[(DIM + 1) * stride + base + q];
-    const double p = (gamma - 1.0) * (E - 0.5 * m2 / rho);
-    lam = fmax(lam, sqrt(m2) / rho + sqrt(gamma * p / rho));
+    const unsigned long long b = dg::euler_speed_bits<DIM>(U, stride, base + q, gamma);
+    lam = b > lam ? b : lam;
   }
-  for (int o = 16; o > 0; o >>= 1) lam = fmax(lam, __shfl_xor_sync(0xffffffffu, lam, o));
-  __shared__ double red[32];
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = lam;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    lam = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) lam = fmax(lam, __shfl_xor_sync(0xffffffffu, lam, o));
-    if (threadIdx.x == 0) atomicMax(slot, (unsigned long long)__double_as_longlong(lam));
-  }
+  lam = dg::block_max_u64(lam);
+  if (threadIdx.x == 0) atomicMax(slot, lam);
 }
 
 dg_status reject(const char** msg, dg_status st, const char* why) {
@@ -78,6 +64,8 @@ extern "C" dg_status dg_max_dt_noalloc(const dg_mesh_desc* inst, int n_inst, dou
     const dg_mesh_desc& m = inst[i];
     if ((m.dim != 2 && m.dim != 3) || m.dim != inst[0].dim || m.N < 1)
       return reject(msg, DG_EINVAL, "bad dim or N");
+    if (m.coords)  // the bound uses the box spacing; a curved mesh's elements can be smaller
+      return reject(msg, DG_EUNSUPPORTED, "curved meshes (coords != NULL) are not supported here");
     long long ne = 1, np = 1;
     for (int l = 0; l < m.dim; ++l) {
       if (m.nel[l] < 1 || !(m.hi[l] > m.lo[l])) return reject(msg, DG_EINVAL, "bad nel or box");
@@ -89,10 +77,12 @@ extern "C" dg_status dg_max_dt_noalloc(const dg_mesh_desc* inst, int n_inst, dou
 
   // once per device, with that device current: the device address of the scratch array
   // (its name in host code is only a host-side stand-in)
-  int dev = 0;
+  int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return reject(msg, DG_ECUDA, "cudaGetDevice failed");
   if (dev < 0 || dev >= kMaxDevices) return reject(msg, DG_EUNSUPPORTED, "device index too large");
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess || sms < 1) return reject(msg, DG_ECUDA, "cudaDeviceGetAttribute failed");
   unsigned long long* slots;
   {
     std::lock_guard<std::mutex> lock(g_setup_mutex);
@@ -114,7 +104,7 @@ extern "C" dg_status dg_max_dt_noalloc(const dg_mesh_desc* inst, int n_inst, dou
     long long n = 1;
     for (int l = 0; l < m.dim; ++l) n *= (long long)m.nel[l] * (m.N + 1);
     long long blocks = (n + 255) / 256;
-    if (blocks > 148 * 16) blocks = 148 * 16;
+    if (blocks > 16LL * sms) blocks = 16LL * sms;
     if (m.dim == 2) k_max_speed_slots<2><<<(int)blocks, 256, 0, s>>>(U, total, off, n, gamma, slots + i);
     else k_max_speed_slots<3><<<(int)blocks, 256, 0, s>>>(U, total, off, n, gamma, slots + i);
     e = cudaGetLastError();
@@ -129,10 +119,12 @@ extern "C" dg_status dg_max_dt_noalloc(const dg_mesh_desc* inst, int n_inst, dou
 
   double best = INFINITY;
   for (int i = 0; i < n_inst; ++i) {
+    if (bits[i] >= dg::kSpeedNonFinite) return reject(msg, DG_ENONFINITE, "the state holds a non-finite value");
+    if (bits[i] >= dg::kSpeedNonPositive)
+      return reject(msg, DG_EPOSITIVITY, "the state has a node with rho <= 0 or p <= 0");
     double lam;
     std::memcpy(&lam, &bits[i], sizeof(lam));
-    if (!(lam > 0.0) || !std::isfinite(lam))
-      return reject(msg, DG_ENONFINITE, "no finite signal speed");
+    if (!(lam > 0.0)) return reject(msg, DG_ENONFINITE, "no positive signal speed");
     const dg_mesh_desc& m = inst[i];
     double dxmin = INFINITY;
     for (int l = 0; l < m.dim; ++l) dxmin = std::fmin(dxmin, (m.hi[l] - m.lo[l]) / m.nel[l]);

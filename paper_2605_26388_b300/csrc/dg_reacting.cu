@@ -1282,34 +1282,33 @@ __global__ void k_max_speed_mix(const double* U, long long stride, long long bas
   __shared__ double sp[4 * NS];
   load_species<NS>(mech, sp, 4);
   __syncthreads();
-  double lam = 0.0, irho = 0.0;
+  // reduction codes (speed_bits): a node with a non-finite value, or with rho <= 0 or T <= 0,
+  // makes the whole bound report it instead of being dropped
+  unsigned long long lam = 0ull, irho = 0ull;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
        q += (long long)gridDim.x * blockDim.x) {
     double u[NV];
+    bool fin = true;
 #pragma unroll
-    for (int v = 0; v < NV; ++v) u[v] = U[v * stride + base + q];
+    for (int v = 0; v < NV; ++v) {
+      u[v] = U[v * stride + base + q];
+      fin = fin && isfinite(u[v]);
+    }
     if (TT) u[NS + 3] -= u[NV - 1];  // the frozen sound speed needs T only: E - E_v
     const Mx m = mixture<NS, false>(u, sp);
-    lam = fmax(lam, sqrt(m.v[0] * m.v[0] + m.v[1] * m.v[1] + m.v[2] * m.v[2]) + m.a);
-    irho = fmax(irho, 1.0 / m.rho);
+    const bool pos = m.rho > 0.0 && m.T > 0.0;
+    const unsigned long long a = speed_bits(pos ? sqrt(m.v[0] * m.v[0] + m.v[1] * m.v[1] + m.v[2] * m.v[2]) + m.a : 0.0,
+                                            fin, pos);
+    const unsigned long long b = speed_bits(pos ? 1.0 / m.rho : 0.0, fin, pos);
+    lam = a > lam ? a : lam;
+    irho = b > irho ? b : irho;
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    lam = fmax(lam, __shfl_xor_sync(0xffffffffu, lam, o));
-    irho = fmax(irho, __shfl_xor_sync(0xffffffffu, irho, o));
-  }
-  __shared__ double red[2][32];
-  if ((threadIdx.x & 31) == 0) {
-    red[0][threadIdx.x >> 5] = lam;
-    red[1][threadIdx.x >> 5] = irho;
-  }
-  __syncthreads();
+  lam = block_max_u64(lam);
+  __syncthreads();  // the reduction's shared scratch is reused
+  irho = block_max_u64(irho);
   if (threadIdx.x == 0) {
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
-      lam = fmax(lam, red[0][w]);
-      irho = fmax(irho, red[1][w]);
-    }
-    atomicMax(out2, (unsigned long long)__double_as_longlong(lam));
-    atomicMax(out2 + 1, (unsigned long long)__double_as_longlong(irho));
+    atomicMax(out2, lam);
+    atomicMax(out2 + 1, irho);
   }
 }
 
@@ -1378,7 +1377,7 @@ cudaError_t launch_react_prims(int ns, int tt, int fp32, const double* U, long l
                                unsigned* err, cudaStream_t s) {
   if (n_nodes <= 0) return cudaSuccess;
   const long long want = (n_nodes + 255) / 256;
-  const unsigned grid = (unsigned)(want < 148 * 16 ? want : 148 * 16);
+  const unsigned grid = (unsigned)(want < grid_cap() ? want : grid_cap());
 #define DG_RP(S2, T2, R2) k_react_prims<S2, T2, R2><<<grid, 256, 0, s>>>(U, stride, base, n_nodes, mech, p_ref, (R2*)P, T64, err)
   if (tt && ns == 5 && fp32) DG_RP(5, true, float);
   else if (tt && ns == 5) DG_RP(5, true, double);
@@ -1433,7 +1432,7 @@ cudaError_t launch_max_speed_mix(int ns, int tt, const double* U, long long stri
                                  unsigned long long* out2, cudaStream_t s) {
   if (n_nodes <= 0) return cudaSuccess;
   const long long want = (n_nodes + 255) / 256;
-  const unsigned grid = (unsigned)(want < 148 * 16 ? want : 148 * 16);
+  const unsigned grid = (unsigned)(want < grid_cap() ? want : grid_cap());
   if (tt && ns == 5) k_max_speed_mix<5, true><<<grid, 256, 0, s>>>(U, stride, base, n_nodes, mech, out2);
   else if (tt) return cudaErrorInvalidValue;
   else if (ns == 1) k_max_speed_mix<1, false><<<grid, 256, 0, s>>>(U, stride, base, n_nodes, mech, out2);

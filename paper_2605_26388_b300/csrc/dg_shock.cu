@@ -377,7 +377,7 @@ template <int DIM, int N>
 cudaError_t blend_dn(int fp32, const ShockArgs& a, cudaStream_t s) {
   if (a.inst.n_elem <= 0) return cudaSuccess;
   const int want = a.inst.n_elem;
-  const unsigned grid = (unsigned)(want < 148 * 16 ? want : 148 * 16);
+  const unsigned grid = (unsigned)(want < grid_cap() ? want : grid_cap());
   if (fp32) k_fv_blend<DIM, N, float><<<grid, 128, 0, s>>>(a);
   else k_fv_blend<DIM, N, double><<<grid, 128, 0, s>>>(a);
   return cudaGetLastError();
