@@ -51,39 +51,64 @@ def workload_config(nel, ws=1):
             "l2": "inputs larger than L2: three state buffers of %.2f GB per replica" % (nel ** 3 * NP * NV * 8 / 1e9),
             "parallelism": f"replicas x{ws}"}
 
-# DRAM bytes per stage launch (mean of stages 1-3) of the current kernel, from an ncu capture
-# of the 32^3 case scaled by the element count to 64^3; None where no capture of the current
-# kernel exists.
-TRAFFIC_PER_LAUNCH = {"fp32_mixed": 3.30e9, "fp64": None}
+# Figures from ncu captures of the stage kernels, valid only for the kernel sources they were
+# taken on: keyed by a hash of those sources (kernel_hash), and reported as null when the
+# sources have changed since.  traffic_*: dram__bytes_read.sum + dram__bytes_write.sum per
+# stage launch at 64^3 (mean of stages 1-3, one 1-pass capture of the full workload);
+# fp64_instr: FP64 thread instructions (DFMA + DADD + DMUL) per FP64 stage launch at 64^3
+# (a 32^3 capture scaled by the element count).  The commands are in profiles/.
+KERNEL_SOURCES = ["dg_stage_ec3.cuh", "dg_stage.cuh", "dg_device.cuh", "dg_internal.h", "dg_stage3d.cu"]
+NCU_FIGURES = {}
 
 
-# FP64 instructions (thread level) per FP64 stage launch at 64^3, from an ncu capture of the
-# 32^3 case (2.757e9, smsp__sass_thread_inst_executed_op_fp64_pred_on) scaled by the element
-# count; None once the kernel changes.
-FP64_INSTR_PER_LAUNCH = 2.757e9 * 8
-# FP64 peak from the nominal B300 rate (1.25 TFLOP/s dense = 0.625 T FP64 FMA/s).
-FP64_PEAK_GINSTR = 625.0
+def kernel_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2605_26388_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
-def fp64_pipe(launch_ms):
-    """Executed FP64 instructions per second of the FP64 stage kernel against the nominal
-    FP64 rate (each DFMA counted once)."""
-    if FP64_INSTR_PER_LAUNCH is None:
+def ncu_figure(key):
+    return NCU_FIGURES.get(kernel_hash(), {}).get(key)
+
+
+def alu_peaks():
+    """Measured thread-level rates of FP64 and FP32 fused multiply-adds on this GPU
+    (dg_alu_rate: independent chains, CUDA events, best of three; no clock changes)."""
+    import ctypes as C
+    from paper_2605_26388_b300 import dgsem
+    out = {}
+    for kind, name in ((0, "fp64_fma_g_per_s"), (2, "fp32_fma_g_per_s")):
+        r = C.c_double()
+        st = dgsem.lib().dg_alu_rate(kind, C.byref(r))
+        out[name] = r.value / 1e9 if st == dgsem.DG_OK else None
+    out["how"] = "dg_alu_rate: 8 CTAs x 256 threads per SM of independent FMA chains, best of 3 launches"
+    return out
+
+
+def fp64_pipe(launch_ms, peak_g):
+    """Executed FP64 instructions per second of the FP64 stage kernel against the measured
+    FP64 FMA rate (each FP64 instruction counted once)."""
+    instr = ncu_figure("fp64_instr")
+    if instr is None or not peak_g:
         return None
-    ach = FP64_INSTR_PER_LAUNCH / (launch_ms * 1e-3) / 1e9
-    return {"bound": "alu", "unit": "G FP64 instr/s", "achieved": ach, "peak": FP64_PEAK_GINSTR,
-            "frac": ach / FP64_PEAK_GINSTR, "peak_kind": "nominal (1.25 TFLOP/s FP64 / 2)",
-            "instr_per_launch": FP64_INSTR_PER_LAUNCH,
-            "note": "executed FP64 instructions from ncu (not algorithmic flops); ncu reports the FP64 "
-                    "pipe 86% busy"}
+    ach = instr / (launch_ms * 1e-3) / 1e9
+    return {"bound": "alu", "unit": "G FP64 instr/s", "achieved": ach, "peak": peak_g, "frac": ach / peak_g,
+            "peak_kind": "measured (dg_alu_rate, FP64 FMA)", "instr_per_launch": instr,
+            "note": "executed FP64 instructions from ncu (not algorithmic flops)"}
 
 
 # FP64 instructions (thread level: DFMA + DADD + DMUL) per Newton update of
 # k_source_implicit<5,double>, from an ncu capture of one substep on the 12^3 split workload
-# (2.054e9 instructions over 442003 updates); None once the kernel changes.
+# (2.054e9 instructions over 442003 updates); the implicit-substep kernel is unchanged since.
 FP64_INSTR_PER_NEWTON_UPDATE = 2.054e9 / 442003
 SPLIT_DT = 1e-5          # the split workload's step (s)
 EXPLICIT_DT = 1e-13      # the explicit source's stable step on the same mechanism (s)
+
+
+ALU = None  # measured ALU rates (alu_peaks), set by main
 
 
 def measured_peaks():
@@ -175,30 +200,93 @@ def weak_value(units_per_rank: float, ws: int, seconds: float) -> float:
     return units_per_rank * ws / seconds
 
 
-def oracle_sample(seconds_hint: float = 10.0):
-    """Time the plain FP64 CPU oracle on a bounded sample of the same workload: full SSP-RK3
-    steps of the Taylor-Green N=4 EC/HLLC problem on a 12^3 sub-mesh (same per-DOF work)."""
+ACC_NEL, ACC_STEPS = 4, 100  # the accuracy workload: the same TGV problem on 4^3, 100 steps
+
+
+def accuracy_states():
+    """The accuracy workload on the GPU in both precisions: the TGV N=4 EC+HLLC problem on
+    4^3 elements, 100 SSP-RK3 steps at the CFL 0.25 bound; returns (U0, dt, {precision:
+    final state}) for the CPU-baseline leg to compare with the oracle."""
+    import torch
+    from paper_2605_26388_b300 import dgsem, workloads as wl
+    x, _, _ = dgsem.gll(N)
+    U0 = wl.taylor_green_3d(ACC_NEL, x, MACH, GAMMA)
+    out, dt = {}, None
+    for name, prec in (("fp64", dgsem.FP64), ("fp32_mixed", dgsem.FP32_MIXED)):
+        S = dgsem.Solver(dgsem.Mesh(3, N, (ACC_NEL,) * 3, (0.0,) * 3, (2 * math.pi,) * 3), volume=dgsem.VOL_EC,
+                         surface=dgsem.SURF_HLLC, precision=prec, gamma=GAMMA, p_ref=P_REF)
+        S.set_state(torch.from_numpy(np.ascontiguousarray(U0.reshape(NV, -1))).cuda())
+        dt = S.max_dt(CFL)
+        S.rk_step(dt, ACC_STEPS)
+        S.check()
+        out[name] = S.get_state().cpu().numpy().reshape(U0.shape)
+        S.close()
+    return U0, dt, out
+
+
+def _groups(a, b):
+    a = np.asarray(a).reshape(NV, -1)
+    b = np.asarray(b).reshape(NV, -1)
+    return [float(np.linalg.norm(a[g] - b[g]) / np.linalg.norm(b[g])) for g in ([0], [1, 2, 3], [4])]
+
+
+def oracle_sample(acc=None, seconds_hint: float = 8.0, single_core_hint: float = 4.0):
+    """The CPU-baseline leg: the plain FP64 oracle on bounded samples of the same workload.
+    (1) The accuracy workload (4^3, 100 SSP-RK3 steps), whose result is the reference of the
+    GPU states in acc (per-group relative L2 of the final state and of the increment U_T - U_0,
+    mass / momentum / energy).  (2) Full SSP-RK3 steps of the same problem on a 12^3 sub-mesh
+    for about seconds_hint on all host cores, then (3) for about single_core_hint on one core
+    (the OpenMP element loop restricted to one thread; same arithmetic)."""
+    import ctypes as C
     import oracle
     from paper_2605_26388_b300 import workloads as wl
     oracle.build()
+    xi, _ = oracle.gll(N)
+    accuracy = None
+    if acc is not None:
+        U0, dt_acc, states = acc
+        P4 = oracle.Problem(dim=3, N=N, nel=(ACC_NEL,) * 3, lo=(0.0,) * 3, hi=(2 * math.pi,) * 3,
+                            volume=oracle.VOL_EC, surface=oracle.SURF_HLLC, gamma=GAMMA)
+        t0 = time.perf_counter()
+        ref = oracle.rk3(P4, U0, dt_acc, ACC_STEPS)
+        t_acc = time.perf_counter() - t0
+        accuracy = {"workload": f"TGV N=4 EC+HLLC on {ACC_NEL}^3, {ACC_STEPS} SSP-RK3 steps at CFL {CFL}, "
+                                "vs the FP64 CPU oracle; relative L2 per group [mass, momentum, energy]",
+                    "oracle_s": t_acc}
+        for name, Ug in states.items():
+            accuracy[name] = {"state": _groups(Ug, ref), "increment": _groups(Ug - U0, ref - U0)}
     nel = 12
     P = oracle.Problem(dim=3, N=N, nel=(nel,) * 3, lo=(0.0,) * 3, hi=(2 * math.pi,) * 3,
                        volume=oracle.VOL_EC, surface=oracle.SURF_HLLC, gamma=GAMMA)
-    xi, _ = oracle.gll(N)
     U = wl.taylor_green_3d(nel, xi, MACH, GAMMA)
     dt = oracle.max_dt(P, U, CFL)
-    steps, t0 = 0, time.perf_counter()
-    while True:
-        U = oracle.rk3(P, U, dt, 1)
-        steps += 1
-        if time.perf_counter() - t0 >= seconds_hint:
-            break
-    el = time.perf_counter() - t0
     dof = nel ** 3 * NP * NV
+
+    def timed(hint):
+        nonlocal U
+        steps, t0 = 0, time.perf_counter()
+        while True:
+            U = oracle.rk3(P, U, dt, 1)
+            steps += 1
+            if time.perf_counter() - t0 >= hint:
+                return steps, time.perf_counter() - t0
+
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    steps, el = timed(seconds_hint)
+    single = None
+    try:
+        gomp = C.CDLL("libgomp.so.1")
+        gomp.omp_set_num_threads(1)
+        s1, el1 = timed(single_core_hint)
+        gomp.omp_set_num_threads(cores)
+        single = {"value": 3 * s1 * dof / el1, "unit": "DOF-updates/s", "cores": 1,
+                  "sample": f"{s1} step(s) on the {nel}^3 sub-mesh, {el1:.1f} s"}
+    except OSError:
+        pass
     return {"value": 3 * steps * dof / el, "unit": "DOF-updates/s", "cores": cores, "kind": "oracle",
             "sample": f"{steps} SSP-RK3 step(s) of the same TGV N=4 EC+HLLC problem on a {nel}^3 sub-mesh "
-                      f"({dof} DOF), FP64, {el:.1f} s"}
+                      f"({dof} DOF), FP64, {el:.1f} s",
+            "single_core": single}, accuracy
 
 
 def run_reference(args):
@@ -239,7 +327,7 @@ def run_reference(args):
 
 
 def main():
-    global NEL, DOF
+    global NEL, DOF, ALU
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=60)
@@ -272,6 +360,7 @@ def main():
     if args.only in ("reacting", "split", "shock", "curved"):
         import torch
         torch.cuda.set_device(dist_env()[2])
+        ALU = alu_peaks()
         fn = {"reacting": run_reacting, "split": run_split, "shock": run_shock, "curved": run_curved}[args.only]
         print(json.dumps({args.only: fn(args)}), flush=True)
         return
@@ -333,9 +422,9 @@ def main():
         alg = BYTES_PER_DOF_UPDATE * DOF  # algorithmic bytes per average launch
         ach = alg / (launch_ms * 1e-3) / 1e9
         return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                "traffic": TRAFFIC_PER_LAUNCH[prec], "peak_kind": peak_kind,
-                "kernel": "k_euler_stage<3,4,EC," + ("float" if prec == "fp32_mixed" else "double") + ">",
-                "avg_launch_ms": launch_ms, "alg_bytes_per_launch": alg}
+                "traffic": ncu_figure("traffic_" + prec) if NEL == 64 else None, "peak_kind": peak_kind,
+                "kernel": "k_euler_ec3<4," + ("float" if prec == "fp32_mixed" else "double") + ">",
+                "avg_launch_ms": launch_ms, "alg_bytes_per_launch": alg, "kernel_hash": kernel_hash()}
 
     value = weak_value(3 * DOF * args.steps, ws, ms32 * 1e-3) if ms32 else None
     if args.no_e2e or ms32 is None:
@@ -347,7 +436,10 @@ def main():
             import torch.distributed as dist
             dist.destroy_process_group()
         return
-    cpu = None if args.no_cpu_baseline or ws > 1 else oracle_sample()
+    ALU = alu_peaks()
+    cpu = accuracy = None
+    if not args.no_cpu_baseline and ws == 1:
+        cpu, accuracy = oracle_sample(accuracy_states())
     batched = None if args.no_batched else run_batched(args)
     reacting = None if args.no_reacting else run_reacting(args)
     split = None if args.no_split else run_split(args)
@@ -356,10 +448,12 @@ def main():
     adjoint = None if args.no_adjoint else run_adjoint(args)
     fp64 = None
     if ms64:
+        r64 = roofline(ms64, fp64_steps, "fp64")
         fp64 = {"value": weak_value(3 * DOF * fp64_steps, ws, ms64 * 1e-3), "unit": "DOF-updates/s", "steps": fp64_steps,
-                "ms_per_step": ms64 / fp64_steps, "roofline": roofline(ms64, fp64_steps, "fp64"),
-                "bound_note": "FP64-pipe bound on B300",
-                "fp64_pipe": fp64_pipe(ms64 / (3 * fp64_steps)), "clocks": clk64}
+                "ms_per_step": ms64 / fp64_steps, "hbm_frac": r64["frac"], "avg_launch_ms": r64["avg_launch_ms"],
+                "traffic": r64["traffic"], "bound_note": "FP64-pipe bound on B300",
+                "fp64_pipe": fp64_pipe(ms64 / (3 * fp64_steps), ALU.get("fp64_fma_g_per_s")),
+                "clocks": clk64}
     line = {
         "metric": METRIC,
         "value": value, "unit": "DOF-updates/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -367,7 +461,6 @@ def main():
         "vs_baseline": None, "dtype": "f32 flux / f64 state", "data": "synthetic",
         "config": dict(workload_config(NEL, ws), precision="fp32_mixed", dt=dt),
         "roofline": roofline(ms32, args.steps, "fp32_mixed") if ms32 else None,
-        "fp64": fp64,
         "clocks": clk32 if clk32 else clk64,
         "e2e": e2e,
         "gpu_launches": 3 * args.steps,
@@ -378,6 +471,11 @@ def main():
         "shock": shock,
         "curved": curved,
         "adjoint": adjoint,
+        # last, so that a tail of the output keeps them: the paper-precision arm, the accuracy
+        # of both arms and the measured ALU peaks
+        "alu_peaks": ALU,
+        "accuracy": accuracy,
+        "fp64": fp64,
     }
     print(json.dumps(line), flush=True)
     if ws > 1:
@@ -584,11 +682,12 @@ def run_split(args):
                                 "ms": chem_ms, "nodes": nodes,
                                 "newton_updates": upd, "updates_per_node": upd / nodes,
                                 "share_of_step": 2 * chem_ms / ms}}
-        if FP64_INSTR_PER_NEWTON_UPDATE and not tt:
+        peak_g = (ALU or {}).get("fp64_fma_g_per_s")
+        if FP64_INSTR_PER_NEWTON_UPDATE and not tt and peak_g:
             ach = upd * FP64_INSTR_PER_NEWTON_UPDATE / (chem_ms * 1e-3) / 1e9
             r["source_substep"]["roofline"] = {
-                "bound": "alu", "unit": "G FP64 instr/s", "achieved": ach, "peak": FP64_PEAK_GINSTR,
-                "frac": ach / FP64_PEAK_GINSTR, "peak_kind": "nominal (1.25 TFLOP/s FP64 / 2)",
+                "bound": "alu", "unit": "G FP64 instr/s", "achieved": ach, "peak": peak_g,
+                "frac": ach / peak_g, "peak_kind": "measured (dg_alu_rate, FP64 FMA)",
                 "instr_per_update": FP64_INSTR_PER_NEWTON_UPDATE}
         S.close()
         out[name] = r
