@@ -88,7 +88,8 @@ def fp32_bar(orc, P, U, ref):
                for g, F in zip(groups, flux))
 
 
-CASES = [(2, 2, 5), (2, 3, 4), (2, 5, 3), (2, 7, 2), (3, 2, 3), (3, 3, 3), (3, 4, 2), (3, 5, 2)]
+# N = 1 is the edge case of the cyclic pair ownership (only the half-way pair of each line)
+CASES = [(2, 1, 6), (2, 2, 5), (2, 3, 4), (2, 5, 3), (2, 7, 2), (3, 1, 4), (3, 2, 3), (3, 3, 3), (3, 4, 2), (3, 5, 2)]
 
 
 @pytest.mark.parametrize("dim,N,nel", CASES)
