@@ -344,20 +344,30 @@ struct EC3 {
     R acc[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) acc[v] = R(0);
-    if (node) {
+    // a thread with both roles runs them in one block, so that the compiler can interleave
+    // the pair fluxes with the face flux
+    auto pairs = [&]() {
       const Q4<R>* Q = rec(sm);
       const Q4<R> ai = Q[nd], bi = Q[NP + nd];
       own_pairs<0>(sm, r, ai, bi, igm1, p_ref, acc);
       own_pairs<1>(sm, r, ai, bi, igm1, p_ref, acc);
       own_pairs<2>(sm, r, ai, bi, igm1, p_ref, acc);
-    }
-    if (t < NJ) {
+    };
+    auto face = [&]() {
       const double* tr = S + ST_T + (r.face - 1) * NV * NFN + r.f;
       double n64[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) n64[v] = tr[v * NFN];
       const int slot = r.face == 1 ? xp : r.face;
       face_flux(sm, A, I, e, r.face >> 1, r.face & 1, r.ndo, n64, slot, r.f);
+    };
+    constexpr int NB = NP < NJ ? NP : NJ;
+    if (t < NB) {
+      pairs();
+      face();
+    } else {
+      if (node) pairs();
+      if (t < NJ) face();
     }
     if (!carry && t < NFN) {  // the x- face (start of a run or of an x line): its own job
       const double* pt = A.U + I.base + (long long)neighbour(I, e, 0) * NP + r.ndn_m;
@@ -378,13 +388,15 @@ struct EC3 {
     partner_pairs<0>(sm, r, acc);
     partner_pairs<1>(sm, r, acc);
     partner_pairs<2>(sm, r, acc);
+    // lifted face terms: one conditional gather per direction (a node lies on at most one of
+    // the two faces of a direction)
     const int i = r.pos[0], j = r.pos[1], kk = r.pos[2];
-    if (i == 0) gather_slot<0>(sm, carry ? (xp == 1 ? NF : 1) : 0, j + N1 * kk, carry ? R(-1) : R(1), acc);
-    if (i == N) gather_slot<0>(sm, xp, j + N1 * kk, R(1), acc);
-    if (j == 0) gather_slot<1>(sm, 2, i + N1 * kk, R(1), acc);
-    if (j == N) gather_slot<1>(sm, 3, i + N1 * kk, R(1), acc);
-    if (kk == 0) gather_slot<2>(sm, 4, i + N1 * j, R(1), acc);
-    if (kk == N) gather_slot<2>(sm, 5, i + N1 * j, R(1), acc);
+    if (i == 0 || i == N) {
+      const bool lo = i == 0;
+      gather_slot<0>(sm, lo ? (carry ? (xp == 1 ? NF : 1) : 0) : xp, j + N1 * kk, lo && carry ? R(-1) : R(1), acc);
+    }
+    if (j == 0 || j == N) gather_slot<1>(sm, j == 0 ? 2 : 3, i + N1 * kk, R(1), acc);
+    if (kk == 0 || kk == N) gather_slot<2>(sm, kk == 0 ? 4 : 5, i + N1 * j, R(1), acc);
 
     double res[NV];
     if (A.mode == 1 && A.alpha && A.alpha[e] > 0.0) {  // shock-flagged: the DG residual only
