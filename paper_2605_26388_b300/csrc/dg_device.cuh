@@ -79,6 +79,16 @@ __device__ __forceinline__ double f2d_w(float f) {
   return __hiloint2double((int)(hi | (b & 0x80000000u)), (int)(b << 29));
 }
 
+// The same widening for a float known to be finite (the caller checks): normal floats exact,
+// zero a signed zero, subnormals a double of the same sign below 2^-126.  Seven integer
+// operations.
+__device__ __forceinline__ double f2d_fin(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const uint32_t a = b & 0x7fffffffu;
+  const uint32_t hi = a ? (a >> 3) + 0x38000000u : 0u;
+  return __hiloint2double((int)(hi | (b & 0x80000000u)), (int)(b << 29));
+}
+
 // 1/x in FP64 for |x| between 2^-125 and 2^125: an FP32 reciprocal seed (relative error
 // below 2^-21) refined by two Newton-Raphson steps y <- y + y (1 - x y), each of which
 // squares the error, so the result is within an ulp or two of the quotient.  Four FP64
@@ -386,12 +396,16 @@ __device__ __forceinline__ void ec_flux_rec(const Q4<float>& a, const Q4<float>&
   Fs = __fmaf_rn(Fs, u.y, 2.0f / 5.0f);
   Fs = __fmaf_rn(Fs, u.y, 2.0f / 3.0f);
   Fs = __fmaf_rn(Fs, u.y, 2.0f);
-  const float2 dl = sub2(make_float2(a.z, a.w), make_float2(b.z, b.w));
-  float r0, r1;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"(dl.x));
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r1) : "f"(d.y));
-  const float hr = u.x < Ar<float>::kLogMeanSeries ? s.x * G : d.x * r0;     // rho^ln / 2
-  const float ib = u.y < Ar<float>::kLogMeanSeries ? is.y * Fs : dl.y * r1;  // 1 / beta^ln
+  float hr = s.x * G, ib = is.y * Fs;
+  const bool lg = !(u.x < Ar<float>::kLogMeanSeries) || !(u.y < Ar<float>::kLogMeanSeries);
+  if (__any_sync(__activemask(), lg)) {
+    const float2 dl = sub2(make_float2(a.z, a.w), make_float2(b.z, b.w));
+    float r0, r1;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"(dl.x));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r1) : "f"(d.y));
+    hr = u.x < Ar<float>::kLogMeanSeries ? hr : d.x * r0;
+    ib = u.y < Ar<float>::kLogMeanSeries ? ib : dl.y * r1;
+  }
   const float2 vs01 = __fadd2_rn(make_float2(av.x, av.y), make_float2(bv.x, bv.y));
   const float vs2 = av.z + bv.z;
   const float2 pv = __fmul2_rn(make_float2(av.x, av.y), make_float2(bv.x, bv.y));

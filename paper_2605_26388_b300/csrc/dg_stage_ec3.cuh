@@ -303,6 +303,12 @@ struct EC3 {
     acc[4] += sgn * sm[OFF_SE + slot * NFN + f];
   }
 
+  // FP64 value of a flux-precision result that the caller checks for finiteness
+  static __device__ __forceinline__ double wide(R x) {
+    if constexpr (sizeof(R) == 4) return f2d_fin(x);
+    else return x;
+  }
+
   static __device__ __forceinline__ void load_ops(R* sm, const double* Dv, const InstArgs& I) {
     for (int q = threadIdx.x; q < 2 * 3 * N1 * NO; q += blockDim.x) {
       const int part = q / (3 * N1 * NO), rem = q - part * (3 * N1 * NO);
@@ -316,14 +322,12 @@ struct EC3 {
   // xp: slot of this element's x+ face; xm: slot its x- face is read from (sgn: its sign) --
   // the previous element's x+ slot (carry, sgn -1) or slot 0 (computed here, sgn +1)
   // S: this element's staging buffer (copies complete)
-  static __device__ __forceinline__ void compute(const StageArgs& A, const InstArgs& I, R* sm, const Role& r,
-                                                 int e, const double* S, bool carry, int xp, bool need_un) {
-    const int t = threadIdx.x, nd = r.nd;
+  // ---- phase 1 (node threads): convert the staged state S, pressure deviation, records ----
+  static __device__ __forceinline__ void phase1(const StageArgs& A, R* sm, const Role& r, const double* S) {
+    const int nd = r.nd;
     const ScalarsT<R>& k = sc<R>(A);
-    const R igm1 = k.igm1, p_ref = k.p_ref;
-    const bool node = t < NP;
-    // phase 1: convert, primitives, records
-    if (node) {
+    const R p_ref = k.p_ref;
+    {
       double u64[NV];
       R u[NV];
 #pragma unroll
@@ -339,9 +343,15 @@ struct EC3 {
       ec_records<3>(q, Q[nd], Q[NP + nd]);
       sm[OFF_E + nd] = u[4];
     }
-    __syncthreads();
-    // phase 2: own pairs; phase 3: face jobs
-    R acc[NV];
+  }
+
+  // ---- phases 2 and 3: own pairs into acc, face jobs (xp: this element's x+ face slot) ----
+  static __device__ __forceinline__ void phase23(const StageArgs& A, const InstArgs& I, R* sm, const Role& r,
+                                                 int e, const double* S, bool carry, int xp, R* acc) {
+    const int t = threadIdx.x, nd = r.nd;
+    const ScalarsT<R>& k = sc<R>(A);
+    const R igm1 = k.igm1, p_ref = k.p_ref;
+    const bool node = t < NP;
 #pragma unroll
     for (int v = 0; v < NV; ++v) acc[v] = R(0);
     // a thread with both roles runs them in one block, so that the compiler can interleave
@@ -376,9 +386,14 @@ struct EC3 {
       for (int v = 0; v < NV; ++v) n64[v] = __ldg(pt + v * A.stride);
       face_flux(sm, A, I, e, 0, 0, r.ndo_m, n64, 0, t);
     }
-    __syncthreads();
-    // phase 4: partners' pairs, lifted faces, update
-    if (!node) return;
+  }
+
+  // ---- phase 4 (node threads): partners' pairs, lifted faces, update of element e ----
+  static __device__ __forceinline__ void phase4(const StageArgs& A, const InstArgs& I, const R* sm, const Role& r,
+                                                int e, const double* S, bool carry, int xp, bool need_un,
+                                                R* acc) {
+    const int nd = r.nd;
+    const ScalarsT<R>& k = sc<R>(A);
     const long long gi = I.base + (long long)e * NP + nd;
     double un[NV];
     if (need_un) {
@@ -398,6 +413,13 @@ struct EC3 {
     if (j == 0 || j == N) gather_slot<1>(sm, j == 0 ? 2 : 3, i + N1 * kk, R(1), acc);
     if (kk == 0 || kk == N) gather_slot<2>(sm, kk == 0 ? 4 : 5, i + N1 * j, R(1), acc);
 
+    // non-finite results are detected on the FP32 residual (a NaN or infinity anywhere in the
+    // node's fluxes reaches it), so that the widenings below need no special cases
+    bool finite = true;
+    if constexpr (sizeof(R) == 4) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) finite = finite && fabsf(acc[v]) < INFINITY;
+    }
     double res[NV];
     if (A.mode == 1 && A.alpha && A.alpha[e] > 0.0) {  // shock-flagged: the DG residual only
 #pragma unroll
@@ -406,12 +428,12 @@ struct EC3 {
     }
     if (A.mode == 0) {
 #pragma unroll
-      for (int v = 0; v < NV; ++v) res[v] = Ar<R>::widen(acc[v]);
+      for (int v = 0; v < NV; ++v) res[v] = wide(acc[v]);
     } else {
       const R cbdt = k.cbdt;
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        double x = fma(A.cb, S[v * NP + nd], Ar<R>::widen(cbdt * acc[v]));
+        double x = fma(A.cb, S[v * NP + nd], wide(cbdt * acc[v]));
         if (need_un) x = fma(A.ca, un[v], x);
         res[v] = x;
       }
@@ -419,7 +441,7 @@ struct EC3 {
         const R abdt = k.abdt;
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-          double y = fma(A.acc_b, S[v * NP + nd], Ar<R>::widen(abdt * acc[v]));
+          double y = fma(A.acc_b, S[v * NP + nd], wide(abdt * acc[v]));
           if (A.acc_a != 0.0) y = fma(A.acc_a, A.acc[v * A.stride + gi], y);
           A.acc[v * A.stride + gi] = y;
         }
@@ -431,21 +453,26 @@ struct EC3 {
         for (int d = 0; d < 3; ++d) kin += res[1 + d] * res[1 + d] / res[0];
         const double p = (A.gamma - 1.0) * (res[4] - 0.5 * kin);
         if (A.p_floor > 0.0 && p < A.p_floor) res[4] = A.p_floor / (A.gamma - 1.0) + 0.5 * kin;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) finite = finite && finite64(res[v]);
       }
     }
-    bool finite = true;
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      finite = finite && finite64(res[v]);
+      if constexpr (sizeof(R) == 8) finite = finite && finite64(res[v]);
       A.out[v * A.stride + gi] = res[v];
-    }
-    if (!finite) atomicOr(A.err, 1u);
+    }    if (!finite) atomicOr(A.err, 1u);
   }
 
-  // Persistent walk: iteration it handles the walk's it-th element; its inputs were copied
-  // during iteration it-1 into buffer it & 1, with its neighbour table in slot it & 1 (filled
-  // two iterations ahead).  The x+ face slot alternates between 1 and 6, so that the next
-  // element of the run reads the carried face while this one's slots are rewritten.
+  // Persistent walk, two barriers per element.  Iteration it handles element e (the walk's
+  // it-th): with e's inputs in buffer it & 1 and its records already built, it requests the
+  // next element's inputs into the other buffer, runs e's pairs and face jobs, and after a
+  // barrier runs e's update together with the next element's records (the update reads the
+  // pair and face slots and e's buffer, the records phase writes the records from the other
+  // buffer: nothing is shared), then a second barrier.  Each thread reads only the staged
+  // values it copied itself, so its own cp.async wait suffices before the records phase.  The
+  // x+ face slot alternates between 1 and 6, so that the next element of the run reads the
+  // carried face while this one's slots are rewritten.
   static __device__ void run(const StageArgs& A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double* st = reinterpret_cast<double*>(smem_raw);
@@ -453,6 +480,7 @@ struct EC3 {
     int* nb = reinterpret_cast<int*>(sm + R_SIZE);
     const InstArgs& I = A.inst;
     const Role r = role();
+    const bool node = threadIdx.x < NP;
     load_ops(sm, A.Dv, I);
     const bool need_un = A.need_un != 0;
     Walk w = walk_start(I);
@@ -463,17 +491,28 @@ struct EC3 {
     __syncthreads();
     if (w.ok) issue(A, I, r, w.elem(), st, nb);
     cp_async_commit();
+    cp_async_wait_all();
+    if (w.ok && node) phase1(A, sm, r, st);
+    __syncthreads();
     for (int it = 0; w.ok; ++it) {
       const int b = it & 1;
-      cp_async_wait_all();
-      __syncthreads();  // this element's copies are in; every thread has left the previous
-                        // element, so buffer b^1 and neighbour slot b are free
+      // buffer b^1 and neighbour slot b are free: their element's update and copies are done
       if (wn.ok) issue(A, I, r, wn.elem(), st + (b ^ 1) * ST_SIZE, nb + (b ^ 1) * NF);
       cp_async_commit();
       if (wnn.ok) fill_nb(I, wnn.elem(), nb + b * NF);  // read by the next iteration's issue
       // the x- face is carried from the previous iteration, which handled element e - 1 of
       // the same run
-      compute(A, I, sm, r, w.elem(), st + b * ST_SIZE, w.m != 0, b ? NF : 1, need_un);
+      const int e = w.elem(), xp = b ? NF : 1;
+      const bool carry = w.m != 0;
+      R acc[NV];
+      phase23(A, I, sm, r, e, st + b * ST_SIZE, carry, xp, acc);
+      __syncthreads();  // pair and face slots complete; the records are free
+      cp_async_wait_all();  // this thread's copies of the next element
+      if (node) {
+        phase4(A, I, sm, r, e, st + b * ST_SIZE, carry, xp, need_un, acc);
+        if (wn.ok) phase1(A, sm, r, st + (b ^ 1) * ST_SIZE);
+      }
+      __syncthreads();  // the next element's records complete; the slots and buffer b are free
       w = wn;
       wn = wnn;
       wnn = walk_next(I, wnn);
