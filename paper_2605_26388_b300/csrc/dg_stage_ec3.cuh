@@ -347,11 +347,16 @@ struct EC3 {
 
   // ---- phases 2 and 3: own pairs into acc, face jobs (xp: this element's x+ face slot) ----
   static __device__ __forceinline__ void phase23(const StageArgs& A, const InstArgs& I, R* sm, const Role& r,
-                                                 int e, const double* S, bool carry, int xp, R* acc) {
+                                                 int e, const double* S, bool carry, int xp, bool need_un, R* acc) {
     const int t = threadIdx.x, nd = r.nd;
     const ScalarsT<R>& k = sc<R>(A);
     const R igm1 = k.igm1, p_ref = k.p_ref;
     const bool node = t < NP;
+    if (need_un && node) {  // U^n, read by the update, towards L2 while the fluxes are computed
+      const double* pn = A.Un + I.base + (long long)e * NP + nd;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) asm volatile("prefetch.global.L2 [%0];" ::"l"(pn + v * A.stride));
+    }
 #pragma unroll
     for (int v = 0; v < NV; ++v) acc[v] = R(0);
     // a thread with both roles runs them in one block, so that the compiler can interleave
@@ -505,7 +510,7 @@ struct EC3 {
       const int e = w.elem(), xp = b ? NF : 1;
       const bool carry = w.m != 0;
       R acc[NV];
-      phase23(A, I, sm, r, e, st + b * ST_SIZE, carry, xp, acc);
+      phase23(A, I, sm, r, e, st + b * ST_SIZE, carry, xp, need_un, acc);
       __syncthreads();  // pair and face slots complete; the records are free
       cp_async_wait_all();  // this thread's copies of the next element
       if (node) {
