@@ -58,20 +58,33 @@ def workload_config(nel, ws=1):
 # fp64_instr: FP64 thread instructions (DFMA + DADD + DMUL) per FP64 stage launch at 64^3
 # (a 32^3 capture scaled by the element count).  The commands are in profiles/.
 KERNEL_SOURCES = ["dg_stage_ec3.cuh", "dg_stage.cuh", "dg_device.cuh", "dg_internal.h", "dg_stage3d.cu"]
-NCU_FIGURES = {}
+BATCHED_SOURCES = ["dg_batched.cuh", "dg_stage.cuh", "dg_device.cuh", "dg_internal.h", "dg_batched2d.cu"]
+NCU_FIGURES = {
+    "fb6454cdca7c61ba": {"traffic_fp32_mixed": 4.247e9, "traffic_fp64": 3.94e9, "fp64_instr": 1.7034e10},
+    # the batched kernel on the 256-instance workload (BATCHED_SOURCES), group scale 1
+    "19a386cc00d68a49": {"traffic_batched": 1.645e9},
+}
 
 
-def kernel_hash():
+def kernel_hash(sources=None):
+    """Hash of a kernel's code (default: the headline stage kernel): its sources with comments
+    and blank lines removed, so that an edit of a comment does not retire the ncu figures
+    taken of the same code."""
     import hashlib
+    import re
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_2605_26388_b300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    for f in sources or KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2605_26388_b300", "csrc", f)) as fh:
+            text = re.sub(r"/\*.*?\*/", "", fh.read(), flags=re.S)
+        for line in text.splitlines():
+            line = line.split("//", 1)[0].rstrip()
+            if line:
+                h.update(line.encode() + b"\n")
     return h.hexdigest()[:16]
 
 
-def ncu_figure(key):
-    return NCU_FIGURES.get(kernel_hash(), {}).get(key)
+def ncu_figure(key, sources=None):
+    return NCU_FIGURES.get(kernel_hash(sources), {}).get(key)
 
 
 def alu_peaks():
@@ -340,8 +353,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-reacting", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
-    ap.add_argument("--only", default="both", choices=["both", "fp32", "fp64", "reacting", "split", "shock", "curved"],
-                    help="precision(s) to time, or only the reacting workload (profiling runs)")
+    ap.add_argument("--only", default="both", choices=["both", "fp32", "fp64", "reacting", "split", "shock", "curved", "batched", "adjoint"],
+                    help="precision(s) to time, or one secondary workload alone (profiling runs)")
     ap.add_argument("--reacting-nel", type=int, default=48,
                     help="elements per direction of the reacting workload (profiling runs)")
     ap.add_argument("--no-split", action="store_true")
@@ -357,11 +370,12 @@ def main():
     if args.impl == "reference":
         run_reference(args)
         return
-    if args.only in ("reacting", "split", "shock", "curved"):
+    if args.only in ("reacting", "split", "shock", "curved", "batched", "adjoint"):
         import torch
         torch.cuda.set_device(dist_env()[2])
         ALU = alu_peaks()
-        fn = {"reacting": run_reacting, "split": run_split, "shock": run_shock, "curved": run_curved}[args.only]
+        fn = {"reacting": run_reacting, "split": run_split, "shock": run_shock, "curved": run_curved,
+              "batched": run_batched, "adjoint": run_adjoint}[args.only]
         print(json.dumps({args.only: fn(args)}), flush=True)
         return
 
@@ -505,6 +519,7 @@ def run_batched(args):
     steps = max(3, args.steps // 3)
     out = {"workload": "256 x 2D Euler isentropic vortex, nel in [8,96], N in {2..5}, strong + Rusanov, FP32-mixed",
            "instances": len(meshes), "elements": sum(m.n_elem for m in meshes), "dof": dof, "steps": steps}
+    peak, peak_kind = measured_peaks()
 
     def timed(label):
         S.set_state(U)
@@ -518,16 +533,41 @@ def run_batched(args):
         torch.cuda.synchronize()
         S.check()
         ms = e0.elapsed_time(e1) / steps
-        out[label] = {"ms_per_step": ms, "value": 3 * dof / (ms * 1e-3), "unit": "DOF-updates/s"}
+        ach = BYTES_PER_DOF_UPDATE * dof / (ms / 3 * 1e-3) / 1e9  # per stage, all instances
+        out[label] = {"ms_per_step": ms, "value": 3 * dof / (ms * 1e-3), "unit": "DOF-updates/s",
+                      "hbm_frac": ach / peak}
+        return ms, ach
 
     S.set_launch(dgsem.LAUNCH_PER_INSTANCE)
     timed("per_instance")
     S.set_launch(dgsem.LAUNCH_BATCHED, 1, 0, 0)
     timed("batched_default")
+    # group scale 2 for every degree, and per degree (a second launch per stage for the
+    # degrees with scale 2): the low degrees, the high degrees
+    per_degree = {}
+    for label, gsv in (("all_2", 2), ("N2_N3_at_2", dgsem.GROUPS_PER_DEGREE | (1 << 2) | (1 << 3)),
+                       ("N4_N5_at_2", dgsem.GROUPS_PER_DEGREE | (1 << 4) | (1 << 5))):
+        S.set_launch(dgsem.LAUNCH_BATCHED, gsv, 0, 0)
+        ms_g, _ = timed("_tmp")
+        per_degree[label] = {"ms_per_step": ms_g, "value": out.pop("_tmp")["value"]}
+    out["per_degree"] = per_degree
     S.set_state(U)
     cfg, _ = S.autotune(dt, 3)
-    out["autotuned_config"] = {"mode": cfg[0], "group_scale": cfg[1], "ctas_per_sm": cfg[2], "order": cfg[3]}
-    timed("batched_autotuned")
+    gs = cfg[1]
+    if gs & dgsem.GROUPS_PER_DEGREE:  # per-degree choice: degree N uses 2 where bit N is set
+        gs = {str(n): 2 if (gs >> n) & 1 else 1 for n in sorted({m.N for m in meshes})}
+    out["autotuned_config"] = {"mode": cfg[0], "group_scale": gs, "ctas_per_sm": cfg[2], "order": cfg[3]}
+    ms, ach = timed("batched_autotuned")
+    # the stage launch of the configuration the autotuner keeps: the same algorithmic bytes per
+    # DOF-update as the headline stage (stage 1 reads U^n and writes U^1, stages 2-3 read two
+    # states and write one), over the mean of the three stage launches of a step
+    out["roofline"] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                       "peak_kind": peak_kind,
+                       "kernel": "k_euler_stage_batched<2,strong,float>" if cfg[0] == dgsem.LAUNCH_BATCHED
+                       else "k_euler_stage<2,N,strong,float> per instance",
+                       "avg_launch_ms": ms / 3, "alg_bytes_per_launch": BYTES_PER_DOF_UPDATE * dof,
+                       "traffic": ncu_figure("traffic_batched", BATCHED_SOURCES) if cfg[0] == dgsem.LAUNCH_BATCHED
+                       and cfg[1] == 1 else None, "kernel_hash": kernel_hash(BATCHED_SOURCES)}
     S.close()
     return out
 

@@ -313,19 +313,27 @@ DG_API dg_status dg_adjoint_gammabar(dg_ctx* ctx, double* gammabar);
 /* Launch modes for contexts with several instances. */
 enum { DG_LAUNCH_PER_INSTANCE = 0, DG_LAUNCH_BATCHED = 1 };
 
+/* Per-degree group scale for dg_set_launch: DG_GROUPS_PER_DEGREE | mask, bit N of mask
+ * (N = 1..5) giving degree N work items of twice the base group (2D only). */
+#define DG_GROUPS_PER_DEGREE 0x100
+
 /* How a stage is launched over the context's instances (batched form; the paper runs
  * one problem at a time): one fused launch per instance, or one persistent launch per stage
  * over a work list of (instance, element group) items covering every instance -- the default
- * when n_inst > 1.  group_scale (1, or 2 in 2D) multiplies the elements per work item;
- * ctas_per_sm caps the persistent grid (0 = as many CTAs as fit); order 0 puts the heaviest
- * items (degree, then instance) first, 1 keeps instance order.  Synchronizes the stream and
- * rebuilds the work list; DG_EINVAL on an out-of-range choice.  The batched mode (and the
- * autotuner below) exists for the Euler equations; Navier-Stokes contexts return
- * DG_EUNSUPPORTED for it. */
+ * when n_inst > 1.  group_scale multiplies the elements per work item: 1 (or 2 in 2D) for
+ * every degree, or, in 2D, DG_GROUPS_PER_DEGREE | mask for a choice per degree (the degrees
+ * with scale 1 and those with scale 2 then run as two persistent launches per stage, one
+ * after the other on the context's stream); ctas_per_sm caps the persistent grid (0 = as many
+ * CTAs as fit); order 0 puts the heaviest items (degree, then instance) first, 1 keeps
+ * instance order.  Synchronizes the stream and rebuilds the work list; DG_EINVAL on an
+ * out-of-range choice.  The batched mode (and the autotuner below) exists for the Euler
+ * equations; Navier-Stokes contexts return DG_EUNSUPPORTED for it. */
 DG_API dg_status dg_set_launch(dg_ctx* ctx, int mode, int group_scale, int ctas_per_sm, int order);
 
 /* Autotuner for the launch configuration: times n_reps SSP-RK3 steps of size dt for the
- * per-instance mode and every batched choice (group_scale x ctas_per_sm in {0,1,2} x order),
+ * per-instance mode and every uniform batched choice (group_scale x ctas_per_sm in {0,1,2} x
+ * order), then, in 2D with several degrees, every per-degree group scale (each subset of the
+ * degrees present taking scale 2) with the best uniform choice's ctas_per_sm and order;
  * restores the context-held state afterwards, keeps the fastest configuration and reports it:
  * config_out[4] = {mode, group_scale, ctas_per_sm, order}, *ms_out (host, may be NULL) = its
  * time per step in ms.  Allocates one temporary state copy; synchronizes the stream. */

@@ -39,6 +39,7 @@ struct dg_ctx {
   int2* d_items = nullptr;
   size_t items_cap = 0;
   int n_items = 0;
+  int n_items_g1 = 0;  // items of the degrees launched with group scale 1 (the list's head)
   double* d_dv = nullptr;
   // adjoint workspace (allocated on the first adjoint call): recomputed stage states W1, W2,
   // co-state temporaries T1..T3, per-CTA gamma partials and their device accumulator
@@ -744,12 +745,21 @@ dg_status run_stage(dg_ctx* c, const double* U, const double* Un, double* out, i
     return DG_OK;
   }
   if (c->batched) {
+    // one persistent launch per group-scale class: the degrees with group scale 1 (the head
+    // of the work list), then those with group scale 2 (per-degree choice, 2D)
     a.insts = c->d_insts;
-    a.items = c->d_items;
-    a.n_items = c->n_items;
     a.dv_table = c->d_dv;
-    cudaError_t e = dg::launch_euler_stage_batched(c->dim, ec, fp32, c->bcfg.group_scale,
-                                                   c->bcfg.ctas_per_sm, a, s);
+    cudaError_t e = cudaSuccess;
+    if (c->n_items_g1 > 0) {
+      a.items = c->d_items;
+      a.n_items = c->n_items_g1;
+      e = dg::launch_euler_stage_batched(c->dim, ec, fp32, 1, c->bcfg.ctas_per_sm, a, s);
+    }
+    if (e == cudaSuccess && c->n_items > c->n_items_g1) {
+      a.items = c->d_items + c->n_items_g1;
+      a.n_items = c->n_items - c->n_items_g1;
+      e = dg::launch_euler_stage_batched(c->dim, ec, fp32, 2, c->bcfg.ctas_per_sm, a, s);
+    }
     return e == cudaSuccess ? DG_OK : cuda_fail(c, e, "batched stage launch");
   }
   for (size_t i = 0; i < c->inst.size(); ++i) {
@@ -776,16 +786,21 @@ dg_status build_batch(dg_ctx* c) {
   std::vector<dg::InstArgs> insts(n);
   for (int i = 0; i < n; ++i) inst_args(c, i, insts[i]);
   struct Item { int inst, group; long long cost; };
-  std::vector<Item> items;
+  std::vector<Item> items, items2;  // group scale 1, group scale 2
   for (int i = 0; i < n; ++i) {
-    const int gsz = dg::batched_group(c->dim, c->inst[i].N, c->bcfg.group_scale);
+    const int gs = dg::group_scale_of(c->bcfg, c->inst[i].N);
+    const int gsz = dg::batched_group(c->dim, c->inst[i].N, gs);
     const int ng = (insts[i].n_elem + gsz - 1) / gsz;
     const long long cost = (long long)gsz * n_p_of(c->inst[i]) * (c->inst[i].N + 1);
-    for (int g = 0; g < ng; ++g) items.push_back({i, g, cost});
+    for (int g = 0; g < ng; ++g) (gs == 2 ? items2 : items).push_back({i, g, cost});
   }
-  if (c->bcfg.order == 0)
-    std::stable_sort(items.begin(), items.end(),
-                     [](const Item& x, const Item& y) { return x.cost > y.cost; });
+  if (c->bcfg.order == 0) {
+    auto heavier = [](const Item& x, const Item& y) { return x.cost > y.cost; };
+    std::stable_sort(items.begin(), items.end(), heavier);
+    std::stable_sort(items2.begin(), items2.end(), heavier);
+  }
+  c->n_items_g1 = (int)items.size();
+  items.insert(items.end(), items2.begin(), items2.end());
   std::vector<int2> host(items.size());
   for (size_t k = 0; k < items.size(); ++k) host[k] = make_int2(items[k].inst, items[k].group);
   const size_t cap = items.size();
@@ -808,8 +823,9 @@ dg_status build_batch(dg_ctx* c) {
   if (e == cudaSuccess) e = cudaMemcpy(c->d_items, host.data(), sizeof(int2) * cap, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(c, e, "batch upload");
   c->n_items = (int)cap;
-  e = dg::prepare_euler_stage_batched(c->dim, c->phys.volume == DG_VOL_EC,
-                                      c->phys.precision == DG_FP32_MIXED, c->bcfg.group_scale);
+  const int ec = c->phys.volume == DG_VOL_EC, fp32 = c->phys.precision == DG_FP32_MIXED;
+  if (c->n_items_g1 > 0) e = dg::prepare_euler_stage_batched(c->dim, ec, fp32, 1);
+  if (e == cudaSuccess && c->n_items > c->n_items_g1) e = dg::prepare_euler_stage_batched(c->dim, ec, fp32, 2);
   if (e != cudaSuccess) return cuda_fail(c, e, "batched kernel set-up");
   return DG_OK;
 }
@@ -1455,8 +1471,10 @@ dg_status dg_set_launch(dg_ctx* c, int mode, int group_scale, int ctas_per_sm, i
     return fail(c, DG_EUNSUPPORTED, "shock-captured stages are launched per instance");
   if (c->met && mode == DG_LAUNCH_BATCHED)
     return fail(c, DG_EUNSUPPORTED, "curved instances are launched per instance");
-  if (group_scale != 1 && !(group_scale == 2 && c->dim == 2))
-    return fail(c, DG_EINVAL, "group_scale must be 1 (or 2 in 2D)");
+  const bool per_degree = (group_scale & DG_GROUPS_PER_DEGREE) != 0;
+  if (per_degree ? (c->dim != 2 || (group_scale & ~(DG_GROUPS_PER_DEGREE | 0x3e)) != 0)
+                 : (group_scale != 1 && !(group_scale == 2 && c->dim == 2)))
+    return fail(c, DG_EINVAL, "group_scale must be 1 (or, in 2D, 2 or DG_GROUPS_PER_DEGREE | mask of degrees 1..5)");
   if (ctas_per_sm < 0 || (order != 0 && order != 1))
     return fail(c, DG_EINVAL, "ctas_per_sm must be >= 0 and order 0 or 1");
   if (mode == DG_LAUNCH_BATCHED)
@@ -1488,11 +1506,20 @@ dg_status dg_autotune(dg_ctx* c, double dt, int n_reps, int* config_out, double*
   for (int gs = 1; gs <= (c->dim == 2 ? 2 : 1); ++gs)
     for (int cps : {0, 1, 2})
       for (int order = 0; order <= 1; ++order) cands.push_back({DG_LAUNCH_BATCHED, gs, cps, order});
+  const size_t n_uniform = cands.size();
+  // degrees present (2D): each proper non-empty subset taking group scale 2 is a candidate of
+  // the second round, with the ctas_per_sm and order of the best uniform choice
+  int present = 0;
+  for (const dg_mesh_desc& m : c->inst) present |= 1 << m.N;
+  std::vector<int> subsets;
+  if (c->dim == 2)
+    for (int m = present; m > 0; m = (m - 1) & present)
+      if (m != present) subsets.push_back(m);
   double best = INFINITY;
   Cand bestc = cands[0];
   dg_status st = DG_OK;
   for (size_t k = 0; k < cands.size() && e == cudaSuccess && st == DG_OK; ++k) {
-    const Cand& q = cands[k];
+    const Cand q = cands[k];  // (a copy: the list grows below)
     if ((st = dg_set_launch(c, q.mode, q.gs, q.cps, q.order)) != DG_OK) break;
     if ((st = one_step(c, dt, c->stream)) != DG_OK) break;  // warm-up
     if ((e = cudaEventRecord(e0, c->stream)) != cudaSuccess) break;
@@ -1503,6 +1530,12 @@ dg_status dg_autotune(dg_ctx* c, double dt, int n_reps, int* config_out, double*
     float ms = 0.f;
     if ((e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) break;
     if (ms / n_reps < best) { best = ms / n_reps; bestc = q; }
+    if (k + 1 == n_uniform) {
+      // per-degree group scales, with the best uniform batched choice's grid and order
+      Cand base = bestc;
+      if (base.mode != DG_LAUNCH_BATCHED) base = cands[1];
+      for (int m : subsets) cands.push_back({DG_LAUNCH_BATCHED, DG_GROUPS_PER_DEGREE | m, base.cps, base.order});
+    }
   }
   // restore the state and keep the fastest configuration
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->buf[c->cur], save, bytes, cudaMemcpyDeviceToDevice, c->stream);

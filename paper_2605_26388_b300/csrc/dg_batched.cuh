@@ -6,44 +6,61 @@
 
 namespace dg {
 
-// staging buffers of the batched kernel (2: one item prefetched; 3: two)
-#ifndef DG_BATCHED_PIPE
-#define DG_BATCHED_PIPE 2
-#endif
-constexpr int kBatchedPipe = DG_BATCHED_PIPE;
-
-
 // ---------------------------------------------------------------------------------------
 // Batched persistent launch: one launch per RK stage for many instances of one dimension
 // and uneven size and degree (1..5).  The host builds a list of work items (instance, element
 // group), heaviest first; each CTA walks a strided slice of it, dispatching on the item's
-// degree, and prefetches the next item's inputs (whatever its degree) while computing the
-// current one.  Shared memory and threads are sized for the largest degree.
+// degree.  Shared memory and threads are sized for the largest degree.
+//
+// Nothing an item needs is read from global memory on the critical path: the instance
+// arguments of the item three ahead are copied with cp.async into a ring of shared-memory
+// slots (its index was loaded into a register one iteration earlier still), the volume
+// operators of all degrees are held in shared memory for the whole launch, and the next
+// item's neighbour table and coefficient tables are built from those copies before the one
+// barrier per item that also publishes the current item's staged inputs.
 // ---------------------------------------------------------------------------------------
 template <int DIM, bool EC, class R, int GS, int N = 1>
 struct BMax {
   using K = EulerStage<DIM, N, EC, R, GS>;
   using Nx = BMax<DIM, EC, R, GS, N + 1>;
   static constexpr int st = cmax(K::ST_SIZE, Nx::st);
-  static constexpr int r = cmax(K::R_SIZE, Nx::r);
+  static constexpr int r = cmax(K::OFF_D, Nx::r);  // R area without the coefficient tables
+  static constexpr int nd = cmax(K::ND, Nx::nd);
   static constexpr int nb = cmax(K::EPB * K::NF, Nx::nb);
   static constexpr int t = cmax(K::T, Nx::t);
 };
 // the batched kernel covers degrees 1..5 in both dimensions
 template <int DIM, bool EC, class R, int GS>
 struct BMax<DIM, EC, R, GS, 6> {
-  static constexpr int st = 0, r = 0, nb = 0, t = 0;
+  static constexpr int st = 0, r = 0, nd = 0, nb = 0, t = 0;
 };
 
-// PIPE staging buffers: the inputs of the next PIPE-1 items are in flight while one computes.
 template <int DIM, bool EC, class R, int GS>
 struct Batched {
   using M = BMax<DIM, EC, R, GS>;
-  static constexpr int MST = M::st, MR = M::r, MNB = M::nb, BT = M::t;
-  static constexpr int PIPE = kBatchedPipe;
-  static constexpr size_t smem_bytes() {
-    return sizeof(double) * PIPE * (size_t)MST + sizeof(R) * (size_t)MR + sizeof(int) * (PIPE * MNB + 4);
-  }
+  static constexpr int MST = M::st, BT = M::t;
+  static constexpr int MR = al4(M::r);                  // R area (16-byte multiple)
+  static constexpr int MD = al4(M::nd);                 // one coefficient-table slot
+  static constexpr int MNB = M::nb;
+  static constexpr int NDV = (kMaxN + 1) * (kMaxN + 1);  // one volume operator (device table)
+  // the operators of degrees 1..kMaxN packed: degree N at dv_off(N) = sum_{m=1}^{N-1} (m+1)^2,
+  // (N+1)^2 values
+  static __host__ __device__ constexpr int dv_off(int N) { return N * (N + 1) * (2 * N + 1) / 6 - 1; }
+  static constexpr int DVS = dv_off(kMaxN + 1);
+  static_assert(dv_off(1) == 0 && dv_off(2) == 4 && dv_off(kMaxN) + (kMaxN + 1) * (kMaxN + 1) == DVS,
+                "packed operator offsets");
+  static constexpr int RING = 4;                         // instance-argument slots (items it..it+3)
+  static constexpr int ORING = 3;                        // coefficient-table slots (items it, it+1)
+  static_assert(sizeof(InstArgs) % 16 == 0, "InstArgs is copied in 16-byte pieces");
+  static constexpr int IA16 = (int)(sizeof(InstArgs) / 16);
+  // layout: staging [2][MST] double | volume operators (packed) [DVS] double | instance
+  // arguments [RING] | R area [MR] | coefficient tables [ORING][MD] | neighbours [2][MNB] int
+  static constexpr size_t OFF_DV = sizeof(double) * 2 * (size_t)MST;
+  static constexpr size_t OFF_IA = OFF_DV + sizeof(double) * (size_t)((DVS + 1) & ~1);
+  static constexpr size_t OFF_R = OFF_IA + sizeof(InstArgs) * RING;
+  static constexpr size_t OFF_OPS = OFF_R + sizeof(R) * (size_t)MR;
+  static constexpr size_t OFF_NB = OFF_OPS + sizeof(R) * (size_t)ORING * MD;
+  static constexpr size_t smem_bytes() { return OFF_NB + sizeof(int) * 2 * (size_t)MNB; }
 };
 
 template <int P>
@@ -61,59 +78,94 @@ __device__ __forceinline__ void cp_async_wait_keep() {  // all but the newest P 
     default: break;                                                           \
   }
 
+// copy the instance arguments of item `item` into slot ia (threads 0..IA16-1, 16 bytes each)
+template <class B>
+__device__ __forceinline__ void copy_inst(const StageArgs& A, int2 item, InstArgs* ia) {
+  const int t = threadIdx.x;
+  if (t < B::IA16) {
+    const char* src = reinterpret_cast<const char*>(A.insts + item.x) + 16 * t;
+    char* dst = reinterpret_cast<char*>(ia) + 16 * t;
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+  }
+}
+
 template <int DIM, bool EC, class R, int GS>
 __global__ void __launch_bounds__(Batched<DIM, EC, R, GS>::BT, (Batched<DIM, EC, R, GS>::BT <= 128 ? (sizeof(R) == 4 ? 6 : 4) : 2))
     k_euler_stage_batched(const StageArgs A) {
   using B = Batched<DIM, EC, R, GS>;
-  constexpr int P = B::PIPE;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* st = reinterpret_cast<double*>(smem_raw);
-  R* sm = reinterpret_cast<R*>(st + P * B::MST);
-  int* nb = reinterpret_cast<int*>(sm + B::MR);
+  double* sdv = reinterpret_cast<double*>(smem_raw + B::OFF_DV);
+  InstArgs* sia = reinterpret_cast<InstArgs*>(smem_raw + B::OFF_IA);
+  R* sm = reinterpret_cast<R*>(smem_raw + B::OFF_R);
+  R* sops = reinterpret_cast<R*>(smem_raw + B::OFF_OPS);
+  int* nb = reinterpret_cast<int*>(smem_raw + B::OFF_NB);
+  __shared__ int2 sitem[B::RING];  // the item of each slot
   const bool need_un = A.need_un != 0;
-  const int k0 = blockIdx.x, step = gridDim.x;
-  // prologue: neighbour tables and copies of the first P-1 items (slot/buffer j for item j)
-  for (int j = 0; j < P - 1; ++j) {
+  const int k0 = blockIdx.x, step = gridDim.x, n = A.n_items;
+  const int t = threadIdx.x;
+  if (k0 >= n) return;
+  // volume operators of all degrees, for the whole launch
+  for (int N = 1; N <= kMaxN; ++N)
+    for (int q = t; q < (N + 1) * (N + 1); q += blockDim.x) sdv[B::dv_off(N) + q] = A.dv_table[N * B::NDV + q];
+  // instance arguments of items 0..2 of this CTA's slice (slot j for item j)
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
     const int kj = k0 + j * step;
-    if (kj < A.n_items) {
+    if (kj < n) {
       const int2 item = A.items[kj];
-      const InstArgs& I = A.insts[item.x];
-      DG_ON_DEGREE(I.N, K::fill_nb(I, item.y, nb + j * B::MNB));
+      copy_inst<B>(A, item, sia + j);
+      if (t == 0) sitem[j] = item;
     }
+  }
+  cp_async_commit();
+  // index of item 3 (its arguments are copied in iteration 0)
+  int2 ahead = make_int2(0, 0);
+  if (k0 + 3 * step < n) ahead = A.items[k0 + 3 * step];
+  cp_async_wait_all();
+  __syncthreads();
+  {
+    const InstArgs& I = sia[0];
+    DG_ON_DEGREE(I.N, K::fill_nb(I, sitem[0].y, nb); K::load_ops(sops, sdv + B::dv_off(I.N), I));
   }
   __syncthreads();
-  for (int j = 0; j < P - 1; ++j) {
-    const int kj = k0 + j * step;
-    if (kj < A.n_items) {
-      const int2 item = A.items[kj];
-      const InstArgs& I = A.insts[item.x];
-      DG_ON_DEGREE(I.N, K::issue(A, I, K::role(), item.y, st + j * B::MST, nb + j * B::MNB, need_un));
-    }
-    cp_async_commit();
+  {
+    const InstArgs& I = sia[0];
+    DG_ON_DEGREE(I.N, K::issue(A, I, K::role(), sitem[0].y, st, nb, need_un));
   }
+  cp_async_commit();
   int it = 0;
-  for (int k = k0; k < A.n_items; k += step, ++it) {
-    const int b = it % P;
-    const int bf = (it + P - 1) % P;  // buffer of the item fetched now (last read by item it-1)
-    const int kf = k + (P - 1) * step;
-    if (kf < A.n_items) {
-      const int2 item = A.items[kf];
-      const InstArgs& I = A.insts[item.x];
-      DG_ON_DEGREE(I.N, K::fill_nb(I, item.y, nb + bf * B::MNB));
+  for (int k = k0; k < n; k += step, ++it) {
+    const int b = it & 1, s0 = it % B::RING, s1 = (it + 1) % B::RING, s3 = (it + 3) % B::RING;
+    const int o0 = it % B::ORING, o1 = (it + 1) % B::ORING;
+    const int kf = k + step;
+    // item it+1: neighbour and coefficient tables from its copied arguments (visible since
+    // the previous iteration's barrier)
+    if (kf < n) {
+      const InstArgs& I = sia[s1];
+      DG_ON_DEGREE(I.N, K::fill_nb(I, sitem[s1].y, nb + (b ^ 1) * B::MNB);
+                   K::load_ops(sops + o1 * B::MD, sdv + B::dv_off(I.N), I));
     }
-    __syncthreads();  // neighbour table ready; the previous item no longer reads buffer bf
-    if (kf < A.n_items) {
-      const int2 item = A.items[kf];
-      const InstArgs& I = A.insts[item.x];
-      DG_ON_DEGREE(I.N, K::issue(A, I, K::role(), item.y, st + bf * B::MST, nb + bf * B::MNB, need_un));
+    cp_async_wait_all();
+    __syncthreads();  // item it's inputs, item it+1's tables and item it+2's arguments are
+                      // visible; every thread has left item it-1 (its buffer, tables and
+                      // argument slot are free)
+    if (kf < n) {
+      const InstArgs& I = sia[s1];
+      DG_ON_DEGREE(I.N, K::issue(A, I, K::role(), sitem[s1].y, st + (b ^ 1) * B::MST,
+                                 nb + (b ^ 1) * B::MNB, need_un));
+    }
+    const int k3 = k + 3 * step;
+    if (k3 < n) {
+      copy_inst<B>(A, ahead, sia + s3);
+      if (t == 0) sitem[s3] = ahead;
     }
     cp_async_commit();
-    cp_async_wait_keep<P - 1>();
-    const int2 item = A.items[k];
-    const InstArgs& I = A.insts[item.x];
-    DG_ON_DEGREE(I.N, K::load_ops(sm, A.dv_table + I.N * (kMaxN + 1) * (kMaxN + 1), I));
-    __syncthreads();  // item k's copies and operators are visible
-    DG_ON_DEGREE(I.N, K::compute(A, I, sm, K::role(), item.y, st + b * B::MST, need_un));
+    if (k3 + step < n) ahead = A.items[k3 + step];  // used one iteration later
+    const InstArgs& I = sia[s0];
+    DG_ON_DEGREE(I.N, K::compute(A, I, sm, sops + o0 * B::MD, K::role(), sitem[s0].y, st + b * B::MST,
+                                 need_un));
   }
 }
 #undef DG_ON_DEGREE

@@ -5,6 +5,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "../../include/dgsem.h"
+
 namespace dg {
 
 constexpr int kMaxN = 7;         // largest polynomial degree with compiled kernels (2D); 3D: 5
@@ -166,10 +168,17 @@ int vjp_blocks(int dim, int N, long long n_elem);
 
 // Batched-launch tuning choices (picked by the autotuner).
 struct BatchConfig {
-  int group_scale;     // elements per work item = group_scale x the kernel's base group
+  int group_scale;     // elements per work item = group scale x the kernel's base group: 1 or 2
+                       // for every degree, or DG_GROUPS_PER_DEGREE | mask (bit N: degree N
+                       // uses 2)
   int ctas_per_sm;     // 0 = as many as fit
   int order;           // 0 = heaviest items first, 1 = instance order
 };
+// The group scale of degree N under configuration b.
+inline int group_scale_of(const BatchConfig& b, int N) {
+  if (b.group_scale & DG_GROUPS_PER_DEGREE) return ((b.group_scale >> N) & 1) ? 2 : 1;
+  return b.group_scale;
+}
 
 // Launch the fused Euler stage kernel for one instance.  Returns a CUDA error code.
 cudaError_t launch_euler_stage(int dim, int N, int ec, int fp32, const StageArgs& a,

@@ -321,10 +321,11 @@ struct EulerStage {
 
   // ---- phase 2 (EC): this node's own pairs in direction L ----
   template <int L>
-  static __device__ __forceinline__ void own_pairs(R* sm, const Role& r, int el, R igm1, R p_ref, R* acc) {
+  static __device__ __forceinline__ void own_pairs(R* sm, const R* D, const Role& r, int el, R igm1, R p_ref,
+                                                   R* acc) {
     constexpr int S = G::stride(L);
     const int nd = r.nd, i = r.pos[L];
-    const R* C = sm + OFF_D + (L * N1 + i) * NO;
+    const R* C = D + (L * N1 + i) * NO;
     const Q4<R>* QA = qa(sm, el);
     const Q4<R> ai = QA[nd], bi = QA[NP + nd];
 #pragma unroll
@@ -345,10 +346,10 @@ struct EulerStage {
 
   // ---- phase 4 (EC): the pairs other nodes evaluated for this node ----
   template <int L>
-  static __device__ __forceinline__ void partner_pairs(const R* sm, const Role& r, int el, R* acc) {
+  static __device__ __forceinline__ void partner_pairs(const R* sm, const R* D, const Role& r, int el, R* acc) {
     constexpr int S = G::stride(L);
     const int nd = r.nd, i = r.pos[L];
-    const R* C = sm + OFF_D + DIM * N1 * NO + (L * N1 + i) * NO;
+    const R* C = D + DIM * N1 * NO + (L * N1 + i) * NO;
 #pragma unroll
     for (int o = 1; o <= NO; ++o) {
       // owner k = i - o (mod N1) of pair (k, i) at offset o
@@ -367,10 +368,10 @@ struct EulerStage {
 
   // ---- phase 4 (strong/weak): contract the volume operator with the staged point fluxes ----
   template <int L>
-  static __device__ __forceinline__ void contract(const R* sm, const Role& r, int el, R* acc) {
+  static __device__ __forceinline__ void contract(const R* sm, const R* D, const Role& r, int el, R* acc) {
     constexpr int S = G::stride(L);
     const int nd = r.nd, i = r.pos[L];
-    const R* Dl = sm + OFF_D + (L * N1 + i) * N1;
+    const R* Dl = D + (L * N1 + i) * N1;
     const R* Fq = sm + OFF_Q + (el * NQ + L * NV) * NP + nd - i * S;
 #pragma unroll
     for (int m = 0; m < N1; ++m) {
@@ -473,8 +474,8 @@ struct EulerStage {
     }
   }
 
-  // ---- one element group, inputs staged in buffer b ----
-  static __device__ __forceinline__ void compute(const StageArgs& A, const InstArgs& I, R* sm,
+  // ---- one element group, inputs staged in buffer b; D: the coefficient tables (load_ops) ----
+  static __device__ __forceinline__ void compute(const StageArgs& A, const InstArgs& I, R* sm, const R* D,
                                                  const Role& r, int g, const double* S,
                                                  bool need_un) {
     const int t = threadIdx.x;
@@ -531,9 +532,9 @@ struct EulerStage {
     for (int v = 0; v < NV; ++v) acc[v] = R(0);
     if constexpr (EC) {
       if (active) {
-        own_pairs<0>(sm, r, el, igm1, p_ref, acc);
-        own_pairs<1>(sm, r, el, igm1, p_ref, acc);
-        if constexpr (DIM == 3) own_pairs<2>(sm, r, el, igm1, p_ref, acc);
+        own_pairs<0>(sm, D, r, el, igm1, p_ref, acc);
+        own_pairs<1>(sm, D, r, el, igm1, p_ref, acc);
+        if constexpr (DIM == 3) own_pairs<2>(sm, D, r, el, igm1, p_ref, acc);
       }
     }
     // phase 3: face jobs
@@ -543,13 +544,13 @@ struct EulerStage {
     // phase 4: gather, then L or the stage update
     if (!active) return;
     if constexpr (EC) {
-      partner_pairs<0>(sm, r, el, acc);
-      partner_pairs<1>(sm, r, el, acc);
-      if constexpr (DIM == 3) partner_pairs<2>(sm, r, el, acc);
+      partner_pairs<0>(sm, D, r, el, acc);
+      partner_pairs<1>(sm, D, r, el, acc);
+      if constexpr (DIM == 3) partner_pairs<2>(sm, D, r, el, acc);
     } else {
-      contract<0>(sm, r, el, acc);
-      contract<1>(sm, r, el, acc);
-      if constexpr (DIM == 3) contract<2>(sm, r, el, acc);
+      contract<0>(sm, D, r, el, acc);
+      contract<1>(sm, D, r, el, acc);
+      if constexpr (DIM == 3) contract<2>(sm, D, r, el, acc);
     }
     gather_faces<0>(sm, r, el, acc);
     gather_faces<1>(sm, r, el, acc);
@@ -612,8 +613,9 @@ struct EulerStage {
     }
   }
 
-  // coefficient tables of instance I (volume operator Dv, row-major (N+1)^2), scaled by 2/dx_l
-  static __device__ __forceinline__ void load_ops(R* sm, const double* Dv, const InstArgs& I) {
+  // coefficient tables of instance I (volume operator Dv, row-major (N+1)^2), scaled by 2/dx_l,
+  // written to D[ND]
+  static __device__ __forceinline__ void load_ops(R* D, const double* Dv, const InstArgs& I) {
     for (int q = threadIdx.x; q < ND; q += blockDim.x) {
       double c;
       if constexpr (EC) {
@@ -625,7 +627,7 @@ struct EulerStage {
         const int L = q / (N1 * N1), rem = q - L * N1 * N1;
         c = I.s[L] * Dv[rem];
       }
-      sm[OFF_D + q] = from64<R>(c);
+      D[q] = from64<R>(c);
     }
   }
 
@@ -637,7 +639,7 @@ struct EulerStage {
     const Smem M = carve();
     const InstArgs& I = A.inst;
     const Role r = role();
-    load_ops(M.sm, A.Dv, I);
+    load_ops(M.sm + OFF_D, A.Dv, I);
     const bool need_un = A.need_un != 0;
     const int ng = (I.n_elem + EPB - 1) / EPB;
     int g = blockIdx.x;
@@ -655,7 +657,7 @@ struct EulerStage {
       if (gn < ng) issue(A, I, r, gn, M.st + (b ^ 1) * ST_SIZE, M.nb + (b ^ 1) * EPB * NF, need_un);
       cp_async_commit();
       if (gnn < ng) fill_nb(I, gnn, M.nb + b * EPB * NF);  // read by the next iteration's issue
-      compute(A, I, M.sm, r, g, M.st + b * ST_SIZE, need_un);
+      compute(A, I, M.sm, M.sm + OFF_D, r, g, M.st + b * ST_SIZE, need_un);
     }
   }
 };

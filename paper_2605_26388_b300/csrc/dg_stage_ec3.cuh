@@ -15,7 +15,8 @@
 //   * the element's FP64 state and the five neighbour traces it needs are copied into shared
 //     memory with cp.async one iteration ahead (two buffers); U^n is read in the update only,
 //     straight from global memory (one coalesced 8-byte load per variable, issued before the
-//     gathers of the partners' pairs and the face terms, which cover its latency);
+//     gathers of the partners' pairs and the face terms, which cover its latency), after a
+//     prefetch to L2 at the start of the element's flux phase;
 //   * per node two 16-byte records of the two-point flux and the FP32 total energy; a face
 //     job rebuilds its own trace from them (momentum as rho v on both sides of the face, so
 //     the two elements of a face still feed identical bits to the single Riemann-flux call

@@ -25,6 +25,7 @@ VOL_STRONG, VOL_WEAK, VOL_EC = 0, 1, 2
 SURF_RUSANOV, SURF_HLLC, SURF_HLL, SURF_EC = 0, 1, 2, 3
 FP64, FP32_MIXED = 0, 1
 LAUNCH_PER_INSTANCE, LAUNCH_BATCHED = 0, 1
+GROUPS_PER_DEGREE = 0x100  # group_scale | (1 << N): degree N uses group scale 2
 BC_PERIODIC, BC_SLIP_WALL, BC_INFLOW, BC_OUTFLOW, BC_DIRICHLET = 0, 1, 2, 3, 4
 BC_NOSLIP_ADIABATIC, BC_NOSLIP_ISOTHERMAL = 5, 6
 MAX_VARS = 12

@@ -51,7 +51,10 @@ def test_batched_equals_per_instance_bitwise(env, orc, prec, vol):
     S.rk_step(dt, 4)
     S.check()
     ref = S.get_state().clone()
-    for gs in (1, 2):
+    # uniform group scales, and per-degree ones (degrees 2, 3, 4, 5 are present: the degrees
+    # with scale 2 run in a second launch per stage)
+    per_degree = [dg.GROUPS_PER_DEGREE | m for m in ((1 << 2), (1 << 3) | (1 << 5), (1 << 4) | (1 << 5) | (1 << 2))]
+    for gs in (1, 2, *per_degree):
         for cps in (0, 1):
             for order in (0, 1):
                 S.set_launch(dg.LAUNCH_BATCHED, gs, cps, order)
@@ -97,5 +100,25 @@ def test_batched_rejects_high_degree_and_autotune_keeps_state(env, orc):
     U0 = torch.from_numpy(U).cuda()
     S.set_state(U0)
     cfg, ms = S.autotune(1e-3, 2)
-    assert cfg[0] in (0, 1) and cfg[1] in (1, 2) and ms > 0
+    per_degree = cfg[1] & dg.GROUPS_PER_DEGREE and not cfg[1] & ~(dg.GROUPS_PER_DEGREE | 0b111100)
+    assert cfg[0] in (0, 1) and (cfg[1] in (1, 2) or per_degree) and ms > 0
     assert torch.equal(S.get_state(), U0)
+
+
+def test_set_launch_rejects_bad_group_scales(env, orc):
+    """Per-degree group scales exist in 2D for degrees 1..5; 3D takes group scale 1 only."""
+    torch, dg = env
+    meshes, U = vortex_set(dg, orc, SPECS)
+    S = dg.Solver(meshes, precision=dg.FP32_MIXED, gamma=GAMMA)
+    for bad in (0, 3, dg.GROUPS_PER_DEGREE | 1, dg.GROUPS_PER_DEGREE | (1 << 6), 0x200 | (1 << 2)):
+        with pytest.raises(dg.DGError) as ei:
+            S.set_launch(dg.LAUNCH_BATCHED, bad)
+        assert ei.value.status == dg.DG_EINVAL, bad
+    S.close()
+    m3 = [dg.Mesh(3, 2, (2, 2, 2), (0.0,) * 3, (1.0,) * 3), dg.Mesh(3, 3, (2, 2, 2), (0.0,) * 3, (1.0,) * 3)]
+    S = dg.Solver(m3, precision=dg.FP32_MIXED, gamma=GAMMA)
+    for bad in (2, dg.GROUPS_PER_DEGREE | (1 << 2)):
+        with pytest.raises(dg.DGError) as ei:
+            S.set_launch(dg.LAUNCH_BATCHED, bad)
+        assert ei.value.status == dg.DG_EINVAL, bad
+    S.close()
