@@ -530,6 +530,7 @@ void launch_args(const dg_ctx* c, dg::StageArgs& a, const double* U, const doubl
   a.Un = Un;
   a.out = out;
   a.err = c->err;
+  a.work = c->err + 2;
   a.stride = c->n_nodes_total;
   a.gamma = c->phys.gamma;
   a.ca = k.ca;
@@ -1127,13 +1128,15 @@ dg_status dg_init_mesh(const dg_mesh_desc* inst, int n_inst, const dg_physics* p
       return DG_ENOMEM;
     }
   }
-  if (cudaMalloc(&c->err, sizeof(unsigned)) != cudaSuccess ||
+  // err[0]: the error word; err[2], err[3]: the work counters of the persistent stage
+  // kernels (next run to claim, CTAs finished), zero between launches
+  if (cudaMalloc(&c->err, 4 * sizeof(unsigned)) != cudaSuccess ||
       cudaMalloc(&c->lam, 3 * sizeof(unsigned long long)) != cudaSuccess) {
     cudaGetLastError();
     dg_free(c);
     return DG_ENOMEM;
   }
-  if (cudaMemset(c->err, 0, sizeof(unsigned)) != cudaSuccess ||
+  if (cudaMemset(c->err, 0, 4 * sizeof(unsigned)) != cudaSuccess ||
       cudaMemset(c->lam, 0, 3 * sizeof(unsigned long long)) != cudaSuccess ||
       cudaMemset(c->buf[0], 0, bytes) != cudaSuccess ||
       cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) {

@@ -66,6 +66,7 @@ struct StageArgs {
   const double* Un;    // U^n (stages 2 and 3), else unused
   double* out;         // U^(k) (mode 1) or L(U) (mode 0)
   unsigned* err;       // device error word (bit 0 non-finite, bit 1 non-positive)
+  unsigned* work;      // [2] work counters of a persistent launch (zero between launches), or null
   long long stride;    // per-variable stride of the SoA state (total nodes)
   double gamma;
   double ca, cb, dt;   // U^(k) = ca Un + cb U^(k-1) + (beta dt) L, beta dt in pd/pf.cbdt

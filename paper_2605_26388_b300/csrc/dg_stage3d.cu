@@ -67,6 +67,8 @@ static cudaError_t prepare_ec3() {
 template <int N, class R>
 static cudaError_t launch_ec3(const StageArgs& a, cudaStream_t s) {
   using K = EC3<N, R>;
+  // the runs of KRUN elements per row (a lower bound of the kernel's run count, which splits
+  // the last rows into shorter runs): every CTA's first run exists
   const int nseg = (a.inst.nel[0] + K::KRUN - 1) / K::KRUN;
   const long long runs = (long long)nseg * a.inst.nel[1] * a.inst.nel[2];
   if (a.inst.n_elem == 0) return cudaSuccess;

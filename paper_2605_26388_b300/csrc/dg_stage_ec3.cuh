@@ -98,21 +98,39 @@ struct EC3 {
     return c[0] + I.nel[0] * (c[1] + I.nel[1] * c[2]);
   }
 
-  // Runs: each row of elements along x (rows in element order) splits into nseg =
-  // ceil(nx / KRUN) runs.  Run q starts at element *e0 and holds *len elements; returns false
-  // past the last run.
+  // Runs: the rows of elements along x (rows in element order) split into runs of KRUN
+  // elements, except the last rows -- about two runs of KRUN per CTA -- which split into runs
+  // of KTAIL, so that the CTAs, taking the runs in order, finish within a few elements of one
+  // another.  Run q starts at element *e0 and holds *len elements; false past the last run.
+  static constexpr int KTAIL = 4;
   static __device__ __forceinline__ bool run_of(const InstArgs& I, int q, int* e0, int* len) {
-    const int nx = I.nel[0];
-    const int nseg = (nx + KRUN - 1) / KRUN;
-    const int row = q / nseg, seg = q - row * nseg;
-    if (row >= I.nel[1] * I.nel[2]) return false;
-    const int x0 = seg * KRUN;
+    const int nx = I.nel[0], nrows = I.nel[1] * I.nel[2];
+    const int tail = (2 * (int)gridDim.x * KRUN + nx - 1) / nx;
+    const int ra = tail < nrows ? nrows - tail : 0;  // rows in runs of KRUN
+    const int nsa = (nx + KRUN - 1) / KRUN, nsb = (nx + KTAIL - 1) / KTAIL;
+    int row, x0, k;
+    if (q < ra * nsa) {
+      row = q / nsa;
+      x0 = (q - row * nsa) * KRUN;
+      k = KRUN;
+    } else {
+      const int qb = q - ra * nsa;
+      const int rb = qb / nsb;
+      row = ra + rb;
+      if (row >= nrows) return false;
+      x0 = (qb - rb * nsb) * KTAIL;
+      k = KTAIL;
+    }
     *e0 = x0 + nx * row;
-    *len = min(KRUN, nx - x0);
+    *len = min(k, nx - x0);
     return true;
   }
 
-  // A CTA's walk: runs blockIdx.x, blockIdx.x + gridDim.x, ...; position m within the run.
+  // A CTA's walk: its first run is run blockIdx.x; each further run is claimed from the
+  // launch-wide counter A.work[0] (claim k gives run gridDim.x + k), so that the runs are
+  // still taken up roughly in element order -- the elements in flight stay within a band of
+  // the mesh, as with a cyclic deal -- and no CTA ends with a run more than another (without
+  // a counter, runs blockIdx.x + k gridDim.x).  Position m within the run.
   struct Walk {
     int run, m, e0, len;
     bool ok;
@@ -125,32 +143,68 @@ struct EC3 {
     w.ok = run_of(I, w.run, &w.e0, &w.len);
     return w;
   }
-  static __device__ __forceinline__ Walk walk_next(const InstArgs& I, Walk w) {
+  // the next element; at the end of a run the walk moves to run `next` (the run claimed
+  // ahead) and sets *used
+  static __device__ __forceinline__ Walk walk_next(const InstArgs& I, Walk w, int next, bool* used) {
     if (!w.ok) return w;
     if (w.m + 1 < w.len) {
       ++w.m;
       return w;
     }
-    w.run += gridDim.x;
+    w.run = next;
+    *used = true;
     w.m = 0;
     w.ok = run_of(I, w.run, &w.e0, &w.len);
     return w;
   }
+  // a run index for the walk to take after `run`: claimed from the counter, or the cyclic deal
+  static __device__ __forceinline__ int claim(const StageArgs& A, int run) {
+    return A.work ? (int)(atomicAdd(A.work, 1u) + gridDim.x) : run + (int)gridDim.x;
+  }
 
-  // start the copies of element e's inputs into staging buffer S
-  static __device__ __forceinline__ void issue(const StageArgs& A, const InstArgs& I, const Role& r,
-                                               int e, double* S, const int* nb) {
+  // start the copies of element e's inputs into staging buffer S: its own state (issue_own),
+  // the five neighbour traces of its face jobs (issue_traces; each thread copies the trace
+  // values of its own face job)
+  static __device__ __forceinline__ void issue_own(const StageArgs& A, const InstArgs& I, int e, double* S) {
     const int t = threadIdx.x;
     if (t < NP) {
       const double* pu = A.U + I.base + (long long)e * NP + t;
 #pragma unroll
       for (int v = 0; v < NV; ++v) cp_async8(S + v * NP + t, pu + v * A.stride);
     }
+  }
+  static __device__ __forceinline__ void issue_traces(const StageArgs& A, const InstArgs& I, const Role& r,
+                                                      double* S, const int* nb) {
+    const int t = threadIdx.x;
     if (t < NJ) {
       const double* pt = A.U + I.base + (long long)nb[r.face] * NP + r.ndn;
       double* st = S + ST_T + (r.face - 1) * NV * NFN + r.f;
 #pragma unroll
       for (int v = 0; v < NV; ++v) cp_async8(st + v * NFN, pt + v * A.stride);
+    }
+  }
+
+  // L2 prefetch of the lines that the copies of element e will read an iteration later: its
+  // own state (NV x NP doubles, 128-byte lines) and, once its neighbour table nb is visible,
+  // the face traces (one line per face node and variable; repeats hit the same line)
+  static __device__ __forceinline__ void prefetch_own(const StageArgs& A, const InstArgs& I, int e) {
+    constexpr int LPV = (NP * 8 + 127) / 128 + 1;  // lines per variable (unaligned start)
+    const int t = threadIdx.x;
+    if (t < NV * LPV) {
+      const int v = t / LPV, q = t - v * LPV;
+      const char* p0 = reinterpret_cast<const char*>(A.U + I.base + (long long)e * NP + v * A.stride);
+      const char* p = p0 + 128 * q;
+      const char* last = p0 + (NP * 8 - 1);
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(p < last ? p : last));
+    }
+  }
+  static __device__ __forceinline__ void prefetch_traces(const StageArgs& A, const InstArgs& I, const Role& r,
+                                                         const int* nb) {
+    const int t = threadIdx.x;
+    if (t < NJ && r.face >= 2) {
+      const double* pt = A.U + I.base + (long long)nb[r.face] * NP + r.ndn;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) asm volatile("prefetch.global.L2 [%0];" ::"l"(pt + v * A.stride));
     }
   }
 
@@ -467,7 +521,8 @@ struct EC3 {
     for (int v = 0; v < NV; ++v) {
       if constexpr (sizeof(R) == 8) finite = finite && finite64(res[v]);
       A.out[v * A.stride + gi] = res[v];
-    }    if (!finite) atomicOr(A.err, 1u);
+    }
+    if (!finite) atomicOr(A.err, 1u);
   }
 
   // Persistent walk, two barriers per element.  Iteration it handles element e (the walk's
@@ -476,7 +531,9 @@ struct EC3 {
   // barrier runs e's update together with the next element's records (the update reads the
   // pair and face slots and e's buffer, the records phase writes the records from the other
   // buffer: nothing is shared), then a second barrier.  Each thread reads only the staged
-  // values it copied itself, so its own cp.async wait suffices before the records phase.  The
+  // values it copied itself, so its own cp.async waits suffice: for the next element's state
+  // before the records phase, for its neighbour traces at the start of the next iteration
+  // (a whole iteration after they were requested).  The
   // x+ face slot alternates between 1 and 6, so that the next element of the run reads the
   // carried face while this one's slots are rewritten.
   static __device__ void run(const StageArgs& A) {
@@ -489,23 +546,46 @@ struct EC3 {
     const bool node = threadIdx.x < NP;
     load_ops(sm, A.Dv, I);
     const bool need_un = A.need_un != 0;
+    __shared__ int s_next;  // the run claimed ahead (thread 0 writes it, after a barrier)
+    const int t = threadIdx.x;
     Walk w = walk_start(I);
-    Walk wn = walk_next(I, w);
-    Walk wnn = walk_next(I, wn);
+    if (t == 0) s_next = claim(A, w.run);
+    __syncthreads();
+    bool used = false;
+    Walk wn = walk_next(I, w, s_next, &used);
+    if (used) {  // a run of one element
+      const int last = wn.run;
+      __syncthreads();
+      if (t == 0) s_next = claim(A, last);
+      __syncthreads();
+      used = false;
+    }
+    Walk wnn = walk_next(I, wn, s_next, &used);
     if (w.ok) fill_nb(I, w.elem(), nb);
     if (wn.ok) fill_nb(I, wn.elem(), nb + NF);
     __syncthreads();
-    if (w.ok) issue(A, I, r, w.elem(), st, nb);
+    if (w.ok) {
+      issue_own(A, I, w.elem(), st);
+      issue_traces(A, I, r, st, nb);
+    }
     cp_async_commit();
     cp_async_wait_all();
     if (w.ok && node) phase1(A, sm, r, st);
     __syncthreads();
     for (int it = 0; w.ok; ++it) {
       const int b = it & 1;
-      // buffer b^1 and neighbour slot b are free: their element's update and copies are done
-      if (wn.ok) issue(A, I, r, wn.elem(), st + (b ^ 1) * ST_SIZE, nb + (b ^ 1) * NF);
+      cp_async_wait_all();  // this thread's copies of e's neighbour traces (requested an iteration ago)
+      // buffer b^1 and neighbour slot b are free: their element's update and copies are done.
+      // The next element's own state and its traces form two groups: the records phase below
+      // waits for the first only, the traces have until the next iteration's face jobs.
+      if (wn.ok) issue_own(A, I, wn.elem(), st + (b ^ 1) * ST_SIZE);
       cp_async_commit();
-      if (wnn.ok) fill_nb(I, wnn.elem(), nb + b * NF);  // read by the next iteration's issue
+      if (wn.ok) issue_traces(A, I, r, st + (b ^ 1) * ST_SIZE, nb + (b ^ 1) * NF);
+      cp_async_commit();
+      if (wnn.ok) {
+        fill_nb(I, wnn.elem(), nb + b * NF);  // read by the next iteration's issue
+        prefetch_own(A, I, wnn.elem());
+      }
       // the x- face is carried from the previous iteration, which handled element e - 1 of
       // the same run
       const int e = w.elem(), xp = b ? NF : 1;
@@ -513,7 +593,12 @@ struct EC3 {
       R acc[NV];
       phase23(A, I, sm, r, e, st + b * ST_SIZE, carry, xp, need_un, acc);
       __syncthreads();  // pair and face slots complete; the records are free
-      cp_async_wait_all();  // this thread's copies of the next element
+      cp_async_wait_prev();  // this thread's copies of the next element's own state
+      if (wnn.ok) prefetch_traces(A, I, r, nb + b * NF);  // the table is visible since the barrier
+      if (used) {  // every thread has read s_next since the walk last took it: claim the next
+        if (t == 0) s_next = claim(A, wnn.run);
+        used = false;
+      }
       if (node) {
         phase4(A, I, sm, r, e, st + b * ST_SIZE, carry, xp, need_un, acc);
         if (wn.ok) phase1(A, sm, r, st + (b ^ 1) * ST_SIZE);
@@ -521,7 +606,16 @@ struct EC3 {
       __syncthreads();  // the next element's records complete; the slots and buffer b are free
       w = wn;
       wn = wnn;
-      wnn = walk_next(I, wnn);
+      wnn = walk_next(I, wnn, s_next, &used);
+    }
+    // the last CTA to finish returns the counters to zero for the next launch (no CTA claims
+    // after it has finished)
+    if (A.work && t == 0) {
+      __threadfence();
+      if (atomicAdd(A.work + 1, 1u) == gridDim.x - 1) {
+        A.work[0] = 0u;
+        A.work[1] = 0u;
+      }
     }
   }
 };
