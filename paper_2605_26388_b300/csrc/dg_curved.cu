@@ -34,9 +34,9 @@ struct CG {
   static constexpr int NJ = NF * NFN;
   static constexpr int T = ((cmax(NP, NJ) + 31) / 32) * 32;
   static constexpr int NQ = EC ? 8 : DIM * NV;  // per node: prims (EC) or contravariant fluxes
-  // two-point pairs along a line: every node owns KO = (N1-1)/2 of them (partner i+k mod N1,
-  // k = 1..KO) and, on a line of even length, the lower half owns the k = N1/2 pair too
-  static constexpr int KO = (N1 - 1) / 2, KM = N1 / 2;
+  // two-point pairs along a line: every node owns (N1-1)/2 of them (partner i+k mod N1,
+  // k = 1..(N1-1)/2) and, on a line of even length, the lower half owns the k = N1/2 pair too
+  static constexpr int KM = N1 / 2;
   // shared layout (R): U [NV][NP], Q [NQ][NP], pd [NP], Ja [DIM*DIM][NP], jinv [NP],
   // S [NF][NFN][NV], D [N1*N1], pair fluxes of one direction P [NP][KM][NV] (EC)
   static constexpr int O_U = 0, O_Q = O_U + NV * NP, O_PD = O_Q + NQ * NP, O_JA = O_PD + NP;
@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(CG<DIM, N, EC, R>::T) k_euler_curved(const Sta
         for (int v = 0; v < NV; ++v) acc[v] -= cd * F[v];
 #pragma unroll
         for (int k = 1; k <= G::KM; ++k) {
-          if (k > G::KO && i >= G::KM) continue;  // the half-way pair of an even line: lower node
+          if (2 * k == G::N1 && i >= G::KM) continue;  // the half-way pair of an even line: lower node
           const int m = i + k < N1 ? i + k : i + k - N1;
           pair_flux(l, nd, base + m * S, F);
           const R cm = two_jinv * Dv[i * N1 + m];
@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(CG<DIM, N, EC, R>::T) k_euler_curved(const Sta
 #pragma unroll
         for (int k = 1; k <= G::KM; ++k) {
           const int j = i - k >= 0 ? i - k : i - k + N1;  // the owner of pair (j, j + k = i)
-          if (k > G::KO && j >= G::KM) continue;
+          if (2 * k == G::N1 && j >= G::KM) continue;
           const R cm = two_jinv * Dv[i * N1 + j];
           const int nj = base + j * S;
 #pragma unroll
