@@ -114,7 +114,7 @@ class Problem:
     bc: tuple = (0, 0, 0, 0, 0, 0)  # per domain face x-, x+, y-, y+, z-, z+; 0 = periodic
     bc_state: tuple = None          # per face: the exterior conserved state (INFLOW, DIRICHLET);
                                     # (T_wall,) for NOSLIP_ISOTHERMAL
-    coords: np.ndarray = None       # Euler: node coordinates (dim, n_elem, n_nodes) of a curved mesh
+    coords: np.ndarray = None       # node coordinates (dim, n_elem, n_nodes) of a curved mesh (reacting: periodic)
     two_temperature: bool = False   # NS_REACTING: E_v appended to the state
     species_limiter: bool = False   # NS_REACTING: Zhang-Shu limiter of rho_s after every RK stage
 

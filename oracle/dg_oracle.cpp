@@ -84,8 +84,9 @@ struct OrcProblem {
                               // no-slip walls (5, 6) exist for ORC_NS_REACTING only
   double bc_state[6][12];     // INFLOW / DIRICHLET: the exterior conserved state (n_vars
                               // values); NOSLIP_ISOTHERMAL: [0] = the wall temperature
-  const double* coords;       // Euler: node coordinates [d][elem][node] of a curved mesh on the
-                              // same element topology (null: the Cartesian box)
+  const double* coords;       // node coordinates [d][elem][node] of a curved mesh on the same
+                              // element topology (null: the Cartesian box); ORC_NS_REACTING:
+                              // periodic, without the species limiter
   int two_temperature;        // ORC_NS_REACTING: 1 -- the two-temperature model (E_v appended
                               // to the state)
   int species_limiter;        // ORC_NS_REACTING: 1 -- the Zhang-Shu limiter of the partial
@@ -964,7 +965,13 @@ int check_problem(const OrcProblem& P) {
     if (P.volume != ORC_VOL_STRONG || P.surface != ORC_SURF_RUSANOV) return -6;
     if (P.rho_floor > 0.0 || P.p_floor > 0.0) return -6;
     if (P.mu < 0.0 || !(P.prandtl > 0.0)) return -1;
-    if (P.shock || P.coords) return -6;
+    if (P.shock) return -6;
+    if (P.coords) {  // curved meshes: periodic, without the species limiter (whose element
+                     // mean would need the Jacobian weights)
+      for (int f = 0; f < 2 * P.dim; ++f)
+        if (P.bc[f] != ORC_BC_PERIODIC) return -6;
+      if (P.species_limiter) return -6;
+    }
     if (P.two_temperature) {
       if (P.two_temperature != 1) return -1;
       for (int s = 0; s < P.mech->n_species; ++s)
@@ -1486,9 +1493,190 @@ void reacting_element_residual(const OrcProblem& P, const Mesh& M, const Ops& op
     for (int v = 0; v < nv; ++v) dU[((size_t)v * M.n_elem + e) * M.n_nodes + nd] = R[nd * nv + v];
 }
 
+// ---------------------------------------------------------------------------------------
+// Reacting Navier-Stokes on a curved mesh (Sec. 3.1.1 metric terms with the discrete GCL;
+// Sec. 3.1.2 BR1 on the mapped element; periodic meshes).
+// BR1 gradient (Step 1): the strong-form DG derivative in reference space -- along each
+// reference direction l, D W plus the lifted jump (W^ - W)/w at the element's faces, W^ the
+// BR1 average of Eq. br1_avg -- then mapped to physical space with the contravariant vectors
+// at the node and rescaled by the inverse Jacobian:
+//   S_d(i) = (1/J_i) sum_l Ja^l_d(i) [ (D_l W)_i + (face terms)_l ].
+// READING: the paper says the gradient is formed by a strong-form operator and rescaled by
+// 1/J after the surface contributions; the reference-space derivative mapped by Ja^l at the
+// node (chain rule) is the form taken here (it equals the Cartesian operator on affine
+// elements and gives a zero gradient of a constant).
+// ---------------------------------------------------------------------------------------
+void curved_br1_gradient(const OrcProblem& P, const Mesh& M, const Ops& ops, const Metrics& Gm,
+                         const double* U, int e, double* G) {
+  const int dim = M.dim, n1 = M.n1, N = M.N, nv = n_vars(P), np = M.n_nodes;
+  auto prim = [&](int el, int nd, double* W) {
+    double u[16];
+    load_node(M, nv, U, el, nd, u);
+    Mix q = mixture(P, u);
+    W[0] = q.v[0]; W[1] = q.v[1]; W[2] = q.v[2]; W[3] = q.T; W[4] = q.Tv;
+  };
+  auto Ja = [&](int nd, int l, int d) { return Gm.Ja[(((size_t)e * np + nd) * 3 + l) * 3 + d]; };
+  for (int nd = 0; nd < np; ++nd) {
+    int ijk[3];
+    M.node_coords(nd, ijk);
+    double ref[5][3] = {};
+    double Wo[5], Wn[5], Wm[5];
+    prim(e, nd, Wo);
+    for (int l = 0; l < dim; ++l) {
+      for (int m = 0; m < n1; ++m) {
+        int mk[3] = {ijk[0], ijk[1], ijk[2]};
+        mk[l] = m;
+        prim(e, M.node(mk), Wm);
+        for (int q = 0; q < 5; ++q) ref[q][l] += ops.D[ijk[l] * n1 + m] * Wm[q];
+      }
+      for (int side = 0; side < 2; ++side) {
+        if (ijk[l] != (side ? N : 0)) continue;
+        int nk[3] = {ijk[0], ijk[1], ijk[2]};
+        nk[l] = side ? 0 : N;
+        prim(M.neighbour(e, l, side ? +1 : -1), M.node(nk), Wn);
+        for (int q = 0; q < 5; ++q) {
+          const double jump = 0.5 * (Wo[q] + Wn[q]) - Wo[q];
+          ref[q][l] += (side ? 1.0 : -1.0) * jump / ops.w[side ? N : 0];
+        }
+      }
+    }
+    const double iJ = 1.0 / Gm.J[(size_t)e * np + nd];
+    for (int q = 0; q < 5; ++q)
+      for (int d = 0; d < 3; ++d) {
+        double g = 0.0;
+        if (d < dim)
+          for (int l = 0; l < dim; ++l) g += Ja(nd, l, d) * ref[q][l];
+        G[((size_t)(e * np + nd) * 5 + q) * 3 + d] = iJ * g;
+      }
+  }
+}
+
+// Rusanov flux of the mixture along the unit direction n: (F_n(U_L) + F_n(U_R))/2 -
+// lambda (U_R - U_L)/2, F_n = sum_d n_d F^d, lambda = max(|u_L . n| + a_L, |u_R . n| + a_R).
+void mix_rusanov_n(const OrcProblem& P, const double* n, const double* uL, const double* uR, double* F) {
+  const int nv = n_vars(P), dim = P.dim;
+  Mix a = mixture(P, uL), b = mixture(P, uR);
+  double unL = 0.0, unR = 0.0;
+  for (int d = 0; d < dim; ++d) {
+    unL += a.v[d] * n[d];
+    unR += b.v[d] * n[d];
+  }
+  const double lam = std::fmax(std::fabs(unL) + a.a, std::fabs(unR) + b.a);
+  double FL[16], FR[16], Fd[16];
+  for (int v = 0; v < nv; ++v) FL[v] = FR[v] = 0.0;
+  for (int d = 0; d < dim; ++d) {
+    mix_flux(P, d, uL, Fd);
+    for (int v = 0; v < nv; ++v) FL[v] += n[d] * Fd[v];
+    mix_flux(P, d, uR, Fd);
+    for (int v = 0; v < nv; ++v) FR[v] += n[d] * Fd[v];
+  }
+  for (int v = 0; v < nv; ++v) F[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * lam * (uR[v] - uL[v]);
+}
+
+// Residual of element e on a curved mesh (Step 2 and the hyperbolic pipeline with the
+// contravariant fluxes, Eqs. vol_weak, surf_int, br1_flux):
+//   R_i = (1/J_i) [ - sum_l sum_m D_{i_l m} (Ftilde^l_inv - Ftilde^l_v)(m)
+//                   -/+ (1/w) (|Ja^l| F*_n - Ftilde^l_inv(i))            (upper / lower face)
+//                   +/- (1/w) (Ja^l . {{F_v}} - Ftilde^l_v(i)) ]        + S(U_i),
+// Ftilde^l = sum_d Ja^l_d F^d, n = Ja^l / |Ja^l| at the own face node (the neighbour's face
+// node has the same Ja^l: it depends on the face's nodes only).
+void curved_reacting_element_residual(const OrcProblem& P, const Mesh& M, const Ops& ops, const Metrics& Gm,
+                                      const double* U, const double* G, int e, double* dU) {
+  const int dim = M.dim, n1 = M.n1, N = M.N, nv = n_vars(P), np = M.n_nodes;
+  const int parts = P.parts ? P.parts : 7;
+  std::vector<double> R((size_t)np * nv, 0.0);
+  auto grad = [&](int el, int nd) { return G + (size_t)(el * np + nd) * 15; };
+  auto Ja = [&](int nd, int l, int d) { return Gm.Ja[(((size_t)e * np + nd) * 3 + l) * 3 + d]; };
+  // contravariant inviscid and viscous fluxes of direction l at node nd of element el with
+  // the metric of own node ndm
+  auto contra = [&](int l, int ndm, const double* u, const double* g, double* Fi, double* Fv) {
+    double Fd[16];
+    for (int v = 0; v < nv; ++v) Fi[v] = Fv[v] = 0.0;
+    for (int d = 0; d < dim; ++d) {
+      const double a = Ja(ndm, l, d);
+      mix_flux(P, d, u, Fd);
+      for (int v = 0; v < nv; ++v) Fi[v] += a * Fd[v];
+      viscous_flux(P, d, u, g, Fd);
+      for (int v = 0; v < nv; ++v) Fv[v] += a * Fd[v];
+    }
+  };
+  double um[16], Fi[16], Fv[16];
+  for (int nd = 0; nd < np; ++nd) {
+    int ijk[3];
+    M.node_coords(nd, ijk);
+    for (int l = 0; l < dim; ++l)
+      for (int m = 0; m < n1; ++m) {
+        int mk[3] = {ijk[0], ijk[1], ijk[2]};
+        mk[l] = m;
+        const int nm = M.node(mk);
+        load_node(M, nv, U, e, nm, um);
+        contra(l, nm, um, grad(e, nm), Fi, Fv);
+        const double c = ops.D[ijk[l] * n1 + m];
+        for (int v = 0; v < nv; ++v) {
+          if (parts & 1) R[nd * nv + v] -= c * Fi[v];
+          if (parts & 2) R[nd * nv + v] += c * Fv[v];
+        }
+      }
+  }
+  for (int l = 0; l < dim; ++l)
+    for (int nd = 0; nd < np; ++nd) {
+      int ijk[3];
+      M.node_coords(nd, ijk);
+      for (int side = 0; side < 2; ++side) {
+        if (ijk[l] != (side ? N : 0)) continue;
+        double uown[16], unbr[16], Fs[16], Fio[16], Fvo[16], Fin[16], Fvn[16], n[3] = {0.0, 0.0, 0.0};
+        load_node(M, nv, U, e, nd, uown);
+        int nk[3] = {ijk[0], ijk[1], ijk[2]};
+        nk[l] = side ? 0 : N;
+        const int en = M.neighbour(e, l, side ? +1 : -1), nn = M.node(nk);
+        load_node(M, nv, U, en, nn, unbr);
+        double s2 = 0.0;
+        for (int d = 0; d < dim; ++d) s2 += Ja(nd, l, d) * Ja(nd, l, d);
+        const double sj = std::sqrt(s2);
+        for (int d = 0; d < dim; ++d) n[d] = Ja(nd, l, d) / sj;
+        contra(l, nd, uown, grad(e, nd), Fio, Fvo);
+        contra(l, nd, unbr, grad(en, nn), Fin, Fvn);
+        const double lift = 1.0 / ops.w[side ? N : 0];
+        if (parts & 1) {
+          if (side) mix_rusanov_n(P, n, uown, unbr, Fs);
+          else mix_rusanov_n(P, n, unbr, uown, Fs);
+          for (int v = 0; v < nv; ++v) R[nd * nv + v] += (side ? -lift : lift) * (sj * Fs[v] - Fio[v]);
+        }
+        if (parts & 2)
+          for (int v = 0; v < nv; ++v)
+            R[nd * nv + v] += (side ? lift : -lift) * (0.5 * (Fvo[v] + Fvn[v]) - Fvo[v]);
+      }
+    }
+  for (int nd = 0; nd < np; ++nd) {
+    const double iJ = 1.0 / Gm.J[(size_t)e * np + nd];
+    for (int v = 0; v < nv; ++v) R[nd * nv + v] *= iJ;
+  }
+  if (parts & 4) {
+    for (int nd = 0; nd < np; ++nd) {
+      load_node(M, nv, U, e, nd, um);
+      chem_source(P, um, Fi);
+      for (int v = 0; v < nv; ++v) R[nd * nv + v] += Fi[v];
+    }
+  }
+  for (int nd = 0; nd < np; ++nd)
+    for (int v = 0; v < nv; ++v) dU[((size_t)v * M.n_elem + e) * np + nd] = R[nd * nv + v];
+}
+
 void residual(const OrcProblem& P, const double* U, double* dU) {
   Mesh M(P);
   Ops ops(P.N);
+  if (P.equations == ORC_NS_REACTING && P.coords) {
+    const Metrics Gm = curved_metrics(P, M, ops);
+    std::vector<double> G((size_t)M.n_elem * M.n_nodes * 15, 0.0);
+    const int parts = P.parts ? P.parts : 7;
+    if (parts & 2) {
+#pragma omp parallel for schedule(static)
+      for (int e = 0; e < M.n_elem; ++e) curved_br1_gradient(P, M, ops, Gm, U, e, G.data());
+    }
+#pragma omp parallel for schedule(static)
+    for (int e = 0; e < M.n_elem; ++e) curved_reacting_element_residual(P, M, ops, Gm, U, G.data(), e, dU);
+    return;
+  }
   if (P.equations == ORC_NS_REACTING) {
     std::vector<double> G((size_t)M.n_elem * M.n_nodes * 15, 0.0);
     const int parts = P.parts ? P.parts : 7;
@@ -1774,6 +1962,11 @@ int orc_br1_gradients(const OrcProblem* P, const double* U, const int* elems, in
   Ops ops(P->N);
   for (int k = 0; k < n; ++k)
     if (elems[k] < 0 || elems[k] >= M.n_elem) return -1;
+  if (P->coords) {
+    const Metrics Gm = curved_metrics(*P, M, ops);
+    for (int k = 0; k < n; ++k) curved_br1_gradient(*P, M, ops, Gm, U, elems[k], G);
+    return 0;
+  }
   for (int k = 0; k < n; ++k) br1_gradient(*P, M, ops, U, elems[k], G);
   return 0;
 }
@@ -1787,6 +1980,11 @@ int orc_rhs_elements_given_gradient(const OrcProblem* P, const double* U, const 
   Ops ops(P->N);
   for (int k = 0; k < n; ++k)
     if (elems[k] < 0 || elems[k] >= M.n_elem) return -1;
+  if (P->coords) {
+    const Metrics Gm = curved_metrics(*P, M, ops);
+    for (int k = 0; k < n; ++k) curved_reacting_element_residual(*P, M, ops, Gm, U, G, elems[k], dU);
+    return 0;
+  }
   for (int k = 0; k < n; ++k) reacting_element_residual(*P, M, ops, U, G, elems[k], dU);
   return 0;
 }
@@ -1822,6 +2020,14 @@ int orc_rhs_elements(const OrcProblem* P, const double* U, const int* elems, int
           const int en = M.neighbour(e, l, dir);
           if (!mark[en]) { mark[en] = 1; need.push_back(en); }
         }
+    }
+    if (P->coords) {
+      const Metrics Gm = curved_metrics(*P, M, ops);
+#pragma omp parallel for schedule(static)
+      for (int k = 0; k < (int)need.size(); ++k) curved_br1_gradient(*P, M, ops, Gm, U, need[k], G.data());
+#pragma omp parallel for schedule(static)
+      for (int k = 0; k < n; ++k) curved_reacting_element_residual(*P, M, ops, Gm, U, G.data(), elems[k], dU);
+      return 0;
     }
 #pragma omp parallel for schedule(static)
     for (int k = 0; k < (int)need.size(); ++k) br1_gradient(*P, M, ops, U, need[k], G.data());
