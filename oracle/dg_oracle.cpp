@@ -2624,6 +2624,28 @@ int orc_rollout_grad(const OrcProblem* P, const double* U0, const double* target
 //   dt = cfl * dx_min / ((2N+1) lambda_max),  lambda_max = max over nodes of |u| + a.
 // READING: |u| is the speed (vector magnitude); the SSP coefficient of SSP-RK3 is 1, so
 // cfl multiplies nothing else; dx_min is the smallest element edge.
+}  // extern "C"
+
+namespace {
+// READING (curved meshes): the element size in direction l is 2 J / |Ja^l| (the physical
+// length of the reference interval; dx_l on the affine box), minimised over the nodes.
+double curved_spacing(const OrcProblem& P, const Mesh& M) {
+  Ops ops(P.N);
+  const Metrics G = curved_metrics(P, M, ops);
+  const size_t stride = (size_t)M.n_elem * M.n_nodes;
+  double dxmin = 1e300;
+  for (size_t q = 0; q < stride; ++q)
+    for (int l = 0; l < M.dim; ++l) {
+      double s2 = 0.0;
+      for (int d = 0; d < M.dim; ++d) s2 += G.Ja[(q * 3 + l) * 3 + d] * G.Ja[(q * 3 + l) * 3 + d];
+      dxmin = std::fmin(dxmin, 2.0 * G.J[q] / std::sqrt(s2));
+    }
+  return dxmin;
+}
+}  // namespace
+
+extern "C" {
+
 int orc_max_dt(const OrcProblem* P, const double* U, double cfl, double* dt) {
   int rc = check_problem(*P);
   if (rc) return rc;
@@ -2648,6 +2670,7 @@ int orc_max_dt(const OrcProblem* P, const double* U, double cfl, double* dt) {
     }
     double dxmin = M.dx[0];
     for (int l = 1; l < dim; ++l) dxmin = std::fmin(dxmin, M.dx[l]);
+    if (P->coords) dxmin = curved_spacing(*P, M);  // as for the curved Euler bound below
     const double dtc = cfl * dxmin / ((2 * P->N + 1) * lam);
     const double n2 = (2.0 * P->N + 1) * (2.0 * P->N + 1);
     *dt = nu > 0.0 ? std::fmin(dtc, cfl * dxmin * dxmin / (n2 * nu)) : dtc;
@@ -2663,19 +2686,7 @@ int orc_max_dt(const OrcProblem* P, const double* U, double cfl, double* dt) {
   }
   double dxmin = M.dx[0];
   for (int l = 1; l < dim; ++l) dxmin = std::fmin(dxmin, M.dx[l]);
-  if (P->coords) {
-    // READING (curved meshes): the element size in direction l is 2 J / |Ja^l| (the physical
-    // length of the reference interval; dx_l on the affine box), minimised over the nodes
-    Ops ops(P->N);
-    const Metrics G = curved_metrics(*P, M, ops);
-    dxmin = 1e300;
-    for (size_t q = 0; q < stride; ++q)
-      for (int l = 0; l < dim; ++l) {
-        double s2 = 0.0;
-        for (int d = 0; d < dim; ++d) s2 += G.Ja[(q * 3 + l) * 3 + d] * G.Ja[(q * 3 + l) * 3 + d];
-        dxmin = std::fmin(dxmin, 2.0 * G.J[q] / std::sqrt(s2));
-      }
-  }
+  if (P->coords) dxmin = curved_spacing(*P, M);
   *dt = cfl * dxmin / ((2 * P->N + 1) * lam);
   return 0;
 }

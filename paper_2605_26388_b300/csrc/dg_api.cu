@@ -632,6 +632,13 @@ dg_status run_stage_ns(dg_ctx* c, const double* U, const double* Un, double* out
       a.sf[l] = (float)a.s[l];
     }
     a.n_elem = (int)n_elem_of(m);
+    const bool curved = !c->curved.empty() && c->curved[i];
+    a.met = curved ? c->met : nullptr;
+    if (curved)  // the 2/dx_l of the element map are part of the metric terms
+      for (int l = 0; l < 3; ++l) {
+        a.s[l] = 1.0;
+        a.sf[l] = 1.0f;
+      }
     double x[dg::kMaxN + 1], w[dg::kMaxN + 1];
     gll_table(m.N, x, w, a.D);
     a.lift = 1.0 / w[0];
@@ -1019,6 +1026,35 @@ dg_status one_step(dg_ctx* c, double dt, cudaStream_t s) {
   return DG_OK;
 }
 
+// Metric terms of the context's curved instances (device array met [dim*dim + 1][nodes], the
+// per-instance flags and smallest spacings); euler: also set up the curved Euler kernel.
+dg_status setup_curved(dg_ctx* c, const dg_mesh_desc* inst, int n_inst, long long off, bool euler) {
+  const int nm = c->dim * c->dim + 1;
+  std::vector<double> met((size_t)nm * off, 0.0);
+  c->curved.assign(n_inst, 0);
+  c->curved_dx.assign(n_inst, 0.0);
+  for (int i = 0; i < n_inst; ++i) {
+    if (!inst[i].coords) continue;
+    c->curved[i] = 1;
+    if (!curved_metrics_host(inst[i], met.data(), off, c->offs[i], c->curved_dx[i]))
+      return DG_EINVAL;  // an element with J <= 0
+    if (euler && dg::launch_curved(inst[i].dim, inst[i].N, c->phys.volume == DG_VOL_EC,
+                                   c->phys.precision == DG_FP32_MIXED, nullptr, nullptr, nullptr) != cudaSuccess) {
+      cudaGetLastError();
+      return DG_ECUDA;
+    }
+  }
+  if (cudaMalloc(&c->met, sizeof(double) * met.size()) != cudaSuccess) {
+    cudaGetLastError();
+    return DG_ENOMEM;
+  }
+  if (cudaMemcpy(c->met, met.data(), sizeof(double) * met.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaGetLastError();
+    return DG_ECUDA;
+  }
+  return DG_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1047,10 +1083,16 @@ dg_status dg_init_mesh(const dg_mesh_desc* inst, int n_inst, const dg_physics* p
   for (int i = 0; i < n_inst; ++i) {
     if (!inst[i].coords) continue;
     any_curved = true;
-    if (phys->equations != DG_EULER || phys->shock || phys->rho_floor > 0.0 || phys->p_floor > 0.0 ||
-        (phys->volume != DG_VOL_STRONG && phys->volume != DG_VOL_EC) ||
-        !dg::have_curved(inst[i].dim, inst[i].N))
-      return DG_EUNSUPPORTED;
+    if (phys->shock || phys->rho_floor > 0.0 || phys->p_floor > 0.0) return DG_EUNSUPPORTED;
+    if (phys->equations == DG_EULER) {
+      if ((phys->volume != DG_VOL_STRONG && phys->volume != DG_VOL_EC) || !dg::have_curved(inst[i].dim, inst[i].N))
+        return DG_EUNSUPPORTED;
+    } else {  // viscous equations: periodic curved meshes, without the species limiter (its
+              // element mean would need the Jacobian weights)
+      if (phys->species_limiter) return DG_EUNSUPPORTED;
+      for (int l = 0; l < inst[i].dim; ++l)
+        if (!inst[i].periodic[l]) return DG_EUNSUPPORTED;
+    }
   }
   dg_physics ph = *phys;  // with the shock-capturing defaults filled in
   if (ph.shock) {
@@ -1178,6 +1220,13 @@ dg_status dg_init_mesh(const dg_mesh_desc* inst, int n_inst, const dg_physics* p
         return DG_ECUDA;
       }
     }
+    if (any_curved) {
+      dg_status st = setup_curved(c, inst, n_inst, off, false);
+      if (st) {
+        dg_free(c);
+        return st;
+      }
+    }
     *out = c;
     return DG_OK;
   }
@@ -1190,33 +1239,10 @@ dg_status dg_init_mesh(const dg_mesh_desc* inst, int n_inst, const dg_physics* p
     }
   }
   if (any_curved) {
-    const int nm = c->dim * c->dim + 1;
-    std::vector<double> met((size_t)nm * off, 0.0);
-    c->curved.assign(n_inst, 0);
-    c->curved_dx.assign(n_inst, 0.0);
-    for (int i = 0; i < n_inst; ++i) {
-      if (!inst[i].coords) continue;
-      c->curved[i] = 1;
-      if (!curved_metrics_host(inst[i], met.data(), off, c->offs[i], c->curved_dx[i])) {
-        dg_free(c);
-        return DG_EINVAL;  // an element with J <= 0
-      }
-      if (dg::launch_curved(inst[i].dim, inst[i].N, phys->volume == DG_VOL_EC,
-                            phys->precision == DG_FP32_MIXED, nullptr, nullptr, nullptr) != cudaSuccess) {
-        cudaGetLastError();
-        dg_free(c);
-        return DG_ECUDA;
-      }
-    }
-    if (cudaMalloc(&c->met, sizeof(double) * met.size()) != cudaSuccess) {
-      cudaGetLastError();
+    dg_status st = setup_curved(c, inst, n_inst, off, true);
+    if (st) {
       dg_free(c);
-      return DG_ENOMEM;
-    }
-    if (cudaMemcpy(c->met, met.data(), sizeof(double) * met.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
-      cudaGetLastError();
-      dg_free(c);
-      return DG_ECUDA;
+      return st;
     }
     *out = c;  // curved instances are launched per instance
     return DG_OK;
@@ -1582,6 +1608,7 @@ dg_status dg_max_dt(dg_ctx* c, double cfl, double* dt_out) {
       if (!(lam > 0.0)) return fail(c, DG_ENONFINITE, "no positive signal speed");
       double dxmin = INFINITY;
       for (int l = 0; l < m.dim; ++l) dxmin = std::fmin(dxmin, (m.hi[l] - m.lo[l]) / m.nel[l]);
+      if (!c->curved.empty() && c->curved[i]) dxmin = c->curved_dx[i];  // 2 J / |Ja^l| on curved meshes
       const double n2 = (2.0 * m.N + 1.0) * (2.0 * m.N + 1.0);
       const double nu = c->phys.mu * irho / std::fmin(1.0, c->phys.prandtl);
       const double cs = cfl * ssp_coefficient(c);

@@ -298,6 +298,10 @@ struct ReactArgs {
   float sf[3], liftf, muf, kfacf, p_reff;  // the same scalars for the FP32 flux arithmetic
   double D[(kMaxReactingN + 1) * (kMaxReactingN + 1)];
   ReactBC bnd;          // boundary conditions of the instance
+  // curved instance (periodic): the metric terms Ja^l_d at row l*3+d, then 1/J at row 9, at
+  // the state's node stride (s = 1: the 2/dx_l of a Cartesian element are in Ja^l); null:
+  // Cartesian
+  const double* met;
 };
 
 // Whether the reacting kernels exist for degree N, n_species and the temperature model

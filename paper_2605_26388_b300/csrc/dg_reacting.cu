@@ -326,6 +326,63 @@ __device__ __forceinline__ void br1_gradient(int q, const R* W, const R* Wt, con
   }
 }
 
+// ---- curved elements (Sec. 3.1.1 metric terms; Sec. 3.1.2 BR1 on the mapped element) ----
+// The node's contravariant vectors Ja[l][d] and 1/J from the metric rows (FP64, converted to
+// the flux precision).
+template <class R>
+__device__ __forceinline__ void node_metric(const ReactArgs& a, long long gi, R (&Ja)[3][3], R& iJ) {
+#pragma unroll
+  for (int l = 0; l < 3; ++l)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) Ja[l][d] = Ar<R>::load(a.met[(long long)(l * 3 + d) * a.stride + gi]);
+  iJ = Ar<R>::load(a.met[9 * a.stride + gi]);
+}
+// The contravariant vector Ja^l of the node (one direction).
+template <class R>
+__device__ __forceinline__ void node_metric_dir(const ReactArgs& a, long long gi, int l, R (&ja)[3]) {
+#pragma unroll
+  for (int d = 0; d < 3; ++d) ja[d] = Ar<R>::load(a.met[(long long)(l * 3 + d) * a.stride + gi]);
+}
+// Physical gradient from the reference-space BR1 derivative (br1_gradient with s = 1):
+// S_d = (1/J) sum_l Ja^l_d S_l.
+template <int NW, class R>
+__device__ __forceinline__ void to_physical(const R (&Ja)[3][3], R iJ, R (&S)[NW][3]) {
+#pragma unroll
+  for (int c = 0; c < NW; ++c) {
+    R p[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) p[d] = iJ * (Ja[0][d] * S[c][0] + Ja[1][d] * S[c][1] + Ja[2][d] * S[c][2]);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) S[c][d] = p[d];
+  }
+}
+// Contravariant viscous flux sum_d ja_d F_v^d.
+template <int NW, int NFV, class R>
+__device__ __forceinline__ void visc_flux_contra(const R (&S)[NW][3], const R* v, R mu, R kcond, R kvib,
+                                                 const R (&ja)[3], R* Fv) {
+  R F0[NFV], F1[NFV], F2[NFV];
+  visc_flux<0, NW, R>(S, v, mu, kcond, kvib, F0);
+  visc_flux<1, NW, R>(S, v, mu, kcond, kvib, F1);
+  visc_flux<2, NW, R>(S, v, mu, kcond, kvib, F2);
+#pragma unroll
+  for (int c = 0; c < NFV; ++c) Fv[c] = ja[0] * F0[c] + ja[1] * F1[c] + ja[2] * F2[c];
+}
+// Contravariant inviscid flux sum_d ja_d F^d of the mixture.
+template <int NS, bool TT, class R>
+__device__ __forceinline__ void inv_flux_contra(const R* u, R v0, R v1, R v2, R pd, R p_ref, const R (&ja)[3],
+                                                R* F) {
+  constexpr int NV = NS + 4 + (TT ? 1 : 0);
+  R Fd[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) F[k] = R(0);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    inv_flux<NS, TT, R>(d, u, v0, v1, v2, pd, p_ref, Fd);
+#pragma unroll
+    for (int k = 0; k < NV; ++k) F[k] = F[k] + ja[d] * Fd[k];
+  }
+}
+
 // Ghost neighbour value of the viscous face flux (momentum rows, energy) at a domain face
 // with normal axis L, from the element's own flux Fv and its conduction part heat = k dT/dx_L,
 // such that the BR1 average (Fv + gh)/2 is the boundary's viscous flux (Sec. 3.1.2 boundary
@@ -550,7 +607,10 @@ __device__ __forceinline__ void load_element(const ReactArgs& a, int e0, R* smem
 // ---------------------------------------------------------------------------------------
 // Launch 1: BR1 gradients and the element's own viscous flux on its faces.
 // ---------------------------------------------------------------------------------------
-template <int N, int NS, bool TT, class R>
+// CURV: a curved instance -- the reference-space derivative is mapped to the physical
+// gradient with the node's contravariant vectors and 1/J, and the face flux written is the
+// contravariant one, sum_d Ja^l_d F_v^d (the face's Ja^l is the same on both sides).
+template <int N, int NS, bool TT, class R, bool CURV>
 __global__ void __launch_bounds__(kRT) k_br1_faces(const ReactArgs a) {
   using G = RG<N, NS, TT, R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -571,6 +631,12 @@ __global__ void __launch_bounds__(kRT) k_br1_faces(const ReactArgs a) {
   const R* sm = el_base + el * G::G_SIZE;
   R S[G::NW][3];
   br1_gradient<N, G::NW, G::NPR, R>(q, sm + G::G_P, sm + G::G_PT, D, rs.s, rs.lift, S);
+  R Ja[3][3];
+  if constexpr (CURV) {
+    R iJ;
+    node_metric<R>(a, a.base + (long long)e * G::NP + q, Ja, iJ);
+    to_physical<G::NW, R>(Ja, iJ, S);
+  }
   const R v[3] = {sm[G::G_P + q], sm[G::G_P + G::NP + q], sm[G::G_P + 2 * G::NP + q]};
   const R kcond = rs.kfac * Ar<R>::load(cpT[0]);
   const R kvib = rs.kfac * Ar<R>::load(cpT[2]);
@@ -578,7 +644,8 @@ __global__ void __launch_bounds__(kRT) k_br1_faces(const ReactArgs a) {
   R Fv[G::NFV];
 #define DG_FACE_OUT(L)                                                                       \
   if (ijk[L] == 0 || ijk[L] == N) {                                                          \
-    visc_flux<L, G::NW, R>(S, v, rs.mu, kcond, kvib, Fv);                                    \
+    if constexpr (CURV) visc_flux_contra<G::NW, G::NFV, R>(S, v, rs.mu, kcond, kvib, Ja[L], Fv); \
+    else visc_flux<L, G::NW, R>(S, v, rs.mu, kcond, kvib, Fv);                               \
     const int jf = L == 0 ? ijk[1] + G::N1 * ijk[2]                                          \
                           : (L == 1 ? ijk[0] + G::N1 * ijk[2] : ijk[0] + G::N1 * ijk[1]);     \
     R* dst = fbe + (2 * L + (ijk[L] == N ? 1 : 0)) * G::NFV * G::NFN + jf;                   \
@@ -593,7 +660,11 @@ __global__ void __launch_bounds__(kRT) k_br1_faces(const ReactArgs a) {
 // ---------------------------------------------------------------------------------------
 // Launch 2: the fused stage.
 // ---------------------------------------------------------------------------------------
-template <int N, int NS, bool TT, class R>
+// CURV: a curved instance (periodic) -- the physical gradient from the node's metric, the
+// contravariant fluxes sum_d Ja^l_d F^d in the volume term, the Rusanov flux along the
+// contravariant normal n = Ja^l / |Ja^l| scaled by |Ja^l| at the faces, the whole transport
+// residual times 1/J (Sec. 3.1.1, Eq. vol_weak with the contravariant flux; Sec. 3.1.2).
+template <int N, int NS, bool TT, class R, bool CURV>
 __global__ void __launch_bounds__(kRT) k_reacting_stage(const ReactArgs a) {
   using G = RG<N, NS, TT, R>;
   constexpr int N1 = G::N1, NP = G::NP, NFN = G::NFN, NV = G::NV, NFV = G::NFV, NPR = G::NPR;
@@ -640,6 +711,7 @@ __global__ void __launch_bounds__(kRT) k_reacting_stage(const ReactArgs a) {
   const int ijk[3] = {q % N1, (q / N1) % N1, q / NFN};
   R u[NV], res[NV], v[3], pd = R(0), kcond = R(0), kvib = R(0);
   R S[G::NW][3];
+  R Ja[3][3], iJ = R(1);
 #pragma unroll
   for (int k = 0; k < NV; ++k) res[k] = R(0);
   if (active) {
@@ -651,14 +723,23 @@ __global__ void __launch_bounds__(kRT) k_reacting_stage(const ReactArgs a) {
     kcond = rs.kfac * Ar<R>::load(cpT[0]);
     kvib = rs.kfac * Ar<R>::load(cpT[2]);
     br1_gradient<N, G::NW, NPR, R>(q, sm + G::E_P, sm + G::E_PT, D, rs.s, rs.lift, S);
+    if constexpr (CURV) {
+      node_metric<R>(a, a.base + (long long)e * NP + q, Ja, iJ);
+      to_physical<G::NW, R>(Ja, iJ, S);
+    }
   }
   // volume term, one direction at a time through the H buffer
 #define DG_VOLUME_DIR(L)                                                                      \
   {                                                                                           \
     if (active) {                                                                             \
       R F[NV], Fv[NFV];                                                                       \
-      inv_flux<NS, TT, R>(L, u, v[0], v[1], v[2], pd, rs.p_ref, F);                           \
-      visc_flux<L, G::NW, R>(S, v, rs.mu, kcond, kvib, Fv);                                   \
+      if constexpr (CURV) {                                                                   \
+        inv_flux_contra<NS, TT, R>(u, v[0], v[1], v[2], pd, rs.p_ref, Ja[L], F);              \
+        visc_flux_contra<G::NW, NFV, R>(S, v, rs.mu, kcond, kvib, Ja[L], Fv);                 \
+      } else {                                                                                \
+        inv_flux<NS, TT, R>(L, u, v[0], v[1], v[2], pd, rs.p_ref, F);                         \
+        visc_flux<L, G::NW, R>(S, v, rs.mu, kcond, kvib, Fv);                                 \
+      }                                                                                       \
       _Pragma("unroll") for (int c = 0; c < NFV; ++c) F[NS + c] -= Fv[c];                     \
       _Pragma("unroll") for (int k = 0; k < NV; ++k) sm[G::E_H + k * NP + q] = F[k];          \
       if (ijk[L] == 0 || ijk[L] == N) {                                                       \
@@ -713,6 +794,31 @@ __global__ void __launch_bounds__(kRT) k_reacting_stage(const ReactArgs a) {
     }
     const R* po = fs + G::E_P + qo;
     const R* pn = fs + G::E_PT + f * NPR * NFN + jf;
+    if constexpr (CURV) {  // periodic: the neighbour's trace; Rusanov along n = Ja^l / |Ja^l|
+      R ja[3], nrm[3];
+      node_metric_dir<R>(a, a.base + (long long)(e0 + fel) * NP + qo, l, ja);
+      const R sj = Ar<R>::sqrt(ja[0] * ja[0] + ja[1] * ja[1] + ja[2] * ja[2]);
+      const R isj = R(1) / sj;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) nrm[d] = ja[d] * isj;
+      R Fo[NV], Fn[NV];
+      inv_flux_contra<NS, TT, R>(uo, po[0], po[NP], po[2 * NP], po[G::RPD * NP], rs.p_ref, nrm, Fo);
+      inv_flux_contra<NS, TT, R>(un, pn[0], pn[NFN], pn[2 * NFN], pn[G::RPD * NFN], rs.p_ref, nrm, Fn);
+      const R vno = nrm[0] * po[0] + nrm[1] * po[NP] + nrm[2] * po[2 * NP];
+      const R vnn = nrm[0] * pn[0] + nrm[1] * pn[NFN] + nrm[2] * pn[2 * NFN];
+      const R lam = Ar<R>::fmax(Ar<R>::abs(vno) + po[G::RA * NP], Ar<R>::abs(vnn) + pn[G::RA * NFN]);
+      const R hl = side ? R(0.5) * lam : R(-0.5) * lam;
+      R dlt[NV];
+#pragma unroll
+      for (int k = 0; k < NV; ++k) dlt[k] = sj * (R(0.5) * (Fn[k] - Fo[k]) - hl * (un[k] - uo[k]));
+#pragma unroll
+      for (int c = 0; c < NFV; ++c)
+        dlt[NS + c] = dlt[NS + c] - R(0.5) * (fs[G::E_FT + f * NFV * NFN + c * NFN + jf] -
+                                              fs[G::E_FO + f * NFV * NFN + c * NFN + jf]);
+#pragma unroll
+      for (int k = 0; k < NV; ++k) fs[G::E_UT + (f * NV + k) * NFN + jf] = dlt[k];
+      continue;
+    }
     R Fo[NV], Fn[NV];
     inv_flux<NS, TT, R>(l, uo, po[0], po[NP], po[2 * NP], po[G::RPD * NP], rs.p_ref, Fo);
     // the exterior state: the neighbour's trace, or at a domain face the boundary functor's
@@ -780,6 +886,10 @@ __global__ void __launch_bounds__(kRT) k_reacting_stage(const ReactArgs a) {
     const R* ls = sm + G::E_UT + (2 * l + side) * NV * NFN + jf;
 #pragma unroll
     for (int k = 0; k < NV; ++k) res[k] = res[k] + c * ls[k * NFN];
+  }
+  if constexpr (CURV) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) res[k] = res[k] * iJ;
   }
   double r64[NV];
 #pragma unroll
@@ -1312,27 +1422,38 @@ __global__ void k_max_speed_mix(const double* U, long long stride, long long bas
   }
 }
 
-template <int N, int NS, bool TT, class R>
-cudaError_t prepare_one() {
+template <int N, int NS, bool TT, class R, bool CURV>
+cudaError_t prepare_kernels() {
   using G = RG<N, NS, TT, R>;
-  cudaError_t e = cudaFuncSetAttribute(k_reacting_stage<N, NS, TT, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)G::stage_smem());
+  cudaError_t e = cudaFuncSetAttribute(k_reacting_stage<N, NS, TT, R, CURV>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::stage_smem());
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_br1_faces<N, NS, TT, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(k_br1_faces<N, NS, TT, R, CURV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)G::grad_smem());
   return e;
 }
 
 template <int N, int NS, bool TT, class R>
-cudaError_t launch_one(const ReactArgs& a, cudaStream_t s) {
+cudaError_t prepare_one() {
+  cudaError_t e = prepare_kernels<N, NS, TT, R, false>();
+  return e == cudaSuccess ? prepare_kernels<N, NS, TT, R, true>() : e;
+}
+
+template <int N, int NS, bool TT, class R, bool CURV>
+cudaError_t launch_kernels(const ReactArgs& a, cudaStream_t s) {
   using G = RG<N, NS, TT, R>;
-  if (a.n_elem <= 0) return cudaSuccess;
   const unsigned grid = (unsigned)((a.n_elem + G::EPB - 1) / G::EPB);
-  k_br1_faces<N, NS, TT, R><<<grid, kRT, G::grad_smem(), s>>>(a);
+  k_br1_faces<N, NS, TT, R, CURV><<<grid, kRT, G::grad_smem(), s>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_reacting_stage<N, NS, TT, R><<<grid, kRT, G::stage_smem(), s>>>(a);
+  k_reacting_stage<N, NS, TT, R, CURV><<<grid, kRT, G::stage_smem(), s>>>(a);
   return cudaGetLastError();
+}
+
+template <int N, int NS, bool TT, class R>
+cudaError_t launch_one(const ReactArgs& a, cudaStream_t s) {
+  if (a.n_elem <= 0) return cudaSuccess;
+  return a.met ? launch_kernels<N, NS, TT, R, true>(a, s) : launch_kernels<N, NS, TT, R, false>(a, s);
 }
 
 // (N, n_species, two-temperature) instantiations: one species (the non-dimensional single

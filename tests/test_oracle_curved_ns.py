@@ -182,3 +182,18 @@ def test_linear_field_gradient_is_exact_on_a_warped_2d_mesh(orc):
             assert np.max(np.abs(G[:, :, c, d] - a[c, 1 + d])) <= 1e-10 * np.abs(a).max(), (c, d)
     assert np.max(np.abs(G[:, :, 3, 0] - 200.0)) <= 1e-9 * 300.0
     assert np.max(np.abs(G[:, :, 3, 1] + 300.0)) <= 1e-9 * 300.0
+
+
+def test_time_step_bound_of_an_affine_map_is_the_cartesian_one(orc):
+    """The curved spacing 2 J / |Ja^l| reduces to dx_l on an axis-aligned affine map, for the
+    convective and the diffusive bound (Eq. dt_hyp, Eq. dt_para)."""
+    m = air()
+    lo, hi = ANISO[3]
+    N, nel = 3, 3
+    xi, _ = orc.gll(N)
+    X = wl.node_coordinates(3, (nel,) * 3, lo, hi, xi)
+    U = tgv_state(orc, m, 3, N, nel, lo, hi)
+    for mu in (3e-3, 40.0):
+        ref = orc.max_dt(problem(orc, m, 3, N, nel, lo, hi, mu=mu), U, 0.3)
+        got = orc.max_dt(problem(orc, m, 3, N, nel, lo, hi, mu=mu, coords=X), U, 0.3)
+        assert abs(got - ref) <= 1e-13 * ref, mu
