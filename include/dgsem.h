@@ -2,8 +2,8 @@
  *
  * The library evaluates the semi-discrete DGSEM residual of the compressible Euler
  * equations, and of the single-temperature reacting Navier-Stokes equations, on Cartesian
- * meshes (periodic, or with per-face boundary conditions; Euler also on curved periodic
- * meshes) and advances it with the SSP-RK33 or SSP-RK54 scheme, entirely in
+ * meshes (periodic, or with per-face boundary conditions) and on curved meshes (periodic
+ * ones for Navier-Stokes) and advances it with the SSP-RK33 or SSP-RK54 scheme, entirely in
  * hand-written CUDA kernels (one fused kernel per RK stage for Euler; a BR1 gradient pass
  * plus one fused kernel for Navier-Stokes; one per-node kernel for the implicit chemistry
  * substep of the Strang split).  The operations follow arXiv 2605.26388:
@@ -147,10 +147,12 @@ typedef struct {
                            * coords[d * n_elem * n_p + e * n_p + q], copied at dg_init_mesh.
                            * Periodic directions must map periodically; a non-periodic direction
                            * takes its boundary conditions along the faces' contravariant normal
-                           * (the slip wall mirrors the velocity across it).  DG_EULER only,
-                           * strong or two-point volume form, no shock capturing, no positivity
-                           * floor (else DG_EUNSUPPORTED); every element must have J > 0 (else
-                           * DG_EINVAL). */
+                           * (the slip wall mirrors the velocity across it).  DG_EULER: strong
+                           * or two-point volume form.  The viscous equations: periodic in every
+                           * direction, no species limiter (Sec. 3.1.2 BR1 on the mapped
+                           * element: the reference derivative mapped by Ja^l and 1/J).  No
+                           * shock capturing, no positivity floor (else DG_EUNSUPPORTED); every
+                           * element must have J > 0 (else DG_EINVAL). */
 } dg_mesh_desc;
 
 /* Species and reactions of a reacting mixture (Sec. 2 thermochemistry, single temperature;
