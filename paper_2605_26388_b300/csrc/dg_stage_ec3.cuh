@@ -103,7 +103,8 @@ struct EC3 {
   // of KTAIL, so that the CTAs, taking the runs in order, finish within a few elements of one
   // another.  Run q starts at element *e0 and holds *len elements; false past the last run.
   static constexpr int KTAIL = 4;
-  static __device__ __forceinline__ bool run_of(const InstArgs& I, int q, int* e0, int* len) {
+  static __device__ __forceinline__ bool run_of(const InstArgs& I, int q, int* e0, int* len, int* x0out,
+                                                int* rowout) {
     const int nx = I.nel[0], nrows = I.nel[1] * I.nel[2];
     const int tail = (2 * (int)gridDim.x * KRUN + nx - 1) / nx;
     const int ra = tail < nrows ? nrows - tail : 0;  // rows in runs of KRUN
@@ -123,6 +124,8 @@ struct EC3 {
     }
     *e0 = x0 + nx * row;
     *len = min(k, nx - x0);
+    *x0out = x0;
+    *rowout = row;
     return true;
   }
 
@@ -131,16 +134,25 @@ struct EC3 {
   // still taken up roughly in element order -- the elements in flight stay within a band of
   // the mesh, as with a cyclic deal -- and no CTA ends with a run more than another (without
   // a counter, runs blockIdx.x + k gridDim.x).  Position m within the run.
+  // (with the x index x0 of the run's first element and the row's y and z indices, for the
+  // neighbour table without divisions per element)
   struct Walk {
-    int run, m, e0, len;
+    int run, m, e0, len, x0, y, z;
     bool ok;
     __device__ __forceinline__ int elem() const { return ok ? e0 + m : -1; }
   };
+  static __device__ __forceinline__ bool locate(const InstArgs& I, Walk& w) {
+    int row = 0;
+    if (!run_of(I, w.run, &w.e0, &w.len, &w.x0, &row)) return false;
+    w.y = row % I.nel[1];
+    w.z = row / I.nel[1];
+    return true;
+  }
   static __device__ __forceinline__ Walk walk_start(const InstArgs& I) {
     Walk w;
     w.run = blockIdx.x;
     w.m = 0;
-    w.ok = run_of(I, w.run, &w.e0, &w.len);
+    w.ok = locate(I, w);
     return w;
   }
   // the next element; at the end of a run the walk moves to run `next` (the run claimed
@@ -154,7 +166,7 @@ struct EC3 {
     w.run = next;
     *used = true;
     w.m = 0;
-    w.ok = run_of(I, w.run, &w.e0, &w.len);
+    w.ok = locate(I, w);
     return w;
   }
   // a run index for the walk to take after `run`: claimed from the counter, or the cyclic deal
@@ -208,9 +220,23 @@ struct EC3 {
     }
   }
 
-  static __device__ __forceinline__ void fill_nb(const InstArgs& I, int e, int* nb) {
+  // neighbour table of the walk's element (periodic wrap), from its indices
+  static __device__ __forceinline__ void fill_nb(const InstArgs& I, const Walk& w, int* nb) {
     const int t = threadIdx.x;
-    if (t < NF) nb[t] = neighbour(I, e, t);
+    if (t < NF) {
+      const int nx = I.nel[0], ny = I.nel[1], nz = I.nel[2], e = w.e0 + w.m, x = w.x0 + w.m;
+      const int sxy = nx * ny;
+      int n;
+      switch (t) {
+        case 0: n = x > 0 ? e - 1 : e + (nx - 1); break;
+        case 1: n = x < nx - 1 ? e + 1 : e - (nx - 1); break;
+        case 2: n = w.y > 0 ? e - nx : e + nx * (ny - 1); break;
+        case 3: n = w.y < ny - 1 ? e + nx : e - nx * (ny - 1); break;
+        case 4: n = w.z > 0 ? e - sxy : e + sxy * (nz - 1); break;
+        default: n = w.z < nz - 1 ? e + sxy : e - sxy * (nz - 1); break;
+      }
+      nb[t] = n;
+    }
   }
 
   // ---- two-point pairs (cyclic ownership, as EulerStage) ----
@@ -561,8 +587,8 @@ struct EC3 {
       used = false;
     }
     Walk wnn = walk_next(I, wn, s_next, &used);
-    if (w.ok) fill_nb(I, w.elem(), nb);
-    if (wn.ok) fill_nb(I, wn.elem(), nb + NF);
+    if (w.ok) fill_nb(I, w, nb);
+    if (wn.ok) fill_nb(I, wn, nb + NF);
     __syncthreads();
     if (w.ok) {
       issue_own(A, I, w.elem(), st);
@@ -583,7 +609,7 @@ struct EC3 {
       if (wn.ok) issue_traces(A, I, r, st + (b ^ 1) * ST_SIZE, nb + (b ^ 1) * NF);
       cp_async_commit();
       if (wnn.ok) {
-        fill_nb(I, wnn.elem(), nb + b * NF);  // read by the next iteration's issue
+        fill_nb(I, wnn, nb + b * NF);  // read by the next iteration's issue
         prefetch_own(A, I, wnn.elem());
       }
       // the x- face is carried from the previous iteration, which handled element e - 1 of
