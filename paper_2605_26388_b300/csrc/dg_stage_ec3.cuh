@@ -38,7 +38,8 @@ struct EC3 {
   static constexpr int NO = N1 / 2;              // pair offsets per direction (cyclic ownership)
   // FP64 staging, two buffers of: U [NV][NP], traces of faces 1..5 [5][NV][NFN]
   static constexpr int ST_T = NV * NP;
-  static constexpr int ST_SIZE = ST_T + 5 * NV * NFN;
+  static constexpr int ST_XM = ST_T + 5 * NV * NFN;  // x- trace [NV][NFN] (first element of a run)
+  static constexpr int ST_SIZE = ST_XM + NV * NFN;
   // flux-precision arrays
   static constexpr int XSLOT = 4 * NP + al4(NP);           // pair slot: Q4 [NP] then F_4 [NP]
   static constexpr int NS = NF + 1;                        // face slots (x+ alternates 1 / 6)
@@ -87,15 +88,6 @@ struct EC3 {
     r.ndo_m = line_node<0>(fm, 0);
     r.ndn_m = line_node<0>(fm, N);
     return r;
-  }
-
-  // neighbour element across face `face` of element e (periodic wrap)
-  static __device__ __forceinline__ int neighbour(const InstArgs& I, int e, int face) {
-    const int l = face >> 1, d = (face & 1) ? 1 : -1;
-    int c[3] = {e % I.nel[0], (e / I.nel[0]) % I.nel[1], e / (I.nel[0] * I.nel[1])};
-    c[l] += d;
-    c[l] = c[l] < 0 ? c[l] + I.nel[l] : (c[l] >= I.nel[l] ? c[l] - I.nel[l] : c[l]);
-    return c[0] + I.nel[0] * (c[1] + I.nel[1] * c[2]);
   }
 
   // Runs: the rows of elements along x (rows in element order) split into runs of KRUN
@@ -186,13 +178,18 @@ struct EC3 {
     }
   }
   static __device__ __forceinline__ void issue_traces(const StageArgs& A, const InstArgs& I, const Role& r,
-                                                      double* S, const int* nb) {
+                                                      double* S, const int* nb, bool first) {
     const int t = threadIdx.x;
     if (t < NJ) {
       const double* pt = A.U + I.base + (long long)nb[r.face] * NP + r.ndn;
       double* st = S + ST_T + (r.face - 1) * NV * NFN + r.f;
 #pragma unroll
       for (int v = 0; v < NV; ++v) cp_async8(st + v * NFN, pt + v * A.stride);
+    }
+    if (first && t < NFN) {  // the first element of a run evaluates its x- face too
+      const double* pt = A.U + I.base + (long long)nb[0] * NP + r.ndn_m;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) cp_async8(S + ST_XM + v * NFN + t, pt + v * A.stride);
     }
   }
 
@@ -465,11 +462,11 @@ struct EC3 {
       if (node) pairs();
       if (t < NJ) face();
     }
-    if (!carry && t < NFN) {  // the x- face (start of a run or of an x line): its own job
-      const double* pt = A.U + I.base + (long long)neighbour(I, e, 0) * NP + r.ndn_m;
+    if (!carry && t < NFN) {  // the x- face (start of a run): its own job, trace staged by
+                              // this thread
       double n64[NV];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) n64[v] = __ldg(pt + v * A.stride);
+      for (int v = 0; v < NV; ++v) n64[v] = S[ST_XM + v * NFN + t];
       face_flux(sm, A, I, e, 0, 0, r.ndo_m, n64, 0, t);
     }
   }
@@ -592,7 +589,7 @@ struct EC3 {
     __syncthreads();
     if (w.ok) {
       issue_own(A, I, w.elem(), st);
-      issue_traces(A, I, r, st, nb);
+      issue_traces(A, I, r, st, nb, true);
     }
     cp_async_commit();
     cp_async_wait_all();
@@ -606,7 +603,7 @@ struct EC3 {
       // waits for the first only, the traces have until the next iteration's face jobs.
       if (wn.ok) issue_own(A, I, wn.elem(), st + (b ^ 1) * ST_SIZE);
       cp_async_commit();
-      if (wn.ok) issue_traces(A, I, r, st + (b ^ 1) * ST_SIZE, nb + (b ^ 1) * NF);
+      if (wn.ok) issue_traces(A, I, r, st + (b ^ 1) * ST_SIZE, nb + (b ^ 1) * NF, wn.m == 0);
       cp_async_commit();
       if (wnn.ok) {
         fill_nb(I, wnn, nb + b * NF);  // read by the next iteration's issue
