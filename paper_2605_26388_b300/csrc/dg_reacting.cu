@@ -356,31 +356,44 @@ __device__ __forceinline__ void to_physical(const R (&Ja)[3][3], R iJ, R (&S)[NW
     for (int d = 0; d < 3; ++d) S[c][d] = p[d];
   }
 }
-// Contravariant viscous flux sum_d ja_d F_v^d.
+// Contravariant viscous flux sum_d ja_d F_v^d, formed directly: the stress tensor applied to
+// ja, the work of that traction, the conduction of the temperature gradient along ja.
 template <int NW, int NFV, class R>
 __device__ __forceinline__ void visc_flux_contra(const R (&S)[NW][3], const R* v, R mu, R kcond, R kvib,
                                                  const R (&ja)[3], R* Fv) {
-  R F0[NFV], F1[NFV], F2[NFV];
-  visc_flux<0, NW, R>(S, v, mu, kcond, kvib, F0);
-  visc_flux<1, NW, R>(S, v, mu, kcond, kvib, F1);
-  visc_flux<2, NW, R>(S, v, mu, kcond, kvib, F2);
+  const R div = S[0][0] + S[1][1] + S[2][2];
+  const R jd = R(2.0 / 3.0) * mu * div;
+  R work = R(0);
 #pragma unroll
-  for (int c = 0; c < NFV; ++c) Fv[c] = ja[0] * F0[c] + ja[1] * F1[c] + ja[2] * F2[c];
+  for (int j = 0; j < 3; ++j) {
+    R t = R(0);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) t = t + ja[d] * (mu * (S[j][d] + S[d][j]));
+    t = t - jd * ja[j];
+    Fv[j] = t;
+    work = work + v[j] * t;
+  }
+  Fv[3] = work + kcond * (ja[0] * S[3][0] + ja[1] * S[3][1] + ja[2] * S[3][2]);
+  if constexpr (NW == 5) {
+    const R qv = kvib * (ja[0] * S[4][0] + ja[1] * S[4][1] + ja[2] * S[4][2]);
+    Fv[3] = Fv[3] + qv;
+    Fv[4] = qv;
+  }
+  (void)kvib;
 }
-// Contravariant inviscid flux sum_d ja_d F^d of the mixture.
+// Contravariant inviscid flux sum_d ja_d F^d of the mixture, formed directly with the
+// contravariant velocity ja . v.
 template <int NS, bool TT, class R>
 __device__ __forceinline__ void inv_flux_contra(const R* u, R v0, R v1, R v2, R pd, R p_ref, const R (&ja)[3],
                                                 R* F) {
-  constexpr int NV = NS + 4 + (TT ? 1 : 0);
-  R Fd[NV];
+  const R vn = ja[0] * v0 + ja[1] * v1 + ja[2] * v2;
 #pragma unroll
-  for (int k = 0; k < NV; ++k) F[k] = R(0);
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    inv_flux<NS, TT, R>(d, u, v0, v1, v2, pd, p_ref, Fd);
-#pragma unroll
-    for (int k = 0; k < NV; ++k) F[k] = F[k] + ja[d] * Fd[k];
-  }
+  for (int s = 0; s < NS; ++s) F[s] = u[s] * vn;
+  F[NS + 0] = u[NS + 0] * vn + ja[0] * pd;
+  F[NS + 1] = u[NS + 1] * vn + ja[1] * pd;
+  F[NS + 2] = u[NS + 2] * vn + ja[2] * pd;
+  F[NS + 3] = (u[NS + 3] + (pd + p_ref)) * vn;
+  if constexpr (TT) F[NS + 4] = u[NS + 4] * vn;
 }
 
 // Ghost neighbour value of the viscous face flux (momentum rows, energy) at a domain face
