@@ -193,7 +193,7 @@ struct EC3 {
     }
   }
 
-  // L2 prefetch of the lines that the copies of element e will read an iteration later: its
+  // L2 prefetch of the lines that the copies of element e will read one or two iterations later: its
   // own state (NV x NP doubles, 128-byte lines) and, once its neighbour table nb is visible,
   // the face traces (one line per face node and variable; repeats hit the same line)
   static __device__ __forceinline__ void prefetch_own(const StageArgs& A, const InstArgs& I, int e) {
@@ -607,7 +607,10 @@ struct EC3 {
       cp_async_commit();
       if (wnn.ok) {
         fill_nb(I, wnn, nb + b * NF);  // read by the next iteration's issue
-        prefetch_own(A, I, wnn.elem());
+        // the own state three elements ahead when it lies in the same run (the walk does not
+        // know the run after the claimed one); an element that starts a run gets it two ahead
+        if (wnn.m == 0) prefetch_own(A, I, wnn.elem());
+        if (wnn.m + 1 < wnn.len) prefetch_own(A, I, wnn.elem() + 1);
       }
       // the x- face is carried from the previous iteration, which handled element e - 1 of
       // the same run
