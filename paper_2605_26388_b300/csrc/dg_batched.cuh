@@ -17,7 +17,9 @@ namespace dg {
 // slots (its index was loaded into a register one iteration earlier still), the volume
 // operators of all degrees are held in shared memory for the whole launch, and the next
 // item's neighbour table and coefficient tables are built from those copies before the one
-// barrier per item that also publishes the current item's staged inputs.
+// barrier per item that also publishes the current item's staged inputs.  The own state
+// and U^n of the item two ahead are prefetched to L2 by lines (its group is a contiguous
+// block of each variable); its neighbours' blocks are not (that measured slower).
 // ---------------------------------------------------------------------------------------
 template <int DIM, bool EC, class R, int GS, int N = 1>
 struct BMax {
@@ -155,6 +157,11 @@ __global__ void __launch_bounds__(Batched<DIM, EC, R, GS>::BT, (Batched<DIM, EC,
       const InstArgs& I = sia[s1];
       DG_ON_DEGREE(I.N, K::issue(A, I, K::role(), sitem[s1].y, st + (b ^ 1) * B::MST,
                                  nb + (b ^ 1) * B::MNB, need_un));
+    }
+    if (k + 2 * step < n) {  // item it+2's own state towards L2 (its arguments are visible)
+      const int s2 = (it + 2) % B::RING;
+      const InstArgs& I2 = sia[s2];
+      DG_ON_DEGREE(I2.N, K::prefetch_group(A, I2, sitem[s2].y, need_un));
     }
     const int k3 = k + 3 * step;
     if (k3 < n) {

@@ -319,6 +319,26 @@ struct EulerStage {
     }
   }
 
+  // L2 prefetch of group g's own state and U^n (the EPB * NP consecutive values of each
+  // variable, by 128-byte lines), for the batched walk two groups ahead
+  static __device__ __forceinline__ void prefetch_group(const StageArgs& A, const InstArgs& I, int g,
+                                                        bool need_un) {
+    constexpr int LPV = (EPB * NP * 8 + 127) / 128 + 1;  // lines per variable (unaligned start)
+    const int ne = min(EPB, I.n_elem - g * EPB);
+    if (ne <= 0) return;
+    const int bytes = ne * NP * 8;
+    for (int q = threadIdx.x; q < 2 * NV * LPV; q += blockDim.x) {
+      const int which = q / (NV * LPV), rem = q - which * (NV * LPV);
+      if (which == 1 && !need_un) break;
+      const int v = rem / LPV, l = rem - v * LPV;
+      const double* base = (which ? A.Un : A.U) + I.base + (long long)g * EPB * NP + (long long)v * A.stride;
+      const char* p0 = reinterpret_cast<const char*>(base);
+      const char* p = p0 + 128 * l;
+      const char* last = p0 + (bytes - 1);
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(p < last ? p : last));
+    }
+  }
+
   // ---- phase 2 (EC): this node's own pairs in direction L ----
   template <int L>
   static __device__ __forceinline__ void own_pairs(R* sm, const R* D, const Role& r, int el, R igm1, R p_ref,
