@@ -189,6 +189,7 @@ def lib():
         _lib.orc_max_dt.argtypes = [pp, dp, C.c_double, dp]
         _lib.orc_rhs_jvp.argtypes = [pp, dp, dp, C.c_double, dp, dp]
         _lib.orc_rhs_vjp_brute.argtypes = [pp, dp, dp, dp, dp]
+        _lib.orc_log_mean_jvp.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, dp, dp]
         _lib.orc_rollout_grad.argtypes = [pp, dp, dp, dp, C.c_double, C.c_int, dp, dp]
         _lib.orc_arrhenius.argtypes = [C.POINTER(_Mech), C.c_int, C.c_double, dp, dp]
         _lib.orc_chem_source.argtypes = [pp, dp, dp]
@@ -329,8 +330,10 @@ def rk3(P: Problem, U: np.ndarray, dt: float, n_steps: int) -> np.ndarray:
 
 def rhs_jvp(P: Problem, U: np.ndarray, V=None, gdot: float = 0.0):
     """(L(U), dL) with dL = (dL/dU) V + (dL/dgamma) gdot, by forward-mode dual numbers
-    (strong or weak volume form, Rusanov surface flux).  Pinned by its value against rhs()
-    and its derivative against central differences of rhs()."""
+    (strong, weak or two-point volume form; Rusanov, HLLC or EC surface flux; periodic
+    Cartesian boxes).  Pinned by its value against rhs(), its derivative against central
+    differences of rhs(), the log mean's closed-form derivative and, for the two-point form
+    with the EC surface flux, the vanishing derivative of the entropy production."""
     U = np.ascontiguousarray(U, dtype=np.float64).reshape(P.shape)
     L = np.zeros_like(U)
     dL = np.zeros_like(U)
@@ -341,6 +344,14 @@ def rhs_jvp(P: Problem, U: np.ndarray, V=None, gdot: float = 0.0):
     c = P._c()
     _check(lib().orc_rhs_jvp(C.byref(c), _ptr(U), Vp, gdot, _ptr(L), _ptr(dL)), "rhs_jvp")
     return L, dL
+
+
+def log_mean_jvp(a: float, b: float, da: float, db: float):
+    """(L, dL): the logarithmic mean of a, b (App. A) and its derivative along (da, db),
+    as the dual-number residual evaluates them."""
+    L, dL = np.zeros(1), np.zeros(1)
+    _check(lib().orc_log_mean_jvp(a, b, da, db, _ptr(L), _ptr(dL)), "log_mean_jvp")
+    return float(L[0]), float(dL[0])
 
 
 def rhs_vjp_brute(P: Problem, U: np.ndarray, lam: np.ndarray):

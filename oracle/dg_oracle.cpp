@@ -1743,11 +1743,12 @@ void positivity_floor(const OrcProblem& P, double* U) {
 
 // ---------------------------------------------------------------------------------------
 // Forward-mode derivatives (for checking the adjoint).  A dual number carries a value and
-// one directional derivative; the residual below is the same strong/weak-form + Rusanov
-// residual as above, written once more over a generic scalar T so that evaluating it on
-// duals gives L(U) and the directional derivative dL = (dL/dU) V + (dL/dgamma) gdot exactly
-// (up to rounding).  Non-smooth points: |x| has derivative sign(x) with sign(0) = 0; max(a, b)
-// follows the larger value, the left argument on a tie.
+// one directional derivative; the residual below is the same Euler residual as above
+// (strong, weak or two-point volume form; Rusanov, HLLC or EC surface flux; periodic Cartesian
+// boxes), written once more over a generic scalar T so that evaluating it on duals gives L(U)
+// and the directional derivative dL = (dL/dU) V + (dL/dgamma) gdot exactly (up to rounding).
+// Non-smooth points: |x| has derivative sign(x) with sign(0) = 0; max(a, b) and min(a, b)
+// follow the selected value, the left argument on a tie; HLLC's branch follows the values.
 // ---------------------------------------------------------------------------------------
 struct Dual {
   double v, d;
@@ -1794,8 +1795,109 @@ void rusanov_t(int dim, int l, const T* uL, const T* uR, T gamma, T* F) {
   for (int v = 0; v < dim + 2; ++v) F[v] = T(0.5) * (FL[v] + FR[v]) - T(0.5) * lam * (uR[v] - uL[v]);
 }
 
-// Eq. vol_weak (strong) or its weak form, plus Eq. surf_int with the Rusanov flux, on
-// element e -- the same loops as euler_element_residual.
+inline double val(double a) { return a; }
+inline double val(const Dual& a) { return a.v; }
+inline Dual dlog(Dual a) { return Dual(std::log(a.v), a.d / a.v); }
+inline Dual dmin(Dual a, Dual b) { return (a.v <= b.v) ? a : b; }
+
+// Logarithmic mean (a - b)/(ln a - ln b) (App. A) over T.  With f = (a - b)/(a + b) and
+// u = f^2, ln a - ln b = 2 atanh(f), so the mean equals ((a + b)/2) / (atanh(f)/f), and
+// atanh(f)/f = sum_k u^k / (2k + 1).  Near a = b (u < 1e-4) that series (eleven terms, far
+// below rounding) is used: its derivative stays accurate as a -> b, where the quotient's
+// derivative is a difference of two large terms; at a = b it gives the mean a and the
+// derivative (da + db)/2.  Otherwise the quotient with the logarithm.
+template <class T>
+T log_mean_t(T a, T b) {
+  const T s = a + b, f = (a - b) / s, u = f * f;
+  if (val(u) < 1e-4) {
+    T F = T(1.0 / 21.0);
+    for (int k = 9; k >= 0; --k) F = T(1.0 / (2 * k + 1)) + u * F;
+    return T(0.5) * s / F;
+  }
+  return (a - b) / dlog(a / b);
+}
+
+template <class T>
+void prims_t(int dim, const T* u, T gamma, T* v, T& p) {
+  T kin = T(0.0);
+  for (int d = 0; d < dim; ++d) {
+    v[d] = u[1 + d] / u[0];
+    kin += u[1 + d] * v[d];
+  }
+  p = (gamma - T(1.0)) * (u[dim + 1] - T(0.5) * kin);
+}
+
+// Ranocha's two-point flux in direction e_l over T -- the same formula as ec_flux.
+template <class T>
+void ec_flux_t(int dim, int l, const T* uL, const T* uR, T gamma, T* F) {
+  T vL[3], vR[3], pL, pR;
+  prims_t(dim, uL, gamma, vL, pL);
+  prims_t(dim, uR, gamma, vR, pR);
+  const T rho_ln = log_mean_t(uL[0], uR[0]);
+  const T beta_ln = log_mean_t(uL[0] / pL, uR[0] / pR);
+  T vLvR = T(0.0);
+  for (int d = 0; d < dim; ++d) vLvR += vL[d] * vR[d];
+  const T pavg = T(0.5) * (pL + pR);
+  const T frho = rho_ln * (T(0.5) * (vL[l] + vR[l]));
+  F[0] = frho;
+  for (int d = 0; d < dim; ++d) F[1 + d] = frho * (T(0.5) * (vL[d] + vR[d])) + (d == l ? pavg : T(0.0));
+  F[dim + 1] = frho * (T(1.0) / ((gamma - T(1.0)) * beta_ln) + T(0.5) * vLvR) + T(0.5) * (pL * vR[l] + pR * vL[l]);
+}
+
+// HLLC flux over T -- the same speeds, star states and branches as hllc_flux; the branch is
+// chosen on the values (min/max follow the selected argument, the left one on a tie).
+template <class T>
+void hllc_flux_t(int dim, int l, const T* uL, const T* uR, T gamma, T* F) {
+  const int nv = dim + 2;
+  T vL[3], vR[3], pL, pR;
+  prims_t(dim, uL, gamma, vL, pL);
+  prims_t(dim, uR, gamma, vR, pR);
+  const T sL = dsqrt(uL[0]), sR = dsqrt(uR[0]);
+  const T HL = (uL[dim + 1] + pL) / uL[0], HR = (uR[dim + 1] + pR) / uR[0];
+  T vt[3], v2 = T(0.0);
+  for (int d = 0; d < dim; ++d) {
+    vt[d] = (sL * vL[d] + sR * vR[d]) / (sL + sR);
+    v2 += vt[d] * vt[d];
+  }
+  const T Ht = (sL * HL + sR * HR) / (sL + sR);
+  const T at = dsqrt((gamma - T(1.0)) * (Ht - T(0.5) * v2));
+  const T aL = dsqrt(gamma * pL / uL[0]), aR = dsqrt(gamma * pR / uR[0]);
+  const T SL = dmin(vL[l] - aL, vt[l] - at), SR = dmax(vR[l] + aR, vt[l] + at);
+  T FL[8], FR[8];
+  flux_t(dim, l, uL, gamma, FL);
+  flux_t(dim, l, uR, gamma, FR);
+  const T Ss = (pR - pL + uL[0] * vL[l] * (SL - vL[l]) - uR[0] * vR[l] * (SR - vR[l])) /
+               (uL[0] * (SL - vL[l]) - uR[0] * (SR - vR[l]));
+  auto star = [&](const T* uK, const T* vK, T pK, T SK, T* Us) {
+    const T fac = uK[0] * (SK - vK[l]) / (SK - Ss);
+    Us[0] = fac;
+    for (int d = 0; d < dim; ++d) Us[1 + d] = fac * (d == l ? Ss : vK[d]);
+    Us[dim + 1] = fac * (uK[dim + 1] / uK[0] + (Ss - vK[l]) * (Ss + pK / (uK[0] * (SK - vK[l]))));
+  };
+  T Us[8];
+  if (val(SL) >= 0.0) {
+    for (int v = 0; v < nv; ++v) F[v] = FL[v];
+  } else if (val(Ss) >= 0.0) {
+    star(uL, vL, pL, SL, Us);
+    for (int v = 0; v < nv; ++v) F[v] = FL[v] + SL * (Us[v] - uL[v]);
+  } else if (val(SR) > 0.0) {
+    star(uR, vR, pR, SR, Us);
+    for (int v = 0; v < nv; ++v) F[v] = FR[v] + SR * (Us[v] - uR[v]);
+  } else {
+    for (int v = 0; v < nv; ++v) F[v] = FR[v];
+  }
+}
+
+template <class T>
+void surface_flux_t(int kind, int dim, int l, const T* uL, const T* uR, T gamma, T* F) {
+  if (kind == ORC_SURF_HLLC) hllc_flux_t(dim, l, uL, uR, gamma, F);
+  else if (kind == ORC_SURF_EC) ec_flux_t(dim, l, uL, uR, gamma, F);
+  else rusanov_t(dim, l, uL, uR, gamma, F);
+}
+
+// Eq. vol_weak (strong) or its weak form, or Eq. vol_split with Ranocha's flux, plus
+// Eq. surf_int with the Rusanov, HLLC or EC flux, on element e -- the same loops as
+// euler_element_residual.
 template <class T>
 void element_residual_t(const OrcProblem& P, const Mesh& M, const Ops& ops, const T* U, T gamma,
                         int e, T* dU) {
@@ -1805,10 +1907,12 @@ void element_residual_t(const OrcProblem& P, const Mesh& M, const Ops& ops, cons
     for (int v = 0; v < nv; ++v) u[v] = U[((size_t)v * M.n_elem + el) * M.n_nodes + nd];
   };
   const bool weak = (P.volume == ORC_VOL_WEAK);
-  T um[8], F[8];
+  const bool ec = (P.volume == ORC_VOL_EC);
+  T ui[8], um[8], F[8];
   for (int nd = 0; nd < M.n_nodes; ++nd) {
     int ijk[3];
     M.node_coords(nd, ijk);
+    load(e, nd, ui);
     for (int l = 0; l < dim; ++l) {
       const double s = 2.0 / M.dx[l];
       const int il = ijk[l];
@@ -1816,8 +1920,10 @@ void element_residual_t(const OrcProblem& P, const Mesh& M, const Ops& ops, cons
         int mk[3] = {ijk[0], ijk[1], ijk[2]};
         mk[l] = m;
         load(e, M.node(mk), um);
-        flux_t(dim, l, um, gamma, F);
-        const double c = weak ? -s * (ops.w[m] / ops.w[il]) * ops.D[m * n1 + il] : s * ops.D[il * n1 + m];
+        if (ec) ec_flux_t(dim, l, ui, um, gamma, F);
+        else flux_t(dim, l, um, gamma, F);
+        const double c = ec ? 2.0 * s * ops.D[il * n1 + m]
+                            : (weak ? -s * (ops.w[m] / ops.w[il]) * ops.D[m * n1 + il] : s * ops.D[il * n1 + m]);
         for (int v = 0; v < nv; ++v) R[nd * nv + v] -= T(c) * F[v];
       }
     }
@@ -1835,7 +1941,7 @@ void element_residual_t(const OrcProblem& P, const Mesh& M, const Ops& ops, cons
         int nk[3] = {ijk[0], ijk[1], ijk[2]};
         nk[l] = 0;
         load(M.neighbour(e, l, +1), M.node(nk), unbr);
-        rusanov_t(dim, l, uown, unbr, gamma, Fs);
+        surface_flux_t(P.surface, dim, l, uown, unbr, gamma, Fs);
         for (int v = 0; v < nv; ++v)
           R[nd * nv + v] -= T(s / ops.w[N]) * (Fs[v] - (weak ? T(0.0) : Fown[v]));
       }
@@ -1843,7 +1949,7 @@ void element_residual_t(const OrcProblem& P, const Mesh& M, const Ops& ops, cons
         int nk[3] = {ijk[0], ijk[1], ijk[2]};
         nk[l] = N;
         load(M.neighbour(e, l, -1), M.node(nk), unbr);
-        rusanov_t(dim, l, unbr, uown, gamma, Fs);
+        surface_flux_t(P.surface, dim, l, unbr, uown, gamma, Fs);
         for (int v = 0; v < nv; ++v)
           R[nd * nv + v] += T(s / ops.w[0]) * (Fs[v] - (weak ? T(0.0) : Fown[v]));
       }
@@ -2526,8 +2632,8 @@ int orc_strang_steps(const OrcProblem* P, int scheme, double* U, double dt, int 
   return 0;
 }
 
-// Directional derivative of the residual (forward mode, dual numbers): for the strong or
-// weak volume form with the Rusanov surface flux,
+// Directional derivative of the residual (forward mode, dual numbers): for the strong, weak
+// or two-point (Ranocha) volume form with the Rusanov, HLLC or EC surface flux,
 //   L  = L(U; gamma)      and      dL = (dL/dU) V + (dL/dgamma) gdot.
 int orc_rhs_jvp(const OrcProblem* P, const double* U, const double* V, double gdot, double* L,
                 double* dL) {
@@ -2535,7 +2641,8 @@ int orc_rhs_jvp(const OrcProblem* P, const double* U, const double* V, double gd
   if (rc) return rc;
   // the dual-number residual has no shock capturing, periodic boundaries and Cartesian boxes only
   if (P->shock || P->coords || P->bc[0] || P->bc[1] || P->bc[2] || P->bc[3] || P->bc[4] || P->bc[5]) return -6;
-  if ((P->volume != ORC_VOL_STRONG && P->volume != ORC_VOL_WEAK) || P->surface != ORC_SURF_RUSANOV ||
+  if ((P->volume != ORC_VOL_STRONG && P->volume != ORC_VOL_WEAK && P->volume != ORC_VOL_EC) ||
+      (P->surface != ORC_SURF_RUSANOV && P->surface != ORC_SURF_HLLC && P->surface != ORC_SURF_EC) ||
       P->equations != ORC_EULER)
     return -6;
   Mesh M(*P);
@@ -2550,6 +2657,16 @@ int orc_rhs_jvp(const OrcProblem* P, const double* U, const double* V, double gd
     if (L) L[q] = Ld[q].v;
     dL[q] = Ld[q].d;
   }
+  return 0;
+}
+
+// The logarithmic mean over duals (test access): *L = {{a}}^ln and
+// *dL = (d{{a}}^ln/da) da + (d{{a}}^ln/db) db.
+int orc_log_mean_jvp(double a, double b, double da, double db, double* L, double* dL) {
+  if (!(a > 0.0) || !(b > 0.0)) return -1;
+  const Dual m = log_mean_t(Dual(a, da), Dual(b, db));
+  *L = m.v;
+  *dL = m.d;
   return 0;
 }
 
@@ -2591,7 +2708,8 @@ int orc_rollout_grad(const OrcProblem* P, const double* U0, const double* target
   if (rc) return rc;
   // the dual-number residual has no shock capturing, periodic boundaries and Cartesian boxes only
   if (P->shock || P->coords || P->bc[0] || P->bc[1] || P->bc[2] || P->bc[3] || P->bc[4] || P->bc[5]) return -6;
-  if ((P->volume != ORC_VOL_STRONG && P->volume != ORC_VOL_WEAK) || P->surface != ORC_SURF_RUSANOV ||
+  if ((P->volume != ORC_VOL_STRONG && P->volume != ORC_VOL_WEAK && P->volume != ORC_VOL_EC) ||
+      (P->surface != ORC_SURF_RUSANOV && P->surface != ORC_SURF_HLLC && P->surface != ORC_SURF_EC) ||
       P->equations != ORC_EULER)
     return -6;
   Mesh M(*P);
