@@ -59,7 +59,7 @@ typedef enum {
   DG_ECUDA = -3,        /* a CUDA runtime call failed */
   DG_ENONFINITE = -4,   /* a kernel produced a non-finite value */
   DG_EPOSITIVITY = -5,  /* a kernel read a state with rho <= 0 or p <= 0 */
-  DG_EUNSUPPORTED = -6, /* valid but not implemented (e.g. the adjoint of the two-point form) */
+  DG_EUNSUPPORTED = -6, /* valid but not implemented (e.g. the adjoint on a curved mesh) */
   DG_ETOOLARGE = -7,    /* more instances than dg_max_dt_noalloc's static scratch holds */
   DG_ECONVERGENCE = -8  /* a node's Newton iteration (implicit source, or the vibrational
                         * temperature of the two-temperature model) did not converge */
@@ -283,14 +283,19 @@ DG_API dg_status dg_rk_stage(dg_ctx* ctx, int stage, const double* Un, const dou
 DG_API dg_status dg_rk_step(dg_ctx* ctx, double dt, int n_steps);
 
 /* Adjoint of the residual (for differentiable rollouts; the paper has no adjoint -- it is the
- * exact transpose of the semi-discrete operator of Eq. vol_weak + Eq. surf_int with the
- * Rusanov flux, strong or weak volume form, Euler equations, affine meshes, periodic or with
- * boundary conditions (the functors' exterior states differentiated with the own trace:
- * the slip wall's mirror state, U_b fixed); other choices return DG_EUNSUPPORTED):
+ * exact transpose of the semi-discrete operator of the Euler equations on affine meshes:
+ * the strong or weak volume form (Eq. vol_weak) or the two-point form (Eq. vol_split with
+ * Ranocha's flux, App. A), with the Rusanov flux -- periodic or with boundary conditions (the
+ * functors' exterior states differentiated with the own trace: the slip wall's mirror state,
+ * U_b fixed) -- or with the HLLC flux on periodic meshes; other choices, shock capturing and
+ * curved meshes return DG_EUNSUPPORTED):
  *   Ubar += (dL/dU)^T lam            (device arrays of dg_state_size() doubles)
  *   *gammabar += lam . dL/dgamma     (host double)
  * Non-smooth points follow the forward evaluation: the larger Rusanov signal speed (the left
- * one on a tie) carries the derivative, and d|u|/du = sign(u) with sign(0) = 0.  Ubar must not
+ * one on a tie) carries the derivative, and d|u|/du = sign(u) with sign(0) = 0; the HLLC
+ * flux's branch and the min/max of its wave speeds follow the values (the left argument on a
+ * tie); the logarithmic means are differentiated in their series form near equal
+ * arguments, where the derivative is 1/2 in each.  Ubar must not
  * alias U or lam.  Allocates the adjoint workspace on first use.  The gamma contribution is
  * added to a device accumulator of the context; with gammabar != NULL the call synchronizes
  * the stream, adds the accumulator to *gammabar and resets it; with gammabar == NULL it stays

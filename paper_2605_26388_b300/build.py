@@ -14,9 +14,10 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libdgsem.so")
 SOURCES = ["dg_api.cu", "dg_kernels.cu", "dg_stage2d.cu", "dg_stage3d.cu", "dg_batched2d.cu",
-           "dg_batched3d.cu", "dg_adjoint.cu", "dg_noalloc.cu", "dg_reacting.cu", "dg_shock.cu", "dg_curved.cu",
-           "dg_peaks.cu"]
-HEADERS = ["dg_device.cuh", "dg_internal.h", "dg_stage.cuh", "dg_batched.cuh", "dg_stage_ec3.cuh"]
+           "dg_batched3d.cu", "dg_adjoint.cu", "dg_adjoint_ec.cu", "dg_noalloc.cu", "dg_reacting.cu",
+           "dg_shock.cu", "dg_curved.cu", "dg_peaks.cu"]
+HEADERS = ["dg_device.cuh", "dg_internal.h", "dg_stage.cuh", "dg_batched.cuh", "dg_stage_ec3.cuh",
+           "dg_adjoint.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -844,8 +844,13 @@ dg_status ensure_adjoint(dg_ctx* c) {
   for (const dg_mesh_desc& m : c->inst) {
     if (m.coords) return fail(c, DG_EUNSUPPORTED, "the adjoint covers affine meshes");
   }
-  if (c->phys.volume == DG_VOL_EC || c->phys.surface != DG_SURF_RUSANOV)
-    return fail(c, DG_EUNSUPPORTED, "the adjoint covers the strong/weak volume form with the Rusanov flux");
+  if (c->phys.surface != DG_SURF_RUSANOV && c->phys.surface != DG_SURF_HLLC)
+    return fail(c, DG_EUNSUPPORTED, "the adjoint covers the Rusanov and HLLC surface fluxes");
+  if (c->phys.surface == DG_SURF_HLLC) {
+    for (const dg_mesh_desc& m : c->inst)
+      for (int l = 0; l < m.dim; ++l)
+        if (m.periodic[l] != 1) return fail(c, DG_EUNSUPPORTED, "the adjoint of the HLLC flux covers periodic meshes");
+  }
   if (c->gacc) return DG_OK;
   const size_t bytes = sizeof(double) * (size_t)c->nv * c->n_nodes_total;
   int maxb = 1;
@@ -887,7 +892,8 @@ dg_status run_vjp(dg_ctx* c, const double* U, const double* lam, double* out, in
     a.gw = gw;
     a.mode = mode;
     a.weak = (c->phys.volume == DG_VOL_WEAK) ? 1 : 0;
-    cudaError_t e = dg::launch_rhs_vjp(c->dim, c->inst[i].N, c->phys.precision == DG_FP32_MIXED, a,
+    const int sch = (c->phys.volume == DG_VOL_EC ? 1 : 0) | (c->phys.surface == DG_SURF_HLLC ? 2 : 0);
+    cudaError_t e = dg::launch_rhs_vjp(c->dim, c->inst[i].N, c->phys.precision == DG_FP32_MIXED, sch, a,
                                        c->gacc, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "adjoint launch");
   }

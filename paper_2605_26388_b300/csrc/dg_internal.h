@@ -163,7 +163,11 @@ cudaError_t launch_shock_blend(int dim, int N, int fp32, const ShockArgs& a, cud
 
 // Launch the adjoint of the residual for one instance, then add the weighted gamma
 // contribution (a deterministic sum of the per-CTA partials) to *gacc (device).
-cudaError_t launch_rhs_vjp(int dim, int N, int fp32, const VjpArgs& a, double* gacc, cudaStream_t s);
+// sch: 0 the strong or weak volume form with the Rusanov flux; bit 0 the two-point form,
+// bit 1 the HLLC flux (periodic meshes)
+cudaError_t launch_rhs_vjp(int dim, int N, int fp32, int sch, const VjpArgs& a, double* gacc, cudaStream_t s);
+// the launch of schemes 1..3 (dg_adjoint_ec.cu); *blocks receives the grid size
+cudaError_t launch_vjp_ec(int sch, int dim, int N, int fp32, const VjpArgs& a, cudaStream_t s, int* blocks);
 // CTAs the adjoint launch uses for an instance (size of the gpart scratch).
 int vjp_blocks(int dim, int N, long long n_elem);
 

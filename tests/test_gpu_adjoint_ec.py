@@ -1,0 +1,178 @@
+"""The adjoint of the two-point volume form (Eq. vol_split, Ranocha's flux of App. A) and of
+the HLLC surface flux on the GPU, against the oracle's dual-number residual:
+
+- residual adjoint vs the oracle's brute-force transpose (one dual-number JVP per unknown),
+  for the two-point form with HLLC or Rusanov and the strong/weak forms with HLLC;
+- dot-product test <lam, J V> = <J^T lam, V> on the 3D Taylor-Green scheme (N = 4, EC + HLLC),
+  FP64 and FP32-mixed;
+- one SSP-RK3 step's adjoint vs chained oracle JVPs through its three stages;
+- the two-point form with Rusanov faces on walls and inflow/outflow boundaries vs central
+  differences of the oracle's residual;
+- the refusal of HLLC on a non-periodic mesh.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2605_26388_b300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+GAMMA = 1.4
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_26388_b300 import build, dgsem
+    build.build_library()
+    return torch, dgsem
+
+
+def make(orc, dg, dim, N, nel, vol, surf, prec=0, lo=0.0, hi=1.0):
+    P = orc.Problem(dim=dim, N=N, nel=(nel,) * dim, lo=(lo,) * dim, hi=(hi,) * dim, volume=vol,
+                    surface=surf, gamma=GAMMA)
+    S = dg.Solver(dg.Mesh(dim, N, (nel,) * dim, (lo,) * dim, (hi,) * dim), volume=vol, surface=surf,
+                  precision=prec, gamma=GAMMA, p_ref=1.0 if prec else 0.0)
+    return P, S
+
+
+def state(orc, P, seed, amp_v=0.4):
+    xi, _ = orc.gll(P.N)
+    X = wl.node_coordinates(P.dim, P.nel, P.lo, P.hi, xi)
+    rho = 1.0 + 0.2 * wl.fourier_field(seed, X, P.lo, P.hi, 2)
+    vel = [amp_v * wl.fourier_field(seed + 1 + d, X, P.lo, P.hi, 2) for d in range(P.dim)]
+    p = 1.0 + 0.2 * wl.fourier_field(seed + 5, X, P.lo, P.hi, 2)
+    return wl.perturbed(wl.conserved(rho, vel, p, GAMMA), seed + 9, 0.02)
+
+
+def dev(torch, a):
+    return torch.from_numpy(np.ascontiguousarray(a.reshape(a.shape[0], -1))).cuda()
+
+
+# volume: 0 strong, 1 weak, 2 two-point; surface: 0 Rusanov, 1 HLLC
+@pytest.mark.parametrize("dim,N,nel,vol,surf", [(2, 2, 2, 2, 1), (2, 3, 3, 2, 0), (3, 2, 2, 2, 1),
+                                                (2, 3, 3, 0, 1), (2, 2, 3, 1, 1), (3, 3, 2, 2, 0),
+                                                (2, 7, 2, 2, 1), (3, 5, 1, 2, 1)])
+def test_rhs_vjp_matches_brute_force_transpose(env, orc, dim, N, nel, vol, surf):
+    torch, dg = env
+    P, S = make(orc, dg, dim, N, nel, vol, surf)
+    U = state(orc, P, 3)
+    lam = wl.uniform(7, U.size).reshape(U.shape) - 0.5
+    ref, gref = orc.rhs_vjp_brute(P, U, lam)
+    Ub, g = S.rhs_vjp(dev(torch, U), dev(torch, lam))
+    S.check()
+    got = Ub.cpu().numpy().reshape(U.shape)
+    S.close()
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+    # lam . dL/dgamma is a sum of signed terms over every node (at N = 7 the pair terms carry
+    # operator entries near 14 and cancel to 0.2% of their magnitudes): its rounding is also
+    # measured against those magnitudes, at 1e-14 of their sum (about 100 ulp)
+    _, Jg = orc.rhs_jvp(P, U, None, 1.0)
+    bar = max(1e-12 * max(1.0, abs(gref)), 1e-14 * float(np.sum(np.abs(lam * Jg))))
+    assert abs(g - gref) <= bar, (g, gref, bar)
+
+
+@pytest.mark.parametrize("prec,tol,gtol", [(0, 1e-12, 1e-12), (1, 3e-8, 3e-5)])
+def test_taylor_green_scheme_dot_product(env, orc, prec, tol, gtol):
+    """3D, N = 4, two-point form + HLLC (the Taylor-Green scheme) on 3^3 elements of
+    [0, 2 pi]^3 at Mach 0.1: <lam, J V> from the oracle's dual numbers against <J^T lam, V>.
+    FP32-mixed measured 3e-9 (the product) and 6e-6 (gamma, whose terms come through the
+    FP32 pressure) of the terms' magnitudes; the bars are about 5 to 10 times those."""
+    torch, dg = env
+    N, nel = 4, 3
+    P, S = make(orc, dg, 3, N, nel, 2, 1, prec=prec, hi=2 * math.pi)
+    xi, _ = orc.gll(N)
+    U = wl.perturbed(wl.taylor_green_3d(nel, xi, 0.1, GAMMA), 5, 1e-3).reshape(P.shape)
+    lam = wl.uniform(13, U.size).reshape(U.shape) - 0.5
+    V = (wl.uniform(17, U.size).reshape(U.shape) - 0.5) * np.abs(U)
+    _, JV = orc.rhs_jvp(P, U, V, 0.0)
+    _, Jg = orc.rhs_jvp(P, U, None, 1.0)
+    Ub, g = S.rhs_vjp(dev(torch, U), dev(torch, lam))
+    S.check()
+    lhs = float(np.sum(lam * JV))
+    rhs = float(np.sum(Ub.cpu().numpy().reshape(U.shape) * V))
+    S.close()
+    scale = float(np.sum(np.abs(lam * JV)))
+    assert abs(lhs - rhs) <= tol * scale, (lhs, rhs, scale)
+    assert abs(g - float(np.sum(lam * Jg))) <= gtol * float(np.sum(np.abs(lam * Jg)))
+
+
+def test_rk_step_vjp_against_chained_oracle_jvps(env, orc):
+    torch, dg = env
+    P, S = make(orc, dg, 2, 3, 4, 2, 1)
+    U = state(orc, P, 19)
+    V = wl.uniform(23, U.size).reshape(U.shape) - 0.5
+    lam = wl.uniform(29, U.size).reshape(U.shape) - 0.5
+    dt = 2e-3
+    L0, dL0 = orc.rhs_jvp(P, U, V, 0.0)
+    U1, V1 = U + dt * L0, V + dt * dL0
+    L1, dL1 = orc.rhs_jvp(P, U1, V1, 0.0)
+    U2, V2 = 0.75 * U + 0.25 * (U1 + dt * L1), 0.75 * V + 0.25 * (V1 + dt * dL1)
+    L2, dL2 = orc.rhs_jvp(P, U2, V2, 0.0)
+    V3 = V / 3.0 + (2.0 / 3.0) * (V2 + dt * dL2)
+    _, g0 = orc.rhs_jvp(P, U, None, 1.0)
+    W1 = dt * g0
+    _, g1 = orc.rhs_jvp(P, U1, W1, 1.0)
+    W2 = 0.25 * (W1 + dt * g1)
+    _, g2 = orc.rhs_jvp(P, U2, W2, 1.0)
+    W3 = (2.0 / 3.0) * (W2 + dt * g2)
+    lam_d = dev(torch, lam)
+    gb = S.rk_step_vjp(dev(torch, U), dt, lam_d)
+    S.check()
+    lhs = float(np.sum(lam * V3))
+    rhs = float(np.sum(lam_d.cpu().numpy().reshape(U.shape) * V))
+    S.close()
+    assert abs(lhs - rhs) <= 1e-12 * float(np.sum(np.abs(lam * V3)))
+    assert abs(gb - float(np.sum(lam * W3))) <= 1e-12 * float(np.sum(np.abs(lam * W3)))
+
+
+@pytest.mark.parametrize("bc", [(1, 1, 0, 0, 0, 0), (2, 3, 1, 1, 0, 0), (4, 4, 1, 1, 0, 0)])
+def test_two_point_form_with_boundaries_against_oracle_differences(env, orc, bc):
+    """The two-point form with Rusanov faces on slip walls, supersonic inflow/outflow and
+    Dirichlet faces: ((dL/dU)^T lam) . V against lam . (L(U + eps V) - L(U - eps V))/(2 eps)
+    of the oracle, and likewise for gamma."""
+    torch, dg = env
+    N, nel = 3, (3, 2)
+    xi, _ = orc.gll(N)
+    lo, hi = (0.0, 0.0), (2.0, 1.0)
+    st = wl.conserved(np.array(1.1), [np.array(2.6), np.array(0.1)], np.array(0.9), GAMMA).reshape(-1)
+    bs = tuple(st if b in (2, 4) else None for b in bc)
+    X = wl.node_coordinates(2, nel, lo, hi, xi)
+    rho = 1.0 + 0.2 * np.cos(np.pi * X[0]) * np.sin(2 * np.pi * X[1] + 0.3)
+    U = wl.conserved(rho, [2.2 + 0.3 * np.sin(np.pi * X[1]), 0.2 * np.cos(np.pi * X[0])], 1.0 + 0.1 * rho,
+                     GAMMA).reshape(4, 6, -1)
+    rng = np.random.default_rng(4)
+    lam = rng.standard_normal(U.shape)
+    V = rng.standard_normal(U.shape) * np.abs(U)
+    S = dg.Solver(dg.Mesh(2, N, nel, lo, hi, bc=bc, bc_state=bs), volume=2, surface=0, gamma=GAMMA)
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a.reshape(4, -1))).cuda()
+    Ubar, gbar = S.rhs_vjp(d(U), d(lam))
+    S.check()
+    got = float(np.sum(Ubar.cpu().numpy().reshape(U.shape) * V))
+    S.close()
+
+    def res(Ux, g=GAMMA):
+        P = orc.Problem(dim=2, N=N, nel=nel, lo=lo, hi=hi, volume=2, surface=0, gamma=g, bc=bc, bc_state=bs)
+        return orc.rhs(P, Ux)
+
+    eps = 1e-6
+    want = float(np.sum(lam * (res(U + eps * V) - res(U - eps * V)) / (2 * eps)))
+    assert abs(got - want) <= 1e-6 * max(abs(want), 1.0), (got, want)
+    gwant = float(np.sum(lam * (res(U, GAMMA + eps) - res(U, GAMMA - eps)) / (2 * eps)))
+    assert abs(gbar - gwant) <= 1e-6 * max(abs(gwant), 1.0), (gbar, gwant)
+
+
+def test_hllc_adjoint_refuses_non_periodic_meshes(env, orc):
+    torch, dg = env
+    lo, hi = (0.0, 0.0), (1.0, 1.0)
+    S = dg.Solver(dg.Mesh(2, 2, (3, 3), lo, hi, bc=(1, 1, 0, 0, 0, 0)), volume=2, surface=1, gamma=GAMMA)
+    U = torch.ones((4, S.n_doubles // 4), dtype=torch.float64, device="cuda")
+    U[3] = 2.5
+    with pytest.raises(dg.DGError) as ei:
+        S.rhs_vjp(U, torch.zeros_like(U))
+    assert ei.value.status == dg.DG_EUNSUPPORTED
+    S.close()
