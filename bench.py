@@ -923,6 +923,56 @@ def run_adjoint(args):
         out[name] = {"forward_ms": 1e3 * t_fwd, "gradient_ms": 1e3 * t_grad,
                      "gradient_over_forward": t_grad / t_fwd,
                      "note": "gradient = checkpointed forward + segment recompute + reverse step adjoints"}
+    out["tgv3d_ec_hllc"] = run_adjoint_tgv(args)
+    return out
+
+
+def run_adjoint_tgv(args):
+    """The adjoint of the Taylor-Green scheme (3D, N = 4, two-point form + HLLC) on 32^3
+    elements: one residual VJP against one residual evaluation, and one SSP-RK3 step's adjoint
+    (three VJPs, two recomputed stages) against one forward step, FP64 and FP32-mixed; CUDA
+    events on the solver's stream."""
+    import torch
+    from paper_2605_26388_b300 import dgsem, workloads as wl
+    nel = 32
+    x, _, _ = dgsem.gll(N)
+    U0 = torch.from_numpy(wl.taylor_green_3d(nel, x, MACH, GAMMA).reshape(NV, -1)).cuda()
+    out = {"workload": f"3D Euler TGV Ma {MACH}, N={N}, {nel}^3, EC + HLLC: residual VJP and SSP-RK3 step VJP"}
+    for name, prec, reps in (("fp64", dgsem.FP64, 3), ("fp32_mixed", dgsem.FP32_MIXED, 10)):
+        S = dgsem.Solver(dgsem.Mesh(3, N, (nel,) * 3, (0.0,) * 3, (2 * math.pi,) * 3), volume=dgsem.VOL_EC,
+                         surface=dgsem.SURF_HLLC, precision=prec, gamma=GAMMA,
+                         p_ref=P_REF if prec == dgsem.FP32_MIXED else 0.0)
+        S.set_state(U0)
+        dt = S.max_dt(CFL)
+        lam = torch.rand_like(U0) - 0.5
+        Ub = torch.zeros_like(U0)
+        S.rhs_vjp(U0, lam, Ub)
+        S.rhs(U0)
+        S.rk_step(dt, 1)
+        S.rk_step_vjp(U0, dt, lam.clone(), defer=True)
+        S.check()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        lam_s = lam.clone()
+        torch.cuda.synchronize()
+        ev[0].record()
+        for _ in range(reps):
+            S.rhs_vjp(U0, lam, Ub)
+        ev[1].record()
+        for _ in range(reps):
+            S.rhs(U0)
+        ev[2].record()
+        for _ in range(reps):
+            S.rk_step_vjp(U0, dt, lam_s, defer=True)
+        ev[3].record()
+        S.rk_step(dt, reps)
+        ev[4].record()
+        torch.cuda.synchronize()
+        S.adjoint_gammabar()
+        S.check()
+        t = [ev[k].elapsed_time(ev[k + 1]) / reps for k in range(4)]
+        out[name] = {"rhs_vjp_ms": t[0], "rhs_ms": t[1], "vjp_over_rhs": t[0] / t[1], "step_vjp_ms": t[2],
+                     "step_ms": t[3], "step_vjp_over_step": t[2] / t[3]}
+        S.close()
     return out
 
 
