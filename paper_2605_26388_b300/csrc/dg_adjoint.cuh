@@ -135,19 +135,19 @@ __device__ __forceinline__ void log_mean_grad(R a, R b, R& m, R& da, R& db) {
 }
 
 // Reverse differentiation of Ranocha's two-point flux F#(U_a, U_b) in direction l (App. A,
-// the energy component in its consistent published form) with respect to its first argument:
-// ga = (dF#/dU_a)^T c, and cg = c . dF#/dgamma (gamma enters through 1/((gamma-1) beta^ln)
-// and both pressures).  A, B: the two nodes' states.
+// the energy component in its consistent published form) in both arguments against one
+// cotangent c: ga = (dF#/dU_a)^T c, gb = (dF#/dU_b)^T c, and cg = c . dF#/dgamma (gamma enters
+// through 1/((gamma-1) beta^ln) and both pressures).  A, B: the two nodes' states with their
+// reciprocal densities and pressures; igm1 = 1/(gamma - 1).
 template <int DIM, class R>
-__device__ __forceinline__ void ec_flux_vjp_a(int l, const NodeState<DIM, R>& A, const NodeState<DIM, R>& B,
-                                              R gamma, const R* c, R* ga, R& cg) {
+__device__ __forceinline__ void ec_flux_vjp(int l, const NodeState<DIM, R>& A, R irhoa, R ipa,
+                                            const NodeState<DIM, R>& B, R irhob, R ipb, R gm1, R igm1,
+                                            const R* c, R* ga, R* gb, R& cg) {
   constexpr int NV = DIM + 2;
-  const R gm1 = gamma - R(1);
-  const R ipa = Ar<R>::rcp(A.p), ipb = Ar<R>::rcp(B.p);
   const R ba = A.rho * ipa, bb = B.rho * ipb;
-  R rln, drln, drlnb, bln, dbln, dblnb;
-  log_mean_grad<R>(A.rho, B.rho, rln, drln, drlnb);
-  log_mean_grad<R>(ba, bb, bln, dbln, dblnb);
+  R rln, drla, drlb, bln, dbla, dblb;
+  log_mean_grad<R>(A.rho, B.rho, rln, drla, drlb);
+  log_mean_grad<R>(ba, bb, bln, dbla, dblb);
   R vavg[DIM], vv = R(0), val = R(0), vbl = R(0), vavl = R(0);
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
@@ -156,7 +156,7 @@ __device__ __forceinline__ void ec_flux_vjp_a(int l, const NodeState<DIM, R>& A,
     if (d == l) { val = A.v[d]; vbl = B.v[d]; vavl = vavg[d]; }
   }
   const R frho = rln * vavl;
-  const R ib = Ar<R>::rcp(gm1 * bln);
+  const R ibln = Ar<R>::rcp(bln), ib = igm1 * ibln;
   const R cE = c[NV - 1];
   R cm = R(0), cl = R(0);
 #pragma unroll
@@ -167,35 +167,45 @@ __device__ __forceinline__ void ec_flux_vjp_a(int l, const NodeState<DIM, R>& A,
   // F0 = frho, F_{1+d} = frho vavg_d + [d = l] (pa + pb)/2,
   // F_E = frho (ib + vv/2) + (pa vb_l + pb va_l)/2
   const R fb = c[0] + cm + cE * (ib + R(0.5) * vv);
-  const R blnb = -cE * frho * ib * Ar<R>::rcp(bln);
-  cg = -cE * frho * ib * Ar<R>::rcp(gm1);
+  const R efr = cE * frho * ib;
+  const R blnb = -efr * ibln;
+  cg = -efr * igm1;
   const R vvb = R(0.5) * cE * frho;
+  const R fr = fb * vavl;  // adjoint of rho^ln
   R pab = R(0.5) * (cE * vbl + cl), pbb = R(0.5) * (cE * val + cl);
-  R vab[DIM];
+  R vab[DIM], vbb[DIM];
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
-    vab[d] = R(0.5) * c[1 + d] * frho + vvb * B.v[d];
-    if (d == l) vab[d] += R(0.5) * (cE * B.p + fb * rln);
+    const R h = R(0.5) * c[1 + d] * frho;
+    vab[d] = h + vvb * B.v[d];
+    vbb[d] = h + vvb * A.v[d];
+    if (d == l) {
+      const R t = R(0.5) * fb * rln;
+      vab[d] += R(0.5) * cE * B.p + t;
+      vbb[d] += R(0.5) * cE * A.p + t;
+    }
   }
-  R rab = fb * vavl * drln;
   // beta = rho / p
-  const R bab = blnb * dbln, bbb = blnb * dblnb;
-  rab += bab * ipa;
+  const R bab = blnb * dbla, bbb = blnb * dblb;
+  const R rab = fr * drla + bab * ipa, rbb = fr * drlb + bbb * ipb;
   pab -= bab * ba * ipa;
   pbb -= bbb * bb * ipb;
-  // p = (gamma - 1)(E - |m|^2/(2 rho)), v = m / rho
   cg += pab * A.rhoe + pbb * B.rhoe;
-  const R irho = Ar<R>::rcp(A.rho);
-  R v2 = R(0), vbv = R(0);
+  // p = (gamma - 1)(E - |m|^2/(2 rho)), v = m / rho
+  R v2a = R(0), v2b = R(0), vva = R(0), vvbb = R(0);
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
-    v2 += A.v[d] * A.v[d];
-    vbv += vab[d] * A.v[d];
+    v2a += A.v[d] * A.v[d];
+    v2b += B.v[d] * B.v[d];
+    vva += vab[d] * A.v[d];
+    vvbb += vbb[d] * B.v[d];
+    ga[1 + d] = vab[d] * irhoa - pab * gm1 * A.v[d];
+    gb[1 + d] = vbb[d] * irhob - pbb * gm1 * B.v[d];
   }
-  ga[0] = rab + pab * gm1 * R(0.5) * v2 - vbv * irho;
-#pragma unroll
-  for (int d = 0; d < DIM; ++d) ga[1 + d] = vab[d] * irho - pab * gm1 * A.v[d];
+  ga[0] = rab + pab * gm1 * R(0.5) * v2a - vva * irhoa;
+  gb[0] = rbb + pbb * gm1 * R(0.5) * v2b - vvbb * irhob;
   ga[NV - 1] = pab * gm1;
+  gb[NV - 1] = pbb * gm1;
 }
 
 // Reverse differentiation of the HLLC flux F*(U_L, U_R) in direction l (Toro, Spruce and
@@ -366,10 +376,13 @@ struct Vjp {
   static constexpr int NF = 2 * DIM, NJS = EPB * NF * NFN;
   static constexpr int T = (((EPB * NP > NJS) ? EPB * NP : NJS) + 31) / 32 * 32;
   // shared: co-state [EPB][NV][NP], face contributions [EPB][NF][NFN][NV], D, (two-point form)
-  // the nodes' rho, v, rho e [EPB][NV][NP], reduction
+  // the nodes' rho, v, rho e, 1/p, 1/rho [EPB][NV + 2][NP] and the partners' parts of the
+  // pairs of one direction [EPB][NO][NV][NP], reduction
+  static constexpr int NO = N1 / 2;  // pair offsets per line (cyclic ownership)
   static constexpr int OFF_L = 0, OFF_S = EPB * NV * NP, OFF_D = OFF_S + EPB * NF * NFN * NV;
   static constexpr int OFF_W = OFF_D + N1 * N1;
-  static constexpr int R_SIZE = OFF_W + (EC ? EPB * NV * NP : 0);
+  static constexpr int OFF_X = OFF_W + (EC ? EPB * (NV + 2) * NP : 0);
+  static constexpr int R_SIZE = OFF_X + (EC ? EPB * NO * NV * NP : 0);
   static constexpr size_t RED_OFF = (sizeof(R) * R_SIZE + 15) / 16 * 16;  // 16-byte aligned
   static constexpr size_t smem_bytes() { return RED_OFF + sizeof(double) * 32; }
 
@@ -414,11 +427,13 @@ struct Vjp {
       for (int v = 0; v < NV; ++v) u64[v] = A.U[v * A.stride + gi];
       ns = node_state<DIM, R>(u64, gamma);
       if constexpr (EC) {
-        R* W = sm + OFF_W + el * NV * NP + nd;
+        R* W = sm + OFF_W + el * (NV + 2) * NP + nd;
         W[0] = ns.rho;
 #pragma unroll
         for (int d = 0; d < DIM; ++d) W[(1 + d) * NP] = ns.v[d];
         W[(NV - 1) * NP] = ns.rhoe;
+        W[NV * NP] = Ar<R>::rcp(ns.p);
+        W[(NV + 1) * NP] = Ar<R>::rcp(ns.rho);
       }
     }
     __syncthreads();
@@ -428,41 +443,80 @@ struct Vjp {
 #pragma unroll
     for (int v = 0; v < NV; ++v) w[v] = R(0);
     if constexpr (EC) {
-      // two-point form: R_i = -s_l sum_m Dv[i][m] F#(U_i, U_m) along each line, so, with F#
-      // symmetric, w_i = -sum_l s_l sum_m (dF#/dU_a (U_i, U_m))^T (Dv[i][m] lam_i + Dv[m][i] lam_m),
-      // and each pair's gamma derivative, met from both of its nodes, counts half
+      // two-point form: R_i = -s_l sum_m Dv[i][m] F#(U_i, U_m) along each line.  F# is symmetric
+      // and a pair's cotangent c = Dv[i][m] lam_i + Dv[m][i] lam_m is the same from both of its
+      // nodes, so each pair is reverse-differentiated once, by its owner (cyclic ownership as in
+      // the forward stage: node i owns the pairs to i+1 .. i+NO, on a line of even length the
+      // half-way pair belongs to the lower half): w_i -= s (dF#/dU_a)^T c, and the partner's
+      // -s (dF#/dU_b)^T c passes through a shared-memory slot.  The diagonal pair (U_i, U_i),
+      // whose Dv[i][i] vanishes inside the line, takes both arguments' parts with c = Dv[i][i]
+      // lam_i.  Every pair's gamma derivative counts once.
+      R li[NV], irhoi = R(0), ipi = R(0);
+      const R igm1 = Ar<R>::rcp(gm1);
       if (active) {
-        R li[NV];
+        const R* Wi = sm + OFF_W + el * (NV + 2) * NP + nd;
+        ipi = Wi[NV * NP];
+        irhoi = Wi[(NV + 1) * NP];
 #pragma unroll
         for (int v = 0; v < NV; ++v) li[v] = sm[OFF_L + (el * NV + v) * NP + nd];
+      }
+      R gsum = R(0);
 #pragma unroll
-        for (int l = 0; l < DIM; ++l) {
-          const int i = pos(l, nd), q = face_line(l, nd);
-          const R s = s_of<R>(I, l);
-          R gsum = R(0);
+      for (int l = 0; l < DIM; ++l) {
+        const R s = s_of<R>(I, l);
+        R* X = sm + OFF_X + el * NO * NV * NP;
+        const int i = active ? pos(l, nd) : 0, q = active ? face_line(l, nd) : 0;
+        if (active) {
+          R gl = R(0);
+          const R dii = sm[OFF_D + i * N1 + i];
+          if (dii != R(0)) {
+            R c[NV], ga[NV], gb[NV], cg;
 #pragma unroll
-          for (int m = 0; m < N1; ++m) {
+            for (int v = 0; v < NV; ++v) c[v] = dii * li[v];
+            ec_flux_vjp<DIM, R>(l, ns, irhoi, ipi, ns, irhoi, ipi, gm1, igm1, c, ga, gb, cg);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) w[v] -= s * (ga[v] + gb[v]);
+            gl += cg;
+          }
+#pragma unroll
+          for (int o = 1; o <= NO; ++o) {
+            if (2 * o == N1 && i >= N1 / 2) break;
+            const int m = i + o < N1 ? i + o : i + o - N1;
             const int nm = line_node(l, q, m);
-            const R* W = sm + OFF_W + el * NV * NP + nm;
+            const R* Wm = sm + OFF_W + el * (NV + 2) * NP + nm;
             NodeState<DIM, R> B;
-            B.rho = W[0];
+            B.rho = Wm[0];
 #pragma unroll
-            for (int d = 0; d < DIM; ++d) B.v[d] = W[(1 + d) * NP];
-            B.rhoe = W[(NV - 1) * NP];
+            for (int d = 0; d < DIM; ++d) B.v[d] = Wm[(1 + d) * NP];
+            B.rhoe = Wm[(NV - 1) * NP];
             B.p = gm1 * B.rhoe;
             const R dim_ = sm[OFF_D + i * N1 + m], dmi = sm[OFF_D + m * N1 + i];
-            R c[NV];
+            R c[NV], ga[NV], gb[NV], cg;
 #pragma unroll
             for (int v = 0; v < NV; ++v) c[v] = dim_ * li[v] + dmi * sm[OFF_L + (el * NV + v) * NP + nm];
-            R ga[NV], cg;
-            ec_flux_vjp_a<DIM, R>(l, ns, B, gamma, c, ga, cg);
+            ec_flux_vjp<DIM, R>(l, ns, irhoi, ipi, B, Wm[(NV + 1) * NP], Wm[NV * NP], gm1, igm1, c, ga, gb, cg);
 #pragma unroll
-            for (int v = 0; v < NV; ++v) w[v] -= s * ga[v];
-            gsum += cg;
+            for (int v = 0; v < NV; ++v) {
+              w[v] -= s * ga[v];
+              X[((o - 1) * NV + v) * NP + nm] = gb[v];
+            }
+            gl += cg;
           }
-          gacc -= (double)(R(0.5) * s * gsum);
+          gsum += s * gl;
         }
+        __syncthreads();  // the partners' parts of direction l are in the slots
+        if (active) {
+#pragma unroll
+          for (int o = 1; o <= NO; ++o) {
+            const int k = i >= o ? i - o : i - o + N1;  // the owner of the pair (k, i)
+            if (2 * o == N1 && k >= N1 / 2) continue;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) w[v] -= s * X[((o - 1) * NV + v) * NP + nd];
+          }
+        }
+        __syncthreads();  // the slots are free for the next direction
       }
+      gacc -= (double)gsum;
     } else if (active) {
 #pragma unroll
       for (int l = 0; l < DIM; ++l) {
@@ -688,6 +742,15 @@ static cudaError_t launch_vjp_one(const VjpArgs& a, cudaStream_t s, int* blocks_
   const int blocks = (a.inst.n_elem + K::EPB - 1) / K::EPB;
   if (blocks_out) *blocks_out = blocks;
   if (blocks == 0) return cudaSuccess;
+  if constexpr (K::smem_bytes() > 48 * 1024) {  // above the default dynamic limit: opt in once
+    static bool opted = false;
+    if (!opted) {
+      const cudaError_t e = cudaFuncSetAttribute(k_rhs_vjp<DIM, N, R, SCH>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K::smem_bytes());
+      if (e != cudaSuccess) return e;
+      opted = true;
+    }
+  }
   k_rhs_vjp<DIM, N, R, SCH><<<blocks, K::T, K::smem_bytes(), s>>>(a);
   return cudaGetLastError();
 }
