@@ -285,10 +285,10 @@ DG_API dg_status dg_rk_step(dg_ctx* ctx, double dt, int n_steps);
 /* Adjoint of the residual (for differentiable rollouts; the paper has no adjoint -- it is the
  * exact transpose of the semi-discrete operator of the Euler equations on affine meshes:
  * the strong or weak volume form (Eq. vol_weak) or the two-point form (Eq. vol_split with
- * Ranocha's flux, App. A), with the Rusanov flux -- periodic or with boundary conditions (the
- * functors' exterior states differentiated with the own trace: the slip wall's mirror state,
- * U_b fixed) -- or with the HLLC flux on periodic meshes; other choices, shock capturing and
- * curved meshes return DG_EUNSUPPORTED):
+ * Ranocha's flux, App. A), with the Rusanov or HLLC flux -- periodic or with boundary
+ * conditions (the functors' exterior states differentiated with the own trace: the slip
+ * wall's mirror state, U_b fixed); other surface fluxes, shock capturing and curved meshes
+ * return DG_EUNSUPPORTED):
  *   Ubar += (dL/dU)^T lam            (device arrays of dg_state_size() doubles)
  *   *gammabar += lam . dL/dgamma     (host double)
  * Non-smooth points follow the forward evaluation: the larger Rusanov signal speed (the left

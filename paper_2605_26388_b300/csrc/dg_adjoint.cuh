@@ -2,8 +2,8 @@
 //
 // For the Euler equations on affine meshes (Sec. 3.1.1): the strong or weak volume form
 // (Eq. vol_weak) or the two-point form (Eq. vol_split with Ranocha's flux, App. A), with the
-// Rusanov surface flux (periodic, or with the boundary functors of the forward pass: slip
-// wall, supersonic inflow and outflow, Dirichlet) or the HLLC flux (periodic).  Given a
+// Rusanov or HLLC surface flux (periodic, or with the boundary functors of the forward pass:
+// slip wall, supersonic inflow and outflow, Dirichlet).  Given a
 // co-state lam this computes, element by element,
 //   w = (dL/dU)^T lam      and      g = lam . dL/dgamma,
 // without atomics.  Strong/weak volume: lam contracted with the transposed volume operator
@@ -366,8 +366,8 @@ __device__ __forceinline__ int wall_face(const InstArgs& I, int e, int l, int si
   return (side ? c == I.nel[l] - 1 : c == 0) ? f : -1;
 }
 
-// SCH: bit 0 the two-point volume form (Ranocha's flux), bit 1 the HLLC surface flux (periodic
-// meshes); 0 is the strong or weak volume form with the Rusanov flux.
+// SCH: bit 0 the two-point volume form (Ranocha's flux), bit 1 the HLLC surface flux; 0 is the
+// strong or weak volume form with the Rusanov flux.
 template <int DIM, int N, class R, int SCH = 0>
 struct Vjp {
   using G = Geo<DIM, N>;
@@ -589,26 +589,41 @@ struct Vjp {
       const NodeState<DIM, R>& sL = side ? so : sn;
       const NodeState<DIM, R>& sR = side ? sn : so;
       if constexpr (HLLC) {
-        // periodic faces: the face's F* enters this element's residual (c lam_own) and the
-        // neighbour's (-c lam_nbr), so its part of w_own is c (dF*/dU_own)^T (lam_own - lam_nbr);
-        // its gamma derivative, met from both sides' jobs with the same c (lam_own - lam_nbr),
-        // counts half here
-        R mu[NV], gLv[NV], gRv[NV], gg, ao[NV];
+        // An interior face's F* enters this element's residual (c lam_own) and the neighbour's
+        // (-c lam_nbr), so its part of w_own is c (dF*/dU_own)^T (lam_own - lam_nbr); its gamma
+        // derivative, met from both sides' jobs with the same c (lam_own - lam_nbr), counts
+        // half.  A domain face (lam_nbr = 0, no second job): slip wall and Dirichlet take the
+        // HLLC flux against the mirror state / U_b (the mirror's part folded back with the
+        // normal momentum negated), supersonic inflow F(U_b), outflow F(U_own).
+        R mu[NV], gLv[NV], gRv[NV], gg = R(0), ao[NV], gown[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) mu[v] = lo[v] - ln[v];
-        hllc_vjp<DIM, R>(l, sL, sR, gamma, mu, gLv, gRv, gg);
-        const R* gown = side ? gLv : gRv;
-        if (!A.weak) flux_jac_t<DIM, R>(l, so.v, so.H, gm1, lo, ao);
+        if (!A.weak || type == 3) flux_jac_t<DIM, R>(l, so.v, so.H, gm1, lo, ao);
+        R mlo = R(0), vlo = R(0), vln = R(0);
+#pragma unroll
+        for (int d = 0; d < DIM; ++d)
+          if (d == l) { mlo = lo[1 + d]; vlo = so.v[d]; vln = sn.v[d]; }
+        if (type == 2 || type == 3) {
+#pragma unroll
+          for (int v = 0; v < NV; ++v) gown[v] = type == 3 ? ao[v] : R(0);
+          gg = type == 3 ? so.rhoe * (mlo + lo[DIM + 1] * vlo) : sn.rhoe * (mlo + lo[DIM + 1] * vln);
+        } else {
+          hllc_vjp<DIM, R>(l, sL, sR, gamma, mu, gLv, gRv, gg);
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            gown[v] = side ? gLv[v] : gRv[v];
+            if (type == 1) {
+              const R ge = side ? gRv[v] : gLv[v];
+              gown[v] += (v == 1 + l) ? -ge : ge;
+            }
+          }
+        }
         const R c = (side ? R(-1) : R(1)) * s_of<R>(I, l) * lift_of<R>(I);
         R* S = sm + OFF_S + ((ej * NF + face) * NFN + f) * NV;
 #pragma unroll
         for (int v = 0; v < NV; ++v) S[v] = c * (gown[v] - (A.weak ? R(0) : ao[v]));
-        R mlo = R(0), vlo = R(0);
-#pragma unroll
-        for (int d = 0; d < DIM; ++d)
-          if (d == l) { mlo = lo[1 + d]; vlo = so.v[d]; }
         const R dFo = A.weak ? R(0) : so.rhoe * (mlo + lo[DIM + 1] * vlo);
-        gacc += (double)(c * (R(0.5) * gg - dFo));
+        gacc += (double)(c * ((fb >= 0 ? R(1) : R(0.5)) * gg - dFo));
         continue;
       }
       R vlL = R(0), vlR = R(0);

@@ -846,11 +846,7 @@ dg_status ensure_adjoint(dg_ctx* c) {
   }
   if (c->phys.surface != DG_SURF_RUSANOV && c->phys.surface != DG_SURF_HLLC)
     return fail(c, DG_EUNSUPPORTED, "the adjoint covers the Rusanov and HLLC surface fluxes");
-  if (c->phys.surface == DG_SURF_HLLC) {
-    for (const dg_mesh_desc& m : c->inst)
-      for (int l = 0; l < m.dim; ++l)
-        if (m.periodic[l] != 1) return fail(c, DG_EUNSUPPORTED, "the adjoint of the HLLC flux covers periodic meshes");
-  }
+
   if (c->gacc) return DG_OK;
   const size_t bytes = sizeof(double) * (size_t)c->nv * c->n_nodes_total;
   int maxb = 1;

@@ -6,9 +6,10 @@ the HLLC surface flux on the GPU, against the oracle's dual-number residual:
 - dot-product test <lam, J V> = <J^T lam, V> on the 3D Taylor-Green scheme (N = 4, EC + HLLC),
   FP64 and FP32-mixed;
 - one SSP-RK3 step's adjoint vs chained oracle JVPs through its three stages;
-- the two-point form with Rusanov faces on walls and inflow/outflow boundaries vs central
-  differences of the oracle's residual;
-- the refusal of HLLC on a non-periodic mesh.
+- the two-point form with Rusanov or HLLC faces, and the strong form with HLLC faces, on
+  walls, inflow/outflow and Dirichlet boundaries vs central differences of the oracle's
+  residual;
+- the refusal of a shock-captured context.
 """
 import math
 
@@ -130,11 +131,12 @@ def test_rk_step_vjp_against_chained_oracle_jvps(env, orc):
     assert abs(gb - float(np.sum(lam * W3))) <= 1e-12 * float(np.sum(np.abs(lam * W3)))
 
 
-@pytest.mark.parametrize("bc", [(1, 1, 0, 0, 0, 0), (2, 3, 1, 1, 0, 0), (4, 4, 1, 1, 0, 0)])
-def test_two_point_form_with_boundaries_against_oracle_differences(env, orc, bc):
-    """The two-point form with Rusanov faces on slip walls, supersonic inflow/outflow and
-    Dirichlet faces: ((dL/dU)^T lam) . V against lam . (L(U + eps V) - L(U - eps V))/(2 eps)
-    of the oracle, and likewise for gamma."""
+@pytest.mark.parametrize("bc", [(1, 1, 0, 0, 0, 0), (2, 3, 1, 1, 0, 0), (4, 4, 1, 1, 0, 0), (1, 3, 4, 2, 0, 0)])
+@pytest.mark.parametrize("vol,surf", [(2, 0), (2, 1), (0, 1)])
+def test_boundaries_against_oracle_differences(env, orc, bc, vol, surf):
+    """The two-point form with Rusanov or HLLC faces, and the strong form with HLLC faces, on
+    slip walls, supersonic inflow/outflow and Dirichlet faces: ((dL/dU)^T lam) . V against
+    lam . (L(U + eps V) - L(U - eps V))/(2 eps) of the oracle, and likewise for gamma."""
     torch, dg = env
     N, nel = 3, (3, 2)
     xi, _ = orc.gll(N)
@@ -148,7 +150,7 @@ def test_two_point_form_with_boundaries_against_oracle_differences(env, orc, bc)
     rng = np.random.default_rng(4)
     lam = rng.standard_normal(U.shape)
     V = rng.standard_normal(U.shape) * np.abs(U)
-    S = dg.Solver(dg.Mesh(2, N, nel, lo, hi, bc=bc, bc_state=bs), volume=2, surface=0, gamma=GAMMA)
+    S = dg.Solver(dg.Mesh(2, N, nel, lo, hi, bc=bc, bc_state=bs), volume=vol, surface=surf, gamma=GAMMA)
     d = lambda a: torch.from_numpy(np.ascontiguousarray(a.reshape(4, -1))).cuda()
     Ubar, gbar = S.rhs_vjp(d(U), d(lam))
     S.check()
@@ -156,7 +158,8 @@ def test_two_point_form_with_boundaries_against_oracle_differences(env, orc, bc)
     S.close()
 
     def res(Ux, g=GAMMA):
-        P = orc.Problem(dim=2, N=N, nel=nel, lo=lo, hi=hi, volume=2, surface=0, gamma=g, bc=bc, bc_state=bs)
+        P = orc.Problem(dim=2, N=N, nel=nel, lo=lo, hi=hi, volume=vol, surface=surf, gamma=g, bc=bc,
+                        bc_state=bs)
         return orc.rhs(P, Ux)
 
     eps = 1e-6
@@ -166,10 +169,9 @@ def test_two_point_form_with_boundaries_against_oracle_differences(env, orc, bc)
     assert abs(gbar - gwant) <= 1e-6 * max(abs(gwant), 1.0), (gbar, gwant)
 
 
-def test_hllc_adjoint_refuses_non_periodic_meshes(env, orc):
+def test_adjoint_refuses_shock_capturing(env, orc):
     torch, dg = env
-    lo, hi = (0.0, 0.0), (1.0, 1.0)
-    S = dg.Solver(dg.Mesh(2, 2, (3, 3), lo, hi, bc=(1, 1, 0, 0, 0, 0)), volume=2, surface=1, gamma=GAMMA)
+    S = dg.Solver(dg.Mesh(2, 3, (4, 4), (0.0, 0.0), (1.0, 1.0)), volume=2, surface=1, gamma=GAMMA, shock=True)
     U = torch.ones((4, S.n_doubles // 4), dtype=torch.float64, device="cuda")
     U[3] = 2.5
     with pytest.raises(dg.DGError) as ei:
