@@ -5,7 +5,8 @@ the HLLC surface flux on the GPU, against the oracle's dual-number residual:
   for the two-point form with HLLC or Rusanov and the strong/weak forms with HLLC;
 - dot-product test <lam, J V> = <J^T lam, V> on the 3D Taylor-Green scheme (N = 4, EC + HLLC),
   FP64 and FP32-mixed;
-- one SSP-RK3 step's adjoint vs chained oracle JVPs through its three stages;
+- one SSP-RK3 step's adjoint vs chained oracle JVPs through its three stages, and the
+  checkpointed rollout gradient (autograd) vs the oracle's exact forward-mode gradient;
 - the two-point form with Rusanov or HLLC faces, and the strong form with HLLC faces, on
   walls, inflow/outflow and Dirichlet boundaries vs central differences of the oracle's
   residual;
@@ -178,3 +179,32 @@ def test_adjoint_refuses_shock_capturing(env, orc):
         S.rhs_vjp(U, torch.zeros_like(U))
     assert ei.value.status == dg.DG_EUNSUPPORTED
     S.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 1e-4)])
+def test_rollout_gradient_matches_oracle(env, orc, prec, tol):
+    """The checkpointed rollout gradient of the two-point form + HLLC (segments of 3 steps
+    over 10 steps, the last one partial) in U0 and gamma against the oracle's exact
+    forward-mode gradient."""
+    torch, dg = env
+    from paper_2605_26388_b300.adjoint import rollout
+    P, S = make(orc, dg, 2, 3, 2, 2, 1, prec=prec)
+    U0 = state(orc, P, 7)
+    rng = np.random.default_rng(3)
+    target = U0[0] * (1.0 + 0.01 * rng.standard_normal(U0[0].shape))
+    _, w = orc.gll(3)
+    wq = np.tile(np.multiply.outer(w, w).ravel(), (P.n_elem, 1)) * 0.0625
+    dt, steps = 2e-3, 10
+    g_ref, gg_ref = orc.rollout_grad(P, U0, target, wq, dt, steps)
+    U = dev(torch, U0).requires_grad_(True)
+    gam = torch.tensor(GAMMA, dtype=torch.float64, requires_grad=True)
+    tg = torch.from_numpy(target.reshape(-1)).cuda()
+    wqt = torch.from_numpy(wq.reshape(-1)).cuda()
+    UT = rollout(S, U, gam, dt, steps, 3)
+    loss = 0.5 * torch.sum(wqt * (UT[0] - tg) ** 2)
+    loss.backward()
+    S.check()
+    got = U.grad.cpu().numpy().reshape(U0.shape)
+    S.close()
+    assert np.linalg.norm(got - g_ref) <= tol * np.linalg.norm(g_ref)
+    assert abs(float(gam.grad) - gg_ref) <= tol * abs(gg_ref)
