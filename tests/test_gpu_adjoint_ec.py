@@ -58,7 +58,8 @@ def dev(torch, a):
 # volume: 0 strong, 1 weak, 2 two-point; surface: 0 Rusanov, 1 HLLC
 @pytest.mark.parametrize("dim,N,nel,vol,surf", [(2, 2, 2, 2, 1), (2, 3, 3, 2, 0), (3, 2, 2, 2, 1),
                                                 (2, 3, 3, 0, 1), (2, 2, 3, 1, 1), (3, 3, 2, 2, 0),
-                                                (2, 7, 2, 2, 1), (3, 5, 1, 2, 1)])
+                                                (2, 7, 2, 2, 1), (3, 5, 1, 2, 1), (2, 1, 4, 2, 1),
+                                                (3, 1, 3, 2, 1), (2, 4, 2, 2, 1), (2, 6, 2, 2, 0)])
 def test_rhs_vjp_matches_brute_force_transpose(env, orc, dim, N, nel, vol, surf):
     torch, dg = env
     P, S = make(orc, dg, dim, N, nel, vol, surf)
