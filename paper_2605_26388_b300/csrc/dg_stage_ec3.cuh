@@ -32,7 +32,7 @@ struct EC3 {
   using G = Geo<3, N>;
   static constexpr int NV = 5, NP = G::NP, N1 = G::N1, NFN = G::NFN;
   static constexpr int NF = 6;
-  static constexpr int KRUN = 16;                // consecutive elements along x per run
+  static constexpr int KRUN = 32;                // consecutive elements along x per run
   static constexpr int NJ = 5 * NFN;             // standard face jobs: x+, y-, y+, z-, z+
   static constexpr int T = ((cmax(NP, NJ) + 31) / 32) * 32;
   static constexpr int NO = N1 / 2;              // pair offsets per direction (cyclic ownership)
@@ -91,14 +91,14 @@ struct EC3 {
   }
 
   // Runs: the rows of elements along x (rows in element order) split into runs of KRUN
-  // elements, except the last rows -- about two runs of KRUN per CTA -- which split into runs
+  // elements, except the last rows -- about one run of KRUN per CTA -- which split into runs
   // of KTAIL, so that the CTAs, taking the runs in order, finish within a few elements of one
   // another.  Run q starts at element *e0 and holds *len elements; false past the last run.
   static constexpr int KTAIL = 4;
   static __device__ __forceinline__ bool run_of(const InstArgs& I, int q, int* e0, int* len, int* x0out,
                                                 int* rowout) {
     const int nx = I.nel[0], nrows = I.nel[1] * I.nel[2];
-    const int tail = (2 * (int)gridDim.x * KRUN + nx - 1) / nx;
+    const int tail = ((int)gridDim.x * KRUN + nx - 1) / nx;
     const int ra = tail < nrows ? nrows - tail : 0;  // rows in runs of KRUN
     const int nsa = (nx + KRUN - 1) / KRUN, nsb = (nx + KTAIL - 1) / KTAIL;
     int row, x0, k;
