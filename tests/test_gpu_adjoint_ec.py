@@ -209,3 +209,31 @@ def test_rollout_gradient_matches_oracle(env, orc, prec, tol):
     S.close()
     assert np.linalg.norm(got - g_ref) <= tol * np.linalg.norm(g_ref)
     assert abs(float(gam.grad) - gg_ref) <= tol * abs(gg_ref)
+
+
+def test_step_function_chains_to_the_rollout_gradient(env, orc):
+    """Six chained DGStep calls (the two-point form + HLLC) give the checkpointed rollout's
+    gradient in U0 and gamma: the same kernels in the same order, the gamma contributions
+    summed in another order."""
+    torch, dg = env
+    from paper_2605_26388_b300.adjoint import rollout, step
+    P, S = make(orc, dg, 2, 3, 3, 2, 1)
+    U0 = dev(torch, state(orc, P, 11))
+    target = U0[0].clone() * 1.01
+    dt, n = 2e-3, 6
+
+    def loss_of(UT):
+        return 0.5 * torch.sum((UT[0] - target) ** 2)
+
+    Ua = U0.clone().requires_grad_(True)
+    ga = torch.tensor(GAMMA, dtype=torch.float64, requires_grad=True)
+    U = Ua
+    for _ in range(n):
+        U = step(S, U, ga, dt)
+    loss_of(U).backward()
+    Ub = U0.clone().requires_grad_(True)
+    gb = torch.tensor(GAMMA, dtype=torch.float64, requires_grad=True)
+    loss_of(rollout(S, Ub, gb, dt, n, 4)).backward()
+    S.close()
+    assert torch.equal(Ua.grad, Ub.grad)
+    assert abs(float(ga.grad) - float(gb.grad)) <= 1e-13 * abs(float(gb.grad))
