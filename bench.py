@@ -1016,10 +1016,31 @@ def run_e2e(args, U0, dt, ws, barrier):
     for S in solvers:
         S.close()
     nbytes = U0.nbytes
+    # the host link's own bound: one step's upload and download moved at once, each on its own
+    # stream with plain copies of the same pinned buffers (no kernels)
+    dev = [torch.empty(host_in.shape, dtype=torch.float64, device="cuda") for _ in range(2)]
+
+    def copies():
+        with torch.cuda.stream(streams[0]):
+            dev[0].copy_(host_in, non_blocking=True)
+        with torch.cuda.stream(streams[1]):
+            host_out[1].copy_(dev[1], non_blocking=True)
+
+    copies()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(3):
+        copies()
+    torch.cuda.synchronize()
+    link_ms = 1e3 * (time.perf_counter() - t0) / 3
+    del dev
+    step_ms = 1e3 * e2e_s / args.e2e_steps
     return {"value": weak_value(3 * DOF * args.e2e_steps, ws, e2e_s), "unit": "DOF-updates/s",
             "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "streams": 2,
+            "ms_per_step": step_ms, "link_ms_per_step": link_ms, "link_frac": link_ms / step_ms,
             "note": "per step: dg_set_state from pinned host memory, one SSP-RK3 step, dg_get_state to "
-                    "pinned host memory; consecutive steps alternate between two contexts/streams"}
+                    "pinned host memory; consecutive steps alternate between two contexts/streams; "
+                    "link_ms_per_step: the same upload and download as plain concurrent copies"}
 
 
 if __name__ == "__main__":
