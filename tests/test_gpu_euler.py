@@ -119,6 +119,23 @@ def test_rhs_parity(orc, dg, torch, dim, N, nel, vol, surf, prec):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
+def test_run_walk_with_ragged_runs_and_tail(orc, dg, torch, prec):
+    """The 3D two-point kernel's walk on a mesh large enough for all its run kinds: rows of 40
+    elements split into a run of 32 and a ragged run of 8, and, with 625 rows, the last rows
+    (about one run per CTA) in runs of 4.  The whole residual against the oracle, 1e-12 FP64,
+    1e-5 FP32-mixed, on an anisotropic box."""
+    lo, hi = (0.0, 0.0, 0.0), (2.0, 1.5, 1.2)
+    P, S = setup(orc, dg, torch, 3, 4, (40, 25, 25), 2, 1, prec, lo=lo, hi=hi, p_ref=0.7 if prec else 0.0)
+    U = smooth_state(orc, P, seed=23, rough=0.02)
+    ref = orc.rhs(P, U)
+    got = S.rhs(to_dev(torch, U)).cpu().numpy().reshape(ref.shape)
+    S.check()
+    S.close()
+    tol = 1e-12 if prec == 0 else 1e-5
+    assert rel_l2(got, ref) <= tol, rel_l2(got, ref)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
 def test_density_wave_100_steps(orc, dg, torch, prec):
     """The 2D workload at full size: 16x16, N=3, weak form, Rusanov, CFL 0.5, 100 steps."""
     P, S = setup(orc, dg, torch, 2, 3, 16, 1, 0, prec)
