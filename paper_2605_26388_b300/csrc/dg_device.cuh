@@ -376,36 +376,51 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b) {
   return make_float2(__uint_as_float((unsigned)rd), __uint_as_float((unsigned)(rd >> 32)));
 }
 
-template <int DIM, int L>
-__device__ __forceinline__ void ec_flux_rec(const Q4<float>& a, const Q4<float>& av, const Q4<float>& b,
-                                            const Q4<float>& bv, float igm1, float p_ref, float* F) {
+// The FP32 flux in three parts, so that a caller may evaluate several pairs under one warp
+// vote: the two logarithmic means by their series (ec_log_means), the quotient form where a
+// lane needs it (ec_log_means_fix, under the caller's vote), the flux from the means
+// (ec_flux_assemble).  ec_flux_rec runs the three for one pair.
+struct EcMeans {
+  float2 s, d, u;  // sums, differences and squared relative differences of (rho, beta)
+  float hr, ib;    // rho^ln / 2 and 1 / beta^ln
+  bool lg;         // this lane needs the quotient form for one of the two
+};
+__device__ __forceinline__ EcMeans ec_log_means(const Q4<float>& a, const Q4<float>& b) {
+  EcMeans m;
   const float2 ra = make_float2(a.x, a.y), rb = make_float2(b.x, b.y);  // (rho, beta)
-  const float2 s = __fadd2_rn(ra, rb);
-  const float2 d = sub2(ra, rb);
+  m.s = __fadd2_rn(ra, rb);
+  m.d = sub2(ra, rb);
   float inv;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(inv) : "f"(s.x * s.y));
-  const float2 is = make_float2(s.y * inv, s.x * inv);                  // (1/s_rho, 1/s_beta)
-  const float2 f = __fmul2_rn(d, is);
-  const float2 u = __fmul2_rn(f, f);
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(inv) : "f"(m.s.x * m.s.y));
+  const float2 is = make_float2(m.s.y * inv, m.s.x * inv);                // (1/s_rho, 1/s_beta)
+  const float2 f = __fmul2_rn(m.d, is);
+  m.u = __fmul2_rn(f, f);
   // G/4 and 2 Fs by Horner's rule (immediate coefficients)
-  float G = __fmaf_rn(-0.25f * 0.030194003527336861f, u.x, -0.25f * 44.0f / 945.0f);
-  G = __fmaf_rn(G, u.x, -0.25f * 4.0f / 45.0f);
-  G = __fmaf_rn(G, u.x, -0.25f / 3.0f);
-  G = __fmaf_rn(G, u.x, 0.25f);
-  float Fs = __fmaf_rn(2.0f / 9.0f, u.y, 2.0f / 7.0f);
-  Fs = __fmaf_rn(Fs, u.y, 2.0f / 5.0f);
-  Fs = __fmaf_rn(Fs, u.y, 2.0f / 3.0f);
-  Fs = __fmaf_rn(Fs, u.y, 2.0f);
-  float hr = s.x * G, ib = is.y * Fs;
-  const bool lg = !(u.x < Ar<float>::kLogMeanSeries) || !(u.y < Ar<float>::kLogMeanSeries);
-  if (__any_sync(__activemask(), lg)) {
-    const float2 dl = sub2(make_float2(a.z, a.w), make_float2(b.z, b.w));
-    float r0, r1;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"(dl.x));
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r1) : "f"(d.y));
-    hr = u.x < Ar<float>::kLogMeanSeries ? hr : d.x * r0;
-    ib = u.y < Ar<float>::kLogMeanSeries ? ib : dl.y * r1;
-  }
+  float G = __fmaf_rn(-0.25f * 0.030194003527336861f, m.u.x, -0.25f * 44.0f / 945.0f);
+  G = __fmaf_rn(G, m.u.x, -0.25f * 4.0f / 45.0f);
+  G = __fmaf_rn(G, m.u.x, -0.25f / 3.0f);
+  G = __fmaf_rn(G, m.u.x, 0.25f);
+  float Fs = __fmaf_rn(2.0f / 9.0f, m.u.y, 2.0f / 7.0f);
+  Fs = __fmaf_rn(Fs, m.u.y, 2.0f / 5.0f);
+  Fs = __fmaf_rn(Fs, m.u.y, 2.0f / 3.0f);
+  Fs = __fmaf_rn(Fs, m.u.y, 2.0f);
+  m.hr = m.s.x * G;
+  m.ib = is.y * Fs;
+  m.lg = !(m.u.x < Ar<float>::kLogMeanSeries) || !(m.u.y < Ar<float>::kLogMeanSeries);
+  return m;
+}
+__device__ __forceinline__ void ec_log_means_fix(const Q4<float>& a, const Q4<float>& b, EcMeans& m) {
+  const float2 dl = sub2(make_float2(a.z, a.w), make_float2(b.z, b.w));
+  float r0, r1;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"(dl.x));
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r1) : "f"(m.d.y));
+  m.hr = m.u.x < Ar<float>::kLogMeanSeries ? m.hr : m.d.x * r0;
+  m.ib = m.u.y < Ar<float>::kLogMeanSeries ? m.ib : dl.y * r1;
+}
+template <int DIM, int L>
+__device__ __forceinline__ void ec_flux_assemble(const Q4<float>& av, const Q4<float>& bv, const EcMeans& m,
+                                                 float igm1, float p_ref, float* F) {
+  const float hr = m.hr, ib = m.ib;
   const float2 vs01 = __fadd2_rn(make_float2(av.x, av.y), make_float2(bv.x, bv.y));
   const float vs2 = av.z + bv.z;
   const float2 pv = __fmul2_rn(make_float2(av.x, av.y), make_float2(bv.x, bv.y));
@@ -424,6 +439,14 @@ __device__ __forceinline__ void ec_flux_rec(const Q4<float>& a, const Q4<float>&
   const float e1 = frho * __fmaf_rn(0.5f, vab, igm1 * ib);
   const float pt = __fmaf_rn(av.w, vbl, bv.w * val);
   F[DIM + 1] = __fmaf_rn(0.5f, __fmaf_rn(p_ref, vsl, pt), e1);
+}
+
+template <int DIM, int L>
+__device__ __forceinline__ void ec_flux_rec(const Q4<float>& a, const Q4<float>& av, const Q4<float>& b,
+                                            const Q4<float>& bv, float igm1, float p_ref, float* F) {
+  EcMeans m = ec_log_means(a, b);
+  if (__any_sync(__activemask(), m.lg)) ec_log_means_fix(a, b, m);
+  ec_flux_assemble<DIM, L>(av, bv, m, igm1, p_ref, F);
 }
 
 template <int DIM, int L>

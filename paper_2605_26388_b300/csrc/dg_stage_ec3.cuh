@@ -272,18 +272,47 @@ struct EC3 {
     R c[NO];
     coefs(sm + OFF_D + (L * N1 + i) * NO, c);
     const Q4<R>* Q = rec(sm);
+    if constexpr (sizeof(R) == 4 && N1 == 5) {
+      // both pairs of the line (offsets 1 and 2) under one warp vote for the logarithmic
+      // means' quotient form, so that their evaluations interleave in one basic block
+      R F[2][NV];
+      Q4<R> aj[2], bj[2];
+      EcMeans m[2];
 #pragma unroll
-    for (int o = 1; o <= NO; ++o) {
-      if (2 * o == N1 && i >= N1 / 2) break;
-      const int nj = (i + o < N1) ? nd + o * S : nd + (o - N1) * S;
-      const Q4<R> aj = Q[nj], bj = Q[NP + nj];
-      R F[NV];
-      ec_flux_rec<3, L>(ai, bi, aj, bj, igm1, p_ref, F);
+      for (int o = 1; o <= 2; ++o) {
+        const int nj = (i + o < N1) ? nd + o * S : nd + (o - N1) * S;
+        aj[o - 1] = Q[nj];
+        bj[o - 1] = Q[NP + nj];
+        m[o - 1] = ec_log_means(ai, aj[o - 1]);
+      }
+      if (__any_sync(__activemask(), m[0].lg || m[1].lg)) {
+        ec_log_means_fix(ai, aj[0], m[0]);
+        ec_log_means_fix(ai, aj[1], m[1]);
+      }
 #pragma unroll
-      for (int v = 0; v < NV; ++v) acc[v] -= c[o - 1] * F[v];
-      R* X = xslot(sm, L, o);
-      reinterpret_cast<Q4<R>*>(X)[nd] = Q4<R>{F[0], F[1], F[2], F[3]};
-      X[4 * NP + nd] = F[4];
+      for (int o = 1; o <= 2; ++o) ec_flux_assemble<3, L>(bi, bj[o - 1], m[o - 1], igm1, p_ref, F[o - 1]);
+#pragma unroll
+      for (int o = 1; o <= 2; ++o) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) acc[v] -= c[o - 1] * F[o - 1][v];
+        R* X = xslot(sm, L, o);
+        reinterpret_cast<Q4<R>*>(X)[nd] = Q4<R>{F[o - 1][0], F[o - 1][1], F[o - 1][2], F[o - 1][3]};
+        X[4 * NP + nd] = F[o - 1][4];
+      }
+    } else {
+#pragma unroll
+      for (int o = 1; o <= NO; ++o) {
+        if (2 * o == N1 && i >= N1 / 2) break;
+        const int nj = (i + o < N1) ? nd + o * S : nd + (o - N1) * S;
+        const Q4<R> aj = Q[nj], bj = Q[NP + nj];
+        R F[NV];
+        ec_flux_rec<3, L>(ai, bi, aj, bj, igm1, p_ref, F);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) acc[v] -= c[o - 1] * F[v];
+        R* X = xslot(sm, L, o);
+        reinterpret_cast<Q4<R>*>(X)[nd] = Q4<R>{F[0], F[1], F[2], F[3]};
+        X[4 * NP + nd] = F[4];
+      }
     }
   }
 
