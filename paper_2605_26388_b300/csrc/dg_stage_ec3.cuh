@@ -272,41 +272,59 @@ struct EC3 {
     R c[NO];
     coefs(sm + OFF_D + (L * N1 + i) * NO, c);
     const Q4<R>* Q = rec(sm);
-    if constexpr (sizeof(R) == 4 && N1 == 5) {
-      // both pairs of the line (offsets 1 and 2) under one warp vote for the logarithmic
-      // means' quotient form, so that their evaluations interleave in one basic block
-      R F[2][NV];
-      Q4<R> aj[2], bj[2];
-      EcMeans m[2];
+#pragma unroll
+    for (int o = 1; o <= NO; ++o) {
+      if (2 * o == N1 && i >= N1 / 2) break;
+      const int nj = (i + o < N1) ? nd + o * S : nd + (o - N1) * S;
+      const Q4<R> aj = Q[nj], bj = Q[NP + nj];
+      R F[NV];
+      ec_flux_rec<3, L>(ai, bi, aj, bj, igm1, p_ref, F);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) acc[v] -= c[o - 1] * F[v];
+      R* X = xslot(sm, L, o);
+      reinterpret_cast<Q4<R>*>(X)[nd] = Q4<R>{F[0], F[1], F[2], F[3]};
+      X[4 * NP + nd] = F[4];
+    }
+  }
+
+  // N = 4, FP32: all six pairs of a node (two per direction) with one warp vote for the log
+  // means' quotient form, so that their six evaluations interleave in one basic block; the
+  // same operations, and the same order of the accumulation, as own_pairs<0..2>
+  static __device__ __forceinline__ void own_pairs_all(R* sm, const Role& r, const Q4<R>& ai, const Q4<R>& bi,
+                                                       R igm1, R p_ref, R* acc) {
+    const int nd = r.nd;
+    const Q4<R>* Q = rec(sm);
+    EcMeans m[3][2];
+    int nj[3][2];
+    bool lg = false;
+#pragma unroll
+    for (int L = 0; L < 3; ++L) {
+      const int S = L == 0 ? 1 : (L == 1 ? N1 : N1 * N1);
+      const int i = r.pos[L];
 #pragma unroll
       for (int o = 1; o <= 2; ++o) {
-        const int nj = (i + o < N1) ? nd + o * S : nd + (o - N1) * S;
-        aj[o - 1] = Q[nj];
-        bj[o - 1] = Q[NP + nj];
-        m[o - 1] = ec_log_means(ai, aj[o - 1]);
+        nj[L][o - 1] = (i + o < N1) ? nd + o * S : nd + (o - N1) * S;
+        m[L][o - 1] = ec_log_means(ai, Q[nj[L][o - 1]]);
+        lg = lg || m[L][o - 1].lg;
       }
-      if (__any_sync(__activemask(), m[0].lg || m[1].lg)) {
-        ec_log_means_fix(ai, aj[0], m[0]);
-        ec_log_means_fix(ai, aj[1], m[1]);
-      }
+    }
+    if (__any_sync(__activemask(), lg)) {
 #pragma unroll
-      for (int o = 1; o <= 2; ++o) ec_flux_assemble<3, L>(bi, bj[o - 1], m[o - 1], igm1, p_ref, F[o - 1]);
+      for (int L = 0; L < 3; ++L)
+#pragma unroll
+        for (int o = 1; o <= 2; ++o) ec_log_means_fix(ai, Q[nj[L][o - 1]], m[L][o - 1]);
+    }
+#pragma unroll
+    for (int L = 0; L < 3; ++L) {
+      R c[NO];
+      coefs(sm + OFF_D + (L * N1 + r.pos[L]) * NO, c);
 #pragma unroll
       for (int o = 1; o <= 2; ++o) {
-#pragma unroll
-        for (int v = 0; v < NV; ++v) acc[v] -= c[o - 1] * F[o - 1][v];
-        R* X = xslot(sm, L, o);
-        reinterpret_cast<Q4<R>*>(X)[nd] = Q4<R>{F[o - 1][0], F[o - 1][1], F[o - 1][2], F[o - 1][3]};
-        X[4 * NP + nd] = F[o - 1][4];
-      }
-    } else {
-#pragma unroll
-      for (int o = 1; o <= NO; ++o) {
-        if (2 * o == N1 && i >= N1 / 2) break;
-        const int nj = (i + o < N1) ? nd + o * S : nd + (o - N1) * S;
-        const Q4<R> aj = Q[nj], bj = Q[NP + nj];
         R F[NV];
-        ec_flux_rec<3, L>(ai, bi, aj, bj, igm1, p_ref, F);
+        const Q4<R> bj = Q[NP + nj[L][o - 1]];
+        if (L == 0) ec_flux_assemble<3, 0>(bi, bj, m[L][o - 1], igm1, p_ref, F);
+        else if (L == 1) ec_flux_assemble<3, 1>(bi, bj, m[L][o - 1], igm1, p_ref, F);
+        else ec_flux_assemble<3, 2>(bi, bj, m[L][o - 1], igm1, p_ref, F);
 #pragma unroll
         for (int v = 0; v < NV; ++v) acc[v] -= c[o - 1] * F[v];
         R* X = xslot(sm, L, o);
@@ -471,9 +489,13 @@ struct EC3 {
     auto pairs = [&]() {
       const Q4<R>* Q = rec(sm);
       const Q4<R> ai = Q[nd], bi = Q[NP + nd];
-      own_pairs<0>(sm, r, ai, bi, igm1, p_ref, acc);
-      own_pairs<1>(sm, r, ai, bi, igm1, p_ref, acc);
-      own_pairs<2>(sm, r, ai, bi, igm1, p_ref, acc);
+      if constexpr (sizeof(R) == 4 && N1 == 5) {
+        own_pairs_all(sm, r, ai, bi, igm1, p_ref, acc);
+      } else {
+        own_pairs<0>(sm, r, ai, bi, igm1, p_ref, acc);
+        own_pairs<1>(sm, r, ai, bi, igm1, p_ref, acc);
+        own_pairs<2>(sm, r, ai, bi, igm1, p_ref, acc);
+      }
     };
     auto face = [&]() {
       const double* tr = S + ST_T + (r.face - 1) * NV * NFN + r.f;
