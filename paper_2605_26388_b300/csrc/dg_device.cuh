@@ -605,8 +605,9 @@ __device__ __forceinline__ void hll(const R* uL, const Prim<DIM, R>& a, const R*
   }
 }
 
-// HLLC (Toro, Spruce and Speares): branches S_L >= 0 -> F_L; S* >= 0 -> F*_L; S_R > 0 ->
-// F*_R; else F_R.  Star state U*_K = rho_K (S_K - u_K)/(S_K - S*) (1, S* e_L + tangential,
+// HLLC (Toro, Spruce and Speares): S_L >= 0 -> F_L; S* >= 0 -> F*_L; S_R > 0 -> F*_R; else
+// F_R (the star flux is always formed and the upwind cases select over it, without a
+// branch).  Star state U*_K = rho_K (S_K - u_K)/(S_K - S*) (1, S* e_L + tangential,
 // E_K/rho_K + (S* - u_K)(S* + p_K/(rho_K (S_K - u_K)))); p_R - p_L is taken as pd_R - pd_L.
 // Written in jump form, identical in exact arithmetic: with m_K = rho_K (S_K - u_K),
 //   S* - u_L = (dp - m_R du)/(m_L - m_R),  S* - u_R = (dp - m_L du)/(m_L - m_R),
@@ -628,15 +629,10 @@ __device__ __forceinline__ void hllc(const R* uL, const Prim<DIM, R>& a, const R
   const R iden = Ar<R>::rcp(mL - mR);
   const R dL = (dp - mR * du) * iden;  // S* - u_L
   const R Ss = a.v[L] + dL;
-  if (SL >= R(0)) {
-#pragma unroll
-    for (int v = 0; v < DIM + 2; ++v) F[v] = FL[v];
-  } else if (SR <= R(0) && Ss < R(0)) {
-#pragma unroll
-    for (int v = 0; v < DIM + 2; ++v) F[v] = FR[v];
-  } else {
+  const bool upl = SL >= R(0), upr = SR <= R(0) && Ss < R(0);
+  {
     // one star state: left if S* >= 0, else right (selects, not pointers, keep it in
-    // registers)
+    // registers); the upwind cases select F_L or F_R over it, without a branch
     const bool left = (Ss >= R(0));
     const R SK = left ? SL : SR;
     const R mK = left ? mL : mR;
@@ -655,7 +651,7 @@ __device__ __forceinline__ void hllc(const R* uL, const Prim<DIM, R>& a, const R
       else if (v == DIM + 1) w = sd * (EK + pK + mK * Ss);
       else if (v == 1 + L) w = rs * SK;
       else w = rs * (left ? a.v[v - 1] : b.v[v - 1]);
-      F[v] = FKv + w;
+      F[v] = upl ? FL[v] : (upr ? FR[v] : FKv + w);
     }
   }
 }

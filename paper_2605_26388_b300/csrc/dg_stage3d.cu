@@ -42,43 +42,58 @@ static cudaError_t launch_one(const StageArgs& a, cudaStream_t s) {
 }
 
 // The two-point form of elements with 64 or more nodes: the run-walking kernel (EC3).
-template <int N, class R>
+template <int N, class R, int SPEC>
 struct EC3Grid {
   static int ctas;
 };
-template <int N, class R>
-int EC3Grid<N, R>::ctas = 0;
+template <int N, class R, int SPEC>
+int EC3Grid<N, R, SPEC>::ctas = 0;
 
-template <int N, class R>
-static cudaError_t prepare_ec3() {
-  using K = EC3<N, R>;
-  cudaError_t e = cudaFuncSetAttribute(k_euler_ec3<N, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+template <int N, class R, int SPEC>
+static cudaError_t prepare_ec3_s() {
+  using K = EC3<N, R, SPEC>;
+  cudaError_t e = cudaFuncSetAttribute(k_euler_ec3<N, R, SPEC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)K::smem_bytes());
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per_sm = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_euler_ec3<N, R>, K::T, K::smem_bytes());
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_euler_ec3<N, R, SPEC>, K::T, K::smem_bytes());
   if (e != cudaSuccess) return e;
-  EC3Grid<N, R>::ctas = sms * (per_sm > 0 ? per_sm : 1);
+  EC3Grid<N, R, SPEC>::ctas = sms * (per_sm > 0 ? per_sm : 1);
   return cudaSuccess;
 }
 
 template <int N, class R>
-static cudaError_t launch_ec3(const StageArgs& a, cudaStream_t s) {
-  using K = EC3<N, R>;
+static cudaError_t prepare_ec3() {
+  cudaError_t e = prepare_ec3_s<N, R, 0>();
+  if (e == cudaSuccess) e = prepare_ec3_s<N, R, 1>();
+  return e;
+}
+
+template <int N, class R, int SPEC>
+static cudaError_t launch_ec3_s(const StageArgs& a, cudaStream_t s) {
+  using K = EC3<N, R, SPEC>;
   // the runs of KRUN elements per row (a lower bound of the kernel's run count, which splits
   // the last rows into shorter runs): every CTA's first run exists
   const int nseg = (a.inst.nel[0] + K::KRUN - 1) / K::KRUN;
   const long long runs = (long long)nseg * a.inst.nel[1] * a.inst.nel[2];
   if (a.inst.n_elem == 0) return cudaSuccess;
-  if (EC3Grid<N, R>::ctas == 0) {
-    cudaError_t e = prepare_ec3<N, R>();
+  if (EC3Grid<N, R, SPEC>::ctas == 0) {
+    cudaError_t e = prepare_ec3_s<N, R, SPEC>();
     if (e != cudaSuccess) return e;
   }
-  const int blocks = runs < EC3Grid<N, R>::ctas ? (int)runs : EC3Grid<N, R>::ctas;
-  k_euler_ec3<N, R><<<blocks, K::T, K::smem_bytes(), s>>>(a);
+  const int blocks = runs < EC3Grid<N, R, SPEC>::ctas ? (int)runs : EC3Grid<N, R, SPEC>::ctas;
+  k_euler_ec3<N, R, SPEC><<<blocks, K::T, K::smem_bytes(), s>>>(a);
   return cudaGetLastError();
+}
+
+// periodic meshes with the HLLC flux (no domain faces, one surface flux) take the
+// specialisation whose face job has no branch
+template <int N, class R>
+static cudaError_t launch_ec3(const StageArgs& a, cudaStream_t s) {
+  if (!a.inst.nonper && a.surface == 1) return launch_ec3_s<N, R, 1>(a, s);
+  return launch_ec3_s<N, R, 0>(a, s);
 }
 
 template <int DIM, int N>

@@ -27,7 +27,9 @@
 
 namespace dg {
 
-template <int N, class R>
+// SPEC = 1: the specialisation for periodic meshes with the HLLC surface flux (no domain
+// faces, no dispatch on the surface flux), whose face job has no branch
+template <int N, class R, int SPEC = 0>
 struct EC3 {
   using G = Geo<3, N>;
   static constexpr int NV = 5, NP = G::NP, N1 = G::N1, NFN = G::NFN;
@@ -377,7 +379,8 @@ struct EC3 {
     trace_momentum<3>(po, own);
     own[4] = sm[OFF_E + ndo];
     R Fs[NV];
-    const int fb = I.nonper ? boundary_face(I, 3, e, l, side) : -1;
+    int fb = -1;
+    if constexpr (SPEC == 0) fb = I.nonper ? boundary_face(I, 3, e, l, side) : -1;
     if (fb >= 0) {
       boundary_flux<3, R>(I, fb, l, side, own, po, A.surface, gamma, igm1, p_ref, A.pd.gm1, A.pd.p_ref, k.hgm1, Fs);
     } else {
@@ -407,7 +410,8 @@ struct EC3 {
       }
       const Prim<3, R>& a = side ? po : pn;
       const Prim<3, R>& b = side ? pn : po;
-      surface_flux<3, 0>(A.surface, uL, a, uR, b, gamma, igm1, p_ref, Fs);  // the single call site
+      if constexpr (SPEC == 1) hllc<3, 0>(uL, a, uR, b, gamma, Fs);  // the single call site
+      else surface_flux<3, 0>(A.surface, uL, a, uR, b, gamma, igm1, p_ref, Fs);
     }
     const R lf = (side ? R(-1) : R(1)) * sv<R>(I, l) * liftv<R>(I);
     // back to Cartesian components: face axis k is Cartesian direction (l + k) mod 3
@@ -507,8 +511,13 @@ struct EC3 {
     };
     constexpr int NB = NP < NJ ? NP : NJ;
     if (t < NB) {
-      pairs();
-      face();
+      if constexpr (SPEC == 1) {  // a branch-free face job first: it shares a basic block with
+        face();                   // the pairs' log means, so their evaluations interleave
+        pairs();
+      } else {
+        pairs();
+        face();
+      }
     } else {
       if (node) pairs();
       if (t < NJ) face();
@@ -697,9 +706,9 @@ struct EC3 {
   }
 };
 
-template <int N, class R>
-__global__ void __launch_bounds__(EC3<N, R>::T, EC3<N, R>::MINB) k_euler_ec3(const StageArgs A) {
-  EC3<N, R>::run(A);
+template <int N, class R, int SPEC>
+__global__ void __launch_bounds__(EC3<N, R, SPEC>::T, EC3<N, R, SPEC>::MINB) k_euler_ec3(const StageArgs A) {
+  EC3<N, R, SPEC>::run(A);
 }
 
 }  // namespace dg
