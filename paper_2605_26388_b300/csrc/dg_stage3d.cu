@@ -88,11 +88,12 @@ static cudaError_t launch_ec3_s(const StageArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// periodic meshes with the HLLC flux (no domain faces, one surface flux) take the
-// specialisation whose face job has no branch
+// the plain stage update on periodic meshes with the HLLC flux (no domain faces, one surface
+// flux, no RK54 sum, floor or shock flag) takes the specialisation without those branches
 template <int N, class R>
 static cudaError_t launch_ec3(const StageArgs& a, cudaStream_t s) {
-  if (!a.inst.nonper && a.surface == 1) return launch_ec3_s<N, R, 1>(a, s);
+  if (!a.inst.nonper && a.surface == 1 && a.mode == 1 && !a.acc && !a.floor_on && !a.alpha)
+    return launch_ec3_s<N, R, 1>(a, s);
   return launch_ec3_s<N, R, 0>(a, s);
 }
 

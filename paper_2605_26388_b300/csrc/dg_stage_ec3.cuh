@@ -27,8 +27,9 @@
 
 namespace dg {
 
-// SPEC = 1: the specialisation for periodic meshes with the HLLC surface flux (no domain
-// faces, no dispatch on the surface flux), whose face job has no branch
+// SPEC = 1: the specialisation for the plain SSP-RK3 stage on periodic meshes with the HLLC
+// surface flux (no domain faces, no dispatch on the surface flux, no RK54 running sum,
+// positivity floor or shock flag), whose face job and update have no branch on those
 template <int N, class R, int SPEC = 0>
 struct EC3 {
   using G = Geo<3, N>;
@@ -564,15 +565,7 @@ struct EC3 {
       for (int v = 0; v < NV; ++v) finite = finite && fabsf(acc[v]) < INFINITY;
     }
     double res[NV];
-    if (A.mode == 1 && A.alpha && A.alpha[e] > 0.0) {  // shock-flagged: the DG residual only
-#pragma unroll
-      for (int v = 0; v < NV; ++v) A.ldg[v * A.stride + gi] = Ar<R>::widen(acc[v]);
-      return;
-    }
-    if (A.mode == 0) {
-#pragma unroll
-      for (int v = 0; v < NV; ++v) res[v] = wide(acc[v]);
-    } else {
+    if constexpr (SPEC == 1) {  // a plain stage update (no RK54 sum, floor or shock flag)
       const R cbdt = k.cbdt;
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
@@ -580,24 +573,42 @@ struct EC3 {
         if (need_un) x = fma(A.ca, un[v], x);
         res[v] = x;
       }
-      if (A.acc) {
-        const R abdt = k.abdt;
+    } else {
+      if (A.mode == 1 && A.alpha && A.alpha[e] > 0.0) {  // shock-flagged: the DG residual only
+#pragma unroll
+        for (int v = 0; v < NV; ++v) A.ldg[v * A.stride + gi] = Ar<R>::widen(acc[v]);
+        return;
+      }
+      if (A.mode == 0) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) res[v] = wide(acc[v]);
+      } else {
+        const R cbdt = k.cbdt;
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-          double y = fma(A.acc_b, S[v * NP + nd], wide(abdt * acc[v]));
-          if (A.acc_a != 0.0) y = fma(A.acc_a, A.acc[v * A.stride + gi], y);
-          A.acc[v * A.stride + gi] = y;
+          double x = fma(A.cb, S[v * NP + nd], wide(cbdt * acc[v]));
+          if (need_un) x = fma(A.ca, un[v], x);
+          res[v] = x;
         }
-      }
-      if (A.floor_on) {
-        if (A.rho_floor > 0.0 && res[0] < A.rho_floor) res[0] = A.rho_floor;
-        double kin = 0.0;
+        if (A.acc) {
+          const R abdt = k.abdt;
 #pragma unroll
-        for (int d = 0; d < 3; ++d) kin += res[1 + d] * res[1 + d] / res[0];
-        const double p = (A.gamma - 1.0) * (res[4] - 0.5 * kin);
-        if (A.p_floor > 0.0 && p < A.p_floor) res[4] = A.p_floor / (A.gamma - 1.0) + 0.5 * kin;
+          for (int v = 0; v < NV; ++v) {
+            double y = fma(A.acc_b, S[v * NP + nd], wide(abdt * acc[v]));
+            if (A.acc_a != 0.0) y = fma(A.acc_a, A.acc[v * A.stride + gi], y);
+            A.acc[v * A.stride + gi] = y;
+          }
+        }
+        if (A.floor_on) {
+          if (A.rho_floor > 0.0 && res[0] < A.rho_floor) res[0] = A.rho_floor;
+          double kin = 0.0;
 #pragma unroll
-        for (int v = 0; v < NV; ++v) finite = finite && finite64(res[v]);
+          for (int d = 0; d < 3; ++d) kin += res[1 + d] * res[1 + d] / res[0];
+          const double p = (A.gamma - 1.0) * (res[4] - 0.5 * kin);
+          if (A.p_floor > 0.0 && p < A.p_floor) res[4] = A.p_floor / (A.gamma - 1.0) + 0.5 * kin;
+#pragma unroll
+          for (int v = 0; v < NV; ++v) finite = finite && finite64(res[v]);
+        }
       }
     }
 #pragma unroll
