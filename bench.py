@@ -437,7 +437,7 @@ def main():
         ach = alg / (launch_ms * 1e-3) / 1e9
         return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                 "traffic": ncu_figure("traffic_" + prec) if NEL == 64 else None, "peak_kind": peak_kind,
-                "kernel": "k_euler_ec3<4," + ("float" if prec == "fp32_mixed" else "double") + ",1> (periodic HLLC)",
+                "kernel": "k_euler_ec3<4," + ("float" if prec == "fp32_mixed" else "double") + ",1|2> (plain SSP-RK3 stage, periodic HLLC)",
                 "avg_launch_ms": launch_ms, "alg_bytes_per_launch": alg, "kernel_hash": kernel_hash()}
 
     value = weak_value(3 * DOF * args.steps, ws, ms32 * 1e-3) if ms32 else None

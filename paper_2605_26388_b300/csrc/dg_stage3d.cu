@@ -68,6 +68,7 @@ template <int N, class R>
 static cudaError_t prepare_ec3() {
   cudaError_t e = prepare_ec3_s<N, R, 0>();
   if (e == cudaSuccess) e = prepare_ec3_s<N, R, 1>();
+  if (e == cudaSuccess) e = prepare_ec3_s<N, R, 2>();
   return e;
 }
 
@@ -89,11 +90,12 @@ static cudaError_t launch_ec3_s(const StageArgs& a, cudaStream_t s) {
 }
 
 // the plain stage update on periodic meshes with the HLLC flux (no domain faces, one surface
-// flux, no RK54 sum, floor or shock flag) takes the specialisation without those branches
+// flux, no RK54 sum, floor or shock flag) takes the specialisations without those branches:
+// SPEC 1 for the stages that read U^n, SPEC 2 for the first stage
 template <int N, class R>
 static cudaError_t launch_ec3(const StageArgs& a, cudaStream_t s) {
   if (!a.inst.nonper && a.surface == 1 && a.mode == 1 && !a.acc && !a.floor_on && !a.alpha)
-    return launch_ec3_s<N, R, 1>(a, s);
+    return a.need_un ? launch_ec3_s<N, R, 1>(a, s) : launch_ec3_s<N, R, 2>(a, s);
   return launch_ec3_s<N, R, 0>(a, s);
 }
 

@@ -27,9 +27,11 @@
 
 namespace dg {
 
-// SPEC = 1: the specialisation for the plain SSP-RK3 stage on periodic meshes with the HLLC
-// surface flux (no domain faces, no dispatch on the surface flux, no RK54 running sum,
-// positivity floor or shock flag), whose face job and update have no branch on those
+// SPEC = 1, 2: the specialisations for the plain SSP-RK3 stage on periodic meshes with the
+// HLLC surface flux (no domain faces, no dispatch on the surface flux, no RK54 running sum,
+// positivity floor or shock flag), whose face job and update have no branch on those; SPEC 1
+// for the stages that read U^n (2 and 3), SPEC 2 for the first, which does not -- the U^n
+// loads and prefetch become unconditional or absent
 template <int N, class R, int SPEC = 0>
 struct EC3 {
   using G = Geo<3, N>;
@@ -411,7 +413,7 @@ struct EC3 {
       }
       const Prim<3, R>& a = side ? po : pn;
       const Prim<3, R>& b = side ? pn : po;
-      if constexpr (SPEC == 1) hllc<3, 0>(uL, a, uR, b, gamma, Fs);  // the single call site
+      if constexpr (SPEC >= 1) hllc<3, 0>(uL, a, uR, b, gamma, Fs);  // the single call site
       else surface_flux<3, 0>(A.surface, uL, a, uR, b, gamma, igm1, p_ref, Fs);
     }
     const R lf = (side ? R(-1) : R(1)) * sv<R>(I, l) * liftv<R>(I);
@@ -512,7 +514,7 @@ struct EC3 {
     };
     constexpr int NB = NP < NJ ? NP : NJ;
     if (t < NB) {
-      if constexpr (SPEC == 1) {  // a branch-free face job first: it shares a basic block with
+      if constexpr (SPEC >= 1) {  // a branch-free face job first: it shares a basic block with
         face();                   // the pairs' log means, so their evaluations interleave
         pairs();
       } else {
@@ -565,7 +567,7 @@ struct EC3 {
       for (int v = 0; v < NV; ++v) finite = finite && fabsf(acc[v]) < INFINITY;
     }
     double res[NV];
-    if constexpr (SPEC == 1) {  // a plain stage update (no RK54 sum, floor or shock flag)
+    if constexpr (SPEC >= 1) {  // a plain stage update (no RK54 sum, floor or shock flag)
       const R cbdt = k.cbdt;
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
@@ -639,7 +641,7 @@ struct EC3 {
     const Role r = role();
     const bool node = threadIdx.x < NP;
     load_ops(sm, A.Dv, I);
-    const bool need_un = A.need_un != 0;
+    const bool need_un = SPEC == 0 ? A.need_un != 0 : SPEC == 1;
     __shared__ int s_next;  // the run claimed ahead (thread 0 writes it, after a barrier)
     const int t = threadIdx.x;
     Walk w = walk_start(I);
