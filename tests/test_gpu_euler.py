@@ -118,6 +118,48 @@ def test_rhs_parity(orc, dg, torch, dim, N, nel, vol, surf, prec):
     assert rel_l2(got, ref) <= tol, rel_l2(got, ref)
 
 
+# Increment bars (mass, momentum, energy) of two SSP-RK3 steps of the perturbed Taylor-Green
+# state on 12^3 at CFL 0.25: against the oracle, about 3x the FP32-mixed levels measured on
+# B300 (1.2e-5, 4.9e-6, 1.2e-5); between the specialised and the generic kernel, about 5x
+# (FP32-mixed, 4e-7) and 20x (FP64, 5e-15) the measured levels.  The two kernels differ only
+# in where the compiler fuses a multiply with an add, so their results agree to rounding and
+# not bit for bit; a dropped term or a wrong coefficient in either moves the increment by
+# O(1) relative.
+SPEC_INC_ORACLE = {0: (1e-10,) * 3, 1: (4e-5, 1.5e-5, 4e-5)}
+SPEC_INC_MUTUAL = {0: (1e-13,) * 3, 1: (2e-6, 1e-6, 2e-6)}
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_specialised_stage_matches_generic(orc, dg, torch, prec):
+    """The plain SSP-RK3 stage on a periodic mesh with HLLC runs as the 3D two-point kernel's
+    specialisations (no boundary, flux-kind, RK54, floor or shock branches; with and without
+    U^n); a context with positivity floors too low to act runs the generic kernel on the same
+    problem.  Two steps of each against the oracle, and against each other."""
+    N, nel = 4, 12
+    xi, _ = orc.gll(N)
+    U0 = wl.perturbed(wl.taylor_green_3d(nel, xi, 0.1, GAMMA), 3, 1e-3)
+    P = orc.Problem(dim=3, N=N, nel=(nel,) * 3, lo=(0.0,) * 3, hi=(2 * math.pi,) * 3, volume=2, surface=1,
+                    gamma=GAMMA)
+    dt = orc.max_dt(P, U0, 0.25)
+    ref = orc.rk3(P, U0, dt, 2)
+    out = []
+    for floor in (0.0, 1e-300):
+        S = dg.Solver(dg.Mesh(3, N, (nel,) * 3, (0.0,) * 3, (2 * math.pi,) * 3), volume=2, surface=1,
+                      precision=prec, gamma=GAMMA, p_ref=P_TGV if prec else 0.0, rho_floor=floor, p_floor=floor)
+        S.set_state(to_dev(torch, U0))
+        S.rk_step(dt, 2)
+        S.check()
+        got = S.get_state().cpu().numpy().reshape(ref.shape)
+        S.close()
+        tol = 1e-12 if prec == 0 else 1e-5
+        assert rel_l2(got, ref) <= tol, (floor, rel_l2(got, ref))
+        inc = rel_l2_groups(got - U0, ref - U0)
+        assert all(e <= b for e, b in zip(inc, SPEC_INC_ORACLE[prec])), (floor, inc)
+        out.append(got)
+    mutual = rel_l2_groups(out[0] - U0, out[1] - U0)
+    assert all(e <= b for e, b in zip(mutual, SPEC_INC_MUTUAL[prec])), mutual
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 def test_run_walk_with_ragged_runs_and_tail(orc, dg, torch, prec):
     """The 3D two-point kernel's walk on a mesh large enough for all its run kinds: rows of 40
