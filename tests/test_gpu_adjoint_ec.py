@@ -104,6 +104,63 @@ def test_taylor_green_scheme_dot_product(env, orc, prec, tol, gtol):
     assert abs(g - float(np.sum(lam * Jg))) <= gtol * float(np.sum(np.abs(lam * Jg)))
 
 
+P_TGV = 1.0 / (GAMMA * 0.1 ** 2)  # background pressure of the Mach 0.1 vortex
+
+
+@pytest.mark.parametrize("prec,tol,gtol,ctol,cgtol", [(0, 1e-12, 1e-12, 1e-14, 1e-12),
+                                                      (1, 3e-8, 3e-5, 1e-6, 3e-5)])
+def test_taylor_green_full_size_properties(env, orc, prec, tol, gtol, ctol, cgtol):
+    """The timed adjoint workload at full size, in its launch configuration: 32^3 elements of
+    [0, 2 pi]^3, N = 4, two-point form + HLLC, the Mach 0.1 vortex (perturbed), FP32-mixed
+    with the vortex's background pressure as p_ref.  Two properties that hold at any size.
+    (1) The dot-product identity <lam, J V> = <J^T lam, V> and lam . dL/dgamma against one
+    dual-number residual of the oracle each.  Measured 4e-19 / 7e-16 (FP64) and 1.2e-10 /
+    7e-8 (FP32-mixed) of the terms' magnitudes; the bars are those of the 3^3 case.
+    (2) Conservation: on a periodic mesh the quadrature-weighted sum of every residual
+    variable vanishes for every state and gamma, so lam = the node weights on one variable
+    gives J^T lam = 0 and lam . dL/dgamma = 0.  J^T lam is measured against the same lam with
+    random signs (3e-16 FP64, 1.5e-7 FP32-mixed); the gamma term against the magnitudes of
+    its terms from the oracle.  A dropped or mis-weighted face or volume term breaks both."""
+    torch, dg = env
+    N, nel = 4, 32
+    P = orc.Problem(dim=3, N=N, nel=(nel,) * 3, lo=(0.0,) * 3, hi=(2 * math.pi,) * 3, volume=2, surface=1,
+                    gamma=GAMMA)
+    S = dg.Solver(dg.Mesh(3, N, (nel,) * 3, (0.0,) * 3, (2 * math.pi,) * 3), volume=2, surface=1,
+                  precision=prec, gamma=GAMMA, p_ref=P_TGV if prec else 0.0)
+    xi, w = orc.gll(N)
+    U = wl.perturbed(wl.taylor_green_3d(nel, xi, 0.1, GAMMA), 5, 1e-3).reshape(P.shape)
+    lam = wl.uniform(13, U.size).reshape(U.shape) - 0.5
+    V = (wl.uniform(17, U.size).reshape(U.shape) - 0.5) * np.abs(U)
+    _, JV = orc.rhs_jvp(P, U, V, 0.0)
+    _, Jg = orc.rhs_jvp(P, U, None, 1.0)
+    Ud = dev(torch, U)
+    Ub, g = S.rhs_vjp(Ud, dev(torch, lam))
+    S.check()
+    lhs = float(np.sum(lam * JV))
+    rhs = float(np.sum(Ub.cpu().numpy().reshape(U.shape) * V))
+    scale = float(np.sum(np.abs(lam * JV)))
+    assert abs(lhs - rhs) <= tol * scale, (lhs, rhs, scale)
+    gl = float(np.sum(lam * Jg))
+    assert abs(g - gl) <= gtol * float(np.sum(np.abs(lam * Jg))), (g, gl)
+
+    # node weights, tiled over the elements (nodes of an element contiguous)
+    wt = np.tile(np.einsum("k,j,i->kji", w, w, w).reshape(-1), nel ** 3)
+    for v in range(U.shape[0]):
+        lc = np.zeros_like(U)
+        lc[v] = wt.reshape(U[v].shape)
+        Ubc, gc = S.rhs_vjp(Ud, dev(torch, lc))
+        lr = np.zeros_like(U)
+        lr[v] = (wt * np.sign(wl.uniform(31 + v, wt.size) - 0.5)).reshape(U[v].shape)
+        Ubr, _ = S.rhs_vjp(Ud, dev(torch, lr))
+        S.check()
+        ubc = float(torch.max(torch.abs(Ubc)))
+        ubr = float(torch.max(torch.abs(Ubr)))
+        assert ubr > 0.0 and ubc <= ctol * ubr, (v, ubc, ubr)
+        gscale = float(np.sum(np.abs(lc * Jg)))
+        assert abs(gc) <= cgtol * gscale, (v, gc, gscale)
+    S.close()
+
+
 def test_rk_step_vjp_against_chained_oracle_jvps(env, orc):
     torch, dg = env
     P, S = make(orc, dg, 2, 3, 4, 2, 1)
