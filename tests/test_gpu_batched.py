@@ -87,6 +87,65 @@ def test_batched_matches_oracle(env, orc, prec, tol):
         assert err <= tol, (k, err)
 
 
+# Bars of the full-size test after 10 SSP-RK3 steps: the state and each variable's increment
+# U_10 - U_0 relative to the oracle's.  Measured on B300 over the sampled instances: FP64
+# 5e-16 / 3.4e-13, FP32-mixed 8.3e-8 / 5.2e-5 (the largest on the 96^2, N = 5 instance, whose
+# residual is the smallest against its fluxes); the increment bars are 4x (FP32-mixed) and
+# 30x (FP64) those.
+FULL_BARS = {0: (1e-12, 1e-11), 1: (1e-5, 2e-4)}
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_full_size_set_in_the_timed_configuration(env, orc, prec):
+    """The timed batched workload at full size: 256 seeded instances (8^2..96^2 elements,
+    N in {2..5}), strong form + Rusanov, CFL 0.5, 10 SSP-RK3 steps.  The default batched
+    launch and the autotuner's choice (the configuration the benchmark times) reproduce the
+    per-instance launches bit for bit; sampled instances (the largest and the smallest mesh,
+    the first of each degree) against the oracle."""
+    torch, dg = env
+    specs = wl.batched_vortex_set(256, seed=5)
+    meshes, U = vortex_set(dg, orc, specs)
+    S = dg.Solver(meshes, volume=dg.VOL_STRONG, surface=dg.SURF_RUSANOV, precision=prec, gamma=GAMMA)
+    U0 = torch.from_numpy(U).cuda()
+    S.set_state(U0)
+    dt = S.max_dt(0.5)
+
+    def run():
+        S.set_state(U0)
+        S.rk_step(dt, 10)
+        S.check()
+        return S.get_state().clone()
+
+    S.set_launch(dg.LAUNCH_PER_INSTANCE)
+    ref_pi = run()
+    S.set_launch(dg.LAUNCH_BATCHED, 1, 0, 0)
+    assert torch.equal(run(), ref_pi)
+    S.set_state(U0)
+    cfg, _ = S.autotune(dt, 3)
+    got_t = run()
+    assert torch.equal(got_t, ref_pi), cfg
+    got = got_t.cpu().numpy()
+    nels = [s[0] for s in specs]
+    pick = {int(np.argmax(nels)), int(np.argmin(nels))}
+    for Nd in (2, 3, 4, 5):
+        pick.add(next(i for i, s in enumerate(specs) if s[1] == Nd))
+    st_bar, inc_bar = FULL_BARS[prec]
+    for k in sorted(pick):
+        nel, N, _ = specs[k]
+        P = orc.Problem(dim=2, N=N, nel=(nel, nel), lo=(-5.0, -5.0), hi=(5.0, 5.0), volume=0, surface=0,
+                        gamma=GAMMA)
+        n = nel * nel * (N + 1) ** 2
+        off = S.offsets[k]
+        u0 = U[:, off:off + n].reshape(P.shape)
+        ref = orc.rk3(P, u0, dt, 10)
+        g = got[:, off:off + n].reshape(P.shape)
+        assert np.linalg.norm(g - ref) / np.linalg.norm(ref) <= st_bar, k
+        for v in range(4):
+            d, r = (g - u0)[v], (ref - u0)[v]
+            assert np.linalg.norm(d - r) / np.linalg.norm(r) <= inc_bar, (k, v)
+    S.close()
+
+
 def test_batched_rejects_high_degree_and_autotune_keeps_state(env, orc):
     torch, dg = env
     meshes, U = vortex_set(dg, orc, SPECS[:3] + [(2, 6, (0.0, 0.0))])
