@@ -188,6 +188,49 @@ def test_curved_and_cartesian_instances_in_one_context(env, orc):
     S.close()
 
 
+# Bars of the full-size test, per conserved group (mass, momentum, energy) of the residual on
+# the sampled elements.  The Taylor-Green state is sampled at the Cartesian node positions,
+# so on the warped mesh it is a distorted field whose residual is O(1) in every variable.
+# Measured on B300: FP64 9e-11 / 6.4e-10 / 9e-11 (the background pressure p ~ 71 cancels
+# through the metric terms, whose rounding differs between the two metric computations),
+# FP32-mixed 8.3e-5 / 4.7e-5 / 9.7e-5; the bars are about 8x and 5x those.
+CURVED_FULL_BARS = {0: (1e-9, 5e-9, 1e-9), 1: (5e-4, 3e-4, 5e-4)}
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_full_size_warped_tgv_sampled(env, orc, prec):
+    """The timed curved workload at full size, in its launch configuration: the Mach 0.1
+    Taylor-Green state on a periodically warped 32^3 mesh of [0, 2 pi]^3 (node displacement
+    5% of the box), N = 4, two-point form + HLLC, p_ref of the vortex.  One SSP-RK3 stage
+    (1e-12 FP64, 1e-5 FP32-mixed) and the residual on sampled elements (the box's corners
+    and 40 seeded ones) against the oracle."""
+    torch, dg = env
+    N, n = 4, 32
+    lo, hi = (0.0,) * 3, (2 * math.pi,) * 3
+    xi, _ = orc.gll(N)
+    X = wl.warped_coordinates(3, (n,) * 3, xi, lo, hi, 0.05)
+    U0 = wl.taylor_green_3d(n, xi, 0.1, GAMMA)
+    P = orc.Problem(dim=3, N=N, nel=(n,) * 3, lo=lo, hi=hi, volume=2, surface=1, gamma=GAMMA, coords=X)
+    S = dg.Solver(dg.Mesh(3, N, (n,) * 3, lo, hi, coords=X), volume=2, surface=1, precision=prec,
+                  gamma=GAMMA, p_ref=1.0 / (GAMMA * 0.1 ** 2))
+    corners = [0, n - 1, n * (n - 1), n * n - 1, n ** 3 - 1, n * n * (n - 1), n * n * (n - 1) + n - 1]
+    elems = sorted(set(corners + [int(x * n ** 3) for x in wl.uniform(78, 40)]))
+    L = orc.rhs_elements(P, U0, elems)
+    dt = 1e-3
+    Ud = dev(torch, U0)
+    out = S.rk_stage(1, Ud, Ud, dt)
+    S.check()
+    got = out.cpu().numpy().reshape(U0.shape)[:, elems, :]
+    tol = 1e-12 if prec == 0 else 1e-5
+    assert rel(got, U0[:, elems, :] + dt * L) <= tol
+    Lg = S.rhs(Ud).cpu().numpy().reshape(U0.shape)[:, elems, :]
+    S.check()
+    S.close()
+    for g, bar in zip(([0], [1, 2, 3], [4]), CURVED_FULL_BARS[prec]):
+        e = np.linalg.norm(Lg[g] - L[g]) / np.linalg.norm(L[g])
+        assert e <= bar, (g, e)
+
+
 def test_refused_and_invalid_curved_meshes(env, orc):
     torch, dg = env
     N = 3
