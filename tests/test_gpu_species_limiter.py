@@ -96,6 +96,36 @@ def test_limited_steps_match_oracle(env, orc, scheme, tt):
     S.close()
 
 
+def test_full_size_limited_stage_sampled(env, orc):
+    """The timed limited workload at full size (48^3 elements, N = 3, FP64, the limiter after
+    every stage), with negative partial densities planted at 15% of the nodes: one SSP-RK3
+    stage on sampled elements (the box's corners and 40 seeded ones) against the oracle's
+    residual followed by its limiter, which is element-local and so is applied to the sampled
+    elements alone (as a row of elements)."""
+    torch, dg = env
+    N, nel = 3, 48
+    S, P = setup(orc, dg, N, nel)
+    U = negative_traces(orc, N, nel)
+    dt = 1e-13
+    Ud = dev(torch, U)
+    out = S.rk_stage(1, Ud, Ud, dt)
+    S.check()
+    got_all = out.cpu().numpy().reshape(U.shape)
+    S.close()
+    corners = [0, nel - 1, nel * (nel - 1), nel * nel - 1, nel ** 3 - 1, nel * nel * (nel - 1),
+               nel * nel * (nel - 1) + nel - 1]
+    elems = sorted(set(corners + [int(x * nel ** 3) for x in wl.uniform(81, 40)]))
+    V = U[:, elems, :] + dt * orc.rhs_elements(P, U, elems)
+    assert V[2:5].min() < 0  # the sample has work for the limiter
+    Ps = orc.Problem(dim=3, N=N, nel=(len(elems), 1, 1), lo=(0.0,) * 3, hi=(TWO_PI,) * 3,
+                     equations=orc.NS_REACTING, mech=P.mech, mu=P.mu, prandtl=0.72, species_limiter=1)
+    ref = orc.species_limiter(Ps, V)
+    got = got_all[:, elems, :]
+    assert grouped_rel(got, ref) <= 1e-12
+    assert nonnegative_where_mean_positive(orc, N, got)
+    assert nonnegative_where_mean_positive(orc, N, got_all)
+
+
 def test_fp32_mixed_limited_step(env, orc):
     torch, dg = env
     S, P = setup(orc, dg, 3, 3, precision=dg.FP32_MIXED, p_ref=101325.0)
