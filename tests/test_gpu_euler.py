@@ -275,6 +275,89 @@ def test_tgv_full_size_sampled_stage(orc, dg, torch, prec):
     assert all(e <= b for e, b in zip(err[1:], bars)), err
 
 
+# Per-group residual bars of the largest-mesh test (mass, momentum, energy); measured on B300
+# 6.9e-13 / 8.8e-13 / 6.6e-13 (FP64) and 2.2e-5 / 6.0e-6 / 3.0e-5 (FP32-mixed).
+LARGEST_RESIDUAL = {0: 1e-11, 1: 2e-4}
+
+
+def device_tgv(torch, n, xi, mach, seed):
+    """The Taylor-Green state of [0, 2 pi]^3 on n^3 elements, built on the device (the layout
+    [var][element x-fastest][node i-fastest]) and multiplied node by node by 1 + 1e-3 (r - 1/2),
+    r uniform from a seeded device generator."""
+    N1 = len(xi)
+    h = 2 * math.pi / n
+    a = (torch.arange(n, device="cuda", dtype=torch.float64)[:, None]
+         + (torch.tensor(xi, device="cuda") + 1.0)[None, :] / 2.0) * h
+    X, Y, Z = a.view(1, 1, n, 1, 1, N1), a.view(1, n, 1, 1, N1, 1), a.view(n, 1, 1, N1, 1, 1)
+    shape = (n, n, n, N1, N1, N1)
+    U = torch.empty((5,) + shape, dtype=torch.float64, device="cuda")
+    U[0] = 1.0
+    U[1] = torch.sin(X) * torch.cos(Y) * torch.cos(Z)
+    U[2] = -torch.cos(X) * torch.sin(Y) * torch.cos(Z)
+    U[3] = 0.0
+    p = 1.0 / (GAMMA * mach ** 2) + (torch.cos(2 * X) + torch.cos(2 * Y)) * (torch.cos(2 * Z) + 2.0) / 16.0
+    U[4] = p / (GAMMA - 1.0) + 0.5 * (U[1] ** 2 + U[2] ** 2)
+    del p
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed)
+    for v in range(5):
+        U[v] *= 1.0 + 1e-3 * (torch.rand(shape, generator=gen, device="cuda", dtype=torch.float64) - 0.5)
+    return U.view(5, -1)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_largest_mesh_past_32bit_offsets(orc, dg, torch, prec):
+    """152^3 elements at N = 4 (the Taylor-Green scheme, perturbed): 5 x 439 M = 2.19e9
+    doubles per state, so the offsets of the last variables exceed 2^31.  The residual and one
+    stage on sampled elements (the box's corners and 24 seeded ones) against the oracle.  An
+    element's residual depends on it and its six face neighbours only, so the oracle evaluates
+    it as the centre of a periodic 3^3 mesh of the same spacing holding the element and its
+    neighbours (the other elements copies of the centre), from the device state's samples."""
+    N, n = 4, 152
+    N1 = N + 1
+    xi, _ = orc.gll(N)
+    U = device_tgv(torch, n, xi, 0.1, 11)
+    ne = n ** 3
+    assert U.numel() > 2 ** 31
+    corners = [0, n - 1, n * (n - 1), n * n - 1, ne - 1, n * n * (n - 1), n * n * (n - 1) + n - 1]
+    elems = sorted(set(corners + [int(x * ne) for x in wl.uniform(83, 24)]))
+    Uv = U.view(5, ne, N1 ** 3)
+    h = 2 * math.pi / n
+    Ps = orc.Problem(dim=3, N=N, nel=(3, 3, 3), lo=(0.0,) * 3, hi=(3 * h,) * 3, volume=2, surface=1,
+                     gamma=GAMMA)
+    Lref, Ue = [], []
+    for e in elems:
+        ix, iy, iz = e % n, (e // n) % n, e // (n * n)
+
+        def at(x, y, z):
+            return (x % n) + n * ((y % n) + n * (z % n))
+
+        sub = np.empty((5, 27, N1 ** 3))
+        sub[:] = Uv[:, e, :].cpu().numpy()[:, None, :]
+        for k, en in ((12, at(ix - 1, iy, iz)), (14, at(ix + 1, iy, iz)), (10, at(ix, iy - 1, iz)),
+                      (16, at(ix, iy + 1, iz)), (4, at(ix, iy, iz - 1)), (22, at(ix, iy, iz + 1))):
+            sub[:, k, :] = Uv[:, en, :].cpu().numpy()
+        Lref.append(orc.rhs(Ps, sub)[:, 13, :])
+        Ue.append(sub[:, 13, :])
+    Lref, Ue = np.stack(Lref, axis=1), np.stack(Ue, axis=1)
+    S = dg.Solver(dg.Mesh(3, N, (n,) * 3, (0.0,) * 3, (2 * math.pi,) * 3), volume=2, surface=1, precision=prec,
+                  gamma=GAMMA, p_ref=P_TGV if prec else 0.0)
+    out = S.rhs(U)
+    S.check()
+    Lg = out.view(5, ne, N1 ** 3)[:, elems, :].cpu().numpy()
+    dt = 1e-3
+    S.rk_stage(1, U, U, dt, out=out)
+    S.check()
+    Sg = out.view(5, ne, N1 ** 3)[:, elems, :].cpu().numpy()
+    S.close()
+    del out, U, Uv
+    torch.cuda.empty_cache()
+    tol = 1e-12 if prec == 0 else 1e-5
+    assert rel_l2(Sg, Ue + dt * Lref) <= tol, rel_l2(Sg, Ue + dt * Lref)
+    err = rel_l2_groups(Lg, Lref)
+    assert max(err) <= LARGEST_RESIDUAL[prec], err
+
+
 @pytest.mark.parametrize("kind", [-1, 0, 1, 2])
 @pytest.mark.parametrize("dim", [2, 3])
 @pytest.mark.parametrize("prec", [0, 1])
