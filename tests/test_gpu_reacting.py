@@ -256,6 +256,31 @@ def test_fp32_residual_matches_oracle(env, orc, N, nel):
         assert err <= 1e-6 + fl, (g, err, fl)
 
 
+def test_fp32_full_size_residual_sampled(env, orc):
+    """48^3 elements, N = 3, FP32-mixed with p_ref = 1 atm, in the launch configuration the
+    benchmark times: the residual on sampled elements within 1e-6 plus the FP32 rounding floor
+    above, per group."""
+    torch, dg = env
+    mech = wl.air5_mechanism()
+    mu = wl.reacting_tgv_viscosity(mech)
+    nel, N = 48, 3
+    S, P = setup(orc, dg, N, nel, mech, mu, precision=dg.FP32_MIXED, p_ref=P0)
+    xi, _ = orc.gll(N)
+    U = wl.reacting_tgv_3d(nel, xi, mech)
+    L = S.rhs(dev(torch, U))
+    S.check()
+    rng = np.random.default_rng(1)
+    n_el = nel ** 3
+    elems = np.unique(np.concatenate([[0, n_el - 1, nel - 1, nel * nel - 1], rng.integers(0, n_el, 60)]))
+    ref = orc.rhs_elements(P, U, elems)
+    got = L.cpu().numpy().reshape(U.shape)[:, elems, :]
+    S.close()
+    floors = fp32_floor(orc, mech, U[:, elems, :], ref, N, nel)
+    for g, fl in zip(groups(5), floors):
+        err = np.linalg.norm(got[g] - ref[g]) / np.linalg.norm(ref[g])
+        assert err <= 1e-6 + fl, (g, err, fl)
+
+
 @pytest.mark.parametrize("reactions", [False, True])
 def test_fp32_hundred_steps_match_oracle(env, orc, reactions):
     """100 SSP-RK3 steps in FP32-mixed against the FP64 oracle: rel-L2 <= 1e-5 per group.

@@ -210,6 +210,29 @@ def test_full_size_sampled(env, orc):
     S.close()
 
 
+def test_fp32_full_size_sampled(env, orc):
+    """The same 48^3 workload in FP32-mixed (p_ref = 1 atm), the benchmark's second
+    two-temperature arm: the residual on sampled elements within 1e-6 plus the FP32 rounding
+    floor above, per group."""
+    torch, dg = env
+    N, nel = 3, 48
+    mech = wl.air5_mechanism()
+    S, P = setup(orc, dg, N, nel, mech, wl.reacting_tgv_viscosity(mech), precision=dg.FP32_MIXED, p_ref=P0)
+    xi, _ = orc.gll(N)
+    U = wl.reacting_tgv_3d(nel, xi, mech, two_temperature=True)
+    L = S.rhs(dev(torch, U)).cpu().numpy().reshape(U.shape)
+    S.check()
+    S.close()
+    rng = np.random.default_rng(2)
+    n_el = nel ** 3
+    elems = np.unique(np.concatenate([[0, n_el - 1, nel - 1, nel * nel - 1], rng.integers(0, n_el, 40)]))
+    ref = orc.rhs_elements(P, U, elems)
+    got = L[:, elems, :]
+    for g, fl in zip(GROUPS, fp32_floor(orc, U[:, elems, :], ref, N, nel)):
+        err = np.linalg.norm(got[g] - ref[g]) / np.linalg.norm(ref[g])
+        assert err <= 1e-6 + fl, (g, err, fl)
+
+
 # ---------------------------------------------------------------------------------------
 # the implicit substep with the E_v row and the Strang split
 # ---------------------------------------------------------------------------------------
